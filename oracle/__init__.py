@@ -1,0 +1,248 @@
+"""FP64 CPU oracle for C-A CUR low-rank approximation (ctypes wrapper).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference legs of ``bench.py`` may import this package.
+The CUDA library neither imports nor links it, and this package imports
+nothing from the library: the two meet only through the seeded inputs of
+``lra_inputs``.
+
+Each function states the paper passage it follows (section, algorithm or
+equation label of arXiv:1710.07946); the arithmetic lives in ``lra_oracle.c``.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class _Problem(ct.Structure):
+    _fields_ = [
+        ("src", ct.c_int32), ("dtype", ct.c_int32), ("m", ct.c_int64), ("n", ct.c_int64),
+        ("W", ct.c_void_p), ("ldw", ct.c_int64), ("X", ct.c_void_p), ("Y", ct.c_void_p),
+        ("ell", ct.c_double), ("mkind", ct.c_int32), ("depth", ct.c_int32),
+        ("perm", ct.c_void_p), ("dsign", ct.c_void_p), ("nnz", ct.c_int32),
+        ("srow", ct.c_void_p), ("ssign", ct.c_void_p),
+    ]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ct.CDLL(path)
+        P = ct.POINTER(_Problem)
+        vp, i32, i64, f64 = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_double
+        L.orc_gather_rows.argtypes = [P, vp, i32, vp]
+        L.orc_gather_cols_t.argtypes = [P, vp, i32, vp]
+        L.orc_gather_rows_orig.argtypes = [P, vp, i32, vp]
+        L.orc_maxvol.argtypes = [vp, i32, i64, vp, f64, i32, vp, vp, vp, vp]
+        L.orc_maxvol.restype = ct.c_int
+        L.orc_nucleus.argtypes = [vp, i32, f64, vp]
+        L.orc_nucleus.restype = i32
+        L.orc_ca_run.argtypes = [P, i32, i32, vp, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_ca_run.restype = ct.c_int
+        L.orc_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp]
+        L.orc_residual_sample.argtypes = [P, vp, vp, vp, i32, vp, i32, vp, i32, vp, vp]
+        L.orc_brute_maxvol.argtypes = [vp, i32, i32, vp]
+        L.orc_brute_maxvol.restype = f64
+        L.orc_hadamard_abridged.argtypes = [i64, i32, vp]
+        L.orc_multiplier_dense.argtypes = [P, vp]
+        L.orc_jacobi_svd.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.orc_jacobi_svd.restype = ct.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+class _Marshalled:
+    """Keeps the numpy arrays referenced by a _Problem alive."""
+
+    def __init__(self, p):
+        self.keep = []
+        s = _Problem()
+        s.src, s.m, s.n = int(p.src), int(p.m), int(p.n)
+        if p.W is not None:
+            W = np.ascontiguousarray(p.W)
+            if W.dtype not in (np.float64, np.float32):
+                raise TypeError("dense input must be float64 or float32")
+            self.keep.append(W)
+            s.W, s.ldw = W.ctypes.data, W.shape[1]
+            s.dtype = 1 if W.dtype == np.float32 else 0
+        for name in ("X", "Y"):
+            a = getattr(p, name)
+            if a is not None:
+                a = np.ascontiguousarray(a, dtype=np.float64)
+                self.keep.append(a)
+                setattr(s, name, a.ctypes.data)
+        s.ell = float(p.ell)
+        s.mkind = int(p.mkind)
+        if p.mkind == 1:
+            perm = np.ascontiguousarray(p.perm, dtype=np.int32)
+            ds = np.ascontiguousarray(p.dsign, dtype=np.int8)
+            self.keep += [perm, ds]
+            s.depth, s.perm, s.dsign = int(p.depth), perm.ctypes.data, ds.ctypes.data
+        elif p.mkind == 2:
+            sr = np.ascontiguousarray(p.srow, dtype=np.int32)
+            ss = np.ascontiguousarray(p.ssign, dtype=np.int8)
+            self.keep += [sr, ss]
+            s.nnz, s.srow, s.ssign = int(p.nnz), sr.ctypes.data, ss.ctypes.data
+        self.s = s
+
+    @property
+    def ref(self):
+        return ct.byref(self.s)
+
+
+# ------------------------------------------------------------------ strips
+def gather_rows(p, I):
+    """W'[I,:] with W' = W M (k x n); multiplier columns as in entry_wp()."""
+    I = np.ascontiguousarray(I, dtype=np.int32)
+    mp = _Marshalled(p)
+    out = np.empty((len(I), p.n))
+    lib().orc_gather_rows(mp.ref, _ptr(I), len(I), _ptr(out))
+    return out
+
+
+def gather_cols(p, J):
+    """W'[:,J] (m x k)."""
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    mp = _Marshalled(p)
+    out = np.empty((len(J), p.m))
+    lib().orc_gather_cols_t(mp.ref, _ptr(J), len(J), _ptr(out))
+    return np.ascontiguousarray(out.T)
+
+
+def gather_rows_orig(p, I):
+    """W[I,:] without the multiplier (k x n)."""
+    I = np.ascontiguousarray(I, dtype=np.int32)
+    mp = _Marshalled(p)
+    out = np.empty((len(I), p.n))
+    lib().orc_gather_rows_orig(mp.ref, _ptr(I), len(I), _ptr(out))
+    return out
+
+
+# ------------------------------------------------------------------ maxvol
+def maxvol(A, J_warm=None, h=1.01, max_swaps=1000):
+    """Dominant k x k submatrix of the k x n matrix A (Algorithms algdomin and
+    alggos).  Returns dict(J, C = B^{-1} A, logdet, nswaps, status)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    k, n = A.shape
+    J = np.empty(k, dtype=np.int32)
+    C = np.empty((k, n))
+    ld = ct.c_double()
+    ns = ct.c_int32()
+    Jw = None if J_warm is None else np.ascontiguousarray(J_warm, dtype=np.int32)
+    st = lib().orc_maxvol(_ptr(A), k, n, _ptr(Jw), h, max_swaps, _ptr(J), _ptr(C), ct.byref(ld), ct.byref(ns))
+    return dict(J=J, C=C, logdet=ld.value, nswaps=ns.value, status=st)
+
+
+def brute_maxvol(A):
+    """Exhaustive maximal |det| over all k-subsets of columns (eqvol)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    k, n = A.shape
+    J = np.empty(k, dtype=np.int32)
+    v = lib().orc_brute_maxvol(_ptr(A), k, n, _ptr(J))
+    return J, v
+
+
+# ------------------------------------------------------------------ nucleus
+def nucleus(G, tol=1e-13):
+    """U = pinv of the rank-r QRP truncation of G (Algorithm algcnnncl with
+    Remark reubsc).  Returns (U, r)."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    k = G.shape[0]
+    assert G.shape == (k, k)
+    U = np.empty((k, k))
+    r = lib().orc_nucleus(_ptr(G), k, tol, _ptr(U))
+    return U, r
+
+
+def jacobi_svd(A):
+    """One-sided Jacobi SVD (m >= n): returns (Uo, s, V)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    m, n = A.shape
+    assert m >= n
+    Uo = np.empty((m, n)); s = np.empty(n); V = np.empty((n, n))
+    lib().orc_jacobi_svd(_ptr(A), m, n, _ptr(Uo), _ptr(s), _ptr(V))
+    return Uo, s, V
+
+
+# ------------------------------------------------------------------ C-A
+def ca_run(p, k, sweeps, I0, h=1.01, max_swaps=1000, rank_tol=1e-13):
+    """alpha C-A loops then the canonical nucleus.  Returns dict with I, J,
+    C (m x k) = W'[:,J], U (k x k), R (k x n) = W[I,:], logvol (2*sweeps),
+    rank, swaps, loops, status."""
+    mp = _Marshalled(p)
+    I0 = np.ascontiguousarray(I0, dtype=np.int32)
+    assert len(I0) == k
+    I = np.empty(k, dtype=np.int32); J = np.empty(k, dtype=np.int32)
+    C = np.empty((p.m, k)); U = np.empty((k, k)); R = np.empty((k, p.n))
+    lv = np.empty(2 * sweeps); info = np.empty(4, dtype=np.int32)
+    lib().orc_ca_run(mp.ref, k, sweeps, _ptr(I0), h, max_swaps, rank_tol, _ptr(I), _ptr(J), _ptr(C), _ptr(U),
+                     _ptr(R), _ptr(lv), _ptr(info))
+    return dict(I=I, J=J, C=C, U=U, R=R, logvol=lv, rank=int(info[0]), swaps=int(info[1]),
+                loops=int(info[2]), status=int(info[3]))
+
+
+def cur_apply(C, U, R, X):
+    """Y = C (U (R X)) in FP64 (FMM stage iii product with the generators)."""
+    C = np.ascontiguousarray(C, dtype=np.float64); U = np.ascontiguousarray(U, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64); X = np.ascontiguousarray(X, dtype=np.float64)
+    m, k = C.shape
+    n = R.shape[1]
+    if X.ndim == 1:
+        X = X[:, None]
+    Y = np.empty((m, X.shape[1]))
+    lib().orc_cur_apply(_ptr(C), _ptr(U), _ptr(R), m, n, k, _ptr(X), X.shape[1], _ptr(Y))
+    return Y
+
+
+def residual_sample(p, C, U, R, Q, S, return_E=False):
+    """Statistics of the q x s sample E[Q,S] of E = W - C U R (a-posteriori
+    estimation from a random submatrix): [mean, var, mean|e|, max|e|, fro ratio]."""
+    mp = _Marshalled(p)
+    C = np.ascontiguousarray(C, dtype=np.float64); U = np.ascontiguousarray(U, dtype=np.float64)
+    R = np.ascontiguousarray(R, dtype=np.float64)
+    Q = np.ascontiguousarray(Q, dtype=np.int32); S = np.ascontiguousarray(S, dtype=np.int32)
+    k = C.shape[1]
+    stats = np.empty(5)
+    E = np.empty((len(Q), len(S))) if return_E else None
+    lib().orc_residual_sample(mp.ref, _ptr(C), _ptr(U), _ptr(R), k, _ptr(Q), len(Q), _ptr(S), len(S),
+                              _ptr(stats), _ptr(E))
+    return (stats, E) if return_E else stats
+
+
+# ------------------------------------------------------------------ multipliers
+def hadamard_abridged(n, d):
+    """Dense H_{n,d} from the recursion eqrfd with H_s = I_s."""
+    H = np.empty((n, n))
+    lib().orc_hadamard_abridged(n, d, _ptr(H))
+    return H
+
+
+def multiplier_dense(p):
+    """Dense n x n multiplier M of the problem (ARHT or sparse +-1)."""
+    mp = _Marshalled(p)
+    M = np.empty((p.n, p.n))
+    lib().orc_multiplier_dense(mp.ref, _ptr(M))
+    return M
+
+
+def ca_run_blocks(p, blocks, k_max, sweeps, I0s, h=1.01, max_swaps=1000, rank_tol=1e-6):
+    """Independent C-A runs over the submatrices W[r0:r0+nr, c0:c0+nc] of a
+    kernel problem (the generators of the neutered block columns of an
+    HSS / FMM matrix).  Returns a list of ca_run results."""
+    from lra_inputs import Problem
+    out = []
+    for b, (r0, nr, c0, nc) in enumerate(np.asarray(blocks)):
+        sub = Problem(p.src, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], ell=p.ell)
+        k = min(k_max, int(nr), int(nc))
+        out.append(ca_run(sub, k, sweeps, I0s[b][:k], h, max_swaps, rank_tol))
+    return out

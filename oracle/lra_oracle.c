@@ -1,0 +1,669 @@
+/*
+ * lra_oracle.c -- plain, slow, FP64 CPU oracle for cross-approximation (C-A)
+ * CUR low-rank approximation, written from "Superfast Accurate Low Rank
+ * Approximation" (Pan, Luan, Svadlenka, Zhao, arXiv:1710.07946).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no code, header or constant with
+ * the CUDA path.
+ *
+ * Everything is FP64, single-threaded, written for a reader to check against
+ * the paper by eye: no blocking, no fusion, no reordering.  Where a floating
+ * point result feeds a discrete decision (an argmax), the operation order is
+ * fixed as stated in each function so that an independent implementation can
+ * reproduce the decision: every dot product is an ascending-index chain of
+ * correctly rounded fma(), every division is one IEEE division, ties in an
+ * argmax go to the lowest index.  Build with -ffp-contract=off.
+ *
+ * Paper passages followed (section / algorithm / equation names are the
+ * paper's LaTeX labels):
+ *   - C-A iterations: Section "CUR LRA; primitive, cynical, and
+ *     cross-approximation algorithms" and the Tests 2 set-up of Section
+ *     "Tests ..." (random initial rows, horizontal step then vertical step).
+ *   - Dominant submatrix (maxvol): Algorithm "Computing a dominant submatrix"
+ *     (algdomin) with its LUP initialisation, Algorithm "An iterative C-A
+ *     algorithm by means of recursive LUP factorization" (alggos).
+ *   - Nucleus: Algorithm "Canonical computation of a nucleus" (algcnnncl),
+ *     with a rank-revealing QR in place of the SVD as Remark reubsc allows.
+ *   - Abridged Hadamard multiplier: Appendix "Abridged Hadamard and Fourier
+ *     Multipliers", equations eqrfd / eqbschf, randomised as D H P.
+ *   - Sparse +-1 multiplier: Section "Pre-processing with quasi Gaussian
+ *     matrices", case (i).
+ *   - Back-transform of a pre-processed CUR: Algorithm alglratpsvd1, stage 4
+ *     (R = R_H H^+, which is W[I,:] for an orthogonal multiplier).
+ *   - Sampled a-posteriori error: Section "Superfast a posteriori error
+ *     estimation for LRA of a matrix filled with i.i.d. values".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Problem description (the oracle's own; not shared with the library) */
+/* ------------------------------------------------------------------ */
+enum { ORC_DENSE = 0, ORC_LAPLACE = 1, ORC_GAUSSIAN = 2 };
+enum { ORC_F64 = 0, ORC_F32 = 1 };
+enum { ORC_MULT_NONE = 0, ORC_MULT_ARHT = 1, ORC_MULT_SPARSE = 2 };
+
+typedef struct {
+  int32_t src;          /* ORC_DENSE / ORC_LAPLACE / ORC_GAUSSIAN            */
+  int32_t dtype;        /* dense storage type: ORC_F64 or ORC_F32             */
+  int64_t m, n;         /* matrix size                                        */
+  const void* W;        /* dense: row-major, leading dimension ldw            */
+  int64_t ldw;
+  const double* X;      /* kernel: m target points, xyz interleaved (m x 3)   */
+  const double* Y;      /* kernel: n source points (n x 3)                    */
+  double ell;           /* Gaussian length scale                              */
+  int32_t mkind;        /* multiplier kind                                    */
+  int32_t depth;        /* ARHT recursion depth d (n = 2^d s)                 */
+  const int32_t* perm;  /* ARHT permutation P: column j of H P = column perm[j] of H */
+  const int8_t* dsign;  /* ARHT diagonal D: +-1, length n                     */
+  int32_t nnz;          /* sparse: nonzeros per column                        */
+  const int32_t* srow;  /* sparse: n*nnz row indices, ascending per column    */
+  const int8_t* ssign;  /* sparse: n*nnz signs (+-1)                          */
+} orc_problem;
+
+/* Entry w_ij of the input W (no multiplier).  Kernel entries follow the
+ * closed forms: Laplace 1/|x-y|, Gaussian exp(-|x-y|^2 / (2 l^2)). */
+static double entry_w(const orc_problem* p, int64_t i, int64_t j) {
+  if (p->src == ORC_DENSE) {
+    if (p->dtype == ORC_F32) return (double)((const float*)p->W)[i * p->ldw + j];
+    return ((const double*)p->W)[i * p->ldw + j];
+  }
+  const double* x = p->X + 3 * i;
+  const double* y = p->Y + 3 * j;
+  double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+  double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+  if (p->src == ORC_LAPLACE) return 1.0 / sqrt(r2);
+  return exp(-(r2 / (2.0 * p->ell * p->ell)));
+}
+
+/* 2^(-d/2): the scale that makes the abridged Hadamard matrix orthogonal
+ * ("orthogonal up to scaling", appendix on abridged multipliers). */
+static double arht_scale(int d) { return 1.0 / sqrt((double)(1LL << d)); }
+
+static int popcount32(uint32_t v) { int c = 0; while (v) { c += (int)(v & 1u); v >>= 1; } return c; }
+
+/* Entry w'_ij of the pre-processed matrix W' = W M.
+ * ARHT: M = 2^(-d/2) D H_{n,d} P with H_{n,d} = H_{2^d} (x) I_s, n = 2^d s
+ *   (recursion eqrfd cut at depth d with H_s = I_s).  With perm[j] = b s + t,
+ *   column j of M holds 2^d nonzeros, at rows a s + t, a = 0..2^d-1, equal to
+ *   2^(-d/2) D_{a s + t} (-1)^{popcount(a & b)}.  The 2^d terms are summed in
+ *   ascending a, then scaled once.
+ * Sparse +-1: column j of M holds nnz entries +-1/2 (for nnz = 4; in general
+ *   +-1/sqrt(nnz)) at rows srow[j*nnz + t]; summed in ascending t, scaled once. */
+static double entry_wp(const orc_problem* p, int64_t i, int64_t j) {
+  if (p->mkind == ORC_MULT_NONE) return entry_w(p, i, j);
+  if (p->mkind == ORC_MULT_ARHT) {
+    int64_t s = p->n >> p->depth;
+    int64_t pj = p->perm[j];
+    int64_t b = pj / s, t = pj % s;
+    double acc = 0.0;
+    for (int64_t a = 0; a < (1LL << p->depth); ++a) {
+      int64_t r = a * s + t;
+      double v = entry_w(p, i, r) * (double)p->dsign[r];
+      if (popcount32((uint32_t)(a & b)) & 1) acc = acc - v; else acc = acc + v;
+    }
+    return acc * arht_scale(p->depth);
+  }
+  /* sparse */
+  double acc = 0.0;
+  for (int t = 0; t < p->nnz; ++t) {
+    int64_t r = p->srow[j * p->nnz + t];
+    double v = entry_w(p, i, r);
+    if (p->ssign[j * p->nnz + t] < 0) acc = acc - v; else acc = acc + v;
+  }
+  return acc * (1.0 / sqrt((double)p->nnz));
+}
+
+/* Row strip W'[I,:] (k x n, row-major). */
+void orc_gather_rows(const orc_problem* p, const int32_t* I, int32_t k, double* out) {
+  for (int32_t a = 0; a < k; ++a)
+    for (int64_t j = 0; j < p->n; ++j) out[(int64_t)a * p->n + j] = entry_wp(p, I[a], j);
+}
+
+/* Column strip W'[:,J], stored transposed: out[a*m + i] = W'[i, J[a]]. */
+void orc_gather_cols_t(const orc_problem* p, const int32_t* J, int32_t k, double* out) {
+  for (int32_t a = 0; a < k; ++a)
+    for (int64_t i = 0; i < p->m; ++i) out[(int64_t)a * p->m + i] = entry_wp(p, i, J[a]);
+}
+
+/* Original rows W[I,:] (no multiplier), k x n. */
+void orc_gather_rows_orig(const orc_problem* p, const int32_t* I, int32_t k, double* out) {
+  for (int32_t a = 0; a < k; ++a)
+    for (int64_t j = 0; j < p->n; ++j) out[(int64_t)a * p->n + j] = entry_w(p, I[a], j);
+}
+
+/* ------------------------------------------------------------------ */
+/* Maxvol on a k x n strip (dominant k x k submatrix)                  */
+/* ------------------------------------------------------------------ */
+enum { ORC_OK = 0, ORC_WARN_RANK_DEFICIENT = 16, ORC_WARN_NOT_CONVERGED = 17 };
+
+/*
+ * orc_maxvol: find k columns J of the k x n matrix A (row-major) whose k x k
+ * submatrix B = A[:,J] is dominant (every entry of B^{-1} A bounded by h).
+ *
+ * Initialisation (Algorithm alggos, stages 1-2):
+ *   cold  (Jwarm == NULL): LU factorisation with column pivoting, A P^T = L (U0 | U1).
+ *         At elimination step t the pivot column is the unchosen column with the
+ *         largest |A(t)[t, q]| (lowest q on ties); rows t+1.. are eliminated with
+ *         multipliers l_p = A(t)[p, j_t] / A(t)[t, j_t] and
+ *         A[p][q] <- fma(-l_p, A[t][q], A[p][q]) over the unchosen columns q.
+ *   warm  (Jwarm given, C-A sweeps after the first): the same elimination with the
+ *         pivot columns forced to Jwarm[0..k-1] in order and partial pivoting over
+ *         rows (pivot row = largest |A(t)[p, j_t]|, p >= t, lowest p on ties;
+ *         rows t and that row are exchanged across the whole strip).
+ *   Then C = Bbar^{-1} A = (I | U0^{-1} U1) in the original column order: each
+ *   unchosen column is solved by back substitution with U0 in descending row
+ *   order, each inner product an ascending fma chain; column J[i] of C is e_i.
+ * Swaps (Algorithm algdomin, stages 1-2): take the entry of largest |C[i][j]|
+ *   over i < k and j not in J, ties to the lowest j then the lowest i.  Stop when
+ *   it is <= h.  Otherwise J[i*] <- j* and C is updated in place to the new
+ *   B^{-1} A: with c* = C[i*][j*] and the old column x = C[:, j*],
+ *   for every column q:  t_q = C[i*][q] / c*;  C[i*][q] = t_q;
+ *   C[p][q] = fma(-x[p], t_q, C[p][q]) for p != i*.
+ *   |det B| is multiplied by |c*| at each swap (strict volume increase for h >= 1).
+ * Outputs: J (position i of J is row i of C), C (k x n) if Cout != NULL,
+ *   logdet = log|det A[:,J]| (LU diagonal at init, + log|c*| per swap), number of
+ *   swaps; the status is ORC_WARN_RANK_DEFICIENT if a zero pivot was met (no
+ *   swaps are then made) and ORC_WARN_NOT_CONVERGED if max_swaps stopped the loop.
+ *   A zero warm pivot falls back to the cold start.
+ */
+int orc_maxvol(const double* A, int32_t k, int64_t n, const int32_t* Jwarm, double h, int32_t max_swaps,
+               int32_t* J, double* Cout, double* logdet_out, int32_t* nswaps_out) {
+  double* M = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
+  double* U0 = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+  double* x = (double*)malloc(sizeof(double) * (size_t)k);
+  unsigned char* chosen = (unsigned char*)calloc((size_t)n, 1);
+  int status = ORC_OK;
+  int warm = (Jwarm != NULL);
+  double logdet = 0.0;
+
+restart:
+  memcpy(M, A, sizeof(double) * (size_t)k * (size_t)n);
+  memset(chosen, 0, (size_t)n);
+  logdet = 0.0;
+  status = ORC_OK;
+  for (int32_t t = 0; t < k; ++t) {
+    int64_t jt;
+    if (!warm) {
+      double bv = -1.0; jt = -1;
+      for (int64_t q = 0; q < n; ++q)
+        if (!chosen[q] && fabs(M[t * n + q]) > bv) { bv = fabs(M[t * n + q]); jt = q; }
+    } else {
+      jt = Jwarm[t];
+      int32_t r = t; double bv = fabs(M[(int64_t)t * n + jt]);
+      for (int32_t p = t + 1; p < k; ++p)
+        if (fabs(M[(int64_t)p * n + jt]) > bv) { bv = fabs(M[(int64_t)p * n + jt]); r = p; }
+      if (r != t)
+        for (int64_t q = 0; q < n; ++q) { double tmp = M[(int64_t)t * n + q]; M[(int64_t)t * n + q] = M[(int64_t)r * n + q]; M[(int64_t)r * n + q] = tmp; }
+    }
+    J[t] = (int32_t)jt;
+    chosen[jt] = 1;
+    double piv = M[(int64_t)t * n + jt];
+    if (piv == 0.0) {
+      if (warm) { warm = 0; goto restart; }
+      status = ORC_WARN_RANK_DEFICIENT;
+      continue;                       /* nothing to eliminate with */
+    }
+    logdet += log(fabs(piv));
+    for (int32_t p = t + 1; p < k; ++p) {
+      double l = M[(int64_t)p * n + jt] / piv;
+      for (int64_t q = 0; q < n; ++q)
+        if (!chosen[q]) M[(int64_t)p * n + q] = fma(-l, M[(int64_t)t * n + q], M[(int64_t)p * n + q]);
+    }
+  }
+  if (status == ORC_WARN_RANK_DEFICIENT) {
+    if (Cout) memset(Cout, 0, sizeof(double) * (size_t)k * (size_t)n);
+    *logdet_out = -INFINITY; *nswaps_out = 0;
+    free(M); free(U0); free(x); free(chosen);
+    return status;
+  }
+  /* U0[s][t] = final row s of pivot column J[t], s <= t */
+  for (int32_t s = 0; s < k; ++s)
+    for (int32_t t = 0; t < k; ++t) U0[s * k + t] = (s <= t) ? M[(int64_t)s * n + J[t]] : 0.0;
+  /* C = (I | U0^{-1} U1) in original column order; reuse M column by column */
+  for (int64_t q = 0; q < n; ++q) {
+    if (chosen[q]) continue;
+    for (int32_t i = k - 1; i >= 0; --i) {
+      double s = M[(int64_t)i * n + q];
+      for (int32_t p = i + 1; p < k; ++p) s = fma(-U0[i * k + p], x[p], s);
+      x[i] = s / U0[i * k + i];
+    }
+    for (int32_t i = 0; i < k; ++i) M[(int64_t)i * n + q] = x[i];
+  }
+  for (int32_t t = 0; t < k; ++t)
+    for (int32_t i = 0; i < k; ++i) M[(int64_t)i * n + J[t]] = (i == t) ? 1.0 : 0.0;
+
+  /* dominance swaps */
+  int32_t nsw = 0;
+  for (;;) {
+    double bv = -1.0; int64_t bj = -1; int32_t bi = -1;
+    for (int64_t q = 0; q < n; ++q) {
+      if (chosen[q]) continue;
+      for (int32_t i = 0; i < k; ++i)
+        if (fabs(M[(int64_t)i * n + q]) > bv) { bv = fabs(M[(int64_t)i * n + q]); bj = q; bi = i; }
+    }
+    if (bj < 0 || !(bv > h)) break;
+    if (nsw >= max_swaps) { status = ORC_WARN_NOT_CONVERGED; break; }
+    double cs = M[(int64_t)bi * n + bj];
+    for (int32_t p = 0; p < k; ++p) x[p] = M[(int64_t)p * n + bj];
+    for (int64_t q = 0; q < n; ++q) {
+      double tq = M[(int64_t)bi * n + q] / cs;
+      M[(int64_t)bi * n + q] = tq;
+      for (int32_t p = 0; p < k; ++p)
+        if (p != bi) M[(int64_t)p * n + q] = fma(-x[p], tq, M[(int64_t)p * n + q]);
+    }
+    chosen[J[bi]] = 0;
+    chosen[bj] = 1;
+    J[bi] = (int32_t)bj;
+    logdet += log(fabs(cs));
+    ++nsw;
+  }
+  if (Cout) memcpy(Cout, M, sizeof(double) * (size_t)k * (size_t)n);
+  *logdet_out = logdet;
+  *nswaps_out = nsw;
+  free(M); free(U0); free(x); free(chosen);
+  return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* Nucleus: U = pseudo-inverse of the rank-r truncation of G (k x k)   */
+/* ------------------------------------------------------------------ */
+
+/* Householder reflector on x[0..len-1] (stride str) in the textbook form
+ * H = I - tau v v^T, v[0] = 1, H x = beta e_1 (Golub & Van Loan, Sec. 5.1).
+ * Returns tau; writes beta into x[0] and v[1..] into x[1..]. */
+static double house(double* x, int len, int str) {
+  double alpha = x[0];
+  double xn2 = 0.0;
+  for (int i = 1; i < len; ++i) xn2 = fma(x[i * str], x[i * str], xn2);
+  if (xn2 == 0.0) return 0.0;
+  double nrm = sqrt(fma(alpha, alpha, xn2));
+  double beta = (alpha >= 0.0) ? -nrm : nrm;
+  double tau = (beta - alpha) / beta;
+  double scal = 1.0 / (alpha - beta);
+  for (int i = 1; i < len; ++i) x[i * str] = x[i * str] * scal;
+  x[0] = beta;
+  return tau;
+}
+
+/* Apply H = I - tau v v^T (v[0] = 1 implicit, v[1..] at vv[1..], stride vs)
+ * from the left to column segment y[0..len-1] (stride ys). */
+static void apply_house(const double* vv, int vs, double tau, double* y, int len, int ys) {
+  if (tau == 0.0) return;
+  double w = y[0];
+  for (int i = 1; i < len; ++i) w = fma(vv[i * vs], y[i * ys], w);
+  double c = tau * w;
+  y[0] = y[0] - c;
+  for (int i = 1; i < len; ++i) y[i * ys] = fma(-c, vv[i * vs], y[i * ys]);
+}
+
+/*
+ * orc_nucleus: Algorithm algcnnncl with a rank-revealing factorisation in place
+ * of the SVD (Remark reubsc).
+ *   1. Householder QR with column pivoting (Businger-Golub): G P = Q R; at step t
+ *      the column with the largest remaining squared norm (rows t.., recomputed,
+ *      ascending fma chain) is moved to position t, lowest index on ties.
+ *   2. Numerical rank r = number of leading |R_tt| > tol |R_00|.
+ *   3. U = pinv(G_r) for the truncation G_r = Q_r [R11 R12] P^T: with
+ *      T = [R11 R12] (r x k) and the QR factorisation T^T = Z S,
+ *      pinv(G_r) = P Z S^{-T} Q_r^T (complete orthogonal decomposition;
+ *      equals P R^{-1} Q^T when r = k).
+ * G and U are k x k row-major; U[j][i] maps row i of W'[:,J] ... i.e. U is the
+ * l x k nucleus with l = k.  Returns r.
+ */
+int32_t orc_nucleus(const double* G, int32_t k, double tol, double* U) {
+  /* column-major working copy: A[col*k + row] */
+  double* A = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+  double* taus = (double*)malloc(sizeof(double) * (size_t)k);
+  int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  for (int32_t i = 0; i < k; ++i)
+    for (int32_t j = 0; j < k; ++j) A[j * k + i] = G[i * k + j];
+  for (int32_t j = 0; j < k; ++j) perm[j] = j;
+  for (int32_t t = 0; t < k; ++t) {
+    int32_t pj = t; double bn = -1.0;
+    for (int32_t j = t; j < k; ++j) {
+      double s = 0.0;
+      for (int32_t i = t; i < k; ++i) s = fma(A[j * k + i], A[j * k + i], s);
+      if (s > bn) { bn = s; pj = j; }
+    }
+    if (pj != t) {
+      for (int32_t i = 0; i < k; ++i) { double tmp = A[t * k + i]; A[t * k + i] = A[pj * k + i]; A[pj * k + i] = tmp; }
+      int32_t tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp;
+    }
+    taus[t] = house(&A[t * k + t], k - t, 1);
+    for (int32_t j = t + 1; j < k; ++j) apply_house(&A[t * k + t], 1, taus[t], &A[j * k + t], k - t, 1);
+  }
+  int32_t r = 0;
+  double r00 = fabs(A[0]);
+  if (r00 > 0.0)
+    while (r < k && fabs(A[r * k + r]) > tol * r00) ++r;
+
+  memset(U, 0, sizeof(double) * (size_t)k * (size_t)k);
+  if (r == 0) { free(A); free(taus); free(perm); return 0; }
+
+  /* Qt = Q^T = H_{k-1} ... H_0 applied to I  (column-major, k x k) */
+  double* Qt = (double*)calloc((size_t)k * (size_t)k, sizeof(double));
+  for (int32_t i = 0; i < k; ++i) Qt[i * k + i] = 1.0;
+  for (int32_t t = 0; t < k; ++t)
+    for (int32_t j = 0; j < k; ++j) apply_house(&A[t * k + t], 1, taus[t], &Qt[j * k + t], k - t, 1);
+
+  /* T^T (k x r, column-major: column c = row c of T = R[c][0..k-1]) and its QR */
+  double* Tt = (double*)calloc((size_t)k * (size_t)r, sizeof(double));
+  double* tz = (double*)malloc(sizeof(double) * (size_t)r);
+  for (int32_t c = 0; c < r; ++c)
+    for (int32_t i = c; i < k; ++i) Tt[c * k + i] = A[i * k + c];
+  if (r < k) {
+    for (int32_t c = 0; c < r; ++c) {
+      tz[c] = house(&Tt[c * k + c], k - c, 1);
+      for (int32_t j = c + 1; j < r; ++j) apply_house(&Tt[c * k + c], 1, tz[c], &Tt[j * k + c], k - c, 1);
+    }
+  } else {
+    for (int32_t c = 0; c < r; ++c) tz[c] = 0.0;   /* T^T is already lower -> use R directly */
+  }
+  /* X (k x k column-major) = Z S^{-T} Q_r^T.
+   * For r = k: S^T = R^T... handle uniformly: when r == k we take Z = I and
+   * S = R^T (T^T = R^T is lower triangular), i.e. solve S^T V = Q_r^T with
+   * S^T = R upper triangular by back substitution. */
+  double* X = (double*)calloc((size_t)k * (size_t)k, sizeof(double));
+  for (int32_t col = 0; col < k; ++col) {
+    /* right-hand side: column col of Q_r^T = (Qt[col*k + 0..r-1]) */
+    double* v = &X[col * k];
+    if (r == k) {
+      /* solve R v = Qt[:,col] (back substitution, descending rows) */
+      for (int32_t i = k - 1; i >= 0; --i) {
+        double s = Qt[col * k + i];
+        for (int32_t p = i + 1; p < k; ++p) s = fma(-A[p * k + i], v[p], s);
+        v[i] = s / A[i * k + i];
+      }
+    } else {
+      /* S is r x r upper triangular in Tt (S[i][c] = Tt[c*k + i], i <= c);
+       * solve S^T v = Qt[0..r-1, col] by forward substitution */
+      for (int32_t i = 0; i < r; ++i) {
+        double s = Qt[col * k + i];
+        for (int32_t p = 0; p < i; ++p) s = fma(-Tt[i * k + p], v[p], s);
+        v[i] = s / Tt[i * k + i];
+      }
+      /* v (length k, zeros below r) <- Z v = H'_0 ... H'_{r-1} v */
+      for (int32_t c = r - 1; c >= 0; --c) apply_house(&Tt[c * k + c], 1, tz[c], &v[c], k - c, 1);
+    }
+  }
+  /* U = P X: row perm[i] of U is row i of X */
+  for (int32_t i = 0; i < k; ++i)
+    for (int32_t col = 0; col < k; ++col) U[(int64_t)perm[i] * k + col] = X[col * k + i];
+  free(A); free(taus); free(perm); free(Qt); free(Tt); free(tz); free(X);
+  return r;
+}
+
+/* ------------------------------------------------------------------ */
+/* C-A iterations                                                      */
+/* ------------------------------------------------------------------ */
+/*
+ * orc_ca_run: alpha C-A loops; each loop is a horizontal step (maxvol over the
+ * columns of the k x n row strip W'[I,:] -> J) followed by a vertical step
+ * (maxvol over the rows of the m x k column strip W'[:,J] -> I), as in the
+ * Tests 2 schedule.  Loop 1 starts from the caller's rows I0 with a cold
+ * column step; every later step is warm-started from the current set, so
+ * |det W'[I,J]| never decreases.  The loop stops early when a whole loop made
+ * no swap.  Outputs:
+ *   I, J            final index sets (k each, in pivot-position order)
+ *   C (m x k)       W'[:,J] row-major;  R (k x n) W[I,:] (original rows, the
+ *                   back-transform of Algorithm alglratpsvd1 stage 4)
+ *   U (k x k)       nucleus of G = W'[I,J] at relative tolerance rank_tol
+ *   logvol[2*alpha] log|det W'[I,J]| after every step (unused slots NaN)
+ *   info[4]         {rank, total swaps, loops run, status}
+ */
+int orc_ca_run(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I0, double h, int32_t max_swaps,
+               double rank_tol, int32_t* I, int32_t* J, double* C, double* U, double* R, double* logvol,
+               int32_t* info) {
+  int64_t m = p->m, n = p->n;
+  double* Rs = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
+  double* Cs = (double*)malloc(sizeof(double) * (size_t)k * (size_t)m);
+  double* G = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+  int32_t* Jn = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  int32_t* In = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  int status = ORC_OK, total = 0, loops = 0;
+  memcpy(I, I0, sizeof(int32_t) * (size_t)k);
+  for (int32_t s = 0; s < 2 * sweeps; ++s) logvol[s] = NAN;
+  for (int32_t s = 0; s < sweeps; ++s) {
+    double ld; int32_t nsw1 = 0, nsw2 = 0;
+    orc_gather_rows(p, I, k, Rs);
+    int st = orc_maxvol(Rs, k, n, s == 0 ? NULL : J, h, max_swaps, Jn, NULL, &ld, &nsw1);
+    if (st > status) status = st;
+    memcpy(J, Jn, sizeof(int32_t) * (size_t)k);
+    logvol[2 * s] = ld;
+    orc_gather_cols_t(p, J, k, Cs);
+    st = orc_maxvol(Cs, k, m, I, h, max_swaps, In, NULL, &ld, &nsw2);
+    if (st > status) status = st;
+    memcpy(I, In, sizeof(int32_t) * (size_t)k);
+    logvol[2 * s + 1] = ld;
+    total += nsw1 + nsw2;
+    loops = s + 1;
+    if (s > 0 && nsw1 == 0 && nsw2 == 0) break;
+  }
+  /* outputs: C = W'[:,J] (transpose of the last column strip, which used the final J) */
+  for (int64_t i = 0; i < m; ++i)
+    for (int32_t a = 0; a < k; ++a) C[i * k + a] = Cs[(int64_t)a * m + i];
+  orc_gather_rows_orig(p, I, k, R);
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t b = 0; b < k; ++b) G[a * k + b] = C[(int64_t)I[a] * k + b];
+  int32_t r = orc_nucleus(G, k, rank_tol, U);
+  if (r < k && status == ORC_OK) status = ORC_WARN_RANK_DEFICIENT;
+  info[0] = r; info[1] = total; info[2] = loops; info[3] = status;
+  free(Rs); free(Cs); free(G); free(Jn); free(In);
+  return status;
+}
+
+/* ------------------------------------------------------------------ */
+/* CUR apply and sampled residual                                      */
+/* ------------------------------------------------------------------ */
+/* Y = C (U (R X)): C m x k, U k x k, R k x n, X n x nrhs, Y m x nrhs, all
+ * row-major; each inner product an ascending fma chain. */
+void orc_cur_apply(const double* C, const double* U, const double* R, int64_t m, int64_t n, int32_t k,
+                   const double* X, int32_t nrhs, double* Y) {
+  double* T1 = (double*)malloc(sizeof(double) * (size_t)k * (size_t)nrhs);
+  double* T2 = (double*)malloc(sizeof(double) * (size_t)k * (size_t)nrhs);
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t c = 0; c < nrhs; ++c) {
+      double s = 0.0;
+      for (int64_t j = 0; j < n; ++j) s = fma(R[(int64_t)a * n + j], X[j * nrhs + c], s);
+      T1[a * nrhs + c] = s;
+    }
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t c = 0; c < nrhs; ++c) {
+      double s = 0.0;
+      for (int32_t b = 0; b < k; ++b) s = fma(U[a * k + b], T1[b * nrhs + c], s);
+      T2[a * nrhs + c] = s;
+    }
+  for (int64_t i = 0; i < m; ++i)
+    for (int32_t c = 0; c < nrhs; ++c) {
+      double s = 0.0;
+      for (int32_t a = 0; a < k; ++a) s = fma(C[i * k + a], T2[a * nrhs + c], s);
+      Y[i * nrhs + c] = s;
+    }
+  free(T1); free(T2);
+}
+
+/*
+ * orc_residual_sample: the q x s submatrix E[Q,S] of E = W - C U R (rows Q,
+ * columns S given), and its statistics
+ *   stats[0] mean of e,  stats[1] variance (1/K) sum (e - mean)^2,
+ *   stats[2] mean of |e|, stats[3] max |e| (Chebyshev norm of the sample),
+ *   stats[4] ||E[Q,S]||_F / ||W[Q,S]||_F (Frobenius-ratio estimate).
+ * The paper tests the sample mean and variance of K = qs >= 100 i.i.d.
+ * entries; the sums here run in ascending (row, column) order.
+ * E (q x s) is written if Eout != NULL.
+ */
+void orc_residual_sample(const orc_problem* p, const double* C, const double* U, const double* R, int32_t k,
+                         const int32_t* Q, int32_t q, const int32_t* S, int32_t s, double* stats, double* Eout) {
+  double* cu = (double*)malloc(sizeof(double) * (size_t)k);
+  double* e = (double*)malloc(sizeof(double) * (size_t)q * (size_t)s);
+  int64_t n = p->n;
+  double sw2 = 0.0;
+  for (int32_t a = 0; a < q; ++a) {
+    /* row Q[a] of C U */
+    for (int32_t b = 0; b < k; ++b) {
+      double t = 0.0;
+      for (int32_t c = 0; c < k; ++c) t = fma(C[(int64_t)Q[a] * k + c], U[c * k + b], t);
+      cu[b] = t;
+    }
+    for (int32_t c = 0; c < s; ++c) {
+      double t = 0.0;
+      for (int32_t b = 0; b < k; ++b) t = fma(cu[b], R[(int64_t)b * n + S[c]], t);
+      double w = entry_w(p, Q[a], S[c]);
+      e[(int64_t)a * s + c] = w - t;
+      sw2 = fma(w, w, sw2);
+    }
+  }
+  double K = (double)q * (double)s;
+  double sum = 0.0, sabs = 0.0, mx = 0.0, se2 = 0.0;
+  for (int64_t t = 0; t < (int64_t)q * s; ++t) {
+    sum += e[t]; sabs += fabs(e[t]); se2 = fma(e[t], e[t], se2);
+    if (fabs(e[t]) > mx) mx = fabs(e[t]);
+  }
+  double mean = sum / K, var = 0.0;
+  for (int64_t t = 0; t < (int64_t)q * s; ++t) { double d = e[t] - mean; var = fma(d, d, var); }
+  stats[0] = mean; stats[1] = var / K; stats[2] = sabs / K; stats[3] = mx;
+  stats[4] = (sw2 > 0.0) ? sqrt(se2) / sqrt(sw2) : 0.0;
+  if (Eout) memcpy(Eout, e, sizeof(double) * (size_t)q * (size_t)s);
+  free(cu); free(e);
+}
+
+/* ------------------------------------------------------------------ */
+/* Test helpers: brute force, dense multipliers, Jacobi SVD            */
+/* ------------------------------------------------------------------ */
+
+/* |det| of a k x k matrix by Gaussian elimination with partial pivoting. */
+static double absdet(double* B, int k) {
+  double d = 1.0;
+  for (int t = 0; t < k; ++t) {
+    int r = t;
+    for (int p = t + 1; p < k; ++p) if (fabs(B[p * k + t]) > fabs(B[r * k + t])) r = p;
+    if (B[r * k + t] == 0.0) return 0.0;
+    if (r != t) for (int q = 0; q < k; ++q) { double tmp = B[t * k + q]; B[t * k + q] = B[r * k + q]; B[r * k + q] = tmp; }
+    d *= fabs(B[t * k + t]);
+    for (int p = t + 1; p < k; ++p) {
+      double l = B[p * k + t] / B[t * k + t];
+      for (int q = t; q < k; ++q) B[p * k + q] -= l * B[t * k + q];
+    }
+  }
+  return d;
+}
+
+/* Exhaustive search over all k-subsets of the n columns of A (k x n): the
+ * maximal |det A[:,J]| (the definition of maximal volume, eqvol).  Returns
+ * the max; best J (ascending) in Jbest. */
+double orc_brute_maxvol(const double* A, int32_t k, int32_t n, int32_t* Jbest) {
+  int32_t* c = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  double* B = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+  for (int32_t i = 0; i < k; ++i) c[i] = i;
+  double best = -1.0;
+  for (;;) {
+    for (int32_t a = 0; a < k; ++a)
+      for (int32_t b = 0; b < k; ++b) B[a * k + b] = A[(int64_t)a * n + c[b]];
+    double d = absdet(B, k);
+    if (d > best) { best = d; memcpy(Jbest, c, sizeof(int32_t) * (size_t)k); }
+    int32_t i = k - 1;
+    while (i >= 0 && c[i] == n - k + i) --i;
+    if (i < 0) break;
+    ++c[i];
+    for (int32_t j = i + 1; j < k; ++j) c[j] = c[j - 1] + 1;
+  }
+  free(c); free(B);
+  return best;
+}
+
+/* Dense n x n H_{n,d} built by the recursion of equation eqrfd,
+ * H_{2q} = [[H_q, H_q], [H_q, -H_q]], started from H_s = I_s (n = 2^d s). */
+void orc_hadamard_abridged(int64_t n, int32_t d, double* H) {
+  int64_t s = n >> d;
+  memset(H, 0, sizeof(double) * (size_t)n * (size_t)n);
+  for (int64_t i = 0; i < s; ++i) H[i * n + i] = 1.0;
+  for (int64_t q = s; q < n; q *= 2) {
+    for (int64_t i = 0; i < q; ++i)
+      for (int64_t j = 0; j < q; ++j) {
+        double v = H[i * n + j];
+        H[i * n + (j + q)] = v;
+        H[(i + q) * n + j] = v;
+        H[(i + q) * n + (j + q)] = -v;
+      }
+  }
+}
+
+/* Dense multiplier M (n x n) of the problem, assembled from its definition:
+ * ARHT M = 2^(-d/2) D H_{n,d} P (H from the recursion above, P moving column
+ * perm[j] of D H to position j); sparse: M[srow][j] = ssign / sqrt(nnz). */
+void orc_multiplier_dense(const orc_problem* p, double* M) {
+  int64_t n = p->n;
+  memset(M, 0, sizeof(double) * (size_t)n * (size_t)n);
+  if (p->mkind == ORC_MULT_NONE) { for (int64_t i = 0; i < n; ++i) M[i * n + i] = 1.0; return; }
+  if (p->mkind == ORC_MULT_SPARSE) {
+    double v = 1.0 / sqrt((double)p->nnz);
+    for (int64_t j = 0; j < n; ++j)
+      for (int t = 0; t < p->nnz; ++t) M[(int64_t)p->srow[j * p->nnz + t] * n + j] = p->ssign[j * p->nnz + t] * v;
+    return;
+  }
+  double* H = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  orc_hadamard_abridged(n, p->depth, H);
+  double sc = arht_scale(p->depth);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < n; ++j) M[i * n + j] = sc * (double)p->dsign[i] * H[i * n + p->perm[j]];
+  free(H);
+}
+
+/* One-sided Jacobi SVD (Hestenes) of A (m x n row-major, m >= n): A = Uo diag(s) V^T.
+ * Columns are rotated until every pair is orthogonal to relative tolerance 1e-15.
+ * Singular values sorted descending.  Uo m x n, s n, V n x n (row-major). */
+int orc_jacobi_svd(const double* A, int32_t m, int32_t n, double* Uo, double* s, double* V) {
+  double* B = (double*)malloc(sizeof(double) * (size_t)m * (size_t)n);
+  memcpy(B, A, sizeof(double) * (size_t)m * (size_t)n);
+  for (int32_t i = 0; i < n; ++i) for (int32_t j = 0; j < n; ++j) V[i * n + j] = (i == j) ? 1.0 : 0.0;
+  int sweep;
+  for (sweep = 0; sweep < 100; ++sweep) {
+    int rotated = 0;
+    for (int32_t p = 0; p < n - 1; ++p)
+      for (int32_t q = p + 1; q < n; ++q) {
+        double al = 0, be = 0, ga = 0;
+        for (int32_t i = 0; i < m; ++i) {
+          al += B[i * n + p] * B[i * n + p];
+          be += B[i * n + q] * B[i * n + q];
+          ga += B[i * n + p] * B[i * n + q];
+        }
+        if (fabs(ga) <= 1e-15 * sqrt(al * be) || ga == 0.0) continue;
+        rotated = 1;
+        double zeta = (be - al) / (2.0 * ga);
+        double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+        for (int32_t i = 0; i < m; ++i) {
+          double bp = B[i * n + p], bq = B[i * n + q];
+          B[i * n + p] = c * bp - sn * bq; B[i * n + q] = sn * bp + c * bq;
+        }
+        for (int32_t i = 0; i < n; ++i) {
+          double vp = V[i * n + p], vq = V[i * n + q];
+          V[i * n + p] = c * vp - sn * vq; V[i * n + q] = sn * vp + c * vq;
+        }
+      }
+    if (!rotated) break;
+  }
+  for (int32_t j = 0; j < n; ++j) {
+    double nr = 0; for (int32_t i = 0; i < m; ++i) nr += B[i * n + j] * B[i * n + j];
+    s[j] = sqrt(nr);
+  }
+  /* sort descending (selection sort, permuting columns) */
+  for (int32_t a = 0; a < n; ++a) {
+    int32_t b = a;
+    for (int32_t c = a + 1; c < n; ++c) if (s[c] > s[b]) b = c;
+    if (b != a) {
+      double t = s[a]; s[a] = s[b]; s[b] = t;
+      for (int32_t i = 0; i < m; ++i) { t = B[i * n + a]; B[i * n + a] = B[i * n + b]; B[i * n + b] = t; }
+      for (int32_t i = 0; i < n; ++i) { t = V[i * n + a]; V[i * n + a] = V[i * n + b]; V[i * n + b] = t; }
+    }
+  }
+  for (int32_t j = 0; j < n; ++j)
+    for (int32_t i = 0; i < m; ++i) Uo[i * n + j] = (s[j] > 0) ? B[i * n + j] / s[j] : 0.0;
+  free(B);
+  return sweep;
+}

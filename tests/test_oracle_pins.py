@@ -1,0 +1,360 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+None of these re-types the oracle's arithmetic: each compares with an
+independent route (exhaustive search, a LAPACK routine through numpy, a dense
+matrix built by a different recursion, a closed form or a printed table).
+"""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import lra_inputs as li
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ------------------------------------------------------------------ maxvol
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("k,n", [(1, 7), (2, 8), (3, 9), (3, 10)])
+def test_maxvol_dominant_and_near_global(seed, k, n):
+    """Algorithm algdomin output: B = A[:,J] is dominant (Lemma lelcliden:
+    max |B^{-1} A| <= h), and by Theorem thlclglb its volume is within
+    h^k k^{k/2} of the global maximum found by exhaustive search."""
+    g = np.random.default_rng(seed)
+    A = g.standard_normal((k, n))
+    h = 1.01
+    r = oracle.maxvol(A, h=h)
+    J = r["J"]
+    assert len(set(J.tolist())) == k
+    C_ref = np.linalg.solve(A[:, J], A)
+    assert np.abs(C_ref).max() <= h * (1 + 1e-12)
+    np.testing.assert_allclose(r["C"], C_ref, rtol=0, atol=1e-12 * max(1.0, np.abs(C_ref).max()))
+    vol = abs(np.linalg.det(A[:, J]))
+    assert math.isclose(r["logdet"], math.log(vol), rel_tol=1e-12, abs_tol=1e-12)
+    _, best = oracle.brute_maxvol(A)
+    assert best >= vol * (1 - 1e-12)
+    assert vol >= best / (h ** k * k ** (k / 2)) * (1 - 1e-12)
+
+
+def test_maxvol_brute_force_agrees_when_h_is_one():
+    """With h = 1 a dominant submatrix is locally maximal; on small random
+    inputs the greedy-initialised search reaches the exhaustive optimum in
+    the large majority of cases (a weaker sub-check of the same theorem)."""
+    hits = 0
+    for seed in range(40):
+        A = np.random.default_rng(100 + seed).standard_normal((3, 8))
+        r = oracle.maxvol(A, h=1.0)
+        Jb, best = oracle.brute_maxvol(A)
+        vol = abs(np.linalg.det(A[:, r["J"]]))
+        hits += vol >= best * (1 - 1e-12)
+    assert hits >= 30
+
+
+def test_maxvol_brute_force_square_identity():
+    """k = n: the only choice is all columns, no swap."""
+    A = np.random.default_rng(3).standard_normal((4, 4))
+    r = oracle.maxvol(A)
+    assert sorted(r["J"].tolist()) == [0, 1, 2, 3]
+    assert r["nswaps"] == 0
+
+
+def test_maxvol_warm_start_never_decreases_volume():
+    """Each swap strictly increases |det| (Algorithm algdomin, stage 2)."""
+    g = np.random.default_rng(7)
+    A = g.standard_normal((5, 60))
+    J0 = np.arange(5, dtype=np.int32)
+    v0 = abs(np.linalg.det(A[:, J0]))
+    r = oracle.maxvol(A, J_warm=J0)
+    v1 = abs(np.linalg.det(A[:, r["J"]]))
+    assert v1 >= v0 * (1 - 1e-12)
+    if r["nswaps"]:
+        assert v1 > v0
+    assert np.abs(np.linalg.solve(A[:, r["J"]], A)).max() <= 1.01 * (1 + 1e-12)
+
+
+def test_maxvol_rank_deficient_strip_flags():
+    """An exactly singular strip (a zero row) meets a zero pivot."""
+    g = np.random.default_rng(1)
+    A = g.standard_normal((3, 12))
+    A[1] = 0.0
+    r = oracle.maxvol(A)
+    assert r["status"] == 16 and r["nswaps"] == 0
+
+
+def test_maxvol_lowest_index_tie_break():
+    """Equal magnitudes: the lowest column index wins (the paper is silent;
+    the tie rule is part of the specification of the pivots)."""
+    A = np.array([[1.0, -1.0, 1.0, 0.5], [0.0, 1.0, 1.0, 1.0]])
+    r = oracle.maxvol(A, h=10.0)
+    assert r["J"][0] == 0
+
+
+# ------------------------------------------------------------------ nucleus
+@pytest.mark.parametrize("k", [1, 2, 5, 16, 48])
+def test_nucleus_full_rank_is_inverse(k):
+    """r = k: the canonical nucleus is G^{-1} (Remark reklr_kl, eq. eqnucinv)."""
+    G = np.random.default_rng(k).standard_normal((k, k))
+    U, r = oracle.nucleus(G)
+    assert r == k
+    np.testing.assert_allclose(U @ G, np.eye(k), atol=1e-10 * np.linalg.cond(G))
+
+
+@pytest.mark.parametrize("k,r", [(6, 1), (7, 3), (16, 9), (33, 20)])
+def test_nucleus_exact_low_rank_equals_library_pinv(k, r):
+    """An exactly rank-r generator: its truncation is itself, so the nucleus
+    must equal the Moore-Penrose inverse (eq. eqnuc+svd) computed by LAPACK's SVD."""
+    g = np.random.default_rng(10 * k + r)
+    G = g.standard_normal((k, r)) @ g.standard_normal((r, k))
+    U, rr = oracle.nucleus(G, tol=1e-9)
+    assert rr == r
+    P = np.linalg.pinv(G, rcond=1e-9)
+    np.testing.assert_allclose(U, P, atol=1e-9 * np.abs(P).max())
+
+
+def test_nucleus_penrose_conditions_on_truncation():
+    """Numerically rank-deficient G (singular values 1..1e-12): the nucleus is
+    a Moore-Penrose inverse of a rank-r approximation G_r with ||G - G_r|| of the
+    order of the dropped singular values."""
+    g = np.random.default_rng(5)
+    Uo, _ = np.linalg.qr(g.standard_normal((12, 12)))
+    Vo, _ = np.linalg.qr(g.standard_normal((12, 12)))
+    s = np.array([1, .5, .2, .1, 1e-2, 1e-3, 1e-8, 1e-9, 1e-10, 1e-11, 1e-12, 1e-12])
+    G = (Uo * s) @ Vo.T
+    U, r = oracle.nucleus(G, tol=1e-6)
+    assert r == 6
+    Gr = np.linalg.pinv(U, rcond=1e-12)             # pinv(pinv(G_r)) = G_r
+    assert np.linalg.matrix_rank(U, tol=1e-6 * np.abs(U).max()) == 6
+    assert np.linalg.norm(G - Gr, 2) < 1e-6
+    np.testing.assert_allclose(U @ Gr @ U, U, atol=1e-8 * np.abs(U).max())
+    np.testing.assert_allclose(Gr @ U @ Gr, Gr, atol=1e-12)
+
+
+def test_jacobi_svd_matches_lapack():
+    A = np.random.default_rng(2).standard_normal((9, 6))
+    Uo, s, V = oracle.jacobi_svd(A)
+    np.testing.assert_allclose(s, np.linalg.svd(A, compute_uv=False), rtol=1e-13)
+    np.testing.assert_allclose((Uo * s) @ V.T, A, atol=1e-13)
+
+
+def test_nucleus_agrees_with_jacobi_svd_truncation_when_gap_is_large():
+    """Remark reubsc: the QRP truncation and the SVD truncation give about the
+    same nucleus when sigma_r >> sigma_{r+1}."""
+    g = np.random.default_rng(11)
+    Uo, _ = np.linalg.qr(g.standard_normal((10, 10)))
+    Vo, _ = np.linalg.qr(g.standard_normal((10, 10)))
+    s = np.array([3, 2, 1, .5, .3, 1e-11, 1e-12, 1e-12, 1e-13, 1e-14])
+    G = (Uo * s) @ Vo.T
+    U, r = oracle.nucleus(G, tol=1e-8)
+    Ju, js, Jv = oracle.jacobi_svd(G)
+    P = (Jv[:, :r] / js[:r]) @ Ju[:, :r].T
+    np.testing.assert_allclose(U, P, atol=1e-8 * np.abs(P).max())
+
+
+# ------------------------------------------------------------------ C-A / CUR
+@pytest.mark.parametrize("seed", range(4))
+@pytest.mark.parametrize("mult", ["none", "arht", "sparse"])
+def test_exact_recovery_rank_r(seed, mult):
+    """Theorem thdcmp: for rank-r W with a nonsingular r x r generator,
+    W = C W_{I,J}^{-1} R exactly; with a multiplier M the back-transformed CUR
+    (W M)[:,J] ((W M)[I,J])^+ W[I,:] is still exact (Algorithm alglratpsvd1 stage 4)."""
+    p = li.dense_lowrank(128, 128, r=6, noise=0.0, seed=seed)
+    if mult == "arht":
+        li.with_arht(p, 2, seed + 50)
+    elif mult == "sparse":
+        li.with_sparse(p, 4, seed + 50)
+    I0 = li.initial_rows(128, 6, seed + 99)
+    o = oracle.ca_run(p, 6, 3, I0)
+    W = p.W
+    err = np.linalg.norm(W - o["C"] @ o["U"] @ o["R"]) / np.linalg.norm(W)
+    assert err < 1e-11, err
+    assert o["rank"] == 6
+    # the outputs are the submatrices they claim to be
+    M = oracle.multiplier_dense(p) if mult != "none" else np.eye(128)
+    WM = W @ M
+    np.testing.assert_allclose(o["C"], WM[:, o["J"]], atol=1e-14)
+    np.testing.assert_array_equal(o["R"], W[o["I"], :])
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_volume_non_decreasing_across_steps(seed):
+    """C-A steps warm-started from the current sets never decrease the volume
+    of the generator (the C-A volume argument; each swap of Algorithm algdomin
+    increases |det|)."""
+    p = li.factor_gaussian(200, 10, 1e-3, seed)
+    o = oracle.ca_run(p, 10, 4, li.initial_rows(200, 10, seed))
+    lv = o["logvol"][~np.isnan(o["logvol"])]
+    assert np.all(np.diff(lv) >= -1e-10 * np.abs(lv[:-1]))
+    # final logvol is log|det W[I,J]| computed independently
+    assert math.isclose(lv[-1], math.log(abs(np.linalg.det(p.W[np.ix_(o["I"], o["J"])]))), rel_tol=1e-10)
+
+
+def test_chebyshev_error_bound_theorem_th12():
+    """Theorem th12 with k = l = r: ||W - CUR||_C <= h (r+1) sigma_{r+1}(W),
+    h = (max volume over all r x r submatrices) / (volume of the generator),
+    both measured by exhaustive search on a tiny matrix."""
+    for seed in range(6):
+        g = np.random.default_rng(seed)
+        W = g.standard_normal((7, 2)) @ g.standard_normal((2, 7)) + 1e-3 * g.standard_normal((7, 7))
+        p = li.Problem(li.SRC_DENSE, 7, 7, W=W)
+        o = oracle.ca_run(p, 2, 3, li.initial_rows(7, 2, seed))
+        best = max(abs(np.linalg.det(W[np.ix_(I, J)]))
+                   for I in itertools.combinations(range(7), 2) for J in itertools.combinations(range(7), 2))
+        h = best / abs(np.linalg.det(W[np.ix_(o["I"], o["J"])]))
+        sig = np.linalg.svd(W, compute_uv=False)
+        E = W - o["C"] @ o["U"] @ o["R"]
+        assert np.abs(E).max() <= h * 3 * sig[2] * (1 + 1e-9)
+
+
+def test_tests2_error_band_from_paper_table():
+    """Table tb_ranrc (Tests 2, n = 256): our C-A with dominance swaps must do
+    at least as well on average as the paper's reported mean error."""
+    table = {}
+    with open(os.path.join(GOLDEN, "tests2_error_table.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                n, r, mean, std = line.split()
+                table[(int(n), int(r))] = float(mean)
+    for (n, r), paper_mean in table.items():
+        errs = []
+        for seed in range(8):
+            p = li.factor_gaussian(n, r, 1e-10, seed)
+            o = oracle.ca_run(p, r, 5, li.initial_rows(n, r, 1000 + seed))
+            E = p.W - o["C"] @ o["U"] @ o["R"]
+            errs.append(np.linalg.norm(E, 2) / np.linalg.norm(p.W, 2))
+        assert np.mean(errs) <= paper_mean
+        # and not below the noise floor 1e-10 ||G3|| / ||W||
+        assert np.min(errs) > 1e-13
+
+
+def test_early_stop_when_no_swap():
+    p = li.dense_lowrank(64, 64, r=4, noise=0.0, seed=3)
+    o = oracle.ca_run(p, 4, 6, li.initial_rows(64, 4, 1))
+    assert o["loops"] < 6
+
+
+# ------------------------------------------------------------------ multipliers
+def _read_blocks():
+    out, cur = {}, None
+    with open(os.path.join(GOLDEN, "abridged_hadamard_blocks.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            if line.startswith("d="):
+                cur = int(line[2:]); out[cur] = []
+            else:
+                out[cur].append([int(v) for v in line.split()])
+    return {d: np.array(v) for d, v in out.items()}
+
+
+@pytest.mark.parametrize("s", [1, 3, 8])
+def test_abridged_hadamard_matches_printed_blocks(s):
+    """H_{n,1} and H_{n,2} printed in equation eqbschf."""
+    for d, B in _read_blocks().items():
+        H = oracle.hadamard_abridged(s * (1 << d), d)
+        np.testing.assert_array_equal(H, np.kron(B, np.eye(s)))
+
+
+@pytest.mark.parametrize("n,d", [(16, 1), (24, 2), (64, 3)])
+def test_arht_orthogonal_and_sparse(n, d):
+    """D H_{n,d} P scaled by 2^{-d/2} is orthogonal and has 2^d nonzeros per
+    row and column (appendix on abridged multipliers)."""
+    p = li.Problem(li.SRC_DENSE, 4, n, W=np.zeros((4, n)))
+    li.with_arht(p, d, 5)
+    M = oracle.multiplier_dense(p)
+    np.testing.assert_allclose(M @ M.T, np.eye(n), atol=1e-15)
+    assert np.all((M != 0).sum(0) == 2 ** d) and np.all((M != 0).sum(1) == 2 ** d)
+
+
+@pytest.mark.parametrize("mult", ["arht1", "arht2", "arht3", "sparse"])
+def test_multiplier_gathers_equal_dense_product(mult):
+    """The strip gathers (closed-form column combinations) equal rows / columns
+    of W M with M assembled densely from its recursive definition."""
+    g = np.random.default_rng(4)
+    W = g.standard_normal((40, 48))
+    p = li.Problem(li.SRC_DENSE, 40, 48, W=W)
+    if mult.startswith("arht"):
+        li.with_arht(p, int(mult[-1]), 8)
+    else:
+        li.with_sparse(p, 4, 8)
+    WM = W @ oracle.multiplier_dense(p)
+    I = np.array([3, 0, 39, 17], dtype=np.int32)
+    J = np.array([47, 5, 6, 0, 22], dtype=np.int32)
+    np.testing.assert_allclose(oracle.gather_rows(p, I), WM[I], atol=1e-14)
+    np.testing.assert_allclose(oracle.gather_cols(p, J), WM[:, J], atol=1e-14)
+    np.testing.assert_array_equal(oracle.gather_rows_orig(p, I), W[I])
+
+
+def test_sparse_multiplier_structure():
+    p = li.Problem(li.SRC_DENSE, 4, 50, W=np.zeros((4, 50)))
+    li.with_sparse(p, 4, 2)
+    M = oracle.multiplier_dense(p)
+    assert np.all((M != 0).sum(0) == 4)
+    np.testing.assert_allclose(np.linalg.norm(M, axis=0), 1.0, rtol=1e-15)
+
+
+def test_float32_input_is_widened_exactly():
+    W = np.random.default_rng(0).standard_normal((10, 12)).astype(np.float32)
+    p = li.Problem(li.SRC_DENSE, 10, 12, W=W)
+    np.testing.assert_array_equal(oracle.gather_rows(p, np.array([2, 5], np.int32)), W[[2, 5]].astype(np.float64))
+
+
+# ------------------------------------------------------------------ kernels
+def test_laplace_entries_closed_form_values():
+    """1/|x - y| at points with known distances (3-4-12 -> 13)."""
+    X = np.array([[0.0, 0.0, 0.0], [1.0, 2.0, 3.0]])
+    Y = np.array([[3.0, 4.0, 12.0], [1.0, 2.0, 5.0]])
+    p = li.Problem(li.SRC_LAPLACE, 2, 2, X=X, Y=Y)
+    R = oracle.gather_rows(p, np.array([0, 1], np.int32))
+    assert R[0, 0] == 1.0 / 13.0 and R[1, 1] == 0.5
+
+
+def test_gaussian_entries_closed_form_values():
+    X = np.array([[0.0, 0.0, 0.0]])
+    Y = np.array([[0.0, 0.0, 0.0], [0.3, 0.0, 0.0]])
+    p = li.Problem(li.SRC_GAUSSIAN, 1, 2, X=X, Y=Y, ell=0.3)
+    R = oracle.gather_rows(p, np.array([0], np.int32))
+    assert R[0, 0] == 1.0 and abs(R[0, 1] - math.exp(-0.5)) < 1e-16
+
+
+def test_separated_laplace_block_error_decays_with_rank():
+    """Interactions of well-separated clusters have low numerical rank: the
+    C-A CUR error falls fast as k grows."""
+    p = li.laplace_clusters(300, 280, seed=1)
+    X, Y = p.X, p.Y
+    K = 1.0 / np.linalg.norm(X[:, None, :] - Y[None, :, :], axis=2)
+    errs = []
+    sig = np.linalg.svd(K, compute_uv=False)
+    for k in (2, 4, 8, 12, 16):
+        o = oracle.ca_run(p, k, 3, li.initial_rows(300, k, 2))
+        err = np.linalg.norm(K - o["C"] @ o["U"] @ o["R"]) / np.linalg.norm(K)
+        best = np.sqrt(np.sum(sig[k:] ** 2)) / np.linalg.norm(K)     # Eckart-Young optimum
+        assert best <= err < 30 * best
+        errs.append(err)
+    assert errs[-1] < 1e-5 and all(b < a for a, b in zip(errs, errs[1:]))
+
+
+# ------------------------------------------------------------------ apply / residual
+def test_cur_apply_matches_matmul():
+    g = np.random.default_rng(0)
+    C, U, R, X = g.standard_normal((30, 5)), g.standard_normal((5, 5)), g.standard_normal((5, 40)), g.standard_normal((40, 3))
+    np.testing.assert_allclose(oracle.cur_apply(C, U, R, X), C @ (U @ (R @ X)), rtol=1e-13, atol=1e-13)
+
+
+def test_residual_sample_full_equals_full_residual():
+    """With Q = all rows and S = all columns the sample is the whole error matrix."""
+    p = li.dense_lowrank(40, 30, r=3, noise=1e-4, seed=2)
+    o = oracle.ca_run(p, 3, 2, li.initial_rows(40, 3, 0))
+    Q = np.arange(40, dtype=np.int32); S = np.arange(30, dtype=np.int32)
+    st, E = oracle.residual_sample(p, o["C"], o["U"], o["R"], Q, S, return_E=True)
+    Eref = p.W - o["C"] @ o["U"] @ o["R"]
+    np.testing.assert_allclose(E, Eref, atol=1e-15)
+    assert math.isclose(st[0], Eref.mean(), rel_tol=1e-9, abs_tol=1e-18)
+    assert math.isclose(st[1], Eref.var(), rel_tol=1e-9)
+    assert math.isclose(st[2], np.abs(Eref).mean(), rel_tol=1e-12)
+    assert st[3] == np.abs(Eref).max()
+    assert math.isclose(st[4], np.linalg.norm(Eref) / np.linalg.norm(p.W), rel_tol=1e-12)
