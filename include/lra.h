@@ -1,0 +1,205 @@
+/*
+ * lra.h -- C ABI of a GB300 (sm_103a) library for superfast cross-approximation
+ * (C-A) CUR low-rank approximation, after Pan, Luan, Svadlenka, Zhao,
+ * "Superfast Accurate Low Rank Approximation" (arXiv:1710.07946).
+ *
+ * Conventions for every entry point:
+ *  - Pointers documented as "device" point to CUDA device memory of the current
+ *    device; "host" pointers to ordinary host memory.  All matrices are row-major.
+ *  - The caller owns every buffer it passes (inputs, outputs, workspace).  The
+ *    library allocates device memory only in lra_precondition (the multiplier
+ *    descriptor, freed by lra_multiplier_destroy); the compute calls allocate
+ *    nothing: scratch comes from the caller's workspace, sized by the matching
+ *    *_workspace_size query.
+ *  - Calls are asynchronous on the given stream (0 = legacy default stream).  The
+ *    returned status covers host-side validation and launch errors only; problems
+ *    detected on the device (zero pivots, non-finite strips, an unfinished swap
+ *    loop, an expired wait) are written to the device status word named in each
+ *    call and are visible after the stream is synchronised.
+ *  - No call aborts, traps or prints.  Every device-side wait is bounded in time
+ *    and reports LRA_ERR_TIMEOUT instead of hanging.
+ */
+#ifndef LRA_H
+#define LRA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* lra_stream_t;   /* a cudaStream_t */
+
+typedef enum {
+  LRA_OK = 0,
+  LRA_ERR_INVALID_ARG = 1,      /* bad sizes, pointers, index sets or options       */
+  LRA_ERR_CUDA = 2,             /* a CUDA runtime call or launch failed             */
+  LRA_ERR_NONFINITE = 3,        /* a gathered strip held NaN or Inf                 */
+  LRA_ERR_TIMEOUT = 4,          /* a bounded device-side wait expired               */
+  LRA_ERR_WORKSPACE = 5,        /* workspace missing or smaller than the query      */
+  LRA_WARN_RANK_DEFICIENT = 16, /* a zero pivot (strip rank < k) or core rank < k   */
+  LRA_WARN_NOT_CONVERGED = 17   /* max_swaps stopped a maxvol swap loop             */
+} lra_status;
+
+typedef enum { LRA_F64 = 0, LRA_F32 = 1, LRA_BF16 = 2 } lra_dtype;
+
+/* Input access (paper: the m x n input W, accessed either as a whole or entry by
+ * entry; "superfast" algorithms touch only O((m+n)k) of its entries). */
+typedef enum {
+  LRA_DENSE = 0,            /* W stored densely                                    */
+  LRA_KERNEL_LAPLACE = 1,   /* w_ij = 1 / |x_i - y_j|, evaluated on demand         */
+  LRA_KERNEL_GAUSSIAN = 2   /* w_ij = exp(-|x_i - y_j|^2 / (2 l^2)), on demand      */
+} lra_source;
+
+typedef struct {
+  int32_t src;           /* lra_source                                               */
+  int32_t dtype;         /* dense storage type: LRA_F64 or LRA_F32                   */
+  int64_t m, n;          /* rows, columns; 1 <= m, n < 2^31                          */
+  const void* W;         /* dense: device, m x n row-major, leading dimension ldw    */
+  int64_t ldw;           /* dense: >= n                                              */
+  const double* X;       /* kernel: device, m target points, 3 doubles each          */
+  const double* Y;       /* kernel: device, n source points, 3 doubles each          */
+  double length_scale;   /* Gaussian kernel l > 0                                    */
+} lra_problem;
+
+/* ------------------------------------------------------------------------- */
+/* Randomised pre-processing (multipliers)                                    */
+/* ------------------------------------------------------------------------- */
+typedef enum {
+  LRA_MULT_NONE = 0,
+  LRA_MULT_ARHT = 1,        /* abridged randomized Hadamard 2^{-d/2} D H_{n,d} P     */
+  LRA_MULT_SPARSE_PM1 = 2   /* sparse +-1/sqrt(nnz) multiplier, nnz entries / column */
+} lra_mult_kind;
+
+typedef struct lra_multiplier_s* lra_multiplier;   /* opaque, library-owned */
+
+/*
+ * lra_precondition -- describe the right multiplier M of the pre-processed
+ * matrix W' = W M, which C-A then approximates (paper: Section "Pre-processing
+ * with matrices of abridged Hadamard and Fourier transforms"; Appendix
+ * "Abridged Hadamard and Fourier Multipliers", eqs. eqrfd / eqbschf; Section
+ * "Pre-processing with quasi Gaussian matrices", case (i)).  M is never formed:
+ * the strip gathers evaluate the needed columns of W M on the fly.
+ *
+ *   kind = LRA_MULT_ARHT: M = 2^{-d/2} D H_{n,d} P, depth_or_nnz = d (1..10),
+ *     n = 2^d s.  H_{n,d} = H_{2^d} (x) I_s is the d-step abridged Hadamard
+ *     recursion, D = diag(signs) with signs[i] = +-1 (n host int8),
+ *     P the permutation taking column perm[j] of D H to position j
+ *     (perm_or_rows: n host int32, a permutation of 0..n-1).
+ *   kind = LRA_MULT_SPARSE_PM1: column j of M holds depth_or_nnz (1..16)
+ *     entries signs[j*nnz+t] / sqrt(nnz) in the rows perm_or_rows[j*nnz+t],
+ *     strictly ascending in t (host arrays of n*nnz int32 / int8).
+ * The random draws (signs, permutation, positions) are inputs, so that runs are
+ * reproducible.  The descriptor is copied to device memory owned by the handle;
+ * the host arrays may be freed on return.  The copy is synchronous.
+ * Errors: LRA_ERR_INVALID_ARG (bad kind, sizes, out-of-range or unsorted
+ * indices, signs not +-1), LRA_ERR_CUDA.
+ */
+lra_status lra_precondition(lra_multiplier* out, int32_t kind, int64_t n, int32_t depth_or_nnz,
+                            const int32_t* perm_or_rows, const int8_t* signs);
+
+/* Free a multiplier handle (NULL is accepted). */
+lra_status lra_multiplier_destroy(lra_multiplier mult);
+
+/* ------------------------------------------------------------------------- */
+/* Cross-approximation                                                        */
+/* ------------------------------------------------------------------------- */
+typedef enum {
+  LRA_MODE_FP64 = 0,        /* every gather, pivot and nucleus step in FP64, in the
+                               operation order of the FP64 reference (bit-exact
+                               pivots)                                              */
+  LRA_MODE_MIXED = 1        /* FP32 strips screened by a running error bound; every
+                               pivot decision still confirmed in FP64                */
+} lra_mode;
+
+typedef struct {
+  int32_t k;             /* target rank = generator size, 1 <= k <= min(m, n, 64)    */
+  int32_t sweeps;        /* C-A loops alpha >= 1 (one loop = column step + row step) */
+  double h;              /* dominance threshold >= 1 (swap while max |B^{-1}A| > h)  */
+  double rank_tol;       /* relative QRP truncation tolerance of the nucleus         */
+  int32_t max_swaps;     /* cap on swaps per maxvol step (>= 0)                      */
+  int32_t mode;          /* lra_mode                                                 */
+} lra_ca_params;
+
+/* Outputs of one C-A CUR approximation W ~ C U R (all device, caller-owned). */
+typedef struct {
+  int32_t* I;            /* k row indices, in generator order                        */
+  int32_t* J;            /* k column indices (of W' = W M), in generator order       */
+  double* C;             /* m x k: W'[:, J]                                          */
+  double* U;             /* k x k: nucleus, pinv of the rank-r truncation of W'[I,J] */
+  double* R;             /* k x n: W[I, :] (original rows: for an orthogonal M this is
+                            the back-transform R_H M^T of Algorithm alglratpsvd1)     */
+  double* logvol;        /* 2*sweeps: log|det W'[I,J]| after each step (NaN if unrun) */
+  int32_t* info;         /* 4 ints: numerical rank r, total swaps, loops run, status */
+} lra_cur;
+
+/*
+ * lra_ca_workspace_size -- bytes of device workspace lra_ca_run needs for this
+ * problem and these parameters (256-byte aligned start required).
+ * Errors: LRA_ERR_INVALID_ARG.
+ */
+lra_status lra_ca_workspace_size(const lra_problem* prob, const lra_ca_params* par, lra_multiplier mult,
+                                 size_t* bytes);
+
+/*
+ * lra_ca_run -- C-A CUR approximation of W' = W M (paper: Section "CUR LRA;
+ * primitive, cynical, and cross-approximation algorithms", the C-A loops of
+ * Figure fig4 in the Tests 2 schedule; Algorithms algdomin and alggos for each
+ * step; Algorithm algcnnncl with Remark reubsc for the nucleus).
+ *
+ * Starting from the k rows I0 (device int32, distinct, in [0, m)), each loop
+ * takes the row strip W'[I,:], finds k columns J whose k x k submatrix is
+ * dominant in it (LUP initialisation with column pivoting in the first loop,
+ * warm start from the current J afterwards, then volume-increasing swaps while
+ * some |(W'[I,J])^{-1} W'[I,:]| entry exceeds h), then does the same on the
+ * column strip W'[:,J] to update I.  The loop stops after `sweeps` loops or when
+ * a loop makes no swap.  Finally C = W'[:,J], R = W[I,:], and U is the
+ * pseudo-inverse of the rank-r truncation of W'[I,J] obtained from Householder
+ * QR with column pivoting, r = #{t : |R_tt| > rank_tol |R_00|}.
+ * In LRA_MODE_FP64 the index sets equal those of a sequential FP64 evaluation of
+ * the same steps bit for bit (ties go to the lowest column, then row, index).
+ * mult may be NULL (M = I).  workspace: device, >= the size query, 256-byte
+ * aligned.  Device status (out->info[3]): LRA_OK, LRA_WARN_*, LRA_ERR_NONFINITE,
+ * LRA_ERR_TIMEOUT or LRA_ERR_INVALID_ARG (I0 not distinct / out of range).
+ * Host errors: LRA_ERR_INVALID_ARG, LRA_ERR_WORKSPACE, LRA_ERR_CUDA.
+ */
+lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_multiplier mult, const int32_t* I0,
+                      const lra_cur* out, void* workspace, size_t workspace_bytes, lra_stream_t stream);
+
+/*
+ * lra_cur_apply -- Y = C (U (R X)) for one CUR triple (paper: FMM / HSS stage
+ * (iii), multiplication with the generators of the neutered block columns).
+ * C m x k, U k x k, R k x n (as written by lra_ca_run), X n x nrhs, Y m x nrhs,
+ * all device FP64 row-major; 1 <= nrhs <= 1024.  Each product is accumulated in
+ * FP64.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
+ */
+lra_status lra_cur_apply(const double* C, const double* U, const double* R, int64_t m, int64_t n, int32_t k,
+                         const double* X, int32_t nrhs, double* Y, void* workspace, size_t workspace_bytes,
+                         lra_stream_t stream);
+/* Workspace bytes of lra_cur_apply for an n-column R, rank k and nrhs right-hand sides. */
+lra_status lra_cur_apply_workspace_size(int64_t n, int32_t k, int32_t nrhs, size_t* bytes);
+
+/*
+ * lra_residual_sample -- a-posteriori error estimate from a q x s submatrix of
+ * E = W - C U R (paper: Section "Superfast a posteriori error estimation for LRA
+ * of a matrix filled with i.i.d. values of a single variable").  Q (q device
+ * int32 rows) and S (s device int32 columns) are the random sample positions;
+ * q*s >= 1.  stats (device, 5 doubles): mean of e, variance (1/K) sum (e-mean)^2,
+ * mean |e|, max |e|, ||E[Q,S]||_F / ||W[Q,S]||_F with K = q s.  E (device q x s,
+ * optional, may be NULL) receives the sampled errors.  W is read through prob
+ * (original matrix, no multiplier).  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
+ */
+lra_status lra_residual_sample(const lra_problem* prob, const double* C, const double* U, const double* R,
+                               int32_t k, const int32_t* Q, int32_t q, const int32_t* S, int32_t s, double* stats,
+                               double* E, void* workspace, size_t workspace_bytes, lra_stream_t stream);
+/* Workspace bytes of lra_residual_sample for rank k and a q x s sample. */
+lra_status lra_residual_sample_workspace_size(int32_t k, int32_t q, int32_t s, size_t* bytes);
+
+/* Library version string, for diagnostics. */
+const char* lra_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRA_H */

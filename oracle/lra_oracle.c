@@ -139,7 +139,12 @@ void orc_gather_rows_orig(const orc_problem* p, const int32_t* I, int32_t k, dou
 /* ------------------------------------------------------------------ */
 /* Maxvol on a k x n strip (dominant k x k submatrix)                  */
 /* ------------------------------------------------------------------ */
-enum { ORC_OK = 0, ORC_WARN_RANK_DEFICIENT = 16, ORC_WARN_NOT_CONVERGED = 17 };
+enum { ORC_OK = 0, ORC_ERR_NONFINITE = 3, ORC_WARN_RANK_DEFICIENT = 16, ORC_WARN_NOT_CONVERGED = 17 };
+
+static int all_finite(const double* a, int64_t cnt) {
+  for (int64_t i = 0; i < cnt; ++i) if (!isfinite(a[i])) return 0;
+  return 1;
+}
 
 /*
  * orc_maxvol: find k columns J of the k x n matrix A (row-major) whose k x k
@@ -156,8 +161,9 @@ enum { ORC_OK = 0, ORC_WARN_RANK_DEFICIENT = 16, ORC_WARN_NOT_CONVERGED = 17 };
  *         rows (pivot row = largest |A(t)[p, j_t]|, p >= t, lowest p on ties;
  *         rows t and that row are exchanged across the whole strip).
  *   Then C = Bbar^{-1} A = (I | U0^{-1} U1) in the original column order: each
- *   unchosen column is solved by back substitution with U0 in descending row
- *   order, each inner product an ascending fma chain; column J[i] of C is e_i.
+ *   unchosen column b is solved by column-sweep back substitution with U0
+ *   (for i = k-1 down to 0: x_i = b_i / U0[i][i], then b_p <- fma(-U0[p][i], x_i, b_p)
+ *   for p < i); column J[i] of C is e_i.
  * Swaps (Algorithm algdomin, stages 1-2): take the entry of largest |C[i][j]|
  *   over i < k and j not in J, ties to the lowest j then the lowest i.  Stop when
  *   it is <= h.  Otherwise J[i*] <- j* and C is updated in place to the new
@@ -228,11 +234,10 @@ restart:
   for (int64_t q = 0; q < n; ++q) {
     if (chosen[q]) continue;
     for (int32_t i = k - 1; i >= 0; --i) {
-      double s = M[(int64_t)i * n + q];
-      for (int32_t p = i + 1; p < k; ++p) s = fma(-U0[i * k + p], x[p], s);
-      x[i] = s / U0[i * k + i];
+      double xi = M[(int64_t)i * n + q] / U0[i * k + i];
+      M[(int64_t)i * n + q] = xi;
+      for (int32_t p = 0; p < i; ++p) M[(int64_t)p * n + q] = fma(-U0[p * k + i], xi, M[(int64_t)p * n + q]);
     }
-    for (int32_t i = 0; i < k; ++i) M[(int64_t)i * n + q] = x[i];
   }
   for (int32_t t = 0; t < k; ++t)
     for (int32_t i = 0; i < k; ++i) M[(int64_t)i * n + J[t]] = (i == t) ? 1.0 : 0.0;
@@ -415,6 +420,8 @@ int32_t orc_nucleus(const double* G, int32_t k, double tol, double* U) {
  *   U (k x k)       nucleus of G = W'[I,J] at relative tolerance rank_tol
  *   logvol[2*alpha] log|det W'[I,J]| after every step (unused slots NaN)
  *   info[4]         {rank, total swaps, loops run, status}
+ * A strip holding NaN or Inf stops the run with status ORC_ERR_NONFINITE (the
+ * outputs are then undefined).
  */
 int orc_ca_run(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I0, double h, int32_t max_swaps,
                double rank_tol, int32_t* I, int32_t* J, double* C, double* U, double* R, double* logvol,
@@ -431,11 +438,13 @@ int orc_ca_run(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I
   for (int32_t s = 0; s < sweeps; ++s) {
     double ld; int32_t nsw1 = 0, nsw2 = 0;
     orc_gather_rows(p, I, k, Rs);
+    if (!all_finite(Rs, (int64_t)k * n)) { status = ORC_ERR_NONFINITE; break; }
     int st = orc_maxvol(Rs, k, n, s == 0 ? NULL : J, h, max_swaps, Jn, NULL, &ld, &nsw1);
     if (st > status) status = st;
     memcpy(J, Jn, sizeof(int32_t) * (size_t)k);
     logvol[2 * s] = ld;
     orc_gather_cols_t(p, J, k, Cs);
+    if (!all_finite(Cs, (int64_t)k * m)) { status = ORC_ERR_NONFINITE; break; }
     st = orc_maxvol(Cs, k, m, I, h, max_swaps, In, NULL, &ld, &nsw2);
     if (st > status) status = st;
     memcpy(I, In, sizeof(int32_t) * (size_t)k);
@@ -443,6 +452,11 @@ int orc_ca_run(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I
     total += nsw1 + nsw2;
     loops = s + 1;
     if (s > 0 && nsw1 == 0 && nsw2 == 0) break;
+  }
+  if (status == ORC_ERR_NONFINITE) {
+    info[0] = 0; info[1] = total; info[2] = loops; info[3] = status;
+    free(Rs); free(Cs); free(G); free(Jn); free(In);
+    return status;
   }
   /* outputs: C = W'[:,J] (transpose of the last column strip, which used the final J) */
   for (int64_t i = 0; i < m; ++i)

@@ -1,0 +1,290 @@
+"""GB300 (sm_103a) library for superfast cross-approximation CUR low-rank
+approximation (Pan, Luan, Svadlenka, Zhao, arXiv:1710.07946).
+
+This module is the thin Python binding of the C ABI declared in include/lra.h:
+the functions named ``lra_*`` marshal torch tensors (device memory, streams)
+into the library's calls and do nothing else; every step of the computation
+runs in the library's CUDA kernels.  There is no CPU fallback: importing the
+binding without a built library, or calling it without a CUDA device, raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+from . import build as _build
+
+__all__ = [
+    "LRA_OK", "LRA_ERR_INVALID_ARG", "LRA_ERR_CUDA", "LRA_ERR_NONFINITE", "LRA_ERR_TIMEOUT", "LRA_ERR_WORKSPACE",
+    "LRA_WARN_RANK_DEFICIENT", "LRA_WARN_NOT_CONVERGED", "LraError", "Problem", "Multiplier",
+    "lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run", "lra_cur_apply",
+    "lra_residual_sample", "lra_version", "library_path",
+]
+
+LRA_OK, LRA_ERR_INVALID_ARG, LRA_ERR_CUDA, LRA_ERR_NONFINITE, LRA_ERR_TIMEOUT, LRA_ERR_WORKSPACE = 0, 1, 2, 3, 4, 5
+LRA_WARN_RANK_DEFICIENT, LRA_WARN_NOT_CONVERGED = 16, 17
+LRA_F64, LRA_F32 = 0, 1
+LRA_DENSE, LRA_KERNEL_LAPLACE, LRA_KERNEL_GAUSSIAN = 0, 1, 2
+LRA_MULT_NONE, LRA_MULT_ARHT, LRA_MULT_SPARSE_PM1 = 0, 1, 2
+LRA_MODE_FP64, LRA_MODE_MIXED = 0, 1
+
+_STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NONFINITE", 4: "TIMEOUT", 5: "WORKSPACE",
+           16: "WARN_RANK_DEFICIENT", 17: "WARN_NOT_CONVERGED"}
+
+
+class LraError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)}")
+        self.status = status
+
+
+class _Problem(ct.Structure):
+    _fields_ = [("src", ct.c_int32), ("dtype", ct.c_int32), ("m", ct.c_int64), ("n", ct.c_int64),
+                ("W", ct.c_void_p), ("ldw", ct.c_int64), ("X", ct.c_void_p), ("Y", ct.c_void_p),
+                ("length_scale", ct.c_double)]
+
+
+class _Params(ct.Structure):
+    _fields_ = [("k", ct.c_int32), ("sweeps", ct.c_int32), ("h", ct.c_double), ("rank_tol", ct.c_double),
+                ("max_swaps", ct.c_int32), ("mode", ct.c_int32)]
+
+
+class _Cur(ct.Structure):
+    _fields_ = [("I", ct.c_void_p), ("J", ct.c_void_p), ("C", ct.c_void_p), ("U", ct.c_void_p),
+                ("R", ct.c_void_p), ("logvol", ct.c_void_p), ("info", ct.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB) or not _build.up_to_date():
+        _build.build()
+    L = ct.CDLL(_build.LIB)
+    vp, i32, i64, f64, sz = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_double, ct.c_size_t
+    P, PP, PC = ct.POINTER(_Problem), ct.POINTER(_Params), ct.POINTER(_Cur)
+    L.lra_precondition.argtypes = [ct.POINTER(vp), i32, i64, i32, vp, vp]
+    L.lra_multiplier_destroy.argtypes = [vp]
+    L.lra_ca_workspace_size.argtypes = [P, PP, vp, ct.POINTER(sz)]
+    L.lra_ca_run.argtypes = [P, PP, vp, vp, PC, vp, sz, vp]
+    L.lra_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp, vp, sz, vp]
+    L.lra_cur_apply_workspace_size.argtypes = [i64, i32, i32, ct.POINTER(sz)]
+    L.lra_residual_sample.argtypes = [P, vp, vp, vp, i32, vp, i32, vp, i32, vp, vp, vp, sz, vp]
+    L.lra_residual_sample_workspace_size.argtypes = [i32, i32, i32, ct.POINTER(sz)]
+    L.lra_version.restype = ct.c_char_p
+    for f in ("lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run",
+              "lra_cur_apply", "lra_cur_apply_workspace_size", "lra_residual_sample",
+              "lra_residual_sample_workspace_size"):
+        getattr(L, f).restype = ct.c_int
+    _lib = L
+    return L
+
+
+def _check(st: int, where: str):
+    if st != LRA_OK:
+        raise LraError(st, where)
+
+
+def _dev(t: Optional[torch.Tensor], dtype=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _stream(stream) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    # 256-byte aligned: torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+@dataclass
+class Problem:
+    """An m x n input on the device: a dense row-major matrix or a kernel on
+    two point sets (targets X: m x 3, sources Y: n x 3, FP64)."""
+
+    src: int
+    m: int
+    n: int
+    W: Optional[torch.Tensor] = None
+    X: Optional[torch.Tensor] = None
+    Y: Optional[torch.Tensor] = None
+    length_scale: float = 1.0
+
+    @staticmethod
+    def dense(W: torch.Tensor) -> "Problem":
+        if W.dim() != 2 or W.dtype not in (torch.float64, torch.float32):
+            raise TypeError("dense W must be a 2-D float64 or float32 CUDA tensor")
+        _dev(W, name="W")
+        return Problem(LRA_DENSE, W.shape[0], W.shape[1], W=W)
+
+    @staticmethod
+    def kernel(kind: str, X: torch.Tensor, Y: torch.Tensor, length_scale: float = 1.0) -> "Problem":
+        src = {"laplace": LRA_KERNEL_LAPLACE, "gaussian": LRA_KERNEL_GAUSSIAN}[kind]
+        _dev(X, torch.float64, "X"); _dev(Y, torch.float64, "Y")
+        return Problem(src, X.shape[0], Y.shape[0], X=X, Y=Y, length_scale=length_scale)
+
+    def _c(self) -> _Problem:
+        p = _Problem()
+        p.src, p.m, p.n = self.src, self.m, self.n
+        if self.W is not None:
+            p.dtype = LRA_F32 if self.W.dtype == torch.float32 else LRA_F64
+            p.W, p.ldw = self.W.data_ptr(), self.W.stride(0)
+        if self.X is not None:
+            p.X, p.Y = self.X.data_ptr(), self.Y.data_ptr()
+        p.length_scale = float(self.length_scale)
+        return p
+
+
+class Multiplier:
+    """Owner of a library multiplier handle (lra_precondition)."""
+
+    def __init__(self, handle: int, kind: int, n: int):
+        self.handle, self.kind, self.n = handle, kind, n
+
+    def __del__(self):
+        try:
+            if self.handle and _lib is not None:
+                _lib.lra_multiplier_destroy(self.handle)
+        except Exception:
+            pass
+        self.handle = None
+
+
+def lra_version() -> str:
+    return _load().lra_version().decode()
+
+
+def lra_precondition(kind: str, n: int, depth_or_nnz: int, perm_or_rows, signs) -> Multiplier:
+    """Right multiplier M of W' = W M: ``kind`` 'arht' (2^{-d/2} D H_{n,d} P) or
+    'sparse' (+-1/sqrt(nnz) entries).  perm_or_rows / signs: host int32 / int8
+    arrays (numpy or CPU tensors) holding the random draws."""
+    import numpy as np
+    L = _load()
+    k = {"arht": LRA_MULT_ARHT, "sparse": LRA_MULT_SPARSE_PM1}[kind]
+    idx = np.ascontiguousarray(np.asarray(perm_or_rows), dtype=np.int32).reshape(-1)
+    sg = np.ascontiguousarray(np.asarray(signs), dtype=np.int8).reshape(-1)
+    h = ct.c_void_p()
+    _check(L.lra_precondition(ct.byref(h), k, int(n), int(depth_or_nnz), idx.ctypes.data, sg.ctypes.data),
+           "lra_precondition")
+    return Multiplier(h.value, k, n)
+
+
+def lra_multiplier_destroy(mult: Multiplier) -> None:
+    if mult is not None and mult.handle:
+        _check(_load().lra_multiplier_destroy(mult.handle), "lra_multiplier_destroy")
+        mult.handle = None
+
+
+def _params(k, sweeps, h, rank_tol, max_swaps, mode) -> _Params:
+    p = _Params()
+    p.k, p.sweeps, p.h, p.rank_tol, p.max_swaps, p.mode = int(k), int(sweeps), float(h), float(rank_tol), \
+        int(max_swaps), int(mode)
+    return p
+
+
+def lra_ca_workspace_size(problem: Problem, k: int, sweeps: int = 3, h: float = 1.01, rank_tol: float = 1e-13,
+                          max_swaps: int = 1000, mode: int = LRA_MODE_FP64,
+                          multiplier: Optional[Multiplier] = None) -> int:
+    L = _load()
+    out = ct.c_size_t()
+    pc, pp = problem._c(), _params(k, sweeps, h, rank_tol, max_swaps, mode)
+    _check(L.lra_ca_workspace_size(ct.byref(pc), ct.byref(pp), multiplier.handle if multiplier else None,
+                                   ct.byref(out)), "lra_ca_workspace_size")
+    return out.value
+
+
+def lra_ca_run(problem: Problem, I0: torch.Tensor, k: int, sweeps: int = 3, h: float = 1.01,
+               rank_tol: float = 1e-13, max_swaps: int = 1000, mode: int = LRA_MODE_FP64,
+               multiplier: Optional[Multiplier] = None, out: Optional[dict] = None,
+               workspace: Optional[torch.Tensor] = None, stream=None) -> dict:
+    """C-A CUR approximation W ~ C U R of W' = W M (see lra_ca_run in lra.h).
+
+    I0: device int32 tensor of k distinct initial rows.  Returns a dict of
+    device tensors I, J, C (m x k), U (k x k), R (k x n), logvol (2*sweeps),
+    info (rank, swaps, loops, status); the call is asynchronous on ``stream``.
+    Pass ``out`` (same dict layout) and ``workspace`` to reuse buffers."""
+    L = _load()
+    dev = (problem.W if problem.W is not None else problem.X).device
+    _dev(I0, torch.int32, "I0")
+    pc, pp = problem._c(), _params(k, sweeps, h, rank_tol, max_swaps, mode)
+    mh = multiplier.handle if multiplier else None
+    if out is None:
+        out = dict(I=torch.empty(k, dtype=torch.int32, device=dev), J=torch.empty(k, dtype=torch.int32, device=dev),
+                   C=torch.empty(problem.m, k, dtype=torch.float64, device=dev),
+                   U=torch.empty(k, k, dtype=torch.float64, device=dev),
+                   R=torch.empty(k, problem.n, dtype=torch.float64, device=dev),
+                   logvol=torch.empty(2 * sweeps, dtype=torch.float64, device=dev),
+                   info=torch.empty(4, dtype=torch.int32, device=dev))
+    if workspace is None:
+        nb = ct.c_size_t()
+        _check(L.lra_ca_workspace_size(ct.byref(pc), ct.byref(pp), mh, ct.byref(nb)), "lra_ca_workspace_size")
+        workspace = _workspace(nb.value, dev)
+    cur = _Cur()
+    for f in ("I", "J", "C", "U", "R", "logvol", "info"):
+        setattr(cur, f, _dev(out[f], name=f).data_ptr())
+    _check(L.lra_ca_run(ct.byref(pc), ct.byref(pp), mh, I0.data_ptr(), ct.byref(cur), workspace.data_ptr(),
+                        workspace.numel(), _stream(stream)), "lra_ca_run")
+    out["_workspace"] = workspace
+    return out
+
+
+def lra_cur_apply(C: torch.Tensor, U: torch.Tensor, R: torch.Tensor, X: torch.Tensor,
+                  Y: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
+                  stream=None) -> torch.Tensor:
+    """Y = C (U (R X)) in FP64 on the device."""
+    L = _load()
+    for t, nm in ((C, "C"), (U, "U"), (R, "R"), (X, "X")):
+        _dev(t, torch.float64, nm)
+    m, k = C.shape
+    n = R.shape[1]
+    X2 = X if X.dim() == 2 else X.view(-1, 1)
+    nrhs = X2.shape[1]
+    if Y is None:
+        Y = torch.empty(m, nrhs, dtype=torch.float64, device=C.device)
+    if workspace is None:
+        nb = ct.c_size_t()
+        _check(L.lra_cur_apply_workspace_size(n, k, nrhs, ct.byref(nb)), "lra_cur_apply_workspace_size")
+        workspace = _workspace(nb.value, C.device)
+    _check(L.lra_cur_apply(C.data_ptr(), U.data_ptr(), R.data_ptr(), m, n, k, X2.data_ptr(), nrhs, Y.data_ptr(),
+                           workspace.data_ptr(), workspace.numel(), _stream(stream)), "lra_cur_apply")
+    return Y
+
+
+def lra_residual_sample(problem: Problem, C: torch.Tensor, U: torch.Tensor, R: torch.Tensor, Q: torch.Tensor,
+                        S: torch.Tensor, E: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Statistics [mean, var, mean|e|, max|e|, fro ratio] (device FP64 tensor of
+    5) of the sample E[Q,S] of W - C U R."""
+    L = _load()
+    k = C.shape[1]
+    q, s = Q.numel(), S.numel()
+    stats = torch.empty(5, dtype=torch.float64, device=C.device)
+    nb = ct.c_size_t()
+    _check(L.lra_residual_sample_workspace_size(k, q, s, ct.byref(nb)), "lra_residual_sample_workspace_size")
+    ws = _workspace(nb.value, C.device)
+    pc = problem._c()
+    _check(L.lra_residual_sample(ct.byref(pc), C.data_ptr(), U.data_ptr(), R.data_ptr(), k,
+                                 _dev(Q, torch.int32, "Q").data_ptr(), q, _dev(S, torch.int32, "S").data_ptr(), s,
+                                 stats.data_ptr(), E.data_ptr() if E is not None else None, ws.data_ptr(),
+                                 ws.numel(), _stream(stream)), "lra_residual_sample")
+    return stats

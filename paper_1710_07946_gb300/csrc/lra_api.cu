@@ -1,0 +1,130 @@
+// lra_api.cu -- multiplier handles, problem validation and small utilities of
+// the C ABI.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "lra_internal.h"
+
+namespace lra {
+
+lra_status make_dev_problem(const lra_problem* p, lra_multiplier mult, DevProblem* out) {
+  if (p == nullptr || out == nullptr) return LRA_ERR_INVALID_ARG;
+  if (p->m < 1 || p->n < 1 || p->m >= (int64_t(1) << 31) || p->n >= (int64_t(1) << 31)) return LRA_ERR_INVALID_ARG;
+  DevProblem d;
+  std::memset(&d, 0, sizeof(d));
+  d.src = p->src;
+  d.dtype = p->dtype;
+  d.m = p->m;
+  d.n = p->n;
+  d.ldw = p->ldw;
+  d.W = p->W;
+  d.X = p->X;
+  d.Y = p->Y;
+  d.ell = p->length_scale;
+  if (p->src == LRA_DENSE) {
+    if (p->W == nullptr || p->ldw < p->n) return LRA_ERR_INVALID_ARG;
+    if (p->dtype != LRA_F64 && p->dtype != LRA_F32) return LRA_ERR_INVALID_ARG;
+  } else if (p->src == LRA_KERNEL_LAPLACE || p->src == LRA_KERNEL_GAUSSIAN) {
+    if (p->X == nullptr || p->Y == nullptr) return LRA_ERR_INVALID_ARG;
+    if (p->src == LRA_KERNEL_GAUSSIAN && !(p->length_scale > 0.0)) return LRA_ERR_INVALID_ARG;
+  } else {
+    return LRA_ERR_INVALID_ARG;
+  }
+  d.mkind = LRA_MULT_NONE;
+  if (mult != nullptr && mult->kind != LRA_MULT_NONE) {
+    if (mult->n != p->n) return LRA_ERR_INVALID_ARG;
+    d.mkind = mult->kind;
+    d.perm = mult->d_idx;
+    d.sign = mult->d_sign;
+    d.mscale = mult->scale;
+    if (mult->kind == LRA_MULT_ARHT) {
+      d.depth = mult->param;
+      d.s = p->n >> mult->param;
+    } else {
+      d.nnz = mult->param;
+    }
+  }
+  *out = d;
+  return LRA_OK;
+}
+
+lra_status current_device_info(DeviceInfo* info) {
+  int dev = 0;
+  LRA_CUDA_TRY(cudaGetDevice(&dev));
+  int sms = 0, optin = 0;
+  LRA_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  LRA_CUDA_TRY(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  info->device = dev;
+  info->sms = sms;
+  info->smem_optin = (size_t)optin;
+  return LRA_OK;
+}
+
+}  // namespace lra
+
+extern "C" {
+
+lra_status lra_precondition(lra_multiplier* out, int32_t kind, int64_t n, int32_t param, const int32_t* idx,
+                            const int8_t* signs) {
+  if (out == nullptr) return LRA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (n < 1 || n >= (int64_t(1) << 31) || idx == nullptr || signs == nullptr) return LRA_ERR_INVALID_ARG;
+  size_t cnt = 0;
+  double scale = 1.0;
+  if (kind == LRA_MULT_ARHT) {
+    if (param < 1 || param > 10 || (n % (int64_t(1) << param)) != 0) return LRA_ERR_INVALID_ARG;
+    cnt = (size_t)n;
+    std::vector<unsigned char> seen((size_t)n, 0);
+    for (int64_t j = 0; j < n; ++j) {
+      if (idx[j] < 0 || idx[j] >= n || seen[(size_t)idx[j]]) return LRA_ERR_INVALID_ARG;
+      seen[(size_t)idx[j]] = 1;
+      if (signs[j] != 1 && signs[j] != -1) return LRA_ERR_INVALID_ARG;
+    }
+    scale = 1.0 / std::sqrt((double)(int64_t(1) << param));
+  } else if (kind == LRA_MULT_SPARSE_PM1) {
+    if (param < 1 || param > 16 || param > n) return LRA_ERR_INVALID_ARG;
+    cnt = (size_t)n * (size_t)param;
+    for (int64_t j = 0; j < n; ++j)
+      for (int t = 0; t < param; ++t) {
+        int32_t r = idx[j * param + t];
+        if (r < 0 || r >= n) return LRA_ERR_INVALID_ARG;
+        if (t > 0 && r <= idx[j * param + t - 1]) return LRA_ERR_INVALID_ARG;
+        int8_t s = signs[j * param + t];
+        if (s != 1 && s != -1) return LRA_ERR_INVALID_ARG;
+      }
+    scale = 1.0 / std::sqrt((double)param);
+  } else {
+    return LRA_ERR_INVALID_ARG;
+  }
+  lra_multiplier m = new lra_multiplier_s;
+  m->kind = kind;
+  m->n = n;
+  m->param = param;
+  m->scale = scale;
+  m->d_idx = nullptr;
+  m->d_sign = nullptr;
+  if (cudaMalloc(&m->d_idx, cnt * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&m->d_sign, cnt * sizeof(int8_t)) != cudaSuccess ||
+      cudaMemcpy(m->d_idx, idx, cnt * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_sign, signs, cnt * sizeof(int8_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(m->d_idx);
+    cudaFree(m->d_sign);
+    delete m;
+    return LRA_ERR_CUDA;
+  }
+  *out = m;
+  return LRA_OK;
+}
+
+lra_status lra_multiplier_destroy(lra_multiplier m) {
+  if (m == nullptr) return LRA_OK;
+  cudaError_t e1 = cudaFree(m->d_idx);
+  cudaError_t e2 = cudaFree(m->d_sign);
+  delete m;
+  return (e1 == cudaSuccess && e2 == cudaSuccess) ? LRA_OK : LRA_ERR_CUDA;
+}
+
+const char* lra_version(void) { return "lra-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// lra_nucleus.cuh -- the canonical nucleus U = pinv(G_r) of a k x k generator G
+// on one CTA, in FP64 (paper: Algorithm algcnnncl, with the rank-revealing
+// factorisation that Remark reubsc allows in place of the SVD).
+//
+//   1. Householder QR with column pivoting, G P = Q R: at step t the column with
+//      the largest squared norm over rows t.. (recomputed each step; one thread
+//      per column accumulates it in ascending row order) moves to position t,
+//      the lowest index winning ties.
+//   2. r = number of leading |R_tt| > tol |R_00|.
+//   3. U = P Z S^{-T} Q_r^T, where T = [R11 R12] (r x k) and T^T = Z S is its QR
+//      (a complete orthogonal decomposition); for r = k this is P R^{-1} Q^T.
+// Every reflector is the textbook H = I - tau v v^T with v_0 = 1 and
+// beta = -sign(alpha) ||x||; each inner product is an ascending fma chain owned
+// by one thread, so the result does not depend on the thread count.
+#pragma once
+
+#include "lra_device.cuh"
+
+namespace lra {
+
+// Shared memory needed by nucleus_cta for generator size k.
+__host__ __device__ inline size_t nucleus_smem_bytes(int k) {
+  return sizeof(double) * (3 * (size_t)k * k + 4 * (size_t)KMAX) + sizeof(int32_t) * 2 * KMAX + 64;
+}
+
+// Householder reflector of the column x[0..len) (unit stride, shared memory),
+// computed by thread 0, scaled by all threads.  Returns tau to every thread.
+__device__ inline double house_cta(double* x, int len, double* bcast) {
+  if (threadIdx.x == 0) {
+    double alpha = x[0], xn2 = 0.0, tau = 0.0, scal = 0.0, beta = alpha;
+    for (int i = 1; i < len; ++i) xn2 = fma(x[i], x[i], xn2);
+    if (xn2 != 0.0) {
+      double nrm = sqrt(fma(alpha, alpha, xn2));
+      beta = (alpha >= 0.0) ? -nrm : nrm;
+      tau = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    bcast[0] = tau; bcast[1] = scal; bcast[2] = beta;
+  }
+  __syncthreads();
+  const double tau = bcast[0], scal = bcast[1];
+  if (tau != 0.0) {
+    for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] = x[i] * scal;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && tau != 0.0) x[0] = bcast[2];
+  __syncthreads();
+  return tau;
+}
+
+// y <- (I - tau v v^T) y for one column, by the calling thread alone.
+__device__ __forceinline__ void apply_house_seq(const double* v, double tau, double* y, int len) {
+  if (tau == 0.0) return;
+  double w = y[0];
+  for (int i = 1; i < len; ++i) w = fma(v[i], y[i], w);
+  const double c = tau * w;
+  y[0] = y[0] - c;
+  for (int i = 1; i < len; ++i) y[i] = fma(-c, v[i], y[i]);
+}
+
+// U (k x k, row-major, global or shared) <- pinv of the rank-r QRP truncation of
+// G (k x k row-major, global).  smem: nucleus_smem_bytes(k).  Returns r.
+__device__ int nucleus_cta(const double* G, int k, double tol, double* U, unsigned char* smem) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* A = reinterpret_cast<double*>(smem);          // column-major k x k
+  double* Q = A + (size_t)k * k;                        // Q^T, column-major
+  double* T = Q + (size_t)k * k;                        // T^T (k x r), column-major
+  double* taus = T + (size_t)k * k;
+  double* tz = taus + KMAX;
+  double* nrm = tz + KMAX;
+  double* bc = nrm + KMAX;
+  int32_t* perm = reinterpret_cast<int32_t*>(bc + KMAX);
+  int32_t* ctl = perm + KMAX;
+
+  for (int it = tid; it < k * k; it += nt) {
+    int i = it / k, j = it - i * k;
+    A[j * k + i] = G[it];
+  }
+  for (int j = tid; j < k; j += nt) perm[j] = j;
+  __syncthreads();
+  for (int t = 0; t < k; ++t) {
+    for (int j = t + tid; j < k; j += nt) {
+      double s = 0.0;
+      for (int i = t; i < k; ++i) s = fma(A[j * k + i], A[j * k + i], s);
+      nrm[j] = s;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int pj = t; double bn = -1.0;
+      for (int j = t; j < k; ++j) if (nrm[j] > bn) { bn = nrm[j]; pj = j; }
+      ctl[0] = pj;
+      if (pj != t) { int tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp; }
+    }
+    __syncthreads();
+    const int pj = ctl[0];
+    if (pj != t)
+      for (int i = tid; i < k; i += nt) {
+        double tmp = A[t * k + i]; A[t * k + i] = A[pj * k + i]; A[pj * k + i] = tmp;
+      }
+    __syncthreads();
+    const double tau = house_cta(&A[t * k + t], k - t, bc);
+    if (tid == 0) taus[t] = tau;
+    for (int j = t + 1 + tid; j < k; j += nt) apply_house_seq(&A[t * k + t], tau, &A[j * k + t], k - t);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    int r = 0;
+    const double r00 = fabs(A[0]);
+    if (r00 > 0.0) while (r < k && fabs(A[r * k + r]) > tol * r00) ++r;
+    ctl[1] = r;
+  }
+  __syncthreads();
+  const int r = ctl[1];
+  for (int it = tid; it < k * k; it += nt) U[it] = 0.0;
+  if (r == 0) { __syncthreads(); return 0; }
+
+  // Q^T = H_{k-1} ... H_0 I, one column per thread
+  for (int j = tid; j < k; j += nt) {
+    for (int i = 0; i < k; ++i) Q[j * k + i] = (i == j) ? 1.0 : 0.0;
+    for (int t = 0; t < k; ++t) apply_house_seq(&A[t * k + t], taus[t], &Q[j * k + t], k - t);
+  }
+  if (r < k) {
+    for (int it = tid; it < k * r; it += nt) {
+      int c = it / k, i = it - c * k;
+      T[c * k + i] = (i >= c) ? A[i * k + c] : 0.0;
+    }
+    __syncthreads();
+    for (int c = 0; c < r; ++c) {
+      const double tau = house_cta(&T[c * k + c], k - c, bc);
+      if (tid == 0) tz[c] = tau;
+      for (int j = c + 1 + tid; j < r; j += nt) apply_house_seq(&T[c * k + c], tau, &T[j * k + c], k - c);
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  // X = Z S^{-T} Q_r^T (or R^{-1} Q^T), one column per thread, in place in Q
+  for (int col = tid; col < k; col += nt) {
+    double* v = &Q[col * k];
+    if (r == k) {
+      for (int i = k - 1; i >= 0; --i) {
+        double s = v[i];
+        for (int p = i + 1; p < k; ++p) s = fma(-A[p * k + i], v[p], s);
+        v[i] = s / A[i * k + i];
+      }
+    } else {
+      for (int i = 0; i < r; ++i) {
+        double s = v[i];
+        for (int p = 0; p < i; ++p) s = fma(-T[i * k + p], v[p], s);
+        v[i] = s / T[i * k + i];
+      }
+      for (int i = r; i < k; ++i) v[i] = 0.0;
+      for (int c = r - 1; c >= 0; --c) apply_house_seq(&T[c * k + c], tz[c], &v[c], k - c);
+    }
+  }
+  __syncthreads();
+  for (int it = tid; it < k * k; it += nt) {
+    int i = it / k, col = it - i * k;
+    U[(size_t)perm[i] * k + col] = Q[col * k + i];
+  }
+  __syncthreads();
+  return r;
+}
+
+}  // namespace lra

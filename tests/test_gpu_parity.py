@@ -1,0 +1,177 @@
+"""GPU parity of the CUDA C-A path with the FP64 oracle (through the C ABI).
+
+Bar: row and column index sets bit-exact (lowest-index tie-break); gathered
+factors C = W'[:,J] and R = W[I,:] identical; the nucleus U within 1e-10
+relative (max-norm); swap / loop counters and statuses equal.
+"""
+import numpy as np
+import pytest
+
+import lra_inputs as li
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from gpu_helpers import assert_parity, gpu_ca  # noqa: E402
+
+
+def run_both(p, k, sweeps, I0, **kw):
+    o = oracle.ca_run(p, k, sweeps, I0, **kw)
+    g = gpu_ca(p, k, sweeps, I0, **kw)
+    return o, g
+
+
+# ---------------------------------------------------------------- the 256 x 256 workload
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("noise", [1e-8, 0.0])
+def test_dense_256_rank8(seed, noise):
+    """256 x 256 FP64, U diag(2^-i) V^T (+1e-8 noise), k = 8, 3 sweeps."""
+    p = li.dense_lowrank(256, 256, r=8, noise=noise, seed=seed)
+    I0 = li.initial_rows(256, 8, 1000 + seed)
+    o, g = run_both(p, 8, 3, I0)
+    assert_parity(o, g)
+    err = np.linalg.norm(p.W - g["C"] @ g["U"] @ g["R"]) / np.linalg.norm(p.W)
+    assert err < (1e-12 if noise == 0 else 1e-5)
+
+
+# ---------------------------------------------------------------- multi-CTA, ragged chunks
+@pytest.mark.parametrize("m,n,k", [(2000, 1500, 16), (1001, 77, 7), (77, 3001, 12), (4099, 4097, 40)])
+def test_dense_multi_cta_ragged(m, n, k):
+    p = li.factor_gaussian(max(m, n), k + 2, 1e-3, seed=m + n)
+    p.W = np.ascontiguousarray(p.W[:m, :n])
+    p.m, p.n = m, n
+    I0 = li.initial_rows(m, k, 7)
+    o, g = run_both(p, k, 3, I0)
+    assert_parity(o, g)
+
+
+@pytest.mark.parametrize("mult,arg", [("arht", 1), ("arht", 2), ("arht", 3), ("sparse", 4)])
+def test_float32_with_multipliers(mult, arg):
+    p = li.dense_spiky(1024, r=16, seed=3)
+    if mult == "arht":
+        li.with_arht(p, arg, 11)
+    else:
+        li.with_sparse(p, arg, 11)
+    I0 = li.initial_rows(1024, 24, 5)
+    o, g = run_both(p, 24, 4, I0)
+    assert_parity(o, g)
+
+
+@pytest.mark.parametrize("k", [8, 32])
+def test_laplace_kernel_entries(k):
+    p = li.laplace_clusters(3000, 2500, seed=2)
+    I0 = li.initial_rows(3000, k, 9)
+    o, g = run_both(p, k, 3, I0)
+    assert_parity(o, g)
+
+
+def test_gaussian_kernel_close_to_oracle():
+    """exp() is not bit-identical across libraries: compare approximation quality."""
+    p = li.gaussian_clusters(900, 800, ell=0.3, seed=4)
+    I0 = li.initial_rows(900, 12, 3)
+    o, g = run_both(p, 12, 3, I0)
+    X, Y = p.X, p.Y
+    K = np.exp(-np.sum((X[:, None, :] - Y[None, :, :]) ** 2, axis=2) / (2 * 0.3 ** 2))
+    eo = np.linalg.norm(K - o["C"] @ o["U"] @ o["R"]) / np.linalg.norm(K)
+    eg = np.linalg.norm(K - g["C"] @ g["U"] @ g["R"]) / np.linalg.norm(K)
+    assert g["status"] == o["status"] and eg <= 2 * eo + 1e-14
+
+
+# ---------------------------------------------------------------- edge cases
+def test_k_equals_one():
+    p = li.factor_gaussian(300, 3, 1e-2, seed=1)
+    o, g = run_both(p, 1, 3, li.initial_rows(300, 1, 0))
+    assert_parity(o, g)
+
+
+def test_k_equals_min_dimension():
+    p = li.factor_gaussian(40, 5, 1e-2, seed=1)
+    p.W = np.ascontiguousarray(p.W[:, :12]); p.n = 12
+    o, g = run_both(p, 12, 2, li.initial_rows(40, 12, 0))
+    assert_parity(o, g)
+
+
+def test_rank_deficient_strip_status():
+    p = li.factor_gaussian(200, 5, 0.0, seed=2)
+    p.W[:, 3] = 0.0
+    W = p.W.copy(); W[:, :] = 0.0; W[:, :3] = p.W[:, :3]      # exact rank <= 3
+    p.W = W
+    o, g = run_both(p, 6, 2, li.initial_rows(200, 6, 1))
+    assert o["status"] == 16 and g["status"] == 16
+    np.testing.assert_array_equal(g["I"], o["I"])
+    np.testing.assert_array_equal(g["J"], o["J"])
+
+
+def test_nonfinite_input_status():
+    p = li.dense_lowrank(128, 128, r=4, seed=0)
+    I0 = li.initial_rows(128, 4, 1)
+    p.W[I0[2], 17] = np.nan
+    o, g = run_both(p, 4, 2, I0)
+    assert o["status"] == 3 and g["status"] == 3
+
+
+def test_max_swaps_zero_not_converged():
+    p = li.factor_gaussian(500, 10, 1e-2, seed=8)
+    o, g = run_both(p, 10, 2, li.initial_rows(500, 10, 3), max_swaps=0)
+    assert_parity(o, g)
+    assert g["status"] == 17
+
+
+def test_invalid_initial_rows_reported():
+    import paper_1710_07946_gb300 as lra
+    p = li.dense_lowrank(64, 64, r=4, seed=0)
+    g = gpu_ca(p, 4, 2, np.array([1, 2, 2, 3], np.int32))
+    assert g["status"] == lra.LRA_ERR_INVALID_ARG
+
+
+def test_host_side_rejections():
+    import paper_1710_07946_gb300 as lra
+    from gpu_helpers import to_device
+    p = li.dense_lowrank(64, 64, r=4, seed=0)
+    prob, _ = to_device(p)
+    I0 = torch.arange(8, dtype=torch.int32, device="cuda")
+    with pytest.raises(lra.LraError):
+        lra.lra_ca_run(prob, I0, 65)          # k > 64
+    with pytest.raises(lra.LraError):
+        lra.lra_ca_run(prob, I0, 8, h=0.5)     # h < 1
+    with pytest.raises(lra.LraError):
+        lra.lra_ca_run(prob, I0, 8, workspace=torch.empty(16, dtype=torch.uint8, device="cuda"))
+
+
+def test_repeatable_and_stream_ordered():
+    p = li.dense_lowrank(512, 384, r=8, noise=1e-6, seed=5)
+    I0 = li.initial_rows(512, 8, 2)
+    a = gpu_ca(p, 8, 3, I0)
+    b = gpu_ca(p, 8, 3, I0)
+    for key in ("I", "J", "C", "U", "R"):
+        np.testing.assert_array_equal(a[key], b[key])
+
+
+# ---------------------------------------------------------------- apply / residual
+def test_cur_apply_matches_oracle():
+    import paper_1710_07946_gb300 as lra
+    p = li.dense_lowrank(700, 900, r=6, noise=1e-6, seed=1)
+    o = oracle.ca_run(p, 6, 2, li.initial_rows(700, 6, 0))
+    X = li.rhs(900, 5, 3)
+    Yo = oracle.cur_apply(o["C"], o["U"], o["R"], X)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    Yg = lra.lra_cur_apply(t(o["C"]), t(o["U"]), t(o["R"]), t(X)).cpu().numpy()
+    assert np.abs(Yg - Yo).max() <= 1e-12 * np.abs(Yo).max()
+
+
+def test_residual_sample_matches_oracle():
+    import paper_1710_07946_gb300 as lra
+    from gpu_helpers import to_device
+    p = li.dense_lowrank(300, 280, r=5, noise=1e-5, seed=2)
+    o = oracle.ca_run(p, 5, 2, li.initial_rows(300, 5, 0))
+    Q, S = li.sample_positions(300, 280, 40, 30, 6)
+    st_o = oracle.residual_sample(p, o["C"], o["U"], o["R"], Q, S)
+    prob, _ = to_device(p)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    st_g = lra.lra_residual_sample(prob, t(o["C"]), t(o["U"]), t(o["R"]), t(Q), t(S)).cpu().numpy()
+    np.testing.assert_allclose(st_g[1:], st_o[1:], rtol=1e-9)
+    assert abs(st_g[0] - st_o[0]) <= 1e-9 * st_o[2]
