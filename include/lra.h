@@ -196,6 +196,28 @@ lra_status lra_residual_sample(const lra_problem* prob, const double* C, const d
 /* Workspace bytes of lra_residual_sample for rank k and a q x s sample. */
 lra_status lra_residual_sample_workspace_size(int32_t k, int32_t q, int32_t s, size_t* bytes);
 
+/* ------------------------------------------------------------------------- */
+/* Instrumentation (no counterpart in the paper: benchmark support)           */
+/* ------------------------------------------------------------------------- */
+#define LRA_PROFILE_NAME_LEN 32
+
+/* Number of kernels the library has launched in this process (all devices). */
+int64_t lra_launch_count(void);
+
+/* on != 0: bracket every subsequent kernel launch with two CUDA events recorded
+ * on the launch's stream (host cost: two event creations per launch).  Do not
+ * enable while capturing a CUDA graph.  Never fails. */
+lra_status lra_profile_enable(int32_t on);
+
+/* Wait for the events recorded since the last collect and report, per kernel
+ * name, the summed elapsed milliseconds and the launch count; the records are
+ * then discarded.  names: max_kernels * LRA_PROFILE_NAME_LEN host chars (or
+ * NULL), total_ms / launches: max_kernels entries (or NULL).  *n_out receives
+ * the number of distinct kernels seen (entries beyond max_kernels are dropped).
+ * Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA (an event failed). */
+lra_status lra_profile_collect(int32_t max_kernels, char* names, double* total_ms, int64_t* launches,
+                               int32_t* n_out);
+
 /* Library version string, for diagnostics. */
 const char* lra_version(void);
 

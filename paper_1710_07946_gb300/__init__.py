@@ -22,7 +22,8 @@ __all__ = [
     "LRA_OK", "LRA_ERR_INVALID_ARG", "LRA_ERR_CUDA", "LRA_ERR_NONFINITE", "LRA_ERR_TIMEOUT", "LRA_ERR_WORKSPACE",
     "LRA_WARN_RANK_DEFICIENT", "LRA_WARN_NOT_CONVERGED", "LraError", "Problem", "Multiplier",
     "lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run", "lra_cur_apply",
-    "lra_residual_sample", "lra_version", "library_path",
+    "lra_residual_sample", "lra_version", "library_path", "lra_launch_count", "lra_profile_enable",
+    "lra_profile_collect",
 ]
 
 LRA_OK, LRA_ERR_INVALID_ARG, LRA_ERR_CUDA, LRA_ERR_NONFINITE, LRA_ERR_TIMEOUT, LRA_ERR_WORKSPACE = 0, 1, 2, 3, 4, 5
@@ -83,9 +84,12 @@ def _load():
     L.lra_residual_sample.argtypes = [P, vp, vp, vp, i32, vp, i32, vp, i32, vp, vp, vp, sz, vp]
     L.lra_residual_sample_workspace_size.argtypes = [i32, i32, i32, ct.POINTER(sz)]
     L.lra_version.restype = ct.c_char_p
+    L.lra_launch_count.restype = ct.c_int64
+    L.lra_profile_enable.argtypes = [i32]
+    L.lra_profile_collect.argtypes = [i32, vp, vp, vp, ct.POINTER(i32)]
     for f in ("lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run",
               "lra_cur_apply", "lra_cur_apply_workspace_size", "lra_residual_sample",
-              "lra_residual_sample_workspace_size"):
+              "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect"):
         getattr(L, f).restype = ct.c_int
     _lib = L
     return L
@@ -288,3 +292,29 @@ def lra_residual_sample(problem: Problem, C: torch.Tensor, U: torch.Tensor, R: t
                                  stats.data_ptr(), E.data_ptr() if E is not None else None, ws.data_ptr(),
                                  ws.numel(), _stream(stream)), "lra_residual_sample")
     return stats
+
+
+def lra_launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(_load().lra_launch_count())
+
+
+def lra_profile_enable(on: bool = True) -> None:
+    """Bracket every later kernel launch with CUDA events on its stream."""
+    _check(_load().lra_profile_enable(1 if on else 0), "lra_profile_enable")
+
+
+def lra_profile_collect(max_kernels: int = 32) -> dict:
+    """{kernel name: (total ms, launches)} since the last collect (waits for the events)."""
+    L = _load()
+    NAME = 32
+    names = ct.create_string_buffer(max_kernels * NAME)
+    ms = (ct.c_double * max_kernels)()
+    cnt = (ct.c_int64 * max_kernels)()
+    n = ct.c_int32()
+    _check(L.lra_profile_collect(max_kernels, names, ms, cnt, ct.byref(n)), "lra_profile_collect")
+    out = {}
+    for i in range(min(n.value, max_kernels)):
+        nm = names.raw[i * NAME:(i + 1) * NAME].split(b"\0", 1)[0].decode()
+        out[nm] = (ms[i], int(cnt[i]))
+    return out

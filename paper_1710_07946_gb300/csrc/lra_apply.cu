@@ -13,6 +13,7 @@
 #include <algorithm>
 
 #include "lra_internal.h"
+#include "lra_profile.h"
 
 namespace lra {
 
@@ -189,14 +190,14 @@ lra_status lra_cur_apply(const double* C, const double* U, const double* R, int6
   double* partial = reinterpret_cast<double*>(ws);
   double* T1 = reinterpret_cast<double*>(ws + align_up(sizeof(double) * (size_t)nb * k * nrhs, 256));
   double* T2 = T1 + align_up(sizeof(double) * (size_t)k * nrhs, 256) / sizeof(double);
-  apply_rx_kernel<<<nb, NT, 0, stream>>>(R, X, n, k, nrhs, partial);
-  apply_u_kernel<<<1, NT, 0, stream>>>(partial, nb, U, k, nrhs, T1, T2);
+  { LaunchScope ls(stream, "apply_rx_kernel"); apply_rx_kernel<<<nb, NT, 0, stream>>>(R, X, n, k, nrhs, partial); }
+  { LaunchScope ls(stream, "apply_u_kernel"); apply_u_kernel<<<1, NT, 0, stream>>>(partial, nb, U, k, nrhs, T1, T2); }
   DeviceInfo dev;
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
   const int64_t tot = m * nrhs;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tot + NT - 1) / NT, (int64_t)dev.sms * 8));
-  apply_c_kernel<<<grid, NT, 0, stream>>>(C, T2, m, k, nrhs, Y);
+  { LaunchScope ls(stream, "apply_c_kernel"); apply_c_kernel<<<grid, NT, 0, stream>>>(C, T2, m, k, nrhs, Y); }
   return cuda_status(cudaGetLastError());
 }
 
@@ -227,10 +228,10 @@ lra_status lra_residual_sample(const lra_problem* prob, const double* C, const d
   DeviceInfo dev;
   if ((st = current_device_info(&dev)) != LRA_OK) return st;
   const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)q * k + NT - 1) / NT, dev.sms * 4));
-  resid_cu_kernel<<<g1, NT, 0, stream>>>(C, U, Q, q, k, CU);
+  { LaunchScope ls(stream, "resid_cu_kernel"); resid_cu_kernel<<<g1, NT, 0, stream>>>(C, U, Q, q, k, CU); }
   const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)q * s + NT - 1) / NT, dev.sms * 8));
-  resid_e_kernel<<<g2, NT, 0, stream>>>(P, CU, R, Q, S, q, s, k, Eout, W2);
-  resid_stats_kernel<<<1, NT, 0, stream>>>(Eout, W2, (int64_t)q * s, stats);
+  { LaunchScope ls(stream, "resid_e_kernel"); resid_e_kernel<<<g2, NT, 0, stream>>>(P, CU, R, Q, S, q, s, k, Eout, W2); }
+  { LaunchScope ls(stream, "resid_stats_kernel"); resid_stats_kernel<<<1, NT, 0, stream>>>(Eout, W2, (int64_t)q * s, stats); }
   return cuda_status(cudaGetLastError());
 }
 

@@ -13,6 +13,7 @@
 #include "lra_ca_core.cuh"
 #include "lra_internal.h"
 #include "lra_nucleus.cuh"
+#include "lra_profile.h"
 
 namespace lra {
 
@@ -164,6 +165,7 @@ lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_mul
   if (pl.nblk == 1) {
     LRA_CUDA_TRY(cudaFuncSetAttribute(ca_kernel<SoloGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)pl.smem));
+    LaunchScope ls(stream, "ca_kernel");
     ca_kernel<SoloGroup><<<1, NT, pl.smem, stream>>>(A, SoloGroup{});
     LRA_CUDA_TRY(cudaGetLastError());
   } else {
@@ -182,11 +184,15 @@ lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_mul
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    LaunchScope ls(stream, "ca_kernel");
     LRA_CUDA_TRY(cudaLaunchKernelEx(&cfg, ca_kernel<GridGroup>, A, grp));
   }
   const size_t nsm = nucleus_smem_bytes(par->k);
   LRA_CUDA_TRY(cudaFuncSetAttribute(nucleus_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)nsm));
-  nucleus_kernel<<<1, NT, nsm, stream>>>(A.G, par->k, par->rank_tol, out->U, out->info);
+  {
+    LaunchScope ls(stream, "nucleus_kernel");
+    nucleus_kernel<<<1, NT, nsm, stream>>>(A.G, par->k, par->rank_tol, out->U, out->info);
+  }
   LRA_CUDA_TRY(cudaGetLastError());
   return LRA_OK;
 }

@@ -175,3 +175,18 @@ def test_residual_sample_matches_oracle():
     st_g = lra.lra_residual_sample(prob, t(o["C"]), t(o["U"]), t(o["R"]), t(Q), t(S)).cpu().numpy()
     np.testing.assert_allclose(st_g[1:], st_o[1:], rtol=1e-9)
     assert abs(st_g[0] - st_o[0]) <= 1e-9 * st_o[2]
+
+
+# ---------------------------------------------------------------- full-size benchmark workload
+@pytest.mark.parametrize("mult", ["arht", "sparse"])
+def test_dense8192_benchmark_workload(mult):
+    """8192 x 8192 FP32 rank-32 + 1% spikes, ARHT d=2 or sparse +-1, k = 48,
+    4 loops: the benchmark's configuration, compared in full."""
+    p = li.dense_spiky(8192, r=32, seed=0)
+    if mult == "arht":
+        li.with_arht(p, 2, 7)
+    else:
+        li.with_sparse(p, 4, 7)
+    I0 = li.initial_rows(8192, 48, 11)
+    o, g = run_both(p, 48, 4, I0)
+    assert_parity(o, g)
