@@ -168,6 +168,32 @@ lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_mul
                       const lra_cur* out, void* workspace, size_t workspace_bytes, lra_stream_t stream);
 
 /*
+ * lra_ca_run_noalloc -- lra_ca_run without a caller-supplied workspace, for
+ * callers that cannot allocate device memory themselves: for instance a plug-in
+ * running inside a host application whose own allocator owns the whole device
+ * and forbids further cudaMalloc calls, or a program that only receives
+ * pre-placed device buffers for its inputs and outputs.  The paper has no
+ * counterpart: this is a deployment variant of lra_ca_run, with the same
+ * arguments (minus the workspace), results and device status.
+ *
+ * Scratch: one static device array of LRA_NOALLOC_SCRATCH_BYTES (256 KiB) per
+ * device, held by every device that loads the library until the process
+ * exits.  Problems whose lra_ca_workspace_size exceeds it are rejected with
+ * LRA_ERR_WORKSPACE before anything is launched (this happens when a strip
+ * chunk does not fit in shared memory, e.g. k = 64 with n = 65536).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  The call allocates no device memory.  All calls on a
+ * device share the one array: calls whose executions overlap on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * The array keeps the last call's contents; every call clears the parts that
+ * must start at zero.
+ */
+#define LRA_NOALLOC_SCRATCH_BYTES (256u * 1024u)
+lra_status lra_ca_run_noalloc(const lra_problem* prob, const lra_ca_params* par, lra_multiplier mult,
+                              const int32_t* I0, const lra_cur* out, lra_stream_t stream);
+
+/*
  * lra_cur_apply -- Y = C (U (R X)) for one CUR triple (paper: FMM / HSS stage
  * (iii), multiplication with the generators of the neutered block columns).
  * C m x k, U k x k, R k x n (as written by lra_ca_run), X n x nrhs, Y m x nrhs,

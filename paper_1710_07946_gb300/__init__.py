@@ -23,7 +23,7 @@ __all__ = [
     "LRA_WARN_RANK_DEFICIENT", "LRA_WARN_NOT_CONVERGED", "LraError", "Problem", "Multiplier",
     "lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run", "lra_cur_apply",
     "lra_residual_sample", "lra_version", "library_path", "lra_launch_count", "lra_profile_enable",
-    "lra_profile_collect",
+    "lra_profile_collect", "lra_ca_run_noalloc",
 ]
 
 LRA_OK, LRA_ERR_INVALID_ARG, LRA_ERR_CUDA, LRA_ERR_NONFINITE, LRA_ERR_TIMEOUT, LRA_ERR_WORKSPACE = 0, 1, 2, 3, 4, 5
@@ -79,6 +79,7 @@ def _load():
     L.lra_multiplier_destroy.argtypes = [vp]
     L.lra_ca_workspace_size.argtypes = [P, PP, vp, ct.POINTER(sz)]
     L.lra_ca_run.argtypes = [P, PP, vp, vp, PC, vp, sz, vp]
+    L.lra_ca_run_noalloc.argtypes = [P, PP, vp, vp, PC, vp]
     L.lra_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp, vp, sz, vp]
     L.lra_cur_apply_workspace_size.argtypes = [i64, i32, i32, ct.POINTER(sz)]
     L.lra_residual_sample.argtypes = [P, vp, vp, vp, i32, vp, i32, vp, i32, vp, vp, vp, sz, vp]
@@ -88,6 +89,7 @@ def _load():
     L.lra_profile_enable.argtypes = [i32]
     L.lra_profile_collect.argtypes = [i32, vp, vp, vp, ct.POINTER(i32)]
     for f in ("lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run",
+              "lra_ca_run_noalloc",
               "lra_cur_apply", "lra_cur_apply_workspace_size", "lra_residual_sample",
               "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect"):
         getattr(L, f).restype = ct.c_int
@@ -250,6 +252,23 @@ def lra_ca_run(problem: Problem, I0: torch.Tensor, k: int, sweeps: int = 3, h: f
     _check(L.lra_ca_run(ct.byref(pc), ct.byref(pp), mh, I0.data_ptr(), ct.byref(cur), workspace.data_ptr(),
                         workspace.numel(), _stream(stream)), "lra_ca_run")
     out["_workspace"] = workspace
+    return out
+
+
+def lra_ca_run_noalloc(problem: Problem, I0: torch.Tensor, out: dict, k: int, sweeps: int = 3, h: float = 1.01,
+                       rank_tol: float = 1e-13, max_swaps: int = 1000, mode: int = LRA_MODE_FP64,
+                       multiplier: Optional[Multiplier] = None, stream=None) -> dict:
+    """lra_ca_run on the library's static device scratch (see lra_ca_run_noalloc
+    in lra.h): nothing is allocated, so ``out`` must hold the output tensors
+    (I, J, C, U, R, logvol, info as returned by lra_ca_run)."""
+    L = _load()
+    _dev(I0, torch.int32, "I0")
+    pc, pp = problem._c(), _params(k, sweeps, h, rank_tol, max_swaps, mode)
+    cur = _Cur()
+    for f in ("I", "J", "C", "U", "R", "logvol", "info"):
+        setattr(cur, f, _dev(out[f], name=f).data_ptr())
+    _check(L.lra_ca_run_noalloc(ct.byref(pc), ct.byref(pp), multiplier.handle if multiplier else None,
+                                I0.data_ptr(), ct.byref(cur), _stream(stream)), "lra_ca_run_noalloc")
     return out
 
 

@@ -198,3 +198,50 @@ lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_mul
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// lra_ca_run_noalloc: the same C-A run for callers that cannot allocate device
+// memory.  Its scratch is one file-scope device array of NOALLOC_SCRATCH_BYTES,
+// resident on every device that loads the library until the process exits.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace lra {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 256 * 1024;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_noalloc_scratch on the current device, looked up once per
+// device (the host-side name of the array is not a device address).
+static lra_status noalloc_scratch(void** addr) {
+  int dev = 0;
+  LRA_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return LRA_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (g_noalloc_addr[dev] == nullptr) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr) return LRA_ERR_CUDA;
+    g_noalloc_addr[dev] = p;
+  }
+  *addr = g_noalloc_addr[dev];
+  return LRA_OK;
+}
+
+}  // namespace lra
+
+extern "C" lra_status lra_ca_run_noalloc(const lra_problem* prob, const lra_ca_params* par, lra_multiplier mult,
+                                         const int32_t* I0, const lra_cur* out, lra_stream_t stream) {
+  size_t need = 0;
+  lra_status st = lra_ca_workspace_size(prob, par, mult, &need);
+  if (st != LRA_OK) return st;
+  if (need > NOALLOC_SCRATCH_BYTES) return LRA_ERR_WORKSPACE;
+  void* scratch = nullptr;
+  if ((st = noalloc_scratch(&scratch)) != LRA_OK) return st;
+  return lra_ca_run(prob, par, mult, I0, out, scratch, NOALLOC_SCRATCH_BYTES, stream);
+}
