@@ -162,14 +162,17 @@ static int all_finite(const double* a, int64_t cnt) {
  *         rows t and that row are exchanged across the whole strip).
  *   Then C = Bbar^{-1} A = (I | U0^{-1} U1) in the original column order: each
  *   unchosen column b is solved by column-sweep back substitution with U0
- *   (for i = k-1 down to 0: x_i = b_i / U0[i][i], then b_p <- fma(-U0[p][i], x_i, b_p)
- *   for p < i); column J[i] of C is e_i.
+ *   (for i = k-1 down to 0: x_i = b_i * (1 / U0[i][i]), then
+ *   b_p <- fma(-U0[p][i], x_i, b_p) for p < i); column J[i] of C is e_i.
  * Swaps (Algorithm algdomin, stages 1-2): take the entry of largest |C[i][j]|
  *   over i < k and j not in J, ties to the lowest j then the lowest i.  Stop when
  *   it is <= h.  Otherwise J[i*] <- j* and C is updated in place to the new
  *   B^{-1} A: with c* = C[i*][j*] and the old column x = C[:, j*],
- *   for every column q:  t_q = C[i*][q] / c*;  C[i*][q] = t_q;
- *   C[p][q] = fma(-x[p], t_q, C[p][q]) for p != i*.
+ *   for every column q:  t_q = C[i*][q] * (1 / c*);  C[i*][q] = t_q;
+ *   C[p][q] = fma(-x[p], t_q, C[p][q]) for p != i*; column j* is then set to
+ *   e_{i*} exactly.
+ *   Every division is one reciprocal per pivot (1 / pivot) followed by
+ *   multiplications, the same solve with one rounding more per entry.
  *   |det B| is multiplied by |c*| at each swap (strict volume increase for h >= 1).
  * Outputs: J (position i of J is row i of C), C (k x n) if Cout != NULL,
  *   logdet = log|det A[:,J]| (LU diagonal at init, + log|c*| per swap), number of
@@ -215,8 +218,9 @@ restart:
       continue;                       /* nothing to eliminate with */
     }
     logdet += log(fabs(piv));
+    double rpiv = 1.0 / piv;
     for (int32_t p = t + 1; p < k; ++p) {
-      double l = M[(int64_t)p * n + jt] / piv;
+      double l = M[(int64_t)p * n + jt] * rpiv;
       for (int64_t q = 0; q < n; ++q)
         if (!chosen[q]) M[(int64_t)p * n + q] = fma(-l, M[(int64_t)t * n + q], M[(int64_t)p * n + q]);
     }
@@ -231,10 +235,11 @@ restart:
   for (int32_t s = 0; s < k; ++s)
     for (int32_t t = 0; t < k; ++t) U0[s * k + t] = (s <= t) ? M[(int64_t)s * n + J[t]] : 0.0;
   /* C = (I | U0^{-1} U1) in original column order; reuse M column by column */
+  for (int32_t i = 0; i < k; ++i) x[i] = 1.0 / U0[i * k + i];     /* reciprocals of the diagonal */
   for (int64_t q = 0; q < n; ++q) {
     if (chosen[q]) continue;
     for (int32_t i = k - 1; i >= 0; --i) {
-      double xi = M[(int64_t)i * n + q] / U0[i * k + i];
+      double xi = M[(int64_t)i * n + q] * x[i];
       M[(int64_t)i * n + q] = xi;
       for (int32_t p = 0; p < i; ++p) M[(int64_t)p * n + q] = fma(-U0[p * k + i], xi, M[(int64_t)p * n + q]);
     }
@@ -254,13 +259,15 @@ restart:
     if (bj < 0 || !(bv > h)) break;
     if (nsw >= max_swaps) { status = ORC_WARN_NOT_CONVERGED; break; }
     double cs = M[(int64_t)bi * n + bj];
+    double rcs = 1.0 / cs;
     for (int32_t p = 0; p < k; ++p) x[p] = M[(int64_t)p * n + bj];
     for (int64_t q = 0; q < n; ++q) {
-      double tq = M[(int64_t)bi * n + q] / cs;
+      double tq = M[(int64_t)bi * n + q] * rcs;
       M[(int64_t)bi * n + q] = tq;
       for (int32_t p = 0; p < k; ++p)
         if (p != bi) M[(int64_t)p * n + q] = fma(-x[p], tq, M[(int64_t)p * n + q]);
     }
+    for (int32_t p = 0; p < k; ++p) M[(int64_t)p * n + bj] = (p == bi) ? 1.0 : 0.0;  /* j* is now e_{i*} */
     chosen[J[bi]] = 0;
     chosen[bj] = 1;
     J[bi] = (int32_t)bj;

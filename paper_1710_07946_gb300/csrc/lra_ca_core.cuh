@@ -45,9 +45,12 @@ struct CaArgs {
 
 // Shared-memory layout of the C-A kernels (all offsets in bytes, 16-aligned).
 struct CaSmem {
-  double* LU;        // k*k : U0 (cold) or the pivoted LU of B (warm)
+  double* LU;        // k*ldl : U0 (cold) or the pivoted LU of B (warm)
+  double* Lm;        // k*ldl : multipliers of the warm LU
   double* x;         // KMAX : the exchanged column
   double* lmul;      // KMAX : multipliers of the current elimination step
+  double* rdiag;     // KMAX : reciprocals of the U0 diagonal
+  double* logt;      // LOGBUF : |pivots| whose logs are still to be added
   double* tq;        // ldm  : per-column scratch (swap ratios)
   int32_t* Is;       // KMAX : current rows I
   int32_t* Js;       // KMAX : current columns J
@@ -55,31 +58,42 @@ struct CaSmem {
   int32_t* pos;      // ldm  : 0 = unchosen, else 1 + position in the selected set
   Cand* win;         // the winner of the last exchange
   unsigned long long* flags;
+  double* bc;        // 4 doubles of broadcast scratch
   int32_t* ctl;      // small control words
+  CandRed* red;      // block reduction scratch
+  ExchangeOut xo;    // where an exchange leaves its result
   double* M;         // the chunk (k x ldm), shared or global
 };
+
+constexpr int LOGBUF = 64;
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
 __host__ __device__ inline size_t ca_smem_fixed(int k, int ldm) {
   size_t b = 0;
-  b += align16(sizeof(double) * (size_t)k * k);
-  b += align16(sizeof(double) * KMAX) * 2;
+  b += align16(sizeof(double) * (size_t)k * (k | 1)) * 2;
+  b += align16(sizeof(double) * KMAX) * 3;
+  b += align16(sizeof(double) * LOGBUF);
   b += align16(sizeof(double) * (size_t)ldm);
   b += align16(sizeof(int32_t) * KMAX) * 3;
   b += align16(sizeof(int32_t) * (size_t)ldm);
   b += align16(sizeof(Cand));
   b += align16(sizeof(unsigned long long));
+  b += align16(sizeof(double) * 4);
   b += align16(sizeof(int32_t) * 8);
+  b += align16(sizeof(CandRed));
   return b;
 }
 
 __device__ inline CaSmem ca_smem_carve(unsigned char* base, int k, int ldm, double* gchunk) {
   CaSmem S;
   size_t o = 0;
-  S.LU = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * (size_t)k * k);
+  S.LU = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * (size_t)k * (k | 1));
+  S.Lm = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * (size_t)k * (k | 1));
   S.x = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * KMAX);
   S.lmul = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * KMAX);
+  S.rdiag = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * KMAX);
+  S.logt = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * LOGBUF);
   S.tq = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * (size_t)ldm);
   S.Is = reinterpret_cast<int32_t*>(base + o); o += align16(sizeof(int32_t) * KMAX);
   S.Js = reinterpret_cast<int32_t*>(base + o); o += align16(sizeof(int32_t) * KMAX);
@@ -87,7 +101,10 @@ __device__ inline CaSmem ca_smem_carve(unsigned char* base, int k, int ldm, doub
   S.pos = reinterpret_cast<int32_t*>(base + o); o += align16(sizeof(int32_t) * (size_t)ldm);
   S.win = reinterpret_cast<Cand*>(base + o); o += align16(sizeof(Cand));
   S.flags = reinterpret_cast<unsigned long long*>(base + o); o += align16(sizeof(unsigned long long));
+  S.bc = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * 4);
   S.ctl = reinterpret_cast<int32_t*>(base + o); o += align16(sizeof(int32_t) * 8);
+  S.red = reinterpret_cast<CandRed*>(base + o); o += align16(sizeof(CandRed));
+  S.xo = ExchangeOut{S.win, S.x, S.flags, &S.ctl[6], S.red};
   S.M = gchunk ? gchunk : reinterpret_cast<double*>(base + o);
   return S;
 }
@@ -105,104 +122,183 @@ struct StepResult {
   double logdet;
 };
 
+// Volume bookkeeping: log|det| = sum of log|pivot| in pivot order.  Only the
+// group's lead CTA keeps it; the |pivots| are buffered and their logs taken
+// LOGBUF at a time in parallel, then added in order by one thread, which keeps
+// the 2000-cycle FP64 log off the critical path of the pivot loop.
+struct LogAcc {
+  double sum;
+  int cnt;
+};
+__device__ inline void log_flush(LogAcc& L, const CaSmem& S) {
+  if (L.cnt == 0) return;
+  __syncthreads();
+  for (int e = threadIdx.x; e < L.cnt; e += blockDim.x) S.logt[e] = log(S.logt[e]);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = L.sum;
+    for (int e = 0; e < L.cnt; ++e) s += S.logt[e];
+    S.bc[3] = s;
+  }
+  __syncthreads();
+  L.sum = S.bc[3];
+  L.cnt = 0;
+  __syncthreads();
+}
+__device__ inline void log_push(LogAcc& L, const CaSmem& S, bool lead, double absval) {
+  if (!lead) return;
+  if (threadIdx.x == 0) S.logt[L.cnt] = absval;
+  ++L.cnt;
+  if (L.cnt == LOGBUF) log_flush(L, S);
+}
+
+// Work split of "rows x own columns" loops: the CTA's threads cover the qn
+// columns; when there are fewer columns than threads, the threads of a column
+// share its rows, thread g taking rows p with p % G == g (a fixed partition, so
+// the same thread owns a given (row, column) entry in every loop of a step).
+struct Map2D {
+  int c0, cstep, g, G;
+  __device__ __forceinline__ explicit Map2D(int qn) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    if (qn >= nt || qn == 0) { c0 = tid; cstep = nt; g = 0; G = 1; }
+    else {
+      G = nt / qn; g = tid / qn; c0 = tid - g * qn; cstep = qn;
+      if (g >= G) c0 = qn;                 // idle thread
+    }
+  }
+  // first row >= lo owned by this thread
+  __device__ __forceinline__ int first(int lo) const {
+    const int r = lo % G;
+    return lo + ((g - r + G) % G);
+  }
+};
+
+// Gather the k x qn chunk of the strip; returns nonzero if any entry is not finite.
+__device__ inline int gather_chunk(const DevProblem& P, int phase, const CaSmem& S, int k, int64_t q0, int qn,
+                                   int ldm, const Map2D& mp) {
+  double* M = S.M;
+  int bad = 0;
+  for (int c = mp.c0; c < qn; c += mp.cstep)
+    for (int a = mp.g; a < k; a += mp.G) {
+      const double v = strip_entry(P, phase, S.Is, S.Js, a, q0 + c);
+      M[(int64_t)a * ldm + c] = v;
+      bad |= !bits_finite(v);
+    }
+  return bad;
+}
+
 // One maxvol step over the k x len strip of `phase`.  Jsel: in = warm set (ignored
 // when cold), out = selected k strip columns in generator order.  seq: exchange
-// round counter, advanced identically in every CTA of the group.
+// round counter, advanced identically in every CTA of the group.  The
+// arithmetic is that of the FP64 reference, operation for operation: LU with
+// column pivoting (cold) or with row pivoting on the warm columns, multipliers
+// a_p * (1/pivot), column-sweep back substitution with the reciprocals of the
+// U0 diagonal, swaps t_q = C[i*][q] * (1/c*), C[p][q] = fma(-x_p, t_q, C[p][q]).
+// The k x k LU is stored with the odd row stride ldl = k | 1 (no bank conflicts
+// when a warp walks down one of its columns).
 template <class Group>
 __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSmem& S, int phase, bool cold,
-                                  int32_t* Jsel, unsigned long long& seq) {
+                                  int32_t* Jsel, unsigned long long& seq, bool lead) {
   const DevProblem& P = A.P;
   const int k = A.k, ldm = A.ldm, tid = threadIdx.x, nt = blockDim.x;
+  const int ldl = k | 1;
+  const int lane = tid & 31, warp = tid >> 5;
   const int64_t len = phase == 0 ? P.n : P.m;
   const int chunk = phase == 0 ? A.chunk_n : A.chunk_m;
   const int64_t q0 = (int64_t)grp.rank() * chunk;
   const int qn = (int)max((int64_t)0, min((int64_t)chunk, len - q0));
+  const Map2D mp(qn);
   double* M = S.M;
+  double* LU = S.LU;
   StepResult res{LRA_OK, 0, 0.0};
+  LogAcc L{0.0, 0};
 
-  // gather the chunk; flag non-finite entries
-  int nonfinite = 0;
-  for (int it = tid; it < k * qn; it += nt) {
-    int a = it / qn, c = it - a * qn;
-    double v = strip_entry(P, phase, S.Is, S.Js, a, q0 + c);
-    M[(int64_t)a * ldm + c] = v;
-    if (!isfinite(v)) nonfinite = 1;
-  }
+  if (tid == 0) S.ctl[0] = 0;
   for (int c = tid; c < qn; c += nt) S.pos[c] = 0;
-  if (tid == 0) { S.ctl[0] = 0; S.ctl[1] = 0; }
   __syncthreads();
-  if (nonfinite) atomicOr(&S.ctl[0], 1);
+  if (gather_chunk(P, phase, S, k, q0, qn, ldm, mp)) atomicOr(&S.ctl[0], 1);
   __syncthreads();
-  unsigned long long myflags = S.ctl[0] ? FLAG_NONFINITE : 0ull;
-  double logdet = 0.0;
+  const unsigned long long myflags = S.ctl[0] ? FLAG_NONFINITE : 0ull;
   bool deficient = false;
 
   if (!cold) {
-    // ---- warm start: B = strip[:, Jsel]; pivoted LU of B replayed by every CTA
+    // ---- warm start: B = strip[:, Jsel]; the pivoted LU of B is replayed by every CTA
     for (int it = tid; it < k * k; it += nt) {
-      int a = it / k, t = it - a * k;
-      S.LU[a * k + t] = strip_entry(P, phase, S.Is, S.Js, a, Jsel[t]);
+      const int a = it / k, t = it - a * k;
+      LU[a * ldl + t] = strip_entry(P, phase, S.Is, S.Js, a, Jsel[t]);
     }
     __syncthreads();
     int fallback = 0;
+    // thread layout for the k x k elimination: column j = tid % 64, row group
+    // tid / 64 (shifts only; k <= 64)
+    const int jj = tid & (KMAX - 1), rg = tid >> 6, NRG = nt >> 6;
     for (int t = 0; t < k; ++t) {
-      if (tid == 0) {
-        int r = t;
-        double bv = fabs(S.LU[t * k + t]);
-        for (int p = t + 1; p < k; ++p) {
-          double v = fabs(S.LU[p * k + t]);
-          if (v > bv) { bv = v; r = p; }
+      if (warp == 0) {
+        // pivot row: largest |B(t)[p][t]| over p >= t, lowest p on ties; every
+        // lane takes the reciprocal of its candidates while the search runs
+        Cand c = cand_none();
+        double rc0 = 0.0, rc1 = 0.0;
+        const int p0 = t + lane, p1 = t + lane + 32;
+        if (p0 < k) { const double v = LU[p0 * ldl + t]; cand_consider(c, mag_key(v), 0, p0); rc0 = 1.0 / v; }
+        if (p1 < k) { const double v = LU[p1 * ldl + t]; cand_consider(c, mag_key(v), 0, p1); rc1 = 1.0 / v; }
+        c = warp_best(c);
+        const int r = (c.key == 0ull) ? t : c.j;
+        const double pv = LU[r * ldl + t];
+        const int rl = (r - t) & 31;
+        const double rsel = (r - t) < 32 ? rc0 : rc1;
+        const double rp = __shfl_sync(0xffffffffu, rsel, rl);
+        if (lane == 0) {
+          S.piv[t] = r;
+          S.bc[0] = (pv == 0.0) ? 0.0 : rp;
+          S.ctl[1] = (pv == 0.0);
         }
-        S.piv[t] = r;
+        // interchange rows t and r in columns t.. only: column t' < t keeps the
+        // multipliers of step t' in the row positions of that step, the order in
+        // which they are replayed on the CTA's own columns below
+        if (r != t)
+          for (int j = t + lane; j < k; j += 32) {
+            const double tmp = LU[t * ldl + j]; LU[t * ldl + j] = LU[r * ldl + j]; LU[r * ldl + j] = tmp;
+          }
       }
       __syncthreads();
-      // interchange rows t and r in columns t.. only: column t' < t keeps the
-      // multipliers of step t' in the row positions of that step, which is the
-      // order in which they are replayed on the CTA's own columns below
-      const int r = S.piv[t];
-      if (r != t)
-        for (int j = t + tid; j < k; j += nt) {
-          double tmp = S.LU[t * k + j]; S.LU[t * k + j] = S.LU[r * k + j]; S.LU[r * k + j] = tmp;
-        }
+      if (S.ctl[1]) { fallback = 1; break; }          // same decision in every CTA
+      const double rp = S.bc[0];
+      // multipliers l_p = B[p][t] * (1/pivot), kept in Lm for the replay below
+      for (int p = t + 1 + tid; p < k; p += nt) S.Lm[p * ldl + t] = LU[p * ldl + t] * rp;
       __syncthreads();
-      const double pv = S.LU[t * k + t];
-      if (pv == 0.0) { fallback = 1; break; }     // same decision in every CTA
-      for (int p = t + 1 + tid; p < k; p += nt) S.LU[p * k + t] = S.LU[p * k + t] / pv;
-      __syncthreads();
-      const int w = k - t - 1;
-      for (int it = tid; it < w * w; it += nt) {
-        int p = t + 1 + it / w, j = t + 1 + it % w;
-        S.LU[p * k + j] = fma(-S.LU[p * k + t], S.LU[t * k + j], S.LU[p * k + j]);
-      }
+      if (jj > t && jj < k)
+        for (int p = t + 1 + rg; p < k; p += NRG)
+          LU[p * ldl + jj] = fma(-S.Lm[p * ldl + t], LU[t * ldl + jj], LU[p * ldl + jj]);
       __syncthreads();
     }
     if (fallback) {
       cold = true;
       __syncthreads();
     } else {
-      for (int t = 0; t < k; ++t) {
-        int64_t jt = Jsel[t];
-        if (jt >= q0 && jt < q0 + qn && tid == 0) S.pos[jt - q0] = t + 1;
-      }
+      if (tid == 0)
+        for (int t = 0; t < k; ++t) {
+          const int64_t jt = Jsel[t];
+          if (jt >= q0 && jt < q0 + qn) S.pos[jt - q0] = t + 1;
+        }
       __syncthreads();
       for (int t = 0; t < k; ++t) {
         const int r = S.piv[t];
         if (r != t)
           for (int c = tid; c < qn; c += nt) {
-            double tmp = M[(int64_t)t * ldm + c];
+            const double tmp = M[(int64_t)t * ldm + c];
             M[(int64_t)t * ldm + c] = M[(int64_t)r * ldm + c];
             M[(int64_t)r * ldm + c] = tmp;
           }
         __syncthreads();
-        const int w = k - t - 1;
-        for (int it = tid; it < w * qn; it += nt) {
-          int p = t + 1 + it / qn, c = it - (p - t - 1) * qn;
-          if (S.pos[c] == 0)
-            M[(int64_t)p * ldm + c] = fma(-S.LU[p * k + t], M[(int64_t)t * ldm + c], M[(int64_t)p * ldm + c]);
+        for (int c = mp.c0; c < qn; c += mp.cstep) {
+          if (S.pos[c]) continue;
+          const double mt = M[(int64_t)t * ldm + c];
+          for (int p = mp.first(t + 1); p < k; p += mp.G)
+            M[(int64_t)p * ldm + c] = fma(-S.Lm[p * ldl + t], mt, M[(int64_t)p * ldm + c]);
         }
         __syncthreads();
       }
-      for (int t = 0; t < k; ++t) logdet += log(fabs(S.LU[t * k + t]));
+      for (int t = 0; t < k; ++t) log_push(L, S, lead, fabs(LU[t * ldl + t]));
     }
   }
 
@@ -210,15 +306,9 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
     // ---- cold start: LU with column pivoting over the whole strip
     for (int t = 0; t < k; ++t) {
       Cand mine = cand_none();
-      for (int c = tid; c < qn; c += nt) {
-        if (S.pos[c]) continue;
-        double v = fabs(M[(int64_t)t * ldm + c]);
-        if (v > mine.v) { mine.v = v; mine.i = 0; mine.j = (int32_t)(q0 + c); }
-      }
-      __shared__ Cand red[33];
-      mine = block_best(mine, red);
-      const double* mycol = (mine.j != 0x7fffffff) ? M + (mine.j - q0) : nullptr;
-      if (!grp.exchange(seq, mine, mycol, ldm, k, myflags, S.win, S.x, S.flags, chunk)) {
+      for (int c = tid; c < qn; c += nt)
+        if (S.pos[c] == 0) cand_consider(mine, mag_key(M[(int64_t)t * ldm + c]), 0, (int32_t)(q0 + c));
+      if (!grp.exchange(seq, mine, myflags, M, ldm, q0, k, chunk, S.xo)) {
         res.status = LRA_ERR_TIMEOUT;
         return res;
       }
@@ -228,19 +318,23 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
       if (tid == 0) {
         Jsel[t] = w.j;
         if (w.j >= q0 && w.j < q0 + qn) S.pos[w.j - q0] = t + 1;
+        const double pv = S.x[t];
+        S.bc[0] = (pv == 0.0) ? 0.0 : 1.0 / pv;
       }
       const double pv = S.x[t];
       if (pv == 0.0) { deficient = true; __syncthreads(); continue; }
-      for (int p = tid; p <= t; p += nt) S.LU[p * k + t] = S.x[p];
-      for (int p = t + 1 + tid; p < k; p += nt) S.lmul[p] = S.x[p] / pv;
       __syncthreads();
-      const int wrows = k - t - 1;
-      for (int it = tid; it < wrows * qn; it += nt) {
-        int p = t + 1 + it / qn, c = it - (p - t - 1) * qn;
-        if (S.pos[c] == 0)
-          M[(int64_t)p * ldm + c] = fma(-S.lmul[p], M[(int64_t)t * ldm + c], M[(int64_t)p * ldm + c]);
+      const double rp = S.bc[0];
+      for (int p = tid; p <= t; p += nt) LU[p * ldl + t] = S.x[p];
+      for (int p = t + 1 + tid; p < k; p += nt) S.lmul[p] = S.x[p] * rp;
+      __syncthreads();
+      for (int c = mp.c0; c < qn; c += mp.cstep) {
+        if (S.pos[c]) continue;
+        const double mt = M[(int64_t)t * ldm + c];
+        for (int p = mp.first(t + 1); p < k; p += mp.G)
+          M[(int64_t)p * ldm + c] = fma(-S.lmul[p], mt, M[(int64_t)p * ldm + c]);
       }
-      logdet += log(fabs(pv));
+      log_push(L, S, lead, fabs(pv));
       __syncthreads();
     }
     if (deficient) {
@@ -250,69 +344,76 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
     }
   }
 
-  // ---- C = (I | U0^{-1} U1): column-sweep back substitution on unchosen columns
-  for (int i = k - 1; i >= 0; --i) {
-    const double d = S.LU[i * k + i];
-    for (int c = tid; c < qn; c += nt)
-      if (S.pos[c] == 0) M[(int64_t)i * ldm + c] = M[(int64_t)i * ldm + c] / d;
-    __syncthreads();
-    for (int it = tid; it < i * qn; it += nt) {
-      int p = it / qn, c = it - p * qn;
-      if (S.pos[c] == 0)
-        M[(int64_t)p * ldm + c] = fma(-S.LU[p * k + i], M[(int64_t)i * ldm + c], M[(int64_t)p * ldm + c]);
+  // ---- C = (I | U0^{-1} U1): column-sweep back substitution on unchosen columns.
+  // The owner of row i scales it (x_i = b_i * (1/U0_ii)) right after its last
+  // update, so one barrier per row suffices.
+  for (int i = tid; i < k; i += nt) S.rdiag[i] = 1.0 / LU[i * ldl + i];
+  __syncthreads();
+  for (int c = mp.c0; c < qn; c += mp.cstep)
+    if (S.pos[c] == 0 && (k - 1) % mp.G == mp.g)
+      M[(int64_t)(k - 1) * ldm + c] = M[(int64_t)(k - 1) * ldm + c] * S.rdiag[k - 1];
+  __syncthreads();
+  for (int i = k - 1; i >= 1; --i) {
+    for (int c = mp.c0; c < qn; c += mp.cstep) {
+      if (S.pos[c]) continue;
+      const double xi = M[(int64_t)i * ldm + c];
+      for (int p = mp.first(0); p < i; p += mp.G) {
+        double v = fma(-LU[p * ldl + i], xi, M[(int64_t)p * ldm + c]);
+        if (p == i - 1) v = v * S.rdiag[i - 1];
+        M[(int64_t)p * ldm + c] = v;
+      }
     }
     __syncthreads();
   }
-  for (int it = tid; it < k * qn; it += nt) {
-    int a = it / qn, c = it - a * qn;
-    if (S.pos[c]) M[(int64_t)a * ldm + c] = (S.pos[c] - 1 == a) ? 1.0 : 0.0;
-  }
+  for (int c = mp.c0; c < qn; c += mp.cstep)
+    if (S.pos[c])
+      for (int a = mp.g; a < k; a += mp.G) M[(int64_t)a * ldm + c] = (S.pos[c] - 1 == a) ? 1.0 : 0.0;
   __syncthreads();
 
   // ---- dominance swaps (Algorithm algdomin)
+  const unsigned long long hkey = mag_key(A.h);
   int nsw = 0;
   for (;;) {
     Cand mine = cand_none();
-    for (int c = tid; c < qn; c += nt) {
+    for (int c = mp.c0; c < qn; c += mp.cstep) {
       if (S.pos[c]) continue;
-      for (int a = 0; a < k; ++a) {
-        double v = fabs(M[(int64_t)a * ldm + c]);
-        if (v > mine.v) { mine.v = v; mine.i = a; mine.j = (int32_t)(q0 + c); }
-      }
+      for (int a = mp.g; a < k; a += mp.G) cand_consider(mine, mag_key(M[(int64_t)a * ldm + c]), a, (int32_t)(q0 + c));
     }
-    __shared__ Cand red2[33];
-    mine = block_best(mine, red2);
-    const double* mycol = (mine.j != 0x7fffffff) ? M + (mine.j - q0) : nullptr;
-    if (!grp.exchange(seq, mine, mycol, ldm, k, myflags, S.win, S.x, S.flags, chunk)) {
+    if (!grp.exchange(seq, mine, myflags, M, ldm, q0, k, chunk, S.xo)) {
       res.status = LRA_ERR_TIMEOUT;
       return res;
     }
     ++seq;
     if (*S.flags & FLAG_NONFINITE) { res.status = LRA_ERR_NONFINITE; return res; }
     const Cand w = *S.win;
-    if (w.j == 0x7fffffff || !(w.v > A.h)) break;
+    if (w.key <= hkey) break;                     // no |c| > h left (or no candidate)
     if (nsw >= A.max_swaps) { res.status = LRA_WARN_NOT_CONVERGED; break; }
-    const double cs = S.x[w.i];
-    for (int c = tid; c < qn; c += nt) S.tq[c] = M[(int64_t)w.i * ldm + c] / cs;
+    if (tid == 0) S.bc[0] = 1.0 / S.x[w.i];
     __syncthreads();
-    for (int it = tid; it < k * qn; it += nt) {
-      int p = it / qn, c = it - p * qn;
-      if (p == w.i) M[(int64_t)p * ldm + c] = S.tq[c];
-      else M[(int64_t)p * ldm + c] = fma(-S.x[p], S.tq[c], M[(int64_t)p * ldm + c]);
+    const double rcs = S.bc[0];
+    for (int c = tid; c < qn; c += nt) S.tq[c] = M[(int64_t)w.i * ldm + c] * rcs;
+    __syncthreads();
+    for (int c = mp.c0; c < qn; c += mp.cstep) {
+      const double tq = S.tq[c];
+      for (int p = mp.g; p < k; p += mp.G)
+        M[(int64_t)p * ldm + c] = (p == w.i) ? tq : fma(-S.x[p], tq, M[(int64_t)p * ldm + c]);
     }
     __syncthreads();
+    if (w.j >= q0 && w.j < q0 + qn)
+      for (int p = tid; p < k; p += nt) M[(int64_t)p * ldm + (w.j - q0)] = (p == w.i) ? 1.0 : 0.0;
     if (tid == 0) {
-      int64_t old = Jsel[w.i];
+      const int64_t old = Jsel[w.i];
       if (old >= q0 && old < q0 + qn) S.pos[old - q0] = 0;
       if (w.j >= q0 && w.j < q0 + qn) S.pos[w.j - q0] = w.i + 1;
       Jsel[w.i] = w.j;
     }
-    logdet += log(fabs(cs));
+    log_push(L, S, lead, fabs(S.x[w.i]));
     ++nsw;
     __syncthreads();
   }
+  log_flush(L, S);
   res.nswaps = nsw;
-  res.logdet = logdet;
+  res.logdet = L.sum;
   return res;
 }
 
@@ -342,11 +443,11 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
   unsigned long long seq = 0;
   int status = LRA_OK, err = LRA_OK, total = 0, loops = 0;
   for (int s = 0; s < A.sweeps; ++s) {
-    StepResult r0 = maxvol_step(grp, A, S, 0, s == 0, S.Js, seq);
+    StepResult r0 = maxvol_step(grp, A, S, 0, s == 0, S.Js, seq, lead);
     if (r0.status != LRA_OK && r0.status < 16) { err = r0.status; break; }
     if (r0.status > status) status = r0.status;
     __syncthreads();
-    StepResult r1 = maxvol_step(grp, A, S, 1, false, S.Is, seq);
+    StepResult r1 = maxvol_step(grp, A, S, 1, false, S.Is, seq, lead);
     if (r1.status != LRA_OK && r1.status < 16) { err = r1.status; break; }
     if (r1.status > status) status = r1.status;
     if (lead && tid == 0) { A.logvol[2 * s] = r0.logdet; A.logvol[2 * s + 1] = r1.logdet; }

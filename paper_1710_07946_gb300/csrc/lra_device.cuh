@@ -17,9 +17,10 @@
 namespace lra {
 
 constexpr int KMAX = 64;        // largest generator size k
-constexpr int NT = 256;         // threads per CTA of the C-A kernels
+constexpr int NT = 512;         // threads per CTA of the C-A kernels
 constexpr int SLOT = 72;        // doubles per exchange slot: v, (i,j), flags, tag, col[KMAX]
 constexpr double WAIT_NS = 2.0e9;   // bound on any device-side wait
+constexpr int TERMS = 4;        // multiplier terms fetched together in a strip gather
 
 // Flags carried through an exchange.
 constexpr unsigned long long FLAG_NONFINITE = 1ull;
@@ -62,88 +63,127 @@ __device__ __forceinline__ double w_entry(const DevProblem& P, int64_t i, int64_
 // w'_ij = (W M)_ij.  ARHT: column j of M has 2^d entries, at rows a*s + t for
 // perm[j] = b*s + t, of sign D_{a s + t} (-1)^{popcount(a & b)}; the terms are
 // added in ascending a and the sum is scaled once.  Sparse: nnz signed terms in
-// ascending stored order, scaled once.
+// ascending stored order, scaled once.  The terms are fetched TERMS at a time
+// before they are added (same order of additions), so their loads overlap.
 __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64_t j) {
   if (P.mkind == LRA_MULT_NONE) return w_entry(P, i, j);
   double acc = 0.0;
   if (P.mkind == LRA_MULT_ARHT) {
-    int64_t pj = __ldg(P.perm + j);
-    int64_t b = pj / P.s, t = pj - b * P.s;
-    int nt = 1 << P.depth;
-    for (int a = 0; a < nt; ++a) {
-      int64_t r = (int64_t)a * P.s + t;
-      double v = w_entry(P, i, r) * (double)__ldg(P.sign + r);
-      if (__popc((unsigned)(a & (int)b)) & 1) acc = acc - v; else acc = acc + v;
+    const int64_t pj = __ldg(P.perm + j);
+    const int64_t b = pj / P.s, t = pj - b * P.s;
+    const int nt = 1 << P.depth;
+    for (int a0 = 0; a0 < nt; a0 += TERMS) {
+      double v[TERMS];
+#pragma unroll
+      for (int e = 0; e < TERMS; ++e) {
+        const int a = a0 + e;
+        if (a < nt) {
+          const int64_t r = (int64_t)a * P.s + t;
+          const double w = w_entry(P, i, r);
+          v[e] = (__ldg(P.sign + r) < 0) ? -w : w;       // == w * (double)sign, exactly
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < TERMS; ++e) {
+        const int a = a0 + e;
+        if (a < nt) {
+          if (__popc((unsigned)(a & (int)b)) & 1) acc = acc - v[e]; else acc = acc + v[e];
+        }
+      }
     }
   } else {
     const int32_t* rows = P.perm + j * P.nnz;
     const int8_t* sg = P.sign + j * P.nnz;
-    for (int t = 0; t < P.nnz; ++t) {
-      double v = w_entry(P, i, __ldg(rows + t));
-      if (__ldg(sg + t) < 0) acc = acc - v; else acc = acc + v;
+    for (int t0 = 0; t0 < P.nnz; t0 += TERMS) {
+      double v[TERMS];
+      bool neg[TERMS];
+#pragma unroll
+      for (int e = 0; e < TERMS; ++e) {
+        if (t0 + e < P.nnz) {
+          v[e] = w_entry(P, i, __ldg(rows + t0 + e));
+          neg[e] = __ldg(sg + t0 + e) < 0;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < TERMS; ++e) {
+        if (t0 + e < P.nnz) { if (neg[e]) acc = acc - v[e]; else acc = acc + v[e]; }
+      }
     }
   }
   return acc * P.mscale;
 }
 
 // ---------------------------------------------------------------------------
-// Pivot candidates: larger |value| first, then lower column j, then lower row i.
+// Pivot candidates.  The magnitude of an FP64 value is compared through its bit
+// pattern: for |x| not NaN, |x| < |y| exactly when (bits(x) & ~sign) <
+// (bits(y) & ~sign) as unsigned integers, so the pivot searches run on the
+// integer pipe instead of the (slow, long-latency) FP64 pipe.  key = abs bits
+// + 1, key 0 = no candidate; NaN never becomes a candidate, as in a search
+// written with "fabs(x) > best".  Order: larger key first, then lower column j,
+// then lower row i.  The reduction also ORs a flags word.
 // ---------------------------------------------------------------------------
+constexpr unsigned long long ABS_MASK = 0x7fffffffffffffffull;
+constexpr unsigned long long INF_BITS = 0x7ff0000000000000ull;
+
+__device__ __forceinline__ unsigned long long mag_key(double x) {
+  const unsigned long long a = (unsigned long long)__double_as_longlong(x) & ABS_MASK;
+  return a > INF_BITS ? 0ull : a + 1ull;
+}
+__device__ __forceinline__ bool bits_finite(double x) {
+  return ((unsigned long long)__double_as_longlong(x) & INF_BITS) != INF_BITS;
+}
+
 struct Cand {
-  double v;
+  unsigned long long key;
   int32_t i, j;
 };
 
-__device__ __forceinline__ Cand cand_none() { return Cand{-1.0, 0x7fffffff, 0x7fffffff}; }
+__device__ __forceinline__ Cand cand_none() { return Cand{0ull, 0x7fffffff, 0x7fffffff}; }
 
 __device__ __forceinline__ bool cand_better(const Cand& a, const Cand& b) {
-  return a.v > b.v || (a.v == b.v && (a.j < b.j || (a.j == b.j && a.i < b.i)));
+  return a.key > b.key || (a.key == b.key && (a.j < b.j || (a.j == b.j && a.i < b.i)));
 }
 
-__device__ __forceinline__ Cand cand_shfl_down(const Cand& c, int off) {
-  Cand o;
-  o.v = __shfl_down_sync(0xffffffffu, c.v, off);
-  o.i = __shfl_down_sync(0xffffffffu, c.i, off);
-  o.j = __shfl_down_sync(0xffffffffu, c.j, off);
-  return o;
+__device__ __forceinline__ void cand_consider(Cand& best, unsigned long long key, int32_t i, int32_t j) {
+  const Cand c{key, i, j};
+  if (key != 0ull && cand_better(c, best)) best = c;
 }
 
-__device__ __forceinline__ Cand warp_best(Cand c) {
+// Best candidate of the CTA (and the OR of the flags), returned to every thread.
+struct CandRed {
+  Cand c[33];
+  unsigned long long f[33];
+};
+
+__device__ __forceinline__ Cand block_best(Cand c, unsigned long long& flags, CandRed* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int off = 16; off > 0; off >>= 1) {
-    Cand o = cand_shfl_down(c, off);
+    Cand o;
+    o.key = __shfl_down_sync(0xffffffffu, c.key, off);
+    o.i = __shfl_down_sync(0xffffffffu, c.i, off);
+    o.j = __shfl_down_sync(0xffffffffu, c.j, off);
+    flags |= __shfl_down_sync(0xffffffffu, flags, off);
     if (cand_better(o, c)) c = o;
   }
-  return c;
-}
-
-// Best candidate of the CTA, returned to every thread.  red: >= 33 Cands of smem.
-__device__ __forceinline__ Cand block_best(Cand c, Cand* red) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  c = warp_best(c);
-  if (lane == 0) red[warp] = c;
+  if (lane == 0) { red->c[warp] = c; red->f[warp] = flags; }
   __syncthreads();
   if (warp == 0) {
-    Cand d = (lane < (int)(blockDim.x >> 5)) ? red[lane] : cand_none();
-    d = warp_best(d);
-    if (lane == 0) red[32] = d;
+    const bool act = lane < (int)(blockDim.x >> 5);
+    Cand d = act ? red->c[lane] : cand_none();
+    unsigned long long g = act ? red->f[lane] : 0ull;
+    for (int off = 16; off > 0; off >>= 1) {
+      Cand o;
+      o.key = __shfl_down_sync(0xffffffffu, d.key, off);
+      o.i = __shfl_down_sync(0xffffffffu, d.i, off);
+      o.j = __shfl_down_sync(0xffffffffu, d.j, off);
+      g |= __shfl_down_sync(0xffffffffu, g, off);
+      if (cand_better(o, d)) d = o;
+    }
+    if (lane == 0) { red->c[32] = d; red->f[32] = g; }
   }
   __syncthreads();
-  Cand r = red[32];
-  __syncthreads();
-  return r;
-}
-
-__device__ __forceinline__ unsigned long long block_or(unsigned long long f, unsigned long long* red) {
-  for (int off = 16; off > 0; off >>= 1) f |= __shfl_down_sync(0xffffffffu, f, off);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = f;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long g = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) g |= red[w];
-    red[32] = g;
-  }
-  __syncthreads();
-  unsigned long long r = red[32];
+  const Cand r = red->c[32];
+  flags = red->f[32];
   __syncthreads();
   return r;
 }
@@ -171,34 +211,70 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 }
 
 // ---------------------------------------------------------------------------
-// Exchange among the CTAs of one maxvol search.  Every CTA posts its best
-// candidate and the current values of that candidate's column; every CTA then
-// reads all posts and keeps the best one (the order above is total, so all CTAs
-// agree) together with its column.  Results land in shared memory:
+// Exchange among the CTAs of one maxvol search.  Every CTA reduces its threads'
+// candidates, posts its best candidate together with the current values of that
+// candidate's column, reads all posts and keeps the best one (the order above is
+// total, so all CTAs agree) with its column.  Results land in shared memory:
 //   win  -- the winning candidate,  x[0..k) -- its column,  flags -- OR of flags.
-// Returns false if a wait expired or another CTA aborted (status in *abort).
+// Two CTA barriers per exchange: warp results -> warp 0 does the rest.
+// Returns false (in every thread) if a wait expired or another CTA aborted.
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ Cand warp_best(Cand c) {
+  for (int off = 16; off > 0; off >>= 1) {
+    Cand o;
+    o.key = __shfl_xor_sync(0xffffffffu, c.key, off);
+    o.i = __shfl_xor_sync(0xffffffffu, c.i, off);
+    o.j = __shfl_xor_sync(0xffffffffu, c.j, off);
+    if (cand_better(o, c)) c = o;
+  }
+  return c;       // every lane holds the warp's best
+}
+
+struct ExchangeOut {
+  Cand* win;
+  double* x;
+  unsigned long long* flags;
+  int* fail;
+  CandRed* red;
+};
+
+// First half, common to all groups: the CTA's best candidate, in warp 0.
+__device__ __forceinline__ Cand cta_best_in_warp0(Cand mine, CandRed* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  mine = warp_best(mine);
+  if (lane == 0) red->c[warp] = mine;
+  __syncthreads();
+  Cand d = cand_none();
+  if (warp == 0) {
+    if (lane < (int)(blockDim.x >> 5)) d = red->c[lane];
+    d = warp_best(d);
+  }
+  return d;       // meaningful in warp 0 only
+}
 
 // A single CTA: nothing to exchange.
 struct SoloGroup {
   __device__ __forceinline__ int rank() const { return 0; }
-  __device__ __forceinline__ bool exchange(unsigned long long /*seq*/, const Cand& mine, const double* mycol,
-                                           int mycol_stride, int k, unsigned long long myflags, Cand* win,
-                                           double* x, unsigned long long* flags, int /*owner_chunk*/) const {
-    if (threadIdx.x == 0) { *win = mine; *flags = myflags; }
-    if (mycol != nullptr)
-      for (int a = threadIdx.x; a < k; a += blockDim.x) x[a] = mycol[(int64_t)a * mycol_stride];
+  __device__ __forceinline__ bool exchange(unsigned long long /*seq*/, Cand mine, unsigned long long myflags,
+                                           const double* M, int ldm, int64_t q0, int k, int /*owner_chunk*/,
+                                           const ExchangeOut& o) const {
+    const Cand d = cta_best_in_warp0(mine, o.red);
+    if (threadIdx.x < 32) {
+      if (threadIdx.x == 0) { *o.win = d; *o.flags = myflags; }
+      if (d.key != 0ull)
+        for (int a = threadIdx.x; a < k; a += 32) o.x[a] = M[(int64_t)a * ldm + (d.j - q0)];
+    }
     __syncthreads();
     return true;
   }
 };
 
 // All CTAs of a cooperative grid, through double-buffered slots in global memory.
-// A slot is (value, (i, j), flags, tag, column); its tag is written last with a
-// release store and polled with acquire loads, so one round costs one post and
-// one read of every slot (no atomics).  Round r uses buffer r & 1: a CTA can
-// only post round r + 2 after every CTA posted round r + 1, i.e. after every CTA
-// finished reading round r.
+// A slot is (key, (i, j), flags, tag, column); one thread writes it and then the
+// tag with a release store, readers poll tags with acquire loads: one round is
+// one post and one read of every slot (no atomics).  Round r uses buffer r & 1:
+// a CTA can only post round r + 2 after every CTA posted round r + 1, i.e. after
+// every CTA finished reading round r.
 struct GridGroup {
   double* slots;             // [2][nblk][SLOT]
   unsigned int* abort;       // 0, or the status of the CTA that gave up
@@ -206,68 +282,57 @@ struct GridGroup {
 
   __device__ __forceinline__ int rank() const { return blockIdx.x; }
 
-  __device__ bool exchange(unsigned long long seq, const Cand& mine, const double* mycol, int mycol_stride, int k,
-                           unsigned long long myflags, Cand* win, double* x, unsigned long long* flags,
-                           int owner_chunk) const {
-    __shared__ Cand red[33];
-    __shared__ unsigned long long redf[33];
-    __shared__ int s_fail;
-    const int tid = threadIdx.x;
-    double* buf = slots + (size_t)(seq & 1ull) * nblk * SLOT;
-    double* me = buf + (size_t)blockIdx.x * SLOT;
-    if (mycol != nullptr)
-      for (int a = tid; a < k; a += blockDim.x) me[4 + a] = mycol[(int64_t)a * mycol_stride];
-    if (tid == 0) {
-      me[0] = mine.v;
-      reinterpret_cast<int2*>(me + 1)[0] = make_int2(mine.i, mine.j);
-      reinterpret_cast<unsigned long long*>(me)[2] = myflags;
-      s_fail = 0;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      st_release_u64(reinterpret_cast<unsigned long long*>(me) + 3, seq + 1ull);
-    }
-    // read every post
-    Cand best = cand_none();
-    unsigned long long f = 0;
-    int fail = 0;
-    for (int r = tid; r < nblk; r += blockDim.x) {
-      const double* sl = buf + (size_t)r * SLOT;
-      const unsigned long long* tag = reinterpret_cast<const unsigned long long*>(sl) + 3;
-      unsigned long long t0 = 0;
-      unsigned spins = 0;
-      while (ld_acquire_u64(tag) != seq + 1ull) {
-        if ((++spins & 255u) == 0u) {
-          if (ld_relaxed_u32(abort) != 0u) { fail = 1; break; }
-          unsigned long long now = globaltimer_ns();
-          if (t0 == 0) t0 = now;
-          else if ((double)(now - t0) > WAIT_NS) { fail = 2; break; }
-        }
+  __device__ bool exchange(unsigned long long seq, Cand mine, unsigned long long myflags, const double* M, int ldm,
+                           int64_t q0, int k, int owner_chunk, const ExchangeOut& o) const {
+    const Cand d = cta_best_in_warp0(mine, o.red);
+    const int lane = threadIdx.x & 31;
+    if (threadIdx.x < 32) {
+      double* buf = slots + (size_t)(seq & 1ull) * nblk * SLOT;
+      if (lane == 0) {
+        double* me = buf + (size_t)blockIdx.x * SLOT;
+        unsigned long long* mu = reinterpret_cast<unsigned long long*>(me);
+        if (d.key != 0ull)
+          for (int a = 0; a < k; ++a) me[4 + a] = M[(int64_t)a * ldm + (d.j - q0)];
+        mu[0] = d.key;
+        reinterpret_cast<int2*>(me + 1)[0] = make_int2(d.i, d.j);
+        mu[2] = myflags;
+        st_release_u64(mu + 3, seq + 1ull);       // orders the slot before the tag
       }
-      if (fail) break;
-      Cand c;
-      c.v = __ldcg(sl);
-      int2 ij = __ldcg(reinterpret_cast<const int2*>(sl + 1));
-      c.i = ij.x; c.j = ij.y;
-      f |= __ldcg(reinterpret_cast<const unsigned long long*>(sl) + 2);
-      if (cand_better(c, best)) best = c;
-    }
-    if (fail) {
+      Cand best = cand_none();
+      unsigned long long f = 0;
+      int fail = 0;
+      for (int r = lane; r < nblk && !fail; r += 32) {
+        const unsigned long long* sl = reinterpret_cast<const unsigned long long*>(buf + (size_t)r * SLOT);
+        unsigned long long t0 = 0;
+        unsigned spins = 0;
+        while (ld_acquire_u64(sl + 3) != seq + 1ull) {
+          if ((++spins & 255u) == 0u) {
+            if (ld_relaxed_u32(abort) != 0u) { fail = 1; break; }
+            const unsigned long long now = globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            else if ((double)(now - t0) > WAIT_NS) { fail = 2; break; }
+          }
+        }
+        if (fail) break;
+        Cand c;
+        c.key = __ldcg(sl);
+        const int2 ij = __ldcg(reinterpret_cast<const int2*>(sl + 1));
+        c.i = ij.x; c.j = ij.y;
+        f |= __ldcg(sl + 2);
+        if (cand_better(c, best)) best = c;
+      }
       if (fail == 2) atomicCAS(abort, 0u, (unsigned)LRA_ERR_TIMEOUT);
-      atomicOr(&s_fail, 1);
+      fail = __any_sync(0xffffffffu, fail != 0);
+      best = warp_best(best);
+      for (int off = 16; off > 0; off >>= 1) f |= __shfl_xor_sync(0xffffffffu, f, off);
+      if (!fail && best.key != 0ull) {
+        const double* ws = buf + (size_t)(best.j / owner_chunk) * SLOT;
+        for (int a = lane; a < k; a += 32) o.x[a] = __ldcg(ws + 4 + a);
+      }
+      if (lane == 0) { *o.win = best; *o.flags = f; *o.fail = fail; }
     }
     __syncthreads();
-    if (s_fail) return false;
-    best = block_best(best, red);
-    f = block_or(f, redf);
-    if (best.j != 0x7fffffff) {
-      const double* ws = buf + (size_t)(best.j / owner_chunk) * SLOT;
-      for (int a = tid; a < k; a += blockDim.x) x[a] = __ldcg(ws + 4 + a);
-    }
-    if (tid == 0) { *win = best; *flags = f; }
-    __syncthreads();
-    return true;
+    return *o.fail == 0;
   }
 };
 

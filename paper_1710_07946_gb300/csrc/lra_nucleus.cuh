@@ -19,8 +19,11 @@
 namespace lra {
 
 // Shared memory needed by nucleus_cta for generator size k.
+// Columns are stored with an odd stride ld = k | 1 so that threads owning
+// different columns hit different shared-memory banks.
+__host__ __device__ inline int nucleus_ld(int k) { return k | 1; }
 __host__ __device__ inline size_t nucleus_smem_bytes(int k) {
-  return sizeof(double) * (3 * (size_t)k * k + 4 * (size_t)KMAX) + sizeof(int32_t) * 2 * KMAX + 64;
+  return sizeof(double) * (3 * (size_t)k * nucleus_ld(k) + 4 * (size_t)KMAX) + sizeof(int32_t) * 2 * KMAX + 64;
 }
 
 // Householder reflector of the column x[0..len) (unit stride, shared memory),
@@ -62,10 +65,11 @@ __device__ __forceinline__ void apply_house_seq(const double* v, double tau, dou
 // G (k x k row-major, global).  smem: nucleus_smem_bytes(k).  Returns r.
 __device__ int nucleus_cta(const double* G, int k, double tol, double* U, unsigned char* smem) {
   const int tid = threadIdx.x, nt = blockDim.x;
-  double* A = reinterpret_cast<double*>(smem);          // column-major k x k
-  double* Q = A + (size_t)k * k;                        // Q^T, column-major
-  double* T = Q + (size_t)k * k;                        // T^T (k x r), column-major
-  double* taus = T + (size_t)k * k;
+  const int ld = nucleus_ld(k);
+  double* A = reinterpret_cast<double*>(smem);          // column-major k x k, stride ld
+  double* Q = A + (size_t)k * ld;                       // Q^T, column-major
+  double* T = Q + (size_t)k * ld;                       // T^T (k x r), column-major
+  double* taus = T + (size_t)k * ld;
   double* tz = taus + KMAX;
   double* nrm = tz + KMAX;
   double* bc = nrm + KMAX;
@@ -74,39 +78,50 @@ __device__ int nucleus_cta(const double* G, int k, double tol, double* U, unsign
 
   for (int it = tid; it < k * k; it += nt) {
     int i = it / k, j = it - i * k;
-    A[j * k + i] = G[it];
+    A[j * ld + i] = G[it];
   }
   for (int j = tid; j < k; j += nt) perm[j] = j;
   __syncthreads();
   for (int t = 0; t < k; ++t) {
     for (int j = t + tid; j < k; j += nt) {
       double s = 0.0;
-      for (int i = t; i < k; ++i) s = fma(A[j * k + i], A[j * k + i], s);
+      for (int i = t; i < k; ++i) s = fma(A[j * ld + i], A[j * ld + i], s);
       nrm[j] = s;
     }
     __syncthreads();
-    if (tid == 0) {
-      int pj = t; double bn = -1.0;
-      for (int j = t; j < k; ++j) if (nrm[j] > bn) { bn = nrm[j]; pj = j; }
-      ctl[0] = pj;
-      if (pj != t) { int tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp; }
+    if (tid < 32) {
+      // largest squared norm, lowest column on ties (integer keys, one warp)
+      Cand c = cand_none();
+      for (int j = t + tid; j < k; j += 32) cand_consider(c, mag_key(nrm[j]), 0, j);
+      for (int off = 16; off > 0; off >>= 1) {
+        Cand o;
+        o.key = __shfl_down_sync(0xffffffffu, c.key, off);
+        o.i = __shfl_down_sync(0xffffffffu, c.i, off);
+        o.j = __shfl_down_sync(0xffffffffu, c.j, off);
+        if (cand_better(o, c)) c = o;
+      }
+      if (tid == 0) {
+        const int pj = (c.key == 0ull) ? t : c.j;
+        ctl[0] = pj;
+        if (pj != t) { int tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp; }
+      }
     }
     __syncthreads();
     const int pj = ctl[0];
     if (pj != t)
       for (int i = tid; i < k; i += nt) {
-        double tmp = A[t * k + i]; A[t * k + i] = A[pj * k + i]; A[pj * k + i] = tmp;
+        double tmp = A[t * ld + i]; A[t * ld + i] = A[pj * ld + i]; A[pj * ld + i] = tmp;
       }
     __syncthreads();
-    const double tau = house_cta(&A[t * k + t], k - t, bc);
+    const double tau = house_cta(&A[t * ld + t], k - t, bc);
     if (tid == 0) taus[t] = tau;
-    for (int j = t + 1 + tid; j < k; j += nt) apply_house_seq(&A[t * k + t], tau, &A[j * k + t], k - t);
+    for (int j = t + 1 + tid; j < k; j += nt) apply_house_seq(&A[t * ld + t], tau, &A[j * ld + t], k - t);
     __syncthreads();
   }
   if (tid == 0) {
     int r = 0;
     const double r00 = fabs(A[0]);
-    if (r00 > 0.0) while (r < k && fabs(A[r * k + r]) > tol * r00) ++r;
+    if (r00 > 0.0) while (r < k && fabs(A[r * ld + r]) > tol * r00) ++r;
     ctl[1] = r;
   }
   __syncthreads();
@@ -116,46 +131,46 @@ __device__ int nucleus_cta(const double* G, int k, double tol, double* U, unsign
 
   // Q^T = H_{k-1} ... H_0 I, one column per thread
   for (int j = tid; j < k; j += nt) {
-    for (int i = 0; i < k; ++i) Q[j * k + i] = (i == j) ? 1.0 : 0.0;
-    for (int t = 0; t < k; ++t) apply_house_seq(&A[t * k + t], taus[t], &Q[j * k + t], k - t);
+    for (int i = 0; i < k; ++i) Q[j * ld + i] = (i == j) ? 1.0 : 0.0;
+    for (int t = 0; t < k; ++t) apply_house_seq(&A[t * ld + t], taus[t], &Q[j * ld + t], k - t);
   }
   if (r < k) {
     for (int it = tid; it < k * r; it += nt) {
       int c = it / k, i = it - c * k;
-      T[c * k + i] = (i >= c) ? A[i * k + c] : 0.0;
+      T[c * ld + i] = (i >= c) ? A[i * ld + c] : 0.0;
     }
     __syncthreads();
     for (int c = 0; c < r; ++c) {
-      const double tau = house_cta(&T[c * k + c], k - c, bc);
+      const double tau = house_cta(&T[c * ld + c], k - c, bc);
       if (tid == 0) tz[c] = tau;
-      for (int j = c + 1 + tid; j < r; j += nt) apply_house_seq(&T[c * k + c], tau, &T[j * k + c], k - c);
+      for (int j = c + 1 + tid; j < r; j += nt) apply_house_seq(&T[c * ld + c], tau, &T[j * ld + c], k - c);
       __syncthreads();
     }
   }
   __syncthreads();
   // X = Z S^{-T} Q_r^T (or R^{-1} Q^T), one column per thread, in place in Q
   for (int col = tid; col < k; col += nt) {
-    double* v = &Q[col * k];
+    double* v = &Q[col * ld];
     if (r == k) {
       for (int i = k - 1; i >= 0; --i) {
         double s = v[i];
-        for (int p = i + 1; p < k; ++p) s = fma(-A[p * k + i], v[p], s);
-        v[i] = s / A[i * k + i];
+        for (int p = i + 1; p < k; ++p) s = fma(-A[p * ld + i], v[p], s);
+        v[i] = s / A[i * ld + i];
       }
     } else {
       for (int i = 0; i < r; ++i) {
         double s = v[i];
-        for (int p = 0; p < i; ++p) s = fma(-T[i * k + p], v[p], s);
-        v[i] = s / T[i * k + i];
+        for (int p = 0; p < i; ++p) s = fma(-T[i * ld + p], v[p], s);
+        v[i] = s / T[i * ld + i];
       }
       for (int i = r; i < k; ++i) v[i] = 0.0;
-      for (int c = r - 1; c >= 0; --c) apply_house_seq(&T[c * k + c], tz[c], &v[c], k - c);
+      for (int c = r - 1; c >= 0; --c) apply_house_seq(&T[c * ld + c], tz[c], &v[c], k - c);
     }
   }
   __syncthreads();
   for (int it = tid; it < k * k; it += nt) {
     int i = it / k, col = it - i * k;
-    U[(size_t)perm[i] * k + col] = Q[col * k + i];
+    U[(size_t)perm[i] * k + col] = Q[col * ld + i];
   }
   __syncthreads();
   return r;
