@@ -193,6 +193,68 @@ lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_mul
 lra_status lra_ca_run_noalloc(const lra_problem* prob, const lra_ca_params* par, lra_multiplier mult,
                               const int32_t* I0, const lra_cur* out, lra_stream_t stream);
 
+/* ------------------------------------------------------------------------- */
+/* Batches of independent blocks (HSS / FMM generators)                       */
+/* ------------------------------------------------------------------------- */
+/* A batch of nb submatrices W[row0 : row0+nrows, col0 : col0+ncols] of one
+ * input (paper: Section "Application: HSS / FMM" -- the generators of the
+ * neutered block columns are low-rank approximations of such off-diagonal
+ * blocks, and C-A computes each of them superfast).  All arrays are device
+ * memory, so a batched call can be captured in a CUDA graph. */
+typedef struct {
+  const int64_t* blocks;   /* nb x 4: row0, nrows, col0, ncols (nrows, ncols >= 1)      */
+  const int64_t* offsets;  /* nb x 2: offsets, in doubles, of C_b in C and R_b in R      */
+  const int32_t* order;    /* optional (NULL = 0..nb-1): the order in which blocks are
+                              taken from the work queue; largest first balances the tail */
+  int32_t nb;              /* number of blocks >= 1                                       */
+  int64_t max_len;         /* >= max over blocks of max(nrows, ncols); sizes the scratch  */
+} lra_batch;
+
+/* Outputs of a batch (device, caller-owned).  Block b has k_b = min(k, nrows,
+ * ncols); its C_b (nrows x k_b) and R_b (k_b x ncols) are row-major at the
+ * block's offsets; the other arrays have one fixed-size slot per block. */
+typedef struct {
+  int32_t* I;              /* nb x k: rows (block-local), first k_b used                  */
+  int32_t* J;              /* nb x k: columns (block-local)                               */
+  double* C;               /* packed C_b                                                  */
+  double* U;               /* nb x k x k: U_b (k_b x k_b, row-major) at the slot start     */
+  double* R;               /* packed R_b                                                  */
+  double* logvol;          /* nb x 2*sweeps                                               */
+  int32_t* info;           /* nb x 4: rank, swaps, loops, status (as lra_cur.info)         */
+} lra_cur_batch;
+
+/* Workspace bytes of lra_ca_run_batched (params: par->k is the largest rank). */
+lra_status lra_ca_batched_workspace_size(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                                         size_t* bytes);
+
+/*
+ * lra_ca_run_batched -- lra_ca_run on every block of the batch, in one
+ * persistent launch: each CTA takes the next block from a device work queue
+ * and runs that block's C-A loop and nucleus alone, so the per-block results
+ * are those of lra_ca_run on the block (same pivots, bit for bit).  k_b =
+ * min(par->k, nrows, ncols); U_b truncates the core at par->rank_tol (adaptive
+ * rank, info[b*4+0]).  Only dense and kernel inputs without multipliers.
+ * I0: device, nb x par->k block-local initial rows (first k_b of each slot
+ * used, distinct).  A block outside the input or larger than max_len gets
+ * status LRA_ERR_INVALID_ARG in its info slot; the others still run.
+ * Errors: LRA_ERR_INVALID_ARG, LRA_ERR_WORKSPACE, LRA_ERR_CUDA.
+ */
+lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                              const int32_t* I0, const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
+                              lra_stream_t stream);
+
+/*
+ * lra_residual_sample_batched -- the a-posteriori sample of lra_residual_sample
+ * for every block of a batch, in one launch: for block b, rows Q[b*q .. b*q+q)
+ * and columns S[b*s .. b*s+s) (block-local, device int32) of W_b - C_b U_b R_b;
+ * stats (device, nb x 5) as in lra_residual_sample (NaN for failed blocks).
+ * kmax: the par->k of the batched run.  8 (q k + 2 q s) bytes must fit in
+ * shared memory.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
+ */
+lra_status lra_residual_sample_batched(const lra_problem* base, const lra_batch* batch, int32_t kmax,
+                                       const lra_cur_batch* cur, const int32_t* Q, int32_t q, const int32_t* S,
+                                       int32_t s, double* stats, lra_stream_t stream);
+
 /*
  * lra_cur_apply -- Y = C (U (R X)) for one CUR triple (paper: FMM / HSS stage
  * (iii), multiplication with the generators of the neutered block columns).

@@ -275,3 +275,37 @@ def gaussian_blocks(nblk: int = 256, size: int = 1024, ell: float = 0.3, offset:
 
 def rhs(n: int, nrhs: int, seed: int, dtype=np.float64) -> np.ndarray:
     return rng(seed).standard_normal((n, nrhs)).astype(dtype)
+
+
+def block_initial_rows(blocks: np.ndarray, kmax: int, seed: int) -> np.ndarray:
+    """Per-block I0 (block-local): the first min(kmax, nrows, ncols) entries of a
+    seeded permutation of the block's rows; unused slots are 0."""
+    g = rng(seed)
+    out = np.zeros((len(blocks), kmax), dtype=np.int32)
+    for b, (r0, nr, c0, nc) in enumerate(np.asarray(blocks)):
+        kb = int(min(kmax, nr, nc))
+        out[b, :kb] = g.permutation(int(nr))[:kb]
+    return out
+
+
+def block_sample_positions(blocks: np.ndarray, q: int, s: int, seed: int):
+    """Per-block residual sample rows (nb x q) and columns (nb x s), block-local,
+    uniform without replacement when the block is large enough."""
+    g = rng(seed)
+    Q = np.zeros((len(blocks), q), dtype=np.int32)
+    S = np.zeros((len(blocks), s), dtype=np.int32)
+    for b, (r0, nr, c0, nc) in enumerate(np.asarray(blocks)):
+        Q[b] = g.choice(int(nr), size=q, replace=q > nr)
+        S[b] = g.choice(int(nc), size=s, replace=s > nc)
+    return Q, S
+
+
+def dense_blocks(n: int = 1500, sizes=(1, 7, 40, 64, 65, 300, 900), seed: int = 0):
+    """Random rectangular blocks of an n x n matrix, sizes drawn from `sizes`."""
+    g = rng(seed)
+    out = []
+    for nr in sizes:
+        for nc in sizes:
+            r0 = int(g.integers(0, n - nr + 1)); c0 = int(g.integers(0, n - nc + 1))
+            out.append((r0, nr, c0, nc))
+    return np.asarray(out, dtype=np.int64)

@@ -23,7 +23,7 @@ __all__ = [
     "LRA_WARN_RANK_DEFICIENT", "LRA_WARN_NOT_CONVERGED", "LraError", "Problem", "Multiplier",
     "lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run", "lra_cur_apply",
     "lra_residual_sample", "lra_version", "library_path", "lra_launch_count", "lra_profile_enable",
-    "lra_profile_collect", "lra_ca_run_noalloc",
+    "lra_profile_collect", "lra_ca_run_noalloc", "Batch", "lra_ca_run_batched", "lra_residual_sample_batched",
 ]
 
 LRA_OK, LRA_ERR_INVALID_ARG, LRA_ERR_CUDA, LRA_ERR_NONFINITE, LRA_ERR_TIMEOUT, LRA_ERR_WORKSPACE = 0, 1, 2, 3, 4, 5
@@ -52,6 +52,16 @@ class _Problem(ct.Structure):
 class _Params(ct.Structure):
     _fields_ = [("k", ct.c_int32), ("sweeps", ct.c_int32), ("h", ct.c_double), ("rank_tol", ct.c_double),
                 ("max_swaps", ct.c_int32), ("mode", ct.c_int32)]
+
+
+class _Batch(ct.Structure):
+    _fields_ = [("blocks", ct.c_void_p), ("offsets", ct.c_void_p), ("order", ct.c_void_p), ("nb", ct.c_int32),
+                ("max_len", ct.c_int64)]
+
+
+class _CurBatch(ct.Structure):
+    _fields_ = [("I", ct.c_void_p), ("J", ct.c_void_p), ("C", ct.c_void_p), ("U", ct.c_void_p),
+                ("R", ct.c_void_p), ("logvol", ct.c_void_p), ("info", ct.c_void_p)]
 
 
 class _Cur(ct.Structure):
@@ -84,6 +94,10 @@ def _load():
     L.lra_cur_apply_workspace_size.argtypes = [i64, i32, i32, ct.POINTER(sz)]
     L.lra_residual_sample.argtypes = [P, vp, vp, vp, i32, vp, i32, vp, i32, vp, vp, vp, sz, vp]
     L.lra_residual_sample_workspace_size.argtypes = [i32, i32, i32, ct.POINTER(sz)]
+    PB, PCB = ct.POINTER(_Batch), ct.POINTER(_CurBatch)
+    L.lra_ca_batched_workspace_size.argtypes = [P, PB, PP, ct.POINTER(sz)]
+    L.lra_ca_run_batched.argtypes = [P, PB, PP, vp, PCB, vp, sz, vp]
+    L.lra_residual_sample_batched.argtypes = [P, PB, i32, PCB, vp, i32, vp, i32, vp, vp]
     L.lra_version.restype = ct.c_char_p
     L.lra_launch_count.restype = ct.c_int64
     L.lra_profile_enable.argtypes = [i32]
@@ -91,7 +105,8 @@ def _load():
     for f in ("lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run",
               "lra_ca_run_noalloc",
               "lra_cur_apply", "lra_cur_apply_workspace_size", "lra_residual_sample",
-              "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect"):
+              "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect",
+              "lra_ca_batched_workspace_size", "lra_ca_run_batched", "lra_residual_sample_batched"):
         getattr(L, f).restype = ct.c_int
     _lib = L
     return L
@@ -337,3 +352,83 @@ def lra_profile_collect(max_kernels: int = 32) -> dict:
         nm = names.raw[i * NAME:(i + 1) * NAME].split(b"\0", 1)[0].decode()
         out[nm] = (ms[i], int(cnt[i]))
     return out
+
+
+class Batch:
+    """Device buffers of a batch of blocks W[r0:r0+nr, c0:c0+nc] of one input
+    (the C ABI's lra_batch and lra_cur_batch).  Allocation and uploads happen
+    here, once; lra_ca_run_batched / lra_residual_sample_batched then only
+    launch kernels, so they can be captured in a CUDA graph."""
+
+    def __init__(self, problem: Problem, blocks, k: int, sweeps: int, I0, h: float = 1.01, rank_tol: float = 1e-6,
+                 max_swaps: int = 1000, order="lpt", device=None):
+        import numpy as np
+        blocks = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64).reshape(-1, 4))
+        nb = len(blocks)
+        dev = device or (problem.W if problem.W is not None else problem.X).device
+        kb = np.minimum(k, np.minimum(blocks[:, 1], blocks[:, 3]))
+        csz, rsz = blocks[:, 1] * kb, kb * blocks[:, 3]
+        offs = np.zeros((nb, 2), dtype=np.int64)
+        offs[1:, 0] = np.cumsum(csz)[:-1]
+        offs[1:, 1] = np.cumsum(rsz)[:-1]
+        if isinstance(order, str) and order == "lpt":
+            order = np.argsort(-(blocks[:, 1] * blocks[:, 3]), kind="stable").astype(np.int32)
+        self.problem, self.k, self.sweeps, self.nb = problem, int(k), int(sweeps), nb
+        self.blocks_np, self.offs_np, self.kb = blocks, offs, kb
+        self.params = _params(k, sweeps, h, rank_tol, max_swaps, LRA_MODE_FP64)
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
+        self.blocks, self.offs = t(blocks, np.int64), t(offs, np.int64)
+        self.order = None if order is None else t(order, np.int32)
+        self.I0 = t(np.asarray(I0).reshape(nb, k), np.int32)
+        self.out = dict(I=torch.zeros(nb, k, dtype=torch.int32, device=dev),
+                        J=torch.zeros(nb, k, dtype=torch.int32, device=dev),
+                        C=torch.zeros(max(int(csz.sum()), 1), dtype=torch.float64, device=dev),
+                        U=torch.zeros(nb, k, k, dtype=torch.float64, device=dev),
+                        R=torch.zeros(max(int(rsz.sum()), 1), dtype=torch.float64, device=dev),
+                        logvol=torch.zeros(nb, 2 * sweeps, dtype=torch.float64, device=dev),
+                        info=torch.zeros(nb, 4, dtype=torch.int32, device=dev))
+        self.cb = _Batch()
+        self.cb.blocks, self.cb.offsets = self.blocks.data_ptr(), self.offs.data_ptr()
+        self.cb.order = self.order.data_ptr() if self.order is not None else None
+        self.cb.nb, self.cb.max_len = nb, int(max(blocks[:, 1].max(), blocks[:, 3].max()))
+        self.cur = _CurBatch()
+        for f in ("I", "J", "C", "U", "R", "logvol", "info"):
+            setattr(self.cur, f, self.out[f].data_ptr())
+        self.pc = problem._c()
+        L = _load()
+        nbytes = ct.c_size_t()
+        _check(L.lra_ca_batched_workspace_size(ct.byref(self.pc), ct.byref(self.cb), ct.byref(self.params),
+                                               ct.byref(nbytes)), "lra_ca_batched_workspace_size")
+        self.workspace = _workspace(nbytes.value, dev)
+
+    def block(self, b: int) -> dict:
+        """Host copies of block b's results (for checks)."""
+        kb, (r0, nr, c0, nc) = int(self.kb[b]), self.blocks_np[b]
+        oc, orr = self.offs_np[b]
+        o = {key: v.cpu().numpy() for key, v in self.out.items()}
+        info = o["info"][b]
+        return dict(I=o["I"][b, :kb], J=o["J"][b, :kb], C=o["C"][oc:oc + nr * kb].reshape(nr, kb),
+                    U=o["U"][b].reshape(-1)[:kb * kb].reshape(kb, kb),
+                    R=o["R"][orr:orr + kb * nc].reshape(kb, nc), logvol=o["logvol"][b],
+                    rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]), status=int(info[3]))
+
+
+def lra_ca_run_batched(batch: Batch, stream=None) -> None:
+    """C-A CUR of every block of `batch` in one persistent launch (results in batch.out)."""
+    L = _load()
+    _check(L.lra_ca_run_batched(ct.byref(batch.pc), ct.byref(batch.cb), ct.byref(batch.params),
+                                batch.I0.data_ptr(), ct.byref(batch.cur), batch.workspace.data_ptr(),
+                                batch.workspace.numel(), _stream(stream)), "lra_ca_run_batched")
+
+
+def lra_residual_sample_batched(batch: Batch, Q: torch.Tensor, S: torch.Tensor, stats: Optional[torch.Tensor] = None,
+                                stream=None) -> torch.Tensor:
+    """Per-block residual sample statistics (nb x 5) of a batched run; Q (nb x q), S (nb x s) device int32."""
+    L = _load()
+    if stats is None:
+        stats = torch.empty(batch.nb, 5, dtype=torch.float64, device=batch.blocks.device)
+    _check(L.lra_residual_sample_batched(ct.byref(batch.pc), ct.byref(batch.cb), batch.k, ct.byref(batch.cur),
+                                         _dev(Q, torch.int32, "Q").data_ptr(), Q.shape[1],
+                                         _dev(S, torch.int32, "S").data_ptr(), S.shape[1], stats.data_ptr(),
+                                         _stream(stream)), "lra_residual_sample_batched")
+    return stats

@@ -63,7 +63,7 @@ __device__ __forceinline__ void apply_house_seq(const double* v, double tau, dou
 
 // U (k x k, row-major, global or shared) <- pinv of the rank-r QRP truncation of
 // G (k x k row-major, global).  smem: nucleus_smem_bytes(k).  Returns r.
-__device__ int nucleus_cta(const double* G, int k, double tol, double* U, unsigned char* smem) {
+__device__ inline int nucleus_cta(const double* G, int k, double tol, double* U, unsigned char* smem) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ld = nucleus_ld(k);
   double* A = reinterpret_cast<double*>(smem);          // column-major k x k, stride ld

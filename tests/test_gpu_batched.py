@@ -1,0 +1,98 @@
+"""Batched C-A (one persistent launch over many blocks) against the FP64 oracle
+run block by block: pivots bit-exact, C and R identical, U within 1e-10."""
+import numpy as np
+import pytest
+
+import lra_inputs as li
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from gpu_helpers import to_device  # noqa: E402
+
+
+def check_block(o, g):
+    assert g["status"] == o["status"], (g["status"], o["status"])
+    assert g["swaps"] == o["swaps"] and g["loops"] == o["loops"]
+    np.testing.assert_array_equal(g["I"], o["I"])
+    np.testing.assert_array_equal(g["J"], o["J"])
+    np.testing.assert_array_equal(g["C"], o["C"])
+    np.testing.assert_array_equal(g["R"], o["R"])
+    assert g["rank"] == o["rank"]
+    if o["rank"] > 0:
+        assert np.abs(g["U"] - o["U"]).max() <= 1e-10 * np.abs(o["U"]).max()
+
+
+def run_batch(p, blocks, k, sweeps, rank_tol, seed=0, check=None):
+    import paper_1710_07946_gb300 as lra
+    prob, _ = to_device(p)
+    I0 = li.block_initial_rows(blocks, k, seed)
+    bt = lra.Batch(prob, blocks, k, sweeps, I0, rank_tol=rank_tol)
+    lra.lra_ca_run_batched(bt)
+    torch.cuda.synchronize()
+    idx = range(len(blocks)) if check is None else check
+    for b in idx:
+        r0, nr, c0, nc = blocks[b]
+        kb = int(min(k, nr, nc))
+        if p.src == li.SRC_DENSE:
+            sub = li.Problem(li.SRC_DENSE, int(nr), int(nc), W=np.ascontiguousarray(p.W[r0:r0 + nr, c0:c0 + nc]))
+        else:
+            sub = li.Problem(p.src, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], ell=p.ell)
+        o = oracle.ca_run(sub, kb, sweeps, I0[b, :kb], rank_tol=rank_tol)
+        check_block(o, bt.block(b))
+    return bt, I0
+
+
+def test_dense_blocks_of_mixed_sizes():
+    p = li.factor_gaussian(1500, 12, 1e-4, seed=3)
+    blocks = li.dense_blocks(1500, sizes=(1, 7, 40, 64, 65, 300, 900), seed=1)
+    run_batch(p, blocks, 16, 3, 1e-13)
+
+
+def test_laplace_fmm_blocks_small_tree():
+    p, blocks, lev = li.fmm_blocks(npts=1 << 15, leaf=64, min_size=64, max_size=2048, nblocks=96, seed=2)
+    assert len(blocks) > 20
+    run_batch(p, blocks, 32, 3, 1e-6)
+
+
+def test_invalid_block_is_isolated():
+    import paper_1710_07946_gb300 as lra
+    p = li.factor_gaussian(300, 5, 1e-3, seed=1)
+    blocks = np.array([[0, 100, 0, 120], [250, 100, 0, 50], [10, 60, 200, 90]], dtype=np.int64)
+    prob, _ = to_device(p)
+    I0 = li.block_initial_rows(np.array([[0, 100, 0, 120], [250, 50, 0, 50], [10, 60, 200, 90]]), 8, 0)
+    bt = lra.Batch(prob, blocks, 8, 2, I0)
+    lra.lra_ca_run_batched(bt)
+    torch.cuda.synchronize()
+    st = bt.out["info"][:, 3].cpu().numpy()
+    assert st[1] == lra.LRA_ERR_INVALID_ARG and st[0] in (0, 16) and st[2] in (0, 16)
+
+
+def test_batched_residual_matches_oracle():
+    import paper_1710_07946_gb300 as lra
+    p = li.factor_gaussian(800, 10, 1e-4, seed=5)
+    blocks = li.dense_blocks(800, sizes=(30, 200), seed=4)
+    bt, I0 = run_batch(p, blocks, 12, 2, 1e-13, check=[0])
+    Q, S = li.block_sample_positions(blocks, 16, 12, 9)
+    st = lra.lra_residual_sample_batched(bt, torch.from_numpy(Q).cuda(), torch.from_numpy(S).cuda()).cpu().numpy()
+    for b in range(len(blocks)):
+        r0, nr, c0, nc = blocks[b]
+        sub = li.Problem(li.SRC_DENSE, int(nr), int(nc), W=np.ascontiguousarray(p.W[r0:r0 + nr, c0:c0 + nc]))
+        g = bt.block(b)
+        so = oracle.residual_sample(sub, g["C"], g["U"], g["R"], Q[b], S[b])
+        np.testing.assert_allclose(st[b, 1:], so[1:], rtol=1e-9, atol=1e-300)
+        assert abs(st[b, 0] - so[0]) <= 1e-9 * so[2] + 1e-300
+
+
+def test_fmm_benchmark_workload_sampled_blocks():
+    """The 1M-point octree workload (about 4096 well-separated block pairs, 64..2048
+    points per box, Laplace kernel, k <= 64, rank tolerance 1e-6), as the
+    benchmark runs it; the oracle checks a sample of small and large blocks."""
+    p, blocks, lev = li.fmm_blocks(npts=1 << 20, seed=0)
+    sizes = blocks[:, 1] * blocks[:, 3]
+    pick = list(np.argsort(sizes)[:3]) + list(np.argsort(sizes)[-2:])
+    run_batch(p, blocks, 64, 3, 1e-6, check=pick)
