@@ -2,18 +2,25 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lib|reference] [--workload NAME]
 
-A step is one pass of the hot path over one synthetic input: the C-A CUR
-approximation (strip gathers with the fused multiplier, FP64 maxvol, nucleus,
-outputs C, U, R) followed by the sampled a-posteriori residual check of the
-result.  Inputs are seeded, synthetic and resident in HBM before the timed
-region; L2 is flushed (a 256 MiB write) before every timed step and each step is
-timed with CUDA events on the launching stream.  ``e2e`` repeats the same steps
-through the same public API from pinned host buffers, copies included.
+Default workload (``fmm``): the generators of an FMM / HSS matrix -- C-A CUR
+approximations of the 4096 well-separated block pairs of an octree over 2^20
+uniform points in [0,1]^3 (boxes of 64..2048 points, Laplace kernel evaluated
+on the fly, rank <= 64 adapted at tolerance 1e-6, 3 C-A loops, FP64 pivots and
+nucleus).  One step = the batched C-A launch (all blocks, nuclei included) +
+the batched a-posteriori residual sample (16 x 16 entries per block); the
+metric counts the blocks whose sampled relative Frobenius error is <= 1e-6.
+The ``dense8192_*`` workloads run one C-A CUR of an 8192 x 8192 FP32 input
+instead (one LRA per step).
 
-Under torchrun every rank runs an independent replica (a single LRA does not
-shard: its maxvol needs a global argmax per swap) and rank 0 prints one JSON
-line with the whole-job throughput (max time over ranks).  ``--impl reference``
-times the FP64 CPU oracle on the same workload (rank 0 only).
+Inputs are seeded, synthetic and resident in HBM before the timed region; L2 is
+flushed (a 256 MiB write, untimed) before every timed step; each step is timed
+with CUDA events on the launching stream, and the library's own per-launch
+events give the dominant kernel's duration.  ``e2e`` repeats the steps through
+the same public API from pinned host buffers, copies included.  Under torchrun
+each rank runs an independent problem of the same size (weak scaling, no
+collective on the data path); rank 0 prints one JSON line with the whole-job
+throughput over the slowest rank.  ``--impl reference`` times the FP64 CPU
+oracle on a bounded sample of the same workload (rank 0 only).
 """
 from __future__ import annotations
 
@@ -35,57 +42,241 @@ sys.path.insert(0, ROOT)
 import lra_inputs as li  # noqa: E402
 
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal; a plain DFMA loop measured 1.2)
+METRIC = "CUR LRAs/s at rel. err <= 1e-6 (FP64 pivots and nucleus)"
+ERR_BOUND = 1e-6
+LAPLACE_FLOPS = 8.0       # 3 sub, 1 mul, 2 fma, sqrt, div per kernel entry (nominal count)
 
 
-# ------------------------------------------------------------------ workloads
-class DenseSpiky:
-    """8192 x 8192 FP32, numerical rank 32 (Gaussian factors, s_i = 2^{-i/2},
-    1e-6 noise) with 1% of the entries replaced by +-10 spikes; right multiplier
-    ARHT (d = 2) or sparse +-1 (4 nonzeros per column); k = 48, 4 C-A loops."""
-
-    def __init__(self, mult: str, n: int = 8192, k: int = 48, sweeps: int = 4, seed: int = 0):
-        self.mult, self.n, self.k, self.sweeps, self.seed = mult, n, k, sweeps, seed
-        self.name = f"dense{n}_f32_rank32_spikes1pct_{'arht2' if mult == 'arht' else 'sparse4'}_k{k}_s{sweeps}"
-        self.q = self.s = 256
-
-    def host(self, rank: int):
-        p = li.dense_spiky(self.n, r=32, seed=self.seed + 1000 * rank)
-        if self.mult == "arht":
-            li.with_arht(p, 2, self.seed + 7)
-        else:
-            li.with_sparse(p, 4, self.seed + 7)
-        I0 = li.initial_rows(self.n, self.k, self.seed + 11)
-        Q, S = li.sample_positions(self.n, self.n, self.q, self.s, self.seed + 13)
-        return p, I0, Q, S
-
-    def config(self):
-        return {"workload": self.name, "m": self.n, "n": self.n, "k": self.k, "sweeps": self.sweeps,
-                "multiplier": "ARHT d=2" if self.mult == "arht" else "sparse +-1, 4 nnz/col",
-                "input_dtype": "f32", "residual_sample": f"{self.q}x{self.s}"}
-
-    def flops_per_lra(self, swaps: int) -> float:
-        """Algorithmic FP64 flops of one C-A run (fma = 2, division = 1): the
-        maxvol steps of the FP64 reference, see maxvol_flops()."""
-        k, n = self.k, self.n
-        f = maxvol_flops(k, n, cold=True)
-        f += (2 * self.sweeps - 1) * maxvol_flops(k, n, cold=False)
-        f += swaps * (2.0 * k * n + n)
-        return f
-
-
-def maxvol_flops(k: int, n: int, cold: bool) -> float:
+def maxvol_flops(k: int, n: int, cold: bool, entry_flops: float = 0.0) -> float:
+    """Algorithmic FP64 flops of one maxvol step on a k x n strip (fma = 2,
+    reciprocal = 1; the swaps are counted separately): LU with column pivoting
+    (cold) or the warm LU of the k x k block plus its replay, then the
+    back substitution; plus the strip's entries when they are evaluated."""
     if cold:
         fma = sum((k - 1 - t) * (n - 1 - t) for t in range(k))
     else:
         fma = sum((k - 1 - t) * (n - k) for t in range(k)) + sum((k - 1 - t) ** 2 for t in range(k))
     fma += (n - k) * k * (k - 1) // 2
-    div = (n - k) * k + (k * (k - 1) // 2)
-    return 2.0 * fma + div
+    div = (n - k) * k + 2 * k
+    ent = entry_flops * (k * n + (0 if cold else k * k))
+    return 2.0 * fma + div + ent
+
+
+def ca_flops(k, m, n, loops, swaps, entry_flops=0.0, nucleus=True):
+    f = maxvol_flops(k, n, True, entry_flops) + maxvol_flops(k, m, False, entry_flops)
+    f += (loops - 1) * (maxvol_flops(k, n, False, entry_flops) + maxvol_flops(k, m, False, entry_flops))
+    f += swaps * (2.0 * k * (m + n) / 2.0 + (m + n) / 2.0)
+    if nucleus:
+        f += 5.0 * k ** 3
+    return f
+
+
+# ------------------------------------------------------------------ workloads
+class FmmWorkload:
+    name = "fmm_laplace_1M_octree_4096blocks_k64_tol1e-6"
+    kernel = "ca_batched_kernel"
+    unit = "LRA/s"
+
+    def __init__(self, npts=1 << 20, nblocks=4096, k=64, sweeps=3, tol=1e-6, q=16, s=16):
+        self.npts, self.nblocks, self.k, self.sweeps, self.tol, self.q, self.s = npts, nblocks, k, sweeps, tol, q, s
+
+    def host(self, rank):
+        p, blocks, lev = li.fmm_blocks(npts=self.npts, nblocks=self.nblocks, seed=rank)
+        I0 = li.block_initial_rows(blocks, self.k, 100 + rank)
+        Q, S = li.block_sample_positions(blocks, self.q, self.s, 200 + rank)
+        self.levels = lev
+        return dict(p=p, blocks=blocks, I0=I0, Q=Q, S=S)
+
+    def config(self, h):
+        b = h["blocks"]
+        return {"workload": self.name, "points": self.npts, "blocks": int(len(b)),
+                "block_rows_min_median_max": [int(b[:, 1].min()), int(np.median(b[:, 1])), int(b[:, 1].max())],
+                "kernel": "Laplace 1/|x-y|, on the fly, FP64", "k_max": self.k, "rank_tol": self.tol,
+                "sweeps": self.sweeps, "residual_sample": f"{self.q}x{self.s} per block"}
+
+    def device(self, h, dev):
+        import torch
+        import paper_1710_07946_gb300 as lra
+        p = h["p"]
+        X = torch.from_numpy(p.X).to(dev)
+        prob = lra.Problem.kernel("laplace", X, X)
+        bt = lra.Batch(prob, h["blocks"], self.k, self.sweeps, h["I0"], rank_tol=self.tol)
+        d = dict(X=X, prob=prob, bt=bt, Q=torch.from_numpy(h["Q"]).to(dev), S=torch.from_numpy(h["S"]).to(dev))
+        d["stats"] = torch.empty(len(h["blocks"]), 5, dtype=torch.float64, device=dev)
+        return d
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        lra.lra_ca_run_batched(d["bt"])
+        lra.lra_residual_sample_batched(d["bt"], d["Q"], d["S"], d["stats"])
+
+    def check(self, d):
+        info = d["bt"].out["info"].cpu().numpy()
+        st = d["stats"].cpu().numpy()
+        ok = (info[:, 3] == 0) | (info[:, 3] >= 16)
+        good = ok & (st[:, 4] <= ERR_BOUND)
+        return dict(units=int(good.sum()), info=info, err=st[:, 4])
+
+    def flops(self, h, res):
+        b, info = h["blocks"], res["info"]
+        f = 0.0
+        for (r0, nr, c0, nc), inf in zip(b, info):
+            kb = int(min(self.k, nr, nc))
+            f += ca_flops(kb, int(nr), int(nc), max(int(inf[2]), 1), int(inf[1]), LAPLACE_FLOPS)
+        return f
+
+    def extra(self, res):
+        info, err = res["info"], res["err"]
+        return {"rank_min_median_max": [int(info[:, 0].min()), int(np.median(info[:, 0])), int(info[:, 0].max())],
+                "swaps_mean": float(info[:, 1].mean()), "loops_hist": np.bincount(info[:, 2]).tolist(),
+                "rel_fro_err_sampled_median": float(np.median(err)), "rel_fro_err_sampled_max": float(err.max()),
+                "frac_blocks_err_le_1e-6": float((err <= ERR_BOUND).mean())}
+
+    # end to end: points from pinned host memory, all C, U, R read back
+    def e2e_setup(self, h, d):
+        import torch
+        out = d["bt"].out
+        hp = dict(X=torch.from_numpy(h["p"].X).pin_memory())
+        hp["out"] = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in out.items()}
+        hp["stats"] = torch.empty(d["stats"].shape, dtype=torch.float64).pin_memory()
+        h2d = hp["X"].numel() * 8
+        d2h = sum(v.numel() * v.element_size() for v in hp["out"].values()) + hp["stats"].numel() * 8
+        return hp, h2d, d2h
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["X"].copy_(hp["X"], non_blocking=True)
+        self.step(d)
+        for key, v in hp["out"].items():
+            v.copy_(d["bt"].out[key], non_blocking=True)
+        hp["stats"].copy_(d["stats"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    # the FP64 oracle on one block
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        b = h["blocks"]
+        order = np.random.default_rng(seed).permutation(len(b))
+        t0 = time.perf_counter()
+        n = 0
+        good = 0
+        for idx in order:
+            r0, nr, c0, nc = b[idx]
+            kb = int(min(self.k, nr, nc))
+            sub = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=h["p"].X[r0:r0 + nr], Y=h["p"].Y[c0:c0 + nc])
+            o = oracle.ca_run(sub, kb, self.sweeps, h["I0"][idx, :kb], rank_tol=self.tol)
+            st = oracle.residual_sample(sub, o["C"], o["U"], o["R"], h["Q"][idx], h["S"][idx])
+            n += 1
+            good += st[4] <= ERR_BOUND
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        el = time.perf_counter() - t0
+        return good, n, el, f"{n} randomly chosen blocks of the same batch (C-A + nucleus + residual sample each)"
+
+
+class DenseWorkload:
+    kernel = "ca_kernel"
+    unit = "LRA/s"
+
+    def __init__(self, mult, n=8192, k=48, sweeps=4):
+        self.mult, self.n, self.k, self.sweeps, self.q, self.s = mult, n, k, sweeps, 256, 256
+        self.name = f"dense{n}_f32_rank32_spikes1pct_{'arht2' if mult == 'arht' else 'sparse4'}_k{k}_s{sweeps}"
+
+    def host(self, rank):
+        p = li.dense_spiky(self.n, r=32, seed=1000 * rank)
+        if self.mult == "arht":
+            li.with_arht(p, 2, 7)
+        else:
+            li.with_sparse(p, 4, 7)
+        I0 = li.initial_rows(self.n, self.k, 11)
+        Q, S = li.sample_positions(self.n, self.n, self.q, self.s, 13)
+        return dict(p=p, I0=I0, Q=Q, S=S)
+
+    def config(self, h):
+        return {"workload": self.name, "m": self.n, "n": self.n, "k": self.k, "sweeps": self.sweeps,
+                "multiplier": "ARHT d=2" if self.mult == "arht" else "sparse +-1, 4 nnz/col",
+                "input_dtype": "f32", "residual_sample": f"{self.q}x{self.s}"}
+
+    def device(self, h, dev):
+        import torch
+        import paper_1710_07946_gb300 as lra
+        p = h["p"]
+        W = torch.from_numpy(p.W).to(dev)
+        prob = lra.Problem.dense(W)
+        mult = (lra.lra_precondition("arht", p.n, p.depth, p.perm, p.dsign) if p.mkind == li.MULT_ARHT
+                else lra.lra_precondition("sparse", p.n, p.nnz, p.srow, p.ssign))
+        I0 = torch.from_numpy(h["I0"]).to(dev)
+        out = lra.lra_ca_run(prob, I0, self.k, self.sweeps, multiplier=mult)
+        return dict(W=W, prob=prob, mult=mult, I0=I0, out=out, Q=torch.from_numpy(h["Q"]).to(dev),
+                    S=torch.from_numpy(h["S"]).to(dev), stats=None)
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        lra.lra_ca_run(d["prob"], d["I0"], self.k, self.sweeps, multiplier=d["mult"], out=d["out"],
+                       workspace=d["out"]["_workspace"])
+        d["stats"] = lra.lra_residual_sample(d["prob"], d["out"]["C"], d["out"]["U"], d["out"]["R"], d["Q"], d["S"])
+
+    def check(self, d):
+        info = d["out"]["info"].cpu().numpy()[None, :]
+        err = d["stats"].cpu().numpy()[4:5]
+        return dict(units=1, info=info, err=err)      # spikes: the error bound is not attainable here
+
+    def flops(self, h, res):
+        inf = res["info"][0]
+        return ca_flops(self.k, self.n, self.n, self.sweeps, int(inf[1]), 0.0, nucleus=False)
+
+    def extra(self, res):
+        inf = res["info"][0]
+        return {"rank": int(inf[0]), "swaps": int(inf[1]), "loops": int(inf[2]), "status": int(inf[3]),
+                "rel_fro_err_sampled": float(res["err"][0])}
+
+    def e2e_setup(self, h, d):
+        import torch
+        hp = dict(W=torch.from_numpy(h["p"].W).pin_memory(), I0=torch.from_numpy(h["I0"]).pin_memory())
+        hp["out"] = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in d["out"].items()
+                     if not key.startswith("_")}
+        hp["stats"] = torch.empty(5, dtype=torch.float64).pin_memory()
+        h2d = hp["W"].numel() * 4 + hp["I0"].numel() * 4
+        d2h = sum(v.numel() * v.element_size() for v in hp["out"].values()) + 40
+        return hp, h2d, d2h
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["W"].copy_(hp["W"], non_blocking=True)
+        d["I0"].copy_(hp["I0"], non_blocking=True)
+        self.step(d)
+        for key, v in hp["out"].items():
+            v.copy_(d["out"][key], non_blocking=True)
+        hp["stats"].copy_(d["stats"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            o = oracle.ca_run(h["p"], self.k, self.sweeps, h["I0"])
+            oracle.residual_sample(h["p"], o["C"], o["U"], o["R"], h["Q"], h["S"])
+            n += 1
+            if time.perf_counter() - t0 >= budget_s or n >= 50:
+                break
+        el = time.perf_counter() - t0
+        return n, n, el, f"{n} complete LRAs of the same input (C-A + nucleus + residual sample)"
+
+
+class FmmSmallWorkload(FmmWorkload):
+    """The same recipe on 2^17 points and 512 block pairs (profiling size)."""
+    name = "fmm_laplace_128K_octree_512blocks_k64_tol1e-6"
+
+    def __init__(self):
+        super().__init__(npts=1 << 17, nblocks=512)
 
 
 WORKLOADS = {
-    "dense8192_arht": lambda: DenseSpiky("arht"),
-    "dense8192_sparse": lambda: DenseSpiky("sparse"),
+    "fmm": FmmWorkload,
+    "fmm_small": FmmSmallWorkload,
+    "dense8192_arht": lambda: DenseWorkload("arht"),
+    "dense8192_sparse": lambda: DenseWorkload("sparse"),
 }
 
 
@@ -107,7 +298,7 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
-        except (OSError, FileNotFoundError):
+        except OSError:
             self.proc = None
 
     def _read(self):
@@ -129,7 +320,8 @@ class ClockSampler:
             if len(f) < 9:
                 continue
             try:
-                sm.append(float(f[1])); mx = float(f[2])
+                sm.append(float(f[1]))
+                mx = float(f[2])
             except ValueError:
                 continue
             for nm, v in zip(names, f[5:9]):
@@ -149,9 +341,9 @@ def csrc_hash() -> str:
 
 
 def ncu_traffic(kernel: str, workload: str):
-    """Per-launch DRAM bytes of `kernel` from a committed ncu summary, if it was
-    taken on the current sources (profiles/<kernel>__<workload>.txt lines
-    'csrc_hash: ...' and 'dram_bytes_per_launch: ...'); else None."""
+    """Per-launch DRAM bytes of `kernel` from a committed ncu summary taken on the
+    current sources (profiles/<kernel>__<workload>.txt lines 'csrc_hash: ...' and
+    'dram_bytes_per_launch: ...'); None otherwise."""
     path = os.path.join(ROOT, "profiles", f"{kernel}__{workload}.txt")
     if not os.path.exists(path):
         return None
@@ -176,55 +368,37 @@ def load_peaks():
         return {}
 
 
-# ------------------------------------------------------------------ oracle arm
-def oracle_step(wl, p, I0, Q, S):
-    import oracle
-    o = oracle.ca_run(p, wl.k, wl.sweeps, I0)
-    st = oracle.residual_sample(p, o["C"], o["U"], o["R"], Q, S)
-    return o, st
+def cpu_cores_used() -> int:
+    return 1
 
 
-def cpu_baseline(wl, p, I0, Q, S, budget_s: float = 12.0):
-    """The oracle as it stands, single-threaded, on whole LRAs until budget_s."""
-    t0 = time.perf_counter()
-    n = 0
-    while True:
-        oracle_step(wl, p, I0, Q, S)
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= budget_s or n >= 50:
-            break
-    return {"value": n / el, "unit": "LRA/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} complete LRAs of the same workload (C-A + nucleus + {wl.q}x{wl.s} residual sample), "
-                      f"{el:.1f} s, 1 thread"}
-
-
+# ------------------------------------------------------------------ arms
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    p, I0, Q, S = wl.host(0)
-    for _ in range(args.warmup):
-        oracle_step(wl, p, I0, Q, S)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle_step(wl, p, I0, Q, S)
-    el = time.perf_counter() - t0
-    v = args.steps / el
-    line = {"metric": METRIC, "value": v, "unit": "LRA/s", "n_gpus": args.gpus, "steps": args.steps,
+    h = wl.host(0)
+    per_step = max(args.ref_budget / max(args.steps + args.warmup, 1), 0.5)
+    for w in range(args.warmup):
+        wl.oracle_units(h, per_step, seed=w)
+    good = n = 0
+    el = 0.0
+    for s in range(args.steps):
+        g, c, e, desc = wl.oracle_units(h, per_step, seed=100 + s)
+        good += g
+        n += c
+        el += e
+    v = good / el
+    line = {"metric": METRIC, "value": v, "unit": wl.unit, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": wl.config(),
-            "cpu_baseline": {"value": v, "unit": "LRA/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} timed LRAs after {args.warmup} warm-up, 1 thread"},
-            "e2e": {"value": v, "unit": "LRA/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "config": wl.config(h),
+            "cpu_baseline": {"value": v, "unit": wl.unit, "cores": cpu_cores_used(), "kind": "oracle",
+                             "sample": f"{args.steps} steps of ~{per_step:.1f} s, each: " + desc},
+            "e2e": {"value": v, "unit": wl.unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-METRIC = "CUR LRAs/s (C-A, FP64 pivots and nucleus)"
-
-
-# ------------------------------------------------------------------ library arm
 def run_lib(args, wl):
     import torch
     import torch.distributed as dist
@@ -240,28 +414,17 @@ def run_lib(args, wl):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
 
-    p, I0, Q, S = wl.host(rank)
-    Wd = torch.from_numpy(p.W).to(dev)
-    prob = lra.Problem.dense(Wd)
-    mult = (lra.lra_precondition("arht", p.n, p.depth, p.perm, p.dsign) if p.mkind == li.MULT_ARHT
-            else lra.lra_precondition("sparse", p.n, p.nnz, p.srow, p.ssign))
-    I0d = torch.from_numpy(I0).to(dev)
-    Qd, Sd = torch.from_numpy(Q).to(dev), torch.from_numpy(S).to(dev)
-    k, sweeps = wl.k, wl.sweeps
-    out = lra.lra_ca_run(prob, I0d, k, sweeps, multiplier=mult)
-    ws = out["_workspace"]
+    h = wl.host(rank)
+    d = wl.device(h, dev)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
-
-    def step():
-        lra.lra_ca_run(prob, I0d, k, sweeps, multiplier=mult, out=out, workspace=ws)
-        return lra.lra_residual_sample(prob, out["C"], out["U"], out["R"], Qd, Sd)
-
-    for _ in range(max(args.warmup, 3)):
-        stats = step()
+    warm = max(args.warmup, 3)
+    for _ in range(warm):
+        wl.step(d)
     torch.cuda.synchronize()
-    info = out["info"].cpu().numpy()
-    if info[3] not in (0, 16, 17):
-        raise RuntimeError(f"C-A run failed with status {info[3]}")
+    l0 = lra.lra_launch_count()
+    wl.step(d)
+    torch.cuda.synchronize()
+    launches_per_step = lra.lra_launch_count() - l0
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -271,91 +434,106 @@ def run_lib(args, wl):
     clocks.start()
     launches0 = lra.lra_launch_count()
     lra.lra_profile_enable(True)
+    units = 0
     t_wall = time.perf_counter()
     for i in range(args.steps):
         flush.fill_(float(i))
         ev[i][0].record(stream)
-        stats = step()
+        wl.step(d)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall
     lra.lra_profile_enable(False)
     launches = lra.lra_launch_count() - launches0
     prof = lra.lra_profile_collect()
+    res = wl.check(d)
+    units = res["units"] * args.steps
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_max = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    tmax = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    tot_units = torch.tensor([float(units)], dtype=torch.float64, device=dev)
     if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
-    value = world * args.steps / (total_ms / 1e3)
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        dist.all_reduce(tot_units, op=dist.ReduceOp.SUM)
+    total_ms = float(tmax.item())
+    value = float(tot_units.item()) / (total_ms / 1e3)
 
-    # end to end through the same API from pinned host memory
-    Wh = torch.from_numpy(p.W).pin_memory()
-    I0h = torch.from_numpy(I0).pin_memory()
-    host_out = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in out.items()
-                if not key.startswith("_")}
-    st_h = torch.empty(5, dtype=torch.float64).pin_memory()
-    h2d = Wh.numel() * Wh.element_size() + I0h.numel() * 4
-    d2h = sum(v.numel() * v.element_size() for v in host_out.values()) + 40
+    # the same step replayed from a CUDA graph (cross-check of launch overhead)
+    graph_ms = None
+    try:
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream(dev)
+        s.wait_stream(stream)
+        with torch.cuda.stream(s):
+            wl.step(d)
+        stream.wait_stream(s)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g):
+            wl.step(d)
+        g.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        gsum = 0.0
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            e1.synchronize()
+            gsum += e0.elapsed_time(e1)
+        graph_ms = gsum / args.steps
+        del g
+    except Exception as exc:  # graph capture is a cross-check only
+        graph_ms = f"capture failed: {type(exc).__name__}"
 
-    def e2e_step():
-        Wd.copy_(Wh, non_blocking=True)
-        I0d.copy_(I0h, non_blocking=True)
-        s = step()
-        for key, v in host_out.items():
-            v.copy_(out[key], non_blocking=True)
-        st_h.copy_(s, non_blocking=True)
-        torch.cuda.current_stream().synchronize()
-
-    e2e_step()
+    # end to end through the public API from pinned host buffers
+    hp, h2d, d2h = wl.e2e_setup(h, d)
+    wl.e2e_step(hp, d)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True); e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    t0 = time.perf_counter()
     for _ in range(args.steps):
-        e2e_step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+        wl.e2e_step(hp, d)
+    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
     if world > 1:
-        dist.all_reduce(e2e_ms, op=dist.ReduceOp.MAX)
-    e2e_value = world * args.steps / (float(e2e_ms.item()) / 1e3)
+        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
+    e2e_value = float(tot_units.item()) / float(e2e_s.item())
 
     if rank == 0:
-        info = out["info"].cpu().numpy()
-        st = stats.cpu().numpy()
-        swaps = int(info[1])
-        ca_ms, ca_n = prof.get("ca_kernel", (float("nan"), 0))
-        ca_avg_s = ca_ms / max(ca_n, 1) / 1e3
-        flops = wl.flops_per_lra(swaps)
-        achieved = flops / ca_avg_s / 1e12
-        traffic = ncu_traffic("ca_kernel", wl.name)
+        kms, kn = prof.get(wl.kernel, (float("nan"), 0))
+        kavg = kms / max(kn, 1) / 1e3
+        flops = wl.flops(h, res)
+        achieved = flops / kavg / 1e12
         peaks = load_peaks()
+        cfg = dict(wl.config(h), l2="flushed before every step (256 MiB write, untimed)",
+                   parallelism=f"{world} independent problem(s), one per GPU", mode="fp64",
+                   graph_ms_per_step=graph_ms, wall_s=t_wall)
+        cfg.update(wl.extra(res))
         line = {
-            "metric": METRIC, "value": value, "unit": "LRA/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": dict(wl.config(), l2="flushed before every step (256 MiB write, untimed)",
-                           parallelism=f"replicas x{world}", mode="fp64",
-                           rank=int(info[0]), swaps=swaps, loops=int(info[2]), status=int(info[3]),
-                           rel_fro_err_sampled=float(st[4]), wall_s=t_wall),
-            "roofline": {"bound": "alu", "kernel": "ca_kernel", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
-                         "peak_source": "FP64 DFMA: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz (nominal 1.25 TFLOP/s)",
-                         "flops_per_launch": flops, "avg_launch_ms": ca_avg_s * 1e3,
+            "metric": METRIC, "value": value, "unit": wl.unit, "n_gpus": world, "steps": args.steps,
+            "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+            "roofline": {"bound": "alu", "kernel": wl.kernel, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": ncu_traffic(wl.kernel, wl.name),
+                         "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26, nominal 1.25 "
+                                        "TFLOP/s (not in MEASURED_PEAKS.json; a plain DFMA loop measured 1.2)",
+                         "flops_per_launch": flops, "avg_launch_ms": kavg * 1e3,
                          "hbm_peak_gbs": peaks.get("hbm_gbs")},
             "kernels": {kname: {"ms_total": v[0], "launches": v[1]} for kname, v in prof.items()},
             "gpu_launches": int(launches),
+            "launches_per_step": int(launches_per_step),
             "clocks": clk,
-            "e2e": {"value": e2e_value, "unit": "LRA/s", "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": e2e_value, "unit": wl.unit, "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(wl, p, I0, Q, S)
+            good, n, el, desc = wl.oracle_units(h, args.cpu_budget)
+            line["cpu_baseline"] = {"value": good / el, "unit": wl.unit, "cores": cpu_cores_used(), "kind": "oracle",
+                                    "sample": f"{desc}; {el:.1f} s on 1 host thread"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -364,11 +542,13 @@ def run_lib(args, wl):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="lib", choices=["lib", "reference"])
-    ap.add_argument("--workload", default="dense8192_arht", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="fmm", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--ref-budget", type=float, default=90.0, help="seconds of oracle time for --impl reference")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]()
     if args.impl == "reference":
