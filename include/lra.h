@@ -109,8 +109,16 @@ typedef enum {
   LRA_MODE_FP64 = 0,        /* every gather, pivot and nucleus step in FP64, in the
                                operation order of the FP64 reference (bit-exact
                                pivots)                                              */
-  LRA_MODE_MIXED = 1        /* FP32 strips screened by a running error bound; every
-                               pivot decision still confirmed in FP64                */
+  LRA_MODE_MIXED = 1        /* each maxvol step first runs in FP32 with a rigorous
+                               bound on every entry's distance to the FP64 reference;
+                               a step whose every decision (pivot, swap, stop) the
+                               bounds certify is kept, any other step is redone in
+                               FP64.  Index sets, swap counts, C, R and U equal those
+                               of LRA_MODE_FP64; logvol is then computed from the FP32
+                               pivots (relative accuracy ~1e-6).  It runs on one CTA:
+                               every block of a batch, and lra_ca_run inputs with
+                               max(m, n) <= 2048; larger single runs and Gaussian
+                               kernels run in FP64.                                 */
 } lra_mode;
 
 typedef struct {
@@ -131,8 +139,12 @@ typedef struct {
   double* R;             /* k x n: W[I, :] (original rows: for an orthogonal M this is
                             the back-transform R_H M^T of Algorithm alglratpsvd1)     */
   double* logvol;        /* 2*sweeps: log|det W'[I,J]| after each step (NaN if unrun) */
-  int32_t* info;         /* 4 ints: numerical rank r, total swaps, loops run, status */
+  int32_t* info;         /* LRA_INFO_LEN ints: numerical rank r, total swaps, loops run,
+                            status, maxvol steps decided in FP32 (mixed mode), maxvol
+                            steps run in FP64, 0, 0                                    */
 } lra_cur;
+
+#define LRA_INFO_LEN 8
 
 /*
  * lra_ca_workspace_size -- bytes of device workspace lra_ca_run needs for this
@@ -220,7 +232,7 @@ typedef struct {
   double* U;               /* nb x k x k: U_b (k_b x k_b, row-major) at the slot start     */
   double* R;               /* packed R_b                                                  */
   double* logvol;          /* nb x 2*sweeps                                               */
-  int32_t* info;           /* nb x 4: rank, swaps, loops, status (as lra_cur.info)         */
+  int32_t* info;           /* nb x LRA_INFO_LEN (as lra_cur.info)                          */
 } lra_cur_batch;
 
 /* Workspace bytes of lra_ca_run_batched (params: par->k is the largest rank). */

@@ -32,6 +32,7 @@ LRA_F64, LRA_F32 = 0, 1
 LRA_DENSE, LRA_KERNEL_LAPLACE, LRA_KERNEL_GAUSSIAN = 0, 1, 2
 LRA_MULT_NONE, LRA_MULT_ARHT, LRA_MULT_SPARSE_PM1 = 0, 1, 2
 LRA_MODE_FP64, LRA_MODE_MIXED = 0, 1
+LRA_INFO_LEN = 8
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NONFINITE", 4: "TIMEOUT", 5: "WORKSPACE",
            16: "WARN_RANK_DEFICIENT", 17: "WARN_NOT_CONVERGED"}
@@ -256,7 +257,7 @@ def lra_ca_run(problem: Problem, I0: torch.Tensor, k: int, sweeps: int = 3, h: f
                    U=torch.empty(k, k, dtype=torch.float64, device=dev),
                    R=torch.empty(k, problem.n, dtype=torch.float64, device=dev),
                    logvol=torch.empty(2 * sweeps, dtype=torch.float64, device=dev),
-                   info=torch.empty(4, dtype=torch.int32, device=dev))
+                   info=torch.empty(LRA_INFO_LEN, dtype=torch.int32, device=dev))
     if workspace is None:
         nb = ct.c_size_t()
         _check(L.lra_ca_workspace_size(ct.byref(pc), ct.byref(pp), mh, ct.byref(nb)), "lra_ca_workspace_size")
@@ -361,7 +362,7 @@ class Batch:
     launch kernels, so they can be captured in a CUDA graph."""
 
     def __init__(self, problem: Problem, blocks, k: int, sweeps: int, I0, h: float = 1.01, rank_tol: float = 1e-6,
-                 max_swaps: int = 1000, order="lpt", device=None):
+                 max_swaps: int = 1000, order="lpt", device=None, mode: int = LRA_MODE_FP64):
         import numpy as np
         blocks = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64).reshape(-1, 4))
         nb = len(blocks)
@@ -375,7 +376,7 @@ class Batch:
             order = np.argsort(-(blocks[:, 1] * blocks[:, 3]), kind="stable").astype(np.int32)
         self.problem, self.k, self.sweeps, self.nb = problem, int(k), int(sweeps), nb
         self.blocks_np, self.offs_np, self.kb = blocks, offs, kb
-        self.params = _params(k, sweeps, h, rank_tol, max_swaps, LRA_MODE_FP64)
+        self.params = _params(k, sweeps, h, rank_tol, max_swaps, mode)
         t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
         self.blocks, self.offs = t(blocks, np.int64), t(offs, np.int64)
         self.order = None if order is None else t(order, np.int32)
@@ -386,7 +387,7 @@ class Batch:
                         U=torch.zeros(nb, k, k, dtype=torch.float64, device=dev),
                         R=torch.zeros(max(int(rsz.sum()), 1), dtype=torch.float64, device=dev),
                         logvol=torch.zeros(nb, 2 * sweeps, dtype=torch.float64, device=dev),
-                        info=torch.zeros(nb, 4, dtype=torch.int32, device=dev))
+                        info=torch.zeros(nb, LRA_INFO_LEN, dtype=torch.int32, device=dev))
         self.cb = _Batch()
         self.cb.blocks, self.cb.offsets = self.blocks.data_ptr(), self.offs.data_ptr()
         self.cb.order = self.order.data_ptr() if self.order is not None else None
@@ -410,7 +411,8 @@ class Batch:
         return dict(I=o["I"][b, :kb], J=o["J"][b, :kb], C=o["C"][oc:oc + nr * kb].reshape(nr, kb),
                     U=o["U"][b].reshape(-1)[:kb * kb].reshape(kb, kb),
                     R=o["R"][orr:orr + kb * nc].reshape(kb, nc), logvol=o["logvol"][b],
-                    rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]), status=int(info[3]))
+                    rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]), status=int(info[3]),
+                    fp32_steps=int(info[4]), fp64_steps=int(info[5]))
 
 
 def lra_ca_run_batched(batch: Batch, stream=None) -> None:

@@ -2,6 +2,7 @@
 // the C ABI.
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 
 #include "lra_internal.h"
@@ -44,9 +45,26 @@ lra_status make_dev_problem(const lra_problem* p, lra_multiplier mult, DevProble
     } else {
       d.nnz = mult->param;
     }
+    // FP32 copy of the scale; exact when it is a power of two (even depth, nnz = 1, 4, 16)
+    const bool exact = (mult->kind == LRA_MULT_ARHT) ? (mult->param % 2 == 0)
+                                                     : (mult->param == 1 || mult->param == 4 || mult->param == 16);
+    d.mscale32 = (float)mult->scale;
+    d.mscale_err = exact ? 0.0f : 1.0001f * 5.9604644775390625e-08f * d.mscale32;
   }
   *out = d;
   return LRA_OK;
+}
+
+__global__ void points_to_f32_kernel(const double* __restrict__ X, int64_t cnt, float* __restrict__ out) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = __double2float_rn(X[i]);
+}
+
+lra_status points_to_f32(const double* X, int64_t npts, float* out, cudaStream_t stream) {
+  const int64_t cnt = 3 * npts;
+  const int grid = (int)std::min<int64_t>((cnt + 255) / 256, 4096);
+  points_to_f32_kernel<<<grid, 256, 0, stream>>>(X, cnt, out);
+  return cuda_status(cudaGetLastError());
 }
 
 lra_status current_device_info(DeviceInfo* info) {

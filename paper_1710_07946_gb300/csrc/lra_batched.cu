@@ -11,7 +11,7 @@
 #include <algorithm>
 #include <cstring>
 
-#include "lra_ca_core.cuh"
+#include "lra_ca_loop.cuh"
 #include "lra_internal.h"
 #include "lra_nucleus.cuh"
 #include "lra_profile.h"
@@ -32,14 +32,16 @@ struct BatchArgs {
   double* R;                // packed
   double* U;                // nb x kmax x kmax (k_b x k_b at the start of each slot)
   double* logvol;           // nb x 2 sweeps
-  int32_t* info;            // nb x 4
+  int32_t* info;            // nb x LRA_INFO_LEN
   unsigned int* counter;    // work queue head
   double* scratch;          // per CTA: G (kmax^2) then, if needed, a strip (kmax x max_len)
   size_t scratch_stride;    // doubles per CTA
   int32_t cap_ldm;          // largest strip length kept in shared memory
   int64_t max_len;          // largest block dimension the scratch was sized for
+  int32_t mixed;
 };
 
+template <bool MIXED>
 __global__ void __launch_bounds__(NT) ca_batched_kernel(BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_b;
@@ -54,12 +56,12 @@ __global__ void __launch_bounds__(NT) ca_batched_kernel(BatchArgs B) {
     const int b = s_b;
     __syncthreads();
     if (b < 0) break;
-    int32_t* info = B.info + 4 * (size_t)b;
+    int32_t* info = B.info + LRA_INFO_LEN * (size_t)b;
     const int64_t r0 = B.blocks[4 * (size_t)b], nr = B.blocks[4 * (size_t)b + 1];
     const int64_t c0 = B.blocks[4 * (size_t)b + 2], nc = B.blocks[4 * (size_t)b + 3];
     if (r0 < 0 || c0 < 0 || nr < 1 || nc < 1 || r0 + nr > B.base.m || c0 + nc > B.base.n || nr > B.max_len ||
         nc > B.max_len) {
-      if (threadIdx.x == 0) { info[0] = 0; info[1] = 0; info[2] = 0; info[3] = LRA_ERR_INVALID_ARG; }
+      for (int e = threadIdx.x; e < LRA_INFO_LEN; e += blockDim.x) info[e] = (e == 3) ? LRA_ERR_INVALID_ARG : 0;
       continue;
     }
     CaArgs A;
@@ -90,9 +92,14 @@ __global__ void __launch_bounds__(NT) ca_batched_kernel(BatchArgs B) {
     A.chunk_m = (int)nr;
     A.ldm = (int)max(nr, nc);
     A.strip_in_smem = A.ldm <= B.cap_ldm;
+    A.mixed = B.mixed;
+    if (B.mixed && A.P.src == LRA_KERNEL_LAPLACE) {
+      A.P.X32 = B.base.X32 + 3 * r0;
+      A.P.Y32 = B.base.Y32 + 3 * c0;
+    }
     A.gstrip = A.strip_in_smem ? nullptr : gstrip;
     const CaSmem S = ca_smem_carve(smem, k, A.ldm, A.strip_in_smem ? nullptr : gstrip);
-    ca_loop(SoloGroup{}, A, S);
+    ca_loop<SoloGroup, MIXED>(SoloGroup{}, A, S);
     __syncthreads();
     const int st = info[3];
     if (!(st != LRA_OK && st < 16)) {
@@ -120,7 +127,7 @@ __global__ void __launch_bounds__(256) resid_batched_kernel(DevProblem base, con
   __shared__ double red[33];
   for (int b = blockIdx.x; b < nb; b += gridDim.x) {
     double* st = stats + 5 * (size_t)b;
-    const int status = info[4 * (size_t)b + 3];
+    const int status = info[LRA_INFO_LEN * (size_t)b + 3];
     const int64_t r0 = blocks[4 * (size_t)b], nr = blocks[4 * (size_t)b + 1];
     const int64_t c0 = blocks[4 * (size_t)b + 2], nc = blocks[4 * (size_t)b + 3];
     if (status != LRA_OK && status < 16) {
@@ -216,6 +223,7 @@ struct BatchPlan {
   int cap_ldm;
   size_t smem;
   size_t scratch_stride;
+  size_t off_pts;
   size_t bytes;
 };
 
@@ -223,7 +231,8 @@ static size_t ca_need(int k, int ldm, bool strip) {
   return ca_smem_fixed(k, ldm) + (strip ? sizeof(double) * (size_t)k * ldm : 0);
 }
 
-static lra_status batch_plan(int32_t kmax, int64_t max_len, BatchPlan* pl) {
+static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int64_t max_len, BatchPlan* pl) {
+  const int32_t kmax = par->k;
   DeviceInfo dev;
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
@@ -240,16 +249,21 @@ static lra_status batch_plan(int32_t kmax, int64_t max_len, BatchPlan* pl) {
   size_t smem = std::max(ca_need(kmax, cap, true), nucleus_smem_bytes(kmax));
   if (max_len > cap) smem = std::max(smem, ca_need(kmax, (int)max_len, false));
   if (smem > budget) return LRA_ERR_INVALID_ARG;
-  LRA_CUDA_TRY(cudaFuncSetAttribute(ca_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const bool mixed = par->mode == LRA_MODE_MIXED && P.src != LRA_KERNEL_GAUSSIAN;
+  auto kern = mixed ? ca_batched_kernel<true> : ca_batched_kernel<false>;
+  LRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  LRA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ca_batched_kernel, NT, smem));
+  LRA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
   if (occ < 1) return LRA_ERR_INVALID_ARG;
   pl->grid = occ * dev.sms;
   pl->cap_ldm = cap;
   pl->smem = smem;
   pl->scratch_stride = (size_t)kmax * kmax + (max_len > cap ? (size_t)kmax * max_len : 0);
   pl->scratch_stride = align_up(pl->scratch_stride, 32);
-  pl->bytes = 256 + sizeof(double) * pl->scratch_stride * pl->grid;
+  pl->off_pts = align_up(256 + sizeof(double) * pl->scratch_stride * pl->grid, 256);
+  pl->bytes = pl->off_pts;
+  if (par->mode == LRA_MODE_MIXED && P.src == LRA_KERNEL_LAPLACE)
+    pl->bytes = align_up(pl->off_pts + sizeof(float) * 3 * (size_t)(P.m + P.n), 256);
   return LRA_OK;
 }
 
@@ -267,7 +281,7 @@ lra_status lra_ca_batched_workspace_size(const lra_problem* base, const lra_batc
   if (st != LRA_OK) return st;
   if (par->k < 1 || par->k > KMAX || batch->nb < 1 || batch->max_len < 1) return LRA_ERR_INVALID_ARG;
   BatchPlan pl;
-  if ((st = batch_plan(par->k, batch->max_len, &pl)) != LRA_OK) return st;
+  if ((st = batch_plan(P, par, batch->max_len, &pl)) != LRA_OK) return st;
   *bytes = pl.bytes;
   return LRA_OK;
 }
@@ -283,11 +297,12 @@ lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, c
   if (batch->blocks == nullptr || batch->offsets == nullptr || batch->nb < 1 || batch->max_len < 1)
     return LRA_ERR_INVALID_ARG;
   if (par->k < 1 || par->k > KMAX || par->sweeps < 1 || par->max_swaps < 0 || !(par->h >= 1.0) ||
-      !(par->h < 1e300) || !(par->rank_tol >= 0.0) || !(par->rank_tol < 1.0) || par->mode != LRA_MODE_FP64)
+      !(par->h < 1e300) || !(par->rank_tol >= 0.0) || !(par->rank_tol < 1.0) ||
+      (par->mode != LRA_MODE_FP64 && par->mode != LRA_MODE_MIXED))
     return LRA_ERR_INVALID_ARG;
   if (!out->I || !out->J || !out->C || !out->U || !out->R || !out->logvol || !out->info) return LRA_ERR_INVALID_ARG;
   BatchPlan pl;
-  if ((st = batch_plan(par->k, batch->max_len, &pl)) != LRA_OK) return st;
+  if ((st = batch_plan(P, par, batch->max_len, &pl)) != LRA_OK) return st;
   if (workspace == nullptr || workspace_bytes < pl.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255u))
     return LRA_ERR_WORKSPACE;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
@@ -316,10 +331,19 @@ lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, c
   A.scratch_stride = pl.scratch_stride;
   A.cap_ldm = pl.cap_ldm;
   A.max_len = batch->max_len;
+  A.mixed = (par->mode == LRA_MODE_MIXED && P.src != LRA_KERNEL_GAUSSIAN) ? 1 : 0;
+  if (A.mixed && P.src == LRA_KERNEL_LAPLACE) {
+    float* X32 = reinterpret_cast<float*>(ws + pl.off_pts);
+    A.base.X32 = X32;
+    A.base.Y32 = X32 + 3 * P.m;
+    if ((st = points_to_f32(P.X, P.m, X32, stream)) != LRA_OK) return st;
+    if ((st = points_to_f32(P.Y, P.n, X32 + 3 * P.m, stream)) != LRA_OK) return st;
+  }
   LRA_CUDA_TRY(cudaMemsetAsync(ws, 0, 256, stream));
   {
     LaunchScope ls(stream, "ca_batched_kernel");
-    ca_batched_kernel<<<pl.grid, NT, pl.smem, stream>>>(A);
+    if (A.mixed) ca_batched_kernel<true><<<pl.grid, NT, pl.smem, stream>>>(A);
+    else ca_batched_kernel<false><<<pl.grid, NT, pl.smem, stream>>>(A);
   }
   return cuda_status(cudaGetLastError());
 }

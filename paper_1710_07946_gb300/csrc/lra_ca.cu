@@ -10,19 +10,19 @@
 #include <algorithm>
 #include <cstring>
 
-#include "lra_ca_core.cuh"
+#include "lra_ca_loop.cuh"
 #include "lra_internal.h"
 #include "lra_nucleus.cuh"
 #include "lra_profile.h"
 
 namespace lra {
 
-template <class Group>
+template <class Group, bool MIXED = false>
 __global__ void __launch_bounds__(NT) ca_kernel(CaArgs A, Group grp) {
   extern __shared__ __align__(16) unsigned char smem[];
   double* gchunk = A.strip_in_smem ? nullptr : A.gstrip + (size_t)grp.rank() * A.k * A.ldm;
   CaSmem S = ca_smem_carve(smem, A.k, A.ldm, gchunk);
-  ca_loop(grp, A, S);
+  ca_loop<Group, MIXED>(grp, A, S);
 }
 
 __global__ void __launch_bounds__(NT) nucleus_kernel(const double* G, int k, double tol, double* U, int32_t* info) {
@@ -38,13 +38,15 @@ __global__ void __launch_bounds__(NT) nucleus_kernel(const double* G, int k, dou
 
 constexpr size_t STATIC_SMEM_RESERVE = 4096;   // the exchange / reduction arrays
 constexpr int MIN_COLS_PER_CTA = 32;
+constexpr int64_t MIXED_SOLO_MAX = 2048;
 
 struct CaPlan {
   int nblk;
   int chunk_n, chunk_m, ldm;
   int strip_in_smem;
   size_t smem;
-  size_t off_hdr, off_G, off_slots, off_strip, bytes;
+  size_t off_hdr, off_G, off_slots, off_strip, off_pts, bytes;
+  int mixed;
 };
 
 static lra_status validate_params(const DevProblem& P, const lra_ca_params* par) {
@@ -54,7 +56,7 @@ static lra_status validate_params(const DevProblem& P, const lra_ca_params* par)
   if (par->sweeps < 1 || par->max_swaps < 0) return LRA_ERR_INVALID_ARG;
   if (!(par->h >= 1.0) || !(par->h < 1e300)) return LRA_ERR_INVALID_ARG;
   if (!(par->rank_tol >= 0.0) || !(par->rank_tol < 1.0)) return LRA_ERR_INVALID_ARG;
-  if (par->mode != LRA_MODE_FP64) return LRA_ERR_INVALID_ARG;
+  if (par->mode != LRA_MODE_FP64 && par->mode != LRA_MODE_MIXED) return LRA_ERR_INVALID_ARG;
   return LRA_OK;
 }
 
@@ -66,6 +68,9 @@ static lra_status make_plan(const DevProblem& P, const lra_ca_params* par, CaPla
   const int64_t maxlen = std::max(P.m, P.n);
   int nblk = (int)std::min<int64_t>((maxlen + MIN_COLS_PER_CTA - 1) / MIN_COLS_PER_CTA, dev.sms);
   nblk = std::max(nblk, 1);
+  // mixed mode runs its certified FP32 steps on one CTA: take the single-CTA plan
+  // for strips up to MIXED_SOLO_MAX columns (larger runs stay on the FP64 grid)
+  if (par->mode == LRA_MODE_MIXED && P.src != LRA_KERNEL_GAUSSIAN && maxlen <= MIXED_SOLO_MAX) nblk = 1;
   const size_t budget = dev.smem_optin - STATIC_SMEM_RESERVE;
   for (;;) {
     const int cn = (int)((P.n + nblk - 1) / nblk);
@@ -98,6 +103,10 @@ static lra_status make_plan(const DevProblem& P, const lra_ca_params* par, CaPla
   pl->off_slots = o; o = align_up(o + sizeof(double) * 2 * (size_t)pl->nblk * SLOT, 256);
   pl->off_strip = o;
   if (!pl->strip_in_smem) o = align_up(o + sizeof(double) * (size_t)pl->nblk * k * pl->ldm, 256);
+  // mixed mode: single-CTA runs of dense or Laplace inputs (Laplace needs FP32 points)
+  pl->mixed = (par->mode == LRA_MODE_MIXED && pl->nblk == 1 && P.src != LRA_KERNEL_GAUSSIAN) ? 1 : 0;
+  pl->off_pts = o;
+  if (pl->mixed && P.src == LRA_KERNEL_LAPLACE) o = align_up(o + sizeof(float) * 3 * (size_t)(P.m + P.n), 256);
   pl->bytes = o;
   return LRA_OK;
 }
@@ -157,16 +166,24 @@ lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_mul
   A.chunk_m = pl.chunk_m;
   A.ldm = pl.ldm;
   A.strip_in_smem = pl.strip_in_smem;
+  A.mixed = pl.mixed;
+  if (pl.mixed && P.src == LRA_KERNEL_LAPLACE) {
+    float* X32 = reinterpret_cast<float*>(ws + pl.off_pts);
+    A.P.X32 = X32;
+    A.P.Y32 = X32 + 3 * P.m;
+    if ((st = points_to_f32(P.X, P.m, X32, stream)) != LRA_OK) return st;
+    if ((st = points_to_f32(P.Y, P.n, X32 + 3 * P.m, stream)) != LRA_OK) return st;
+  }
 
   // exchange tags and the abort word start at zero in every run
   LRA_CUDA_TRY(cudaMemsetAsync(ws + pl.off_hdr, 0, 256, stream));
   if (pl.nblk > 1) LRA_CUDA_TRY(cudaMemsetAsync(ws + pl.off_slots, 0, pl.off_strip - pl.off_slots, stream));
 
   if (pl.nblk == 1) {
-    LRA_CUDA_TRY(cudaFuncSetAttribute(ca_kernel<SoloGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)pl.smem));
+    auto kern = pl.mixed ? ca_kernel<SoloGroup, true> : ca_kernel<SoloGroup, false>;
+    LRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem));
     LaunchScope ls(stream, "ca_kernel");
-    ca_kernel<SoloGroup><<<1, NT, pl.smem, stream>>>(A, SoloGroup{});
+    kern<<<1, NT, pl.smem, stream>>>(A, SoloGroup{});
     LRA_CUDA_TRY(cudaGetLastError());
   } else {
     GridGroup grp;

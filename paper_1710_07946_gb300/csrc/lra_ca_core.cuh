@@ -41,7 +41,10 @@ struct CaArgs {
   double* gstrip;      // global chunks when not in shared memory (nblk * k * ldm)
   int32_t chunk_n, chunk_m, ldm;
   int32_t strip_in_smem;
+  int32_t mixed;       // try the FP32 certified step first (single-CTA groups)
 };
+
+struct Cert;           // lra_mixed.cuh
 
 // Shared-memory layout of the C-A kernels (all offsets in bytes, 16-aligned).
 struct CaSmem {
@@ -61,6 +64,8 @@ struct CaSmem {
   double* bc;        // 4 doubles of broadcast scratch
   int32_t* ctl;      // small control words
   CandRed* red;      // block reduction scratch
+  int32_t* Jsave;    // KMAX : selected set on entry of a mixed step
+  Cert* cert;        // 33 : certificate reduction scratch
   ExchangeOut xo;    // where an exchange leaves its result
   double* M;         // the chunk (k x ldm), shared or global
 };
@@ -82,6 +87,8 @@ __host__ __device__ inline size_t ca_smem_fixed(int k, int ldm) {
   b += align16(sizeof(double) * 4);
   b += align16(sizeof(int32_t) * 8);
   b += align16(sizeof(CandRed));
+  b += align16(sizeof(int32_t) * KMAX);
+  b += align16(48 * 33);
   return b;
 }
 
@@ -104,6 +111,8 @@ __device__ inline CaSmem ca_smem_carve(unsigned char* base, int k, int ldm, doub
   S.bc = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * 4);
   S.ctl = reinterpret_cast<int32_t*>(base + o); o += align16(sizeof(int32_t) * 8);
   S.red = reinterpret_cast<CandRed*>(base + o); o += align16(sizeof(CandRed));
+  S.Jsave = reinterpret_cast<int32_t*>(base + o); o += align16(sizeof(int32_t) * KMAX);
+  S.cert = reinterpret_cast<Cert*>(base + o); o += align16(48 * 33);
   S.xo = ExchangeOut{S.win, S.x, S.flags, &S.ctl[6], S.red};
   S.M = gchunk ? gchunk : reinterpret_cast<double*>(base + o);
   return S;
@@ -415,74 +424,6 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
   res.nswaps = nsw;
   res.logdet = L.sum;
   return res;
-}
-
-// The whole C-A loop for one problem, then the outputs C, R, I, J, G, logvol.
-template <class Group>
-__device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
-  const DevProblem& P = A.P;
-  const int k = A.k, tid = threadIdx.x, nt = blockDim.x;
-  const bool lead = grp.rank() == 0;
-  // initial rows; every CTA validates them identically
-  if (tid == 0) {
-    int bad = 0;
-    for (int a = 0; a < k; ++a) {
-      int32_t v = A.I0[a];
-      S.Is[a] = v;
-      if (v < 0 || v >= P.m) bad = 1;
-      for (int b = 0; b < a; ++b) if (S.Is[b] == v) bad = 1;
-    }
-    S.ctl[4] = bad;
-  }
-  if (lead) for (int s = tid; s < 2 * A.sweeps; s += nt) A.logvol[s] = __longlong_as_double(0x7ff8000000000000ll);
-  __syncthreads();
-  if (S.ctl[4]) {
-    if (lead && tid == 0) { A.info[0] = 0; A.info[1] = 0; A.info[2] = 0; A.info[3] = LRA_ERR_INVALID_ARG; }
-    return;
-  }
-  unsigned long long seq = 0;
-  int status = LRA_OK, err = LRA_OK, total = 0, loops = 0;
-  for (int s = 0; s < A.sweeps; ++s) {
-    StepResult r0 = maxvol_step(grp, A, S, 0, s == 0, S.Js, seq, lead);
-    if (r0.status != LRA_OK && r0.status < 16) { err = r0.status; break; }
-    if (r0.status > status) status = r0.status;
-    __syncthreads();
-    StepResult r1 = maxvol_step(grp, A, S, 1, false, S.Is, seq, lead);
-    if (r1.status != LRA_OK && r1.status < 16) { err = r1.status; break; }
-    if (r1.status > status) status = r1.status;
-    if (lead && tid == 0) { A.logvol[2 * s] = r0.logdet; A.logvol[2 * s + 1] = r1.logdet; }
-    total += r0.nswaps + r1.nswaps;
-    loops = s + 1;
-    __syncthreads();
-    if (s > 0 && r0.nswaps == 0 && r1.nswaps == 0) break;
-  }
-  if (err != LRA_OK) {
-    if (lead && tid == 0) { A.info[0] = 0; A.info[1] = total; A.info[2] = loops; A.info[3] = err; }
-    return;
-  }
-  // outputs: C = W'[:, J] over this CTA's rows, R = W[I, :] over its columns
-  {
-    const int64_t r0 = (int64_t)grp.rank() * A.chunk_m;
-    const int rn = (int)max((int64_t)0, min((int64_t)A.chunk_m, P.m - r0));
-    for (int it = tid; it < rn * k; it += nt) {
-      int c = it / k, a = it - c * k;
-      A.C[(r0 + c) * k + a] = wp_entry(P, r0 + c, S.Js[a]);
-    }
-    const int64_t c0 = (int64_t)grp.rank() * A.chunk_n;
-    const int cn = (int)max((int64_t)0, min((int64_t)A.chunk_n, P.n - c0));
-    for (int it = tid; it < k * cn; it += nt) {
-      int a = it / cn, c = it - a * cn;
-      A.R[(int64_t)a * P.n + c0 + c] = w_entry(P, S.Is[a], c0 + c);
-    }
-  }
-  if (lead) {
-    for (int it = tid; it < k * k; it += nt) {
-      int a = it / k, b = it - a * k;
-      A.G[it] = wp_entry(P, S.Is[a], S.Js[b]);
-    }
-    for (int a = tid; a < k; a += nt) { A.I[a] = S.Is[a]; A.J[a] = S.Js[a]; }
-    if (tid == 0) { A.info[0] = 0; A.info[1] = total; A.info[2] = loops; A.info[3] = status; }
-  }
 }
 
 }  // namespace lra

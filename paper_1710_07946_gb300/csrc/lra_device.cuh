@@ -42,6 +42,11 @@ struct DevProblem {
   const int32_t* perm;       // ARHT permutation, or sparse rows (n*nnz)
   const int8_t* sign;        // ARHT diagonal, or sparse signs (n*nnz)
   double mscale;             // 2^{-d/2} or 1/sqrt(nnz), computed on the host
+  // FP32 copies for the mixed-precision steps
+  const float* X32;          // kernel points rounded to FP32 (m x 3), or null
+  const float* Y32;          // (n x 3), or null
+  float mscale32;            // mscale rounded to FP32
+  float mscale_err;          // bound on |mscale32 - exact scale|
 };
 
 // w_ij of the original input (no multiplier).

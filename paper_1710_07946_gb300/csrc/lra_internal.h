@@ -32,6 +32,9 @@ inline lra_status cuda_status(cudaError_t e) { return e == cudaSuccess ? LRA_OK 
 // Validate a problem (and an optional multiplier) and fill the device view.
 lra_status make_dev_problem(const lra_problem* p, lra_multiplier mult, DevProblem* out);
 
+// Round the 3 x npts coordinates of X to FP32 into out (stream-ordered).
+lra_status points_to_f32(const double* X, int64_t npts, float* out, cudaStream_t stream);
+
 struct DeviceInfo {
   int device;
   int sms;

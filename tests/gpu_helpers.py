@@ -30,7 +30,8 @@ def gpu_ca(p: li.Problem, k, sweeps, I0, **kw):
     torch.cuda.synchronize()
     res = {key: v.cpu().numpy() for key, v in out.items() if not key.startswith("_")}
     info = res.pop("info")
-    res.update(rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]), status=int(info[3]))
+    res.update(rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]), status=int(info[3]),
+               fp32_steps=int(info[4]), fp64_steps=int(info[5]))
     return res
 
 

@@ -29,7 +29,7 @@ def _outputs(m, n, k, sweeps, dev):
                 U=torch.empty(k, k, dtype=torch.float64, device=dev),
                 R=torch.empty(k, n, dtype=torch.float64, device=dev),
                 logvol=torch.empty(2 * sweeps, dtype=torch.float64, device=dev),
-                info=torch.empty(4, dtype=torch.int32, device=dev))
+                info=torch.empty(8, dtype=torch.int32, device=dev))
 
 
 def _compare(ref, got):
