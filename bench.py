@@ -42,6 +42,7 @@ sys.path.insert(0, ROOT)
 import lra_inputs as li  # noqa: E402
 
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal; a plain DFMA loop measured 1.2)
+FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (nominal; a plain FFMA loop measured 74)
 METRIC = "CUR LRAs/s at rel. err <= 1e-6 (FP64 pivots and nucleus)"
 ERR_BOUND = 1e-6
 LAPLACE_FLOPS = 8.0       # 3 sub, 1 mul, 2 fma, sqrt, div per kernel entry (nominal count)
@@ -264,6 +265,102 @@ class DenseWorkload:
         return n, n, el, f"{n} complete LRAs of the same input (C-A + nucleus + residual sample)"
 
 
+class GaussApplyWorkload:
+    """Differentiable CUR apply: 256 Gaussian-kernel blocks exp(-|x-y|^2/(2 l^2)), l = 0.3, 1024 x 1024 each
+    (targets in [0,1]^3, sources in [2,3]x[0,1]^2), pivots of rank 32 from a batched C-A run (untimed set-up);
+    one step = forward y = C U R x and the hand-written backward (dx, dl) for nrhs FP32 right-hand sides."""
+    kernel = "gauss_bwd_kernel"
+    unit = "blocks/s"
+    peak_name = "fp32"
+
+    def __init__(self, nblk=256, size=1024, k=32, nrhs=64):
+        self.nblk, self.size, self.k, self.nrhs = nblk, size, k, nrhs
+        self.name = f"gauss_apply_{nblk}blocks_{size}_k{k}_nrhs{nrhs}_fwd_bwd"
+
+    def host(self, rank):
+        X, Y, ell = li.gaussian_blocks(nblk=self.nblk, size=self.size, ell=0.3, seed=rank)
+        g = np.random.default_rng(50 + rank)
+        x = g.standard_normal((self.nblk, self.size, self.nrhs)).astype(np.float32)
+        dy = g.standard_normal((self.nblk, self.size, self.nrhs)).astype(np.float32)
+        return dict(X=X, Y=Y, ell=ell, x=x, dy=dy)
+
+    def config(self, h):
+        return {"workload": self.name, "blocks": self.nblk, "block": f"{self.size}x{self.size}", "k": self.k,
+                "nrhs": self.nrhs, "kernel": "Gaussian l=0.3, entries on the fly in FP32, core inverse FP64",
+                "pivots": "batched C-A (FP64), untimed set-up"}
+
+    def device(self, h, dev):
+        import torch
+        import paper_1710_07946_gb300 as lra
+        nb, sz, k = self.nblk, self.size, self.k
+        Xall = torch.from_numpy(np.ascontiguousarray(h["X"].reshape(-1, 3))).to(dev)
+        Yall = torch.from_numpy(np.ascontiguousarray(h["Y"].reshape(-1, 3))).to(dev)
+        prob = lra.Problem.kernel("gaussian", Xall, Yall, h["ell"])
+        blocks = np.array([[b * sz, sz, b * sz, sz] for b in range(nb)], dtype=np.int64)
+        bt = lra.Batch(prob, blocks, k, 3, li.block_initial_rows(blocks, k, 3), rank_tol=1e-13)
+        lra.lra_ca_run_batched(bt)
+        torch.cuda.synchronize()
+        d = dict(X=Xall.view(nb, sz, 3), Y=Yall.view(nb, sz, 3), I=bt.out["I"].contiguous(),
+                 J=bt.out["J"].contiguous(), ell=h["ell"], x=torch.from_numpy(h["x"]).to(dev),
+                 dy=torch.from_numpy(h["dy"]).to(dev))
+        d["pivots"] = (d["I"].cpu().numpy(), d["J"].cpu().numpy())
+        return d
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        y, ctx = lra.lra_gauss_cur_forward(d["X"], d["Y"], d["I"], d["J"], d["ell"], d["x"])
+        g = lra.lra_gauss_cur_backward(d["X"], d["Y"], d["I"], d["J"], d["ell"], d["x"], d["dy"], ctx)
+        d["y"], d["dx"], d["dell"] = y, g["dx"], g["dell"]
+
+    def check(self, d):
+        ok = bool(np.isfinite(d["dell"].cpu().numpy()).all())
+        return dict(units=self.nblk if ok else 0, dell=float(d["dell"].sum().item()))
+
+    def flops(self, h, res):
+        """FP32 flops per backward launch: entries (exp, distance: ~12 flops) and the fused products."""
+        m = n = self.size
+        k, r = self.k, self.nrhs
+        per_block = (m * k + k * n) * (12 + 2 * r) + 2 * (m * k * r + k * n * r)
+        return float(self.nblk * per_block)
+
+    def extra(self, res):
+        return {"dl_sum": res["dell"]}
+
+    def e2e_setup(self, h, d):
+        import torch
+        hp = dict(x=torch.from_numpy(h["x"]).pin_memory(), dy=torch.from_numpy(h["dy"]).pin_memory())
+        hp["dx"] = torch.empty(d["x"].shape, dtype=torch.float32).pin_memory()
+        hp["y"] = torch.empty((self.nblk, self.size, self.nrhs), dtype=torch.float32).pin_memory()
+        hp["dell"] = torch.empty(self.nblk, dtype=torch.float64).pin_memory()
+        h2d = 2 * hp["x"].numel() * 4
+        d2h = 2 * hp["dx"].numel() * 4 + self.nblk * 8
+        return hp, h2d, d2h
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["x"].copy_(hp["x"], non_blocking=True)
+        d["dy"].copy_(hp["dy"], non_blocking=True)
+        self.step(d)
+        hp["y"].copy_(d["y"], non_blocking=True)
+        hp["dx"].copy_(d["dx"], non_blocking=True)
+        hp["dell"].copy_(d["dell"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        I, J = self._host_pivots
+        t0 = time.perf_counter()
+        n = 0
+        for b in np.random.default_rng(seed).permutation(self.nblk):
+            oracle.gauss_cur_backward(h["X"][b], h["Y"][b], I[b], J[b], h["ell"], h["x"][b].astype(np.float64),
+                                      h["dy"][b].astype(np.float64))
+            n += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        el = time.perf_counter() - t0
+        return n, n, el, f"{n} blocks of the same batch (FP64 forward + backward each)"
+
+
 class FmmSmallWorkload(FmmWorkload):
     """The same recipe on 2^17 points and 512 block pairs (profiling size)."""
     name = "fmm_laplace_128K_octree_512blocks_k64_tol1e-6"
@@ -275,6 +372,7 @@ class FmmSmallWorkload(FmmWorkload):
 WORKLOADS = {
     "fmm": FmmWorkload,
     "fmm_small": FmmSmallWorkload,
+    "gauss_apply": GaussApplyWorkload,
     "dense8192_arht": lambda: DenseWorkload("arht"),
     "dense8192_sparse": lambda: DenseWorkload("sparse"),
 }
@@ -416,6 +514,8 @@ def run_lib(args, wl):
 
     h = wl.host(rank)
     d = wl.device(h, dev)
+    if "pivots" in d:
+        wl._host_pivots = d["pivots"]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MiB > L2
     warm = max(args.warmup, 3)
     for _ in range(warm):
@@ -507,6 +607,11 @@ def run_lib(args, wl):
         kavg = kms / max(kn, 1) / 1e3
         flops = wl.flops(h, res)
         achieved = flops / kavg / 1e12
+        fp32 = getattr(wl, "peak_name", "fp64") == "fp32"
+        peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+        peak_src = ("FP32 pipe: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz = 80.5 TFLOP/s nominal (a plain FFMA loop "
+                    "measured 74)") if fp32 else ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26, nominal "
+                                                 "1.25 TFLOP/s (not in MEASURED_PEAKS.json; a plain DFMA loop measured 1.2)")
         peaks = load_peaks()
         cfg = dict(wl.config(h), l2="flushed before every step (256 MiB write, untimed)",
                    parallelism=f"{world} independent problem(s), one per GPU", mode="fp64",
@@ -515,12 +620,12 @@ def run_lib(args, wl):
         line = {
             "metric": METRIC, "value": value, "unit": wl.unit, "n_gpus": world, "steps": args.steps,
             "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
-            "roofline": {"bound": "alu", "kernel": wl.kernel, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
+            "config": cfg,
+            "roofline": {"bound": "alu", "kernel": wl.kernel, "achieved": achieved, "peak": peak,
+                         "unit": "TFLOP/s", "frac": achieved / peak,
                          "traffic": ncu_traffic(wl.kernel, wl.name),
-                         "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26, nominal 1.25 "
-                                        "TFLOP/s (not in MEASURED_PEAKS.json; a plain DFMA loop measured 1.2)",
+                         "peak_source": peak_src,
                          "flops_per_launch": flops, "avg_launch_ms": kavg * 1e3,
                          "hbm_peak_gbs": peaks.get("hbm_gbs")},
             "kernels": {kname: {"ms_total": v[0], "launches": v[1]} for kname, v in prof.items()},

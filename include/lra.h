@@ -267,6 +267,51 @@ lra_status lra_residual_sample_batched(const lra_problem* base, const lra_batch*
                                        const lra_cur_batch* cur, const int32_t* Q, int32_t q, const int32_t* S,
                                        int32_t s, double* stats, lra_stream_t stream);
 
+/* ------------------------------------------------------------------------- */
+/* Differentiable CUR apply on Gaussian-kernel blocks (fixed pivots)          */
+/* ------------------------------------------------------------------------- */
+/* nb independent blocks of equal shape: block b has targets X[b] (m x 3) and
+ * sources Y[b] (n x 3), kernel K(x, y) = exp(-|x - y|^2 / (2 l^2)), and fixed
+ * pivots I[b] (k rows of X[b]) and J[b] (k rows of Y[b]), e.g. from
+ * lra_ca_run_batched.  All pointers device. */
+typedef struct {
+  const double* X;          /* nb x m x 3 */
+  const double* Y;          /* nb x n x 3 */
+  const int32_t* I;         /* nb x k, block-local */
+  const int32_t* J;         /* nb x k, block-local */
+  int32_t nb, m, n, k;      /* 1 <= k <= min(m, n, 64) */
+  double length_scale;      /* l > 0 */
+} lra_gauss_blocks;
+
+/*
+ * lra_gauss_cur_forward -- y[b] = C U R x[b] per block (paper: FMM stage (iii)
+ * product with the generators; the gradient machinery has no counterpart in the
+ * paper), with C = K(X, Y_J), R = K(X_I, Y), U = K(X_I, Y_J)^{-1} (FP64
+ * Gauss-Jordan with partial pivoting).  C and R are evaluated on the fly in FP32
+ * and never stored; R x is accumulated in FP32, U (R x) in FP64, C (U R x) in
+ * FP32.  x: nb x n x nrhs FP32, y: nb x m x nrhs FP32 (1 <= nrhs <= 256).
+ * ctx: nb x (k*k + 2*k*nrhs) FP64 written for the backward (U, R x, U R x).
+ * A singular core gives NaN outputs for its block.  Errors: LRA_ERR_INVALID_ARG,
+ * LRA_ERR_CUDA.
+ */
+lra_status lra_gauss_cur_forward(const lra_gauss_blocks* g, const float* x, int32_t nrhs, float* y, double* ctx,
+                                 lra_stream_t stream);
+
+/*
+ * lra_gauss_cur_backward -- gradients of a scalar loss through y = C U R x at
+ * fixed pivots, given dy = dL/dy (nb x m x nrhs FP32) and the forward's ctx:
+ *   dx = R^T U^T C^T dy (nb x n x nrhs FP32);
+ *   dell[b] = dL/dl of block b (FP64; the entries of C, R and the core all depend
+ *             on l through dK/dl = K |x - y|^2 / l^3);
+ *   optional (may be NULL): dC = dy (U R x)^T (nb x m x k), dR = U^T C^T dy x^T
+ *   (nb x k x n), dG = -U^T C^T dy (U R x)^T (nb x k x k), the gradients with
+ *   respect to the sampled kernel entries (FP32).
+ * Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
+ */
+lra_status lra_gauss_cur_backward(const lra_gauss_blocks* g, const float* x, const float* dy, int32_t nrhs,
+                                  const double* ctx, float* dx, double* dell, float* dC, float* dR, float* dG,
+                                  lra_stream_t stream);
+
 /*
  * lra_cur_apply -- Y = C (U (R X)) for one CUR triple (paper: FMM / HSS stage
  * (iii), multiplication with the generators of the neutered block columns).

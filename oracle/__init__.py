@@ -52,6 +52,8 @@ def lib():
         L.orc_hadamard_abridged.argtypes = [i64, i32, vp]
         L.orc_multiplier_dense.argtypes = [P, vp]
         L.orc_jacobi_svd.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.orc_gauss_cur_apply.argtypes = [vp, i64, vp, i64, vp, vp, i32, f64, vp, i32, vp, vp, vp, vp]
+        L.orc_gauss_cur_backward.argtypes = [vp, i64, vp, i64, vp, vp, i32, f64, vp, vp, i32, vp, vp, vp, vp, vp]
         L.orc_jacobi_svd.restype = ct.c_int
         _lib = L
     return _lib
@@ -246,3 +248,34 @@ def ca_run_blocks(p, blocks, k_max, sweeps, I0s, h=1.01, max_swaps=1000, rank_to
         k = min(k_max, int(nr), int(nc))
         out.append(ca_run(sub, k, sweeps, I0s[b][:k], h, max_swaps, rank_tol))
     return out
+
+
+def gauss_cur_apply(X, Y, I, J, ell, x):
+    """y = C U R x with C = K(X, Y_J), R = K(X_I, Y), U = K(X_I, Y_J)^{-1},
+    K(x, y) = exp(-|x - y|^2 / (2 ell^2)) (FMM stage (iii) product on a
+    Gaussian block with fixed pivots).  Returns (y, U, t1 = R x, t2 = U t1)."""
+    X = np.ascontiguousarray(X, dtype=np.float64); Y = np.ascontiguousarray(Y, dtype=np.float64)
+    I = np.ascontiguousarray(I, dtype=np.int32); J = np.ascontiguousarray(J, dtype=np.int32)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    if x.ndim == 1:
+        x = x[:, None]
+    m, n, k, nrhs = len(X), len(Y), len(I), x.shape[1]
+    y = np.empty((m, nrhs)); U = np.empty((k, k)); t1 = np.empty((k, nrhs)); t2 = np.empty((k, nrhs))
+    lib().orc_gauss_cur_apply(_ptr(X), m, _ptr(Y), n, _ptr(I), _ptr(J), k, float(ell), _ptr(x), nrhs, _ptr(y),
+                              _ptr(U), _ptr(t1), _ptr(t2))
+    return y, U, t1, t2
+
+
+def gauss_cur_backward(X, Y, I, J, ell, x, dy):
+    """Backward of gauss_cur_apply at fixed pivots: returns dict(dx, dC, dR, dG, dell)."""
+    X = np.ascontiguousarray(X, dtype=np.float64); Y = np.ascontiguousarray(Y, dtype=np.float64)
+    I = np.ascontiguousarray(I, dtype=np.int32); J = np.ascontiguousarray(J, dtype=np.int32)
+    x = np.ascontiguousarray(x, dtype=np.float64); dy = np.ascontiguousarray(dy, dtype=np.float64)
+    if x.ndim == 1:
+        x, dy = x[:, None], dy[:, None]
+    m, n, k, nrhs = len(X), len(Y), len(I), x.shape[1]
+    dx = np.empty((n, nrhs)); dC = np.empty((m, k)); dR = np.empty((k, n)); dG = np.empty((k, k))
+    dl = ct.c_double()
+    lib().orc_gauss_cur_backward(_ptr(X), m, _ptr(Y), n, _ptr(I), _ptr(J), k, float(ell), _ptr(x), _ptr(dy), nrhs,
+                                 _ptr(dx), _ptr(dC), _ptr(dR), _ptr(dG), ct.byref(dl))
+    return dict(dx=dx, dC=dC, dR=dR, dG=dG, dell=dl.value)

@@ -688,3 +688,113 @@ int orc_jacobi_svd(const double* A, int32_t m, int32_t n, double* Uo, double* s,
   free(B);
   return sweep;
 }
+
+/* ------------------------------------------------------------------ */
+/* Differentiable CUR apply with a Gaussian kernel (no counterpart in   */
+/* the paper; the FMM stage (iii) product y = C U R x with C, R and the */
+/* core G = W[I,J] sampled from K(x, y) = exp(-|x - y|^2 / (2 l^2)) at  */
+/* fixed pivots, U = G^{-1})                                            */
+/* ------------------------------------------------------------------ */
+static double gauss_k(const double* x, const double* y, double ell, double* d2out) {
+  double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+  double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+  if (d2out) *d2out = r2;
+  return exp(-(r2 / (2.0 * ell * ell)));
+}
+
+/* y = C U R x for one block: X (m x 3), Y (n x 3), pivots I (k rows of X),
+ * J (k rows of Y), x (n x nrhs), y (m x nrhs); U = G^{-1} by orc_nucleus with
+ * tolerance 0 (G is assumed nonsingular).  t1 = R x and t2 = U t1 (k x nrhs)
+ * are returned for the backward when non-NULL. */
+void orc_gauss_cur_apply(const double* X, int64_t m, const double* Y, int64_t n, const int32_t* I, const int32_t* J,
+                         int32_t k, double ell, const double* x, int32_t nrhs, double* y, double* Uout, double* t1o,
+                         double* t2o) {
+  double* G = (double*)malloc(sizeof(double) * (size_t)k * k);
+  double* U = (double*)malloc(sizeof(double) * (size_t)k * k);
+  double* t1 = (double*)calloc((size_t)k * nrhs, sizeof(double));
+  double* t2 = (double*)calloc((size_t)k * nrhs, sizeof(double));
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t b = 0; b < k; ++b) G[a * k + b] = gauss_k(X + 3 * (int64_t)I[a], Y + 3 * (int64_t)J[b], ell, NULL);
+  orc_nucleus(G, k, 0.0, U);
+  for (int32_t a = 0; a < k; ++a)
+    for (int64_t j = 0; j < n; ++j) {
+      double r = gauss_k(X + 3 * (int64_t)I[a], Y + 3 * j, ell, NULL);
+      for (int32_t c = 0; c < nrhs; ++c) t1[a * nrhs + c] = fma(r, x[j * nrhs + c], t1[a * nrhs + c]);
+    }
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t c = 0; c < nrhs; ++c) {
+      double s = 0.0;
+      for (int32_t b = 0; b < k; ++b) s = fma(U[a * k + b], t1[b * nrhs + c], s);
+      t2[a * nrhs + c] = s;
+    }
+  for (int64_t i = 0; i < m; ++i)
+    for (int32_t c = 0; c < nrhs; ++c) y[i * nrhs + c] = 0.0;
+  for (int64_t i = 0; i < m; ++i)
+    for (int32_t a = 0; a < k; ++a) {
+      double cv = gauss_k(X + 3 * i, Y + 3 * (int64_t)J[a], ell, NULL);
+      for (int32_t c = 0; c < nrhs; ++c) y[i * nrhs + c] = fma(cv, t2[a * nrhs + c], y[i * nrhs + c]);
+    }
+  if (Uout) memcpy(Uout, U, sizeof(double) * (size_t)k * k);
+  if (t1o) memcpy(t1o, t1, sizeof(double) * (size_t)k * nrhs);
+  if (t2o) memcpy(t2o, t2, sizeof(double) * (size_t)k * nrhs);
+  free(G); free(U); free(t1); free(t2);
+}
+
+/* Backward of y = C U R x at fixed pivots, given dy = dL/dy (m x nrhs):
+ *   s1 = C^T dy, s2 = U^T s1, dx = R^T s2,
+ *   dC = dy t2^T (m x k), dR = s2 x^T (k x n), dG = -s2 t2^T (k x k)  (U = G^{-1}),
+ *   dl = sum of dC, dR, dG against dK/dl = K |x - y|^2 / l^3 over their entries.
+ * Any of dC, dR, dG may be NULL. */
+void orc_gauss_cur_backward(const double* X, int64_t m, const double* Y, int64_t n, const int32_t* I,
+                            const int32_t* J, int32_t k, double ell, const double* x, const double* dy, int32_t nrhs,
+                            double* dx, double* dC, double* dR, double* dG, double* dell) {
+  double* U = (double*)malloc(sizeof(double) * (size_t)k * k);
+  double* t1 = (double*)malloc(sizeof(double) * (size_t)k * nrhs);
+  double* t2 = (double*)malloc(sizeof(double) * (size_t)k * nrhs);
+  double* yv = (double*)malloc(sizeof(double) * (size_t)m * nrhs);
+  double* s1 = (double*)calloc((size_t)k * nrhs, sizeof(double));
+  double* s2 = (double*)calloc((size_t)k * nrhs, sizeof(double));
+  orc_gauss_cur_apply(X, m, Y, n, I, J, k, ell, x, nrhs, yv, U, t1, t2);
+  const double l3 = ell * ell * ell;
+  double dl = 0.0;
+  for (int64_t i = 0; i < m; ++i)
+    for (int32_t a = 0; a < k; ++a) {
+      double d2, cv = gauss_k(X + 3 * i, Y + 3 * (int64_t)J[a], ell, &d2);
+      double g = 0.0;
+      for (int32_t c = 0; c < nrhs; ++c) {
+        s1[a * nrhs + c] = fma(cv, dy[i * nrhs + c], s1[a * nrhs + c]);
+        g = fma(dy[i * nrhs + c], t2[a * nrhs + c], g);
+      }
+      if (dC) dC[i * k + a] = g;
+      dl = fma(g, cv * d2 / l3, dl);
+    }
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t c = 0; c < nrhs; ++c) {
+      double s = 0.0;
+      for (int32_t b = 0; b < k; ++b) s = fma(U[b * k + a], s1[b * nrhs + c], s);
+      s2[a * nrhs + c] = s;
+    }
+  for (int64_t j = 0; j < n; ++j)
+    for (int32_t c = 0; c < nrhs; ++c) dx[j * nrhs + c] = 0.0;
+  for (int32_t a = 0; a < k; ++a)
+    for (int64_t j = 0; j < n; ++j) {
+      double d2, r = gauss_k(X + 3 * (int64_t)I[a], Y + 3 * j, ell, &d2);
+      double g = 0.0;
+      for (int32_t c = 0; c < nrhs; ++c) {
+        dx[j * nrhs + c] = fma(r, s2[a * nrhs + c], dx[j * nrhs + c]);
+        g = fma(s2[a * nrhs + c], x[j * nrhs + c], g);
+      }
+      if (dR) dR[(int64_t)a * n + j] = g;
+      dl = fma(g, r * d2 / l3, dl);
+    }
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t b = 0; b < k; ++b) {
+      double d2, gv = gauss_k(X + 3 * (int64_t)I[a], Y + 3 * (int64_t)J[b], ell, &d2);
+      double g = 0.0;
+      for (int32_t c = 0; c < nrhs; ++c) g = fma(-s2[a * nrhs + c], t2[b * nrhs + c], g);
+      if (dG) dG[a * k + b] = g;
+      dl = fma(g, gv * d2 / l3, dl);
+    }
+  *dell = dl;
+  free(U); free(t1); free(t2); free(yv); free(s1); free(s2);
+}

@@ -24,6 +24,7 @@ __all__ = [
     "lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run", "lra_cur_apply",
     "lra_residual_sample", "lra_version", "library_path", "lra_launch_count", "lra_profile_enable",
     "lra_profile_collect", "lra_ca_run_noalloc", "Batch", "lra_ca_run_batched", "lra_residual_sample_batched",
+    "lra_gauss_cur_forward", "lra_gauss_cur_backward", "GaussCurApply", "gauss_cur_apply",
 ]
 
 LRA_OK, LRA_ERR_INVALID_ARG, LRA_ERR_CUDA, LRA_ERR_NONFINITE, LRA_ERR_TIMEOUT, LRA_ERR_WORKSPACE = 0, 1, 2, 3, 4, 5
@@ -65,6 +66,12 @@ class _CurBatch(ct.Structure):
                 ("R", ct.c_void_p), ("logvol", ct.c_void_p), ("info", ct.c_void_p)]
 
 
+class _Gauss(ct.Structure):
+    _fields_ = [("X", ct.c_void_p), ("Y", ct.c_void_p), ("I", ct.c_void_p), ("J", ct.c_void_p),
+                ("nb", ct.c_int32), ("m", ct.c_int32), ("n", ct.c_int32), ("k", ct.c_int32),
+                ("length_scale", ct.c_double)]
+
+
 class _Cur(ct.Structure):
     _fields_ = [("I", ct.c_void_p), ("J", ct.c_void_p), ("C", ct.c_void_p), ("U", ct.c_void_p),
                 ("R", ct.c_void_p), ("logvol", ct.c_void_p), ("info", ct.c_void_p)]
@@ -99,6 +106,9 @@ def _load():
     L.lra_ca_batched_workspace_size.argtypes = [P, PB, PP, ct.POINTER(sz)]
     L.lra_ca_run_batched.argtypes = [P, PB, PP, vp, PCB, vp, sz, vp]
     L.lra_residual_sample_batched.argtypes = [P, PB, i32, PCB, vp, i32, vp, i32, vp, vp]
+    PG = ct.POINTER(_Gauss)
+    L.lra_gauss_cur_forward.argtypes = [PG, vp, i32, vp, vp, vp]
+    L.lra_gauss_cur_backward.argtypes = [PG, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
     L.lra_version.restype = ct.c_char_p
     L.lra_launch_count.restype = ct.c_int64
     L.lra_profile_enable.argtypes = [i32]
@@ -107,7 +117,8 @@ def _load():
               "lra_ca_run_noalloc",
               "lra_cur_apply", "lra_cur_apply_workspace_size", "lra_residual_sample",
               "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect",
-              "lra_ca_batched_workspace_size", "lra_ca_run_batched", "lra_residual_sample_batched"):
+              "lra_ca_batched_workspace_size", "lra_ca_run_batched", "lra_residual_sample_batched",
+              "lra_gauss_cur_forward", "lra_gauss_cur_backward"):
         getattr(L, f).restype = ct.c_int
     _lib = L
     return L
@@ -434,3 +445,77 @@ def lra_residual_sample_batched(batch: Batch, Q: torch.Tensor, S: torch.Tensor, 
                                          _dev(S, torch.int32, "S").data_ptr(), S.shape[1], stats.data_ptr(),
                                          _stream(stream)), "lra_residual_sample_batched")
     return stats
+
+
+def _gauss_struct(X, Y, I, J, ell):
+    for t, nm, dt in ((X, "X", torch.float64), (Y, "Y", torch.float64), (I, "I", torch.int32), (J, "J", torch.int32)):
+        _dev(t, dt, nm)
+    g = _Gauss()
+    g.X, g.Y, g.I, g.J = X.data_ptr(), Y.data_ptr(), I.data_ptr(), J.data_ptr()
+    g.nb, g.m, g.n, g.k = X.shape[0], X.shape[1], Y.shape[1], I.shape[1]
+    g.length_scale = float(ell)
+    return g
+
+
+def lra_gauss_cur_forward(X, Y, I, J, ell, x, stream=None):
+    """y[b] = C U R x[b] on Gaussian blocks at fixed pivots.  X (nb, m, 3), Y (nb, n, 3)
+    float64; I, J (nb, k) int32; x (nb, n, nrhs) float32.  Returns (y, ctx)."""
+    L = _load()
+    g = _gauss_struct(X, Y, I, J, ell)
+    _dev(x, torch.float32, "x")
+    nb, n, nrhs = x.shape
+    y = torch.empty(nb, g.m, nrhs, dtype=torch.float32, device=x.device)
+    ctx = torch.empty(nb, g.k * g.k + 2 * g.k * nrhs, dtype=torch.float64, device=x.device)
+    _check(L.lra_gauss_cur_forward(ct.byref(g), x.data_ptr(), nrhs, y.data_ptr(), ctx.data_ptr(), _stream(stream)),
+           "lra_gauss_cur_forward")
+    return y, ctx
+
+
+def lra_gauss_cur_backward(X, Y, I, J, ell, x, dy, ctx, entry_grads=False, stream=None):
+    """Backward of lra_gauss_cur_forward: returns dict(dx, dell (nb,) float64[, dC, dR, dG])."""
+    L = _load()
+    g = _gauss_struct(X, Y, I, J, ell)
+    _dev(x, torch.float32, "x"); _dev(dy, torch.float32, "dy"); _dev(ctx, torch.float64, "ctx")
+    nb, n, nrhs = x.shape
+    dx = torch.empty_like(x)
+    dell = torch.empty(nb, dtype=torch.float64, device=x.device)
+    out = dict(dx=dx, dell=dell)
+    ptrs = [None, None, None]
+    if entry_grads:
+        out["dC"] = torch.empty(nb, g.m, g.k, dtype=torch.float32, device=x.device)
+        out["dR"] = torch.empty(nb, g.k, g.n, dtype=torch.float32, device=x.device)
+        out["dG"] = torch.empty(nb, g.k, g.k, dtype=torch.float32, device=x.device)
+        ptrs = [out["dC"].data_ptr(), out["dR"].data_ptr(), out["dG"].data_ptr()]
+    _check(L.lra_gauss_cur_backward(ct.byref(g), x.data_ptr(), dy.data_ptr(), nrhs, ctx.data_ptr(), dx.data_ptr(),
+                                    dell.data_ptr(), ptrs[0], ptrs[1], ptrs[2], _stream(stream)),
+           "lra_gauss_cur_backward")
+    return out
+
+
+class GaussCurApply(torch.autograd.Function):
+    """y = C U R x on Gaussian-kernel blocks at fixed pivots, differentiable in x
+    and in the length scale ell (a 0-dim tensor); the forward and the hand-written
+    backward both run in the library's kernels."""
+
+    @staticmethod
+    def forward(ctx, x, ell, X, Y, I, J):
+        e = float(ell)
+        y, c = lra_gauss_cur_forward(X, Y, I, J, e, x.contiguous())
+        ctx.save_for_backward(x, X, Y, I, J, c)
+        ctx.ell = e
+        ctx.ell_meta = (ell.dtype, ell.device) if torch.is_tensor(ell) else None
+        return y
+
+    @staticmethod
+    def backward(ctx, dy):
+        x, X, Y, I, J, c = ctx.saved_tensors
+        g = lra_gauss_cur_backward(X, Y, I, J, ctx.ell, x, dy.contiguous().float(), c)
+        dell = None
+        if ctx.ell_meta is not None:
+            dell = g["dell"].sum().to(ctx.ell_meta[0])
+        return g["dx"], dell, None, None, None, None
+
+
+def gauss_cur_apply(x, ell, X, Y, I, J):
+    """Differentiable y = C U R x (see GaussCurApply)."""
+    return GaussCurApply.apply(x, ell, X, Y, I, J)

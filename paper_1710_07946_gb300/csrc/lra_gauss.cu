@@ -1,0 +1,421 @@
+// lra_gauss.cu -- differentiable CUR apply y = C U R x on Gaussian-kernel
+// blocks at fixed pivots (the FMM stage (iii) product of the generators, made
+// differentiable in x, in the sampled kernel entries and in the length scale).
+//
+// Per block: K(x, y) = exp(-|x - y|^2 / (2 l^2)), C = K(X, Y_J) (m x k),
+// R = K(X_I, Y) (k x n), G = K(X_I, Y_J), U = G^{-1}.  The entries of C and R are
+// evaluated on the fly in FP32 (never stored); G and U are FP64 (Gauss-Jordan
+// with partial pivoting); t1 = R x is accumulated in FP32, t2 = U t1 in FP64,
+// y = C t2 in FP32.  The backward recomputes the entries and fuses
+//   s1 = C^T dy, dC = dy t2^T, s2 = U^T s1, dx = R^T s2, dR = s2 x^T,
+//   dG = -s2 t2^T (U = G^{-1}), dl = sum over C, R, G of dK * K |x - y|^2 / l^3.
+// One CTA per block; the tiles of C and R live in shared memory only.
+#include <algorithm>
+#include <cstring>
+
+#include "lra_internal.h"
+#include "lra_profile.h"
+
+namespace lra {
+
+constexpr int GT = 256;          // threads per CTA
+constexpr int TILE = 64;         // rows (of C) or columns (of R) per tile
+
+struct GaussArgs {
+  const double* X;
+  const double* Y;
+  const int32_t* I;
+  const int32_t* J;
+  int32_t nb, m, n, k, nrhs;
+  double ell;
+  const float* x;
+  const float* dy;
+  float* y;
+  float* dx;
+  double* ctx;                   // per block: U (k*k), t1 (k*nrhs), t2 (k*nrhs)
+  double* dell;                  // per block
+  float* dC;
+  float* dR;
+  float* dG;
+};
+
+// Points are staged in shared memory as FP32 (hi, lo) pairs, x = hi + lo: the
+// difference (ph - qh) + (pl - ql) is then as accurate as the rounded FP64
+// difference, and the entry costs FP32 work only.
+struct P32 {
+  float h[3], l[3];
+};
+__device__ __forceinline__ P32 split_point(const double* p) {
+  P32 r;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    r.h[c] = __double2float_rn(p[c]);
+    r.l[c] = __double2float_rn(p[c] - (double)r.h[c]);
+  }
+  return r;
+}
+__device__ __forceinline__ float gk32s(const P32& p, const P32& q, float inv2l2, float* d2) {
+  const float dx = (p.h[0] - q.h[0]) + (p.l[0] - q.l[0]);
+  const float dy = (p.h[1] - q.h[1]) + (p.l[1] - q.l[1]);
+  const float dz = (p.h[2] - q.h[2]) + (p.l[2] - q.l[2]);
+  const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+  *d2 = r2;
+  return expf(-r2 * inv2l2);
+}
+
+__device__ __forceinline__ double gk64(const double* p, const double* q, double ell, double* d2) {
+  const double dx = p[0] - q[0], dy = p[1] - q[1], dz = p[2] - q[2];
+  const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+  *d2 = r2;
+  return exp(-(r2 / (2.0 * ell * ell)));
+}
+
+__device__ double block_sum_d(double v, double* red) {
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r += red[w];
+    red[32] = r;
+  }
+  __syncthreads();
+  const double r = red[32];
+  __syncthreads();
+  return r;
+}
+
+// U = G^{-1} (k x k, FP64) by Gauss-Jordan with partial pivoting on [G | I] in
+// shared memory A (k x 2k).  Returns 0 when a pivot is exactly zero.
+__device__ int gauss_jordan(double* A, int k, double* f, int* ctl) {
+  const int w2 = 2 * k, tid = threadIdx.x, nt = blockDim.x;
+  for (int t = 0; t < k; ++t) {
+    if (tid < 32) {
+      int best = -1;
+      double bv = -1.0;
+      for (int p = t + tid; p < k; p += 32) {
+        const double v = fabs(A[p * w2 + t]);
+        if (v > bv) { bv = v; best = p; }
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+        const int ob = __shfl_down_sync(0xffffffffu, best, off);
+        if (ov > bv || (ov == bv && ob >= 0 && (best < 0 || ob < best))) { bv = ov; best = ob; }
+      }
+      if (tid == 0) { ctl[0] = best; ctl[1] = (bv > 0.0); }
+    }
+    __syncthreads();
+    if (!ctl[1]) return 0;
+    const int r = ctl[0];
+    if (r != t)
+      for (int j = tid; j < w2; j += nt) {
+        const double tmp = A[t * w2 + j]; A[t * w2 + j] = A[r * w2 + j]; A[r * w2 + j] = tmp;
+      }
+    __syncthreads();
+    const double rp = 1.0 / A[t * w2 + t];
+    for (int p = tid; p < k; p += nt) f[p] = A[p * w2 + t];
+    __syncthreads();
+    for (int j = tid; j < w2; j += nt) A[t * w2 + j] = A[t * w2 + j] * rp;
+    __syncthreads();
+    for (int it = tid; it < k * w2; it += nt) {
+      const int p = it / w2, j = it - p * w2;
+      if (p != t) A[it] = fma(-f[p], A[t * w2 + j], A[it]);
+    }
+    __syncthreads();
+  }
+  return 1;
+}
+
+__global__ void __launch_bounds__(GT) gauss_fwd_kernel(GaussArgs g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int k = g.k, nrhs = g.nrhs, m = g.m, n = g.n, tid = threadIdx.x, nt = blockDim.x;
+  const int ldr = nrhs | 1;                                      // odd strides: no bank conflicts
+  const float inv2l2 = (float)(1.0 / (2.0 * g.ell * g.ell));
+  double* A = reinterpret_cast<double*>(smem);                  // k x 2k
+  double* f = A + (size_t)k * 2 * k;                            // KMAX
+  double* t1d = f + KMAX;                                       // k x nrhs
+  P32* pk = reinterpret_cast<P32*>(t1d + (size_t)k * nrhs);      // k pivot points (I, then J)
+  P32* pt = pk + KMAX;                                          // TILE tile points
+  float* tile = reinterpret_cast<float*>(pt + TILE);            // TILE x (k|1) entries
+  float* xt = tile + (size_t)TILE * (k | 1);                    // TILE x ldr
+  float* t2f = xt + (size_t)TILE * ldr;                         // k x ldr
+  const int ldk = k | 1;
+  __shared__ int ctl[4];
+  for (int b = blockIdx.x; b < g.nb; b += gridDim.x) {
+    const double* X = g.X + (size_t)b * m * 3;
+    const double* Y = g.Y + (size_t)b * n * 3;
+    const int32_t* I = g.I + (size_t)b * k;
+    const int32_t* J = g.J + (size_t)b * k;
+    double* ctx = g.ctx + (size_t)b * ((size_t)k * k + 2 * (size_t)k * nrhs);
+    double* U = ctx;
+    double* t1 = U + (size_t)k * k;
+    double* t2 = t1 + (size_t)k * nrhs;
+    // G and U = G^{-1}
+    for (int it = tid; it < k * k; it += nt) {
+      const int a = it / k, c = it - a * k;
+      double d2;
+      A[a * 2 * k + c] = gk64(X + 3 * (size_t)I[a], Y + 3 * (size_t)J[c], g.ell, &d2);
+      A[a * 2 * k + k + c] = (a == c) ? 1.0 : 0.0;
+    }
+    for (int a = tid; a < k; a += nt) pk[a] = split_point(X + 3 * (size_t)I[a]);
+    __syncthreads();
+    const int ok = gauss_jordan(A, k, f, ctl);
+    for (int it = tid; it < k * k; it += nt) {
+      const int a = it / k, c = it - a * k;
+      U[it] = ok ? A[a * 2 * k + k + c] : __longlong_as_double(0x7ff8000000000000ll);
+    }
+    // t1 = R x, R entries on the fly
+    for (int it = tid; it < k * nrhs; it += nt) t1d[it] = 0.0;
+    __syncthreads();
+    for (int j0 = 0; j0 < n; j0 += TILE) {
+      const int tj = min(TILE, n - j0);
+      for (int j = tid; j < tj; j += nt) pt[j] = split_point(Y + 3 * (size_t)(j0 + j));
+      for (int it = tid; it < tj * nrhs; it += nt) {
+        const int j = it / nrhs, c = it - j * nrhs;
+        xt[j * ldr + c] = g.x[((size_t)b * n + j0) * nrhs + it];
+      }
+      __syncthreads();
+      for (int it = tid; it < k * tj; it += nt) {
+        const int a = it / tj, j = it - a * tj;
+        float d2;
+        tile[j * ldk + a] = gk32s(pk[a], pt[j], inv2l2, &d2);
+      }
+      __syncthreads();
+      for (int o = tid; o < k * nrhs; o += nt) {
+        const int a = o / nrhs, c = o - a * nrhs;
+        float s = 0.f;
+        for (int j = 0; j < tj; ++j) s = fmaf(tile[j * ldk + a], xt[j * ldr + c], s);
+        t1d[o] += (double)s;
+      }
+      __syncthreads();
+    }
+    // t2 = U t1 (FP64); the J points replace the I points
+    for (int o = tid; o < k * nrhs; o += nt) {
+      const int a = o / nrhs, c = o - a * nrhs;
+      double s = 0.0;
+      for (int q = 0; q < k; ++q) s = fma(U[a * k + q], t1d[q * nrhs + c], s);
+      t2[o] = s;
+      t1[o] = t1d[o];
+      t2f[a * ldr + c] = (float)s;
+    }
+    __syncthreads();
+    for (int a = tid; a < k; a += nt) pk[a] = split_point(Y + 3 * (size_t)J[a]);
+    // y = C t2, C entries on the fly
+    for (int i0 = 0; i0 < m; i0 += TILE) {
+      const int ti = min(TILE, m - i0);
+      for (int i = tid; i < ti; i += nt) pt[i] = split_point(X + 3 * (size_t)(i0 + i));
+      __syncthreads();
+      for (int it = tid; it < ti * k; it += nt) {
+        const int i = it / k, a = it - i * k;
+        float d2;
+        tile[i * ldk + a] = gk32s(pt[i], pk[a], inv2l2, &d2);
+      }
+      __syncthreads();
+      for (int o = tid; o < ti * nrhs; o += nt) {
+        const int i = o / nrhs, c = o - i * nrhs;
+        float s = 0.f;
+        for (int a = 0; a < k; ++a) s = fmaf(tile[i * ldk + a], t2f[a * ldr + c], s);
+        g.y[((size_t)b * m + i0) * nrhs + o] = s;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void __launch_bounds__(GT) gauss_bwd_kernel(GaussArgs g) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int k = g.k, nrhs = g.nrhs, m = g.m, n = g.n, tid = threadIdx.x, nt = blockDim.x;
+  const int ldr = nrhs | 1, ldk = k | 1;
+  const float inv2l2 = (float)(1.0 / (2.0 * g.ell * g.ell));
+  const float il3 = (float)(1.0 / (g.ell * g.ell * g.ell));
+  double* s1 = reinterpret_cast<double*>(smem);                 // k x nrhs
+  double* s2d = s1 + (size_t)k * nrhs;                           // k x nrhs
+  P32* pk = reinterpret_cast<P32*>(s2d + (size_t)k * nrhs);      // k pivot points
+  P32* pt = pk + KMAX;                                          // TILE tile points
+  float* t2f = reinterpret_cast<float*>(pt + TILE);             // k x ldr
+  float* s2f = t2f + (size_t)k * ldr;                            // k x ldr
+  float* tile = s2f + (size_t)k * ldr;                           // TILE x ldk entries
+  float* dtile = tile + (size_t)TILE * ldk;                      // TILE x ldk dK/dl
+  float* vt = dtile + (size_t)TILE * ldk;                        // TILE x ldr (dy or x tile)
+  __shared__ double red[33];
+  for (int b = blockIdx.x; b < g.nb; b += gridDim.x) {
+    const double* X = g.X + (size_t)b * m * 3;
+    const double* Y = g.Y + (size_t)b * n * 3;
+    const int32_t* I = g.I + (size_t)b * k;
+    const int32_t* J = g.J + (size_t)b * k;
+    const double* ctx = g.ctx + (size_t)b * ((size_t)k * k + 2 * (size_t)k * nrhs);
+    const double* U = ctx;
+    const double* t2 = ctx + (size_t)k * k + (size_t)k * nrhs;
+    double dl = 0.0;
+    for (int it = tid; it < k * nrhs; it += nt) {
+      const int a = it / nrhs, c = it - a * nrhs;
+      s1[it] = 0.0;
+      t2f[a * ldr + c] = (float)t2[it];
+    }
+    for (int a = tid; a < k; a += nt) pk[a] = split_point(Y + 3 * (size_t)J[a]);
+    __syncthreads();
+    // pass over C: s1 = C^T dy, dC = dy t2^T, dl_C
+    for (int i0 = 0; i0 < m; i0 += TILE) {
+      const int ti = min(TILE, m - i0);
+      for (int i = tid; i < ti; i += nt) pt[i] = split_point(X + 3 * (size_t)(i0 + i));
+      for (int it = tid; it < ti * nrhs; it += nt) {
+        const int i = it / nrhs, c = it - i * nrhs;
+        vt[i * ldr + c] = g.dy[((size_t)b * m + i0) * nrhs + it];
+      }
+      __syncthreads();
+      for (int it = tid; it < ti * k; it += nt) {
+        const int i = it / k, a = it - i * k;
+        float d2;
+        const float kv = gk32s(pt[i], pk[a], inv2l2, &d2);
+        tile[i * ldk + a] = kv;
+        dtile[i * ldk + a] = kv * d2 * il3;
+      }
+      __syncthreads();
+      for (int o = tid; o < k * nrhs; o += nt) {
+        const int a = o / nrhs, c = o - a * nrhs;
+        float s = 0.f;
+        for (int i = 0; i < ti; ++i) s = fmaf(tile[i * ldk + a], vt[i * ldr + c], s);
+        s1[o] += (double)s;
+      }
+      float dls = 0.f;
+      for (int it = tid; it < ti * k; it += nt) {
+        const int i = it / k, a = it - i * k;
+        float s = 0.f;
+        for (int c = 0; c < nrhs; ++c) s = fmaf(vt[i * ldr + c], t2f[a * ldr + c], s);
+        if (g.dC) g.dC[((size_t)b * m + i0 + i) * k + a] = s;
+        dls = fmaf(s, dtile[i * ldk + a], dls);
+      }
+      dl += (double)dls;
+      __syncthreads();
+    }
+    // s2 = U^T s1
+    for (int o = tid; o < k * nrhs; o += nt) {
+      const int a = o / nrhs, c = o - a * nrhs;
+      double s = 0.0;
+      for (int q = 0; q < k; ++q) s = fma(U[q * k + a], s1[q * nrhs + c], s);
+      s2d[o] = s;
+      s2f[a * ldr + c] = (float)s;
+    }
+    __syncthreads();
+    for (int a = tid; a < k; a += nt) pk[a] = split_point(X + 3 * (size_t)I[a]);
+    // pass over R: dx = R^T s2, dR = s2 x^T, dl_R
+    for (int j0 = 0; j0 < n; j0 += TILE) {
+      const int tj = min(TILE, n - j0);
+      for (int j = tid; j < tj; j += nt) pt[j] = split_point(Y + 3 * (size_t)(j0 + j));
+      for (int it = tid; it < tj * nrhs; it += nt) {
+        const int j = it / nrhs, c = it - j * nrhs;
+        vt[j * ldr + c] = g.x[((size_t)b * n + j0) * nrhs + it];
+      }
+      __syncthreads();
+      for (int it = tid; it < k * tj; it += nt) {
+        const int a = it / tj, j = it - a * tj;
+        float d2;
+        const float kv = gk32s(pk[a], pt[j], inv2l2, &d2);
+        tile[j * ldk + a] = kv;
+        dtile[j * ldk + a] = kv * d2 * il3;
+      }
+      __syncthreads();
+      for (int o = tid; o < tj * nrhs; o += nt) {
+        const int j = o / nrhs, c = o - j * nrhs;
+        float s = 0.f;
+        for (int a = 0; a < k; ++a) s = fmaf(tile[j * ldk + a], s2f[a * ldr + c], s);
+        g.dx[((size_t)b * n + j0) * nrhs + o] = s;
+      }
+      float dls = 0.f;
+      for (int it = tid; it < k * tj; it += nt) {
+        const int j = it / k, a = it - j * k;
+        float s = 0.f;
+        for (int c = 0; c < nrhs; ++c) s = fmaf(s2f[a * ldr + c], vt[j * ldr + c], s);
+        if (g.dR) g.dR[((size_t)b * k + a) * n + j0 + j] = s;
+        dls = fmaf(s, dtile[j * ldk + a], dls);
+      }
+      dl += (double)dls;
+      __syncthreads();
+    }
+    // dG = -s2 t2^T and dl_G
+    for (int it = tid; it < k * k; it += nt) {
+      const int a = it / k, c = it - a * k;
+      double s = 0.0;
+      for (int q = 0; q < nrhs; ++q) s = fma(-s2d[a * nrhs + q], t2[c * nrhs + q], s);
+      double d2;
+      const double gv = gk64(X + 3 * (size_t)I[a], Y + 3 * (size_t)J[c], g.ell, &d2);
+      if (g.dG) g.dG[(size_t)b * k * k + it] = (float)s;
+      dl = fma(s, gv * d2 / (g.ell * g.ell * g.ell), dl);
+    }
+    dl = block_sum_d(dl, red);
+    if (tid == 0) g.dell[b] = dl;
+    __syncthreads();
+  }
+}
+
+static lra_status gauss_check(const lra_gauss_blocks* gb, int32_t nrhs) {
+  if (gb == nullptr || gb->X == nullptr || gb->Y == nullptr || gb->I == nullptr || gb->J == nullptr) return LRA_ERR_INVALID_ARG;
+  if (gb->nb < 1 || gb->m < 1 || gb->n < 1 || gb->k < 1 || gb->k > KMAX || gb->k > gb->m || gb->k > gb->n)
+    return LRA_ERR_INVALID_ARG;
+  if (nrhs < 1 || nrhs > 256 || !(gb->length_scale > 0.0)) return LRA_ERR_INVALID_ARG;
+  return LRA_OK;
+}
+
+static size_t fwd_smem(int k, int nrhs) {
+  return sizeof(double) * ((size_t)k * 2 * k + KMAX + (size_t)k * nrhs) + sizeof(P32) * (KMAX + TILE) +
+         sizeof(float) * ((size_t)TILE * (k | 1) + (size_t)TILE * (nrhs | 1) + (size_t)k * (nrhs | 1));
+}
+static size_t bwd_smem(int k, int nrhs) {
+  return sizeof(double) * 2 * (size_t)k * nrhs + sizeof(P32) * (KMAX + TILE) +
+         sizeof(float) * (2 * (size_t)k * (nrhs | 1) + 2 * (size_t)TILE * (k | 1) + (size_t)TILE * (nrhs | 1));
+}
+
+}  // namespace lra
+
+using namespace lra;
+
+extern "C" {
+
+lra_status lra_gauss_cur_forward(const lra_gauss_blocks* gb, const float* x, int32_t nrhs, float* y, double* ctx,
+                                 lra_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  lra_status st = gauss_check(gb, nrhs);
+  if (st != LRA_OK) return st;
+  if (!x || !y || !ctx) return LRA_ERR_INVALID_ARG;
+  GaussArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.X = gb->X; a.Y = gb->Y; a.I = gb->I; a.J = gb->J;
+  a.nb = gb->nb; a.m = gb->m; a.n = gb->n; a.k = gb->k; a.nrhs = nrhs; a.ell = gb->length_scale;
+  a.x = x; a.y = y; a.ctx = ctx;
+  const size_t smem = fwd_smem(gb->k, nrhs);
+  DeviceInfo dev;
+  if ((st = current_device_info(&dev)) != LRA_OK) return st;
+  if (smem > dev.smem_optin - 1024) return LRA_ERR_INVALID_ARG;
+  LRA_CUDA_TRY(cudaFuncSetAttribute(gauss_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    LaunchScope ls(stream, "gauss_fwd_kernel");
+    gauss_fwd_kernel<<<std::min(gb->nb, dev.sms * 4), GT, smem, stream>>>(a);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+lra_status lra_gauss_cur_backward(const lra_gauss_blocks* gb, const float* x, const float* dy, int32_t nrhs,
+                                  const double* ctx, float* dx, double* dell, float* dC, float* dR, float* dG,
+                                  lra_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  lra_status st = gauss_check(gb, nrhs);
+  if (st != LRA_OK) return st;
+  if (!x || !dy || !ctx || !dx || !dell) return LRA_ERR_INVALID_ARG;
+  GaussArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.X = gb->X; a.Y = gb->Y; a.I = gb->I; a.J = gb->J;
+  a.nb = gb->nb; a.m = gb->m; a.n = gb->n; a.k = gb->k; a.nrhs = nrhs; a.ell = gb->length_scale;
+  a.x = x; a.dy = dy; a.ctx = const_cast<double*>(ctx); a.dx = dx; a.dell = dell; a.dC = dC; a.dR = dR; a.dG = dG;
+  const size_t smem = bwd_smem(gb->k, nrhs);
+  DeviceInfo dev;
+  if ((st = current_device_info(&dev)) != LRA_OK) return st;
+  if (smem > dev.smem_optin - 1024) return LRA_ERR_INVALID_ARG;
+  LRA_CUDA_TRY(cudaFuncSetAttribute(gauss_bwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  {
+    LaunchScope ls(stream, "gauss_bwd_kernel");
+    gauss_bwd_kernel<<<std::min(gb->nb, dev.sms * 4), GT, smem, stream>>>(a);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

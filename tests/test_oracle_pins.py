@@ -358,3 +358,49 @@ def test_residual_sample_full_equals_full_residual():
     assert math.isclose(st[2], np.abs(Eref).mean(), rel_tol=1e-12)
     assert st[3] == np.abs(Eref).max()
     assert math.isclose(st[4], np.linalg.norm(Eref) / np.linalg.norm(p.W), rel_tol=1e-12)
+
+
+# ------------------------------------------------------------------ differentiable apply
+def _gauss_case(seed=0, m=60, n=50, k=6, nrhs=3):
+    g = np.random.default_rng(seed)
+    X = g.random((m, 3)); Y = g.random((n, 3)); Y[:, 0] += 1.0
+    I = np.sort(g.choice(m, k, replace=False)).astype(np.int32)
+    J = np.sort(g.choice(n, k, replace=False)).astype(np.int32)
+    return X, Y, I, J, g.standard_normal((n, nrhs)), g.standard_normal((m, nrhs))
+
+
+def test_gauss_cur_apply_matches_dense_formula():
+    """y = C G^{-1} R x with the sampled entries (closed-form kernel, LAPACK inverse)."""
+    X, Y, I, J, x, _ = _gauss_case()
+    ell = 0.4
+    K = np.exp(-np.sum((X[:, None] - Y[None]) ** 2, axis=2) / (2 * ell ** 2))
+    y, U, t1, t2 = oracle.gauss_cur_apply(X, Y, I, J, ell, x)
+    yref = K[:, J] @ np.linalg.solve(K[np.ix_(I, J)], K[I] @ x)
+    np.testing.assert_allclose(y, yref, rtol=1e-9, atol=1e-12 * np.abs(yref).max())
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_gauss_cur_backward_finite_differences(seed):
+    """dL/dx, dL/dl and the entry gradients of L = <dy, y> against central
+    finite differences of the forward in FP64."""
+    X, Y, I, J, x, dy = _gauss_case(seed)
+    ell = 0.45
+    b = oracle.gauss_cur_backward(X, Y, I, J, ell, x, dy)
+    L = lambda e, xx: float(np.sum(dy * oracle.gauss_cur_apply(X, Y, I, J, e, xx)[0]))
+    h = 1e-6
+    fd = (L(ell + h, x) - L(ell - h, x)) / (2 * h)
+    assert abs(fd - b["dell"]) <= 1e-6 * max(1.0, abs(fd))
+    xp = x.copy(); xp[3, 1] += h; xm = x.copy(); xm[3, 1] -= h
+    fdx = (L(ell, xp) - L(ell, xm)) / (2 * h)
+    assert abs(fdx - b["dx"][3, 1]) <= 1e-6 * max(1.0, abs(fdx))
+    # entry gradients: perturb one entry of C, R, G through a dense re-evaluation
+    K = np.exp(-np.sum((X[:, None] - Y[None]) ** 2, axis=2) / (2 * ell ** 2))
+    C, R, G = K[:, J].copy(), K[I].copy(), K[np.ix_(I, J)].copy()
+    f = lambda C_, R_, G_: float(np.sum(dy * (C_ @ np.linalg.solve(G_, R_ @ x))))
+    for name, M, idx in (("dC", C, (7, 2)), ("dR", R, (1, 11)), ("dG", G, (3, 4))):
+        Mp, Mm = M.copy(), M.copy(); Mp[idx] += h; Mm[idx] -= h
+        args_p = dict(C_=C, R_=R, G_=G); args_m = dict(C_=C, R_=R, G_=G)
+        key = {"dC": "C_", "dR": "R_", "dG": "G_"}[name]
+        args_p[key] = Mp; args_m[key] = Mm
+        fdv = (f(**args_p) - f(**args_m)) / (2 * h)
+        assert abs(fdv - b[name][idx]) <= 1e-6 * max(1.0, abs(fdv)), (name, fdv, b[name][idx])
