@@ -54,12 +54,13 @@ class Problem:
     nnz: int = 0                            # sparse multiplier nonzeros per column
     srow: Optional[np.ndarray] = None       # (n, nnz) int32 ascending per column
     ssign: Optional[np.ndarray] = None      # (n, nnz) int8, +-1
+    entries: str = "f64"                    # kernel: entries evaluated in "f64" or "f32"
     meta: dict = field(default_factory=dict)
 
     @property
     def dtype(self) -> str:
         if self.W is None:
-            return "f64"
+            return self.entries
         return "f32" if self.W.dtype == np.float32 else "f64"
 
 

@@ -76,7 +76,17 @@ static double entry_w(const orc_problem* p, int64_t i, int64_t j) {
   const double* y = p->Y + 3 * j;
   double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
   double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-  if (p->src == ORC_LAPLACE) return 1.0 / sqrt(r2);
+  if (p->src == ORC_LAPLACE) {
+    if (p->dtype == ORC_F32) {
+      /* FP32 entries: r2 rounded to single precision, then the IEEE single
+       * square root and quotient, each correctly rounded. */
+      float r2f = (float)r2;
+      float sf = sqrtf(r2f);
+      float ef = 1.0f / sf;
+      return (double)ef;
+    }
+    return 1.0 / sqrt(r2);
+  }
   return exp(-(r2 / (2.0 * p->ell * p->ell)));
 }
 

@@ -338,6 +338,79 @@ def test_separated_laplace_block_error_decays_with_rank():
     assert errs[-1] < 1e-5 and all(b < a for a, b in zip(errs, errs[1:]))
 
 
+def _fl64(q):
+    """Round an exact rational to the nearest double (CPython int / int is correctly rounded)."""
+    return float(q.numerator / q.denominator) if q.denominator != 1 else float(q.numerator)
+
+
+def _laplace_f32_exact(x, y):
+    """The FP32 Laplace entry from its definition, with exact rational arithmetic for
+    the FP64 squared distance r2 = fma(dz, dz, fma(dy, dy, dx*dx)) and numpy's IEEE
+    single-precision square root and quotient."""
+    from fractions import Fraction as F
+    dx, dy, dz = (float(np.float64(a) - np.float64(b)) for a, b in zip(x, y))
+    dxx = float(np.float64(dx) * np.float64(dx))
+    t = _fl64(F(dy) * F(dy) + F(dxx))
+    r2 = _fl64(F(dz) * F(dz) + F(t))
+    s = np.sqrt(np.float32(r2))
+    return float(np.float32(1.0) / s)
+
+
+def test_laplace_f32_entries_follow_their_definition():
+    """Kernel entries in FP32: fl32(1 / fl32(sqrt(fl32(r2)))), r2 the fused FP64
+    squared distance; checked entry by entry against exact rational r2 and numpy's
+    single-precision operations, including nearly coincident and far points."""
+    g = np.random.default_rng(11)
+    X = g.random((24, 3))
+    Y = np.concatenate([g.random((20, 3)) + [3.0, 0.0, 0.0], X[:4] + 1e-9 * g.standard_normal((4, 3))])
+    p = li.Problem(li.SRC_LAPLACE, 24, 24, X=X, Y=Y, entries="f32")
+    R = oracle.gather_rows(p, np.arange(24, dtype=np.int32))
+    for i in range(24):
+        for j in range(24):
+            assert R[i, j] == _laplace_f32_exact(X[i], Y[j]), (i, j)
+
+
+def test_laplace_f32_entries_relative_error_bound():
+    """Three correctly rounded FP32 operations: |w32 / w64 - 1| <= (1/2 + 1 + 1) 2^-24 + O(2^-48)."""
+    p = li.laplace_clusters(300, 280, seed=5)
+    q = li.Problem(li.SRC_LAPLACE, 300, 280, X=p.X, Y=p.Y, entries="f32")
+    rows = np.arange(300, dtype=np.int32)
+    W64, W32 = oracle.gather_rows(p, rows), oracle.gather_rows(q, rows)
+    rel = np.abs(W32 / W64 - 1.0)
+    assert rel.max() <= 2.5 * 2.0 ** -24 * (1 + 1e-6)
+    assert np.all(W32 == W32.astype(np.float32))      # every entry is an FP32 number
+    assert rel.max() > 0                               # and they differ from the FP64 entries
+
+
+def test_laplace_f32_kernel_run_equals_dense_f32_run():
+    """A C-A run that evaluates the FP32 kernel entries on demand equals the run on the
+    dense FP32 matrix of the same entries (gathers, core and outputs use one definition)."""
+    p = li.laplace_clusters(260, 230, seed=6)
+    q = li.Problem(li.SRC_LAPLACE, 260, 230, X=p.X, Y=p.Y, entries="f32")
+    W32 = oracle.gather_rows(q, np.arange(260, dtype=np.int32)).astype(np.float32)
+    d = li.Problem(li.SRC_DENSE, 260, 230, W=W32)
+    I0 = li.initial_rows(260, 12, 4)
+    a, b = oracle.ca_run(q, 12, 3, I0), oracle.ca_run(d, 12, 3, I0)
+    for key in ("I", "J", "C", "U", "R", "logvol"):
+        np.testing.assert_array_equal(a[key], b[key])
+    assert (a["swaps"], a["loops"], a["status"]) == (b["swaps"], b["loops"], b["status"])
+
+
+def test_laplace_f32_entries_error_against_fp64_matrix():
+    """With FP32 entries the CUR of the separated clusters still approximates the FP64
+    matrix to <= 1e-6 relative Frobenius error at k = 24 (the FP32 perturbation adds at
+    most 1.25 * 2^-23 relative per entry, about 1.5e-7 in the Frobenius ratio)."""
+    p = li.laplace_clusters(400, 350, seed=7)
+    q = li.Problem(li.SRC_LAPLACE, 400, 350, X=p.X, Y=p.Y, entries="f32")
+    K = oracle.gather_rows(p, np.arange(400, dtype=np.int32))
+    I0 = li.initial_rows(400, 24, 1)
+    o64, o32 = oracle.ca_run(p, 24, 3, I0), oracle.ca_run(q, 24, 3, I0)
+    e64 = np.linalg.norm(K - o64["C"] @ o64["U"] @ o64["R"]) / np.linalg.norm(K)
+    e32 = np.linalg.norm(K - o32["C"] @ o32["U"] @ o32["R"]) / np.linalg.norm(K)
+    assert e64 < 1e-6 and e32 < 1e-6, (e64, e32)
+    assert e32 <= 1.5 * e64 + 1.25 * 2.0 ** -23
+
+
 # ------------------------------------------------------------------ apply / residual
 def test_cur_apply_matches_matmul():
     g = np.random.default_rng(0)
