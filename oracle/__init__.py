@@ -45,6 +45,8 @@ def lib():
         L.orc_nucleus.restype = i32
         L.orc_ca_run.argtypes = [P, i32, i32, vp, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_ca_run.restype = ct.c_int
+        L.orc_ca_run_adaptive.argtypes = [P, vp, i32, i32, i32, vp, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_ca_run_adaptive.restype = ct.c_int
         L.orc_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp]
         L.orc_residual_sample.argtypes = [P, vp, vp, vp, i32, vp, i32, vp, i32, vp, vp]
         L.orc_brute_maxvol.argtypes = [vp, i32, i32, vp]
@@ -193,6 +195,28 @@ def ca_run(p, k, sweeps, I0, h=1.01, max_swaps=1000, rank_tol=1e-13):
                      _ptr(R), _ptr(lv), _ptr(info))
     return dict(I=I, J=J, C=C, U=U, R=R, logvol=lv, rank=int(info[0]), swaps=int(info[1]),
                 loops=int(info[2]), status=int(info[3]))
+
+
+def ca_run_adaptive(p, stages, margin, sweeps, I0, h=1.01, max_swaps=1000, rank_tol=1e-6):
+    """C-A with staged generator sizes (orc_ca_run_adaptive): a run at each size
+    k_s of ``stages`` (clipped to min(m, n)) until the nucleus rank r_s < k_s -
+    margin or the last size.  I0 holds min(stages[-1], m, n) distinct rows.
+    Returns ca_run's dict at the final size plus k (final size) and stages (run)."""
+    mp = _Marshalled(p)
+    st = np.ascontiguousarray(stages, dtype=np.int32)
+    assert len(st) >= 1 and np.all(np.diff(st) > 0) and st[0] >= 1
+    kmax = int(min(st[-1], p.m, p.n))
+    I0 = np.ascontiguousarray(I0, dtype=np.int32)[:kmax]
+    assert len(I0) == kmax
+    I = np.empty(kmax, dtype=np.int32); J = np.empty(kmax, dtype=np.int32)
+    C = np.empty(p.m * kmax); U = np.empty(kmax * kmax); R = np.empty(kmax * p.n)
+    lv = np.empty(2 * sweeps); info = np.empty(6, dtype=np.int32)
+    lib().orc_ca_run_adaptive(mp.ref, _ptr(st), len(st), int(margin), sweeps, _ptr(I0), h, max_swaps, rank_tol,
+                              _ptr(I), _ptr(J), _ptr(C), _ptr(U), _ptr(R), _ptr(lv), _ptr(info))
+    k = int(info[4])
+    return dict(I=I[:k].copy(), J=J[:k].copy(), C=C[:p.m * k].reshape(p.m, k), U=U[:k * k].reshape(k, k),
+                R=R[:k * p.n].reshape(k, p.n), logvol=lv, rank=int(info[0]), swaps=int(info[1]),
+                loops=int(info[2]), status=int(info[3]), k=k, stages=int(info[5]))
 
 
 def cur_apply(C, U, R, X):

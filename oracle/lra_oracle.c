@@ -488,6 +488,62 @@ int orc_ca_run(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I
   return status;
 }
 
+/*
+ * orc_ca_run_adaptive: C-A with the generator size fitted to the numerical
+ * rank.  The paper's tests take r x r generators with r the numerical rank of
+ * the input at 1e-6 (section "Numerical Experiments", Test Overview); here
+ * that rank is found from the nucleus of the C-A run itself, in stages:
+ *   sizes k_1 < k_2 < ... < k_S, each clipped to kmax = min(k_S, m, n);
+ *   stage s: a complete C-A run (orc_ca_run) of size k_s from initial rows
+ *     I_s, then the nucleus rank r_s at rank_tol;
+ *   stop when r_s < k_s - margin (the core has spare room) or k_s = kmax;
+ *   otherwise I_{s+1} = the stage's rows I, then the caller's initial rows
+ *     I0[0 .. kmax-1] that are not in I, in their order, up to k_{s+1} rows.
+ * I0 holds kmax distinct rows; I_1 = I0[0 .. k_1-1].
+ * Outputs at the final size kf: I, J (kf), C (m x kf), U (kf x kf),
+ * R (kf x n), logvol of the final stage; info[0] rank, info[1] swaps and
+ * info[2] loops summed over the stages, info[3] the final stage's status,
+ * info[4] kf, info[5] stages run.  Buffers are sized for kmax.
+ */
+int orc_ca_run_adaptive(const orc_problem* p, const int32_t* stages, int32_t nstages, int32_t margin,
+                        int32_t sweeps, const int32_t* I0, double h, int32_t max_swaps, double rank_tol, int32_t* I,
+                        int32_t* J, double* C, double* U, double* R, double* logvol, int32_t* info) {
+  int64_t lim = p->m < p->n ? p->m : p->n;
+  int32_t kmax = stages[nstages - 1];
+  if (kmax > lim) kmax = (int32_t)lim;
+  int32_t* Icur = (int32_t*)malloc(sizeof(int32_t) * (size_t)kmax);
+  int32_t s = 0, k = stages[0] < kmax ? stages[0] : kmax;
+  int32_t swaps = 0, loops = 0, nrun = 0, st = ORC_OK;
+  int32_t inf[4];
+  memcpy(Icur, I0, sizeof(int32_t) * (size_t)k);
+  for (;;) {
+    st = orc_ca_run(p, k, sweeps, Icur, h, max_swaps, rank_tol, I, J, C, U, R, logvol, inf);
+    ++nrun;
+    swaps += inf[1];
+    loops += inf[2];
+    if (st != ORC_OK && st < 16) break;
+    if (k >= kmax || inf[0] < k - margin) break;
+    /* next larger stage size */
+    int32_t kn = k;
+    while (s + 1 < nstages && kn <= k) {
+      ++s;
+      kn = stages[s] < kmax ? stages[s] : kmax;
+    }
+    if (kn <= k) break;
+    memcpy(Icur, I, sizeof(int32_t) * (size_t)k);
+    int32_t c = k;
+    for (int32_t t = 0; t < kmax && c < kn; ++t) {
+      int in = 0;
+      for (int32_t a = 0; a < k; ++a) in |= (I[a] == I0[t]);
+      if (!in) Icur[c++] = I0[t];
+    }
+    k = kn;
+  }
+  info[0] = inf[0]; info[1] = swaps; info[2] = loops; info[3] = st; info[4] = k; info[5] = nrun;
+  free(Icur);
+  return st;
+}
+
 /* ------------------------------------------------------------------ */
 /* CUR apply and sampled residual                                      */
 /* ------------------------------------------------------------------ */

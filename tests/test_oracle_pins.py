@@ -411,6 +411,63 @@ def test_laplace_f32_entries_error_against_fp64_matrix():
     assert e32 <= 1.5 * e64 + 1.25 * 2.0 ** -23
 
 
+# ------------------------------------------------------------------ adaptive generator size
+def test_adaptive_single_stage_is_the_fixed_run():
+    p = li.laplace_clusters(300, 280, seed=3)
+    I0 = li.initial_rows(300, 20, 2)
+    a = oracle.ca_run_adaptive(p, (20,), 2, 3, I0)
+    b = oracle.ca_run(p, 20, 3, I0, rank_tol=1e-6)
+    for key in ("I", "J", "C", "U", "R", "logvol"):
+        np.testing.assert_array_equal(a[key], b[key])
+    assert (a["k"], a["stages"], a["swaps"], a["loops"]) == (20, 1, b["swaps"], b["loops"])
+
+
+@pytest.mark.parametrize("r, kf, nst", [(5, 8, 1), (13, 16, 2), (20, 32, 3)])
+def test_adaptive_exact_low_rank_recovery(r, kf, nst):
+    """Rank-r W = A B (Theorem thdcmp: W = CUR once the core has rank r): the
+    stages 8, 16, 32 with margin 2 grow until the core rank r < k - 2."""
+    g = np.random.default_rng(r)
+    W = g.standard_normal((90, r)) @ g.standard_normal((r, 70))
+    p = li.Problem(li.SRC_DENSE, 90, 70, W=W)
+    o = oracle.ca_run_adaptive(p, (8, 16, 32), 2, 3, li.initial_rows(90, 32, 4), rank_tol=1e-9)
+    assert (o["k"], o["stages"], o["rank"]) == (kf, nst, r)
+    assert np.linalg.norm(W - o["C"] @ o["U"] @ o["R"]) <= 1e-9 * np.linalg.norm(W)
+
+
+def test_adaptive_next_stage_starts_from_current_rows():
+    """Stage 2 is the fixed run of size k_2 from the stage-1 rows followed by the
+    caller's rows not among them, in order."""
+    p = li.laplace_clusters(500, 450, seed=8)
+    I0 = li.initial_rows(500, 40, 6)
+    a = oracle.ca_run_adaptive(p, (12, 40), 0, 3, I0)
+    s1 = oracle.ca_run(p, 12, 3, I0[:12], rank_tol=1e-6)
+    assert s1["rank"] >= 12 and a["stages"] == 2
+    rest = [i for i in I0 if i not in set(s1["I"].tolist())]
+    I2 = np.concatenate([s1["I"], np.array(rest[:28], np.int32)])
+    b = oracle.ca_run(p, 40, 3, I2, rank_tol=1e-6)
+    for key in ("I", "J", "C", "U", "R"):
+        np.testing.assert_array_equal(a[key], b[key])
+    assert a["swaps"] == s1["swaps"] + b["swaps"] and a["loops"] == s1["loops"] + b["loops"]
+
+
+def test_adaptive_fmm_blocks_accuracy_and_size():
+    """Octree interaction blocks of the Laplace kernel: with stages 28, 40, 64 and
+    margin 2 every block ends within 1e-6 relative Frobenius error, with a final
+    size at least the numerical rank at 1e-6 (the paper's rank(., 1e-6)) and the
+    stop rule met."""
+    p, blocks, lev = li.fmm_blocks(npts=1 << 16, nblocks=256, seed=4)
+    I0s = li.block_initial_rows(blocks, 64, 3)
+    for b in np.random.default_rng(0).choice(len(blocks), 10, replace=False):
+        r0, nr, c0, nc = blocks[b]
+        s = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc])
+        o = oracle.ca_run_adaptive(s, (28, 40, 64), 2, 3, I0s[b])
+        K = oracle.gather_rows(s, np.arange(s.m, dtype=np.int32))
+        sv = np.linalg.svd(K, compute_uv=False)
+        err = np.linalg.norm(K - o["C"] @ o["U"] @ o["R"]) / np.linalg.norm(K)
+        assert err <= 1e-6 and o["k"] >= int((sv > 1e-6 * sv[0]).sum())
+        assert o["rank"] < o["k"] - 2 or o["k"] == min(64, nr, nc)
+
+
 # ------------------------------------------------------------------ apply / residual
 def test_cur_apply_matches_matmul():
     g = np.random.default_rng(0)
