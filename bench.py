@@ -73,13 +73,40 @@ def ca_flops(k, m, n, loops, swaps, entry_flops=0.0, nucleus=True):
 
 
 # ------------------------------------------------------------------ workloads
+def staged_flops(stages, kb, m, n, nrun, loops, swaps, entry_flops):
+    """Lower bound on the algorithmic flops of a staged run: the sizes actually run
+    (stages clipped to kb), every stage but the last with the fewest loops it can
+    have (2, or 1 when it is the only loop allowed) and the remaining loops and all
+    swaps charged to the smallest size."""
+    sizes = []
+    for st in stages:
+        k = min(st, kb)
+        if not sizes or k > sizes[-1]:
+            sizes.append(k)
+    sizes = sizes[:nrun] if stages else [kb]
+    f = 0.0
+    left = loops
+    for i, k in enumerate(sizes):
+        lk = max(1, left - 2 * (len(sizes) - 1 - i)) if i == 0 else min(2, left) if i < len(sizes) - 1 else left
+        lk = max(lk, 1)
+        left -= lk
+        f += ca_flops(k, m, n, lk, swaps if i == 0 else 0, entry_flops)
+    return f
+
+
 class FmmWorkload:
     name = "fmm_laplace_1M_octree_4096blocks_k64_tol1e-6"
     kernel = "ca_batched_kernel"
     unit = "LRA/s"
 
-    def __init__(self, npts=1 << 20, nblocks=4096, k=64, sweeps=3, tol=1e-6, q=16, s=16):
+    def __init__(self, npts=1 << 20, nblocks=4096, k=64, sweeps=3, tol=1e-6, q=16, s=16, entries="f64",
+                 stages=(28, 40, 64), margin=2):
         self.npts, self.nblocks, self.k, self.sweeps, self.tol, self.q, self.s = npts, nblocks, k, sweeps, tol, q, s
+        self.entries, self.stages, self.margin = entries, stages, margin
+        if entries == "f32":
+            self.name = self.name + "_f32entries"
+        if stages is None:
+            self.name = self.name + "_fixedk"
 
     def host(self, rank):
         p, blocks, lev = li.fmm_blocks(npts=self.npts, nblocks=self.nblocks, seed=rank)
@@ -92,7 +119,11 @@ class FmmWorkload:
         b = h["blocks"]
         return {"workload": self.name, "points": self.npts, "blocks": int(len(b)),
                 "block_rows_min_median_max": [int(b[:, 1].min()), int(np.median(b[:, 1])), int(b[:, 1].max())],
-                "kernel": "Laplace 1/|x-y|, on the fly, FP64", "k_max": self.k, "rank_tol": self.tol,
+                "kernel": f"Laplace 1/|x-y|, on the fly, entries {self.entries.upper()}",
+                "pivots_nucleus": "FP64", "residual_against": "FP64 entries", "k_max": self.k,
+                "generator_sizes": (f"staged {'/'.join(map(str, self.stages))}, grow while nucleus rank >= "
+                                    f"size - {self.margin}" if self.stages else "fixed min(k_max, rows, cols)"),
+                "rank_tol": self.tol,
                 "sweeps": self.sweeps, "residual_sample": f"{self.q}x{self.s} per block"}
 
     def device(self, h, dev):
@@ -100,16 +131,19 @@ class FmmWorkload:
         import paper_1710_07946_gb300 as lra
         p = h["p"]
         X = torch.from_numpy(p.X).to(dev)
-        prob = lra.Problem.kernel("laplace", X, X)
-        bt = lra.Batch(prob, h["blocks"], self.k, self.sweeps, h["I0"], rank_tol=self.tol)
-        d = dict(X=X, prob=prob, bt=bt, Q=torch.from_numpy(h["Q"]).to(dev), S=torch.from_numpy(h["S"]).to(dev))
+        prob = lra.Problem.kernel("laplace", X, X, entries=self.entries)
+        prob64 = lra.Problem.kernel("laplace", X, X)
+        bt = lra.Batch(prob, h["blocks"], self.k, self.sweeps, h["I0"], rank_tol=self.tol, stages=self.stages,
+                       rank_margin=self.margin)
+        d = dict(X=X, prob=prob, prob64=prob64, bt=bt, Q=torch.from_numpy(h["Q"]).to(dev),
+                 S=torch.from_numpy(h["S"]).to(dev))
         d["stats"] = torch.empty(len(h["blocks"]), 5, dtype=torch.float64, device=dev)
         return d
 
     def step(self, d):
         import paper_1710_07946_gb300 as lra
         lra.lra_ca_run_batched(d["bt"])
-        lra.lra_residual_sample_batched(d["bt"], d["Q"], d["S"], d["stats"])
+        lra.lra_residual_sample_batched(d["bt"], d["Q"], d["S"], d["stats"], problem=d["prob64"])
 
     def check(self, d):
         info = d["bt"].out["info"].cpu().numpy()
@@ -123,12 +157,14 @@ class FmmWorkload:
         f = 0.0
         for (r0, nr, c0, nc), inf in zip(b, info):
             kb = int(min(self.k, nr, nc))
-            f += ca_flops(kb, int(nr), int(nc), max(int(inf[2]), 1), int(inf[1]), LAPLACE_FLOPS)
+            f += staged_flops(self.stages or (), kb, int(nr), int(nc), max(int(inf[7]), 1), max(int(inf[2]), 1),
+                              int(inf[1]), LAPLACE_FLOPS)
         return f
 
     def extra(self, res):
         info, err = res["info"], res["err"]
         return {"rank_min_median_max": [int(info[:, 0].min()), int(np.median(info[:, 0])), int(info[:, 0].max())],
+                "generator_size_hist": {int(k): int(c) for k, c in zip(*np.unique(info[:, 6], return_counts=True))},
                 "swaps_mean": float(info[:, 1].mean()), "loops_hist": np.bincount(info[:, 2]).tolist(),
                 "rel_fro_err_sampled_median": float(np.median(err)), "rel_fro_err_sampled_max": float(err.max()),
                 "frac_blocks_err_le_1e-6": float((err <= ERR_BOUND).mean())}
@@ -165,7 +201,12 @@ class FmmWorkload:
             r0, nr, c0, nc = b[idx]
             kb = int(min(self.k, nr, nc))
             sub = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=h["p"].X[r0:r0 + nr], Y=h["p"].Y[c0:c0 + nc])
-            o = oracle.ca_run(sub, kb, self.sweeps, h["I0"][idx, :kb], rank_tol=self.tol)
+            sube = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=sub.X, Y=sub.Y, entries=self.entries)
+            if self.stages:
+                o = oracle.ca_run_adaptive(sube, self.stages, self.margin, self.sweeps, h["I0"][idx],
+                                           rank_tol=self.tol)
+            else:
+                o = oracle.ca_run(sube, kb, self.sweeps, h["I0"][idx, :kb], rank_tol=self.tol)
             st = oracle.residual_sample(sub, o["C"], o["U"], o["R"], h["Q"][idx], h["S"][idx])
             n += 1
             good += st[4] <= ERR_BOUND
@@ -263,6 +304,100 @@ class DenseWorkload:
                 break
         el = time.perf_counter() - t0
         return n, n, el, f"{n} complete LRAs of the same input (C-A + nucleus + residual sample)"
+
+
+class LaplaceSingleWorkload:
+    """One C-A CUR of the 65536 x 65536 Laplace kernel between two unit cubes whose
+    centres are 3 apart, entries evaluated on the fly (FP64 or FP32), rank k,
+    3 loops, FP64 pivots and nucleus, on the whole GPU (cooperative grid)."""
+    kernel = "ca_kernel"
+    unit = "LRA/s"
+
+    def __init__(self, k, entries="f64", n=65536, sweeps=3):
+        self.k, self.entries, self.n, self.sweeps, self.q, self.s = k, entries, n, sweeps, 256, 256
+        self.name = f"laplace{n}_cubes3apart_k{k}_s{sweeps}_{entries}entries"
+
+    def host(self, rank):
+        p = li.laplace_clusters(self.n, self.n, seed=1 + 1000 * rank)
+        I0 = li.initial_rows(self.n, self.k, 0)
+        Q, S = li.sample_positions(self.n, self.n, self.q, self.s, 13)
+        return dict(p=p, I0=I0, Q=Q, S=S)
+
+    def config(self, h):
+        return {"workload": self.name, "m": self.n, "n": self.n, "k": self.k, "sweeps": self.sweeps,
+                "kernel": f"Laplace 1/|x-y|, on the fly, entries {self.entries.upper()}",
+                "pivots_nucleus": "FP64", "residual_sample": f"{self.q}x{self.s} against FP64 entries"}
+
+    def device(self, h, dev):
+        import torch
+        import paper_1710_07946_gb300 as lra
+        p = h["p"]
+        X, Y = torch.from_numpy(p.X).to(dev), torch.from_numpy(p.Y).to(dev)
+        prob = lra.Problem.kernel("laplace", X, Y, entries=self.entries)
+        prob64 = lra.Problem.kernel("laplace", X, Y)
+        I0 = torch.from_numpy(h["I0"]).to(dev)
+        out = lra.lra_ca_run(prob, I0, self.k, self.sweeps)
+        return dict(X=X, Y=Y, prob=prob, prob64=prob64, I0=I0, out=out, Q=torch.from_numpy(h["Q"]).to(dev),
+                    S=torch.from_numpy(h["S"]).to(dev), stats=None)
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        lra.lra_ca_run(d["prob"], d["I0"], self.k, self.sweeps, out=d["out"], workspace=d["out"]["_workspace"])
+        d["stats"] = lra.lra_residual_sample(d["prob64"], d["out"]["C"], d["out"]["U"], d["out"]["R"], d["Q"],
+                                             d["S"])
+
+    def check(self, d):
+        info = d["out"]["info"].cpu().numpy()[None, :]
+        err = d["stats"].cpu().numpy()[4:5]
+        ok = (info[0, 3] == 0 or info[0, 3] >= 16) and err[0] <= ERR_BOUND
+        return dict(units=int(ok), info=info, err=err)
+
+    def flops(self, h, res):
+        inf = res["info"][0]
+        return ca_flops(self.k, self.n, self.n, max(int(inf[2]), 1), int(inf[1]), LAPLACE_FLOPS, nucleus=False)
+
+    def extra(self, res):
+        inf = res["info"][0]
+        return {"rank": int(inf[0]), "swaps": int(inf[1]), "loops": int(inf[2]), "status": int(inf[3]),
+                "rel_fro_err_sampled": float(res["err"][0])}
+
+    def e2e_setup(self, h, d):
+        import torch
+        hp = dict(X=torch.from_numpy(h["p"].X).pin_memory(), Y=torch.from_numpy(h["p"].Y).pin_memory(),
+                  I0=torch.from_numpy(h["I0"]).pin_memory())
+        hp["out"] = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in d["out"].items()
+                     if not key.startswith("_")}
+        hp["stats"] = torch.empty(5, dtype=torch.float64).pin_memory()
+        h2d = (hp["X"].numel() + hp["Y"].numel()) * 8 + hp["I0"].numel() * 4
+        d2h = sum(v.numel() * v.element_size() for v in hp["out"].values()) + 40
+        return hp, h2d, d2h
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["X"].copy_(hp["X"], non_blocking=True)
+        d["Y"].copy_(hp["Y"], non_blocking=True)
+        d["I0"].copy_(hp["I0"], non_blocking=True)
+        self.step(d)
+        for key, v in hp["out"].items():
+            v.copy_(d["out"][key], non_blocking=True)
+        hp["stats"].copy_(d["stats"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        p = h["p"]
+        pe = li.Problem(li.SRC_LAPLACE, p.m, p.n, X=p.X, Y=p.Y, entries=self.entries)
+        t0 = time.perf_counter()
+        n = good = 0
+        while True:
+            o = oracle.ca_run(pe, self.k, self.sweeps, h["I0"])
+            st = oracle.residual_sample(p, o["C"], o["U"], o["R"], h["Q"], h["S"])
+            n += 1
+            good += st[4] <= ERR_BOUND
+            if time.perf_counter() - t0 >= budget_s or n >= 50:
+                break
+        el = time.perf_counter() - t0
+        return good, n, el, f"{n} complete LRAs of the same input (C-A + nucleus + residual sample)"
 
 
 class GaussApplyWorkload:
@@ -371,7 +506,11 @@ class FmmSmallWorkload(FmmWorkload):
 
 WORKLOADS = {
     "fmm": FmmWorkload,
+    "fmm_f32": lambda: FmmWorkload(entries="f32"),
+    "fmm_fixedk": lambda: FmmWorkload(stages=None),
     "fmm_small": FmmSmallWorkload,
+    **{f"laplace65536_k{k}{sfx}": (lambda k=k, e=e: LaplaceSingleWorkload(k, e))
+       for k in (16, 32, 64) for sfx, e in (("", "f64"), ("_f32", "f32"))},
     "gauss_apply": GaussApplyWorkload,
     "dense8192_arht": lambda: DenseWorkload("arht"),
     "dense8192_sparse": lambda: DenseWorkload("sparse"),

@@ -54,7 +54,12 @@ typedef enum {
 
 typedef struct {
   int32_t src;           /* lra_source                                               */
-  int32_t dtype;         /* dense storage type: LRA_F64 or LRA_F32                   */
+  int32_t dtype;         /* dense: storage type, LRA_F64 or LRA_F32.  Laplace kernel:
+                            LRA_F64 (w = 1/sqrt(r2), FP64) or LRA_F32 (w = fl32(1 /
+                            sqrt(fl32(r2))), each FP32 operation correctly rounded,
+                            r2 the FP64 squared distance; relative distance to the
+                            FP64 entry <= 1.5 * 2^-23).  Gaussian kernel: LRA_F64.
+                            Any other value is LRA_ERR_INVALID_ARG.                  */
   int64_t m, n;          /* rows, columns; 1 <= m, n < 2^31                          */
   const void* W;         /* dense: device, m x n row-major, leading dimension ldw    */
   int64_t ldw;           /* dense: >= n                                              */
@@ -117,8 +122,10 @@ typedef enum {
                                of LRA_MODE_FP64; logvol is then computed from the FP32
                                pivots (relative accuracy ~1e-6).  It runs on one CTA:
                                every block of a batch, and lra_ca_run inputs with
-                               max(m, n) <= 2048; larger single runs and Gaussian
-                               kernels run in FP64.                                 */
+                               max(m, n) <= 2048; larger single runs, Gaussian
+                               kernels and FP32 Laplace entries run in FP64.  After
+                               a step falls back, the rest of that run (or block)
+                               skips the FP32 attempt.                              */
 } lra_mode;
 
 typedef struct {
@@ -128,7 +135,21 @@ typedef struct {
   double rank_tol;       /* relative QRP truncation tolerance of the nucleus         */
   int32_t max_swaps;     /* cap on swaps per maxvol step (>= 0)                      */
   int32_t mode;          /* lra_mode                                                 */
+  /* Generator size fitted to the numerical rank (batched runs only; lra_ca_run
+     rejects nstages != 0).  The paper's tests size the generators at the
+     numerical rank of the input at 1e-6; here it comes from the nucleus of the
+     run itself.  nstages = 0: one run of size k.  Otherwise sizes
+     k_stages[0] < ... < k_stages[nstages-1] = k, each clipped to the block's
+     min(rows, cols): a complete C-A run of size k_s then its nucleus rank r_s;
+     stop when r_s < k_s - rank_margin or at the largest size, else the next
+     stage starts from the stage's rows I followed by the block's initial rows
+     not in I (in order).  info[1], info[2] sum over the stages.               */
+  int32_t nstages;       /* 0 .. LRA_MAX_STAGES                                      */
+  int32_t rank_margin;   /* >= 0                                                     */
+  int32_t k_stages[8];   /* LRA_MAX_STAGES entries, the first nstages used           */
 } lra_ca_params;
+
+#define LRA_MAX_STAGES 8
 
 /* Outputs of one C-A CUR approximation W ~ C U R (all device, caller-owned). */
 typedef struct {
@@ -141,7 +162,7 @@ typedef struct {
   double* logvol;        /* 2*sweeps: log|det W'[I,J]| after each step (NaN if unrun) */
   int32_t* info;         /* LRA_INFO_LEN ints: numerical rank r, total swaps, loops run,
                             status, maxvol steps decided in FP32 (mixed mode), maxvol
-                            steps run in FP64, 0, 0                                    */
+                            steps run in FP64, generator size k used, stages run       */
 } lra_cur;
 
 #define LRA_INFO_LEN 8
@@ -222,14 +243,16 @@ typedef struct {
   int64_t max_len;         /* >= max over blocks of max(nrows, ncols); sizes the scratch  */
 } lra_batch;
 
-/* Outputs of a batch (device, caller-owned).  Block b has k_b = min(k, nrows,
- * ncols); its C_b (nrows x k_b) and R_b (k_b x ncols) are row-major at the
- * block's offsets; the other arrays have one fixed-size slot per block. */
+/* Outputs of a batch (device, caller-owned).  Block b has slots for k_b =
+ * min(k, nrows, ncols) generators and uses kf_b = info[b*LRA_INFO_LEN+6] of
+ * them (kf_b = k_b without stages); its C_b (nrows x kf_b) and R_b (kf_b x
+ * ncols) are row-major at the block's offsets (slots of nrows x k_b and
+ * k_b x ncols); the other arrays have one fixed-size slot per block. */
 typedef struct {
-  int32_t* I;              /* nb x k: rows (block-local), first k_b used                  */
+  int32_t* I;              /* nb x k: rows (block-local), first kf_b used                 */
   int32_t* J;              /* nb x k: columns (block-local)                               */
   double* C;               /* packed C_b                                                  */
-  double* U;               /* nb x k x k: U_b (k_b x k_b, row-major) at the slot start     */
+  double* U;               /* nb x k x k: U_b (kf_b x kf_b, row-major) at the slot start   */
   double* R;               /* packed R_b                                                  */
   double* logvol;          /* nb x 2*sweeps                                               */
   int32_t* info;           /* nb x LRA_INFO_LEN (as lra_cur.info)                          */
@@ -245,7 +268,10 @@ lra_status lra_ca_batched_workspace_size(const lra_problem* base, const lra_batc
  * and runs that block's C-A loop and nucleus alone, so the per-block results
  * are those of lra_ca_run on the block (same pivots, bit for bit).  k_b =
  * min(par->k, nrows, ncols); U_b truncates the core at par->rank_tol (adaptive
- * rank, info[b*4+0]).  Only dense and kernel inputs without multipliers.
+ * rank, info[0] of the block).  With par->nstages > 0 the generator size of
+ * each block is staged up to k_b as lra_ca_params describes (info[6] = the
+ * size used, info[7] = stages run).  Only dense and kernel inputs without
+ * multipliers.
  * I0: device, nb x par->k block-local initial rows (first k_b of each slot
  * used, distinct).  A block outside the input or larger than max_len gets
  * status LRA_ERR_INVALID_ARG in its info slot; the others still run.

@@ -34,6 +34,7 @@ LRA_DENSE, LRA_KERNEL_LAPLACE, LRA_KERNEL_GAUSSIAN = 0, 1, 2
 LRA_MULT_NONE, LRA_MULT_ARHT, LRA_MULT_SPARSE_PM1 = 0, 1, 2
 LRA_MODE_FP64, LRA_MODE_MIXED = 0, 1
 LRA_INFO_LEN = 8
+LRA_MAX_STAGES = 8
 
 _STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "NONFINITE", 4: "TIMEOUT", 5: "WORKSPACE",
            16: "WARN_RANK_DEFICIENT", 17: "WARN_NOT_CONVERGED"}
@@ -53,7 +54,8 @@ class _Problem(ct.Structure):
 
 class _Params(ct.Structure):
     _fields_ = [("k", ct.c_int32), ("sweeps", ct.c_int32), ("h", ct.c_double), ("rank_tol", ct.c_double),
-                ("max_swaps", ct.c_int32), ("mode", ct.c_int32)]
+                ("max_swaps", ct.c_int32), ("mode", ct.c_int32), ("nstages", ct.c_int32),
+                ("rank_margin", ct.c_int32), ("k_stages", ct.c_int32 * LRA_MAX_STAGES)]
 
 
 class _Batch(ct.Structure):
@@ -163,6 +165,7 @@ class Problem:
     X: Optional[torch.Tensor] = None
     Y: Optional[torch.Tensor] = None
     length_scale: float = 1.0
+    entries: str = "f64"
 
     @staticmethod
     def dense(W: torch.Tensor) -> "Problem":
@@ -172,10 +175,15 @@ class Problem:
         return Problem(LRA_DENSE, W.shape[0], W.shape[1], W=W)
 
     @staticmethod
-    def kernel(kind: str, X: torch.Tensor, Y: torch.Tensor, length_scale: float = 1.0) -> "Problem":
+    def kernel(kind: str, X: torch.Tensor, Y: torch.Tensor, length_scale: float = 1.0,
+               entries: str = "f64") -> "Problem":
+        """Kernel entries w_ij = K(x_i, y_j) evaluated on demand; ``entries``
+        'f32' evaluates the Laplace kernel in FP32 (correctly rounded ops)."""
         src = {"laplace": LRA_KERNEL_LAPLACE, "gaussian": LRA_KERNEL_GAUSSIAN}[kind]
+        if entries not in ("f64", "f32"):
+            raise ValueError("entries must be 'f64' or 'f32'")
         _dev(X, torch.float64, "X"); _dev(Y, torch.float64, "Y")
-        return Problem(src, X.shape[0], Y.shape[0], X=X, Y=Y, length_scale=length_scale)
+        return Problem(src, X.shape[0], Y.shape[0], X=X, Y=Y, length_scale=length_scale, entries=entries)
 
     def _c(self) -> _Problem:
         p = _Problem()
@@ -185,6 +193,7 @@ class Problem:
             p.W, p.ldw = self.W.data_ptr(), self.W.stride(0)
         if self.X is not None:
             p.X, p.Y = self.X.data_ptr(), self.Y.data_ptr()
+            p.dtype = LRA_F32 if self.entries == "f32" else LRA_F64
         p.length_scale = float(self.length_scale)
         return p
 
@@ -229,10 +238,17 @@ def lra_multiplier_destroy(mult: Multiplier) -> None:
         mult.handle = None
 
 
-def _params(k, sweeps, h, rank_tol, max_swaps, mode) -> _Params:
+def _params(k, sweeps, h, rank_tol, max_swaps, mode, stages=None, rank_margin=0) -> _Params:
     p = _Params()
     p.k, p.sweeps, p.h, p.rank_tol, p.max_swaps, p.mode = int(k), int(sweeps), float(h), float(rank_tol), \
         int(max_swaps), int(mode)
+    if stages is not None:
+        stages = [int(x) for x in stages]
+        if not 1 <= len(stages) <= LRA_MAX_STAGES:
+            raise ValueError(f"1..{LRA_MAX_STAGES} stages")
+        p.nstages, p.rank_margin = len(stages), int(rank_margin)
+        for i, v in enumerate(stages):
+            p.k_stages[i] = v
     return p
 
 
@@ -373,7 +389,11 @@ class Batch:
     launch kernels, so they can be captured in a CUDA graph."""
 
     def __init__(self, problem: Problem, blocks, k: int, sweeps: int, I0, h: float = 1.01, rank_tol: float = 1e-6,
-                 max_swaps: int = 1000, order="lpt", device=None, mode: int = LRA_MODE_FP64):
+                 max_swaps: int = 1000, order="lpt", device=None, mode: int = LRA_MODE_FP64, stages=None,
+                 rank_margin: int = 2):
+        """``stages``: ascending generator sizes ending at k (the size of each block is
+        fitted to its nucleus rank: a larger stage runs while rank >= size - rank_margin);
+        None runs every block at min(k, rows, cols)."""
         import numpy as np
         blocks = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64).reshape(-1, 4))
         nb = len(blocks)
@@ -387,7 +407,7 @@ class Batch:
             order = np.argsort(-(blocks[:, 1] * blocks[:, 3]), kind="stable").astype(np.int32)
         self.problem, self.k, self.sweeps, self.nb = problem, int(k), int(sweeps), nb
         self.blocks_np, self.offs_np, self.kb = blocks, offs, kb
-        self.params = _params(k, sweeps, h, rank_tol, max_swaps, mode)
+        self.params = _params(k, sweeps, h, rank_tol, max_swaps, mode, stages, rank_margin)
         t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
         self.blocks, self.offs = t(blocks, np.int64), t(offs, np.int64)
         self.order = None if order is None else t(order, np.int32)
@@ -415,15 +435,16 @@ class Batch:
 
     def block(self, b: int) -> dict:
         """Host copies of block b's results (for checks)."""
-        kb, (r0, nr, c0, nc) = int(self.kb[b]), self.blocks_np[b]
+        (r0, nr, c0, nc) = self.blocks_np[b]
         oc, orr = self.offs_np[b]
         o = {key: v.cpu().numpy() for key, v in self.out.items()}
         info = o["info"][b]
+        kb = int(info[6]) if info[6] > 0 else int(self.kb[b])
         return dict(I=o["I"][b, :kb], J=o["J"][b, :kb], C=o["C"][oc:oc + nr * kb].reshape(nr, kb),
                     U=o["U"][b].reshape(-1)[:kb * kb].reshape(kb, kb),
                     R=o["R"][orr:orr + kb * nc].reshape(kb, nc), logvol=o["logvol"][b],
                     rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]), status=int(info[3]),
-                    fp32_steps=int(info[4]), fp64_steps=int(info[5]))
+                    fp32_steps=int(info[4]), fp64_steps=int(info[5]), k=kb, stages=int(info[7]))
 
 
 def lra_ca_run_batched(batch: Batch, stream=None) -> None:
@@ -435,12 +456,17 @@ def lra_ca_run_batched(batch: Batch, stream=None) -> None:
 
 
 def lra_residual_sample_batched(batch: Batch, Q: torch.Tensor, S: torch.Tensor, stats: Optional[torch.Tensor] = None,
-                                stream=None) -> torch.Tensor:
-    """Per-block residual sample statistics (nb x 5) of a batched run; Q (nb x q), S (nb x s) device int32."""
+                                stream=None, problem: Optional[Problem] = None) -> torch.Tensor:
+    """Per-block residual sample statistics (nb x 5) of a batched run; Q (nb x q), S (nb x s) device int32.
+    ``problem`` (default: the batch's) gives the entries the residual is measured against, e.g. the
+    FP64 kernel for a run on FP32 entries."""
     L = _load()
     if stats is None:
         stats = torch.empty(batch.nb, 5, dtype=torch.float64, device=batch.blocks.device)
-    _check(L.lra_residual_sample_batched(ct.byref(batch.pc), ct.byref(batch.cb), batch.k, ct.byref(batch.cur),
+    pc = batch.pc if problem is None else problem._c()
+    if problem is not None and (problem.m, problem.n) != (batch.problem.m, batch.problem.n):
+        raise ValueError("residual problem must have the batch problem's shape")
+    _check(L.lra_residual_sample_batched(ct.byref(pc), ct.byref(batch.cb), batch.k, ct.byref(batch.cur),
                                          _dev(Q, torch.int32, "Q").data_ptr(), Q.shape[1],
                                          _dev(S, torch.int32, "S").data_ptr(), S.shape[1], stats.data_ptr(),
                                          _stream(stream)), "lra_residual_sample_batched")

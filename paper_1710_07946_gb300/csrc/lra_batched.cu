@@ -39,12 +39,15 @@ struct BatchArgs {
   int32_t cap_ldm;          // largest strip length kept in shared memory
   int64_t max_len;          // largest block dimension the scratch was sized for
   int32_t mixed;
+  int32_t nstages, margin;  // staged generator sizes (0: one run of size k_b)
+  int32_t stages[LRA_MAX_STAGES];
 };
 
 template <bool MIXED>
 __global__ void __launch_bounds__(NT) ca_batched_kernel(BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_b;
+  __shared__ int32_t s_I0[KMAX];
   double* G = B.scratch + (size_t)blockIdx.x * B.scratch_stride;
   double* gstrip = G + (size_t)B.kmax * B.kmax;
   for (;;) {
@@ -75,8 +78,7 @@ __global__ void __launch_bounds__(NT) ca_batched_kernel(BatchArgs B) {
       A.P.X = B.base.X + 3 * r0;
       A.P.Y = B.base.Y + 3 * c0;
     }
-    const int k = (int)min((int64_t)B.kmax, min(nr, nc));
-    A.k = k;
+    const int kb = (int)min((int64_t)B.kmax, min(nr, nc));
     A.sweeps = B.sweeps;
     A.max_swaps = B.max_swaps;
     A.h = B.h;
@@ -98,16 +100,46 @@ __global__ void __launch_bounds__(NT) ca_batched_kernel(BatchArgs B) {
       A.P.Y32 = B.base.Y32 + 3 * c0;
     }
     A.gstrip = A.strip_in_smem ? nullptr : gstrip;
-    const CaSmem S = ca_smem_carve(smem, k, A.ldm, A.strip_in_smem ? nullptr : gstrip);
-    ca_loop<SoloGroup, MIXED>(SoloGroup{}, A, S);
-    __syncthreads();
-    const int st = info[3];
-    if (!(st != LRA_OK && st < 16)) {
-      const int r = nucleus_cta(G, k, B.rank_tol, B.U + (size_t)b * B.kmax * B.kmax, smem);
-      if (threadIdx.x == 0) {
-        info[0] = r;
-        if (r < k && st == LRA_OK) info[3] = LRA_WARN_RANK_DEFICIENT;
+    // Generator sizes: the caller's stages clipped to kb (one run of size kb
+    // without stages).  Each stage is a complete C-A run and nucleus; the next
+    // stage starts from this stage's rows, then the block's unused initial rows.
+    const int32_t* I0b = B.I0 + (size_t)b * B.kmax;
+    int stage = 0, k = B.nstages > 0 ? min(B.stages[0], kb) : kb;
+    int swaps = 0, loops = 0, n32 = 0, n64 = 0, nrun = 0, r = 0, st = LRA_OK;
+    for (;;) {
+      A.k = k;
+      A.I0 = (nrun == 0) ? I0b : s_I0;
+      const CaSmem S = ca_smem_carve(smem, k, A.ldm, A.strip_in_smem ? nullptr : gstrip);
+      ca_loop<SoloGroup, MIXED>(SoloGroup{}, A, S);
+      __syncthreads();
+      ++nrun;
+      st = info[3];
+      swaps += info[1]; loops += info[2]; n32 += info[4]; n64 += info[5];
+      if (st != LRA_OK && st < 16) break;
+      r = nucleus_cta(G, k, B.rank_tol, B.U + (size_t)b * B.kmax * B.kmax, smem);
+      if (r < k && st == LRA_OK) st = LRA_WARN_RANK_DEFICIENT;
+      if (k >= kb || r < k - B.margin) break;
+      int kn = k;
+      while (stage + 1 < B.nstages && kn <= k) kn = min(B.stages[++stage], kb);
+      if (kn <= k) break;
+      if (threadIdx.x == 0) {           // next initial rows: I, then unused I0b rows in order
+        for (int a = 0; a < k; ++a) s_I0[a] = A.I[a];
+        int c = k;
+        for (int t = 0; t < kb && c < kn; ++t) {
+          const int32_t v = I0b[t];
+          bool in = false;
+          for (int a = 0; a < k; ++a) in |= (s_I0[a] == v);
+          if (!in) s_I0[c++] = v;
+        }
       }
+      __syncthreads();
+      k = kn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      info[0] = (st != LRA_OK && st < 16) ? 0 : r;
+      info[1] = swaps; info[2] = loops; info[3] = st;
+      info[4] = n32; info[5] = n64; info[6] = k; info[7] = nrun;
     }
     __syncthreads();
   }
@@ -134,7 +166,8 @@ __global__ void __launch_bounds__(256) resid_batched_kernel(DevProblem base, con
       if (threadIdx.x < 5) st[threadIdx.x] = __longlong_as_double(0x7ff8000000000000ll);
       continue;
     }
-    const int k = (int)min((int64_t)kmax, min(nr, nc));
+    const int kf = info[LRA_INFO_LEN * (size_t)b + 6];
+    const int k = (kf > 0) ? kf : (int)min((int64_t)kmax, min(nr, nc));
     const double* Cb = C + offs[2 * (size_t)b];
     const double* Rb = R + offs[2 * (size_t)b + 1];
     const double* Ub = U + (size_t)b * kmax * kmax;
@@ -249,7 +282,7 @@ static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int6
   size_t smem = std::max(ca_need(kmax, cap, true), nucleus_smem_bytes(kmax));
   if (max_len > cap) smem = std::max(smem, ca_need(kmax, (int)max_len, false));
   if (smem > budget) return LRA_ERR_INVALID_ARG;
-  const bool mixed = par->mode == LRA_MODE_MIXED && P.src != LRA_KERNEL_GAUSSIAN;
+  const bool mixed = par->mode == LRA_MODE_MIXED && mixed_supported(P);
   auto kern = mixed ? ca_batched_kernel<true> : ca_batched_kernel<false>;
   LRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
@@ -262,7 +295,7 @@ static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int6
   pl->scratch_stride = align_up(pl->scratch_stride, 32);
   pl->off_pts = align_up(256 + sizeof(double) * pl->scratch_stride * pl->grid, 256);
   pl->bytes = pl->off_pts;
-  if (par->mode == LRA_MODE_MIXED && P.src == LRA_KERNEL_LAPLACE)
+  if (mixed && P.src == LRA_KERNEL_LAPLACE)
     pl->bytes = align_up(pl->off_pts + sizeof(float) * 3 * (size_t)(P.m + P.n), 256);
   return LRA_OK;
 }
@@ -298,7 +331,7 @@ lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, c
     return LRA_ERR_INVALID_ARG;
   if (par->k < 1 || par->k > KMAX || par->sweeps < 1 || par->max_swaps < 0 || !(par->h >= 1.0) ||
       !(par->h < 1e300) || !(par->rank_tol >= 0.0) || !(par->rank_tol < 1.0) ||
-      (par->mode != LRA_MODE_FP64 && par->mode != LRA_MODE_MIXED))
+      (par->mode != LRA_MODE_FP64 && par->mode != LRA_MODE_MIXED) || !stages_valid(par))
     return LRA_ERR_INVALID_ARG;
   if (!out->I || !out->J || !out->C || !out->U || !out->R || !out->logvol || !out->info) return LRA_ERR_INVALID_ARG;
   BatchPlan pl;
@@ -331,7 +364,10 @@ lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, c
   A.scratch_stride = pl.scratch_stride;
   A.cap_ldm = pl.cap_ldm;
   A.max_len = batch->max_len;
-  A.mixed = (par->mode == LRA_MODE_MIXED && P.src != LRA_KERNEL_GAUSSIAN) ? 1 : 0;
+  A.mixed = (par->mode == LRA_MODE_MIXED && mixed_supported(P)) ? 1 : 0;
+  A.nstages = par->nstages;
+  A.margin = par->rank_margin;
+  for (int s = 0; s < par->nstages; ++s) A.stages[s] = par->k_stages[s];
   if (A.mixed && P.src == LRA_KERNEL_LAPLACE) {
     float* X32 = reinterpret_cast<float*>(ws + pl.off_pts);
     A.base.X32 = X32;

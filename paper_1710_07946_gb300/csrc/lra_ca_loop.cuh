@@ -3,7 +3,7 @@
 // early stop), then the outputs C, R, I, J, the core G and the volume trace.
 // Each maxvol step tries the FP32 certified path first when the group is one
 // CTA and the run is in mixed mode, and otherwise (or on a fallback) the FP64
-// path.
+// path; after a fallback the run's remaining steps go straight to FP64.
 #pragma once
 
 #include <type_traits>
@@ -17,7 +17,9 @@ template <class Group, bool MIXED>
 __device__ StepResult run_step(const Group& grp, const CaArgs& A, const CaSmem& S, int phase, bool cold,
                                int32_t* Jsel, unsigned long long& seq, bool lead, int& n32, int& n64) {
   if constexpr (MIXED && std::is_same<Group, SoloGroup>::value) {
-    {
+    // every FP64 step of a mixed run is a fallback: after the first one the run
+    // stays in FP64 (the FP32 attempt would only add its cost)
+    if (n64 == 0) {
       const MixedStep m = maxvol_step_mixed(A, S, phase, cold, Jsel, lead);
       if (!m.fallback) {
         ++n32;
@@ -71,7 +73,7 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
   if (err != LRA_OK) {
     if (lead && tid == 0) {
       A.info[0] = 0; A.info[1] = total; A.info[2] = loops; A.info[3] = err;
-      A.info[4] = n32; A.info[5] = n64; A.info[6] = 0; A.info[7] = 0;
+      A.info[4] = n32; A.info[5] = n64; A.info[6] = k; A.info[7] = 1;
     }
     return;
   }
@@ -98,7 +100,7 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
     for (int a = tid; a < k; a += nt) { A.I[a] = S.Is[a]; A.J[a] = S.Js[a]; }
     if (tid == 0) {
       A.info[0] = 0; A.info[1] = total; A.info[2] = loops; A.info[3] = status;
-      A.info[4] = n32; A.info[5] = n64; A.info[6] = 0; A.info[7] = 0;
+      A.info[4] = n32; A.info[5] = n64; A.info[6] = k; A.info[7] = 1;
     }
   }
 }

@@ -61,7 +61,12 @@ __device__ __forceinline__ double w_entry(const DevProblem& P, int64_t i, int64_
   double dy = __ldg(x + 1) - __ldg(y + 1);
   double dz = __ldg(x + 2) - __ldg(y + 2);
   double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-  if (P.src == LRA_KERNEL_LAPLACE) return 1.0 / sqrt(r2);
+  if (P.src == LRA_KERNEL_LAPLACE) {
+    // FP32 entries: the FP64 squared distance rounded to FP32, then a correctly
+    // rounded FP32 square root and reciprocal (the FP32 pipe instead of FP64)
+    if (P.dtype == LRA_F32) return (double)__fdiv_rn(1.0f, __fsqrt_rn(__double2float_rn(r2)));
+    return 1.0 / sqrt(r2);
+  }
   return exp(-(r2 / (2.0 * P.ell * P.ell)));
 }
 

@@ -44,4 +44,22 @@ lra_status current_device_info(DeviceInfo* info);
 
 inline size_t align_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
 
+// Staged generator sizes of lra_ca_params: none, or ascending sizes >= 1 that
+// end at par->k, with a margin >= 0.
+inline bool stages_valid(const lra_ca_params* par) {
+  if (par->nstages == 0) return true;
+  if (par->nstages < 0 || par->nstages > LRA_MAX_STAGES || par->rank_margin < 0) return false;
+  for (int s = 0; s < par->nstages; ++s) {
+    if (par->k_stages[s] < 1) return false;
+    if (s > 0 && par->k_stages[s] <= par->k_stages[s - 1]) return false;
+  }
+  return par->k_stages[par->nstages - 1] == par->k;
+}
+
+// Inputs whose maxvol steps the certified FP32 mode handles: dense inputs and
+// the FP64 Laplace kernel (its FP32 bounds are relative to the FP64 entries).
+inline bool mixed_supported(const DevProblem& P) {
+  return P.src == LRA_DENSE || (P.src == LRA_KERNEL_LAPLACE && P.dtype == LRA_F64);
+}
+
 }  // namespace lra

@@ -13,7 +13,8 @@ def to_device(p: li.Problem):
         prob = lra.Problem.dense(torch.from_numpy(np.ascontiguousarray(p.W)).to(dev))
     else:
         kind = "laplace" if p.src == li.SRC_LAPLACE else "gaussian"
-        prob = lra.Problem.kernel(kind, torch.from_numpy(p.X).to(dev), torch.from_numpy(p.Y).to(dev), p.ell)
+        prob = lra.Problem.kernel(kind, torch.from_numpy(p.X).to(dev), torch.from_numpy(p.Y).to(dev), p.ell,
+                                  entries=p.entries)
     mult = None
     if p.mkind == li.MULT_ARHT:
         mult = lra.lra_precondition("arht", p.n, p.depth, p.perm, p.dsign)

@@ -41,10 +41,60 @@ def run_batch(p, blocks, k, sweeps, rank_tol, seed=0, check=None):
         if p.src == li.SRC_DENSE:
             sub = li.Problem(li.SRC_DENSE, int(nr), int(nc), W=np.ascontiguousarray(p.W[r0:r0 + nr, c0:c0 + nc]))
         else:
-            sub = li.Problem(p.src, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], ell=p.ell)
+            sub = li.Problem(p.src, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], ell=p.ell,
+                             entries=p.entries)
         o = oracle.ca_run(sub, kb, sweeps, I0[b, :kb], rank_tol=rank_tol)
         check_block(o, bt.block(b))
     return bt, I0
+
+
+def run_batch_staged(p, blocks, stages, margin, sweeps, rank_tol, seed=0, check=None):
+    """Batched run with staged generator sizes; blocks checked against the oracle's
+    staged run (final size, stage count, pivots, factors, counters)."""
+    import paper_1710_07946_gb300 as lra
+    prob, _ = to_device(p)
+    kmax = stages[-1]
+    I0 = li.block_initial_rows(blocks, kmax, seed)
+    bt = lra.Batch(prob, blocks, kmax, sweeps, I0, rank_tol=rank_tol, stages=stages, rank_margin=margin)
+    lra.lra_ca_run_batched(bt)
+    torch.cuda.synchronize()
+    idx = range(len(blocks)) if check is None else check
+    for b in idx:
+        r0, nr, c0, nc = blocks[b]
+        if p.src == li.SRC_DENSE:
+            sub = li.Problem(li.SRC_DENSE, int(nr), int(nc), W=np.ascontiguousarray(p.W[r0:r0 + nr, c0:c0 + nc]))
+        else:
+            sub = li.Problem(p.src, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], ell=p.ell,
+                             entries=p.entries)
+        o = oracle.ca_run_adaptive(sub, stages, margin, sweeps, I0[b], rank_tol=rank_tol)
+        g = bt.block(b)
+        assert (g["k"], g["stages"]) == (o["k"], o["stages"]), (b, g["k"], o["k"], g["stages"], o["stages"])
+        check_block(o, g)
+    return bt, I0
+
+
+def test_staged_sizes_fmm_blocks():
+    """Generator sizes 28, 40, 64 (margin 2) fitted per block to the nucleus rank:
+    every block equals the oracle's staged run, bit for bit in the pivots."""
+    p, blocks, lev = li.fmm_blocks(npts=1 << 15, leaf=64, min_size=64, max_size=2048, nblocks=96, seed=2)
+    bt, _ = run_batch_staged(p, blocks, (28, 40, 64), 2, 3, 1e-6)
+    info = bt.out["info"].cpu().numpy()
+    assert set(info[:, 6]) <= {28, 40, 64} and info[:, 7].max() >= 2      # some blocks grew
+
+
+def test_staged_sizes_dense_low_rank_and_small_blocks():
+    """Dense blocks of exact rank 12 (some smaller than the stages): stages 8, 16, 32
+    with margin 2 stop at 16; blocks below a stage size are clipped."""
+    p = li.factor_gaussian(1200, 12, 0.0, seed=4)
+    blocks = li.dense_blocks(1200, sizes=(5, 12, 15, 40, 300), seed=2)
+    run_batch_staged(p, blocks, (8, 16, 32), 2, 3, 1e-9)
+
+
+def test_staged_sizes_fmm_benchmark_workload_sampled_blocks():
+    p, blocks, lev = li.fmm_blocks(npts=1 << 20, seed=0)
+    sizes = blocks[:, 1] * blocks[:, 3]
+    pick = list(np.argsort(sizes)[:3]) + list(np.argsort(sizes)[-2:])
+    run_batch_staged(p, blocks, (28, 40, 64), 2, 3, 1e-6, check=pick)
 
 
 def test_dense_blocks_of_mixed_sizes():
@@ -57,6 +107,24 @@ def test_laplace_fmm_blocks_small_tree():
     p, blocks, lev = li.fmm_blocks(npts=1 << 15, leaf=64, min_size=64, max_size=2048, nblocks=96, seed=2)
     assert len(blocks) > 20
     run_batch(p, blocks, 32, 3, 1e-6)
+
+
+def test_laplace_fmm_blocks_f32_entries():
+    """FP32 kernel entries, FP64 pivots and nucleus: every block equals the oracle run
+    on the same FP32 entries, and the largest residual sampled against the FP64
+    entries stays within twice the FP64 run's plus the FP32 perturbation."""
+    import paper_1710_07946_gb300 as lra
+    p, blocks, lev = li.fmm_blocks(npts=1 << 15, leaf=64, min_size=64, max_size=2048, nblocks=96, seed=2)
+    p32 = li.Problem(p.src, p.m, p.n, X=p.X, Y=p.Y, entries="f32")
+    bt32, I0 = run_batch(p32, blocks, 32, 3, 1e-6)
+    prob64, _ = to_device(p)
+    bt64 = lra.Batch(prob64, blocks, 32, 3, I0, rank_tol=1e-6)
+    lra.lra_ca_run_batched(bt64)
+    Q, S = li.block_sample_positions(blocks, 32, 32, 5)
+    Qd, Sd = torch.from_numpy(Q).cuda(), torch.from_numpy(S).cuda()
+    e32 = lra.lra_residual_sample_batched(bt32, Qd, Sd, problem=prob64).cpu().numpy()[:, 4]
+    e64 = lra.lra_residual_sample_batched(bt64, Qd, Sd).cpu().numpy()[:, 4]
+    assert e32.max() <= 2 * e64.max() + 2.0 ** -22, (e32.max(), e64.max())
 
 
 def test_invalid_block_is_isolated():
