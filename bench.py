@@ -135,6 +135,9 @@ class FmmWorkload:
         prob64 = lra.Problem.kernel("laplace", X, X)
         bt = lra.Batch(prob, h["blocks"], self.k, self.sweeps, h["I0"], rank_tol=self.tol, stages=self.stages,
                        rank_margin=self.margin)
+        tuned = lra.lra_ca_batched_tune(bt, reps=2)          # untimed set-up: CTA shape autotuner
+        self.tuned = {"chosen": f"{bt.cb.cta_threads}x{bt.cb.ctas_per_sm}",
+                      "ms": {f"{t}x{c}": round(v, 3) for (t, c), v in tuned.items()}}
         d = dict(X=X, prob=prob, prob64=prob64, bt=bt, Q=torch.from_numpy(h["Q"]).to(dev),
                  S=torch.from_numpy(h["S"]).to(dev))
         d["stats"] = torch.empty(len(h["blocks"]), 5, dtype=torch.float64, device=dev)
@@ -163,7 +166,7 @@ class FmmWorkload:
 
     def extra(self, res):
         info, err = res["info"], res["err"]
-        return {"rank_min_median_max": [int(info[:, 0].min()), int(np.median(info[:, 0])), int(info[:, 0].max())],
+        return {"cta_shape_tuner": getattr(self, "tuned", None),"rank_min_median_max": [int(info[:, 0].min()), int(np.median(info[:, 0])), int(info[:, 0].max())],
                 "generator_size_hist": {int(k): int(c) for k, c in zip(*np.unique(info[:, 6], return_counts=True))},
                 "swaps_mean": float(info[:, 1].mean()), "loops_hist": np.bincount(info[:, 2]).tolist(),
                 "rel_fro_err_sampled_median": float(np.median(err)), "rel_fro_err_sampled_max": float(err.max()),

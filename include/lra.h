@@ -241,6 +241,9 @@ typedef struct {
                               taken from the work queue; largest first balances the tail */
   int32_t nb;              /* number of blocks >= 1                                       */
   int64_t max_len;         /* >= max over blocks of max(nrows, ncols); sizes the scratch  */
+  int32_t cta_threads;     /* CTA shape of the batched kernel: threads per CTA and CTAs  */
+  int32_t ctas_per_sm;     /* per SM, one of lra_ca_batched_shapes (0, 0: the library's
+                              default 256 x 2; lra_ca_batched_tune picks the fastest)    */
 } lra_batch;
 
 /* Outputs of a batch (device, caller-owned).  Block b has slots for k_b =
@@ -258,7 +261,8 @@ typedef struct {
   int32_t* info;           /* nb x LRA_INFO_LEN (as lra_cur.info)                          */
 } lra_cur_batch;
 
-/* Workspace bytes of lra_ca_run_batched (params: par->k is the largest rank). */
+/* Workspace bytes of lra_ca_run_batched (params: par->k is the largest rank),
+ * enough for every CTA shape that can hold the batch. */
 lra_status lra_ca_batched_workspace_size(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
                                          size_t* bytes);
 
@@ -280,6 +284,31 @@ lra_status lra_ca_batched_workspace_size(const lra_problem* base, const lra_batc
 lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
                               const int32_t* I0, const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
                               lra_stream_t stream);
+
+/*
+ * lra_ca_batched_shapes -- the CTA shapes the batched kernel is built for:
+ * writes up to cap (threads per CTA, CTAs per SM) pairs and returns their
+ * number.  Each shape holds 16 warps per SM (128 registers a thread); they
+ * trade parallelism inside one block for overlap between blocks.
+ */
+int32_t lra_ca_batched_shapes(int32_t* threads, int32_t* ctas_per_sm, int32_t cap);
+
+/*
+ * lra_ca_batched_tune -- autotuner of lra_ca_run_batched (no counterpart in the
+ * paper): runs the whole batch reps times in each CTA shape, timing each launch
+ * with CUDA events on the stream, and returns the fastest shape in
+ * *cta_threads, *ctas_per_sm (store them in lra_batch for later calls) and, if
+ * ms is not NULL, the fastest time of every shape (lra_ca_batched_shapes
+ * order; -1 for a shape whose shared-memory share cannot hold the batch's
+ * largest block at par->k, which is skipped).  Every shape computes the same
+ * results, left in out.  Blocks the
+ * calling thread until the stream has run the launches; not capturable.
+ * Arguments and errors as lra_ca_run_batched; reps >= 1.
+ */
+lra_status lra_ca_batched_tune(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                               const int32_t* I0, const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
+                               lra_stream_t stream, int32_t reps, int32_t* cta_threads, int32_t* ctas_per_sm,
+                               float* ms);
 
 /*
  * lra_residual_sample_batched -- the a-posteriori sample of lra_residual_sample

@@ -60,7 +60,7 @@ class _Params(ct.Structure):
 
 class _Batch(ct.Structure):
     _fields_ = [("blocks", ct.c_void_p), ("offsets", ct.c_void_p), ("order", ct.c_void_p), ("nb", ct.c_int32),
-                ("max_len", ct.c_int64)]
+                ("max_len", ct.c_int64), ("cta_threads", ct.c_int32), ("ctas_per_sm", ct.c_int32)]
 
 
 class _CurBatch(ct.Structure):
@@ -108,6 +108,9 @@ def _load():
     L.lra_ca_batched_workspace_size.argtypes = [P, PB, PP, ct.POINTER(sz)]
     L.lra_ca_run_batched.argtypes = [P, PB, PP, vp, PCB, vp, sz, vp]
     L.lra_residual_sample_batched.argtypes = [P, PB, i32, PCB, vp, i32, vp, i32, vp, vp]
+    L.lra_ca_batched_tune.argtypes = [P, PB, PP, vp, PCB, vp, sz, vp, i32, ct.POINTER(i32), ct.POINTER(i32), vp]
+    L.lra_ca_batched_shapes.argtypes = [vp, vp, i32]
+    L.lra_ca_batched_shapes.restype = i32
     PG = ct.POINTER(_Gauss)
     L.lra_gauss_cur_forward.argtypes = [PG, vp, i32, vp, vp, vp]
     L.lra_gauss_cur_backward.argtypes = [PG, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
@@ -120,6 +123,7 @@ def _load():
               "lra_cur_apply", "lra_cur_apply_workspace_size", "lra_residual_sample",
               "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect",
               "lra_ca_batched_workspace_size", "lra_ca_run_batched", "lra_residual_sample_batched",
+              "lra_ca_batched_tune",
               "lra_gauss_cur_forward", "lra_gauss_cur_backward"):
         getattr(L, f).restype = ct.c_int
     _lib = L
@@ -445,6 +449,30 @@ class Batch:
                     R=o["R"][orr:orr + kb * nc].reshape(kb, nc), logvol=o["logvol"][b],
                     rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]), status=int(info[3]),
                     fp32_steps=int(info[4]), fp64_steps=int(info[5]), k=kb, stages=int(info[7]))
+
+
+def lra_ca_batched_shapes() -> list:
+    """The (threads per CTA, CTAs per SM) shapes the batched kernel is built for."""
+    L = _load()
+    t = (ct.c_int32 * 16)(); c = (ct.c_int32 * 16)()
+    n = L.lra_ca_batched_shapes(t, c, 16)
+    return [(t[i], c[i]) for i in range(min(n, 16))]
+
+
+def lra_ca_batched_tune(batch: Batch, reps: int = 2, stream=None) -> dict:
+    """Autotuner: times the whole batch in every CTA shape, stores the fastest in
+    ``batch`` (later lra_ca_run_batched calls use it) and returns
+    {(threads, ctas): ms}.  Synchronises the stream."""
+    L = _load()
+    shapes = lra_ca_batched_shapes()
+    ms = (ct.c_float * len(shapes))()
+    th, cs = ct.c_int32(), ct.c_int32()
+    _check(L.lra_ca_batched_tune(ct.byref(batch.pc), ct.byref(batch.cb), ct.byref(batch.params),
+                                 batch.I0.data_ptr(), ct.byref(batch.cur), batch.workspace.data_ptr(),
+                                 batch.workspace.numel(), _stream(stream), int(reps), ct.byref(th), ct.byref(cs), ms),
+           "lra_ca_batched_tune")
+    batch.cb.cta_threads, batch.cb.ctas_per_sm = th.value, cs.value
+    return {shp: ms[i] for i, shp in enumerate(shapes) if ms[i] >= 0}
 
 
 def lra_ca_run_batched(batch: Batch, stream=None) -> None:

@@ -1,149 +1,15 @@
 // lra_batched.cu -- many independent C-A CUR approximations (the generators of
-// the neutered block columns of an HSS / FMM matrix) in one persistent launch.
-//
-// Each CTA takes blocks from a device work queue (one atomic counter; the
-// caller's processing order, largest blocks first for a balanced tail) and
-// runs the whole C-A loop of a block, then its nucleus, on its own: the block's
-// strips sit in the CTA's shared memory when they fit, otherwise in the CTA's
-// slice of a global scratch area.  The per-block arithmetic is the single-CTA
-// path of lra_ca_run, operation for operation.  A second kernel draws the
-// a-posteriori residual sample of every block.
+// the neutered block columns of an HSS / FMM matrix) in one persistent launch:
+// the launch plan per CTA shape, the autotuner over the shapes, and the
+// batched residual sample.  The kernel itself is in lra_batched_kernel.cuh.
 #include <algorithm>
 #include <cstring>
 
-#include "lra_ca_loop.cuh"
+#include "lra_batched_kernel.cuh"
 #include "lra_internal.h"
-#include "lra_nucleus.cuh"
 #include "lra_profile.h"
 
 namespace lra {
-
-struct BatchArgs {
-  DevProblem base;
-  const int64_t* blocks;    // nb x 4: row0, nrows, col0, ncols
-  const int64_t* offs;      // nb x 2: offsets (in doubles) of C_b and R_b
-  const int32_t* order;     // processing order (nb) or null
-  int32_t nb, kmax, sweeps, max_swaps;
-  double h, rank_tol;
-  const int32_t* I0;        // nb x kmax initial rows (block-local)
-  int32_t* I;               // nb x kmax
-  int32_t* J;               // nb x kmax
-  double* C;                // packed
-  double* R;                // packed
-  double* U;                // nb x kmax x kmax (k_b x k_b at the start of each slot)
-  double* logvol;           // nb x 2 sweeps
-  int32_t* info;            // nb x LRA_INFO_LEN
-  unsigned int* counter;    // work queue head
-  double* scratch;          // per CTA: G (kmax^2) then, if needed, a strip (kmax x max_len)
-  size_t scratch_stride;    // doubles per CTA
-  int32_t cap_ldm;          // largest strip length kept in shared memory
-  int64_t max_len;          // largest block dimension the scratch was sized for
-  int32_t mixed;
-  int32_t nstages, margin;  // staged generator sizes (0: one run of size k_b)
-  int32_t stages[LRA_MAX_STAGES];
-};
-
-template <bool MIXED>
-__global__ void __launch_bounds__(NT) ca_batched_kernel(BatchArgs B) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_b;
-  __shared__ int32_t s_I0[KMAX];
-  double* G = B.scratch + (size_t)blockIdx.x * B.scratch_stride;
-  double* gstrip = G + (size_t)B.kmax * B.kmax;
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const unsigned int q = atomicAdd(B.counter, 1u);
-      s_b = (q < (unsigned)B.nb) ? (B.order ? B.order[q] : (int)q) : -1;
-    }
-    __syncthreads();
-    const int b = s_b;
-    __syncthreads();
-    if (b < 0) break;
-    int32_t* info = B.info + LRA_INFO_LEN * (size_t)b;
-    const int64_t r0 = B.blocks[4 * (size_t)b], nr = B.blocks[4 * (size_t)b + 1];
-    const int64_t c0 = B.blocks[4 * (size_t)b + 2], nc = B.blocks[4 * (size_t)b + 3];
-    if (r0 < 0 || c0 < 0 || nr < 1 || nc < 1 || r0 + nr > B.base.m || c0 + nc > B.base.n || nr > B.max_len ||
-        nc > B.max_len) {
-      for (int e = threadIdx.x; e < LRA_INFO_LEN; e += blockDim.x) info[e] = (e == 3) ? LRA_ERR_INVALID_ARG : 0;
-      continue;
-    }
-    CaArgs A;
-    A.P = B.base;
-    A.P.m = nr;
-    A.P.n = nc;
-    if (A.P.src == LRA_DENSE) {
-      const size_t esz = (A.P.dtype == LRA_F32) ? 4 : 8;
-      A.P.W = static_cast<const unsigned char*>(B.base.W) + (size_t)(r0 * B.base.ldw + c0) * esz;
-    } else {
-      A.P.X = B.base.X + 3 * r0;
-      A.P.Y = B.base.Y + 3 * c0;
-    }
-    const int kb = (int)min((int64_t)B.kmax, min(nr, nc));
-    A.sweeps = B.sweeps;
-    A.max_swaps = B.max_swaps;
-    A.h = B.h;
-    A.I0 = B.I0 + (size_t)b * B.kmax;
-    A.I = B.I + (size_t)b * B.kmax;
-    A.J = B.J + (size_t)b * B.kmax;
-    A.C = B.C + B.offs[2 * (size_t)b];
-    A.R = B.R + B.offs[2 * (size_t)b + 1];
-    A.logvol = B.logvol + (size_t)b * 2 * B.sweeps;
-    A.info = info;
-    A.G = G;
-    A.chunk_n = (int)nc;
-    A.chunk_m = (int)nr;
-    A.ldm = (int)max(nr, nc);
-    A.strip_in_smem = A.ldm <= B.cap_ldm;
-    A.mixed = B.mixed;
-    if (B.mixed && A.P.src == LRA_KERNEL_LAPLACE) {
-      A.P.X32 = B.base.X32 + 3 * r0;
-      A.P.Y32 = B.base.Y32 + 3 * c0;
-    }
-    A.gstrip = A.strip_in_smem ? nullptr : gstrip;
-    // Generator sizes: the caller's stages clipped to kb (one run of size kb
-    // without stages).  Each stage is a complete C-A run and nucleus; the next
-    // stage starts from this stage's rows, then the block's unused initial rows.
-    const int32_t* I0b = B.I0 + (size_t)b * B.kmax;
-    int stage = 0, k = B.nstages > 0 ? min(B.stages[0], kb) : kb;
-    int swaps = 0, loops = 0, n32 = 0, n64 = 0, nrun = 0, r = 0, st = LRA_OK;
-    for (;;) {
-      A.k = k;
-      A.I0 = (nrun == 0) ? I0b : s_I0;
-      const CaSmem S = ca_smem_carve(smem, k, A.ldm, A.strip_in_smem ? nullptr : gstrip);
-      ca_loop<SoloGroup, MIXED>(SoloGroup{}, A, S);
-      __syncthreads();
-      ++nrun;
-      st = info[3];
-      swaps += info[1]; loops += info[2]; n32 += info[4]; n64 += info[5];
-      if (st != LRA_OK && st < 16) break;
-      r = nucleus_cta(G, k, B.rank_tol, B.U + (size_t)b * B.kmax * B.kmax, smem);
-      if (r < k && st == LRA_OK) st = LRA_WARN_RANK_DEFICIENT;
-      if (k >= kb || r < k - B.margin) break;
-      int kn = k;
-      while (stage + 1 < B.nstages && kn <= k) kn = min(B.stages[++stage], kb);
-      if (kn <= k) break;
-      if (threadIdx.x == 0) {           // next initial rows: I, then unused I0b rows in order
-        for (int a = 0; a < k; ++a) s_I0[a] = A.I[a];
-        int c = k;
-        for (int t = 0; t < kb && c < kn; ++t) {
-          const int32_t v = I0b[t];
-          bool in = false;
-          for (int a = 0; a < k; ++a) in |= (s_I0[a] == v);
-          if (!in) s_I0[c++] = v;
-        }
-      }
-      __syncthreads();
-      k = kn;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      info[0] = (st != LRA_OK && st < 16) ? 0 : r;
-      info[1] = swaps; info[2] = loops; info[3] = st;
-      info[4] = n32; info[5] = n64; info[6] = k; info[7] = nrun;
-    }
-    __syncthreads();
-  }
-}
 
 // Residual sample of every block: E_b[Q_b, S_b] = W_b[Q_b, S_b] - (C_b U_b)[Q_b, :] R_b[:, S_b]
 // and its statistics (mean, variance, mean |e|, max |e|, Frobenius ratio).
@@ -252,52 +118,79 @@ __global__ void __launch_bounds__(256) resid_batched_kernel(DevProblem base, con
 }
 
 struct BatchPlan {
+  int threads, ctas;        // CTA shape and CTAs per SM
   int grid;
-  int cap_ldm;
   size_t smem;
   size_t scratch_stride;
   size_t off_pts;
   size_t bytes;
 };
 
+// CTA shapes of the batched kernel: NTB threads x MINB CTAs per SM, 16 warps
+// per SM in each case (128 registers a thread fill the register file).  Fewer
+// threads per block and more blocks per SM trade the parallelism inside one
+// block for overlap between blocks (their barriers and FP64 latencies).
+struct BatchShape { int threads, ctas; };
+constexpr BatchShape kShapes[] = {{512, 1}, {256, 2}, {128, 4}};
+constexpr int kNumShapes = 3;
+
 static size_t ca_need(int k, int ldm, bool strip) {
   return ca_smem_fixed(k, ldm) + (strip ? sizeof(double) * (size_t)k * ldm : 0);
 }
 
-static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int64_t max_len, BatchPlan* pl) {
+static void* batched_kernel_ptr(bool mixed, int threads) {
+  if (threads == 512) return batched_kernel_512(mixed);
+  if (threads == 256) return batched_kernel_256(mixed);
+  return batched_kernel_128(mixed);
+}
+
+static bool shape_known(int threads, int ctas) {
+  for (int i = 0; i < kNumShapes; ++i)
+    if (kShapes[i].threads == threads && kShapes[i].ctas == ctas) return true;
+  return false;
+}
+
+static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int64_t max_len, int threads, int ctas,
+                             BatchPlan* pl) {
   const int32_t kmax = par->k;
   DeviceInfo dev;
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
-  const size_t budget = dev.smem_optin - 4096;
-  int cap = 0;
-  {
-    int lo = 0, hi = (int)std::min<int64_t>(max_len, 1 << 20);
-    while (lo < hi) {                       // largest ldm whose strip fits in shared memory
-      const int mid = (lo + hi + 1) / 2;
-      if (ca_need(kmax, mid, true) <= budget) lo = mid; else hi = mid - 1;
-    }
-    cap = lo;
-  }
-  size_t smem = std::max(ca_need(kmax, cap, true), nucleus_smem_bytes(kmax));
-  if (max_len > cap) smem = std::max(smem, ca_need(kmax, (int)max_len, false));
-  if (smem > budget) return LRA_ERR_INVALID_ARG;
+  int per_sm = 0;
+  LRA_CUDA_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev.device));
+  // per CTA: its share of the SM's shared memory, less the 1 KiB the hardware
+  // reserves per CTA and the kernel's static arrays
+  const size_t budget = std::min(dev.smem_optin, (size_t)per_sm / ctas - 1024) - 512;
+  const int ldm = (int)std::min<int64_t>(max_len, 1 << 30);
+  size_t smem = std::max(ca_need(kmax, ldm, true), nucleus_smem_bytes(kmax));
+  if (smem > budget) smem = budget;
+  if (ca_need(kmax, ldm, false) > smem || nucleus_smem_bytes(kmax) > smem) return LRA_ERR_INVALID_ARG;
   const bool mixed = par->mode == LRA_MODE_MIXED && mixed_supported(P);
-  auto kern = mixed ? ca_batched_kernel<true> : ca_batched_kernel<false>;
+  const void* kern = batched_kernel_ptr(mixed, threads);
   LRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
-  LRA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, smem));
+  LRA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
   if (occ < 1) return LRA_ERR_INVALID_ARG;
-  pl->grid = occ * dev.sms;
-  pl->cap_ldm = cap;
+  pl->threads = threads;
+  pl->ctas = std::min(occ, ctas);
+  pl->grid = pl->ctas * dev.sms;
   pl->smem = smem;
-  pl->scratch_stride = (size_t)kmax * kmax + (max_len > cap ? (size_t)kmax * max_len : 0);
+  // global strip scratch when the largest strip does not fit beside the fixed part
+  pl->scratch_stride = (size_t)kmax * kmax + (ca_need(kmax, ldm, true) > smem ? (size_t)kmax * max_len : 0);
   pl->scratch_stride = align_up(pl->scratch_stride, 32);
   pl->off_pts = align_up(256 + sizeof(double) * pl->scratch_stride * pl->grid, 256);
   pl->bytes = pl->off_pts;
   if (mixed && P.src == LRA_KERNEL_LAPLACE)
     pl->bytes = align_up(pl->off_pts + sizeof(float) * 3 * (size_t)(P.m + P.n), 256);
   return LRA_OK;
+}
+
+// The CTA shape a batch asks for (0, 0: the default, 512 x 1, which measured
+// fastest on the octree Laplace batch: the largest blocks keep the most threads).
+static void batch_shape(const lra_batch* batch, int* threads, int* ctas) {
+  *threads = batch->cta_threads;
+  *ctas = batch->ctas_per_sm;
+  if (*threads == 0 && *ctas == 0) { *threads = 512; *ctas = 1; }
 }
 
 }  // namespace lra
@@ -313,18 +206,29 @@ lra_status lra_ca_batched_workspace_size(const lra_problem* base, const lra_batc
   lra_status st = make_dev_problem(base, nullptr, &P);
   if (st != LRA_OK) return st;
   if (par->k < 1 || par->k > KMAX || batch->nb < 1 || batch->max_len < 1) return LRA_ERR_INVALID_ARG;
-  BatchPlan pl;
-  if ((st = batch_plan(P, par, batch->max_len, &pl)) != LRA_OK) return st;
-  *bytes = pl.bytes;
+  // enough for every CTA shape that can hold the batch (a shape whose shared
+  // memory share is too small for the largest block is left out), so that one
+  // workspace serves the tuner and any choice
+  size_t most = 0;
+  lra_status first = LRA_ERR_INVALID_ARG;
+  for (int i = 0; i < kNumShapes; ++i) {
+    BatchPlan pl;
+    st = batch_plan(P, par, batch->max_len, kShapes[i].threads, kShapes[i].ctas, &pl);
+    if (st == LRA_ERR_INVALID_ARG) continue;
+    if (st != LRA_OK) return st;
+    first = LRA_OK;
+    most = std::max(most, pl.bytes);
+  }
+  if (first != LRA_OK) return first;
+  *bytes = most;
   return LRA_OK;
 }
 
-lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
-                              const int32_t* I0, const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
-                              lra_stream_t stream_) {
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  DevProblem P;
-  lra_status st = make_dev_problem(base, nullptr, &P);
+namespace {
+
+lra_status batched_check(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par, const int32_t* I0,
+                         const lra_cur_batch* out, DevProblem* P) {
+  lra_status st = make_dev_problem(base, nullptr, P);
   if (st != LRA_OK) return st;
   if (batch == nullptr || par == nullptr || out == nullptr || I0 == nullptr) return LRA_ERR_INVALID_ARG;
   if (batch->blocks == nullptr || batch->offsets == nullptr || batch->nb < 1 || batch->max_len < 1)
@@ -334,8 +238,16 @@ lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, c
       (par->mode != LRA_MODE_FP64 && par->mode != LRA_MODE_MIXED) || !stages_valid(par))
     return LRA_ERR_INVALID_ARG;
   if (!out->I || !out->J || !out->C || !out->U || !out->R || !out->logvol || !out->info) return LRA_ERR_INVALID_ARG;
+  return LRA_OK;
+}
+
+lra_status batched_launch(const DevProblem& P, const lra_batch* batch, const lra_ca_params* par, const int32_t* I0,
+                          const lra_cur_batch* out, void* workspace, size_t workspace_bytes, cudaStream_t stream,
+                          int threads, int ctas) {
+  if (!shape_known(threads, ctas)) return LRA_ERR_INVALID_ARG;
   BatchPlan pl;
-  if ((st = batch_plan(P, par, batch->max_len, &pl)) != LRA_OK) return st;
+  lra_status st;
+  if ((st = batch_plan(P, par, batch->max_len, threads, ctas, &pl)) != LRA_OK) return st;
   if (workspace == nullptr || workspace_bytes < pl.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255u))
     return LRA_ERR_WORKSPACE;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
@@ -362,7 +274,7 @@ lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, c
   A.counter = reinterpret_cast<unsigned int*>(ws);
   A.scratch = reinterpret_cast<double*>(ws + 256);
   A.scratch_stride = pl.scratch_stride;
-  A.cap_ldm = pl.cap_ldm;
+  A.smem_bytes = pl.smem;
   A.max_len = batch->max_len;
   A.mixed = (par->mode == LRA_MODE_MIXED && mixed_supported(P)) ? 1 : 0;
   A.nstages = par->nstages;
@@ -378,10 +290,79 @@ lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, c
   LRA_CUDA_TRY(cudaMemsetAsync(ws, 0, 256, stream));
   {
     LaunchScope ls(stream, "ca_batched_kernel");
-    if (A.mixed) ca_batched_kernel<true><<<pl.grid, NT, pl.smem, stream>>>(A);
-    else ca_batched_kernel<false><<<pl.grid, NT, pl.smem, stream>>>(A);
+    const void* kern = batched_kernel_ptr(A.mixed != 0, pl.threads);
+    void* args[] = {&A};
+    LRA_CUDA_TRY(cudaLaunchKernel(kern, dim3(pl.grid), dim3(pl.threads), args, pl.smem, stream));
   }
   return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                              const int32_t* I0, const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
+                              lra_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  DevProblem P;
+  lra_status st = batched_check(base, batch, par, I0, out, &P);
+  if (st != LRA_OK) return st;
+  int threads, ctas;
+  batch_shape(batch, &threads, &ctas);
+  return batched_launch(P, batch, par, I0, out, workspace, workspace_bytes, stream, threads, ctas);
+}
+
+lra_status lra_ca_batched_tune(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                               const int32_t* I0, const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
+                               lra_stream_t stream_, int32_t reps, int32_t* cta_threads, int32_t* ctas_per_sm,
+                               float* ms) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  DevProblem P;
+  lra_status st = batched_check(base, batch, par, I0, out, &P);
+  if (st != LRA_OK) return st;
+  if (cta_threads == nullptr || ctas_per_sm == nullptr || reps < 1) return LRA_ERR_INVALID_ARG;
+  cudaEvent_t e0, e1;
+  LRA_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LRA_ERR_CUDA; }
+  float best = 0.f;
+  int bi = -1;
+  for (int i = 0; i < kNumShapes && st == LRA_OK; ++i) {
+    float fastest = 0.f;
+    BatchPlan pl;
+    const lra_status fit = batch_plan(P, par, batch->max_len, kShapes[i].threads, kShapes[i].ctas, &pl);
+    if (fit == LRA_ERR_INVALID_ARG) {           // this shape cannot hold the batch
+      if (ms != nullptr) ms[i] = -1.f;
+      continue;
+    }
+    if (fit != LRA_OK) { st = fit; break; }
+    for (int r = 0; r < reps && st == LRA_OK; ++r) {
+      if (cudaEventRecord(e0, stream) != cudaSuccess) { st = LRA_ERR_CUDA; break; }
+      st = batched_launch(P, batch, par, I0, out, workspace, workspace_bytes, stream, kShapes[i].threads,
+                          kShapes[i].ctas);
+      if (st != LRA_OK) break;
+      float t = 0.f;
+      if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) { st = LRA_ERR_CUDA; break; }
+      if (r == 0 || t < fastest) fastest = t;
+    }
+    if (st != LRA_OK) break;
+    if (ms != nullptr) ms[i] = fastest;
+    if (bi < 0 || fastest < best) { best = fastest; bi = i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LRA_OK) return st;
+  if (bi < 0) return LRA_ERR_INVALID_ARG;
+  *cta_threads = kShapes[bi].threads;
+  *ctas_per_sm = kShapes[bi].ctas;
+  return LRA_OK;
+}
+
+int32_t lra_ca_batched_shapes(int32_t* threads, int32_t* ctas, int32_t cap) {
+  for (int i = 0; i < kNumShapes && i < cap; ++i) {
+    if (threads) threads[i] = kShapes[i].threads;
+    if (ctas) ctas[i] = kShapes[i].ctas;
+  }
+  return kNumShapes;
 }
 
 lra_status lra_residual_sample_batched(const lra_problem* base, const lra_batch* batch, int32_t kmax,

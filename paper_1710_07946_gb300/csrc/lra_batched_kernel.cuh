@@ -1,0 +1,151 @@
+// lra_batched_kernel.cuh -- the persistent C-A kernel over a batch of blocks.
+//
+// Each CTA takes blocks from a device work queue (one atomic counter; the
+// caller's processing order, largest blocks first for a balanced tail) and
+// runs the whole C-A loop of a block, then its nucleus, on its own: the block's
+// strips sit in the CTA's shared memory when they fit, otherwise in the CTA's
+// slice of a global scratch area.  The per-block arithmetic is the single-CTA
+// path of lra_ca_run, operation for operation.  The kernel is built in one
+// translation unit per CTA shape (lra_batched_k*.cu).
+#pragma once
+
+#include "lra_ca_loop.cuh"
+#include "lra_nucleus.cuh"
+
+namespace lra {
+
+struct BatchArgs {
+  DevProblem base;
+  const int64_t* blocks;    // nb x 4: row0, nrows, col0, ncols
+  const int64_t* offs;      // nb x 2: offsets (in doubles) of C_b and R_b
+  const int32_t* order;     // processing order (nb) or null
+  int32_t nb, kmax, sweeps, max_swaps;
+  double h, rank_tol;
+  const int32_t* I0;        // nb x kmax initial rows (block-local)
+  int32_t* I;               // nb x kmax
+  int32_t* J;               // nb x kmax
+  double* C;                // packed
+  double* R;                // packed
+  double* U;                // nb x kmax x kmax (k_b x k_b at the start of each slot)
+  double* logvol;           // nb x 2 sweeps
+  int32_t* info;            // nb x LRA_INFO_LEN
+  unsigned int* counter;    // work queue head
+  double* scratch;          // per CTA: G (kmax^2) then, if needed, a strip (kmax x max_len)
+  size_t scratch_stride;    // doubles per CTA
+  size_t smem_bytes;        // dynamic shared memory per CTA: a stage's strip is kept
+                            // there when it fits with the fixed part
+  int64_t max_len;          // largest block dimension the scratch was sized for
+  int32_t mixed;
+  int32_t nstages, margin;  // staged generator sizes (0: one run of size k_b)
+  int32_t stages[LRA_MAX_STAGES];
+};
+
+// NTB threads per CTA, MINB CTAs per SM (NTB * MINB = 512: 128 registers a thread).
+template <bool MIXED, int NTB, int MINB>
+__global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_b;
+  __shared__ int32_t s_I0[KMAX];
+  double* G = B.scratch + (size_t)blockIdx.x * B.scratch_stride;
+  double* gstrip = G + (size_t)B.kmax * B.kmax;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned int q = atomicAdd(B.counter, 1u);
+      s_b = (q < (unsigned)B.nb) ? (B.order ? B.order[q] : (int)q) : -1;
+    }
+    __syncthreads();
+    const int b = s_b;
+    __syncthreads();
+    if (b < 0) break;
+    int32_t* info = B.info + LRA_INFO_LEN * (size_t)b;
+    const int64_t r0 = B.blocks[4 * (size_t)b], nr = B.blocks[4 * (size_t)b + 1];
+    const int64_t c0 = B.blocks[4 * (size_t)b + 2], nc = B.blocks[4 * (size_t)b + 3];
+    if (r0 < 0 || c0 < 0 || nr < 1 || nc < 1 || r0 + nr > B.base.m || c0 + nc > B.base.n || nr > B.max_len ||
+        nc > B.max_len) {
+      for (int e = threadIdx.x; e < LRA_INFO_LEN; e += blockDim.x) info[e] = (e == 3) ? LRA_ERR_INVALID_ARG : 0;
+      continue;
+    }
+    CaArgs A;
+    A.P = B.base;
+    A.P.m = nr;
+    A.P.n = nc;
+    if (A.P.src == LRA_DENSE) {
+      const size_t esz = (A.P.dtype == LRA_F32) ? 4 : 8;
+      A.P.W = static_cast<const unsigned char*>(B.base.W) + (size_t)(r0 * B.base.ldw + c0) * esz;
+    } else {
+      A.P.X = B.base.X + 3 * r0;
+      A.P.Y = B.base.Y + 3 * c0;
+    }
+    const int kb = (int)min((int64_t)B.kmax, min(nr, nc));
+    A.sweeps = B.sweeps;
+    A.max_swaps = B.max_swaps;
+    A.h = B.h;
+    A.I0 = B.I0 + (size_t)b * B.kmax;
+    A.I = B.I + (size_t)b * B.kmax;
+    A.J = B.J + (size_t)b * B.kmax;
+    A.C = B.C + B.offs[2 * (size_t)b];
+    A.R = B.R + B.offs[2 * (size_t)b + 1];
+    A.logvol = B.logvol + (size_t)b * 2 * B.sweeps;
+    A.info = info;
+    A.G = G;
+    A.chunk_n = (int)nc;
+    A.chunk_m = (int)nr;
+    A.ldm = (int)max(nr, nc);
+    A.mixed = B.mixed;
+    if (B.mixed && A.P.src == LRA_KERNEL_LAPLACE) {
+      A.P.X32 = B.base.X32 + 3 * r0;
+      A.P.Y32 = B.base.Y32 + 3 * c0;
+    }
+    // Generator sizes: the caller's stages clipped to kb (one run of size kb
+    // without stages).  Each stage is a complete C-A run and nucleus; the next
+    // stage starts from this stage's rows, then the block's unused initial rows.
+    const int32_t* I0b = B.I0 + (size_t)b * B.kmax;
+    int stage = 0, k = B.nstages > 0 ? min(B.stages[0], kb) : kb;
+    int swaps = 0, loops = 0, n32 = 0, n64 = 0, nrun = 0, r = 0, st = LRA_OK;
+    for (;;) {
+      A.k = k;
+      A.I0 = (nrun == 0) ? I0b : s_I0;
+      A.strip_in_smem = ca_smem_fixed(k, A.ldm) + sizeof(double) * (size_t)k * A.ldm <= B.smem_bytes;
+      A.gstrip = A.strip_in_smem ? nullptr : gstrip;
+      const CaSmem S = ca_smem_carve(smem, k, A.ldm, A.gstrip);
+      ca_loop<SoloGroup, MIXED>(SoloGroup{}, A, S);
+      __syncthreads();
+      ++nrun;
+      st = info[3];
+      swaps += info[1]; loops += info[2]; n32 += info[4]; n64 += info[5];
+      if (st != LRA_OK && st < 16) break;
+      r = nucleus_cta(G, k, B.rank_tol, B.U + (size_t)b * B.kmax * B.kmax, smem);
+      if (r < k && st == LRA_OK) st = LRA_WARN_RANK_DEFICIENT;
+      if (k >= kb || r < k - B.margin) break;
+      int kn = k;
+      while (stage + 1 < B.nstages && kn <= k) kn = min(B.stages[++stage], kb);
+      if (kn <= k) break;
+      if (threadIdx.x == 0) {           // next initial rows: I, then unused I0b rows in order
+        for (int a = 0; a < k; ++a) s_I0[a] = A.I[a];
+        int c = k;
+        for (int t = 0; t < kb && c < kn; ++t) {
+          const int32_t v = I0b[t];
+          bool in = false;
+          for (int a = 0; a < k; ++a) in |= (s_I0[a] == v);
+          if (!in) s_I0[c++] = v;
+        }
+      }
+      __syncthreads();
+      k = kn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      info[0] = (st != LRA_OK && st < 16) ? 0 : r;
+      info[1] = swaps; info[2] = loops; info[3] = st;
+      info[4] = n32; info[5] = n64; info[6] = k; info[7] = nrun;
+    }
+    __syncthreads();
+  }
+}
+
+// Kernel entry of one CTA shape (defined in lra_batched_k<threads>.cu).
+void* batched_kernel_512(bool mixed);
+void* batched_kernel_256(bool mixed);
+void* batched_kernel_128(bool mixed);
+
+}  // namespace lra

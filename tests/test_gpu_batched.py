@@ -97,6 +97,41 @@ def test_staged_sizes_fmm_benchmark_workload_sampled_blocks():
     run_batch_staged(p, blocks, (28, 40, 64), 2, 3, 1e-6, check=pick)
 
 
+def test_cta_shapes_give_identical_results_and_tuner_picks_one():
+    """Every CTA shape of the batched kernel (threads per CTA x CTAs per SM) computes
+    the same bits; the autotuner times them all and stores a known shape."""
+    import paper_1710_07946_gb300 as lra
+    p, blocks, lev = li.fmm_blocks(npts=1 << 15, leaf=64, min_size=64, max_size=2048, nblocks=96, seed=5)
+    prob, _ = to_device(p)
+    I0 = li.block_initial_rows(blocks, 64, 1)
+    shapes = lra.lra_ca_batched_shapes()
+    assert len(shapes) >= 2 and all(t * c == 512 for t, c in shapes)
+    outs = []
+    ran = []
+    for t, c in shapes:
+        bt = lra.Batch(prob, blocks, 64, 3, I0, rank_tol=1e-6, stages=(28, 40, 64))
+        bt.cb.cta_threads, bt.cb.ctas_per_sm = t, c
+        try:
+            lra.lra_ca_run_batched(bt)
+        except RuntimeError:          # a shape whose shared memory cannot hold k = 64
+            continue
+        ran.append((t, c))
+        torch.cuda.synchronize()
+        outs.append({key: v.cpu().numpy() for key, v in bt.out.items()})
+    for o in outs[1:]:
+        for key in outs[0]:
+            np.testing.assert_array_equal(o[key], outs[0][key], err_msg=key)
+    bt = lra.Batch(prob, blocks, 64, 3, I0, rank_tol=1e-6, stages=(28, 40, 64))
+    ms = lra.lra_ca_batched_tune(bt, reps=1)
+    assert len(ran) >= 2 and set(ms) == set(ran) and all(v > 0 for v in ms.values())
+    assert (bt.cb.cta_threads, bt.cb.ctas_per_sm) == min(ms, key=ms.get)
+    for key, v in bt.out.items():
+        np.testing.assert_array_equal(v.cpu().numpy(), outs[0][key], err_msg=key)
+    bt.cb.cta_threads, bt.cb.ctas_per_sm = 300, 1          # not a built shape
+    with pytest.raises(RuntimeError):
+        lra.lra_ca_run_batched(bt)
+
+
 def test_dense_blocks_of_mixed_sizes():
     p = li.factor_gaussian(1500, 12, 1e-4, seed=3)
     blocks = li.dense_blocks(1500, sizes=(1, 7, 40, 64, 65, 300, 900), seed=1)
