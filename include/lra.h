@@ -243,7 +243,7 @@ typedef struct {
   int64_t max_len;         /* >= max over blocks of max(nrows, ncols); sizes the scratch  */
   int32_t cta_threads;     /* CTA shape of the batched kernel: threads per CTA and CTAs  */
   int32_t ctas_per_sm;     /* per SM, one of lra_ca_batched_shapes (0, 0: the library's
-                              default 256 x 2; lra_ca_batched_tune picks the fastest)    */
+                              default 512 x 1; lra_ca_batched_tune picks the fastest)    */
 } lra_batch;
 
 /* Outputs of a batch (device, caller-owned).  Block b has slots for k_b =
