@@ -182,6 +182,29 @@ struct Map2D {
   }
 };
 
+// Work split of the column-local phases (the warm replay and the back
+// substitution, where a column needs nothing from other columns): G lanes of
+// one warp share a column when there are fewer columns than threads (G a power
+// of two), lane g taking rows p with p % G == g and meeting its column's other
+// lanes at __syncwarp; every lane of a warp runs the same loop trip counts.
+struct ColMap {
+  int c0, cstep, g, G;
+  __device__ __forceinline__ explicit ColMap(int qn) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    G = 1;
+    if (qn > 0)
+      while (G < 32 && qn * (2 * G) <= nt) G *= 2;
+    g = tid & (G - 1);
+    c0 = tid / G;
+    cstep = nt / G;
+  }
+  // trips of the column loop, equal for all lanes of a warp
+  __device__ __forceinline__ int trips(int qn) const {
+    const int wc0 = (threadIdx.x & ~31) / G;       // first column of this warp
+    return wc0 < qn ? (qn - wc0 + cstep - 1) / cstep : 0;
+  }
+};
+
 // Gather the k x qn chunk of the strip; returns nonzero if any entry is not finite.
 __device__ inline int gather_chunk(const DevProblem& P, int phase, const CaSmem& S, int k, int64_t q0, int qn,
                                    int ldm, const Map2D& mp) {
@@ -290,23 +313,34 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
           if (jt >= q0 && jt < q0 + qn) S.pos[jt - q0] = t + 1;
         }
       __syncthreads();
-      for (int t = 0; t < k; ++t) {
-        const int r = S.piv[t];
-        if (r != t)
-          for (int c = tid; c < qn; c += nt) {
-            const double tmp = M[(int64_t)t * ldm + c];
-            M[(int64_t)t * ldm + c] = M[(int64_t)r * ldm + c];
-            M[(int64_t)r * ldm + c] = tmp;
+      // replay the row interchanges and eliminations on every column, one column
+      // (or one group of lanes) at a time: the columns are independent
+      {
+        const ColMap cm(qn);
+        const int trips = cm.trips(qn);
+        for (int u = 0; u < trips; ++u) {
+          const int c = cm.c0 + u * cm.cstep;
+          const bool act = c < qn;
+          for (int t = 0; t < k; ++t) {
+            const int r = S.piv[t];
+            if (act && r != t && cm.g == 0) {
+              const double tmp = M[(int64_t)t * ldm + c];
+              M[(int64_t)t * ldm + c] = M[(int64_t)r * ldm + c];
+              M[(int64_t)r * ldm + c] = tmp;
+            }
+            if (cm.G > 1) __syncwarp();
+            if (act && !S.pos[c]) {
+              const double mt = M[(int64_t)t * ldm + c];
+              int p = t + 1;
+              p += (cm.g - p % cm.G + cm.G) % cm.G;
+              for (; p < k; p += cm.G)
+                M[(int64_t)p * ldm + c] = fma(-S.Lm[p * ldl + t], mt, M[(int64_t)p * ldm + c]);
+            }
+            if (cm.G > 1) __syncwarp();
           }
-        __syncthreads();
-        for (int c = mp.c0; c < qn; c += mp.cstep) {
-          if (S.pos[c]) continue;
-          const double mt = M[(int64_t)t * ldm + c];
-          for (int p = mp.first(t + 1); p < k; p += mp.G)
-            M[(int64_t)p * ldm + c] = fma(-S.Lm[p * ldl + t], mt, M[(int64_t)p * ldm + c]);
         }
-        __syncthreads();
       }
+      __syncthreads();
       for (int t = 0; t < k; ++t) log_push(L, S, lead, fabs(LU[t * ldl + t]));
     }
   }
@@ -358,22 +392,30 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
   // update, so one barrier per row suffices.
   for (int i = tid; i < k; i += nt) S.rdiag[i] = 1.0 / LU[i * ldl + i];
   __syncthreads();
-  for (int c = mp.c0; c < qn; c += mp.cstep)
-    if (S.pos[c] == 0 && (k - 1) % mp.G == mp.g)
-      M[(int64_t)(k - 1) * ldm + c] = M[(int64_t)(k - 1) * ldm + c] * S.rdiag[k - 1];
-  __syncthreads();
-  for (int i = k - 1; i >= 1; --i) {
-    for (int c = mp.c0; c < qn; c += mp.cstep) {
-      if (S.pos[c]) continue;
-      const double xi = M[(int64_t)i * ldm + c];
-      for (int p = mp.first(0); p < i; p += mp.G) {
-        double v = fma(-LU[p * ldl + i], xi, M[(int64_t)p * ldm + c]);
-        if (p == i - 1) v = v * S.rdiag[i - 1];
-        M[(int64_t)p * ldm + c] = v;
+  {
+    // column by column (lanes of one column meet at __syncwarp): no CTA barrier
+    const ColMap cm(qn);
+    const int trips = cm.trips(qn);
+    for (int u = 0; u < trips; ++u) {
+      const int c = cm.c0 + u * cm.cstep;
+      const bool act = c < qn && S.pos[c] == 0;
+      if (act && (k - 1) % cm.G == cm.g)
+        M[(int64_t)(k - 1) * ldm + c] = M[(int64_t)(k - 1) * ldm + c] * S.rdiag[k - 1];
+      for (int i = k - 1; i >= 1; --i) {
+        if (cm.G > 1) __syncwarp();
+        if (act) {
+          const double xi = M[(int64_t)i * ldm + c];
+          for (int p = cm.g; p < i; p += cm.G) {
+            double v = fma(-LU[p * ldl + i], xi, M[(int64_t)p * ldm + c]);
+            if (p == i - 1) v = v * S.rdiag[i - 1];
+            M[(int64_t)p * ldm + c] = v;
+          }
+        }
       }
+      if (cm.G > 1) __syncwarp();
     }
-    __syncthreads();
   }
+  __syncthreads();
   for (int c = mp.c0; c < qn; c += mp.cstep)
     if (S.pos[c])
       for (int a = mp.g; a < k; a += mp.G) M[(int64_t)a * ldm + c] = (S.pos[c] - 1 == a) ? 1.0 : 0.0;
