@@ -95,7 +95,7 @@ def staged_flops(stages, kb, m, n, nrun, loops, swaps, entry_flops):
 
 
 class FmmWorkload:
-    name = "fmm_laplace_1M_octree_4096blocks_k64_tol1e-6"
+    base = "fmm_laplace_1M_octree_4096blocks"
     kernel = "ca_batched_kernel"
     unit = "LRA/s"
 
@@ -103,10 +103,8 @@ class FmmWorkload:
                  stages=(28, 40, 64), margin=2):
         self.npts, self.nblocks, self.k, self.sweeps, self.tol, self.q, self.s = npts, nblocks, k, sweeps, tol, q, s
         self.entries, self.stages, self.margin = entries, stages, margin
-        if entries == "f32":
-            self.name = self.name + "_f32entries"
-        if stages is None:
-            self.name = self.name + "_fixedk"
+        sizes = "-".join(map(str, stages)) if stages else str(k)
+        self.name = f"{self.base}_k{sizes}_tol{tol:.0e}".replace("e-0", "e-") + ("_f32entries" if entries == "f32" else "")
 
     def host(self, rank):
         p, blocks, lev = li.fmm_blocks(npts=self.npts, nblocks=self.nblocks, seed=rank)
@@ -501,7 +499,7 @@ class GaussApplyWorkload:
 
 class FmmSmallWorkload(FmmWorkload):
     """The same recipe on 2^17 points and 512 block pairs (profiling size)."""
-    name = "fmm_laplace_128K_octree_512blocks_k64_tol1e-6"
+    base = "fmm_laplace_128K_octree_512blocks"
 
     def __init__(self):
         super().__init__(npts=1 << 17, nblocks=512)
@@ -613,6 +611,20 @@ def cpu_cores_used() -> int:
 
 
 # ------------------------------------------------------------------ arms
+def job_totals(elapsed, units, world, device):
+    """Whole-job figures of a weak-scaling run: the slowest rank's elapsed time
+    and the units of all ranks (each rank runs its own independent problem; this
+    is the only exchange, outside the timed region)."""
+    import torch
+    t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_reference(args, wl):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -694,13 +706,8 @@ def run_lib(args, wl):
         dist.barrier()
     clk = clocks.stop()
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    tmax = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    tot_units = torch.tensor([float(units)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        dist.all_reduce(tot_units, op=dist.ReduceOp.SUM)
-    total_ms = float(tmax.item())
-    value = float(tot_units.item()) / (total_ms / 1e3)
+    total_ms, job_units = job_totals(step_ms, units, world, dev)
+    value = job_units / (total_ms / 1e3)
 
     # the same step replayed from a CUDA graph (cross-check of launch overhead)
     graph_ms = None
@@ -739,10 +746,8 @@ def run_lib(args, wl):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         wl.e2e_step(hp, d)
-    e2e_s = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(e2e_s, op=dist.ReduceOp.MAX)
-    e2e_value = float(tot_units.item()) / float(e2e_s.item())
+    e2e_s, _ = job_totals(time.perf_counter() - t0, 0, world, dev)
+    e2e_value = job_units / e2e_s
 
     if rank == 0:
         kms, kn = prof.get(wl.kernel, (float("nan"), 0))
