@@ -172,8 +172,8 @@ static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int6
   LRA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
   if (occ < 1) return LRA_ERR_INVALID_ARG;
   pl->threads = threads;
-  pl->ctas = std::min(occ, ctas);
-  pl->grid = pl->ctas * dev.sms;
+  pl->ctas = ctas;                                  // the shape
+  pl->grid = std::min(occ, ctas) * dev.sms;         // resident CTAs of the persistent launch
   pl->smem = smem;
   // global strip scratch when the largest strip does not fit beside the fixed part
   pl->scratch_stride = (size_t)kmax * kmax + (ca_need(kmax, ldm, true) > smem ? (size_t)kmax * max_len : 0);
