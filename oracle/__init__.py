@@ -47,6 +47,8 @@ def lib():
         L.orc_ca_run.restype = ct.c_int
         L.orc_ca_run_adaptive.argtypes = [P, vp, i32, i32, i32, vp, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_ca_run_adaptive.restype = ct.c_int
+        L.orc_cynical.argtypes = [P, i32, i32, i32, vp, vp, vp, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp]
+        L.orc_cynical.restype = ct.c_int
         L.orc_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp]
         L.orc_residual_sample.argtypes = [P, vp, vp, vp, i32, vp, i32, vp, i32, vp, vp]
         L.orc_brute_maxvol.argtypes = [vp, i32, i32, vp]
@@ -217,6 +219,26 @@ def ca_run_adaptive(p, stages, margin, sweeps, I0, h=1.01, max_swaps=1000, rank_
     return dict(I=I[:k].copy(), J=J[:k].copy(), C=C[:p.m * k].reshape(p.m, k), U=U[:k * k].reshape(k, k),
                 R=R[:k * p.n].reshape(k, p.n), logvol=lv, rank=int(info[0]), swaps=int(info[1]),
                 loops=int(info[2]), status=int(info[3]), k=k, stages=int(info[5]))
+
+
+def cynical(p, kind, r, q, K, L, I0s, sweeps=3, h=1.01, max_swaps=1000, rank_tol=1e-13):
+    """Cynical CUR (orc_cynical): kind 0 = Tests 3 (sketch W'[K, L] from the
+    caller's K, L), kind 1 = Tests 4 (one C-A loop with q x q generators from the
+    caller's L makes the sketch); then an r x r C-A generator inside the sketch
+    from its initial rows I0s (r indices in [0, q)).  Returns ca_run's keys
+    (without logvol) plus K, L (the sketch sets used)."""
+    mp = _Marshalled(p)
+    K = np.ascontiguousarray(np.zeros(q) if K is None else K, dtype=np.int32).copy()
+    L = np.ascontiguousarray(L, dtype=np.int32).copy()
+    I0s = np.ascontiguousarray(I0s, dtype=np.int32)
+    assert len(K) == q and len(L) == q and len(I0s) == r
+    I = np.zeros(r, dtype=np.int32); J = np.zeros(r, dtype=np.int32)
+    C = np.zeros((p.m, r)); U = np.zeros((r, r)); R = np.zeros((r, p.n))
+    info = np.zeros(4, dtype=np.int32)
+    lib().orc_cynical(mp.ref, int(kind), int(r), int(q), _ptr(K), _ptr(L), _ptr(I0s), int(sweeps), h, max_swaps,
+                      rank_tol, _ptr(I), _ptr(J), _ptr(C), _ptr(U), _ptr(R), _ptr(info))
+    return dict(I=I, J=J, C=C, U=U, R=R, K=K, L=L, rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]),
+                status=int(info[3]))
 
 
 def cur_apply(C, U, R, X):

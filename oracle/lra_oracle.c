@@ -544,6 +544,90 @@ int orc_ca_run_adaptive(const orc_problem* p, const int32_t* stages, int32_t nst
   return st;
 }
 
+/*
+ * orc_cynical: the cynical CUR algorithms of the paper's tests (section
+ * "Four algorithms used", Tests 3 and 4; section "CUR LRA; primitive, cynical,
+ * and cross-approximation algorithms"): an r x r generator of locally maximal
+ * volume inside a q x q sketch W'[K, L] (q = 4r in the paper).
+ *   kind 0 (Tests 3): K and L are the caller's random index sets.
+ *   kind 1 (Tests 4): L is the caller's random column set; a single C-A loop
+ *     with q x q generators makes the sketch: K = the rows that maxvol
+ *     (orc_maxvol, cold start) selects in the column strip W'[:, L], then
+ *     L = the columns it selects in the row strip W'[K, :].
+ * A C-A run (orc_ca_run, sweeps loops from the initial rows I0s: r distinct
+ * indices in [0, q)) on the dense sketch S = W'[K, L] gives I', J' and the
+ * nucleus of S[I', J'] = W'[I, J]; the generators are I = K[I'], J = L[J'],
+ * with C = W'[:, J] (m x r), R = W[I, :] (r x n).
+ * info: rank, swaps of every maxvol step, loops of the sketch C-A, status.
+ * K and L (q each) are inputs and, for kind 1, receive the computed sets.
+ */
+int orc_cynical(const orc_problem* p, int32_t kind, int32_t r, int32_t q, int32_t* K, int32_t* L,
+                const int32_t* I0s, int32_t sweeps, double h, int32_t max_swaps, double rank_tol, int32_t* I,
+                int32_t* J, double* C, double* U, double* R, int32_t* info) {
+  int64_t m = p->m, n = p->n;
+  int status = ORC_OK, swaps = 0;
+  info[0] = 0; info[1] = 0; info[2] = 0; info[3] = ORC_OK;
+  if (kind == 1) {
+    int32_t nsw = 0;
+    double ld;
+    double* Cs = (double*)malloc(sizeof(double) * (size_t)q * (size_t)m);
+    orc_gather_cols_t(p, L, q, Cs);
+    if (!all_finite(Cs, (int64_t)q * m)) status = ORC_ERR_NONFINITE;
+    else {
+      int st = orc_maxvol(Cs, q, m, NULL, h, max_swaps, K, NULL, &ld, &nsw);
+      if (st > status) status = st;
+      swaps += nsw;
+    }
+    free(Cs);
+    if (status != ORC_ERR_NONFINITE) {
+      double* Rs = (double*)malloc(sizeof(double) * (size_t)q * (size_t)n);
+      orc_gather_rows(p, K, q, Rs);
+      if (!all_finite(Rs, (int64_t)q * n)) status = ORC_ERR_NONFINITE;
+      else {
+        int st = orc_maxvol(Rs, q, n, NULL, h, max_swaps, L, NULL, &ld, &nsw);
+        if (st > status) status = st;
+        swaps += nsw;
+      }
+      free(Rs);
+    }
+    if (status == ORC_ERR_NONFINITE) {
+      info[1] = swaps; info[3] = status;
+      return status;
+    }
+  }
+  /* the sketch as a dense problem of its own */
+  double* S = (double*)malloc(sizeof(double) * (size_t)q * (size_t)q);
+  for (int32_t a = 0; a < q; ++a)
+    for (int32_t b = 0; b < q; ++b) S[(int64_t)a * q + b] = entry_wp(p, K[a], L[b]);
+  orc_problem ps;
+  memset(&ps, 0, sizeof(ps));
+  ps.src = ORC_DENSE; ps.dtype = ORC_F64; ps.m = q; ps.n = q; ps.W = S; ps.ldw = q; ps.mkind = ORC_MULT_NONE;
+  int32_t* Ii = (int32_t*)malloc(sizeof(int32_t) * (size_t)r);
+  int32_t* Jj = (int32_t*)malloc(sizeof(int32_t) * (size_t)r);
+  double* Cq = (double*)malloc(sizeof(double) * (size_t)q * (size_t)r);
+  double* Rq = (double*)malloc(sizeof(double) * (size_t)r * (size_t)q);
+  double* lv = (double*)malloc(sizeof(double) * 2 * (size_t)sweeps);
+  int32_t inf[4];
+  int st = orc_ca_run(&ps, r, sweeps, I0s, h, max_swaps, rank_tol, Ii, Jj, Cq, U, Rq, lv, inf);
+  swaps += inf[1];
+  if (st == ORC_ERR_NONFINITE || (st != ORC_OK && st < 16)) {
+    status = st;
+    info[1] = swaps; info[2] = inf[2]; info[3] = status;
+  } else {
+    if (st > status) status = st;
+    for (int32_t a = 0; a < r; ++a) { I[a] = K[Ii[a]]; J[a] = L[Jj[a]]; }
+    double* Ct = (double*)malloc(sizeof(double) * (size_t)r * (size_t)m);
+    orc_gather_cols_t(p, J, r, Ct);
+    for (int64_t i = 0; i < m; ++i)
+      for (int32_t a = 0; a < r; ++a) C[i * r + a] = Ct[(int64_t)a * m + i];
+    free(Ct);
+    orc_gather_rows_orig(p, I, r, R);
+    info[0] = inf[0]; info[1] = swaps; info[2] = inf[2]; info[3] = status;
+  }
+  free(S); free(Ii); free(Jj); free(Cq); free(Rq); free(lv);
+  return status;
+}
+
 /* ------------------------------------------------------------------ */
 /* CUR apply and sampled residual                                      */
 /* ------------------------------------------------------------------ */

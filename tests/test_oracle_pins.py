@@ -468,6 +468,85 @@ def test_adaptive_fmm_blocks_accuracy_and_size():
         assert o["rank"] < o["k"] - 2 or o["k"] == min(64, nr, nc)
 
 
+# ------------------------------------------------------------------ cynical algorithms (Tests 3, 4)
+def _sketch_sets(n, r, seed):
+    g = np.random.default_rng(seed)
+    q = 4 * r
+    return q, g.choice(n, q, replace=False), g.choice(n, q, replace=False), g.choice(q, r, replace=False)
+
+
+def test_cynical_error_band_from_paper_table():
+    """Table tb_ranrc (Tests 3 and 4, n = 256..1024, r = 8, 16): our mean relative
+    spectral error is at most the paper's printed mean, and above the 1e-10 noise
+    floor's order."""
+    with open(os.path.join(GOLDEN, "tests34_error_table.txt")) as f:
+        rows = [line.split() for line in f if line.strip() and not line.startswith("#")]
+    for test, n, r, mean, _ in rows:
+        test, n, r, mean = int(test), int(n), int(r), float(mean)
+        errs = []
+        for seed in range(6):
+            p = li.factor_gaussian(n, r, 1e-10, seed)
+            q, K, L, I0s = _sketch_sets(n, r, 700 + seed)
+            o = oracle.cynical(p, test - 3, r, q, K if test == 3 else None, L, I0s, sweeps=5)
+            E = p.W - o["C"] @ o["U"] @ o["R"]
+            errs.append(np.linalg.norm(E, 2) / np.linalg.norm(p.W, 2))
+        assert np.mean(errs) <= mean, (test, n, r, np.mean(errs))
+        assert np.min(errs) > 1e-13
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_cynical_exact_recovery_rank_r(kind):
+    """Theorem thdcmp: W = CUR once the r x r generator of a rank-r W is nonsingular."""
+    g = np.random.default_rng(40 + kind)
+    W = g.standard_normal((300, 6)) @ g.standard_normal((6, 250))
+    p = li.Problem(li.SRC_DENSE, 300, 250, W=W)
+    q, K, L, I0s = _sketch_sets(250, 6, 9)
+    o = oracle.cynical(p, kind, 6, q, K, L, I0s)
+    assert o["rank"] == 6 and o["status"] in (0, 16)
+    assert np.linalg.norm(W - o["C"] @ o["U"] @ o["R"]) <= 1e-10 * np.linalg.norm(W)
+    assert set(o["I"]) <= set(o["K"]) and set(o["J"]) <= set(o["L"])
+
+
+def test_cynical_generator_dominant_in_sketch():
+    """Tests 3: when the sketch C-A converged, the generator B = S[I', J'] is dominant
+    in the sketch S = W[K, L] both ways: max |S[:, J'] B^-1| <= h and max |B^-1 S[I', :]| <= h
+    (Lemma lelcliden's condition, checked with numpy.linalg.solve)."""
+    for seed in range(4):
+        p = li.factor_gaussian(256, 8, 1e-6, seed)
+        q, K, L, I0s = _sketch_sets(256, 8, 900 + seed)
+        o = oracle.cynical(p, 0, 8, q, K, L, I0s, sweeps=8)
+        if o["loops"] >= 8:
+            continue
+        S = p.W[np.ix_(K, L)]
+        Ip = [list(K).index(i) for i in o["I"]]
+        Jp = [list(L).index(j) for j in o["J"]]
+        B = S[np.ix_(Ip, Jp)]
+        assert np.abs(np.linalg.solve(B, S[Ip, :])).max() <= 1.01 + 1e-9
+        assert np.abs(np.linalg.solve(B.T, S[:, Jp].T)).max() <= 1.01 + 1e-9
+
+
+def test_cynical_one_loop_sketch_sets_are_dominant():
+    """Tests 4: K is a dominant row set of the column strip W[:, L0] (L0 the caller's
+    columns) and the final L a dominant column set of the row strip W[K, :]."""
+    p = li.factor_gaussian(512, 8, 1e-8, 3)
+    q, _, L0, I0s = _sketch_sets(512, 8, 77)
+    o = oracle.cynical(p, 1, 8, q, None, L0, I0s)
+    K, L = o["K"], o["L"]
+    A = p.W[:, L0]
+    assert np.abs(np.linalg.solve(A[K, :].T, A.T)).max() <= 1.01 + 1e-9
+    Rk = p.W[K, :]
+    assert np.abs(np.linalg.solve(Rk[:, L], Rk)).max() <= 1.01 + 1e-9
+
+
+def test_cynical_sketch_of_generator_size_keeps_it():
+    """q = r: the sketch is the generator itself, so I, J are K, L reordered."""
+    p = li.factor_gaussian(200, 5, 1e-6, 1)
+    g = np.random.default_rng(2)
+    K, L = g.choice(200, 5, replace=False), g.choice(200, 5, replace=False)
+    o = oracle.cynical(p, 0, 5, 5, K, L, np.arange(5))
+    assert sorted(o["I"]) == sorted(K) and sorted(o["J"]) == sorted(L)
+
+
 # ------------------------------------------------------------------ apply / residual
 def test_cur_apply_matches_matmul():
     g = np.random.default_rng(0)
