@@ -286,6 +286,36 @@ lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, c
                               lra_stream_t stream);
 
 /*
+ * lra_cynical_run_batched -- the cynical CUR algorithms on every block of a
+ * batch (paper: Section "CUR LRA; primitive, cynical, and cross-approximation
+ * algorithms"; the tests' Tests 3 and Tests 4), one CTA per block from a work
+ * queue.  Block b's r x r generator (r = par->k) is taken inside a q x q sketch
+ * W_b[K_b, L_b] (q = 4r in the paper, r <= q <= 64, q <= min(nrows, ncols)):
+ *   kind 0 (Tests 3): K_b, L_b are the caller's (random) row and column sets;
+ *   kind 1 (Tests 4): L_b is the caller's; one C-A loop with q x q generators
+ *     makes the sketch (a cold maxvol step on the column strip W_b[:, L_b]
+ *     picks K_b, one on the row strip W_b[K_b, :] picks L_b) and both sets are
+ *     written back to K and L.
+ * A C-A run of size r (par->sweeps loops, par->h, par->max_swaps) on the dense
+ * sketch from its initial rows I0s[b] (r distinct indices in [0, q)) picks I',
+ * J'; the outputs are I_b = K_b[I'], J_b = L_b[J'], C_b = W_b[:, J_b], R_b =
+ * W_b[I_b, :] and U_b = the nucleus of W_b[I_b, J_b] at par->rank_tol, in the
+ * layout of lra_cur_batch with k = r; info as lra_ca_run_batched (swaps of
+ * every maxvol step, loops of the sketch run).  The results equal the FP64
+ * reference's operation for operation.  par->mode must be LRA_MODE_FP64 and
+ * par->nstages 0.  K, L: device nb x q int32 (block-local; for kind 1, K is
+ * output only); I0s: device nb x r.  A block with invalid sets or smaller than
+ * q gets status LRA_ERR_INVALID_ARG in its info slot.
+ * Errors: LRA_ERR_INVALID_ARG, LRA_ERR_WORKSPACE, LRA_ERR_CUDA.
+ */
+lra_status lra_cynical_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
+                                              const lra_ca_params* par, int32_t kind, int32_t q, size_t* bytes);
+lra_status lra_cynical_run_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                                   int32_t kind, int32_t q, int32_t* K, int32_t* L, const int32_t* I0s,
+                                   const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
+                                   lra_stream_t stream);
+
+/*
  * lra_ca_batched_shapes -- the CTA shapes the batched kernel is built for:
  * writes up to cap (threads per CTA, CTAs per SM) pairs and returns their
  * number.  Each shape holds 16 warps per SM (128 registers a thread); they
