@@ -401,6 +401,142 @@ class LaplaceSingleWorkload:
         return good, n, el, f"{n} complete LRAs of the same input (C-A + nucleus + residual sample)"
 
 
+class RandomTestsWorkload:
+    """The paper's random-input tests (Table tb_ranrc recipe): nb independent n x n
+    inputs W = G1 G2 + 1e-10 G3 of expected rank r, stacked as blocks of one
+    matrix, each approximated by Tests 2 (C-A, r x r generators, 5 loops from r
+    random rows), Tests 3 (an r x r generator inside a random 4r x 4r sketch) or
+    Tests 4 (one C-A loop with 4r x 4r generators from 4r random columns, then
+    Tests 3 inside it).  One step = the batched run + a 16 x 16 residual sample
+    per block; units = blocks whose sampled error is <= 1e-6."""
+    unit = "LRA/s"
+
+    def __init__(self, test, n=256, r=8, nb=4096, sweeps=5):
+        self.test, self.n, self.r, self.nb, self.sweeps, self.q = test, n, r, nb, sweeps, 4 * r
+        self.kernel = "ca_batched_kernel" if test == 2 else "cynical_batched_kernel"
+        self.name = f"tests{test}_factor_gaussian_{nb}x{n}x{n}_r{r}"
+
+    def host(self, rank):
+        g = np.random.default_rng(4000 + rank)
+        n, r, nb = self.n, self.r, self.nb
+        W = np.empty((nb * n, n))
+        for b in range(nb):
+            W[b * n:(b + 1) * n] = g.standard_normal((n, r)) @ g.standard_normal((r, n))
+        W += 1e-10 * g.standard_normal(W.shape)
+        blocks = np.array([[b * n, n, 0, n] for b in range(nb)], dtype=np.int64)
+        K = np.stack([g.choice(n, self.q, replace=False) for _ in range(nb)]).astype(np.int32)
+        L = np.stack([g.choice(n, self.q, replace=False) for _ in range(nb)]).astype(np.int32)
+        I0s = np.stack([g.choice(self.q, r, replace=False) for _ in range(nb)]).astype(np.int32)
+        I0 = np.stack([g.choice(n, r, replace=False) for _ in range(nb)]).astype(np.int32)
+        Q, S = li.block_sample_positions(blocks, 16, 16, 300 + rank)
+        return dict(W=W, blocks=blocks, K=K, L=L, I0s=I0s, I0=I0, Q=Q, S=S)
+
+    def config(self, h):
+        alg = {2: "C-A (Tests 2): r x r generators, 5 loops from r random rows",
+               3: "cynical (Tests 3): r x r generator in a random 4r x 4r sketch, sketch C-A 5 loops",
+               4: "Tests 4: one C-A loop with 4r x 4r generators from 4r random columns, then Tests 3"}[self.test]
+        return {"workload": self.name, "inputs": f"{self.nb} x (G1 G2 + 1e-10 G3), n = {self.n}, r = {self.r}",
+                "algorithm": alg, "sketch": self.q if self.test > 2 else None, "residual_sample": "16x16 per block"}
+
+    def device(self, h, dev):
+        import torch
+        import paper_1710_07946_gb300 as lra
+        W = torch.from_numpy(h["W"]).to(dev)
+        prob = lra.Problem.dense(W)
+        I0 = h["I0"] if self.test == 2 else h["I0s"]
+        bt = lra.Batch(prob, h["blocks"], self.r, self.sweeps, I0, rank_tol=1e-13)
+        t = lambda a: torch.from_numpy(a).to(dev)
+        d = dict(W=W, prob=prob, bt=bt, K=t(h["K"]), L=t(h["L"]), L0=t(h["L"]), I0s=t(h["I0s"]), Q=t(h["Q"]),
+                 S=t(h["S"]))
+        d["stats"] = torch.empty(self.nb, 5, dtype=torch.float64, device=dev)
+        # untimed set-up: CTA shape autotuner (Tests 4 rewrites its inputs: library default shape)
+        if self.test == 2:
+            tuned = lra.lra_ca_batched_tune(bt, reps=2)
+        elif self.test == 3:
+            tuned = lra.lra_cynical_batched_tune(bt, self.q, d["K"], d["L"], d["I0s"], reps=2)
+        else:
+            tuned = None
+        self.tuned = None if tuned is None else {
+            "chosen": f"{bt.cb.cta_threads}x{bt.cb.ctas_per_sm}",
+            "ms": {f"{a}x{b}": round(v, 3) for (a, b), v in tuned.items()}}
+        return d
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        if self.test == 2:
+            lra.lra_ca_run_batched(d["bt"])
+        else:
+            if self.test == 4:
+                d["L"].copy_(d["L0"])          # Tests 4 overwrites the sketch sets
+            lra.lra_cynical_run_batched(d["bt"], self.test - 3, self.q, d["K"], d["L"], d["I0s"])
+        lra.lra_residual_sample_batched(d["bt"], d["Q"], d["S"], d["stats"])
+
+    def check(self, d):
+        info = d["bt"].out["info"].cpu().numpy()
+        st = d["stats"].cpu().numpy()
+        ok = ((info[:, 3] == 0) | (info[:, 3] >= 16)) & (st[:, 4] <= ERR_BOUND)
+        return dict(units=int(ok.sum()), info=info, err=st[:, 4])
+
+    def flops(self, h, res):
+        n, r, q = self.n, self.r, self.q
+        f = 0.0
+        for inf in res["info"]:
+            loops, swaps = max(int(inf[2]), 1), int(inf[1])
+            if self.test == 2:
+                f += ca_flops(r, n, n, loops, swaps)
+            else:
+                f += ca_flops(r, q, q, loops, swaps)
+                if self.test == 4:
+                    f += maxvol_flops(q, n, True) * 2
+        return f
+
+    def extra(self, res):
+        err = res["err"]
+        return {"cta_shape_tuner": getattr(self, "tuned", None),
+                "swaps_mean": float(res["info"][:, 1].mean()), "loops_mean": float(res["info"][:, 2].mean()),
+                "rel_fro_err_sampled_median": float(np.median(err)), "rel_fro_err_sampled_max": float(err.max()),
+                "frac_blocks_err_le_1e-6": float((err <= ERR_BOUND).mean())}
+
+    def e2e_setup(self, h, d):
+        import torch
+        out = d["bt"].out
+        hp = dict(W=torch.from_numpy(h["W"]).pin_memory())
+        hp["out"] = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in out.items()}
+        hp["stats"] = torch.empty(d["stats"].shape, dtype=torch.float64).pin_memory()
+        h2d = hp["W"].numel() * 8
+        d2h = sum(v.numel() * v.element_size() for v in hp["out"].values()) + hp["stats"].numel() * 8
+        return hp, h2d, d2h
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["W"].copy_(hp["W"], non_blocking=True)
+        self.step(d)
+        for key, v in hp["out"].items():
+            v.copy_(d["bt"].out[key], non_blocking=True)
+        hp["stats"].copy_(d["stats"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        n, r = self.n, self.r
+        t0 = time.perf_counter()
+        cnt = good = 0
+        for b in np.random.default_rng(seed).permutation(self.nb):
+            sub = li.Problem(li.SRC_DENSE, n, n, W=np.ascontiguousarray(h["W"][b * n:(b + 1) * n]))
+            if self.test == 2:
+                o = oracle.ca_run(sub, r, self.sweeps, h["I0"][b])
+            else:
+                o = oracle.cynical(sub, self.test - 3, r, self.q, h["K"][b] if self.test == 3 else None, h["L"][b],
+                                   h["I0s"][b], sweeps=self.sweeps)
+            st = oracle.residual_sample(sub, o["C"], o["U"], o["R"], h["Q"][b], h["S"][b])
+            cnt += 1
+            good += st[4] <= ERR_BOUND
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        el = time.perf_counter() - t0
+        return good, cnt, el, f"{cnt} randomly chosen inputs of the same batch (LRA + residual sample each)"
+
+
 class GaussApplyWorkload:
     """Differentiable CUR apply: 256 Gaussian-kernel blocks exp(-|x-y|^2/(2 l^2)), l = 0.3, 1024 x 1024 each
     (targets in [0,1]^3, sources in [2,3]x[0,1]^2), pivots of rank 32 from a batched C-A run (untimed set-up);
@@ -513,6 +649,12 @@ WORKLOADS = {
     **{f"laplace65536_k{k}{sfx}": (lambda k=k, e=e: LaplaceSingleWorkload(k, e))
        for k in (16, 32, 64) for sfx, e in (("", "f64"), ("_f32", "f32"))},
     "gauss_apply": GaussApplyWorkload,
+    "tests2_n256_r8": lambda: RandomTestsWorkload(2),
+    "tests3_n256_r8": lambda: RandomTestsWorkload(3),
+    "tests4_n256_r8": lambda: RandomTestsWorkload(4),
+    "tests3_n256_r16": lambda: RandomTestsWorkload(3, r=16),
+    "tests4_n256_r16": lambda: RandomTestsWorkload(4, r=16),
+    "tests2_n256_r16": lambda: RandomTestsWorkload(2, r=16),
     "dense8192_arht": lambda: DenseWorkload("arht"),
     "dense8192_sparse": lambda: DenseWorkload("sparse"),
 }

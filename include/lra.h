@@ -305,7 +305,12 @@ lra_status lra_ca_run_batched(const lra_problem* base, const lra_batch* batch, c
  * reference's operation for operation.  par->mode must be LRA_MODE_FP64 and
  * par->nstages 0.  K, L: device nb x q int32 (block-local; for kind 1, K is
  * output only); I0s: device nb x r.  A block with invalid sets or smaller than
- * q gets status LRA_ERR_INVALID_ARG in its info slot.
+ * q gets status LRA_ERR_INVALID_ARG in its info slot.  The CTA shape is the
+ * batch's cta_threads x ctas_per_sm (one of lra_ca_batched_shapes; 0, 0 =
+ * for kind 0 the smallest CTAs whose shared-memory share holds the run, the
+ * sketch runs having little work per barrier; for kind 1 512 x 1, its q-wide
+ * maxvol steps being C-A steps).  The workspace query covers every shape that
+ * fits.
  * Errors: LRA_ERR_INVALID_ARG, LRA_ERR_WORKSPACE, LRA_ERR_CUDA.
  */
 lra_status lra_cynical_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
@@ -314,6 +319,19 @@ lra_status lra_cynical_run_batched(const lra_problem* base, const lra_batch* bat
                                    int32_t kind, int32_t q, int32_t* K, int32_t* L, const int32_t* I0s,
                                    const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
                                    lra_stream_t stream);
+
+/*
+ * lra_cynical_batched_tune -- autotuner of lra_cynical_run_batched for kind 0
+ * (Tests 3; kind 1 rewrites its inputs and is rejected): times every CTA shape
+ * as lra_ca_batched_tune does and returns the fastest in *cta_threads,
+ * *ctas_per_sm, with the times in ms (-1 for shapes that do not fit) when ms is
+ * not NULL.  Blocks the calling thread; not capturable.
+ */
+lra_status lra_cynical_batched_tune(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                                    int32_t kind, int32_t q, int32_t* K, int32_t* L, const int32_t* I0s,
+                                    const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
+                                    lra_stream_t stream, int32_t reps, int32_t* cta_threads, int32_t* ctas_per_sm,
+                                    float* ms);
 
 /*
  * lra_ca_batched_shapes -- the CTA shapes the batched kernel is built for:

@@ -111,6 +111,8 @@ def _load():
     L.lra_ca_batched_tune.argtypes = [P, PB, PP, vp, PCB, vp, sz, vp, i32, ct.POINTER(i32), ct.POINTER(i32), vp]
     L.lra_cynical_batched_workspace_size.argtypes = [P, PB, PP, i32, i32, ct.POINTER(sz)]
     L.lra_cynical_run_batched.argtypes = [P, PB, PP, i32, i32, vp, vp, vp, PCB, vp, sz, vp]
+    L.lra_cynical_batched_tune.argtypes = [P, PB, PP, i32, i32, vp, vp, vp, PCB, vp, sz, vp, i32,
+                                           ct.POINTER(i32), ct.POINTER(i32), vp]
     L.lra_ca_batched_shapes.argtypes = [vp, vp, i32]
     L.lra_ca_batched_shapes.restype = i32
     PG = ct.POINTER(_Gauss)
@@ -126,6 +128,7 @@ def _load():
               "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect",
               "lra_ca_batched_workspace_size", "lra_ca_run_batched", "lra_residual_sample_batched",
               "lra_ca_batched_tune", "lra_cynical_batched_workspace_size", "lra_cynical_run_batched",
+              "lra_cynical_batched_tune",
               "lra_gauss_cur_forward", "lra_gauss_cur_backward"):
         getattr(L, f).restype = ct.c_int
     _lib = L
@@ -477,6 +480,34 @@ def lra_ca_batched_tune(batch: Batch, reps: int = 2, stream=None) -> dict:
     return {shp: ms[i] for i, shp in enumerate(shapes) if ms[i] >= 0}
 
 
+def _cyn_workspace(batch: Batch, kind: int, q: int):
+    key = (int(kind), int(q))
+    if getattr(batch, "_cyn_key", None) != key:
+        nbytes = ct.c_size_t()
+        _check(_load().lra_cynical_batched_workspace_size(ct.byref(batch.pc), ct.byref(batch.cb),
+                                                          ct.byref(batch.params), int(kind), int(q),
+                                                          ct.byref(nbytes)), "lra_cynical_batched_workspace_size")
+        batch._cyn_ws, batch._cyn_key = _workspace(nbytes.value, batch.blocks.device), key
+    return batch._cyn_ws
+
+
+def lra_cynical_batched_tune(batch: Batch, q: int, K: torch.Tensor, L: torch.Tensor, I0s: torch.Tensor,
+                             reps: int = 2, stream=None) -> dict:
+    """Autotuner of the cynical kernel (Tests 3 runs): times every CTA shape, stores
+    the fastest in ``batch`` and returns {(threads, ctas): ms}.  Synchronises."""
+    L_ = _load()
+    ws = _cyn_workspace(batch, 0, q)
+    shapes = lra_ca_batched_shapes()
+    ms = (ct.c_float * len(shapes))()
+    th, cs = ct.c_int32(), ct.c_int32()
+    _check(L_.lra_cynical_batched_tune(ct.byref(batch.pc), ct.byref(batch.cb), ct.byref(batch.params), 0, int(q),
+                                       K.data_ptr(), L.data_ptr(), I0s.data_ptr(), ct.byref(batch.cur),
+                                       ws.data_ptr(), ws.numel(), _stream(stream), int(reps), ct.byref(th),
+                                       ct.byref(cs), ms), "lra_cynical_batched_tune")
+    batch.cb.cta_threads, batch.cb.ctas_per_sm = th.value, cs.value
+    return {shp: ms[i] for i, shp in enumerate(shapes) if ms[i] >= 0}
+
+
 def lra_cynical_run_batched(batch: Batch, kind: int, q: int, K: torch.Tensor, L: torch.Tensor, I0s: torch.Tensor,
                             stream=None) -> None:
     """Cynical CUR of every block (kind 0: Tests 3 with the sketch sets K, L;
@@ -488,13 +519,7 @@ def lra_cynical_run_batched(batch: Batch, kind: int, q: int, K: torch.Tensor, L:
         _dev(t, torch.int32, nm)
         if tuple(t.shape) != shp or not t.is_contiguous():
             raise ValueError(f"{nm} must be a contiguous {shp} int32 tensor")
-    key = (int(kind), int(q))
-    if getattr(batch, "_cyn_key", None) != key:
-        nbytes = ct.c_size_t()
-        _check(L_.lra_cynical_batched_workspace_size(ct.byref(batch.pc), ct.byref(batch.cb), ct.byref(batch.params),
-                                                     int(kind), int(q), ct.byref(nbytes)),
-               "lra_cynical_batched_workspace_size")
-        batch._cyn_ws, batch._cyn_key = _workspace(nbytes.value, batch.blocks.device), key
+    _cyn_workspace(batch, kind, q)
     _check(L_.lra_cynical_run_batched(ct.byref(batch.pc), ct.byref(batch.cb), ct.byref(batch.params), int(kind),
                                       int(q), K.data_ptr(), L.data_ptr(), I0s.data_ptr(), ct.byref(batch.cur),
                                       batch._cyn_ws.data_ptr(), batch._cyn_ws.numel(), _stream(stream)),

@@ -127,12 +127,13 @@ struct BatchPlan {
 };
 
 // CTA shapes of the batched kernel: NTB threads x MINB CTAs per SM, 16 warps
-// per SM in each case (128 registers a thread fill the register file).  Fewer
+// per SM in each case (128 registers a thread fill the register file; 64
+// threads is the smallest CTA the k x k elimination's layout allows).  Fewer
 // threads per block and more blocks per SM trade the parallelism inside one
 // block for overlap between blocks (their barriers and FP64 latencies).
 struct BatchShape { int threads, ctas; };
-constexpr BatchShape kShapes[] = {{512, 1}, {256, 2}, {128, 4}};
-constexpr int kNumShapes = 3;
+constexpr BatchShape kShapes[] = {{512, 1}, {256, 2}, {128, 4}, {64, 8}};
+constexpr int kNumShapes = 4;
 
 static size_t ca_need(int k, int ldm, bool strip) {
   return ca_smem_fixed(k, ldm) + (strip ? sizeof(double) * (size_t)k * ldm : 0);
@@ -141,7 +142,8 @@ static size_t ca_need(int k, int ldm, bool strip) {
 static void* batched_kernel_ptr(bool mixed, int threads) {
   if (threads == 512) return batched_kernel_512(mixed);
   if (threads == 256) return batched_kernel_256(mixed);
-  return batched_kernel_128(mixed);
+  if (threads == 128) return batched_kernel_128(mixed);
+  return batched_kernel_64(mixed);
 }
 
 static bool shape_known(int threads, int ctas) {
@@ -320,38 +322,15 @@ lra_status lra_ca_batched_tune(const lra_problem* base, const lra_batch* batch, 
   lra_status st = batched_check(base, batch, par, I0, out, &P);
   if (st != LRA_OK) return st;
   if (cta_threads == nullptr || ctas_per_sm == nullptr || reps < 1) return LRA_ERR_INVALID_ARG;
-  cudaEvent_t e0, e1;
-  LRA_CUDA_TRY(cudaEventCreate(&e0));
-  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LRA_ERR_CUDA; }
-  float best = 0.f;
   int bi = -1;
-  for (int i = 0; i < kNumShapes && st == LRA_OK; ++i) {
-    float fastest = 0.f;
+  st = time_shapes(kNumShapes, reps, stream, [&](int i) {
     BatchPlan pl;
     const lra_status fit = batch_plan(P, par, batch->max_len, kShapes[i].threads, kShapes[i].ctas, &pl);
-    if (fit == LRA_ERR_INVALID_ARG) {           // this shape cannot hold the batch
-      if (ms != nullptr) ms[i] = -1.f;
-      continue;
-    }
-    if (fit != LRA_OK) { st = fit; break; }
-    for (int r = 0; r < reps && st == LRA_OK; ++r) {
-      if (cudaEventRecord(e0, stream) != cudaSuccess) { st = LRA_ERR_CUDA; break; }
-      st = batched_launch(P, batch, par, I0, out, workspace, workspace_bytes, stream, kShapes[i].threads,
+    if (fit != LRA_OK) return fit;
+    return batched_launch(P, batch, par, I0, out, workspace, workspace_bytes, stream, kShapes[i].threads,
                           kShapes[i].ctas);
-      if (st != LRA_OK) break;
-      float t = 0.f;
-      if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) { st = LRA_ERR_CUDA; break; }
-      if (r == 0 || t < fastest) fastest = t;
-    }
-    if (st != LRA_OK) break;
-    if (ms != nullptr) ms[i] = fastest;
-    if (bi < 0 || fastest < best) { best = fastest; bi = i; }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  }, ms, &bi);
   if (st != LRA_OK) return st;
-  if (bi < 0) return LRA_ERR_INVALID_ARG;
   *cta_threads = kShapes[bi].threads;
   *ctas_per_sm = kShapes[bi].ctas;
   return LRA_OK;

@@ -147,5 +147,6 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
 void* batched_kernel_512(bool mixed);
 void* batched_kernel_256(bool mixed);
 void* batched_kernel_128(bool mixed);
+void* batched_kernel_64(bool mixed);
 
 }  // namespace lra

@@ -44,6 +44,40 @@ lra_status current_device_info(DeviceInfo* info);
 
 inline size_t align_up(size_t b, size_t a) { return (b + a - 1) / a * a; }
 
+// Autotuner core: runs launch(i) reps times for each i < n (a launch returning
+// LRA_ERR_INVALID_ARG marks shape i as unusable, time -1), timing each launch
+// with CUDA events on the stream, and returns the fastest usable i in *best.
+template <class Launch>
+lra_status time_shapes(int n, int reps, cudaStream_t stream, Launch launch, float* ms, int* best) {
+  cudaEvent_t e0, e1;
+  LRA_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LRA_ERR_CUDA; }
+  lra_status st = LRA_OK;
+  float bt = 0.f;
+  int bi = -1;
+  for (int i = 0; i < n && st == LRA_OK; ++i) {
+    float fastest = -1.f;
+    for (int r = 0; r < reps; ++r) {
+      if (cudaEventRecord(e0, stream) != cudaSuccess) { st = LRA_ERR_CUDA; break; }
+      const lra_status ls = launch(i);
+      if (ls == LRA_ERR_INVALID_ARG) { fastest = -1.f; break; }
+      if (ls != LRA_OK) { st = ls; break; }
+      float t = 0.f;
+      if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) { st = LRA_ERR_CUDA; break; }
+      if (fastest < 0.f || t < fastest) fastest = t;
+    }
+    if (ms != nullptr) ms[i] = fastest;
+    if (fastest >= 0.f && (bi < 0 || fastest < bt)) { bt = fastest; bi = i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LRA_OK) return st;
+  if (bi < 0) return LRA_ERR_INVALID_ARG;
+  *best = bi;
+  return LRA_OK;
+}
+
 // Staged generator sizes of lra_ca_params: none, or ascending sizes >= 1 that
 // end at par->k, with a margin >= 0.
 inline bool stages_valid(const lra_ca_params* par) {
