@@ -5,12 +5,17 @@
 Default workload (``fmm``): the generators of an FMM / HSS matrix -- C-A CUR
 approximations of the 4096 well-separated block pairs of an octree over 2^20
 uniform points in [0,1]^3 (boxes of 64..2048 points, Laplace kernel evaluated
-on the fly, rank <= 64 adapted at tolerance 1e-6, 3 C-A loops, FP64 pivots and
-nucleus).  One step = the batched C-A launch (all blocks, nuclei included) +
-the batched a-posteriori residual sample (16 x 16 entries per block); the
-metric counts the blocks whose sampled relative Frobenius error is <= 1e-6.
-The ``dense8192_*`` workloads run one C-A CUR of an 8192 x 8192 FP32 input
-instead (one LRA per step).
+on the fly, rank <= 64 adapted at tolerance 1e-6 with generator sizes staged
+28/40/64, 3 C-A loops), in the mixed form: kernel entries in FP32, pivots, LU,
+swaps and nucleus in FP64.  One step = the batched C-A launch (all blocks,
+nuclei included) + the batched a-posteriori residual sample (16 x 16 entries
+per block, against the FP64 entries); the metric counts the blocks whose
+sampled relative Frobenius error is <= 1e-6.  The plain FP64 forms of the same
+batch (same sizes, and fixed k = 64) are measured in the same run and reported
+under config.comparisons.  Other workloads: ``fmm_f64``, ``fmm_fixedk``,
+``laplace65536_k*`` (one LRA of the 65536^2 Laplace kernel), ``dense8192_*``
+(one LRA of an 8192^2 FP32 input with a multiplier), ``tests{2,3,4}_*`` (the
+paper's random-input tests), ``gauss_apply`` (differentiable CUR apply).
 
 Inputs are seeded, synthetic and resident in HBM before the timed region; L2 is
 flushed (a 256 MiB write, untimed) before every timed step; each step is timed
@@ -145,6 +150,15 @@ class FmmWorkload:
         import paper_1710_07946_gb300 as lra
         lra.lra_ca_run_batched(d["bt"])
         lra.lra_residual_sample_batched(d["bt"], d["Q"], d["S"], d["stats"], problem=d["prob64"])
+
+    def comparisons(self):
+        """The plain FP64 GPU forms of the same batch, measured in the same run."""
+        if self.entries != "f32":
+            return []
+        kw = dict(npts=self.npts, nblocks=self.nblocks, k=self.k, sweeps=self.sweeps, tol=self.tol, q=self.q,
+                  s=self.s)
+        return [("plain_fp64_same_sizes", type(self)(entries="f64", stages=self.stages, margin=self.margin, **kw)),
+                ("plain_fp64_fixed_k64", type(self)(entries="f64", stages=None, **kw))]
 
     def check(self, d):
         info = d["bt"].out["info"].cpu().numpy()
@@ -642,8 +656,8 @@ class FmmSmallWorkload(FmmWorkload):
 
 
 WORKLOADS = {
-    "fmm": FmmWorkload,
-    "fmm_f32": lambda: FmmWorkload(entries="f32"),
+    "fmm": lambda: FmmWorkload(entries="f32"),
+    "fmm_f64": FmmWorkload,
     "fmm_fixedk": lambda: FmmWorkload(stages=None),
     "fmm_small": FmmSmallWorkload,
     **{f"laplace65536_k{k}{sfx}": (lambda k=k, e=e: LaplaceSingleWorkload(k, e))
@@ -891,6 +905,30 @@ def run_lib(args, wl):
     e2e_s, _ = job_totals(time.perf_counter() - t0, 0, world, dev)
     e2e_value = job_units / e2e_s
 
+    # comparison forms of the same problem (each rank its own; rank 0 reports)
+    comparisons = {}
+    for label, other in (wl.comparisons() if hasattr(wl, "comparisons") else []):
+        d2 = other.device(h, dev)
+        for _ in range(2):
+            other.step(d2)
+        torch.cuda.synchronize()
+        nst = max(1, min(args.steps, 3))
+        ms2 = 0.0
+        for i in range(nst):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            other.step(d2)
+            e1.record(stream)
+            e1.synchronize()
+            ms2 += e0.elapsed_time(e1)
+        r2 = other.check(d2)
+        v2 = r2["units"] * nst / (ms2 / 1e3)
+        comparisons[label] = {"workload": other.name, "value": v2, "ms_per_step": ms2 / nst, "steps": nst,
+                              "rel_fro_err_sampled_max": float(np.max(r2["err"])),
+                              "frac_blocks_err_le_1e-6": float(np.mean(r2["err"] <= ERR_BOUND)),
+                              "speedup_of_this_line": None}
+        del d2
     if rank == 0:
         kms, kn = prof.get(wl.kernel, (float("nan"), 0))
         kavg = kms / max(kn, 1) / 1e3
@@ -906,6 +944,10 @@ def run_lib(args, wl):
                    parallelism=f"{world} independent problem(s), one per GPU", mode="fp64",
                    graph_ms_per_step=graph_ms, wall_s=t_wall)
         cfg.update(wl.extra(res))
+        for c in comparisons.values():
+            c["speedup_of_this_line"] = value / c["value"] if c["value"] > 0 else None
+        if comparisons:
+            cfg["comparisons"] = comparisons
         line = {
             "metric": METRIC, "value": value, "unit": wl.unit, "n_gpus": world, "steps": args.steps,
             "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
