@@ -32,7 +32,7 @@ from typing import Optional
 import numpy as np
 
 SRC_DENSE, SRC_LAPLACE, SRC_GAUSSIAN = 0, 1, 2
-MULT_NONE, MULT_ARHT, MULT_SPARSE = 0, 1, 2
+MULT_NONE, MULT_ARHT, MULT_SPARSE, MULT_BIDIAG = 0, 1, 2, 3
 
 
 @dataclass
@@ -48,9 +48,9 @@ class Problem:
     Y: Optional[np.ndarray] = None          # (n, 3) float64 source points
     ell: float = 1.0                        # Gaussian length scale
     mkind: int = MULT_NONE
-    depth: int = 0                          # ARHT recursion depth d
-    perm: Optional[np.ndarray] = None       # ARHT permutation (n,) int32
-    dsign: Optional[np.ndarray] = None      # ARHT diagonal (n,) int8, +-1
+    depth: int = 0                          # ARHT recursion depth d (bidiagonal: number of factors q)
+    perm: Optional[np.ndarray] = None       # ARHT permutation (n,) int32 (bidiagonal: (q, n) permutations)
+    dsign: Optional[np.ndarray] = None      # ARHT diagonal (n,) int8, +-1 (bidiagonal: (q, n) signs)
     nnz: int = 0                            # sparse multiplier nonzeros per column
     srow: Optional[np.ndarray] = None       # (n, nnz) int32 ascending per column
     ssign: Optional[np.ndarray] = None      # (n, nnz) int8, +-1
@@ -101,6 +101,23 @@ def sparse_pm1_descriptor(n: int, nnz: int, seed: int):
         srow[j] = np.sort(g.choice(n, size=nnz, replace=False))
     ssign = np.where(g.random((n, nnz)) < 0.5, -1, 1).astype(np.int8)
     return srow, ssign
+
+
+def bidiag_descriptor(n: int, q: int, seed: int):
+    """q factors (I + D_i S) P_i: per factor a random permutation (column a of P_i
+    is e_{perm[i, a]}) and Rademacher signs D_i (q x n each)."""
+    if q < 1 or n < 2:
+        raise ValueError("q >= 1 factors, n >= 2")
+    g = rng(seed)
+    perms = np.stack([g.permutation(n) for _ in range(q)]).astype(np.int32)
+    signs = np.where(g.random((q, n)) < 0.5, -1, 1).astype(np.int8)
+    return perms, signs
+
+
+def with_bidiag(p: Problem, q: int, seed: int) -> Problem:
+    perms, signs = bidiag_descriptor(p.n, q, seed)
+    p.mkind, p.depth, p.perm, p.dsign = MULT_BIDIAG, q, perms, signs
+    return p
 
 
 def with_arht(p: Problem, depth: int, seed: int) -> Problem:

@@ -25,7 +25,7 @@ class _Problem(ct.Structure):
         ("W", ct.c_void_p), ("ldw", ct.c_int64), ("X", ct.c_void_p), ("Y", ct.c_void_p),
         ("ell", ct.c_double), ("mkind", ct.c_int32), ("depth", ct.c_int32),
         ("perm", ct.c_void_p), ("dsign", ct.c_void_p), ("nnz", ct.c_int32),
-        ("srow", ct.c_void_p), ("ssign", ct.c_void_p),
+        ("srow", ct.c_void_p), ("ssign", ct.c_void_p), ("brow", ct.c_void_p), ("bval", ct.c_void_p),
     ]
 
 
@@ -47,6 +47,7 @@ def lib():
         L.orc_ca_run.restype = ct.c_int
         L.orc_ca_run_adaptive.argtypes = [P, vp, i32, i32, i32, vp, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_ca_run_adaptive.restype = ct.c_int
+        L.orc_bidiag_columns.argtypes = [i64, i32, vp, vp, vp, vp]
         L.orc_cynical.argtypes = [P, i32, i32, i32, vp, vp, vp, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp]
         L.orc_cynical.restype = ct.c_int
         L.orc_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp]
@@ -101,6 +102,13 @@ class _Marshalled:
             ss = np.ascontiguousarray(p.ssign, dtype=np.int8)
             self.keep += [sr, ss]
             s.nnz, s.srow, s.ssign = int(p.nnz), sr.ctypes.data, ss.ctypes.data
+        elif p.mkind == 3:
+            perms = np.ascontiguousarray(p.perm, dtype=np.int32)
+            sg = np.ascontiguousarray(p.dsign, dtype=np.int8)
+            brow, bval = bidiag_columns(p.n, p.depth, perms, sg)
+            self.keep += [perms, sg, brow, bval]
+            s.depth, s.perm, s.dsign = int(p.depth), perms.ctypes.data, sg.ctypes.data
+            s.brow, s.bval = brow.ctypes.data, bval.ctypes.data
         self.s = s
 
     @property
@@ -239,6 +247,17 @@ def cynical(p, kind, r, q, K, L, I0s, sweeps=3, h=1.01, max_swaps=1000, rank_tol
                       rank_tol, _ptr(I), _ptr(J), _ptr(C), _ptr(U), _ptr(R), _ptr(info))
     return dict(I=I, J=J, C=C, U=U, R=R, K=K, L=L, rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]),
                 status=int(info[3]))
+
+
+def bidiag_columns(n, q, perms, signs):
+    """Columns of the product of q quasi-Gaussian factors (I + D_i S) P_i:
+    (n, 2^q) rows and integer values (0 = unused slot), ascending rows."""
+    perms = np.ascontiguousarray(perms, dtype=np.int32)
+    signs = np.ascontiguousarray(signs, dtype=np.int8)
+    rows = np.zeros((n, 1 << q), dtype=np.int32)
+    vals = np.zeros((n, 1 << q), dtype=np.int32)
+    lib().orc_bidiag_columns(int(n), int(q), _ptr(perms), _ptr(signs), _ptr(rows), _ptr(vals))
+    return rows, vals
 
 
 def cur_apply(C, U, R, X):

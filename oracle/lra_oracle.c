@@ -45,7 +45,7 @@
 /* ------------------------------------------------------------------ */
 enum { ORC_DENSE = 0, ORC_LAPLACE = 1, ORC_GAUSSIAN = 2 };
 enum { ORC_F64 = 0, ORC_F32 = 1 };
-enum { ORC_MULT_NONE = 0, ORC_MULT_ARHT = 1, ORC_MULT_SPARSE = 2 };
+enum { ORC_MULT_NONE = 0, ORC_MULT_ARHT = 1, ORC_MULT_SPARSE = 2, ORC_MULT_BIDIAG = 3 };
 
 typedef struct {
   int32_t src;          /* ORC_DENSE / ORC_LAPLACE / ORC_GAUSSIAN            */
@@ -63,6 +63,12 @@ typedef struct {
   int32_t nnz;          /* sparse: nonzeros per column                        */
   const int32_t* srow;  /* sparse: n*nnz row indices, ascending per column    */
   const int8_t* ssign;  /* sparse: n*nnz signs (+-1)                          */
+  /* bidiagonal products (mkind ORC_MULT_BIDIAG, depth = q factors; perm and
+   * dsign hold q x n permutations and signs): the columns of the product,
+   * expanded by orc_bidiag_columns, 2^q slots each, ascending rows, value 0
+   * marking an unused slot */
+  const int32_t* brow;
+  const int32_t* bval;
 } orc_problem;
 
 /* Entry w_ij of the input W (no multiplier).  Kernel entries follow the
@@ -90,6 +96,40 @@ static double entry_w(const orc_problem* p, int64_t i, int64_t j) {
   return exp(-(r2 / (2.0 * p->ell * p->ell)));
 }
 
+/* Columns of the product M = F_1 F_2 ... F_q of the paper's quasi-Gaussian
+ * factors F_i = (I + D_i S) P_i (section "Approximation of a Gaussian matrix by
+ * the product of random bidiagonal matrices", eq. def11): S the cyclic
+ * down-shift, D_i = diag(signs[i]), column a of P_i = e_{perms[i][a]}, so that
+ * F_i e_a = e_b + signs[i][b'] e_{b'} with b = perms[i][a], b' = (b + 1) mod n.
+ * Column j is M e_j = F_1 (F_2 (... (F_q e_j))): a dense work vector, then its
+ * nonzeros in ascending rows into 2^q slots (integer values; 0 = unused). */
+void orc_bidiag_columns(int64_t n, int32_t q, const int32_t* perms, const int8_t* signs, int32_t* rows,
+                        int32_t* vals) {
+  int64_t w = 1LL << q;
+  int64_t* v = (int64_t*)calloc((size_t)n, sizeof(int64_t));
+  int64_t* u = (int64_t*)calloc((size_t)n, sizeof(int64_t));
+  for (int64_t j = 0; j < n; ++j) {
+    memset(v, 0, sizeof(int64_t) * (size_t)n);
+    v[j] = 1;
+    for (int32_t f = q - 1; f >= 0; --f) {
+      memset(u, 0, sizeof(int64_t) * (size_t)n);
+      for (int64_t a = 0; a < n; ++a) {
+        if (v[a] == 0) continue;
+        int64_t b = perms[(int64_t)f * n + a];
+        int64_t b1 = (b + 1) % n;
+        u[b] += v[a];
+        u[b1] += (int64_t)signs[(int64_t)f * n + b1] * v[a];
+      }
+      memcpy(v, u, sizeof(int64_t) * (size_t)n);
+    }
+    int64_t c = 0;
+    for (int64_t a = 0; a < n; ++a)
+      if (v[a] != 0 && c < w) { rows[j * w + c] = (int32_t)a; vals[j * w + c] = (int32_t)v[a]; ++c; }
+    for (; c < w; ++c) { rows[j * w + c] = 0; vals[j * w + c] = 0; }
+  }
+  free(v); free(u);
+}
+
 /* 2^(-d/2): the scale that makes the abridged Hadamard matrix orthogonal
  * ("orthogonal up to scaling", appendix on abridged multipliers). */
 static double arht_scale(int d) { return 1.0 / sqrt((double)(1LL << d)); }
@@ -115,6 +155,17 @@ static double entry_wp(const orc_problem* p, int64_t i, int64_t j) {
       int64_t r = a * s + t;
       double v = entry_w(p, i, r) * (double)p->dsign[r];
       if (popcount32((uint32_t)(a & b)) & 1) acc = acc - v; else acc = acc + v;
+    }
+    return acc * arht_scale(p->depth);
+  }
+  if (p->mkind == ORC_MULT_BIDIAG) {
+    /* nonzero slots in ascending row order, each an fma with its integer weight */
+    int64_t w = 1LL << p->depth;
+    double acc = 0.0;
+    for (int64_t t = 0; t < w; ++t) {
+      int32_t v = p->bval[j * w + t];
+      if (v == 0) continue;
+      acc = fma((double)v, entry_w(p, i, p->brow[j * w + t]), acc);
     }
     return acc * arht_scale(p->depth);
   }
@@ -775,6 +826,23 @@ void orc_multiplier_dense(const orc_problem* p, double* M) {
     double v = 1.0 / sqrt((double)p->nnz);
     for (int64_t j = 0; j < n; ++j)
       for (int t = 0; t < p->nnz; ++t) M[(int64_t)p->srow[j * p->nnz + t] * n + j] = p->ssign[j * p->nnz + t] * v;
+    return;
+  }
+  if (p->mkind == ORC_MULT_BIDIAG) {
+    /* M = F_1 ... F_q built left to right: column a of M F = M e_b + s M e_b' */
+    double* T = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    for (int64_t i = 0; i < n; ++i) M[i * n + i] = 1.0;
+    for (int32_t f = 0; f < p->depth; ++f) {
+      for (int64_t a = 0; a < n; ++a) {
+        int64_t b = p->perm[(int64_t)f * n + a], b1 = (b + 1) % n;
+        double sg = (double)p->dsign[(int64_t)f * n + b1];
+        for (int64_t i = 0; i < n; ++i) T[i * n + a] = M[i * n + b] + sg * M[i * n + b1];
+      }
+      memcpy(M, T, sizeof(double) * (size_t)n * (size_t)n);
+    }
+    double sc = arht_scale(p->depth);
+    for (int64_t i = 0; i < n * n; ++i) M[i] *= sc;
+    free(T);
     return;
   }
   double* H = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);

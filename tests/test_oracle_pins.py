@@ -156,7 +156,7 @@ def test_nucleus_agrees_with_jacobi_svd_truncation_when_gap_is_large():
 
 # ------------------------------------------------------------------ C-A / CUR
 @pytest.mark.parametrize("seed", range(4))
-@pytest.mark.parametrize("mult", ["none", "arht", "sparse"])
+@pytest.mark.parametrize("mult", ["none", "arht", "sparse", "bidiag"])
 def test_exact_recovery_rank_r(seed, mult):
     """Theorem thdcmp: for rank-r W with a nonsingular r x r generator,
     W = C W_{I,J}^{-1} R exactly; with a multiplier M the back-transformed CUR
@@ -166,6 +166,8 @@ def test_exact_recovery_rank_r(seed, mult):
         li.with_arht(p, 2, seed + 50)
     elif mult == "sparse":
         li.with_sparse(p, 4, seed + 50)
+    elif mult == "bidiag":
+        li.with_bidiag(p, 3, seed + 50)
     I0 = li.initial_rows(128, 6, seed + 99)
     o = oracle.ca_run(p, 6, 3, I0)
     W = p.W
@@ -270,7 +272,7 @@ def test_arht_orthogonal_and_sparse(n, d):
     assert np.all((M != 0).sum(0) == 2 ** d) and np.all((M != 0).sum(1) == 2 ** d)
 
 
-@pytest.mark.parametrize("mult", ["arht1", "arht2", "arht3", "sparse"])
+@pytest.mark.parametrize("mult", ["arht1", "arht2", "arht3", "sparse", "bidiag1", "bidiag3", "bidiag5"])
 def test_multiplier_gathers_equal_dense_product(mult):
     """The strip gathers (closed-form column combinations) equal rows / columns
     of W M with M assembled densely from its recursive definition."""
@@ -279,6 +281,8 @@ def test_multiplier_gathers_equal_dense_product(mult):
     p = li.Problem(li.SRC_DENSE, 40, 48, W=W)
     if mult.startswith("arht"):
         li.with_arht(p, int(mult[-1]), 8)
+    elif mult.startswith("bidiag"):
+        li.with_bidiag(p, int(mult[-1]), 8)
     else:
         li.with_sparse(p, 4, 8)
     WM = W @ oracle.multiplier_dense(p)
@@ -295,6 +299,33 @@ def test_sparse_multiplier_structure():
     M = oracle.multiplier_dense(p)
     assert np.all((M != 0).sum(0) == 4)
     np.testing.assert_allclose(np.linalg.norm(M, axis=0), 1.0, rtol=1e-15)
+
+
+def test_bidiag_single_factor_closed_form():
+    """q = 1: M = 2^{-1/2} (I + D S) P of eq. def11, built entry by entry with numpy
+    (column a: 1 at row b = perm[a], the sign of row b+1 at row (b+1) mod n)."""
+    n = 37
+    p = li.Problem(li.SRC_DENSE, 3, n, W=np.zeros((3, n)))
+    li.with_bidiag(p, 1, 4)
+    F = np.zeros((n, n))
+    for a in range(n):
+        b = p.perm[0, a]
+        F[b, a] += 1.0
+        F[(b + 1) % n, a] += float(p.dsign[0, (b + 1) % n])
+    np.testing.assert_array_equal(oracle.multiplier_dense(p), F / np.sqrt(2.0))
+
+
+def test_bidiag_product_structure():
+    """The product of q factors: at most 2^q nonzeros per column, integer multiples
+    of 2^{-q/2}, E[M^T M] = I (each factor has E[F^T F] = 2 I): the mean squared
+    column norm over many columns is close to 1."""
+    n, q = 400, 4
+    p = li.Problem(li.SRC_DENSE, 3, n, W=np.zeros((3, n)))
+    li.with_bidiag(p, q, 11)
+    M = oracle.multiplier_dense(p) * 2.0 ** (q / 2)
+    assert (M != 0).sum(0).max() <= 2 ** q
+    np.testing.assert_array_equal(M, np.round(M))
+    assert abs(np.mean((M ** 2).sum(0)) / 2 ** q - 1.0) < 0.05
 
 
 def test_float32_input_is_widened_exactly():
