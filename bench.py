@@ -237,12 +237,15 @@ class DenseWorkload:
 
     def __init__(self, mult, n=8192, k=48, sweeps=4):
         self.mult, self.n, self.k, self.sweeps, self.q, self.s = mult, n, k, sweeps, 256, 256
-        self.name = f"dense{n}_f32_rank32_spikes1pct_{'arht2' if mult == 'arht' else 'sparse4'}_k{k}_s{sweeps}"
+        tag = {"arht": "arht2", "sparse": "sparse4", "bidiag": "bidiag3"}[mult]
+        self.name = f"dense{n}_f32_rank32_spikes1pct_{tag}_k{k}_s{sweeps}"
 
     def host(self, rank):
         p = li.dense_spiky(self.n, r=32, seed=1000 * rank)
         if self.mult == "arht":
             li.with_arht(p, 2, 7)
+        elif self.mult == "bidiag":
+            li.with_bidiag(p, 3, 7)
         else:
             li.with_sparse(p, 4, 7)
         I0 = li.initial_rows(self.n, self.k, 11)
@@ -251,7 +254,8 @@ class DenseWorkload:
 
     def config(self, h):
         return {"workload": self.name, "m": self.n, "n": self.n, "k": self.k, "sweeps": self.sweeps,
-                "multiplier": "ARHT d=2" if self.mult == "arht" else "sparse +-1, 4 nnz/col",
+                "multiplier": {"arht": "ARHT d=2", "sparse": "sparse +-1, 4 nnz/col",
+                               "bidiag": "product of 3 cyclic bidiagonal +-1 factors"}[self.mult],
                 "input_dtype": "f32", "residual_sample": f"{self.q}x{self.s}"}
 
     def device(self, h, dev):
@@ -260,8 +264,12 @@ class DenseWorkload:
         p = h["p"]
         W = torch.from_numpy(p.W).to(dev)
         prob = lra.Problem.dense(W)
-        mult = (lra.lra_precondition("arht", p.n, p.depth, p.perm, p.dsign) if p.mkind == li.MULT_ARHT
-                else lra.lra_precondition("sparse", p.n, p.nnz, p.srow, p.ssign))
+        if p.mkind == li.MULT_ARHT:
+            mult = lra.lra_precondition("arht", p.n, p.depth, p.perm, p.dsign)
+        elif p.mkind == li.MULT_BIDIAG:
+            mult = lra.lra_precondition("bidiag", p.n, p.depth, p.perm, p.dsign)
+        else:
+            mult = lra.lra_precondition("sparse", p.n, p.nnz, p.srow, p.ssign)
         I0 = torch.from_numpy(h["I0"]).to(dev)
         out = lra.lra_ca_run(prob, I0, self.k, self.sweeps, multiplier=mult)
         return dict(W=W, prob=prob, mult=mult, I0=I0, out=out, Q=torch.from_numpy(h["Q"]).to(dev),
@@ -671,6 +679,7 @@ WORKLOADS = {
     "tests2_n256_r16": lambda: RandomTestsWorkload(2, r=16),
     "dense8192_arht": lambda: DenseWorkload("arht"),
     "dense8192_sparse": lambda: DenseWorkload("sparse"),
+    "dense8192_bidiag": lambda: DenseWorkload("bidiag"),
 }
 
 

@@ -74,7 +74,8 @@ typedef struct {
 typedef enum {
   LRA_MULT_NONE = 0,
   LRA_MULT_ARHT = 1,        /* abridged randomized Hadamard 2^{-d/2} D H_{n,d} P     */
-  LRA_MULT_SPARSE_PM1 = 2   /* sparse +-1/sqrt(nnz) multiplier, nnz entries / column */
+  LRA_MULT_SPARSE_PM1 = 2,  /* sparse +-1/sqrt(nnz) multiplier, nnz entries / column */
+  LRA_MULT_BIDIAG = 3       /* 2^{-q/2} prod_{i=1..q} (I + D_i S) P_i, quasi-Gaussian */
 } lra_mult_kind;
 
 typedef struct lra_multiplier_s* lra_multiplier;   /* opaque, library-owned */
@@ -95,6 +96,14 @@ typedef struct lra_multiplier_s* lra_multiplier;   /* opaque, library-owned */
  *   kind = LRA_MULT_SPARSE_PM1: column j of M holds depth_or_nnz (1..16)
  *     entries signs[j*nnz+t] / sqrt(nnz) in the rows perm_or_rows[j*nnz+t],
  *     strictly ascending in t (host arrays of n*nnz int32 / int8).
+ *   kind = LRA_MULT_BIDIAG (Section "Approximation of a Gaussian matrix by the
+ *     product of random bidiagonal matrices", eq. def11): M = 2^{-q/2} F_1 ...
+ *     F_q, q = depth_or_nnz (1..6), F_i = (I + D_i S) P_i with S the cyclic
+ *     down-shift, D_i = diag(signs[i*n .. i*n+n)) (+-1) and column a of P_i equal
+ *     to e_b, b = perm_or_rows[i*n + a] (host arrays of q*n int32 / int8, each
+ *     row of perm_or_rows a permutation of 0..n-1).  Column j of M has at most
+ *     2^q nonzeros, integer multiples of 2^{-q/2}; w'_ij adds them in ascending
+ *     rows, each as fma(value, w, sum), and scales once.  n >= 2.
  * The random draws (signs, permutation, positions) are inputs, so that runs are
  * reproducible.  The descriptor is copied to device memory owned by the handle;
  * the host arrays may be freed on return.  The copy is synchronous.

@@ -31,7 +31,7 @@ LRA_OK, LRA_ERR_INVALID_ARG, LRA_ERR_CUDA, LRA_ERR_NONFINITE, LRA_ERR_TIMEOUT, L
 LRA_WARN_RANK_DEFICIENT, LRA_WARN_NOT_CONVERGED = 16, 17
 LRA_F64, LRA_F32 = 0, 1
 LRA_DENSE, LRA_KERNEL_LAPLACE, LRA_KERNEL_GAUSSIAN = 0, 1, 2
-LRA_MULT_NONE, LRA_MULT_ARHT, LRA_MULT_SPARSE_PM1 = 0, 1, 2
+LRA_MULT_NONE, LRA_MULT_ARHT, LRA_MULT_SPARSE_PM1, LRA_MULT_BIDIAG = 0, 1, 2, 3
 LRA_MODE_FP64, LRA_MODE_MIXED = 0, 1
 LRA_INFO_LEN = 8
 LRA_MAX_STAGES = 8
@@ -227,12 +227,13 @@ def lra_version() -> str:
 
 
 def lra_precondition(kind: str, n: int, depth_or_nnz: int, perm_or_rows, signs) -> Multiplier:
-    """Right multiplier M of W' = W M: ``kind`` 'arht' (2^{-d/2} D H_{n,d} P) or
-    'sparse' (+-1/sqrt(nnz) entries).  perm_or_rows / signs: host int32 / int8
-    arrays (numpy or CPU tensors) holding the random draws."""
+    """Right multiplier M of W' = W M: ``kind`` 'arht' (2^{-d/2} D H_{n,d} P),
+    'sparse' (+-1/sqrt(nnz) entries) or 'bidiag' (2^{-q/2} prod (I + D_i S) P_i,
+    q = depth_or_nnz factors; perm_or_rows, signs q x n).  perm_or_rows / signs:
+    host int32 / int8 arrays (numpy or CPU tensors) holding the random draws."""
     import numpy as np
     L = _load()
-    k = {"arht": LRA_MULT_ARHT, "sparse": LRA_MULT_SPARSE_PM1}[kind]
+    k = {"arht": LRA_MULT_ARHT, "sparse": LRA_MULT_SPARSE_PM1, "bidiag": LRA_MULT_BIDIAG}[kind]
     idx = np.ascontiguousarray(np.asarray(perm_or_rows), dtype=np.int32).reshape(-1)
     sg = np.ascontiguousarray(np.asarray(signs), dtype=np.int8).reshape(-1)
     h = ct.c_void_p()

@@ -44,6 +44,9 @@ lra_status make_dev_problem(const lra_problem* p, lra_multiplier mult, DevProble
     if (mult->kind == LRA_MULT_ARHT) {
       d.depth = mult->param;
       d.s = p->n >> mult->param;
+    } else if (mult->kind == LRA_MULT_BIDIAG) {
+      d.depth = mult->param;
+      d.nnz = 1 << mult->param;
     } else {
       d.nnz = mult->param;
     }
@@ -81,6 +84,62 @@ lra_status current_device_info(DeviceInfo* info) {
   return LRA_OK;
 }
 
+// The columns of M = F_1 ... F_q (F_f = (I + D_f S) P_f): column j is
+// F_1 (... (F_q e_j)), kept as a short list of (row, integer value) terms that
+// is expanded factor by factor (each term a -> b = perm_f[a] with its value and
+// b' = (b + 1) mod n with sign_f[b'] times it), merged by row after every
+// factor.  Stored with 2^q slots per column in ascending rows, value 0 in the
+// unused slots; the scale 2^{-q/2} is applied by the gathers.
+static lra_status make_bidiag(lra_multiplier* out, int64_t n, int32_t q, const int32_t* perms,
+                              const int8_t* signs) {
+  const size_t w = (size_t)1 << q;
+  std::vector<int32_t> rows((size_t)n * w, 0);
+  std::vector<int8_t> vals((size_t)n * w, 0);
+  std::vector<std::pair<int64_t, int64_t>> cur, nxt;
+  for (int64_t j = 0; j < n; ++j) {
+    cur.assign(1, {j, 1});
+    for (int f = q - 1; f >= 0; --f) {
+      nxt.clear();
+      for (const auto& tv : cur) {
+        const int64_t b = perms[(int64_t)f * n + tv.first], b1 = (b + 1) % n;
+        nxt.push_back({b, tv.second});
+        nxt.push_back({b1, (int64_t)signs[(int64_t)f * n + b1] * tv.second});
+      }
+      std::sort(nxt.begin(), nxt.end());
+      cur.clear();
+      for (const auto& tv : nxt) {
+        if (!cur.empty() && cur.back().first == tv.first) cur.back().second += tv.second;
+        else cur.push_back(tv);
+      }
+    }
+    size_t c = 0;
+    for (const auto& tv : cur)
+      if (tv.second != 0) {
+        rows[(size_t)j * w + c] = (int32_t)tv.first;
+        vals[(size_t)j * w + c] = (int8_t)tv.second;
+        ++c;
+      }
+  }
+  lra_multiplier m = new lra_multiplier_s;
+  m->kind = LRA_MULT_BIDIAG;
+  m->n = n;
+  m->param = q;
+  m->scale = 1.0 / std::sqrt((double)(int64_t(1) << q));
+  m->d_idx = nullptr;
+  m->d_sign = nullptr;
+  if (cudaMalloc(&m->d_idx, rows.size() * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&m->d_sign, vals.size() * sizeof(int8_t)) != cudaSuccess ||
+      cudaMemcpy(m->d_idx, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_sign, vals.data(), vals.size() * sizeof(int8_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(m->d_idx);
+    cudaFree(m->d_sign);
+    delete m;
+    return LRA_ERR_CUDA;
+  }
+  *out = m;
+  return LRA_OK;
+}
+
 }  // namespace lra
 
 extern "C" {
@@ -114,6 +173,20 @@ lra_status lra_precondition(lra_multiplier* out, int32_t kind, int64_t n, int32_
         if (s != 1 && s != -1) return LRA_ERR_INVALID_ARG;
       }
     scale = 1.0 / std::sqrt((double)param);
+  } else if (kind == LRA_MULT_BIDIAG) {
+    if (param < 1 || param > 6 || n < 2) return LRA_ERR_INVALID_ARG;
+    std::vector<unsigned char> seen((size_t)n);
+    for (int f = 0; f < param; ++f) {
+      std::fill(seen.begin(), seen.end(), 0);
+      for (int64_t a = 0; a < n; ++a) {
+        const int32_t b = idx[(int64_t)f * n + a];
+        if (b < 0 || b >= n || seen[(size_t)b]) return LRA_ERR_INVALID_ARG;
+        seen[(size_t)b] = 1;
+        const int8_t sg = signs[(int64_t)f * n + a];
+        if (sg != 1 && sg != -1) return LRA_ERR_INVALID_ARG;
+      }
+    }
+    return lra::make_bidiag(out, n, param, idx, signs);
   } else {
     return LRA_ERR_INVALID_ARG;
   }

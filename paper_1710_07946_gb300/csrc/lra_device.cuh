@@ -78,6 +78,28 @@ __device__ __forceinline__ double w_entry(const DevProblem& P, int64_t i, int64_
 __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64_t j) {
   if (P.mkind == LRA_MULT_NONE) return w_entry(P, i, j);
   double acc = 0.0;
+  if (P.mkind == LRA_MULT_BIDIAG) {
+    // product of bidiagonal factors: up to 2^q integer-weighted terms in
+    // ascending rows (value 0 = unused slot), each fma(value, w, sum)
+    const int32_t* rows = P.perm + j * P.nnz;
+    const int8_t* vs = P.sign + j * P.nnz;
+    for (int t0 = 0; t0 < P.nnz; t0 += TERMS) {
+      double v[TERMS];
+      int c[TERMS];
+#pragma unroll
+      for (int e = 0; e < TERMS; ++e) {
+        c[e] = 0;
+        if (t0 + e < P.nnz) {
+          c[e] = __ldg(vs + t0 + e);
+          if (c[e] != 0) v[e] = w_entry(P, i, __ldg(rows + t0 + e));
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < TERMS; ++e)
+        if (c[e] != 0) acc = fma((double)c[e], v[e], acc);
+    }
+    return acc * P.mscale;
+  }
   if (P.mkind == LRA_MULT_ARHT) {
     const int64_t pj = __ldg(P.perm + j);
     const int64_t b = pj / P.s, t = pj - b * P.s;

@@ -91,8 +91,10 @@ inline bool stages_valid(const lra_ca_params* par) {
 }
 
 // Inputs whose maxvol steps the certified FP32 mode handles: dense inputs and
-// the FP64 Laplace kernel (its FP32 bounds are relative to the FP64 entries).
+// the FP64 Laplace kernel (its FP32 bounds are relative to the FP64 entries),
+// without the bidiagonal-product multiplier.
 inline bool mixed_supported(const DevProblem& P) {
+  if (P.mkind == LRA_MULT_BIDIAG) return false;       // no FP32 bounds for integer-weighted sums
   return P.src == LRA_DENSE || (P.src == LRA_KERNEL_LAPLACE && P.dtype == LRA_F64);
 }
 

@@ -20,6 +20,8 @@ def to_device(p: li.Problem):
         mult = lra.lra_precondition("arht", p.n, p.depth, p.perm, p.dsign)
     elif p.mkind == li.MULT_SPARSE:
         mult = lra.lra_precondition("sparse", p.n, p.nnz, p.srow, p.ssign)
+    elif p.mkind == li.MULT_BIDIAG:
+        mult = lra.lra_precondition("bidiag", p.n, p.depth, p.perm, p.dsign)
     return prob, mult
 
 

@@ -49,11 +49,13 @@ def test_dense_multi_cta_ragged(m, n, k):
     assert_parity(o, g)
 
 
-@pytest.mark.parametrize("mult,arg", [("arht", 1), ("arht", 2), ("arht", 3), ("sparse", 4)])
+@pytest.mark.parametrize("mult,arg", [("arht", 1), ("arht", 2), ("arht", 3), ("sparse", 4), ("bidiag", 1), ("bidiag", 3), ("bidiag", 5)])
 def test_float32_with_multipliers(mult, arg):
     p = li.dense_spiky(1024, r=16, seed=3)
     if mult == "arht":
         li.with_arht(p, arg, 11)
+    elif mult == "bidiag":
+        li.with_bidiag(p, arg, 11)
     else:
         li.with_sparse(p, arg, 11)
     I0 = li.initial_rows(1024, 24, 5)
@@ -178,13 +180,15 @@ def test_residual_sample_matches_oracle():
 
 
 # ---------------------------------------------------------------- full-size benchmark workload
-@pytest.mark.parametrize("mult", ["arht", "sparse"])
+@pytest.mark.parametrize("mult", ["arht", "sparse", "bidiag"])
 def test_dense8192_benchmark_workload(mult):
-    """8192 x 8192 FP32 rank-32 + 1% spikes, ARHT d=2 or sparse +-1, k = 48,
-    4 loops: the benchmark's configuration, compared in full."""
+    """8192 x 8192 FP32 rank-32 + 1% spikes, ARHT d=2, sparse +-1 or a product of 3
+    bidiagonal factors, k = 48, 4 loops: the benchmark's configuration, compared in full."""
     p = li.dense_spiky(8192, r=32, seed=0)
     if mult == "arht":
         li.with_arht(p, 2, 7)
+    elif mult == "bidiag":
+        li.with_bidiag(p, 3, 7)
     else:
         li.with_sparse(p, 4, 7)
     I0 = li.initial_rows(8192, 48, 11)
