@@ -48,6 +48,10 @@ def lib():
         L.orc_ca_run_adaptive.argtypes = [P, vp, i32, i32, i32, vp, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_ca_run_adaptive.restype = ct.c_int
         L.orc_bidiag_columns.argtypes = [i64, i32, vp, vp, vp, vp]
+        L.orc_nucleus_rect.argtypes = [vp, i32, i32, f64, vp]
+        L.orc_nucleus_rect.restype = i32
+        L.orc_oversample.argtypes = [P, vp, vp, i32, i32, f64, f64, vp, vp, vp, vp, vp]
+        L.orc_oversample.restype = ct.c_int
         L.orc_cynical.argtypes = [P, i32, i32, i32, vp, vp, vp, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp]
         L.orc_cynical.restype = ct.c_int
         L.orc_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp]
@@ -258,6 +262,35 @@ def bidiag_columns(n, q, perms, signs):
     vals = np.zeros((n, 1 << q), dtype=np.int32)
     lib().orc_bidiag_columns(int(n), int(q), _ptr(perms), _ptr(signs), _ptr(rows), _ptr(vals))
     return rows, vals
+
+
+def nucleus_rect(G, tol):
+    """U (l x k) = pinv of the rank-r QRP truncation of the k x l generator G (k <= l); returns (U, r)."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    k, l = G.shape
+    assert k <= l
+    U = np.empty((l, k))
+    r = lib().orc_nucleus_rect(_ptr(G), k, l, tol, _ptr(U))
+    return U, int(r)
+
+
+def oversample(p, I, J, pextra, h=1.01, rank_tol=1e-13):
+    """Rectangular k x (k + pextra) generator grown from the square one (I, J) by
+    greedy volume expansions (orc_oversample).  Returns J (l), C (m x l),
+    U (l x k), R (k x n), rank, l, status."""
+    mp = _Marshalled(p)
+    I = np.ascontiguousarray(I, dtype=np.int32)
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    k, L = len(I), len(I) + int(pextra)
+    Jo = np.zeros(L, dtype=np.int32)
+    C = np.zeros((p.m, L)); U = np.zeros((L, k)); R = np.zeros((k, p.n))
+    info = np.zeros(3, dtype=np.int32)
+    lib().orc_oversample(mp.ref, _ptr(I), _ptr(J), k, int(pextra), h, rank_tol, _ptr(Jo), _ptr(C), _ptr(U), _ptr(R),
+                         _ptr(info))
+    l = int(info[1])
+    return dict(J=Jo[:l].copy(), C=np.ascontiguousarray(C.reshape(-1)[:p.m * l].reshape(p.m, l)),
+                U=np.ascontiguousarray(U.reshape(-1)[:l * k].reshape(l, k)), R=R, rank=int(info[0]), l=l,
+                status=int(info[2]))
 
 
 def cur_apply(C, U, R, X):

@@ -471,6 +471,75 @@ int32_t orc_nucleus(const double* G, int32_t k, double tol, double* U) {
   return r;
 }
 
+/*
+ * orc_nucleus_rect: the nucleus of a rectangular k x l generator G (k <= l,
+ * row-major): U = pinv of the rank-r truncation of its QRP factorisation
+ * (Algorithm algcnnncl with Remark reubsc's rank-revealing factorisation),
+ * l x k row-major.  As orc_nucleus: Householder QR with column pivoting over
+ * the l columns (k steps, column norms over rows t.. recomputed each step,
+ * lowest index on ties), r = #{|R_tt| > tol |R_00|}, then the complete
+ * orthogonal decomposition: T^T = (rows 0..r-1 of R)^T (l x r) = Z S, and
+ * U = P Z S^{-T} Q_r^T.  Returns r.
+ */
+int32_t orc_nucleus_rect(const double* G, int32_t k, int32_t l, double tol, double* U) {
+  double* A = (double*)malloc(sizeof(double) * (size_t)k * (size_t)l);     /* A[col*k + row] */
+  double* taus = (double*)malloc(sizeof(double) * (size_t)k);
+  int32_t* perm = (int32_t*)malloc(sizeof(int32_t) * (size_t)l);
+  for (int32_t i = 0; i < k; ++i)
+    for (int32_t j = 0; j < l; ++j) A[(int64_t)j * k + i] = G[(int64_t)i * l + j];
+  for (int32_t j = 0; j < l; ++j) perm[j] = j;
+  for (int32_t t = 0; t < k; ++t) {
+    int32_t pj = t; double bn = -1.0;
+    for (int32_t j = t; j < l; ++j) {
+      double s = 0.0;
+      for (int32_t i = t; i < k; ++i) s = fma(A[(int64_t)j * k + i], A[(int64_t)j * k + i], s);
+      if (s > bn) { bn = s; pj = j; }
+    }
+    if (pj != t) {
+      for (int32_t i = 0; i < k; ++i) {
+        double tmp = A[(int64_t)t * k + i]; A[(int64_t)t * k + i] = A[(int64_t)pj * k + i]; A[(int64_t)pj * k + i] = tmp;
+      }
+      int32_t tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp;
+    }
+    taus[t] = house(&A[(int64_t)t * k + t], k - t, 1);
+    for (int32_t j = t + 1; j < l; ++j) apply_house(&A[(int64_t)t * k + t], 1, taus[t], &A[(int64_t)j * k + t], k - t, 1);
+  }
+  int32_t r = 0;
+  double r00 = fabs(A[0]);
+  if (r00 > 0.0)
+    while (r < k && fabs(A[(int64_t)r * k + r]) > tol * r00) ++r;
+  memset(U, 0, sizeof(double) * (size_t)l * (size_t)k);
+  if (r == 0) { free(A); free(taus); free(perm); return 0; }
+  double* Qt = (double*)calloc((size_t)k * (size_t)k, sizeof(double));      /* Q^T, column-major */
+  for (int32_t i = 0; i < k; ++i) Qt[i * k + i] = 1.0;
+  for (int32_t t = 0; t < k; ++t)
+    for (int32_t j = 0; j < k; ++j) apply_house(&A[(int64_t)t * k + t], 1, taus[t], &Qt[j * k + t], k - t, 1);
+  /* T^T (l x r, column-major: column c = row c of R over columns c..l-1) and its QR */
+  double* Tt = (double*)calloc((size_t)l * (size_t)r, sizeof(double));
+  double* tz = (double*)malloc(sizeof(double) * (size_t)r);
+  for (int32_t c = 0; c < r; ++c)
+    for (int32_t i = c; i < l; ++i) Tt[(int64_t)c * l + i] = A[(int64_t)i * k + c];
+  for (int32_t c = 0; c < r; ++c) {
+    tz[c] = house(&Tt[(int64_t)c * l + c], l - c, 1);
+    for (int32_t j = c + 1; j < r; ++j) apply_house(&Tt[(int64_t)c * l + c], 1, tz[c], &Tt[(int64_t)j * l + c], l - c, 1);
+  }
+  /* X (l x k, column-major) = Z S^{-T} Q_r^T, one column at a time */
+  double* X = (double*)calloc((size_t)l * (size_t)k, sizeof(double));
+  for (int32_t col = 0; col < k; ++col) {
+    double* v = &X[(int64_t)col * l];
+    for (int32_t i = 0; i < r; ++i) {
+      double s = Qt[col * k + i];
+      for (int32_t p = 0; p < i; ++p) s = fma(-Tt[(int64_t)i * l + p], v[p], s);
+      v[i] = s / Tt[(int64_t)i * l + i];
+    }
+    for (int32_t c = r - 1; c >= 0; --c) apply_house(&Tt[(int64_t)c * l + c], 1, tz[c], &v[c], l - c, 1);
+  }
+  for (int32_t i = 0; i < l; ++i)
+    for (int32_t col = 0; col < k; ++col) U[(int64_t)perm[i] * k + col] = X[(int64_t)col * l + i];
+  free(A); free(taus); free(perm); free(Qt); free(Tt); free(tz); free(X);
+  return r;
+}
+
 /* ------------------------------------------------------------------ */
 /* C-A iterations                                                      */
 /* ------------------------------------------------------------------ */
@@ -676,6 +745,93 @@ int orc_cynical(const orc_problem* p, int32_t kind, int32_t r, int32_t q, int32_
     info[0] = inf[0]; info[1] = swaps; info[2] = inf[2]; info[3] = status;
   }
   free(S); free(Ii); free(Jj); free(Cq); free(Rq); free(lv);
+  return status;
+}
+
+/*
+ * orc_oversample: a rectangular k x l generator (l = k + p) from the rows I
+ * and columns J of a square one: Algorithm algrup's greedy expansions of a
+ * k x k submatrix to k x l, each adding the column that increases the volume
+ * of the generator C_g (sqrt det C_g C_g^T) the most; Theorem th3 bounds the
+ * CUR error of such generators.
+ *  1. X = B^{-1} W'[I, :], B = W'[I, J]: the C matrix of a maxvol step
+ *     (orc_maxvol) on the row strip warm-started at J with no swaps; its
+ *     selected set J0 (J unless the warm LU met a zero pivot) starts J'.
+ *  2. p times: the column j outside J' with the largest s_j = ||X[:, j]||^2
+ *     (ascending fma chain; lowest j on ties) joins J' (the squared volume
+ *     grows by the factor 1 + s_j); with x = X[:, j] and sigma = s_j, every
+ *     column q outside J' becomes X[:, q] - gamma (x . X[:, q]) x, gamma =
+ *     (1 - 1/sqrt(1 + sigma)) / sigma, which keeps s_q = b_q^T (C C^T)^{-1} b_q
+ *     for the grown generator (Sherman-Morrison), and s_q is recomputed.  No
+ *     column is added once the largest s_j is 0.
+ *  3. U = orc_nucleus_rect of W'[I, J'] (k x l), C = W'[:, J'] (m x l), R =
+ *     W[I, :] (k x n).
+ * J' (k + p), C (m x (k+p)), U ((k+p) x k) are sized for l = k + p; info:
+ * rank, l (used), status (worst of the maxvol step and the nucleus).
+ */
+int orc_oversample(const orc_problem* p, const int32_t* I, const int32_t* J, int32_t k, int32_t pextra,
+                   double h, double rank_tol, int32_t* Jo, double* C, double* U, double* R, int32_t* info) {
+  int64_t m = p->m, n = p->n;
+  int32_t l = k;
+  double* X = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
+  double* Rs = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
+  orc_gather_rows(p, I, k, Rs);
+  if (!all_finite(Rs, (int64_t)k * n)) {
+    info[0] = 0; info[1] = k; info[2] = ORC_ERR_NONFINITE;
+    free(X); free(Rs);
+    return ORC_ERR_NONFINITE;
+  }
+  double ld;
+  int32_t nsw = 0;
+  int status = orc_maxvol(Rs, k, n, J, h, 0, Jo, X, &ld, &nsw);
+  if (status == ORC_WARN_NOT_CONVERGED) status = ORC_OK;        /* no swaps wanted here */
+  unsigned char* in = (unsigned char*)calloc((size_t)n, 1);
+  double* s = (double*)malloc(sizeof(double) * (size_t)n);
+  double* x = (double*)malloc(sizeof(double) * (size_t)k);
+  for (int32_t a = 0; a < k; ++a) in[Jo[a]] = 1;
+  if (status != ORC_WARN_RANK_DEFICIENT) {
+    for (int64_t j = 0; j < n; ++j) {
+      double v = 0.0;
+      for (int32_t i = 0; i < k; ++i) v = fma(X[(int64_t)i * n + j], X[(int64_t)i * n + j], v);
+      s[j] = v;
+    }
+    for (int32_t g = 0; g < pextra; ++g) {
+      int64_t js = -1;
+      for (int64_t j = 0; j < n; ++j)
+        if (!in[j] && (js < 0 || s[j] > s[js])) js = j;
+      if (js < 0 || s[js] == 0.0) break;
+      double sigma = s[js];
+      double gamma = (1.0 - 1.0 / sqrt(1.0 + sigma)) / sigma;
+      for (int32_t i = 0; i < k; ++i) x[i] = X[(int64_t)i * n + js];
+      in[js] = 1;
+      Jo[l++] = (int32_t)js;
+      for (int64_t q = 0; q < n; ++q) {
+        if (in[q]) continue;
+        double t = 0.0;
+        for (int32_t i = 0; i < k; ++i) t = fma(x[i], X[(int64_t)i * n + q], t);
+        double c = gamma * t;
+        double v = 0.0;
+        for (int32_t i = 0; i < k; ++i) {
+          X[(int64_t)i * n + q] = fma(-c, x[i], X[(int64_t)i * n + q]);
+          v = fma(X[(int64_t)i * n + q], X[(int64_t)i * n + q], v);
+        }
+        s[q] = v;
+      }
+    }
+  }
+  /* outputs at l */
+  double* Ct = (double*)malloc(sizeof(double) * (size_t)l * (size_t)m);
+  orc_gather_cols_t(p, Jo, l, Ct);
+  for (int64_t i = 0; i < m; ++i)
+    for (int32_t a = 0; a < l; ++a) C[i * l + a] = Ct[(int64_t)a * m + i];
+  orc_gather_rows_orig(p, I, k, R);
+  double* G = (double*)malloc(sizeof(double) * (size_t)k * (size_t)l);
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t b = 0; b < l; ++b) G[(int64_t)a * l + b] = C[(int64_t)I[a] * l + b];
+  int32_t r = orc_nucleus_rect(G, k, l, rank_tol, U);
+  if (r < k && status == ORC_OK) status = ORC_WARN_RANK_DEFICIENT;
+  info[0] = r; info[1] = l; info[2] = status;
+  free(X); free(Rs); free(in); free(s); free(x); free(Ct); free(G);
   return status;
 }
 

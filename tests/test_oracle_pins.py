@@ -578,6 +578,76 @@ def test_cynical_sketch_of_generator_size_keeps_it():
     assert sorted(o["I"]) == sorted(K) and sorted(o["J"]) == sorted(L)
 
 
+# ------------------------------------------------------------------ rectangular generators
+@pytest.mark.parametrize("k,l", [(1, 5), (4, 9), (6, 6), (8, 20)])
+def test_nucleus_rect_full_rank_is_pinv(k, l):
+    G = np.random.default_rng(k * l).standard_normal((k, l))
+    U, r = oracle.nucleus_rect(G, 1e-13)
+    assert r == k
+    np.testing.assert_allclose(U, np.linalg.pinv(G), atol=1e-12 * np.abs(np.linalg.pinv(G)).max())
+
+
+def test_nucleus_rect_exact_low_rank_is_pinv():
+    """G = A B of exact rank 3 (k = 6, l = 11): the truncated nucleus is its pseudo-inverse."""
+    g = np.random.default_rng(3)
+    G = g.standard_normal((6, 3)) @ g.standard_normal((3, 11))
+    U, r = oracle.nucleus_rect(G, 1e-10)
+    assert r == 3
+    np.testing.assert_allclose(U, np.linalg.pinv(G, rcond=1e-10), atol=1e-11 * np.abs(U).max())
+
+
+def test_oversample_each_step_maximises_the_volume():
+    """Algorithm algrup: every added column maximises det(C_{g+1} C_{g+1}^T) over all
+    columns outside the generator (brute force with numpy determinants)."""
+    p = li.dense_lowrank(50, 60, r=10, noise=1e-6, seed=2)
+    o = oracle.ca_run(p, 4, 3, li.initial_rows(50, 4, 1))
+    ov = oracle.oversample(p, o["I"], o["J"], 5)
+    assert ov["l"] == 9
+    W = p.W
+    Jp = list(ov["J"])
+    for g in range(4, 9):
+        base = Jp[:g]
+        dets = []
+        for q in range(60):
+            if q in base:
+                dets.append(-1.0)
+                continue
+            Cg = W[np.ix_(o["I"], base + [q])]
+            dets.append(np.linalg.det(Cg @ Cg.T))
+        best = int(np.argmax(dets))
+        assert dets[Jp[g]] >= dets[best] * (1 - 1e-9), (g, Jp[g], best)
+
+
+def test_oversample_zero_is_the_square_generator():
+    p = li.dense_lowrank(80, 70, r=6, noise=1e-7, seed=4)
+    o = oracle.ca_run(p, 6, 3, li.initial_rows(80, 6, 2))
+    ov = oracle.oversample(p, o["I"], o["J"], 0)
+    assert ov["l"] == 6
+    np.testing.assert_array_equal(ov["J"], o["J"])
+    np.testing.assert_array_equal(ov["C"], o["C"])
+    U, _ = oracle.nucleus_rect(p.W[np.ix_(o["I"], o["J"])], 1e-13)
+    np.testing.assert_array_equal(ov["U"], U)
+
+
+def test_oversampled_generators_reduce_the_error():
+    """Theorem th3: wider generators (k x l, l > k) lower the CUR error bound; on
+    inputs with a decaying spectrum the mean error falls as columns are added and
+    stays above the Eckart-Young optimum of rank k."""
+    means = []
+    for pe in (0, 4, 12):
+        errs = []
+        for seed in range(6):
+            p = li.dense_lowrank(200, 180, r=20, noise=1e-9, seed=seed)
+            o = oracle.ca_run(p, 8, 3, li.initial_rows(200, 8, seed))
+            ov = oracle.oversample(p, o["I"], o["J"], pe)
+            E = p.W - ov["C"] @ ov["U"] @ ov["R"]
+            sv = np.linalg.svd(p.W, compute_uv=False)
+            errs.append(np.linalg.norm(E, 2) / sv[8])
+            assert errs[-1] >= 1 - 1e-9
+        means.append(np.mean(errs))
+    assert means[0] > means[1] > means[2], means
+
+
 # ------------------------------------------------------------------ apply / residual
 def test_cur_apply_matches_matmul():
     g = np.random.default_rng(0)
