@@ -78,6 +78,18 @@ def ca_flops(k, m, n, loops, swaps, entry_flops=0.0, nucleus=True):
 
 
 # ------------------------------------------------------------------ workloads
+def stages_run(stages, kb, kf):
+    """Stages a staged run went through to end at size kf (every clipped stage size up to kf)."""
+    if not stages:
+        return 1
+    sizes = []
+    for st in stages:
+        k = min(st, kb)
+        if not sizes or k > sizes[-1]:
+            sizes.append(k)
+    return sum(1 for k in sizes if k <= kf) or 1
+
+
 def staged_flops(stages, kb, m, n, nrun, loops, swaps, entry_flops):
     """Lower bound on the algorithmic flops of a staged run: the sizes actually run
     (stages clipped to kb), every stage but the last with the fewest loops it can
@@ -172,8 +184,8 @@ class FmmWorkload:
         f = 0.0
         for (r0, nr, c0, nc), inf in zip(b, info):
             kb = int(min(self.k, nr, nc))
-            f += staged_flops(self.stages or (), kb, int(nr), int(nc), max(int(inf[7]), 1), max(int(inf[2]), 1),
-                              int(inf[1]), LAPLACE_FLOPS)
+            f += staged_flops(self.stages or (), kb, int(nr), int(nc), stages_run(self.stages, kb, int(inf[6])),
+                              max(int(inf[2]), 1), int(inf[1]), LAPLACE_FLOPS)
         return f
 
     def extra(self, res):

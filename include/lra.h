@@ -171,7 +171,9 @@ typedef struct {
   double* logvol;        /* 2*sweeps: log|det W'[I,J]| after each step (NaN if unrun) */
   int32_t* info;         /* LRA_INFO_LEN ints: numerical rank r, total swaps, loops run,
                             status, maxvol steps decided in FP32 (mixed mode), maxvol
-                            steps run in FP64, generator size k used, stages run       */
+                            steps run in FP64, generator rows k (rows of R, columns of
+                            U), generator columns l (columns of C, rows of U; l = k
+                            for square generators)                                  */
 } lra_cur;
 
 #define LRA_INFO_LEN 8
@@ -283,7 +285,7 @@ lra_status lra_ca_batched_workspace_size(const lra_problem* base, const lra_batc
  * min(par->k, nrows, ncols); U_b truncates the core at par->rank_tol (adaptive
  * rank, info[0] of the block).  With par->nstages > 0 the generator size of
  * each block is staged up to k_b as lra_ca_params describes (info[6] = the
- * size used, info[7] = stages run).  Only dense and kernel inputs without
+ * size used; the stages run follow from it).  Only dense and kernel inputs without
  * multipliers.
  * I0: device, nb x par->k block-local initial rows (first k_b of each slot
  * used, distinct).  A block outside the input or larger than max_len gets
@@ -343,6 +345,38 @@ lra_status lra_cynical_batched_tune(const lra_problem* base, const lra_batch* ba
                                     float* ms);
 
 /*
+ * lra_oversample_batched -- rectangular generators for every block of a batch
+ * that lra_ca_run_batched has processed (paper: Algorithm algrup, greedy
+ * expansions of a k x k submatrix to k x l; Theorem th3 for the error bound of
+ * k x l generators), one CTA per block from a work queue.  Block b's square
+ * generator (rows in->I, columns in->J, size k_b = in->info[6]) grows by up to
+ * pextra columns, l_b = min(k_b + pextra, ncols):
+ *   X = B^{-1} W'[I, :] (B = W'[I, J]) is the C matrix of a maxvol step on the
+ *   row strip warm-started at J with no swaps (its set J0 starts J'; a zero
+ *   pivot keeps J' = J and adds nothing); then, pextra times, the column outside
+ *   J' with the largest s_j = ||X[:, j]||^2 (lowest j on ties) joins J' (the
+ *   squared volume of the generator grows by 1 + s_j) and every other column is
+ *   whitened again, X[:, q] -= gamma (x . X[:, q]) x with gamma = (1 - 1/sqrt(1 +
+ *   sigma)) / sigma, sigma = s_j; no column is added once the largest s_j is 0.
+ * Outputs (out, layout of lra_cur_batch with these slots): I (nb x par->k),
+ * J' (nb x (par->k + pextra)), C_b = W'[:, J'] (nrows x l_b) and R_b = W[I, :]
+ * (k_b x ncols) packed at batch->offsets (which must size the slots for
+ * min(par->k + pextra, ncols) and par->k), U_b (l_b x k_b, row-major) at the
+ * start of an (par->k + pextra) x par->k slot: the pinv of the rank-r QRP
+ * truncation of W'[I, J'] at par->rank_tol (r = info[0]); info[3] status,
+ * info[6] = k_b, info[7] = l_b.  Blocks whose C-A run failed keep its status.
+ * par->k: the C-A run's largest size; par->h: the maxvol threshold.
+ * Errors: LRA_ERR_INVALID_ARG (also when the rectangular nucleus of par->k x
+ * (par->k + pextra) does not fit in shared memory), LRA_ERR_WORKSPACE,
+ * LRA_ERR_CUDA.
+ */
+lra_status lra_oversample_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
+                                                 const lra_ca_params* par, int32_t pextra, size_t* bytes);
+lra_status lra_oversample_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                                  int32_t pextra, const lra_cur_batch* in, const lra_cur_batch* out, void* workspace,
+                                  size_t workspace_bytes, lra_stream_t stream);
+
+/*
  * lra_ca_batched_shapes -- the CTA shapes the batched kernel is built for:
  * writes up to cap (threads per CTA, CTAs per SM) pairs and returns their
  * number.  Each shape holds 16 warps per SM (128 registers a thread); they
@@ -378,6 +412,16 @@ lra_status lra_ca_batched_tune(const lra_problem* base, const lra_batch* batch, 
 lra_status lra_residual_sample_batched(const lra_problem* base, const lra_batch* batch, int32_t kmax,
                                        const lra_cur_batch* cur, const int32_t* Q, int32_t q, const int32_t* S,
                                        int32_t s, double* stats, lra_stream_t stream);
+
+/*
+ * lra_residual_sample_batched_rect -- the same for rectangular generators (the
+ * outputs of lra_oversample_batched): block b's C_b is nrows x l_b, U_b l_b x
+ * k_b at the start of an lmax x kmax slot, R_b k_b x ncols, with k_b =
+ * info[6] and l_b = info[7].  kmax <= lmax <= 128.
+ */
+lra_status lra_residual_sample_batched_rect(const lra_problem* base, const lra_batch* batch, int32_t kmax,
+                                            int32_t lmax, const lra_cur_batch* cur, const int32_t* Q, int32_t q,
+                                            const int32_t* S, int32_t s, double* stats, lra_stream_t stream);
 
 /* ------------------------------------------------------------------------- */
 /* Differentiable CUR apply on Gaussian-kernel blocks (fixed pivots)          */

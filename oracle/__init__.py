@@ -49,6 +49,7 @@ def lib():
         L.orc_ca_run_adaptive.restype = ct.c_int
         L.orc_bidiag_columns.argtypes = [i64, i32, vp, vp, vp, vp]
         L.orc_nucleus_rect.argtypes = [vp, i32, i32, f64, vp]
+        L.orc_residual_sample_rect.argtypes = [P, vp, vp, vp, i32, i32, vp, i32, vp, i32, vp, vp]
         L.orc_nucleus_rect.restype = i32
         L.orc_oversample.argtypes = [P, vp, vp, i32, i32, f64, f64, vp, vp, vp, vp, vp]
         L.orc_oversample.restype = ct.c_int
@@ -308,16 +309,18 @@ def cur_apply(C, U, R, X):
 
 def residual_sample(p, C, U, R, Q, S, return_E=False):
     """Statistics of the q x s sample E[Q,S] of E = W - C U R (a-posteriori
-    estimation from a random submatrix): [mean, var, mean|e|, max|e|, fro ratio]."""
+    estimation from a random submatrix): [mean, var, mean|e|, max|e|, fro ratio].
+    C m x l, U l x k, R k x n (l = k for square generators)."""
     mp = _Marshalled(p)
     C = np.ascontiguousarray(C, dtype=np.float64); U = np.ascontiguousarray(U, dtype=np.float64)
     R = np.ascontiguousarray(R, dtype=np.float64)
     Q = np.ascontiguousarray(Q, dtype=np.int32); S = np.ascontiguousarray(S, dtype=np.int32)
-    k = C.shape[1]
+    l, k = C.shape[1], R.shape[0]
+    assert U.shape == (l, k)
     stats = np.empty(5)
     E = np.empty((len(Q), len(S))) if return_E else None
-    lib().orc_residual_sample(mp.ref, _ptr(C), _ptr(U), _ptr(R), k, _ptr(Q), len(Q), _ptr(S), len(S),
-                              _ptr(stats), _ptr(E))
+    lib().orc_residual_sample_rect(mp.ref, _ptr(C), _ptr(U), _ptr(R), k, l, _ptr(Q), len(Q), _ptr(S), len(S),
+                                   _ptr(stats), _ptr(E))
     return (stats, E) if return_E else stats
 
 

@@ -756,7 +756,8 @@ int orc_cynical(const orc_problem* p, int32_t kind, int32_t r, int32_t q, int32_
  * CUR error of such generators.
  *  1. X = B^{-1} W'[I, :], B = W'[I, J]: the C matrix of a maxvol step
  *     (orc_maxvol) on the row strip warm-started at J with no swaps; its
- *     selected set J0 (J unless the warm LU met a zero pivot) starts J'.
+ *     selected set J0 (J unless the warm LU met a zero pivot) starts J'.  A
+ *     rank-deficient strip (zero pivot) keeps J' = J and adds nothing.
  *  2. p times: the column j outside J' with the largest s_j = ||X[:, j]||^2
  *     (ascending fma chain; lowest j on ties) joins J' (the squared volume
  *     grows by the factor 1 + s_j); with x = X[:, j] and sigma = s_j, every
@@ -785,6 +786,7 @@ int orc_oversample(const orc_problem* p, const int32_t* I, const int32_t* J, int
   int32_t nsw = 0;
   int status = orc_maxvol(Rs, k, n, J, h, 0, Jo, X, &ld, &nsw);
   if (status == ORC_WARN_NOT_CONVERGED) status = ORC_OK;        /* no swaps wanted here */
+  if (status == ORC_WARN_RANK_DEFICIENT) memcpy(Jo, J, sizeof(int32_t) * (size_t)k);   /* no expansion */
   unsigned char* in = (unsigned char*)calloc((size_t)n, 1);
   double* s = (double*)malloc(sizeof(double) * (size_t)n);
   double* x = (double*)malloc(sizeof(double) * (size_t)k);
@@ -875,8 +877,18 @@ void orc_cur_apply(const double* C, const double* U, const double* R, int64_t m,
  * entries; the sums here run in ascending (row, column) order.
  * E (q x s) is written if Eout != NULL.
  */
+void orc_residual_sample_rect(const orc_problem* p, const double* C, const double* U, const double* R, int32_t k,
+                              int32_t l, const int32_t* Q, int32_t q, const int32_t* S, int32_t s, double* stats,
+                              double* Eout);
 void orc_residual_sample(const orc_problem* p, const double* C, const double* U, const double* R, int32_t k,
                          const int32_t* Q, int32_t q, const int32_t* S, int32_t s, double* stats, double* Eout) {
+  orc_residual_sample_rect(p, C, U, R, k, k, Q, q, S, s, stats, Eout);
+}
+
+/* The same for a rectangular generator: C m x l, U l x k, R k x n. */
+void orc_residual_sample_rect(const orc_problem* p, const double* C, const double* U, const double* R, int32_t k,
+                              int32_t l, const int32_t* Q, int32_t q, const int32_t* S, int32_t s, double* stats,
+                              double* Eout) {
   double* cu = (double*)malloc(sizeof(double) * (size_t)k);
   double* e = (double*)malloc(sizeof(double) * (size_t)q * (size_t)s);
   int64_t n = p->n;
@@ -885,7 +897,7 @@ void orc_residual_sample(const orc_problem* p, const double* C, const double* U,
     /* row Q[a] of C U */
     for (int32_t b = 0; b < k; ++b) {
       double t = 0.0;
-      for (int32_t c = 0; c < k; ++c) t = fma(C[(int64_t)Q[a] * k + c], U[c * k + b], t);
+      for (int32_t c = 0; c < l; ++c) t = fma(C[(int64_t)Q[a] * l + c], U[c * k + b], t);
       cu[b] = t;
     }
     for (int32_t c = 0; c < s; ++c) {

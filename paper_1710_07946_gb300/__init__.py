@@ -113,6 +113,9 @@ def _load():
     L.lra_cynical_run_batched.argtypes = [P, PB, PP, i32, i32, vp, vp, vp, PCB, vp, sz, vp]
     L.lra_cynical_batched_tune.argtypes = [P, PB, PP, i32, i32, vp, vp, vp, PCB, vp, sz, vp, i32,
                                            ct.POINTER(i32), ct.POINTER(i32), vp]
+    L.lra_oversample_batched_workspace_size.argtypes = [P, PB, PP, i32, ct.POINTER(sz)]
+    L.lra_oversample_batched.argtypes = [P, PB, PP, i32, PCB, PCB, vp, sz, vp]
+    L.lra_residual_sample_batched_rect.argtypes = [P, PB, i32, i32, PCB, vp, i32, vp, i32, vp, vp]
     L.lra_ca_batched_shapes.argtypes = [vp, vp, i32]
     L.lra_ca_batched_shapes.restype = i32
     PG = ct.POINTER(_Gauss)
@@ -128,7 +131,8 @@ def _load():
               "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect",
               "lra_ca_batched_workspace_size", "lra_ca_run_batched", "lra_residual_sample_batched",
               "lra_ca_batched_tune", "lra_cynical_batched_workspace_size", "lra_cynical_run_batched",
-              "lra_cynical_batched_tune",
+              "lra_cynical_batched_tune", "lra_oversample_batched_workspace_size", "lra_oversample_batched",
+              "lra_residual_sample_batched_rect",
               "lra_gauss_cur_forward", "lra_gauss_cur_backward"):
         getattr(L, f).restype = ct.c_int
     _lib = L
@@ -454,7 +458,7 @@ class Batch:
                     U=o["U"][b].reshape(-1)[:kb * kb].reshape(kb, kb),
                     R=o["R"][orr:orr + kb * nc].reshape(kb, nc), logvol=o["logvol"][b],
                     rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]), status=int(info[3]),
-                    fp32_steps=int(info[4]), fp64_steps=int(info[5]), k=kb, stages=int(info[7]))
+                    fp32_steps=int(info[4]), fp64_steps=int(info[5]), k=kb)
 
 
 def lra_ca_batched_shapes() -> list:
@@ -525,6 +529,77 @@ def lra_cynical_run_batched(batch: Batch, kind: int, q: int, K: torch.Tensor, L:
                                       int(q), K.data_ptr(), L.data_ptr(), I0s.data_ptr(), ct.byref(batch.cur),
                                       batch._cyn_ws.data_ptr(), batch._cyn_ws.numel(), _stream(stream)),
            "lra_cynical_run_batched")
+
+
+class Oversampled:
+    """Device outputs of lra_oversample_batched for a processed Batch: rectangular
+    k_b x l_b generators (l_b = min(k_b + pextra, ncols))."""
+
+    def __init__(self, batch: Batch, pextra: int):
+        import numpy as np
+        b, k, p = batch, batch.k, int(pextra)
+        blocks = b.blocks_np
+        lcap = np.minimum(k + p, blocks[:, 3])
+        csz, rsz = blocks[:, 1] * lcap, np.minimum(k, np.minimum(blocks[:, 1], blocks[:, 3])) * blocks[:, 3]
+        offs = np.zeros((b.nb, 2), dtype=np.int64)
+        offs[1:, 0] = np.cumsum(csz)[:-1]
+        offs[1:, 1] = np.cumsum(rsz)[:-1]
+        dev = b.blocks.device
+        self.batch, self.pextra, self.offs_np = b, p, offs
+        self.offs = torch.from_numpy(offs).to(dev)
+        self.out = dict(I=torch.zeros(b.nb, k, dtype=torch.int32, device=dev),
+                        J=torch.zeros(b.nb, k + p, dtype=torch.int32, device=dev),
+                        C=torch.zeros(max(int(csz.sum()), 1), dtype=torch.float64, device=dev),
+                        U=torch.zeros(b.nb, k + p, k, dtype=torch.float64, device=dev),
+                        R=torch.zeros(max(int(rsz.sum()), 1), dtype=torch.float64, device=dev),
+                        logvol=torch.zeros(1, dtype=torch.float64, device=dev),
+                        info=torch.zeros(b.nb, LRA_INFO_LEN, dtype=torch.int32, device=dev))
+        self.cb = _Batch()
+        self.cb.blocks, self.cb.offsets = b.blocks.data_ptr(), self.offs.data_ptr()
+        self.cb.order = b.cb.order
+        self.cb.nb, self.cb.max_len = b.nb, b.cb.max_len
+        self.cur = _CurBatch()
+        for f in ("I", "J", "C", "U", "R", "logvol", "info"):
+            setattr(self.cur, f, self.out[f].data_ptr())
+        nbytes = ct.c_size_t()
+        _check(_load().lra_oversample_batched_workspace_size(ct.byref(b.pc), ct.byref(self.cb), ct.byref(b.params), p,
+                                                             ct.byref(nbytes)), "lra_oversample_batched_workspace_size")
+        self.workspace = _workspace(nbytes.value, dev)
+
+    def block(self, i: int) -> dict:
+        (r0, nr, c0, nc) = self.batch.blocks_np[i]
+        o = {key: v.cpu().numpy() for key, v in self.out.items()}
+        info = o["info"][i]
+        k, l = int(info[6]), int(info[7])
+        oc, orr = self.offs_np[i]
+        return dict(I=o["I"][i, :k], J=o["J"][i, :l], C=o["C"][oc:oc + nr * l].reshape(nr, l),
+                    U=o["U"][i].reshape(-1)[:l * k].reshape(l, k), R=o["R"][orr:orr + k * nc].reshape(k, nc),
+                    rank=int(info[0]), status=int(info[3]), k=k, l=l)
+
+
+def lra_oversample_batched(batch: Batch, pextra: int, ov: Optional[Oversampled] = None, stream=None) -> Oversampled:
+    """Rectangular generators grown from the batch's square ones (run lra_ca_run_batched first)."""
+    ov = ov or Oversampled(batch, pextra)
+    _check(_load().lra_oversample_batched(ct.byref(batch.pc), ct.byref(ov.cb), ct.byref(batch.params), ov.pextra,
+                                          ct.byref(batch.cur), ct.byref(ov.cur), ov.workspace.data_ptr(),
+                                          ov.workspace.numel(), _stream(stream)), "lra_oversample_batched")
+    return ov
+
+
+def lra_residual_sample_oversampled(ov: Oversampled, Q: torch.Tensor, S: torch.Tensor,
+                                    stats: Optional[torch.Tensor] = None, stream=None,
+                                    problem: Optional[Problem] = None) -> torch.Tensor:
+    """Per-block residual sample statistics (nb x 5) of rectangular generators."""
+    b = ov.batch
+    if stats is None:
+        stats = torch.empty(b.nb, 5, dtype=torch.float64, device=b.blocks.device)
+    pc = b.pc if problem is None else problem._c()
+    _check(_load().lra_residual_sample_batched_rect(ct.byref(pc), ct.byref(ov.cb), b.k, b.k + ov.pextra,
+                                                    ct.byref(ov.cur), _dev(Q, torch.int32, "Q").data_ptr(),
+                                                    Q.shape[1], _dev(S, torch.int32, "S").data_ptr(), S.shape[1],
+                                                    stats.data_ptr(), _stream(stream)),
+           "lra_residual_sample_batched_rect")
+    return stats
 
 
 def lra_ca_run_batched(batch: Batch, stream=None) -> None:

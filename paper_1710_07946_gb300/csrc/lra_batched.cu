@@ -15,6 +15,7 @@ namespace lra {
 // and its statistics (mean, variance, mean |e|, max |e|, Frobenius ratio).
 __global__ void __launch_bounds__(256) resid_batched_kernel(DevProblem base, const int64_t* blocks,
                                                             const int64_t* offs, int32_t nb, int32_t kmax,
+                                                            int32_t lmax,
                                                             const double* C, const double* U, const double* R,
                                                             const int32_t* info, const int32_t* Qs, int32_t q,
                                                             const int32_t* Ss, int32_t s, double* stats) {
@@ -32,11 +33,13 @@ __global__ void __launch_bounds__(256) resid_batched_kernel(DevProblem base, con
       if (threadIdx.x < 5) st[threadIdx.x] = __longlong_as_double(0x7ff8000000000000ll);
       continue;
     }
-    const int kf = info[LRA_INFO_LEN * (size_t)b + 6];
-    const int k = (kf > 0) ? kf : (int)min((int64_t)kmax, min(nr, nc));
+    // generator rows k (R, U columns) and columns l (C, U rows); l = k when square
+    const int kf = info[LRA_INFO_LEN * (size_t)b + 6], lf = info[LRA_INFO_LEN * (size_t)b + 7];
+    const int k = min(kmax, (kf > 0) ? kf : (int)min((int64_t)kmax, min(nr, nc)));
+    const int l = min(lmax, (lf > 0) ? lf : k);
     const double* Cb = C + offs[2 * (size_t)b];
     const double* Rb = R + offs[2 * (size_t)b + 1];
-    const double* Ub = U + (size_t)b * kmax * kmax;
+    const double* Ub = U + (size_t)b * lmax * kmax;
     const int32_t* Q = Qs + (size_t)b * q;
     const int32_t* S = Ss + (size_t)b * s;
     DevProblem P = base;
@@ -53,7 +56,7 @@ __global__ void __launch_bounds__(256) resid_batched_kernel(DevProblem base, con
       const int a = it / k, bb = it - a * k;
       const int64_t row = min((int64_t)Q[a], nr - 1);
       double t = 0.0;
-      for (int d = 0; d < k; ++d) t = fma(Cb[row * k + d], Ub[d * k + bb], t);
+      for (int d = 0; d < l; ++d) t = fma(Cb[row * l + d], Ub[d * k + bb], t);
       CU[it] = t;
     }
     __syncthreads();
@@ -347,12 +350,18 @@ int32_t lra_ca_batched_shapes(int32_t* threads, int32_t* ctas, int32_t cap) {
 lra_status lra_residual_sample_batched(const lra_problem* base, const lra_batch* batch, int32_t kmax,
                                        const lra_cur_batch* cur, const int32_t* Q, int32_t q, const int32_t* S,
                                        int32_t s, double* stats, lra_stream_t stream_) {
+  return lra_residual_sample_batched_rect(base, batch, kmax, kmax, cur, Q, q, S, s, stats, stream_);
+}
+
+lra_status lra_residual_sample_batched_rect(const lra_problem* base, const lra_batch* batch, int32_t kmax,
+                                            int32_t lmax, const lra_cur_batch* cur, const int32_t* Q, int32_t q,
+                                            const int32_t* S, int32_t s, double* stats, lra_stream_t stream_) {
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   DevProblem P;
   lra_status st = make_dev_problem(base, nullptr, &P);
   if (st != LRA_OK) return st;
   if (batch == nullptr || cur == nullptr || !Q || !S || !stats || q < 1 || s < 1 || kmax < 1 || kmax > KMAX ||
-      batch->nb < 1 || !cur->C || !cur->U || !cur->R || !cur->info)
+      lmax < kmax || lmax > 2 * KMAX || batch->nb < 1 || !cur->C || !cur->U || !cur->R || !cur->info)
     return LRA_ERR_INVALID_ARG;
   const size_t smem = sizeof(double) * ((size_t)q * kmax + 2 * (size_t)q * s);
   DeviceInfo dev;
@@ -362,8 +371,8 @@ lra_status lra_residual_sample_batched(const lra_problem* base, const lra_batch*
   const int grid = std::min(batch->nb, dev.sms * 8);
   {
     LaunchScope ls(stream, "resid_batched_kernel");
-    resid_batched_kernel<<<grid, 256, smem, stream>>>(P, batch->blocks, batch->offsets, batch->nb, kmax, cur->C,
-                                                      cur->U, cur->R, cur->info, Q, q, S, s, stats);
+    resid_batched_kernel<<<grid, 256, smem, stream>>>(P, batch->blocks, batch->offsets, batch->nb, kmax, lmax,
+                                                      cur->C, cur->U, cur->R, cur->info, Q, q, S, s, stats);
   }
   return cuda_status(cudaGetLastError());
 }

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
     if (threadIdx.x == 0) {
       info[0] = (st != LRA_OK && st < 16) ? 0 : r;
       info[1] = swaps; info[2] = loops; info[3] = st;
-      info[4] = n32; info[5] = n64; info[6] = k; info[7] = nrun;
+      info[4] = n32; info[5] = n64; info[6] = k; info[7] = k;
     }
     __syncthreads();
   }

@@ -73,7 +73,7 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
   if (err != LRA_OK) {
     if (lead && tid == 0) {
       A.info[0] = 0; A.info[1] = total; A.info[2] = loops; A.info[3] = err;
-      A.info[4] = n32; A.info[5] = n64; A.info[6] = k; A.info[7] = 1;
+      A.info[4] = n32; A.info[5] = n64; A.info[6] = k; A.info[7] = k;
     }
     return;
   }
@@ -100,7 +100,7 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
     for (int a = tid; a < k; a += nt) { A.I[a] = S.Is[a]; A.J[a] = S.Js[a]; }
     if (tid == 0) {
       A.info[0] = 0; A.info[1] = total; A.info[2] = loops; A.info[3] = status;
-      A.info[4] = n32; A.info[5] = n64; A.info[6] = k; A.info[7] = 1;
+      A.info[4] = n32; A.info[5] = n64; A.info[6] = k; A.info[7] = k;
     }
   }
 }

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(NTB, MINB) cynical_batched_kernel(CynArgs B) {
       if (st != LRA_OK && st < 16) {
         if (tid == 0) {
           info[0] = 0; info[1] = swaps; info[2] = 0; info[3] = st;
-          info[4] = 0; info[5] = 2; info[6] = r; info[7] = 1;
+          info[4] = 0; info[5] = 2; info[6] = r; info[7] = r;
         }
         __syncthreads();
         continue;
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(NTB, MINB) cynical_batched_kernel(CynArgs B) {
     if (st2 != LRA_OK && st2 < 16) {
       if (tid == 0) {
         info[0] = 0; info[1] = swaps + swaps2; info[2] = loops2; info[3] = st2;
-        info[4] = 0; info[6] = r; info[7] = 1;
+        info[4] = 0; info[6] = r; info[7] = r;
       }
       __syncthreads();
       continue;
@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(NTB, MINB) cynical_batched_kernel(CynArgs B) {
       int s = max(st, st2);
       if (rank < r && s == LRA_OK) s = LRA_WARN_RANK_DEFICIENT;
       info[0] = rank; info[1] = swaps + swaps2; info[2] = loops2; info[3] = s;
-      info[4] = 0; info[5] = (B.kind == 1 ? 2 : 0) + info[5]; info[6] = r; info[7] = 1;
+      info[4] = 0; info[5] = (B.kind == 1 ? 2 : 0) + info[5]; info[6] = r; info[7] = r;
     }
     __syncthreads();
   }

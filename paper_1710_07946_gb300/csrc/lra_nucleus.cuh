@@ -176,4 +176,121 @@ __device__ inline int nucleus_cta(const double* G, int k, double tol, double* U,
   return r;
 }
 
+// Shared memory of nucleus_rect_cta for a k x l generator.
+__host__ __device__ inline size_t nucleus_rect_smem_bytes(int k, int l) {
+  const size_t ldk = (size_t)(k | 1), ldl = (size_t)(l | 1);
+  return sizeof(double) * ((size_t)l * ldk + (size_t)k * ldk + 2 * (size_t)k * ldl + 2 * (size_t)KMAX + 4) +
+         sizeof(int32_t) * ((size_t)l + 4) + 64;
+}
+
+// U (l x k, row-major) <- pinv of the rank-r QRP truncation of the k x l
+// generator G (row-major, global, k <= l <= 2 KMAX): QRP over the l columns
+// (k steps), r = #{|R_tt| > tol |R_00|}, then T^T = (rows 0..r-1 of R)^T = Z S
+// and U = P Z S^{-T} Q_r^T, each inner product an ascending fma chain owned by
+// one thread (the arithmetic of the FP64 reference's rectangular nucleus).
+// smem: nucleus_rect_smem_bytes(k, l).  Returns r.
+__device__ inline int nucleus_rect_cta(const double* G, int k, int l, double tol, double* U, unsigned char* smem) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int ldk = k | 1, ldl = l | 1;
+  double* A = reinterpret_cast<double*>(smem);          // column-major k x l, stride ldk
+  double* Q = A + (size_t)l * ldk;                      // Q^T, column-major k x k
+  double* T = Q + (size_t)k * ldk;                      // T^T (l x r), column-major, stride ldl
+  double* X = T + (size_t)k * ldl;                      // l x k, column-major, stride ldl
+  double* taus = X + (size_t)k * ldl;
+  double* tz = taus + KMAX;
+  double* bc = tz + KMAX;
+  int32_t* perm = reinterpret_cast<int32_t*>(bc + 4);
+  int32_t* ctl = perm + l;
+
+  for (int it = tid; it < k * l; it += nt) {
+    const int i = it / l, j = it - i * l;
+    A[j * ldk + i] = G[it];
+  }
+  for (int j = tid; j < l; j += nt) perm[j] = j;
+  __syncthreads();
+  for (int t = 0; t < k; ++t) {
+    // largest squared column norm over rows t.., lowest column on ties (one thread
+    // per column accumulates, one warp compares integer keys)
+    double* nrm = X;                                    // l scratch doubles (X is unused yet)
+    for (int j = t + tid; j < l; j += nt) {
+      double s = 0.0;
+      for (int i = t; i < k; ++i) s = fma(A[j * ldk + i], A[j * ldk + i], s);
+      nrm[j] = s;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      Cand c = cand_none();
+      for (int j = t + tid; j < l; j += 32) cand_consider(c, mag_key(nrm[j]), 0, j);
+      for (int off = 16; off > 0; off >>= 1) {
+        Cand o;
+        o.key = __shfl_down_sync(0xffffffffu, c.key, off);
+        o.i = __shfl_down_sync(0xffffffffu, c.i, off);
+        o.j = __shfl_down_sync(0xffffffffu, c.j, off);
+        if (cand_better(o, c)) c = o;
+      }
+      if (tid == 0) {
+        const int pj = (c.key == 0ull) ? t : c.j;
+        ctl[0] = pj;
+        if (pj != t) { int tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp; }
+      }
+    }
+    __syncthreads();
+    const int pj = ctl[0];
+    if (pj != t)
+      for (int i = tid; i < k; i += nt) {
+        double tmp = A[t * ldk + i]; A[t * ldk + i] = A[pj * ldk + i]; A[pj * ldk + i] = tmp;
+      }
+    __syncthreads();
+    const double tau = house_cta(&A[t * ldk + t], k - t, bc);
+    if (tid == 0) taus[t] = tau;
+    for (int j = t + 1 + tid; j < l; j += nt) apply_house_seq(&A[t * ldk + t], tau, &A[j * ldk + t], k - t);
+    __syncthreads();
+  }
+  if (tid == 0) {
+    int r = 0;
+    const double r00 = fabs(A[0]);
+    if (r00 > 0.0) while (r < k && fabs(A[r * ldk + r]) > tol * r00) ++r;
+    ctl[1] = r;
+  }
+  __syncthreads();
+  const int r = ctl[1];
+  for (int it = tid; it < l * k; it += nt) U[it] = 0.0;
+  if (r == 0) { __syncthreads(); return 0; }
+  // Q^T = H_{k-1} ... H_0 I, one column per thread
+  for (int j = tid; j < k; j += nt) {
+    for (int i = 0; i < k; ++i) Q[j * ldk + i] = (i == j) ? 1.0 : 0.0;
+    for (int t = 0; t < k; ++t) apply_house_seq(&A[t * ldk + t], taus[t], &Q[j * ldk + t], k - t);
+  }
+  // T^T and its QR
+  for (int it = tid; it < l * r; it += nt) {
+    const int c = it / l, i = it - c * l;
+    T[c * ldl + i] = (i >= c) ? A[i * ldk + c] : 0.0;
+  }
+  __syncthreads();
+  for (int c = 0; c < r; ++c) {
+    const double tz_c = house_cta(&T[c * ldl + c], l - c, bc);
+    if (tid == 0) tz[c] = tz_c;
+    for (int j = c + 1 + tid; j < r; j += nt) apply_house_seq(&T[c * ldl + c], tz_c, &T[j * ldl + c], l - c);
+    __syncthreads();
+  }
+  // X = Z S^{-T} Q_r^T, one column per thread
+  for (int col = tid; col < k; col += nt) {
+    double* v = &X[col * ldl];
+    for (int i = 0; i < l; ++i) v[i] = 0.0;
+    for (int i = 0; i < r; ++i) {
+      double s = Q[col * ldk + i];
+      for (int p = 0; p < i; ++p) s = fma(-T[i * ldl + p], v[p], s);
+      v[i] = s / T[i * ldl + i];
+    }
+    for (int c = r - 1; c >= 0; --c) apply_house_seq(&T[c * ldl + c], tz[c], &v[c], l - c);
+  }
+  __syncthreads();
+  for (int it = tid; it < l * k; it += nt) {
+    const int i = it / k, col = it - i * k;
+    U[(size_t)perm[i] * k + col] = X[col * ldl + i];
+  }
+  __syncthreads();
+  return r;
+}
+
 }  // namespace lra
