@@ -48,7 +48,7 @@ import lra_inputs as li  # noqa: E402
 
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal; a plain DFMA loop measured 1.2)
 FP32_PEAK_TFLOPS = 80.5   # 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz (nominal; a plain FFMA loop measured 74)
-METRIC = "CUR LRAs/s at rel. err <= 1e-6 (FP64 pivots and nucleus)"
+METRIC = "CUR LRAs/s at rel. err <=1e-6 (mixed vs plain FP64 GPU); % of HBM roofline"
 ERR_BOUND = 1e-6
 LAPLACE_FLOPS = 8.0       # 3 sub, 1 mul, 2 fma, sqrt, div per kernel entry (nominal count)
 
@@ -667,6 +667,74 @@ class GaussApplyWorkload:
         return n, n, el, f"{n} blocks of the same batch (FP64 forward + backward each)"
 
 
+class FmmOversampleWorkload(FmmWorkload):
+    """The FMM batch (mixed form) with every block's square generator grown to a
+    rectangular k x (k + p) one by greedy volume expansions (Algorithm algrup);
+    one step = the batched C-A launch + the batched expansion + the rectangular
+    residual sample against the FP64 entries."""
+
+    def __init__(self, pextra=8, **kw):
+        super().__init__(entries="f32", **kw)
+        self.pextra = pextra
+        self.name = self.name + f"_oversample{pextra}"
+
+    def config(self, h):
+        c = super().config(h)
+        c["generator"] = f"rectangular k x (k + {self.pextra}) by greedy volume expansions"
+        return c
+
+    def device(self, h, dev):
+        import paper_1710_07946_gb300 as lra
+        d = super().device(h, dev)
+        d["ov"] = lra.Oversampled(d["bt"], self.pextra)
+        return d
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        lra.lra_ca_run_batched(d["bt"])
+        lra.lra_oversample_batched(d["bt"], self.pextra, d["ov"])
+        lra.lra_residual_sample_oversampled(d["ov"], d["Q"], d["S"], d["stats"], problem=d["prob64"])
+
+    def check(self, d):
+        info = d["ov"].out["info"].cpu().numpy()
+        st = d["stats"].cpu().numpy()
+        ok = (info[:, 3] == 0) | (info[:, 3] >= 16)
+        good = ok & (st[:, 4] <= ERR_BOUND)
+        return dict(units=int(good.sum()), info=d["bt"].out["info"].cpu().numpy(), err=st[:, 4])
+
+    def comparisons(self):
+        return []
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["X"].copy_(hp["X"], non_blocking=True)
+        self.step(d)
+        for key, v in hp["out"].items():
+            v.copy_(d["bt"].out[key], non_blocking=True)
+        hp["stats"].copy_(d["stats"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        b = h["blocks"]
+        order = np.random.default_rng(seed).permutation(len(b))
+        t0 = time.perf_counter()
+        n = good = 0
+        for idx in order:
+            r0, nr, c0, nc = b[idx]
+            sub = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=h["p"].X[r0:r0 + nr], Y=h["p"].Y[c0:c0 + nc])
+            sube = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=sub.X, Y=sub.Y, entries=self.entries)
+            o = oracle.ca_run_adaptive(sube, self.stages, self.margin, self.sweeps, h["I0"][idx], rank_tol=self.tol)
+            ov = oracle.oversample(sube, o["I"], o["J"], self.pextra, rank_tol=self.tol)
+            st = oracle.residual_sample(sub, ov["C"], ov["U"], ov["R"], h["Q"][idx], h["S"][idx])
+            n += 1
+            good += st[4] <= ERR_BOUND
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        el = time.perf_counter() - t0
+        return good, n, el, f"{n} randomly chosen blocks of the same batch (C-A + expansion + residual sample each)"
+
+
 class FmmSmallWorkload(FmmWorkload):
     """The same recipe on 2^17 points and 512 block pairs (profiling size)."""
     base = "fmm_laplace_128K_octree_512blocks"
@@ -679,6 +747,7 @@ WORKLOADS = {
     "fmm": lambda: FmmWorkload(entries="f32"),
     "fmm_f64": FmmWorkload,
     "fmm_fixedk": lambda: FmmWorkload(stages=None),
+    "fmm_oversample8": lambda: FmmOversampleWorkload(8),
     "fmm_small": FmmSmallWorkload,
     **{f"laplace65536_k{k}{sfx}": (lambda k=k, e=e: LaplaceSingleWorkload(k, e))
        for k in (16, 32, 64) for sfx, e in (("", "f64"), ("_f32", "f32"))},
