@@ -348,8 +348,9 @@ class LaplaceSingleWorkload:
     kernel = "ca_kernel"
     unit = "LRA/s"
 
-    def __init__(self, k, entries="f64", n=65536, sweeps=3):
+    def __init__(self, k, entries="f64", n=65536, sweeps=3, rank_tol=1e-8):
         self.k, self.entries, self.n, self.sweeps, self.q, self.s = k, entries, n, sweeps, 256, 256
+        self.rank_tol = rank_tol          # truncation above the core's rounding level
         self.name = f"laplace{n}_cubes3apart_k{k}_s{sweeps}_{entries}entries"
 
     def host(self, rank):
@@ -361,7 +362,8 @@ class LaplaceSingleWorkload:
     def config(self, h):
         return {"workload": self.name, "m": self.n, "n": self.n, "k": self.k, "sweeps": self.sweeps,
                 "kernel": f"Laplace 1/|x-y|, on the fly, entries {self.entries.upper()}",
-                "pivots_nucleus": "FP64", "residual_sample": f"{self.q}x{self.s} against FP64 entries"}
+                "pivots_nucleus": "FP64", "rank_tol": self.rank_tol,
+                "residual_sample": f"{self.q}x{self.s} against FP64 entries"}
 
     def device(self, h, dev):
         import torch
@@ -371,13 +373,14 @@ class LaplaceSingleWorkload:
         prob = lra.Problem.kernel("laplace", X, Y, entries=self.entries)
         prob64 = lra.Problem.kernel("laplace", X, Y)
         I0 = torch.from_numpy(h["I0"]).to(dev)
-        out = lra.lra_ca_run(prob, I0, self.k, self.sweeps)
+        out = lra.lra_ca_run(prob, I0, self.k, self.sweeps, rank_tol=self.rank_tol)
         return dict(X=X, Y=Y, prob=prob, prob64=prob64, I0=I0, out=out, Q=torch.from_numpy(h["Q"]).to(dev),
                     S=torch.from_numpy(h["S"]).to(dev), stats=None)
 
     def step(self, d):
         import paper_1710_07946_gb300 as lra
-        lra.lra_ca_run(d["prob"], d["I0"], self.k, self.sweeps, out=d["out"], workspace=d["out"]["_workspace"])
+        lra.lra_ca_run(d["prob"], d["I0"], self.k, self.sweeps, rank_tol=self.rank_tol, out=d["out"],
+                       workspace=d["out"]["_workspace"])
         d["stats"] = lra.lra_residual_sample(d["prob64"], d["out"]["C"], d["out"]["U"], d["out"]["R"], d["Q"],
                                              d["S"])
 
@@ -425,7 +428,7 @@ class LaplaceSingleWorkload:
         t0 = time.perf_counter()
         n = good = 0
         while True:
-            o = oracle.ca_run(pe, self.k, self.sweeps, h["I0"])
+            o = oracle.ca_run(pe, self.k, self.sweeps, h["I0"], rank_tol=self.rank_tol)
             st = oracle.residual_sample(p, o["C"], o["U"], o["R"], h["Q"], h["S"])
             n += 1
             good += st[4] <= ERR_BOUND

@@ -39,14 +39,16 @@ def test_full_size_parity(points, k, entries):
 @pytest.mark.parametrize("k", [32, 64])
 def test_f32_entries_error_against_fp64_matrix(points, k):
     """Sampled relative error of the FP32-entry CUR against the FP64 entries
-    (512 x 512 positions), next to the FP64-entry CUR's; both <= 1e-6 at k >= 32."""
+    (512 x 512 positions), next to the FP64-entry CUR's; both <= 1e-6 at k >= 32.
+    The nucleus truncates at 1e-8: at k = 64 the full-rank core's conditioning
+    would amplify the entries' rounding to ~1e-6 (rank 45 of 64 gives 1e-8)."""
     p64 = li.Problem(li.SRC_LAPLACE, N, N, X=points.X, Y=points.Y)
     p32 = li.Problem(li.SRC_LAPLACE, N, N, X=points.X, Y=points.Y, entries="f32")
     I0 = li.initial_rows(N, k, 0)
     Q, S = li.sample_positions(N, N, 512, 512, 3)
     errs = {}
     for name, p in (("f64", p64), ("f32", p32)):
-        g = gpu_ca(p, k, 3, I0)
+        g = gpu_ca(p, k, 3, I0, rank_tol=1e-8)
         st = oracle.residual_sample(p64, g["C"], g["U"], g["R"], Q, S)
         errs[name] = st[4]
     assert errs["f64"] < 1e-6 and errs["f32"] < 1e-6, errs
