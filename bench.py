@@ -117,9 +117,10 @@ class FmmWorkload:
     unit = "LRA/s"
 
     def __init__(self, npts=1 << 20, nblocks=4096, k=64, sweeps=3, tol=1e-6, q=16, s=16, entries="f64",
-                 stages=(28, 40, 64), margin=2):
+                 stages=(28, 40, 64), margin=2, h=1.05):
         self.npts, self.nblocks, self.k, self.sweeps, self.tol, self.q, self.s = npts, nblocks, k, sweeps, tol, q, s
         self.entries, self.stages, self.margin = entries, stages, margin
+        self.h = h                        # dominance threshold, between the paper's "h = 1.1 or h = 1.01"
         sizes = "-".join(map(str, stages)) if stages else str(k)
         self.name = f"{self.base}_k{sizes}_tol{tol:.0e}".replace("e-0", "e-") + ("_f32entries" if entries == "f32" else "")
 
@@ -138,7 +139,7 @@ class FmmWorkload:
                 "pivots_nucleus": "FP64", "residual_against": "FP64 entries", "k_max": self.k,
                 "generator_sizes": (f"staged {'/'.join(map(str, self.stages))}, grow while nucleus rank >= "
                                     f"size - {self.margin}" if self.stages else "fixed min(k_max, rows, cols)"),
-                "rank_tol": self.tol,
+                "rank_tol": self.tol, "h": self.h,
                 "sweeps": self.sweeps, "residual_sample": f"{self.q}x{self.s} per block"}
 
     def device(self, h, dev):
@@ -148,8 +149,8 @@ class FmmWorkload:
         X = torch.from_numpy(p.X).to(dev)
         prob = lra.Problem.kernel("laplace", X, X, entries=self.entries)
         prob64 = lra.Problem.kernel("laplace", X, X)
-        bt = lra.Batch(prob, h["blocks"], self.k, self.sweeps, h["I0"], rank_tol=self.tol, stages=self.stages,
-                       rank_margin=self.margin)
+        bt = lra.Batch(prob, h["blocks"], self.k, self.sweeps, h["I0"], h=self.h, rank_tol=self.tol,
+                       stages=self.stages, rank_margin=self.margin)
         tuned = lra.lra_ca_batched_tune(bt, reps=2)          # untimed set-up: CTA shape autotuner
         self.tuned = {"chosen": f"{bt.cb.cta_threads}x{bt.cb.ctas_per_sm}",
                       "ms": {f"{t}x{c}": round(v, 3) for (t, c), v in tuned.items()}}
@@ -168,7 +169,7 @@ class FmmWorkload:
         if self.entries != "f32":
             return []
         kw = dict(npts=self.npts, nblocks=self.nblocks, k=self.k, sweeps=self.sweeps, tol=self.tol, q=self.q,
-                  s=self.s)
+                  s=self.s, h=self.h)
         return [("plain_fp64_same_sizes", type(self)(entries="f64", stages=self.stages, margin=self.margin, **kw)),
                 ("plain_fp64_fixed_k64", type(self)(entries="f64", stages=None, **kw))]
 
@@ -230,10 +231,10 @@ class FmmWorkload:
             sub = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=h["p"].X[r0:r0 + nr], Y=h["p"].Y[c0:c0 + nc])
             sube = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=sub.X, Y=sub.Y, entries=self.entries)
             if self.stages:
-                o = oracle.ca_run_adaptive(sube, self.stages, self.margin, self.sweeps, h["I0"][idx],
+                o = oracle.ca_run_adaptive(sube, self.stages, self.margin, self.sweeps, h["I0"][idx], h=self.h,
                                            rank_tol=self.tol)
             else:
-                o = oracle.ca_run(sube, kb, self.sweeps, h["I0"][idx, :kb], rank_tol=self.tol)
+                o = oracle.ca_run(sube, kb, self.sweeps, h["I0"][idx, :kb], h=self.h, rank_tol=self.tol)
             st = oracle.residual_sample(sub, o["C"], o["U"], o["R"], h["Q"][idx], h["S"][idx])
             n += 1
             good += st[4] <= ERR_BOUND
@@ -727,8 +728,9 @@ class FmmOversampleWorkload(FmmWorkload):
             r0, nr, c0, nc = b[idx]
             sub = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=h["p"].X[r0:r0 + nr], Y=h["p"].Y[c0:c0 + nc])
             sube = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=sub.X, Y=sub.Y, entries=self.entries)
-            o = oracle.ca_run_adaptive(sube, self.stages, self.margin, self.sweeps, h["I0"][idx], rank_tol=self.tol)
-            ov = oracle.oversample(sube, o["I"], o["J"], self.pextra, rank_tol=self.tol)
+            o = oracle.ca_run_adaptive(sube, self.stages, self.margin, self.sweeps, h["I0"][idx], h=self.h,
+                                       rank_tol=self.tol)
+            ov = oracle.oversample(sube, o["I"], o["J"], self.pextra, h=self.h, rank_tol=self.tol)
             st = oracle.residual_sample(sub, ov["C"], ov["U"], ov["R"], h["Q"][idx], h["S"][idx])
             n += 1
             good += st[4] <= ERR_BOUND

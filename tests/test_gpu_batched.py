@@ -27,11 +27,11 @@ def check_block(o, g):
         assert np.abs(g["U"] - o["U"]).max() <= 1e-10 * np.abs(o["U"]).max()
 
 
-def run_batch(p, blocks, k, sweeps, rank_tol, seed=0, check=None):
+def run_batch(p, blocks, k, sweeps, rank_tol, seed=0, check=None, h=1.01):
     import paper_1710_07946_gb300 as lra
     prob, _ = to_device(p)
     I0 = li.block_initial_rows(blocks, k, seed)
-    bt = lra.Batch(prob, blocks, k, sweeps, I0, rank_tol=rank_tol)
+    bt = lra.Batch(prob, blocks, k, sweeps, I0, h=h, rank_tol=rank_tol)
     lra.lra_ca_run_batched(bt)
     torch.cuda.synchronize()
     idx = range(len(blocks)) if check is None else check
@@ -43,19 +43,19 @@ def run_batch(p, blocks, k, sweeps, rank_tol, seed=0, check=None):
         else:
             sub = li.Problem(p.src, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], ell=p.ell,
                              entries=p.entries)
-        o = oracle.ca_run(sub, kb, sweeps, I0[b, :kb], rank_tol=rank_tol)
+        o = oracle.ca_run(sub, kb, sweeps, I0[b, :kb], h=h, rank_tol=rank_tol)
         check_block(o, bt.block(b))
     return bt, I0
 
 
-def run_batch_staged(p, blocks, stages, margin, sweeps, rank_tol, seed=0, check=None):
+def run_batch_staged(p, blocks, stages, margin, sweeps, rank_tol, seed=0, check=None, h=1.01):
     """Batched run with staged generator sizes; blocks checked against the oracle's
     staged run (final size, stage count, pivots, factors, counters)."""
     import paper_1710_07946_gb300 as lra
     prob, _ = to_device(p)
     kmax = stages[-1]
     I0 = li.block_initial_rows(blocks, kmax, seed)
-    bt = lra.Batch(prob, blocks, kmax, sweeps, I0, rank_tol=rank_tol, stages=stages, rank_margin=margin)
+    bt = lra.Batch(prob, blocks, kmax, sweeps, I0, h=h, rank_tol=rank_tol, stages=stages, rank_margin=margin)
     lra.lra_ca_run_batched(bt)
     torch.cuda.synchronize()
     idx = range(len(blocks)) if check is None else check
@@ -66,7 +66,7 @@ def run_batch_staged(p, blocks, stages, margin, sweeps, rank_tol, seed=0, check=
         else:
             sub = li.Problem(p.src, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], ell=p.ell,
                              entries=p.entries)
-        o = oracle.ca_run_adaptive(sub, stages, margin, sweeps, I0[b], rank_tol=rank_tol)
+        o = oracle.ca_run_adaptive(sub, stages, margin, sweeps, I0[b], h=h, rank_tol=rank_tol)
         g = bt.block(b)
         assert g["k"] == o["k"], (b, g["k"], o["k"])
         check_block(o, g)
@@ -95,7 +95,7 @@ def test_staged_sizes_fmm_benchmark_workload_sampled_blocks():
     p, blocks, lev = li.fmm_blocks(npts=1 << 20, seed=0)
     sizes = blocks[:, 1] * blocks[:, 3]
     pick = list(np.argsort(sizes)[:3]) + list(np.argsort(sizes)[-2:])
-    run_batch_staged(p, blocks, (28, 40, 64), 2, 3, 1e-6, check=pick)
+    run_batch_staged(p, blocks, (28, 40, 64), 2, 3, 1e-6, check=pick, h=1.05)
 
 
 def test_cta_shapes_give_identical_results_and_tuner_picks_one():
@@ -199,4 +199,4 @@ def test_fmm_benchmark_workload_sampled_blocks():
     p, blocks, lev = li.fmm_blocks(npts=1 << 20, seed=0)
     sizes = blocks[:, 1] * blocks[:, 3]
     pick = list(np.argsort(sizes)[:3]) + list(np.argsort(sizes)[-2:])
-    run_batch(p, blocks, 64, 3, 1e-6, check=pick)
+    run_batch(p, blocks, 64, 3, 1e-6, check=pick, h=1.05)
