@@ -45,6 +45,8 @@ def lib():
         L.orc_nucleus.restype = i32
         L.orc_ca_run.argtypes = [P, i32, i32, vp, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_ca_run.restype = ct.c_int
+        L.orc_ca_run_warm.argtypes = [P, i32, i32, vp, vp, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_ca_run_warm.restype = ct.c_int
         L.orc_ca_run_adaptive.argtypes = [P, vp, i32, i32, i32, vp, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_ca_run_adaptive.restype = ct.c_int
         L.orc_bidiag_columns.argtypes = [i64, i32, vp, vp, vp, vp]
@@ -196,18 +198,21 @@ def jacobi_svd(A):
 
 
 # ------------------------------------------------------------------ C-A
-def ca_run(p, k, sweeps, I0, h=1.01, max_swaps=1000, rank_tol=1e-13):
+def ca_run(p, k, sweeps, I0, h=1.01, max_swaps=1000, rank_tol=1e-13, J0=None):
     """alpha C-A loops then the canonical nucleus.  Returns dict with I, J,
     C (m x k) = W'[:,J], U (k x k), R (k x n) = W[I,:], logvol (2*sweeps),
-    rank, swaps, loops, status."""
+    rank, swaps, loops, status.  J0: columns warm-starting the first column
+    step (resume from a previous run's (I, J)), or None for the cold start."""
     mp = _Marshalled(p)
     I0 = np.ascontiguousarray(I0, dtype=np.int32)
     assert len(I0) == k
+    J0 = None if J0 is None else np.ascontiguousarray(J0, dtype=np.int32)
+    assert J0 is None or len(J0) == k
     I = np.empty(k, dtype=np.int32); J = np.empty(k, dtype=np.int32)
     C = np.empty((p.m, k)); U = np.empty((k, k)); R = np.empty((k, p.n))
     lv = np.empty(2 * sweeps); info = np.empty(4, dtype=np.int32)
-    lib().orc_ca_run(mp.ref, k, sweeps, _ptr(I0), h, max_swaps, rank_tol, _ptr(I), _ptr(J), _ptr(C), _ptr(U),
-                     _ptr(R), _ptr(lv), _ptr(info))
+    lib().orc_ca_run_warm(mp.ref, k, sweeps, _ptr(I0), _ptr(J0), h, max_swaps, rank_tol, _ptr(I), _ptr(J), _ptr(C),
+                          _ptr(U), _ptr(R), _ptr(lv), _ptr(info))
     return dict(I=I, J=J, C=C, U=U, R=R, logvol=lv, rank=int(info[0]), swaps=int(info[1]),
                 loops=int(info[2]), status=int(info[3]))
 

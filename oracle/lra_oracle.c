@@ -594,9 +594,20 @@ int32_t orc_nucleus_rect(const double* G, int32_t k, int32_t l, double tol, doub
  * A strip holding NaN or Inf stops the run with status ORC_ERR_NONFINITE (the
  * outputs are then undefined).
  */
+int orc_ca_run_warm(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I0, const int32_t* J0,
+                    double h, int32_t max_swaps, double rank_tol, int32_t* I, int32_t* J, double* C, double* U,
+                    double* R, double* logvol, int32_t* info);
 int orc_ca_run(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I0, double h, int32_t max_swaps,
                double rank_tol, int32_t* I, int32_t* J, double* C, double* U, double* R, double* logvol,
                int32_t* info) {
+  return orc_ca_run_warm(p, k, sweeps, I0, NULL, h, max_swaps, rank_tol, I, J, C, U, R, logvol, info);
+}
+
+/* orc_ca_run with the first column step warm-started at the columns J0 (k
+ * distinct, or NULL for the cold start): resuming a run from its (I, J). */
+int orc_ca_run_warm(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I0, const int32_t* J0,
+                    double h, int32_t max_swaps, double rank_tol, int32_t* I, int32_t* J, double* C, double* U,
+                    double* R, double* logvol, int32_t* info) {
   int64_t m = p->m, n = p->n;
   double* Rs = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
   double* Cs = (double*)malloc(sizeof(double) * (size_t)k * (size_t)m);
@@ -605,12 +616,13 @@ int orc_ca_run(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I
   int32_t* In = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
   int status = ORC_OK, total = 0, loops = 0;
   memcpy(I, I0, sizeof(int32_t) * (size_t)k);
+  if (J0 != NULL) memcpy(J, J0, sizeof(int32_t) * (size_t)k);
   for (int32_t s = 0; s < 2 * sweeps; ++s) logvol[s] = NAN;
   for (int32_t s = 0; s < sweeps; ++s) {
     double ld; int32_t nsw1 = 0, nsw2 = 0;
     orc_gather_rows(p, I, k, Rs);
     if (!all_finite(Rs, (int64_t)k * n)) { status = ORC_ERR_NONFINITE; break; }
-    int st = orc_maxvol(Rs, k, n, s == 0 ? NULL : J, h, max_swaps, Jn, NULL, &ld, &nsw1);
+    int st = orc_maxvol(Rs, k, n, (s == 0 && J0 == NULL) ? NULL : J, h, max_swaps, Jn, NULL, &ld, &nsw1);
     if (st > status) status = st;
     memcpy(J, Jn, sizeof(int32_t) * (size_t)k);
     logvol[2 * s] = ld;

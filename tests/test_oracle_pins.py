@@ -648,6 +648,68 @@ def test_oversampled_generators_reduce_the_error():
     assert means[0] > means[1] > means[2], means
 
 
+# ------------------------------------------------------------------ limits of superfast LRA
+def test_delta_matrices_defeat_superfast_approximation():
+    """Example exdlt: of the 2mn +-delta matrices (one entry +-1, the rest 0) a superfast
+    algorithm approximates nearly half as poorly as the zero matrix, since it never
+    reads most entries.  C-A with k = 2 on 12 x 12: at least 45% end with relative
+    error >= 1."""
+    m = n = 12
+    I0 = np.array([3, 7], np.int32)
+    fail = tot = 0
+    for i in range(m):
+        for j in range(n):
+            for sgn in (1.0, -1.0):
+                W = np.zeros((m, n))
+                W[i, j] = sgn
+                o = oracle.ca_run(li.Problem(li.SRC_DENSE, m, n, W=W), 2, 3, I0)
+                err = np.linalg.norm(W - o["C"] @ o["U"] @ o["R"]) / np.linalg.norm(W)
+                tot += 1
+                fail += err >= 1 - 1e-12
+    assert fail / tot >= 0.45, fail / tot
+
+
+def test_residual_sample_sees_a_missed_delta_only_inside_its_sample():
+    """Remark reerrdlt and the superfast a-posteriori estimate: on a +-delta matrix whose
+    spike the CUR missed, the sampled residual is exactly 1 at the spike when the sample
+    covers it and exactly 0 otherwise (a superfast check cannot verify such an output)."""
+    m = n = 20
+    W = np.zeros((m, n))
+    W[13, 5] = -1.0
+    p = li.Problem(li.SRC_DENSE, m, n, W=W)
+    o = oracle.ca_run(p, 2, 3, np.array([0, 1], np.int32))
+    assert np.abs(o["C"] @ o["U"] @ o["R"]).max() == 0.0            # the spike was never read
+    hit = oracle.residual_sample(p, o["C"], o["U"], o["R"], np.array([2, 13, 17], np.int32),
+                                 np.array([5, 9], np.int32))
+    miss = oracle.residual_sample(p, o["C"], o["U"], o["R"], np.array([2, 12, 17], np.int32),
+                                  np.array([5, 9], np.int32))
+    assert hit[3] == 1.0 and hit[4] == 1.0 and miss[3] == 0.0 and miss[4] == 0.0
+
+
+def test_log_volume_equals_log_det_of_the_final_core():
+    """eq. eqb: every swap multiplies the volume by |c_ij|, every LUP pivot contributes
+    its modulus, so the tracked log-volume of the last step is log|det W'[I, J]|."""
+    for seed in range(4):
+        p = li.factor_gaussian(150, 10, 1e-3, seed)
+        o = oracle.ca_run(p, 8, 3, li.initial_rows(150, 8, seed))
+        lv = o["logvol"][np.isfinite(o["logvol"])][-1]
+        sign, ld = np.linalg.slogdet(p.W[np.ix_(o["I"], o["J"])])
+        assert abs(lv - ld) <= 1e-9 * max(1.0, abs(ld)), (lv, ld)
+
+
+def test_resuming_from_the_output_sets_keeps_the_volume():
+    """Checkpoint / resume: a run restarted warm from the (I, J) of a finished run reaches
+    a core of at least the same volume (the C-A volume never decreases); restarting cold
+    from I alone does not guarantee it (a cold LUP may pick a smaller core)."""
+    for seed in range(4):
+        p = li.factor_gaussian(200, 12, 1e-4, seed)
+        a = oracle.ca_run(p, 10, 1, li.initial_rows(200, 10, seed))
+        b = oracle.ca_run(p, 10, 3, a["I"], J0=a["J"])
+        va = np.linalg.slogdet(p.W[np.ix_(a["I"], a["J"])])[1]
+        vb = np.linalg.slogdet(p.W[np.ix_(b["I"], b["J"])])[1]
+        assert vb >= va - 1e-9
+
+
 # ------------------------------------------------------------------ apply / residual
 def test_cur_apply_matches_matmul():
     g = np.random.default_rng(0)
