@@ -212,6 +212,19 @@ lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_mul
                       const lra_cur* out, void* workspace, size_t workspace_bytes, lra_stream_t stream);
 
 /*
+ * lra_ca_run_warm -- lra_ca_run with the first column step warm-started at the
+ * columns J0 (device, k distinct indices in [0, n), or NULL for the cold
+ * start): resuming a run from its output (I, J) as (I0, J0) continues the
+ * volume-increasing swaps, so the core's volume never decreases across the
+ * restart (checkpoint / resume; the paper's C-A loops are defined by their
+ * current (I, J)).  Invalid J0 gives status LRA_ERR_INVALID_ARG in info.
+ * Arguments, workspace and errors otherwise as lra_ca_run.
+ */
+lra_status lra_ca_run_warm(const lra_problem* prob, const lra_ca_params* par, lra_multiplier mult, const int32_t* I0,
+                           const int32_t* J0, const lra_cur* out, void* workspace, size_t workspace_bytes,
+                           lra_stream_t stream);
+
+/*
  * lra_ca_run_noalloc -- lra_ca_run without a caller-supplied workspace, for
  * callers that cannot allocate device memory themselves: for instance a plug-in
  * running inside a host application whose own allocator owns the whole device

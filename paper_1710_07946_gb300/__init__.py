@@ -100,6 +100,7 @@ def _load():
     L.lra_ca_workspace_size.argtypes = [P, PP, vp, ct.POINTER(sz)]
     L.lra_ca_run.argtypes = [P, PP, vp, vp, PC, vp, sz, vp]
     L.lra_ca_run_noalloc.argtypes = [P, PP, vp, vp, PC, vp]
+    L.lra_ca_run_warm.argtypes = [P, PP, vp, vp, vp, PC, vp, sz, vp]
     L.lra_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp, vp, sz, vp]
     L.lra_cur_apply_workspace_size.argtypes = [i64, i32, i32, ct.POINTER(sz)]
     L.lra_residual_sample.argtypes = [P, vp, vp, vp, i32, vp, i32, vp, i32, vp, vp, vp, sz, vp]
@@ -125,7 +126,7 @@ def _load():
     L.lra_launch_count.restype = ct.c_int64
     L.lra_profile_enable.argtypes = [i32]
     L.lra_profile_collect.argtypes = [i32, vp, vp, vp, ct.POINTER(i32)]
-    for f in ("lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run",
+    for f in ("lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run", "lra_ca_run_warm",
               "lra_ca_run_noalloc",
               "lra_cur_apply", "lra_cur_apply_workspace_size", "lra_residual_sample",
               "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect",
@@ -280,16 +281,20 @@ def lra_ca_workspace_size(problem: Problem, k: int, sweeps: int = 3, h: float = 
 def lra_ca_run(problem: Problem, I0: torch.Tensor, k: int, sweeps: int = 3, h: float = 1.01,
                rank_tol: float = 1e-13, max_swaps: int = 1000, mode: int = LRA_MODE_FP64,
                multiplier: Optional[Multiplier] = None, out: Optional[dict] = None,
-               workspace: Optional[torch.Tensor] = None, stream=None) -> dict:
+               workspace: Optional[torch.Tensor] = None, stream=None, J0: Optional[torch.Tensor] = None) -> dict:
     """C-A CUR approximation W ~ C U R of W' = W M (see lra_ca_run in lra.h).
 
-    I0: device int32 tensor of k distinct initial rows.  Returns a dict of
+    I0: device int32 tensor of k distinct initial rows; J0 (optional): k columns
+    warm-starting the first column step (lra_ca_run_warm: resume from a previous
+    run's I, J).  Returns a dict of
     device tensors I, J, C (m x k), U (k x k), R (k x n), logvol (2*sweeps),
     info (rank, swaps, loops, status); the call is asynchronous on ``stream``.
     Pass ``out`` (same dict layout) and ``workspace`` to reuse buffers."""
     L = _load()
     dev = (problem.W if problem.W is not None else problem.X).device
     _dev(I0, torch.int32, "I0")
+    if J0 is not None:
+        _dev(J0, torch.int32, "J0")
     pc, pp = problem._c(), _params(k, sweeps, h, rank_tol, max_swaps, mode)
     mh = multiplier.handle if multiplier else None
     if out is None:
@@ -306,8 +311,8 @@ def lra_ca_run(problem: Problem, I0: torch.Tensor, k: int, sweeps: int = 3, h: f
     cur = _Cur()
     for f in ("I", "J", "C", "U", "R", "logvol", "info"):
         setattr(cur, f, _dev(out[f], name=f).data_ptr())
-    _check(L.lra_ca_run(ct.byref(pc), ct.byref(pp), mh, I0.data_ptr(), ct.byref(cur), workspace.data_ptr(),
-                        workspace.numel(), _stream(stream)), "lra_ca_run")
+    _check(L.lra_ca_run_warm(ct.byref(pc), ct.byref(pp), mh, I0.data_ptr(), None if J0 is None else J0.data_ptr(),
+                             ct.byref(cur), workspace.data_ptr(), workspace.numel(), _stream(stream)), "lra_ca_run")
     out["_workspace"] = workspace
     return out
 

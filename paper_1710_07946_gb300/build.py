@@ -71,7 +71,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs, capture_output=True, text=True)
+    r = subprocess.run([cc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + ["-ldl"], capture_output=True,
+                       text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)

@@ -66,6 +66,7 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
       continue;
     }
     CaArgs A;
+    memset(&A, 0, sizeof(A));
     A.P = B.base;
     A.P.m = nr;
     A.P.n = nc;

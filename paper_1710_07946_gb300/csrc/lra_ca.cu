@@ -133,6 +133,12 @@ lra_status lra_ca_workspace_size(const lra_problem* prob, const lra_ca_params* p
 
 lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_multiplier mult, const int32_t* I0,
                       const lra_cur* out, void* workspace, size_t workspace_bytes, lra_stream_t stream_) {
+  return lra_ca_run_warm(prob, par, mult, I0, nullptr, out, workspace, workspace_bytes, stream_);
+}
+
+lra_status lra_ca_run_warm(const lra_problem* prob, const lra_ca_params* par, lra_multiplier mult, const int32_t* I0,
+                           const int32_t* J0, const lra_cur* out, void* workspace, size_t workspace_bytes,
+                           lra_stream_t stream_) {
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   DevProblem P;
   lra_status st = make_dev_problem(prob, mult, &P);
@@ -155,6 +161,7 @@ lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_mul
   A.max_swaps = par->max_swaps;
   A.h = par->h;
   A.I0 = I0;
+  A.J0 = J0;
   A.I = out->I;
   A.J = out->J;
   A.C = out->C;

@@ -31,6 +31,7 @@ struct CaArgs {
   int32_t k, sweeps, max_swaps;
   double h;
   const int32_t* I0;
+  const int32_t* J0 = nullptr;   // columns warm-starting the first column step, or null (cold start)
   int32_t* I;
   int32_t* J;
   double* C;           // m x k

@@ -37,7 +37,7 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
   const DevProblem& P = A.P;
   const int k = A.k, tid = threadIdx.x, nt = blockDim.x;
   const bool lead = grp.rank() == 0;
-  // initial rows; every CTA validates them identically
+  // initial rows (and warm-start columns); every CTA validates them identically
   if (tid == 0) {
     int bad = 0;
     for (int a = 0; a < k; ++a) {
@@ -46,6 +46,13 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
       if (v < 0 || v >= P.m) bad = 1;
       for (int b = 0; b < a; ++b) if (S.Is[b] == v) bad = 1;
     }
+    if (A.J0 != nullptr)
+      for (int a = 0; a < k; ++a) {
+        int32_t v = A.J0[a];
+        S.Js[a] = v;
+        if (v < 0 || v >= P.n) bad = 1;
+        for (int b = 0; b < a; ++b) if (S.Js[b] == v) bad = 1;
+      }
     S.ctl[4] = bad;
   }
   if (lead) for (int s = tid; s < 2 * A.sweeps; s += nt) A.logvol[s] = __longlong_as_double(0x7ff8000000000000ll);
@@ -57,7 +64,7 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
   unsigned long long seq = 0;
   int status = LRA_OK, err = LRA_OK, total = 0, loops = 0, n32 = 0, n64 = 0;
   for (int s = 0; s < A.sweeps; ++s) {
-    StepResult r0 = run_step<Group, MIXED>(grp, A, S, 0, s == 0, S.Js, seq, lead, n32, n64);
+    StepResult r0 = run_step<Group, MIXED>(grp, A, S, 0, s == 0 && A.J0 == nullptr, S.Js, seq, lead, n32, n64);
     if (r0.status != LRA_OK && r0.status < 16) { err = r0.status; break; }
     if (r0.status > status) status = r0.status;
     __syncthreads();

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(NTB, MINB) cynical_batched_kernel(CynArgs B) {
     }
     // the block as a problem of its own
     CaArgs A;
+    std::memset(&A, 0, sizeof(A));
     A.P = B.base;
     A.P.m = nr;
     A.P.n = nc;

@@ -1,15 +1,20 @@
-// lra_profile.cu -- launch counting and optional per-launch CUDA-event timing.
+// lra_profile.cu -- launch counting, NVTX ranges and optional per-launch
+// CUDA-event timing.
 //
 // Every kernel launch of the library goes through LaunchScope: it counts the
-// launch and, when timing is enabled, brackets it with two CUDA events recorded
-// on the launch's own stream.  lra_profile_collect() waits for the recorded
-// events and returns per-kernel totals.  Timing is meant for benchmarks; leave
-// it off while capturing a CUDA graph.
+// launch, opens an NVTX range named after the kernel around the launch call
+// (free when no tracing tool is attached), and, when timing is enabled,
+// brackets it with two CUDA events recorded on the launch's own stream.
+// lra_profile_collect() waits for the recorded events and returns per-kernel
+// totals.  Timing is meant for benchmarks; leave it off while capturing a CUDA
+// graph.
 #include <atomic>
 #include <cstring>
 #include <mutex>
 #include <string>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "lra_internal.h"
 #include "lra_profile.h"
@@ -27,6 +32,7 @@ static std::vector<Rec> g_recs;
 
 LaunchScope::LaunchScope(cudaStream_t s, const char* name) : stream_(s), name_(name), a_(nullptr), b_(nullptr) {
   g_launches.fetch_add(1, std::memory_order_relaxed);
+  nvtxRangePushA(name);
   if (g_timing.load(std::memory_order_relaxed)) {
     if (cudaEventCreate(&a_) == cudaSuccess && cudaEventCreate(&b_) == cudaSuccess) {
       cudaEventRecord(a_, stream_);
@@ -43,6 +49,7 @@ LaunchScope::~LaunchScope() {
     std::lock_guard<std::mutex> lk(g_mu);
     g_recs.push_back(Rec{name_, a_, b_});
   }
+  nvtxRangePop();
 }
 
 }  // namespace lra

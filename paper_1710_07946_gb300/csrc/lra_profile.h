@@ -1,5 +1,5 @@
 // lra_profile.h -- RAII scope around each kernel launch of the library
-// (launch counting; CUDA-event timing when enabled).
+// (launch counting; an NVTX range; CUDA-event timing when enabled).
 #pragma once
 
 #include <cuda_runtime.h>

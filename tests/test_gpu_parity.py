@@ -154,6 +154,25 @@ def test_repeatable_and_stream_ordered():
 
 
 # ---------------------------------------------------------------- apply / residual
+def test_resume_from_output_sets():
+    """lra_ca_run_warm resumed from a finished run's (I, J) equals the oracle's warm
+    run and never loses volume; an invalid J0 is reported in the status word."""
+    import paper_1710_07946_gb300 as lra
+    p = li.factor_gaussian(600, 14, 1e-4, seed=6)
+    I0 = li.initial_rows(600, 12, 2)
+    a = gpu_ca(p, 12, 1, I0)
+    o = oracle.ca_run(p, 12, 3, a["I"], J0=a["J"])
+    g = gpu_ca(p, 12, 3, a["I"], J0=torch.from_numpy(a["J"]).cuda())
+    assert_parity(o, g)
+    va = np.linalg.slogdet(p.W[np.ix_(a["I"], a["J"])])[1]
+    vg = np.linalg.slogdet(p.W[np.ix_(g["I"], g["J"])])[1]
+    assert vg >= va - 1e-9
+    bad = a["J"].copy()
+    bad[1] = bad[0]
+    gb = gpu_ca(p, 12, 3, a["I"], J0=torch.from_numpy(bad).cuda())
+    assert gb["status"] == lra.LRA_ERR_INVALID_ARG
+
+
 def test_cur_apply_matches_oracle():
     import paper_1710_07946_gb300 as lra
     p = li.dense_lowrank(700, 900, r=6, noise=1e-6, seed=1)
