@@ -18,7 +18,7 @@
 
 namespace lra {
 
-constexpr int GT = 256;          // threads per CTA
+constexpr int GT = 512;          // threads per CTA
 constexpr int TILE = 64;         // rows (of C) or columns (of R) per tile
 
 struct GaussArgs {
