@@ -55,6 +55,8 @@ def lib():
         L.orc_nucleus_rect.restype = i32
         L.orc_oversample.argtypes = [P, vp, vp, i32, i32, f64, f64, vp, vp, vp, vp, vp]
         L.orc_oversample.restype = ct.c_int
+        L.orc_oversample_cycle.argtypes = [P, vp, vp, i32, i32, i32, i32, f64, f64, vp, vp, vp, vp, vp]
+        L.orc_oversample_cycle.restype = ct.c_int
         L.orc_cynical.argtypes = [P, i32, i32, i32, vp, vp, vp, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp]
         L.orc_cynical.restype = ct.c_int
         L.orc_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp]
@@ -280,23 +282,25 @@ def nucleus_rect(G, tol):
     return U, int(r)
 
 
-def oversample(p, I, J, pextra, h=1.01, rank_tol=1e-13):
+def oversample(p, I, J, pextra, h=1.01, rank_tol=1e-13, pmax=0, max_cycles=0):
     """Rectangular k x (k + pextra) generator grown from the square one (I, J) by
-    greedy volume expansions (orc_oversample).  Returns J (l), C (m x l),
-    U (l x k), R (k x n), rank, l, status."""
+    greedy volume expansions, then (pmax > 0) expansion/contraction cycles
+    until the generator passes the local h-maximality test of Corollary colclmx
+    (orc_oversample_cycle).  Returns J (l), C (m x l), U (l x k), R (k x n),
+    rank, l, status, cycles (kept), ptried (largest p tried)."""
     mp = _Marshalled(p)
     I = np.ascontiguousarray(I, dtype=np.int32)
     J = np.ascontiguousarray(J, dtype=np.int32)
     k, L = len(I), len(I) + int(pextra)
-    Jo = np.zeros(L, dtype=np.int32)
+    Jo = np.zeros(L + max(int(pmax), 0), dtype=np.int32)
     C = np.zeros((p.m, L)); U = np.zeros((L, k)); R = np.zeros((k, p.n))
-    info = np.zeros(3, dtype=np.int32)
-    lib().orc_oversample(mp.ref, _ptr(I), _ptr(J), k, int(pextra), h, rank_tol, _ptr(Jo), _ptr(C), _ptr(U), _ptr(R),
-                         _ptr(info))
+    info = np.zeros(5, dtype=np.int32)
+    lib().orc_oversample_cycle(mp.ref, _ptr(I), _ptr(J), k, int(pextra), int(pmax), int(max_cycles), h, rank_tol,
+                               _ptr(Jo), _ptr(C), _ptr(U), _ptr(R), _ptr(info))
     l = int(info[1])
     return dict(J=Jo[:l].copy(), C=np.ascontiguousarray(C.reshape(-1)[:p.m * l].reshape(p.m, l)),
                 U=np.ascontiguousarray(U.reshape(-1)[:l * k].reshape(l, k)), R=R, rank=int(info[0]), l=l,
-                status=int(info[2]))
+                status=int(info[2]), cycles=int(info[3]), ptried=int(info[4]))
 
 
 def cur_apply(C, U, R, X):

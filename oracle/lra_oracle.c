@@ -795,36 +795,117 @@ int orc_cynical(const orc_problem* p, int32_t kind, int32_t r, int32_t q, int32_
 }
 
 /*
- * orc_oversample: a rectangular k x l generator (l = k + p) from the rows I
- * and columns J of a square one: Algorithm algrup's greedy expansions of a
- * k x k submatrix to k x l, each adding the column that increases the volume
- * of the generator C_g (sqrt det C_g C_g^T) the most; Theorem th3 bounds the
- * CUR error of such generators.
+ * Whitening update of X for one column entering (sign = +1) or leaving
+ * (sign = -1) the generator C_g.  X = T W'[I, :] with T^T T = (C_g C_g^T)^{-1},
+ * so s_q = ||X[:, q]||^2 = b_q^T (C_g C_g^T)^{-1} b_q for every column b_q.
+ * With x = X[:, j] (copied first) and sigma = ||x||^2, Sherman-Morrison gives
+ *   entering: T' = (I - g x x^T) T,  g = (1 - 1/sqrt(1 + sigma)) / sigma,
+ *   leaving:  T' = (I + g x x^T) T,  g = (1/sqrt(1 - sigma) - 1) / sigma,
+ * applied to every column q (inside the generator or not, j included):
+ * t = x . X[:, q] (ascending fma chain), X[:, q] <- fma(-+g t, x, X[:, q]),
+ * and s_q is recomputed (ascending fma chain).  sigma = 0 changes nothing.
+ */
+static void ov_whiten(double* X, double* s, double* x, int32_t k, int64_t n, int64_t j, int sign) {
+  double sigma = s[j];
+  if (sigma == 0.0) return;
+  double g = (sign > 0) ? (1.0 - 1.0 / sqrt(1.0 + sigma)) / sigma : (1.0 / sqrt(1.0 - sigma) - 1.0) / sigma;
+  double gs = (sign > 0) ? -g : g;
+  for (int32_t i = 0; i < k; ++i) x[i] = X[(int64_t)i * n + j];
+  for (int64_t q = 0; q < n; ++q) {
+    double t = 0.0;
+    for (int32_t i = 0; i < k; ++i) t = fma(x[i], X[(int64_t)i * n + q], t);
+    double c = gs * t;
+    double v = 0.0;
+    for (int32_t i = 0; i < k; ++i) {
+      X[(int64_t)i * n + q] = fma(c, x[i], X[(int64_t)i * n + q]);
+      v = fma(X[(int64_t)i * n + q], X[(int64_t)i * n + q], v);
+    }
+    s[q] = v;
+  }
+}
+
+/* Greedy expansion by up to p columns (Algorithm algrup): the column outside
+ * the generator with the largest s_j (lowest j on ties) joins it, appended to
+ * Jo; none joins once the largest s_j is 0.  rho is multiplied by 1 + s_j
+ * (Theorem th2: the squared volume grows by that factor).  Returns the number
+ * added. */
+static int32_t ov_expand(double* X, double* s, double* x, unsigned char* in, int32_t* Jo, int32_t* l, int32_t k,
+                         int64_t n, int32_t p, double* rho) {
+  int32_t added = 0;
+  for (int32_t g = 0; g < p; ++g) {
+    int64_t js = -1;
+    for (int64_t j = 0; j < n; ++j)
+      if (!in[j] && (js < 0 || s[j] > s[js])) js = j;
+    if (js < 0 || !(s[js] > 0.0)) break;
+    *rho = *rho * (1.0 + s[js]);
+    in[js] = 1;
+    Jo[(*l)++] = (int32_t)js;
+    ov_whiten(X, s, x, k, n, js, +1);
+    ++added;
+  }
+  return added;
+}
+
+/* Greedy contraction by p columns (the reverse of Algorithm algrup): the
+ * column inside the generator with the smallest s_j (lowest j on ties) leaves
+ * it; Jo keeps the order of the columns that stay.  rho is multiplied by
+ * 1 - s_j (Theorem th2: the squared volume shrinks by that factor).  Returns 0,
+ * or -1 if the smallest s_j is not below 1 (the generator would lose rank). */
+static int ov_contract(double* X, double* s, double* x, unsigned char* in, int32_t* Jo, int32_t* l, int32_t k,
+                       int64_t n, int32_t p, double* rho) {
+  for (int32_t g = 0; g < p; ++g) {
+    int64_t jr = -1;
+    for (int64_t j = 0; j < n; ++j)
+      if (in[j] && !isnan(s[j]) && (jr < 0 || s[j] < s[jr])) jr = j;
+    if (jr < 0 || !(s[jr] < 1.0)) return -1;
+    *rho = *rho * (1.0 - s[jr]);
+    int32_t a = 0;
+    while (Jo[a] != (int32_t)jr) ++a;
+    for (; a + 1 < *l; ++a) Jo[a] = Jo[a + 1];
+    --(*l);
+    in[jr] = 0;
+    ov_whiten(X, s, x, k, n, jr, -1);
+  }
+  return 0;
+}
+
+/*
+ * orc_oversample_cycle: a rectangular k x l generator (l = k + p) from the
+ * rows I and columns J of a square one.
  *  1. X = B^{-1} W'[I, :], B = W'[I, J]: the C matrix of a maxvol step
  *     (orc_maxvol) on the row strip warm-started at J with no swaps; its
- *     selected set J0 (J unless the warm LU met a zero pivot) starts J'.  A
- *     rank-deficient strip (zero pivot) keeps J' = J and adds nothing.
- *  2. p times: the column j outside J' with the largest s_j = ||X[:, j]||^2
- *     (ascending fma chain; lowest j on ties) joins J' (the squared volume
- *     grows by the factor 1 + s_j); with x = X[:, j] and sigma = s_j, every
- *     column q outside J' becomes X[:, q] - gamma (x . X[:, q]) x, gamma =
- *     (1 - 1/sqrt(1 + sigma)) / sigma, which keeps s_q = b_q^T (C C^T)^{-1} b_q
- *     for the grown generator (Sherman-Morrison), and s_q is recomputed.  No
- *     column is added once the largest s_j is 0.
- *  3. U = orc_nucleus_rect of W'[I, J'] (k x l), C = W'[:, J'] (m x l), R =
+ *     columns J are exact unit vectors, and its selected set J0 (J unless the
+ *     warm LU met a zero pivot) starts J'.  A rank-deficient strip (zero
+ *     pivot) keeps J' = J; nothing is added and no cycle runs.
+ *  2. Algorithm algrup: pextra greedy expansions (ov_expand), each adding the
+ *     column that increases the volume of the generator C_g (sqrt det C_g C_g^T)
+ *     the most; Theorem th3 bounds the CUR error of such generators.
+ *  3. Section scrsorth's expansion/contraction cycles, when pmax > 0.  The
+ *     generator is accepted as locally h-maximal when 1 + max s_q over the
+ *     columns q outside it is at most h (Corollary colclmx with b^2 = max s_q).
+ *     Otherwise a p-cycle expands by p columns and contracts back by p
+ *     (ov_contract).  It is kept when it changed the set and its volume factor
+ *     rho (the product of the 1 + s and 1 - s factors) is above 1, and p
+ *     restarts at 1.  Otherwise X, s and J' are restored and p grows by one.
+ *     The loop ends when the test passes (status unchanged), or when p passes
+ *     pmax or max_cycles cycles were kept (status ORC_WARN_NOT_CONVERGED).
+ *  4. U = orc_nucleus_rect of W'[I, J'] (k x l), C = W'[:, J'] (m x l), R =
  *     W[I, :] (k x n).
- * J' (k + p), C (m x (k+p)), U ((k+p) x k) are sized for l = k + p; info:
- * rank, l (used), status (worst of the maxvol step and the nucleus).
+ * C (m x (k+pextra)) and U ((k+pextra) x k) are sized for l = k + pextra; J'
+ * needs k + pextra + pmax entries (a cycle grows it by p before contracting).
+ * info: rank, l (used), status (worst of the maxvol step, the cycles and the
+ * nucleus), cycles kept, the largest p tried.
  */
-int orc_oversample(const orc_problem* p, const int32_t* I, const int32_t* J, int32_t k, int32_t pextra,
-                   double h, double rank_tol, int32_t* Jo, double* C, double* U, double* R, int32_t* info) {
+int orc_oversample_cycle(const orc_problem* p, const int32_t* I, const int32_t* J, int32_t k, int32_t pextra,
+                         int32_t pmax, int32_t max_cycles, double h, double rank_tol, int32_t* Jo, double* C,
+                         double* U, double* R, int32_t* info) {
   int64_t m = p->m, n = p->n;
-  int32_t l = k;
+  int32_t l = k, cycles = 0, ptried = 0;
   double* X = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
   double* Rs = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
   orc_gather_rows(p, I, k, Rs);
   if (!all_finite(Rs, (int64_t)k * n)) {
-    info[0] = 0; info[1] = k; info[2] = ORC_ERR_NONFINITE;
+    info[0] = 0; info[1] = k; info[2] = ORC_ERR_NONFINITE; info[3] = 0; info[4] = 0;
     free(X); free(Rs);
     return ORC_ERR_NONFINITE;
   }
@@ -843,28 +924,52 @@ int orc_oversample(const orc_problem* p, const int32_t* I, const int32_t* J, int
       for (int32_t i = 0; i < k; ++i) v = fma(X[(int64_t)i * n + j], X[(int64_t)i * n + j], v);
       s[j] = v;
     }
-    for (int32_t g = 0; g < pextra; ++g) {
-      int64_t js = -1;
-      for (int64_t j = 0; j < n; ++j)
-        if (!in[j] && (js < 0 || s[j] > s[js])) js = j;
-      if (js < 0 || s[js] == 0.0) break;
-      double sigma = s[js];
-      double gamma = (1.0 - 1.0 / sqrt(1.0 + sigma)) / sigma;
-      for (int32_t i = 0; i < k; ++i) x[i] = X[(int64_t)i * n + js];
-      in[js] = 1;
-      Jo[l++] = (int32_t)js;
-      for (int64_t q = 0; q < n; ++q) {
-        if (in[q]) continue;
-        double t = 0.0;
-        for (int32_t i = 0; i < k; ++i) t = fma(x[i], X[(int64_t)i * n + q], t);
-        double c = gamma * t;
-        double v = 0.0;
-        for (int32_t i = 0; i < k; ++i) {
-          X[(int64_t)i * n + q] = fma(-c, x[i], X[(int64_t)i * n + q]);
-          v = fma(X[(int64_t)i * n + q], X[(int64_t)i * n + q], v);
+    double rho = 1.0;
+    ov_expand(X, s, x, in, Jo, &l, k, n, pextra, &rho);
+    if (pmax > 0) {
+      int32_t ltarget = l;
+      double* Xb = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
+      double* sb = (double*)malloc(sizeof(double) * (size_t)n);
+      int32_t* Jb = (int32_t*)malloc(sizeof(int32_t) * (size_t)(ltarget + pmax));
+      int converged = 0;
+      int32_t pc = 1;
+      for (;;) {
+        double smax = 0.0;
+        for (int64_t q = 0; q < n; ++q)
+          if (!in[q] && s[q] > smax) smax = s[q];
+        if (1.0 + smax <= h) { converged = 1; break; }
+        if (pc > pmax || cycles >= max_cycles) break;
+        if (pc > ptried) ptried = pc;
+        memcpy(Xb, X, sizeof(double) * (size_t)k * (size_t)n);
+        memcpy(sb, s, sizeof(double) * (size_t)n);
+        memcpy(Jb, Jo, sizeof(int32_t) * (size_t)ltarget);
+        rho = 1.0;
+        int32_t added = ov_expand(X, s, x, in, Jo, &l, k, n, pc, &rho);
+        int ok = (added > 0) && ov_contract(X, s, x, in, Jo, &l, k, n, added, &rho) == 0;
+        int changed = 0;
+        if (ok) {
+          /* the same set iff every kept column was in the old set */
+          for (int32_t a = 0; a < l && !changed; ++a) {
+            int found = 0;
+            for (int32_t b = 0; b < ltarget; ++b) if (Jb[b] == Jo[a]) { found = 1; break; }
+            if (!found) changed = 1;
+          }
         }
-        s[q] = v;
+        if (ok && changed && rho > 1.0) {
+          ++cycles;
+          pc = 1;
+        } else {
+          for (int32_t a = 0; a < l; ++a) in[Jo[a]] = 0;
+          memcpy(X, Xb, sizeof(double) * (size_t)k * (size_t)n);
+          memcpy(s, sb, sizeof(double) * (size_t)n);
+          memcpy(Jo, Jb, sizeof(int32_t) * (size_t)ltarget);
+          l = ltarget;
+          for (int32_t a = 0; a < l; ++a) in[Jo[a]] = 1;
+          ++pc;
+        }
       }
+      if (!converged && status == ORC_OK) status = ORC_WARN_NOT_CONVERGED;
+      free(Xb); free(sb); free(Jb);
     }
   }
   /* outputs at l */
@@ -878,9 +983,19 @@ int orc_oversample(const orc_problem* p, const int32_t* I, const int32_t* J, int
     for (int32_t b = 0; b < l; ++b) G[(int64_t)a * l + b] = C[(int64_t)I[a] * l + b];
   int32_t r = orc_nucleus_rect(G, k, l, rank_tol, U);
   if (r < k && status == ORC_OK) status = ORC_WARN_RANK_DEFICIENT;
-  info[0] = r; info[1] = l; info[2] = status;
+  info[0] = r; info[1] = l; info[2] = status; info[3] = cycles; info[4] = ptried;
   free(X); free(Rs); free(in); free(s); free(x); free(Ct); free(G);
   return status;
+}
+
+/* orc_oversample: orc_oversample_cycle without cycles (pmax = 0); info: rank,
+ * l (used), status. */
+int orc_oversample(const orc_problem* p, const int32_t* I, const int32_t* J, int32_t k, int32_t pextra,
+                   double h, double rank_tol, int32_t* Jo, double* C, double* U, double* R, int32_t* info) {
+  int32_t inf[5];
+  int st = orc_oversample_cycle(p, I, J, k, pextra, 0, 0, h, rank_tol, Jo, C, U, R, inf);
+  info[0] = inf[0]; info[1] = inf[1]; info[2] = inf[2];
+  return st;
 }
 
 /* ------------------------------------------------------------------ */

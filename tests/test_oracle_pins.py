@@ -648,6 +648,117 @@ def test_oversampled_generators_reduce_the_error():
     assert means[0] > means[1] > means[2], means
 
 
+# ------------------------------------------------------------------ expansion/contraction cycles
+def _leverages(Rs, J):
+    """s_q = b_q^T (A A^T)^{-1} b_q for every column b_q of Rs, A = Rs[:, J] (Theorem th2)."""
+    A = Rs[:, list(J)]
+    Gi = np.linalg.inv(A @ A.T)
+    return np.einsum("ij,ik,kj->j", Rs, Gi, Rs)
+
+
+def _greedy_expand(Rs, J, p):
+    J = list(J)
+    for _ in range(p):
+        s = _leverages(Rs, J)
+        s[J] = -np.inf
+        js = int(np.argmax(s))
+        if not s[js] > 0:
+            break
+        J.append(js)
+    return J
+
+
+def _cycles_by_definition(Rs, J0, pextra, pmax, max_cycles, h):
+    """Section scrsorth's recipe from scratch: leverages and volumes recomputed
+    from their definitions at every step (no Sherman-Morrison updates)."""
+    n = Rs.shape[1]
+    vol = lambda JJ: np.linalg.slogdet(Rs[:, JJ] @ Rs[:, JJ].T)[1]
+    J = _greedy_expand(Rs, J0, pextra)
+    cycles = ptried = 0
+    pc, converged = 1, False
+    while True:
+        s = _leverages(Rs, J)
+        out = np.ones(n, bool)
+        out[J] = False
+        if 1 + (s[out].max() if out.any() else 0.0) <= h:
+            converged = True
+            break
+        if pc > pmax or cycles >= max_cycles:
+            break
+        ptried = max(ptried, pc)
+        Jn = _greedy_expand(Rs, J, pc)
+        added = len(Jn) - len(J)
+        ok = added > 0
+        for _ in range(added if ok else 0):
+            s = _leverages(Rs, Jn)
+            jr = min(Jn, key=lambda j: (s[j], j))
+            if not s[jr] < 1:
+                ok = False
+                break
+            Jn.remove(jr)
+        if ok and set(Jn) != set(J) and vol(Jn) > vol(J):
+            J, cycles, pc = Jn, cycles + 1, 1
+        else:
+            pc += 1
+    return J, cycles, ptried, converged
+
+
+def test_cycles_follow_the_definition():
+    """The oracle's cycles (whitening updates of Theorem th2) take the same
+    decisions as the recipe evaluated from the definitions of the leverages and
+    volumes: the same final column list, kept cycles, largest p and outcome."""
+    kept = 0
+    for seed in range(16):
+        p = li.dense_lowrank(60, 80, r=12, noise=1e-4, seed=seed)
+        o = oracle.ca_run(p, 5, 3, li.initial_rows(60, 5, seed))
+        ov = oracle.oversample(p, o["I"], o["J"], 3, h=1.05, pmax=3, max_cycles=20)
+        J, cycles, ptried, converged = _cycles_by_definition(p.W[o["I"], :], o["J"], 3, 3, 20, 1.05)
+        assert list(ov["J"]) == J, seed
+        assert (ov["cycles"], ov["ptried"]) == (cycles, ptried), seed
+        assert (ov["status"] == 0) == converged, seed
+        kept += cycles
+    assert kept > 5
+
+
+def test_cycles_reach_the_colclmx_test():
+    """A generator that fails Corollary colclmx's test after the greedy
+    expansion (1 + max outside leverage > h) passes it after a kept cycle; the
+    status says which (0, or LRA_WARN_NOT_CONVERGED)."""
+    p = li.dense_lowrank(60, 80, r=6, noise=1e-3, seed=3)
+    o = oracle.ca_run(p, 4, 3, li.initial_rows(60, 4, 3))
+    Rs = p.W[o["I"], :]
+    h = 1.25
+    plain = oracle.oversample(p, o["I"], o["J"], 8, h=h)
+    cyc = oracle.oversample(p, o["I"], o["J"], 8, h=h, pmax=4, max_cycles=20)
+    smax = lambda J: np.delete(_leverages(Rs, J), list(J)).max()
+    assert 1 + smax(plain["J"]) > h
+    assert cyc["status"] == 0 and cyc["cycles"] >= 1
+    assert 1 + smax(cyc["J"]) <= h
+    stuck = oracle.oversample(p, o["I"], o["J"], 8, h=1.0001, pmax=4, max_cycles=20)
+    assert stuck["status"] == 17 and stuck["ptried"] == 4
+
+
+def test_cycles_never_lower_the_volume():
+    """Each kept cycle raises det(C_l C_l^T); a large h keeps the plain greedy
+    expansion (the test passes at once, no cycle)."""
+    gains = []
+    for seed in range(10):
+        p = li.dense_lowrank(120, 150, r=16, noise=1e-5, seed=seed)
+        o = oracle.ca_run(p, 6, 3, li.initial_rows(120, 6, seed))
+        Rs = p.W[o["I"], :]
+        plain = oracle.oversample(p, o["I"], o["J"], 6, h=1.05)
+        cyc = oracle.oversample(p, o["I"], o["J"], 6, h=1.05, pmax=4, max_cycles=50)
+        v = lambda J: np.linalg.slogdet(Rs[:, list(J)] @ Rs[:, list(J)].T)[1]
+        gains.append(v(cyc["J"]) - v(plain["J"]))
+        assert gains[-1] >= -1e-12, seed
+        assert (gains[-1] > 0) == (cyc["cycles"] > 0), seed
+        big = oracle.oversample(p, o["I"], o["J"], 6, h=1e6, pmax=4, max_cycles=50)
+        assert big["status"] == 0 and big["cycles"] == 0 and big["ptried"] == 0
+        np.testing.assert_array_equal(big["J"], plain["J"])
+        np.testing.assert_array_equal(big["U"], plain["U"])
+    assert max(gains) > 0
+
+
 # ------------------------------------------------------------------ limits of superfast LRA
 def test_delta_matrices_defeat_superfast_approximation():
     """Example exdlt: of the 2mn +-delta matrices (one entry +-1, the rest 0) a superfast
