@@ -677,26 +677,32 @@ class FmmOversampleWorkload(FmmWorkload):
     one step = the batched C-A launch + the batched expansion + the rectangular
     residual sample against the FP64 entries."""
 
-    def __init__(self, pextra=8, **kw):
+    def __init__(self, pextra=8, pmax=0, max_cycles=32, **kw):
         super().__init__(entries="f32", **kw)
-        self.pextra = pextra
-        self.name = self.name + f"_oversample{pextra}"
+        self.pextra, self.pmax, self.max_cycles = pextra, pmax, max_cycles
+        self.name = self.name + f"_oversample{pextra}" + (f"_cycles{pmax}" if pmax else "")
 
     def config(self, h):
         c = super().config(h)
         c["generator"] = f"rectangular k x (k + {self.pextra}) by greedy volume expansions"
+        if self.pmax:
+            c["generator"] += (f", then expansion/contraction cycles (p <= {self.pmax}, "
+                               f"<= {self.max_cycles} kept)")
         return c
 
     def device(self, h, dev):
         import paper_1710_07946_gb300 as lra
         d = super().device(h, dev)
-        d["ov"] = lra.Oversampled(d["bt"], self.pextra)
+        d["ov"] = lra.Oversampled(d["bt"], self.pextra, self.pmax)
         return d
 
     def step(self, d):
         import paper_1710_07946_gb300 as lra
         lra.lra_ca_run_batched(d["bt"])
-        lra.lra_oversample_batched(d["bt"], self.pextra, d["ov"])
+        if self.pmax:
+            lra.lra_oversample_cycle_batched(d["bt"], self.pextra, self.pmax, self.max_cycles, d["ov"])
+        else:
+            lra.lra_oversample_batched(d["bt"], self.pextra, d["ov"])
         lra.lra_residual_sample_oversampled(d["ov"], d["Q"], d["S"], d["stats"], problem=d["prob64"])
 
     def check(self, d):
@@ -730,7 +736,8 @@ class FmmOversampleWorkload(FmmWorkload):
             sube = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=sub.X, Y=sub.Y, entries=self.entries)
             o = oracle.ca_run_adaptive(sube, self.stages, self.margin, self.sweeps, h["I0"][idx], h=self.h,
                                        rank_tol=self.tol)
-            ov = oracle.oversample(sube, o["I"], o["J"], self.pextra, h=self.h, rank_tol=self.tol)
+            ov = oracle.oversample(sube, o["I"], o["J"], self.pextra, h=self.h, rank_tol=self.tol, pmax=self.pmax,
+                                   max_cycles=self.max_cycles)
             st = oracle.residual_sample(sub, ov["C"], ov["U"], ov["R"], h["Q"][idx], h["S"][idx])
             n += 1
             good += st[4] <= ERR_BOUND
@@ -756,6 +763,7 @@ WORKLOADS = {
     "fmm_f64": FmmWorkload,
     "fmm_fixedk": lambda: FmmWorkload(stages=None),
     "fmm_oversample8": lambda: FmmOversampleWorkload(8),
+    "fmm_oversample8_cycles4": lambda: FmmOversampleWorkload(8, pmax=4),
     "fmm_small": FmmSmallWorkload,
     **{f"laplace65536_k{k}{sfx}": (lambda k=k, e=e: LaplaceSingleWorkload(k, e))
        for k in (16, 32, 64) for sfx, e in (("", "f64"), ("_f32", "f32"))},

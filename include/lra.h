@@ -377,7 +377,8 @@ lra_status lra_cynical_batched_tune(const lra_problem* base, const lra_batch* ba
  * min(par->k + pextra, ncols) and par->k), U_b (l_b x k_b, row-major) at the
  * start of an (par->k + pextra) x par->k slot: the pinv of the rank-r QRP
  * truncation of W'[I, J'] at par->rank_tol (r = info[0]); info[3] status,
- * info[6] = k_b, info[7] = l_b.  Blocks whose C-A run failed keep its status.
+ * info[6] = k_b, info[7] = l_b, info[1] = info[2] = 0.  Blocks whose C-A run
+ * failed keep its status.
  * par->k: the C-A run's largest size; par->h: the maxvol threshold.
  * Errors: LRA_ERR_INVALID_ARG (also when the rectangular nucleus of par->k x
  * (par->k + pextra) does not fit in shared memory), LRA_ERR_WORKSPACE,
@@ -388,6 +389,36 @@ lra_status lra_oversample_batched_workspace_size(const lra_problem* base, const 
 lra_status lra_oversample_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
                                   int32_t pextra, const lra_cur_batch* in, const lra_cur_batch* out, void* workspace,
                                   size_t workspace_bytes, lra_stream_t stream);
+
+/*
+ * lra_oversample_cycle_batched -- lra_oversample_batched followed by the
+ * expansion/contraction cycles of Section scrsorth (QRP-based greedy iterative
+ * search for locally maximal volume).  After the greedy expansion to l_b:
+ *   while the generator fails Corollary colclmx's test of local
+ *   par->h-maximality, 1 + max s_q over the columns q outside J' <= par->h,
+ *   a p-cycle (p starts at 1) expands J' greedily by p columns and contracts it
+ *   greedily by p: the column of J' with the smallest s_j (lowest j on ties;
+ *   it must be below 1) leaves, the others keep their order, and X[:, q] +=
+ *   gamma' (x . X[:, q]) x for every column with gamma' = (1/sqrt(1 - sigma)
+ *   - 1) / sigma (Theorem th2: the squared volume shrinks by 1 - s_j).  The
+ *   cycle is kept when it changed the set and the product of its 1 + s and
+ *   1 - s factors is above 1 (p restarts at 1); otherwise the state before it
+ *   is restored and p grows by one.  The loop ends when the test passes, p
+ *   exceeds pmax, or par->max_swaps cycles were kept.
+ * Arguments, outputs and errors as lra_oversample_batched, plus: pmax (0..16;
+ * 0 = lra_oversample_batched), par->max_swaps >= 0 (largest number of kept
+ * cycles).  info[1] = cycles kept, info[2] = largest p tried; info[3] is
+ * LRA_WARN_NOT_CONVERGED when the test did not pass (the generator is still
+ * valid).  The workspace adds (par->k + 1) x batch->max_len doubles per CTA for
+ * the copy of X and s.
+ */
+lra_status lra_oversample_cycle_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
+                                                       const lra_ca_params* par, int32_t pextra, int32_t pmax,
+                                                       size_t* bytes);
+lra_status lra_oversample_cycle_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                                        int32_t pextra, int32_t pmax, const lra_cur_batch* in,
+                                        const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
+                                        lra_stream_t stream);
 
 /*
  * lra_ca_batched_shapes -- the CTA shapes the batched kernel is built for:

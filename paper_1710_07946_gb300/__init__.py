@@ -116,6 +116,8 @@ def _load():
                                            ct.POINTER(i32), ct.POINTER(i32), vp]
     L.lra_oversample_batched_workspace_size.argtypes = [P, PB, PP, i32, ct.POINTER(sz)]
     L.lra_oversample_batched.argtypes = [P, PB, PP, i32, PCB, PCB, vp, sz, vp]
+    L.lra_oversample_cycle_batched_workspace_size.argtypes = [P, PB, PP, i32, i32, ct.POINTER(sz)]
+    L.lra_oversample_cycle_batched.argtypes = [P, PB, PP, i32, i32, PCB, PCB, vp, sz, vp]
     L.lra_residual_sample_batched_rect.argtypes = [P, PB, i32, i32, PCB, vp, i32, vp, i32, vp, vp]
     L.lra_ca_batched_shapes.argtypes = [vp, vp, i32]
     L.lra_ca_batched_shapes.restype = i32
@@ -133,6 +135,7 @@ def _load():
               "lra_ca_batched_workspace_size", "lra_ca_run_batched", "lra_residual_sample_batched",
               "lra_ca_batched_tune", "lra_cynical_batched_workspace_size", "lra_cynical_run_batched",
               "lra_cynical_batched_tune", "lra_oversample_batched_workspace_size", "lra_oversample_batched",
+              "lra_oversample_cycle_batched_workspace_size", "lra_oversample_cycle_batched",
               "lra_residual_sample_batched_rect",
               "lra_gauss_cur_forward", "lra_gauss_cur_backward"):
         getattr(L, f).restype = ct.c_int
@@ -537,12 +540,14 @@ def lra_cynical_run_batched(batch: Batch, kind: int, q: int, K: torch.Tensor, L:
 
 
 class Oversampled:
-    """Device outputs of lra_oversample_batched for a processed Batch: rectangular
-    k_b x l_b generators (l_b = min(k_b + pextra, ncols))."""
+    """Device outputs of lra_oversample_batched (or, with pmax > 0,
+    lra_oversample_cycle_batched) for a processed Batch: rectangular k_b x l_b
+    generators (l_b = min(k_b + pextra, ncols))."""
 
-    def __init__(self, batch: Batch, pextra: int):
+    def __init__(self, batch: Batch, pextra: int, pmax: int = 0):
         import numpy as np
         b, k, p = batch, batch.k, int(pextra)
+        self.pmax = int(pmax)
         blocks = b.blocks_np
         lcap = np.minimum(k + p, blocks[:, 3])
         csz, rsz = blocks[:, 1] * lcap, np.minimum(k, np.minimum(blocks[:, 1], blocks[:, 3])) * blocks[:, 3]
@@ -567,8 +572,10 @@ class Oversampled:
         for f in ("I", "J", "C", "U", "R", "logvol", "info"):
             setattr(self.cur, f, self.out[f].data_ptr())
         nbytes = ct.c_size_t()
-        _check(_load().lra_oversample_batched_workspace_size(ct.byref(b.pc), ct.byref(self.cb), ct.byref(b.params), p,
-                                                             ct.byref(nbytes)), "lra_oversample_batched_workspace_size")
+        _check(_load().lra_oversample_cycle_batched_workspace_size(ct.byref(b.pc), ct.byref(self.cb),
+                                                                   ct.byref(b.params), p, self.pmax,
+                                                                   ct.byref(nbytes)),
+               "lra_oversample_cycle_batched_workspace_size")
         self.workspace = _workspace(nbytes.value, dev)
 
     def block(self, i: int) -> dict:
@@ -579,7 +586,7 @@ class Oversampled:
         oc, orr = self.offs_np[i]
         return dict(I=o["I"][i, :k], J=o["J"][i, :l], C=o["C"][oc:oc + nr * l].reshape(nr, l),
                     U=o["U"][i].reshape(-1)[:l * k].reshape(l, k), R=o["R"][orr:orr + k * nc].reshape(k, nc),
-                    rank=int(info[0]), status=int(info[3]), k=k, l=l)
+                    rank=int(info[0]), status=int(info[3]), k=k, l=l, cycles=int(info[1]), ptried=int(info[2]))
 
 
 def lra_oversample_batched(batch: Batch, pextra: int, ov: Optional[Oversampled] = None, stream=None) -> Oversampled:
@@ -588,6 +595,24 @@ def lra_oversample_batched(batch: Batch, pextra: int, ov: Optional[Oversampled] 
     _check(_load().lra_oversample_batched(ct.byref(batch.pc), ct.byref(ov.cb), ct.byref(batch.params), ov.pextra,
                                           ct.byref(batch.cur), ct.byref(ov.cur), ov.workspace.data_ptr(),
                                           ov.workspace.numel(), _stream(stream)), "lra_oversample_batched")
+    return ov
+
+
+def lra_oversample_cycle_batched(batch: Batch, pextra: int, pmax: int, max_cycles: int,
+                                 ov: Optional[Oversampled] = None, stream=None) -> Oversampled:
+    """Rectangular generators grown greedily from the batch's square ones, then
+    refined by expansion/contraction cycles (p = 1..pmax, at most max_cycles
+    kept) until they pass the local h-maximality test at the batch's h."""
+    ov = ov or Oversampled(batch, pextra, pmax)
+    if ov.pmax < int(pmax):
+        raise ValueError("the Oversampled workspace was sized for a smaller pmax")
+    par = _Params()
+    ct.memmove(ct.byref(par), ct.byref(batch.params), ct.sizeof(_Params))
+    par.max_swaps = int(max_cycles)
+    _check(_load().lra_oversample_cycle_batched(ct.byref(batch.pc), ct.byref(ov.cb), ct.byref(par), ov.pextra,
+                                                int(pmax), ct.byref(batch.cur), ct.byref(ov.cur),
+                                                ov.workspace.data_ptr(), ov.workspace.numel(), _stream(stream)),
+           "lra_oversample_cycle_batched")
     return ov
 
 

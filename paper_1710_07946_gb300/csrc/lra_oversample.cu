@@ -10,7 +10,14 @@
 // ||X[:, j]||^2 joins it (the squared volume grows by 1 + s_j) and every other
 // column is whitened again, X[:, q] -= gamma (x . X[:, q]) x with gamma =
 // (1 - 1/sqrt(1 + sigma)) / sigma (Sherman-Morrison for (C C^T)^{-1}); the
-// columns are independent, one thread each.  Outputs C = W'[:, J'], the
+// columns are independent, one thread each.  With pmax > 0, Section scrsorth's
+// expansion/contraction cycles follow: while the generator fails the local
+// h-maximality test of Corollary colclmx (1 + max s_q over the columns outside
+// it <= h), a p-cycle adds p columns greedily and removes p greedily (the column
+// with the smallest s_j leaves, X[:, q] += gamma' (x . X[:, q]) x with
+// gamma' = (1/sqrt(1 - sigma) - 1) / sigma, Theorem th2); a cycle that changed
+// the set and raised the volume is kept and p restarts at 1, otherwise X, s and
+// J' are restored from a per-CTA copy and p grows.  Outputs C = W'[:, J'], the
 // rectangular nucleus U of W'[I, J'] and R = W[I, :].
 #include <algorithm>
 #include <cstring>
@@ -28,6 +35,7 @@ struct OvArgs {
   const int64_t* offs;        // nb x 2: offsets of C_b (nrows x l_b) and R_b (k_b x ncols) in the outputs
   const int32_t* order;
   int32_t nb, kmax, pextra, lmax;
+  int32_t pmax, max_cycles;   // expansion/contraction cycles (pmax = 0: none)
   double h, rank_tol;
   const int32_t* Iin;         // nb x kmax
   const int32_t* Jin;         // nb x kmax
@@ -39,17 +47,119 @@ struct OvArgs {
   double* U;                  // nb x lmax x kmax
   int32_t* info;              // nb x LRA_INFO_LEN
   unsigned int* counter;
-  double* scratch;            // per CTA: G (kmax x lmax) then, if needed, a strip (kmax x max_len)
+  double* scratch;            // per CTA: G (kmax x lmax), if needed a strip (kmax x max_len), and with
+                              // cycles a copy of X and s ((kmax + 1) x max_len)
   size_t scratch_stride;
+  size_t backup_offset;       // doubles from the CTA's scratch to its copy of X and s
   size_t smem_bytes;
   int64_t max_len;
 };
+
+constexpr int PMAX = 16;     // largest p of an expansion/contraction cycle
+
+// Key that orders candidates by the smallest |x| first (0 = no candidate, NaN never one).
+__device__ __forceinline__ unsigned long long min_key(double x) {
+  const unsigned long long a = mag_key(x);
+  return a == 0ull ? 0ull : (INF_BITS + 2ull) - a;
+}
+
+// Whitening update of X (k x nc, leading dimension ldm) for column j entering
+// (sign = +1) or leaving (sign = -1) the generator: with x = X[:, j] and
+// sigma = s_j, X[:, q] <- fma(c_q, x, X[:, q]) for every column q, c_q = -+g t_q,
+// t_q = x . X[:, q], g = (1 - 1/sqrt(1 + sigma)) / sigma entering and
+// (1/sqrt(1 - sigma) - 1) / sigma leaving (Sherman-Morrison), then s_q is
+// recomputed.  sigma = 0 changes nothing.  Called by the whole CTA.
+__device__ void ov_whiten(double* M, int ldm, double* s, int k, int nc, int j, int sign, double* s_x, double* s_g) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const double sigma = s[j];
+  if (sigma == 0.0) return;
+  if (tid == 0)
+    s_g[0] = (sign > 0) ? -((1.0 - 1.0 / sqrt(1.0 + sigma)) / sigma) : (1.0 / sqrt(1.0 - sigma) - 1.0) / sigma;
+  for (int i = tid; i < k; i += nt) s_x[i] = M[(int64_t)i * ldm + j];
+  __syncthreads();
+  const double gs = s_g[0];
+  for (int c = tid; c < nc; c += nt) {
+    double t = 0.0;
+    for (int i = 0; i < k; ++i) t = fma(s_x[i], M[(int64_t)i * ldm + c], t);
+    const double cc = gs * t;
+    double v = 0.0;
+    for (int i = 0; i < k; ++i) {
+      const double x = fma(cc, s_x[i], M[(int64_t)i * ldm + c]);
+      M[(int64_t)i * ldm + c] = x;
+      v = fma(x, x, v);
+    }
+    s[c] = v;
+  }
+  __syncthreads();
+}
+
+// Greedy expansion by up to p columns (Algorithm algrup): the column outside
+// the generator with the largest s_j (lowest j on ties) is appended to Jw; none
+// once the largest s_j is 0.  rho[0] *= 1 + s_j.  Returns the number added.
+__device__ int ov_expand(double* M, int ldm, double* s, int32_t* pos, int32_t* Jw, int& l, int k, int nc, int p,
+                         double* rho, double* s_x, double* s_g, CandRed* red) {
+  int added = 0;
+  for (int g = 0; g < p; ++g) {
+    Cand mine = cand_none();
+    for (int c = threadIdx.x; c < nc; c += blockDim.x)
+      if (!pos[c]) cand_consider(mine, mag_key(s[c]), 0, c);
+    unsigned long long fl = 0;
+    const Cand w = block_best(mine, fl, red);
+    if (w.key == 0ull || w.key == mag_key(0.0)) break;
+    const int js = w.j;
+    if (threadIdx.x == 0) {
+      rho[0] = rho[0] * (1.0 + s[js]);
+      pos[js] = 1;
+      Jw[l] = js;
+    }
+    __syncthreads();
+    ++l;
+    ov_whiten(M, ldm, s, k, nc, js, +1, s_x, s_g);
+    ++added;
+  }
+  __syncthreads();
+  return added;
+}
+
+// Greedy contraction by p columns (the reverse of Algorithm algrup): the column
+// inside the generator with the smallest s_j (lowest j on ties) leaves Jw, whose
+// other entries keep their order.  rho[0] *= 1 - s_j.  Returns false if the
+// smallest s_j is not below 1.
+__device__ bool ov_contract(double* M, int ldm, double* s, int32_t* pos, int32_t* Jw, int& l, int k, int nc, int p,
+                            double* rho, double* s_x, double* s_g, CandRed* red) {
+  for (int g = 0; g < p; ++g) {
+    Cand mine = cand_none();
+    for (int c = threadIdx.x; c < nc; c += blockDim.x)
+      if (pos[c]) cand_consider(mine, min_key(s[c]), 0, c);
+    unsigned long long fl = 0;
+    const Cand w = block_best(mine, fl, red);
+    if (w.key == 0ull) return false;
+    const int jr = w.j;
+    if (!(s[jr] < 1.0)) return false;
+    if (threadIdx.x == 0) {
+      rho[0] = rho[0] * (1.0 - s[jr]);
+      int a = 0;
+      while (a < l && Jw[a] != jr) ++a;
+      for (; a + 1 < l; ++a) Jw[a] = Jw[a + 1];
+      pos[jr] = 0;
+    }
+    __syncthreads();
+    --l;
+    ov_whiten(M, ldm, s, k, nc, jr, -1, s_x, s_g);
+  }
+  __syncthreads();
+  return true;
+}
 
 __global__ void __launch_bounds__(NT) oversample_kernel(OvArgs B) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_b;
   __shared__ double s_x[KMAX];
   __shared__ double s_g[2];
+  __shared__ double s_rho[1];
+  __shared__ int s_flag;
+  __shared__ int32_t s_Jw[2 * KMAX + PMAX];   // the generator's columns during expansion and cycles
+  __shared__ int32_t s_Jb[2 * KMAX];          // their copy at the start of a cycle
   double* G = B.scratch + (size_t)blockIdx.x * B.scratch_stride;
   double* gstrip = G + (size_t)B.kmax * B.lmax;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -96,7 +206,7 @@ __global__ void __launch_bounds__(NT) oversample_kernel(OvArgs B) {
     A.strip_in_smem = ca_smem_fixed(k, A.ldm) + sizeof(double) * (size_t)k * A.ldm <= B.smem_bytes;
     A.gstrip = A.strip_in_smem ? nullptr : gstrip;
     int32_t* Jb = B.J + (size_t)b * B.lmax;
-    int l = k, st = LRA_OK;
+    int l = k, st = LRA_OK, cycles = 0, ptried = 0;
     {
       const CaSmem S = ca_smem_carve(smem, k, A.ldm, A.gstrip);
       for (int a = tid; a < k; a += nt) {
@@ -119,50 +229,75 @@ __global__ void __launch_bounds__(NT) oversample_kernel(OvArgs B) {
         // zero pivot: no expansion, the square generator as given
         for (int a = tid; a < k; a += nt) Jb[a] = B.Jin[(size_t)b * B.kmax + a];
       } else {
-        for (int a = tid; a < k; a += nt) Jb[a] = S.Js[a];
+        for (int a = tid; a < k; a += nt) s_Jw[a] = S.Js[a];
         double* M = S.M;
         double* s = S.tq;                        // per-column s_j (ldm doubles)
-        // s_j of the columns outside the generator, ascending rows
+        // s_j of every column, ascending rows (the generator's columns are unit vectors)
         for (int c = tid; c < nc; c += nt) {
-          if (S.pos[c]) continue;
           double v = 0.0;
           for (int i = 0; i < k; ++i) v = fma(M[(int64_t)i * A.ldm + c], M[(int64_t)i * A.ldm + c], v);
           s[c] = v;
         }
+        if (tid == 0) s_rho[0] = 1.0;
         __syncthreads();
-        for (int g = 0; g < B.pextra && l < lb; ++g) {
-          Cand mine = cand_none();
-          for (int c = tid; c < nc; c += nt)
-            if (!S.pos[c]) cand_consider(mine, mag_key(s[c]), 0, c);
-          unsigned long long fl = 0;
-          const Cand w = block_best(mine, fl, S.red);
-          if (w.key == 0ull || w.key == mag_key(0.0)) break;     // nothing left, or no volume gain
-          const int js = w.j;
-          if (tid == 0) {
-            const double sigma = s[js];
-            s_g[0] = (1.0 - 1.0 / sqrt(1.0 + sigma)) / sigma;
-            S.pos[js] = l + 1;
-            Jb[l] = js;
-          }
-          for (int i = tid; i < k; i += nt) s_x[i] = M[(int64_t)i * A.ldm + js];
-          __syncthreads();
-          ++l;
-          const double gamma = s_g[0];
-          for (int c = tid; c < nc; c += nt) {
-            if (S.pos[c]) continue;
-            double t = 0.0;
-            for (int i = 0; i < k; ++i) t = fma(s_x[i], M[(int64_t)i * A.ldm + c], t);
-            const double cc = gamma * t;
-            double v = 0.0;
-            for (int i = 0; i < k; ++i) {
-              const double x = fma(-cc, s_x[i], M[(int64_t)i * A.ldm + c]);
-              M[(int64_t)i * A.ldm + c] = x;
-              v = fma(x, x, v);
+        ov_expand(M, A.ldm, s, S.pos, s_Jw, l, k, (int)nc, lb - k, s_rho, s_x, s_g, S.red);
+        if (B.pmax > 0) {
+          const int ltarget = l;
+          double* Mb = G + B.backup_offset;
+          bool converged = false;
+          int pc = 1;
+          for (;;) {
+            Cand mine = cand_none();
+            for (int c = tid; c < nc; c += nt)
+              if (!S.pos[c]) cand_consider(mine, mag_key(s[c]), 0, c);
+            unsigned long long fl = 0;
+            const Cand w = block_best(mine, fl, S.red);
+            const double smax = (w.key == 0ull) ? 0.0 : s[w.j];
+            if (1.0 + smax <= B.h) { converged = true; break; }
+            if (pc > B.pmax || cycles >= B.max_cycles) break;
+            ptried = max(ptried, pc);
+            for (int64_t it = tid; it < (int64_t)k * nc; it += nt) {
+              const int i = (int)(it / nc);
+              Mb[it] = M[(int64_t)i * A.ldm + (it - (int64_t)i * nc)];
             }
-            s[c] = v;
+            for (int c = tid; c < nc; c += nt) Mb[(int64_t)k * nc + c] = s[c];
+            for (int a = tid; a < ltarget; a += nt) s_Jb[a] = s_Jw[a];
+            if (tid == 0) { s_rho[0] = 1.0; s_flag = 0; }
+            __syncthreads();
+            const int added = ov_expand(M, A.ldm, s, S.pos, s_Jw, l, k, (int)nc, pc, s_rho, s_x, s_g, S.red);
+            const bool ok = added > 0 && ov_contract(M, A.ldm, s, S.pos, s_Jw, l, k, (int)nc, added, s_rho, s_x,
+                                                     s_g, S.red);
+            if (ok) {
+              for (int a = tid; a < l; a += nt) {
+                bool found = false;
+                for (int e = 0; e < ltarget; ++e) found = found || (s_Jb[e] == s_Jw[a]);
+                if (!found) s_flag = 1;
+              }
+            }
+            __syncthreads();
+            if (ok && s_flag != 0 && s_rho[0] > 1.0) {
+              ++cycles;
+              pc = 1;
+            } else {
+              for (int a = tid; a < l; a += nt) S.pos[s_Jw[a]] = 0;
+              __syncthreads();
+              for (int64_t it = tid; it < (int64_t)k * nc; it += nt) {
+                const int i = (int)(it / nc);
+                M[(int64_t)i * A.ldm + (it - (int64_t)i * nc)] = Mb[it];
+              }
+              for (int c = tid; c < nc; c += nt) s[c] = Mb[(int64_t)k * nc + c];
+              for (int a = tid; a < ltarget; a += nt) {
+                s_Jw[a] = s_Jb[a];
+                S.pos[s_Jb[a]] = 1;
+              }
+              l = ltarget;
+              ++pc;
+            }
+            __syncthreads();
           }
-          __syncthreads();
+          if (!converged && st == LRA_OK) st = LRA_WARN_NOT_CONVERGED;
         }
+        for (int a = tid; a < l; a += nt) Jb[a] = s_Jw[a];
       }
     }
     __syncthreads();
@@ -189,7 +324,8 @@ __global__ void __launch_bounds__(NT) oversample_kernel(OvArgs B) {
     const int rank = nucleus_rect_cta(G, k, l, B.rank_tol, B.U + (size_t)b * B.lmax * B.kmax, smem);
     if (tid == 0) {
       if (rank < k && st == LRA_OK) st = LRA_WARN_RANK_DEFICIENT;
-      info[0] = rank; info[1] = 0; info[2] = 0; info[3] = st; info[4] = 0; info[5] = 0; info[6] = k; info[7] = l;
+      info[0] = rank; info[1] = cycles; info[2] = ptried; info[3] = st; info[4] = 0; info[5] = 0; info[6] = k;
+      info[7] = l;
     }
     __syncthreads();
   }
@@ -197,10 +333,10 @@ __global__ void __launch_bounds__(NT) oversample_kernel(OvArgs B) {
 
 struct OvPlan {
   int grid;
-  size_t smem, scratch_stride, bytes;
+  size_t smem, scratch_stride, backup_offset, bytes;
 };
 
-static lra_status ov_plan(int kmax, int lmax, int64_t max_len, OvPlan* pl) {
+static lra_status ov_plan(int kmax, int lmax, int64_t max_len, int pmax, OvPlan* pl) {
   DeviceInfo dev;
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
@@ -217,13 +353,14 @@ static lra_status ov_plan(int kmax, int lmax, int64_t max_len, OvPlan* pl) {
   if (occ < 1) return LRA_ERR_INVALID_ARG;
   pl->grid = occ * dev.sms;
   pl->smem = need;
-  pl->scratch_stride = align_up((size_t)kmax * lmax + (gstrip ? (size_t)kmax * max_len : 0), 32);
+  pl->backup_offset = (size_t)kmax * lmax + (gstrip ? (size_t)kmax * max_len : 0);
+  pl->scratch_stride = align_up(pl->backup_offset + (pmax > 0 ? (size_t)(kmax + 1) * max_len : 0), 32);
   pl->bytes = align_up(256 + sizeof(double) * pl->scratch_stride * pl->grid, 256);
   return LRA_OK;
 }
 
 static lra_status ov_check(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par, int32_t pextra,
-                           DevProblem* P) {
+                           int32_t pmax, DevProblem* P) {
   lra_status st = make_dev_problem(base, nullptr, P);
   if (st != LRA_OK) return st;
   if (batch == nullptr || par == nullptr || batch->blocks == nullptr || batch->offsets == nullptr || batch->nb < 1 ||
@@ -232,39 +369,21 @@ static lra_status ov_check(const lra_problem* base, const lra_batch* batch, cons
   if (par->k < 1 || par->k > KMAX || pextra < 0 || pextra > KMAX || !(par->h >= 1.0) || !(par->h < 1e300) ||
       !(par->rank_tol >= 0.0) || !(par->rank_tol < 1.0))
     return LRA_ERR_INVALID_ARG;
+  if (pmax < 0 || pmax > PMAX || (pmax > 0 && par->max_swaps < 0)) return LRA_ERR_INVALID_ARG;
   return LRA_OK;
 }
 
-}  // namespace lra
-
-using namespace lra;
-
-extern "C" {
-
-lra_status lra_oversample_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
-                                                 const lra_ca_params* par, int32_t pextra, size_t* bytes) {
-  if (bytes == nullptr) return LRA_ERR_INVALID_ARG;
+static lra_status ov_run(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par, int32_t pextra,
+                         int32_t pmax, const lra_cur_batch* in, const lra_cur_batch* out, void* workspace,
+                         size_t workspace_bytes, cudaStream_t stream) {
   DevProblem P;
-  lra_status st = ov_check(base, batch, par, pextra, &P);
-  if (st != LRA_OK) return st;
-  OvPlan pl;
-  if ((st = ov_plan(par->k, par->k + pextra, batch->max_len, &pl)) != LRA_OK) return st;
-  *bytes = pl.bytes;
-  return LRA_OK;
-}
-
-lra_status lra_oversample_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
-                                  int32_t pextra, const lra_cur_batch* in, const lra_cur_batch* out, void* workspace,
-                                  size_t workspace_bytes, lra_stream_t stream_) {
-  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  DevProblem P;
-  lra_status st = ov_check(base, batch, par, pextra, &P);
+  lra_status st = ov_check(base, batch, par, pextra, pmax, &P);
   if (st != LRA_OK) return st;
   if (in == nullptr || out == nullptr || !in->I || !in->J || !in->info || !out->I || !out->J || !out->C || !out->U ||
       !out->R || !out->info)
     return LRA_ERR_INVALID_ARG;
   OvPlan pl;
-  if ((st = ov_plan(par->k, par->k + pextra, batch->max_len, &pl)) != LRA_OK) return st;
+  if ((st = ov_plan(par->k, par->k + pextra, batch->max_len, pmax, &pl)) != LRA_OK) return st;
   if (workspace == nullptr || workspace_bytes < pl.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255u))
     return LRA_ERR_WORKSPACE;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
@@ -278,6 +397,8 @@ lra_status lra_oversample_batched(const lra_problem* base, const lra_batch* batc
   A.kmax = par->k;
   A.pextra = pextra;
   A.lmax = par->k + pextra;
+  A.pmax = pmax;
+  A.max_cycles = pmax > 0 ? par->max_swaps : 0;
   A.h = par->h;
   A.rank_tol = par->rank_tol;
   A.Iin = in->I;
@@ -292,6 +413,7 @@ lra_status lra_oversample_batched(const lra_problem* base, const lra_batch* batc
   A.counter = reinterpret_cast<unsigned int*>(ws);
   A.scratch = reinterpret_cast<double*>(ws + 256);
   A.scratch_stride = pl.scratch_stride;
+  A.backup_offset = pl.backup_offset;
   A.smem_bytes = pl.smem;
   A.max_len = batch->max_len;
   LRA_CUDA_TRY(cudaMemsetAsync(ws, 0, 256, stream));
@@ -300,6 +422,50 @@ lra_status lra_oversample_batched(const lra_problem* base, const lra_batch* batc
     oversample_kernel<<<pl.grid, NT, pl.smem, stream>>>(A);
   }
   return cuda_status(cudaGetLastError());
+}
+
+static lra_status ov_workspace(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                               int32_t pextra, int32_t pmax, size_t* bytes) {
+  if (bytes == nullptr) return LRA_ERR_INVALID_ARG;
+  DevProblem P;
+  lra_status st = ov_check(base, batch, par, pextra, pmax, &P);
+  if (st != LRA_OK) return st;
+  OvPlan pl;
+  if ((st = ov_plan(par->k, par->k + pextra, batch->max_len, pmax, &pl)) != LRA_OK) return st;
+  *bytes = pl.bytes;
+  return LRA_OK;
+}
+
+}  // namespace lra
+
+using namespace lra;
+
+extern "C" {
+
+lra_status lra_oversample_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
+                                                 const lra_ca_params* par, int32_t pextra, size_t* bytes) {
+  return ov_workspace(base, batch, par, pextra, 0, bytes);
+}
+
+lra_status lra_oversample_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                                  int32_t pextra, const lra_cur_batch* in, const lra_cur_batch* out, void* workspace,
+                                  size_t workspace_bytes, lra_stream_t stream) {
+  return ov_run(base, batch, par, pextra, 0, in, out, workspace, workspace_bytes,
+                reinterpret_cast<cudaStream_t>(stream));
+}
+
+lra_status lra_oversample_cycle_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
+                                                       const lra_ca_params* par, int32_t pextra, int32_t pmax,
+                                                       size_t* bytes) {
+  return ov_workspace(base, batch, par, pextra, pmax, bytes);
+}
+
+lra_status lra_oversample_cycle_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                                        int32_t pextra, int32_t pmax, const lra_cur_batch* in,
+                                        const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
+                                        lra_stream_t stream) {
+  return ov_run(base, batch, par, pextra, pmax, in, out, workspace, workspace_bytes,
+                reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -1,7 +1,8 @@
 """Rectangular k x l generators grown from a batched C-A run's square ones
-(greedy volume expansions) and their rectangular nucleus, against the FP64
-oracle block by block: the grown column sets and gathered factors bit-exact, U
-within 1e-10; the rectangular residual sample against the oracle's."""
+(greedy volume expansions, then expansion/contraction cycles) and their
+rectangular nucleus, against the FP64 oracle block by block: the grown column
+sets, cycle counts and gathered factors bit-exact, U within 1e-10; the
+rectangular residual sample against the oracle's."""
 import numpy as np
 import pytest
 
@@ -24,20 +25,25 @@ def sub_problem(p, blk):
     return li.Problem(p.src, nr, nc, X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], ell=p.ell, entries=p.entries)
 
 
-def run(p, blocks, k, pextra, rank_tol, stages=None, seed=0):
+def run(p, blocks, k, pextra, rank_tol, stages=None, seed=0, pmax=0, max_cycles=0, h=1.01):
     import paper_1710_07946_gb300 as lra
     prob, _ = to_device(p)
     I0 = li.block_initial_rows(blocks, k, seed)
-    bt = lra.Batch(prob, blocks, k, 3, I0, rank_tol=rank_tol, stages=stages)
+    bt = lra.Batch(prob, blocks, k, 3, I0, h=h, rank_tol=rank_tol, stages=stages)
     lra.lra_ca_run_batched(bt)
-    ov = lra.lra_oversample_batched(bt, pextra)
+    if pmax > 0:
+        ov = lra.lra_oversample_cycle_batched(bt, pextra, pmax, max_cycles)
+    else:
+        ov = lra.lra_oversample_batched(bt, pextra)
     torch.cuda.synchronize()
     for b in range(len(blocks)):
         g0 = bt.block(b)
         sub = sub_problem(p, blocks[b])
-        o = oracle.oversample(sub, g0["I"], g0["J"], pextra, rank_tol=rank_tol)
+        o = oracle.oversample(sub, g0["I"], g0["J"], pextra, h=h, rank_tol=rank_tol, pmax=pmax,
+                              max_cycles=max_cycles)
         g = ov.block(b)
         assert (g["status"], g["rank"], g["l"], g["k"]) == (o["status"], o["rank"], o["l"], len(g0["I"])), b
+        assert (g["cycles"], g["ptried"]) == (o["cycles"], o["ptried"]), b
         np.testing.assert_array_equal(g["J"], o["J"])
         np.testing.assert_array_equal(g["C"], o["C"])
         np.testing.assert_array_equal(g["R"], o["R"])
@@ -74,3 +80,34 @@ def test_rectangular_residual_matches_oracle_and_improves():
         np.testing.assert_allclose(st_ov[b, 1:], so[1:], rtol=1e-9, atol=1e-300)
     # wider generators lower the error (Theorem th3), on average over the blocks
     assert np.mean(np.log(st_ov[:, 4])) < np.mean(np.log(st_sq[:, 4]))
+
+
+def test_cycles_on_fmm_blocks_match_oracle():
+    """Section scrsorth: expansion/contraction cycles after the greedy expansion,
+    at the FMM threshold h = 1.05: the kept cycles, the largest p tried and the
+    final column sets equal the oracle's; no cycle lowers the volume."""
+    p, blocks, lev = li.fmm_blocks(npts=1 << 15, leaf=64, min_size=64, max_size=2048, nblocks=48, seed=8)
+    bt, ov = run(p, blocks, 32, 8, 1e-6, stages=(16, 24, 32), pmax=4, max_cycles=32, h=1.05)
+    ov0 = __import__("paper_1710_07946_gb300").lra_oversample_batched(bt, 8)
+    torch.cuda.synchronize()
+    kept = 0
+    for b in range(len(blocks)):
+        g, g0 = ov.block(b), ov0.block(b)
+        kept += g["cycles"]
+        if g["rank"] == g["k"] and g["l"] > g["k"]:
+            v = np.linalg.slogdet(g["C"][g["I"], :] @ g["C"][g["I"], :].T)[1]
+            v0 = np.linalg.slogdet(g0["C"][g0["I"], :] @ g0["C"][g0["I"], :].T)[1]
+            assert v >= v0 - 1e-9, b
+    assert kept > 0
+
+
+def test_cycles_limits_and_clipped_blocks():
+    """max_cycles = 1 stops after one kept cycle; blocks with no column left
+    outside the generator pass the test at once; a large h passes it at once."""
+    p = li.dense_lowrank(600, 700, r=30, noise=1e-7, seed=5)
+    blocks = np.array([[0, 600, 0, 700], [10, 300, 40, 20], [100, 200, 300, 400], [0, 64, 0, 70]], dtype=np.int64)
+    run(p, blocks, 12, 6, 1e-13, pmax=3, max_cycles=1)
+    run(p, blocks, 12, 6, 1e-13, pmax=16, max_cycles=100)
+    run(p, blocks, 12, 6, 1e-13, pmax=2, max_cycles=8, h=100.0)
+    q = li.factor_gaussian(400, 5, 0.0, seed=4)
+    run(q, np.array([[0, 200, 0, 150], [100, 300, 200, 200]], dtype=np.int64), 8, 4, 1e-13, pmax=2, max_cycles=8)
