@@ -192,6 +192,28 @@ def gaussian_clusters(m: int = 1024, n: int = 1024, ell: float = 0.3, offset: fl
     return Problem(SRC_GAUSSIAN, m, n, X=np.ascontiguousarray(X), Y=np.ascontiguousarray(Y), ell=ell)
 
 
+def hmt11_laplacian(n: int = 1024, nodes: int = 8) -> Problem:
+    """The discretised single-layer Laplacian of the bidiagonal pre-processing
+    tests (input matrices (i), replicated from [HMT11, Section 7.1]): targets
+    x_i = 2 w^i on the circle of radius 2 (w = exp(2 pi sqrt(-1) / n)), sources
+    the arcs of the unit circle between the angles 2 pi j / n and 2 pi (j+1) / n,
+    and w_ij = psi * integral over arc j of log|x_i - y| dy.  Since
+    |2 e^{i t} - e^{i f}|^2 = 5 - 4 cos(t - f), each arc integral is taken by
+    ``nodes``-point Gauss-Legendre quadrature of 0.5 log(5 - 4 cos(t - f)); the
+    entry depends on (i - j) mod n only, so W is built circulant.  psi =
+    1 / (2 pi ln 2) makes ||W|| = 1: the mean of log|x - y| over the unit circle
+    is log|x| = ln 2, the largest eigenvalue.  Dense FP64, n x n."""
+    t, wq = np.polynomial.legendre.leggauss(nodes)
+    psi = 1.0 / (2.0 * np.pi * np.log(2.0))
+    d = np.arange(n, dtype=np.float64)
+    # angle between target i and the quadrature points of arc j, for d = i - j
+    ang = 2.0 * np.pi * (d[:, None] - 0.5 * (1.0 + t[None, :])) / n
+    c = psi * (np.pi / n) * (0.5 * np.log(5.0 - 4.0 * np.cos(ang)) @ wq)
+    i = np.arange(n)
+    W = c[(i[:, None] - i[None, :]) % n]
+    return Problem(SRC_DENSE, n, n, W=np.ascontiguousarray(W), meta={"psi": psi})
+
+
 def _morton3(ix: np.ndarray, iy: np.ndarray, iz: np.ndarray, bits: int) -> np.ndarray:
     code = np.zeros(ix.shape, dtype=np.int64)
     for b in range(bits):

@@ -263,11 +263,12 @@ def cynical(p, kind, r, q, K, L, I0s, sweeps=3, h=1.01, max_swaps=1000, rank_tol
 
 def bidiag_columns(n, q, perms, signs):
     """Columns of the product of q quasi-Gaussian factors (I + D_i S) P_i:
-    (n, 2^q) rows and integer values (0 = unused slot), ascending rows."""
+    (n, min(2^q, n)) rows and integer values (0 = unused slot), ascending rows."""
     perms = np.ascontiguousarray(perms, dtype=np.int32)
     signs = np.ascontiguousarray(signs, dtype=np.int8)
-    rows = np.zeros((n, 1 << q), dtype=np.int32)
-    vals = np.zeros((n, 1 << q), dtype=np.int32)
+    w = min(1 << int(q), int(n))
+    rows = np.zeros((n, w), dtype=np.int32)
+    vals = np.zeros((n, w), dtype=np.int32)
     lib().orc_bidiag_columns(int(n), int(q), _ptr(perms), _ptr(signs), _ptr(rows), _ptr(vals))
     return rows, vals
 

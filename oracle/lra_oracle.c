@@ -65,7 +65,7 @@ typedef struct {
   const int8_t* ssign;  /* sparse: n*nnz signs (+-1)                          */
   /* bidiagonal products (mkind ORC_MULT_BIDIAG, depth = q factors; perm and
    * dsign hold q x n permutations and signs): the columns of the product,
-   * expanded by orc_bidiag_columns, 2^q slots each, ascending rows, value 0
+   * expanded by orc_bidiag_columns, min(2^q, n) slots each, ascending rows, value 0
    * marking an unused slot */
   const int32_t* brow;
   const int32_t* bval;
@@ -102,10 +102,11 @@ static double entry_w(const orc_problem* p, int64_t i, int64_t j) {
  * down-shift, D_i = diag(signs[i]), column a of P_i = e_{perms[i][a]}, so that
  * F_i e_a = e_b + signs[i][b'] e_{b'} with b = perms[i][a], b' = (b + 1) mod n.
  * Column j is M e_j = F_1 (F_2 (... (F_q e_j))): a dense work vector, then its
- * nonzeros in ascending rows into 2^q slots (integer values; 0 = unused). */
+ * nonzeros in ascending rows into min(2^q, n) slots (a column has at most that
+ * many; integer values, |value| <= 2^q; 0 = unused). */
 void orc_bidiag_columns(int64_t n, int32_t q, const int32_t* perms, const int8_t* signs, int32_t* rows,
                         int32_t* vals) {
-  int64_t w = 1LL << q;
+  int64_t w = (1LL << q) < n ? (1LL << q) : n;
   int64_t* v = (int64_t*)calloc((size_t)n, sizeof(int64_t));
   int64_t* u = (int64_t*)calloc((size_t)n, sizeof(int64_t));
   for (int64_t j = 0; j < n; ++j) {
@@ -160,7 +161,7 @@ static double entry_wp(const orc_problem* p, int64_t i, int64_t j) {
   }
   if (p->mkind == ORC_MULT_BIDIAG) {
     /* nonzero slots in ascending row order, each an fma with its integer weight */
-    int64_t w = 1LL << p->depth;
+    int64_t w = (1LL << p->depth) < p->n ? (1LL << p->depth) : p->n;
     double acc = 0.0;
     for (int64_t t = 0; t < w; ++t) {
       int32_t v = p->bval[j * w + t];

@@ -328,6 +328,74 @@ def test_bidiag_product_structure():
     assert abs(np.mean((M ** 2).sum(0)) / 2 ** q - 1.0) < 0.05
 
 
+def test_bidiag_twenty_factors_dense_columns():
+    """The paper's 20-factor products (n = 48 < 2^20): every column fills at
+    most n slots; the slot list equals the left-to-right dense product exactly
+    (integers), and the gathered strip W M agrees with numpy's product."""
+    n, q = 48, 20
+    g = np.random.default_rng(3)
+    W = g.standard_normal((6, n))
+    p = li.Problem(li.SRC_DENSE, 6, n, W=W)
+    li.with_bidiag(p, q, 13)
+    rows, vals = oracle.bidiag_columns(n, q, p.perm, p.dsign)
+    assert rows.shape == (n, n)
+    M = oracle.multiplier_dense(p) * 2.0 ** (q / 2)
+    np.testing.assert_array_equal(M, np.round(M))
+    assert np.abs(M).max() <= 2.0 ** q
+    S = np.zeros((n, n))
+    for j in range(n):
+        nz = vals[j] != 0
+        assert np.all(np.diff(rows[j][nz]) > 0)
+        S[rows[j][nz], j] = vals[j][nz]
+    np.testing.assert_array_equal(S, M)
+    R = oracle.gather_rows(p, np.arange(6, dtype=np.int32))
+    ref = W @ (M * 2.0 ** (-q / 2))
+    np.testing.assert_allclose(R, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+def test_hmt11_laplacian_spectrum_closed_form():
+    """The single-layer Laplacian input (bidiagonal pre-processing tests, inputs
+    (i)) is circulant: log|2 e^{it} - e^{if}| = ln 2 - sum_m 2^-m cos(m(t-f)) / m,
+    so its singular values are psi * 2 pi ln 2 = 1 once and
+    psi * pi 2^-m / m * sinc(pi m / n) twice for m = 1, 2, ... (the sinc from
+    averaging e^{imf} over an arc), up to aliasing terms of size 2^-(n-m)."""
+    n = 256
+    p = li.hmt11_laplacian(n)
+    psi = 1.0 / (2.0 * np.pi * np.log(2.0))
+    sv = np.linalg.svd(p.W, compute_uv=False)
+    m = np.arange(1, 40)
+    lam = psi * np.pi * 2.0 ** -m / m * np.sin(np.pi * m / n) / (np.pi * m / n)
+    expected = np.sort(np.concatenate([[1.0], lam, lam]))[::-1][:40]
+    np.testing.assert_allclose(sv[:40], expected, rtol=1e-8)
+    np.testing.assert_allclose(p.W.sum(axis=1), 1.0, rtol=1e-13)
+
+
+def test_hmt11_laplacian_entries_by_adaptive_quadrature():
+    """Entries against scipy's adaptive quadrature of psi * log|2 w^i - y| over arc j."""
+    from scipy.integrate import quad
+    n = 64
+    p = li.hmt11_laplacian(n)
+    psi = 1.0 / (2.0 * np.pi * np.log(2.0))
+    for i, j in [(0, 0), (5, 9), (63, 1), (17, 40), (32, 0)]:
+        z = 2.0 * np.exp(2j * np.pi * i / n)
+        v, _ = quad(lambda f: np.log(abs(z - np.exp(1j * f))), 2 * np.pi * j / n, 2 * np.pi * (j + 1) / n,
+                    epsabs=1e-15, epsrel=1e-13)
+        assert abs(p.W[i, j] - psi * v) <= 1e-14 * max(abs(psi * v), 1e-3), (i, j)
+
+
+def test_hmt11_laplacian_ca_with_twenty_bidiagonal_factors():
+    """C-A (five loops, as in Tests 2) on the 20-factor pre-processed input: the
+    spectral error stays within a small factor of sigma_{k+1}."""
+    n = 256
+    for k, seed in [(31, 0), (39, 1), (35, 2)]:
+        p = li.hmt11_laplacian(n)
+        li.with_bidiag(p, 20, 100 + seed)
+        o = oracle.ca_run(p, k, 5, li.initial_rows(n, k, seed))
+        sv = np.linalg.svd(p.W, compute_uv=False)
+        err = np.linalg.norm(p.W - o["C"] @ o["U"] @ o["R"], 2)
+        assert sv[k] <= err <= 10 * sv[k], (k, err, sv[k])
+
+
 def test_float32_input_is_widened_exactly():
     W = np.random.default_rng(0).standard_normal((10, 12)).astype(np.float32)
     p = li.Problem(li.SRC_DENSE, 10, 12, W=W)
