@@ -342,6 +342,119 @@ class DenseWorkload:
         return n, n, el, f"{n} complete LRAs of the same input (C-A + nucleus + residual sample)"
 
 
+class Hmt11Workload:
+    """The single-layer Laplacian inputs of the bidiagonal pre-processing tests
+    (inputs (i), [HMT11, Section 7.1]): n x n dense FP64, pre-processed by the
+    product of q = 20 random bidiagonal factors, C-A with five loops (Tests 2).
+    One step = ``runs`` independent LRAs (each its own multiplier draw and
+    initial rows, as the paper's mean/std over trials) plus the exact Frobenius
+    error of each (the residual over all n^2 entries)."""
+    kernel = "ca_kernel"
+    unit = "LRA/s"
+
+    def __init__(self, n=1024, k=39, q=20, runs=10, sweeps=5):
+        self.n, self.k, self.q, self.runs, self.sweeps = n, k, q, runs, sweeps
+        self.name = f"hmt11_laplacian{n}_bidiag{q}_k{k}_s{sweeps}_x{runs}"
+
+    def host(self, rank):
+        p = li.hmt11_laplacian(self.n)
+        mults = []
+        for r in range(self.runs):
+            pr = li.Problem(li.SRC_DENSE, self.n, self.n, W=p.W)
+            li.with_bidiag(pr, self.q, 100 + 1000 * rank + r)
+            mults.append((pr.perm, pr.dsign))
+        I0 = [li.initial_rows(self.n, self.k, 7 + 1000 * rank + r) for r in range(self.runs)]
+        # nonzeros of each multiplier column (integer arithmetic on the factors) for the flop count
+        nnz = []
+        for perm, sg in mults:
+            M = np.eye(self.n, dtype=np.int64)
+            for f in range(self.q):
+                b = perm[f].astype(np.int64)
+                b1 = (b + 1) % self.n
+                M = M[:, b] + M[:, b1] * sg[f][b1].astype(np.int64)[None, :]
+            nnz.append(float((M != 0).sum(axis=0).mean()))
+        return dict(p=p, mults=mults, I0=I0, nnz=float(np.mean(nnz)))
+
+    def config(self, h):
+        return {"workload": self.name, "m": self.n, "n": self.n, "k": self.k, "sweeps": self.sweeps,
+                "multiplier": f"product of {self.q} cyclic bidiagonal +-1 factors (every column dense)",
+                "runs_per_step": self.runs, "input_dtype": "f64",
+                "residual_sample": f"all {self.n}x{self.n} entries (exact Frobenius ratio)"}
+
+    def device(self, h, dev):
+        import torch
+        import paper_1710_07946_gb300 as lra
+        W = torch.from_numpy(h["p"].W).to(dev)
+        prob = lra.Problem.dense(W)
+        mults = [lra.lra_precondition("bidiag", self.n, self.q, perm, sg) for perm, sg in h["mults"]]
+        I0 = [torch.from_numpy(x).to(dev) for x in h["I0"]]
+        outs = [lra.lra_ca_run(prob, I0[r], self.k, self.sweeps, multiplier=mults[r]) for r in range(self.runs)]
+        QS = torch.arange(self.n, dtype=torch.int32, device=dev)
+        return dict(W=W, prob=prob, mults=mults, I0=I0, outs=outs, Q=QS, S=QS, stats=[None] * self.runs)
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        for r in range(self.runs):
+            o = d["outs"][r]
+            lra.lra_ca_run(d["prob"], d["I0"][r], self.k, self.sweeps, multiplier=d["mults"][r], out=o,
+                           workspace=o["_workspace"])
+            d["stats"][r] = lra.lra_residual_sample(d["prob"], o["C"], o["U"], o["R"], d["Q"], d["S"])
+
+    def check(self, d):
+        info = np.stack([o["info"].cpu().numpy() for o in d["outs"]])
+        err = np.array([float(st[4].item()) for st in d["stats"]])
+        return dict(units=int((err <= ERR_BOUND).sum()), info=info, err=err)
+
+    def flops(self, h, res):
+        f = [ca_flops(self.k, self.n, self.n, int(inf[2]), int(inf[1]), 2.0 * h["nnz"], nucleus=False)
+             for inf in res["info"]]
+        return float(np.mean(f))
+
+    def extra(self, res):
+        return {"rel_fro_err_mean": float(np.mean(res["err"])), "rel_fro_err_std": float(np.std(res["err"])),
+                "rel_fro_err_max": float(np.max(res["err"])), "swaps_mean": float(np.mean(res["info"][:, 1])),
+                "statuses": sorted(set(int(x) for x in res["info"][:, 3])),
+                "flops_note": "entry cost = 2 x mean nonzeros per multiplier column (fma per term)"}
+
+    def e2e_setup(self, h, d):
+        import torch
+        hp = dict(W=torch.from_numpy(h["p"].W).pin_memory())
+        hp["out"] = [{key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in o.items()
+                      if not key.startswith("_")} for o in d["outs"]]
+        hp["stats"] = torch.empty(self.runs, 5, dtype=torch.float64).pin_memory()
+        h2d = hp["W"].numel() * 8
+        d2h = sum(v.numel() * v.element_size() for o in hp["out"] for v in o.values()) + 40 * self.runs
+        return hp, h2d, d2h
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["W"].copy_(hp["W"], non_blocking=True)
+        self.step(d)
+        for r in range(self.runs):
+            for key, v in hp["out"][r].items():
+                v.copy_(d["outs"][r][key], non_blocking=True)
+            hp["stats"][r].copy_(d["stats"][r], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        t0 = time.perf_counter()
+        n = good = 0
+        QS = np.arange(self.n, dtype=np.int32)
+        for r in range(self.runs):
+            pr = li.Problem(li.SRC_DENSE, self.n, self.n, W=h["p"].W)
+            perm, sg = h["mults"][r]
+            pr.mkind, pr.depth, pr.perm, pr.dsign = li.MULT_BIDIAG, self.q, perm, sg
+            o = oracle.ca_run(pr, self.k, self.sweeps, h["I0"][r])
+            st = oracle.residual_sample(h["p"], o["C"], o["U"], o["R"], QS, QS)
+            n += 1
+            good += st[4] <= ERR_BOUND
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        el = time.perf_counter() - t0
+        return good, n, el, f"{n} complete LRAs (C-A + nucleus + exact residual) of the step's {self.runs}"
+
+
 class LaplaceSingleWorkload:
     """One C-A CUR of the 65536 x 65536 Laplace kernel between two unit cubes whose
     centres are 3 apart, entries evaluated on the fly (FP64 or FP32), rank k,
@@ -765,6 +878,8 @@ WORKLOADS = {
     "fmm_oversample8": lambda: FmmOversampleWorkload(8),
     "fmm_oversample8_cycles4": lambda: FmmOversampleWorkload(8, pmax=4),
     "fmm_small": FmmSmallWorkload,
+    "hmt11_n1024_k39_bidiag20": Hmt11Workload,
+    "hmt11_n256_k31_bidiag20": lambda: Hmt11Workload(n=256, k=31),
     **{f"laplace65536_k{k}{sfx}": (lambda k=k, e=e: LaplaceSingleWorkload(k, e))
        for k in (16, 32, 64) for sfx, e in (("", "f64"), ("_f32", "f32"))},
     "gauss_apply": GaussApplyWorkload,

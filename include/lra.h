@@ -98,12 +98,15 @@ typedef struct lra_multiplier_s* lra_multiplier;   /* opaque, library-owned */
  *     strictly ascending in t (host arrays of n*nnz int32 / int8).
  *   kind = LRA_MULT_BIDIAG (Section "Approximation of a Gaussian matrix by the
  *     product of random bidiagonal matrices", eq. def11): M = 2^{-q/2} F_1 ...
- *     F_q, q = depth_or_nnz (1..6), F_i = (I + D_i S) P_i with S the cyclic
+ *     F_q, q = depth_or_nnz (1..30), F_i = (I + D_i S) P_i with S the cyclic
  *     down-shift, D_i = diag(signs[i*n .. i*n+n)) (+-1) and column a of P_i equal
  *     to e_b, b = perm_or_rows[i*n + a] (host arrays of q*n int32 / int8, each
  *     row of perm_or_rows a permutation of 0..n-1).  Column j of M has at most
- *     2^q nonzeros, integer multiples of 2^{-q/2}; w'_ij adds them in ascending
- *     rows, each as fma(value, w, sum), and scales once.  n >= 2.
+ *     min(2^q, n) nonzeros, integer multiples of 2^{-q/2} (|integer| <= 2^q);
+ *     w'_ij adds them in ascending rows, each as fma(value, w, sum), and scales
+ *     once.  The handle holds n * min(2^q, n) (row, int32 weight) slots, built on
+ *     the host in O(n q min(2^q, n)) time; small q keeps the gathers superfast,
+ *     and the paper's 20-factor products make every column dense.  2 <= n < 2^31.
  * The random draws (signs, permutation, positions) are inputs, so that runs are
  * reproducible.  The descriptor is copied to device memory owned by the handle;
  * the host arrays may be freed on return.  The copy is synchronous.

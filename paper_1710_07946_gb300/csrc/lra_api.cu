@@ -46,7 +46,8 @@ lra_status make_dev_problem(const lra_problem* p, lra_multiplier mult, DevProble
       d.s = p->n >> mult->param;
     } else if (mult->kind == LRA_MULT_BIDIAG) {
       d.depth = mult->param;
-      d.nnz = 1 << mult->param;
+      d.nnz = mult->width;
+      d.bval = mult->d_val;
     } else {
       d.nnz = mult->param;
     }
@@ -85,54 +86,71 @@ lra_status current_device_info(DeviceInfo* info) {
 }
 
 // The columns of M = F_1 ... F_q (F_f = (I + D_f S) P_f): column j is
-// F_1 (... (F_q e_j)), kept as a short list of (row, integer value) terms that
-// is expanded factor by factor (each term a -> b = perm_f[a] with its value and
-// b' = (b + 1) mod n with sign_f[b'] times it), merged by row after every
-// factor.  Stored with 2^q slots per column in ascending rows, value 0 in the
-// unused slots; the scale 2^{-q/2} is applied by the gathers.
+// F_1 (... (F_q e_j)), a list of (row, integer value) terms expanded factor by
+// factor (each term a -> b = perm_f[a] with its value and b' = (b + 1) mod n
+// with sign_f[b'] times it) and merged by row in a dense accumulator after
+// every factor.  A column has at most min(2^q, n) nonzeros; they are stored in
+// that many slots per column in ascending rows, value 0 in the unused slots.
+// |values| <= 2^q (int32 for q <= 30); the scale 2^{-q/2} is applied by the
+// gathers.
 static lra_status make_bidiag(lra_multiplier* out, int64_t n, int32_t q, const int32_t* perms,
                               const int8_t* signs) {
-  const size_t w = (size_t)1 << q;
-  std::vector<int32_t> rows((size_t)n * w, 0);
-  std::vector<int8_t> vals((size_t)n * w, 0);
-  std::vector<std::pair<int64_t, int64_t>> cur, nxt;
+  const int64_t w = std::min<int64_t>(int64_t(1) << q, n);
+  std::vector<int32_t> rows((size_t)n * (size_t)w, 0);
+  std::vector<int32_t> vals((size_t)n * (size_t)w, 0);
+  std::vector<int64_t> acc((size_t)n, 0);
+  std::vector<unsigned char> touched((size_t)n, 0);
+  std::vector<int64_t> cur, nxt;       // rows with a nonzero value
   for (int64_t j = 0; j < n; ++j) {
-    cur.assign(1, {j, 1});
+    cur.assign(1, j);
+    acc[(size_t)j] = 1;
     for (int f = q - 1; f >= 0; --f) {
-      nxt.clear();
-      for (const auto& tv : cur) {
-        const int64_t b = perms[(int64_t)f * n + tv.first], b1 = (b + 1) % n;
-        nxt.push_back({b, tv.second});
-        nxt.push_back({b1, (int64_t)signs[(int64_t)f * n + b1] * tv.second});
+      std::vector<std::pair<int64_t, int64_t>> terms;
+      terms.reserve(cur.size());
+      for (int64_t a : cur) {
+        terms.push_back({a, acc[(size_t)a]});
+        acc[(size_t)a] = 0;
       }
-      std::sort(nxt.begin(), nxt.end());
+      nxt.clear();
+      for (const auto& tv : terms) {
+        const int64_t b = perms[(int64_t)f * n + tv.first], b1 = (b + 1) % n;
+        const int64_t add[2] = {tv.second, (int64_t)signs[(int64_t)f * n + b1] * tv.second};
+        const int64_t at[2] = {b, b1};
+        for (int e = 0; e < 2; ++e) {
+          if (!touched[(size_t)at[e]]) { touched[(size_t)at[e]] = 1; nxt.push_back(at[e]); }
+          acc[(size_t)at[e]] += add[e];
+        }
+      }
       cur.clear();
-      for (const auto& tv : nxt) {
-        if (!cur.empty() && cur.back().first == tv.first) cur.back().second += tv.second;
-        else cur.push_back(tv);
+      for (int64_t r : nxt) {
+        touched[(size_t)r] = 0;
+        if (acc[(size_t)r] != 0) cur.push_back(r);
       }
     }
+    std::sort(cur.begin(), cur.end());
     size_t c = 0;
-    for (const auto& tv : cur)
-      if (tv.second != 0) {
-        rows[(size_t)j * w + c] = (int32_t)tv.first;
-        vals[(size_t)j * w + c] = (int8_t)tv.second;
-        ++c;
-      }
+    for (int64_t r : cur) {
+      rows[(size_t)j * w + c] = (int32_t)r;
+      vals[(size_t)j * w + c] = (int32_t)acc[(size_t)r];
+      acc[(size_t)r] = 0;
+      ++c;
+    }
   }
   lra_multiplier m = new lra_multiplier_s;
   m->kind = LRA_MULT_BIDIAG;
   m->n = n;
   m->param = q;
+  m->width = (int32_t)w;
   m->scale = 1.0 / std::sqrt((double)(int64_t(1) << q));
   m->d_idx = nullptr;
   m->d_sign = nullptr;
+  m->d_val = nullptr;
   if (cudaMalloc(&m->d_idx, rows.size() * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&m->d_sign, vals.size() * sizeof(int8_t)) != cudaSuccess ||
+      cudaMalloc(&m->d_val, vals.size() * sizeof(int32_t)) != cudaSuccess ||
       cudaMemcpy(m->d_idx, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(m->d_sign, vals.data(), vals.size() * sizeof(int8_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaMemcpy(m->d_val, vals.data(), vals.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(m->d_idx);
-    cudaFree(m->d_sign);
+    cudaFree(m->d_val);
     delete m;
     return LRA_ERR_CUDA;
   }
@@ -174,7 +192,7 @@ lra_status lra_precondition(lra_multiplier* out, int32_t kind, int64_t n, int32_
       }
     scale = 1.0 / std::sqrt((double)param);
   } else if (kind == LRA_MULT_BIDIAG) {
-    if (param < 1 || param > 6 || n < 2) return LRA_ERR_INVALID_ARG;
+    if (param < 1 || param > 30 || n < 2 || n > INT32_MAX) return LRA_ERR_INVALID_ARG;
     std::vector<unsigned char> seen((size_t)n);
     for (int f = 0; f < param; ++f) {
       std::fill(seen.begin(), seen.end(), 0);
@@ -195,8 +213,10 @@ lra_status lra_precondition(lra_multiplier* out, int32_t kind, int64_t n, int32_
   m->n = n;
   m->param = param;
   m->scale = scale;
+  m->width = 0;
   m->d_idx = nullptr;
   m->d_sign = nullptr;
+  m->d_val = nullptr;
   if (cudaMalloc(&m->d_idx, cnt * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&m->d_sign, cnt * sizeof(int8_t)) != cudaSuccess ||
       cudaMemcpy(m->d_idx, idx, cnt * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -214,8 +234,9 @@ lra_status lra_multiplier_destroy(lra_multiplier m) {
   if (m == nullptr) return LRA_OK;
   cudaError_t e1 = cudaFree(m->d_idx);
   cudaError_t e2 = cudaFree(m->d_sign);
+  cudaError_t e3 = cudaFree(m->d_val);
   delete m;
-  return (e1 == cudaSuccess && e2 == cudaSuccess) ? LRA_OK : LRA_ERR_CUDA;
+  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess) ? LRA_OK : LRA_ERR_CUDA;
 }
 
 const char* lra_version(void) { return "lra-gb300 0.1 (sm_103a)"; }

@@ -41,6 +41,7 @@ struct DevProblem {
   int64_t s;                 // ARHT block size n / 2^d
   const int32_t* perm;       // ARHT permutation, or sparse rows (n*nnz)
   const int8_t* sign;        // ARHT diagonal, or sparse signs (n*nnz)
+  const int32_t* bval;       // bidiagonal products: integer weights (n*nnz, nnz = min(2^q, n) slots)
   double mscale;             // 2^{-d/2} or 1/sqrt(nnz), computed on the host
   // FP32 copies for the mixed-precision steps
   const float* X32;          // kernel points rounded to FP32 (m x 3), or null
@@ -79,10 +80,10 @@ __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64
   if (P.mkind == LRA_MULT_NONE) return w_entry(P, i, j);
   double acc = 0.0;
   if (P.mkind == LRA_MULT_BIDIAG) {
-    // product of bidiagonal factors: up to 2^q integer-weighted terms in
-    // ascending rows (value 0 = unused slot), each fma(value, w, sum)
+    // product of bidiagonal factors: up to min(2^q, n) integer-weighted terms
+    // in ascending rows (value 0 = unused slot), each fma(value, w, sum)
     const int32_t* rows = P.perm + j * P.nnz;
-    const int8_t* vs = P.sign + j * P.nnz;
+    const int32_t* vs = P.bval + j * P.nnz;
     for (int t0 = 0; t0 < P.nnz; t0 += TERMS) {
       double v[TERMS];
       int c[TERMS];

@@ -13,10 +13,12 @@
 struct lra_multiplier_s {
   int32_t kind;
   int64_t n;
-  int32_t param;        // depth d (ARHT) or nnz (sparse)
-  int32_t* d_idx;       // ARHT perm (n) or sparse rows (n*nnz)
+  int32_t param;        // depth d (ARHT), nnz (sparse) or the number of factors q (bidiagonal)
+  int32_t width;        // bidiagonal: slots per column, min(2^q, n)
+  int32_t* d_idx;       // ARHT perm (n), sparse rows (n*nnz) or bidiagonal rows (n*width)
   int8_t* d_sign;       // ARHT diagonal (n) or sparse signs (n*nnz)
-  double scale;         // 2^{-d/2} or 1/sqrt(nnz)
+  int32_t* d_val;       // bidiagonal integer weights (n*width)
+  double scale;         // 2^{-d/2}, 1/sqrt(nnz) or 2^{-q/2}
 };
 
 namespace lra {

@@ -63,6 +63,27 @@ def test_float32_with_multipliers(mult, arg):
     assert_parity(o, g)
 
 
+@pytest.mark.parametrize("n,k,q", [(256, 31, 20), (1024, 39, 20), (512, 35, 12)])
+def test_hmt11_laplacian_bidiagonal(n, k, q):
+    """The single-layer Laplacian input with q bidiagonal factors (every column of
+    the product dense at q = 20), five C-A loops as in Tests 2."""
+    p = li.hmt11_laplacian(n)
+    li.with_bidiag(p, q, 100 + k)
+    I0 = li.initial_rows(n, k, k)
+    o, g = run_both(p, k, 5, I0)
+    assert_parity(o, g)
+
+
+def test_hmt11_laplacian_arht():
+    """The same input under the abridged Hadamard multiplier, k = 15 (the ARHT/ARFT
+    table's rank)."""
+    p = li.hmt11_laplacian(512)
+    li.with_arht(p, 3, 21)
+    I0 = li.initial_rows(512, 15, 4)
+    o, g = run_both(p, 15, 5, I0)
+    assert_parity(o, g)
+
+
 @pytest.mark.parametrize("k", [8, 32])
 def test_laplace_kernel_entries(k):
     p = li.laplace_clusters(3000, 2500, seed=2)
