@@ -348,13 +348,19 @@ class Hmt11Workload:
     product of q = 20 random bidiagonal factors, C-A with five loops (Tests 2).
     One step = ``runs`` independent LRAs (each its own multiplier draw and
     initial rows, as the paper's mean/std over trials) plus the exact Frobenius
-    error of each (the residual over all n^2 entries)."""
-    kernel = "ca_kernel"
+    error of each (the residual over all n^2 entries).
+
+    ``materialize`` (default): the paper's order of work -- every W'_r = W M_r
+    is written out (lra_multiplier_apply, bit-identical entries), the runs go
+    as blocks of one batched C-A launch over the stacked W'_r, and R_r = W[I_r, :]
+    is gathered from W (lra_gather_rows).  Otherwise each run is one lra_ca_run
+    on (W, M_r) forming the entries of W' inside the strips."""
     unit = "LRA/s"
 
-    def __init__(self, n=1024, k=39, q=20, runs=10, sweeps=5):
-        self.n, self.k, self.q, self.runs, self.sweeps = n, k, q, runs, sweeps
-        self.name = f"hmt11_laplacian{n}_bidiag{q}_k{k}_s{sweeps}_x{runs}"
+    def __init__(self, n=1024, k=39, q=20, runs=10, sweeps=5, materialize=True):
+        self.n, self.k, self.q, self.runs, self.sweeps, self.mat = n, k, q, runs, sweeps, materialize
+        self.name = f"hmt11_laplacian{n}_bidiag{q}_k{k}_s{sweeps}_x{runs}" + ("" if materialize else "_onthefly")
+        self.kernel = "multiplier_apply_kernel" if materialize else "ca_kernel"
 
     def host(self, rank):
         p = li.hmt11_laplacian(self.n)
@@ -379,33 +385,66 @@ class Hmt11Workload:
         return {"workload": self.name, "m": self.n, "n": self.n, "k": self.k, "sweeps": self.sweeps,
                 "multiplier": f"product of {self.q} cyclic bidiagonal +-1 factors (every column dense)",
                 "runs_per_step": self.runs, "input_dtype": "f64",
+                "form": ("W' = W M written out, runs batched (one CTA each), R from W" if self.mat
+                         else "entries of W' formed inside the C-A strips, one run at a time"),
                 "residual_sample": f"all {self.n}x{self.n} entries (exact Frobenius ratio)"}
 
     def device(self, h, dev):
         import torch
         import paper_1710_07946_gb300 as lra
+        n, k = self.n, self.k
         W = torch.from_numpy(h["p"].W).to(dev)
         prob = lra.Problem.dense(W)
-        mults = [lra.lra_precondition("bidiag", self.n, self.q, perm, sg) for perm, sg in h["mults"]]
-        I0 = [torch.from_numpy(x).to(dev) for x in h["I0"]]
-        outs = [lra.lra_ca_run(prob, I0[r], self.k, self.sweeps, multiplier=mults[r]) for r in range(self.runs)]
-        QS = torch.arange(self.n, dtype=torch.int32, device=dev)
-        return dict(W=W, prob=prob, mults=mults, I0=I0, outs=outs, Q=QS, S=QS, stats=[None] * self.runs)
+        mults = [lra.lra_precondition("bidiag", n, self.q, perm, sg) for perm, sg in h["mults"]]
+        QS = torch.arange(n, dtype=torch.int32, device=dev)
+        d = dict(W=W, prob=prob, mults=mults, Q=QS, S=QS, stats=[None] * self.runs)
+        if self.mat:
+            Wp = torch.empty(self.runs * n, n, dtype=torch.float64, device=dev)
+            blocks = np.array([[r * n, n, 0, n] for r in range(self.runs)], dtype=np.int64)
+            bt = lra.Batch(lra.Problem.dense(Wp), blocks, k, self.sweeps, np.stack(h["I0"]), rank_tol=1e-13,
+                           order=None)
+            views = []
+            for r in range(self.runs):
+                oc, orr = (int(x) for x in bt.offs_np[r])
+                views.append(dict(C=bt.out["C"][oc:oc + n * k].view(n, k), U=bt.out["U"][r],
+                                  R=bt.out["R"][orr:orr + k * n].view(k, n), I=bt.out["I"][r]))
+            d.update(Wp=Wp, bt=bt, views=views)
+        else:
+            I0 = [torch.from_numpy(x).to(dev) for x in h["I0"]]
+            outs = [lra.lra_ca_run(prob, I0[r], k, self.sweeps, multiplier=mults[r]) for r in range(self.runs)]
+            d.update(I0=I0, outs=outs)
+        return d
 
     def step(self, d):
         import paper_1710_07946_gb300 as lra
+        n = self.n
+        if self.mat:
+            for r in range(self.runs):
+                lra.lra_multiplier_apply(d["prob"], d["mults"][r], d["Wp"][r * n:(r + 1) * n])
+            lra.lra_ca_run_batched(d["bt"])
+            for r, v in enumerate(d["views"]):
+                lra.lra_gather_rows(d["prob"], v["I"], out=v["R"])
+                d["stats"][r] = lra.lra_residual_sample(d["prob"], v["C"], v["U"], v["R"], d["Q"], d["S"])
+            return
         for r in range(self.runs):
             o = d["outs"][r]
             lra.lra_ca_run(d["prob"], d["I0"][r], self.k, self.sweeps, multiplier=d["mults"][r], out=o,
                            workspace=o["_workspace"])
             d["stats"][r] = lra.lra_residual_sample(d["prob"], o["C"], o["U"], o["R"], d["Q"], d["S"])
 
+    def _infos(self, d):
+        if self.mat:
+            return d["bt"].out["info"].cpu().numpy()
+        return np.stack([o["info"].cpu().numpy() for o in d["outs"]])
+
     def check(self, d):
-        info = np.stack([o["info"].cpu().numpy() for o in d["outs"]])
+        info = self._infos(d)
         err = np.array([float(st[4].item()) for st in d["stats"]])
         return dict(units=int((err <= ERR_BOUND).sum()), info=info, err=err)
 
     def flops(self, h, res):
+        if self.mat:      # one W' = W M per launch: n^2 entries of nnz fused multiply-adds each
+            return 2.0 * self.n * self.n * h["nnz"]
         f = [ca_flops(self.k, self.n, self.n, int(inf[2]), int(inf[1]), 2.0 * h["nnz"], nucleus=False)
              for inf in res["info"]]
         return float(np.mean(f))
@@ -414,25 +453,33 @@ class Hmt11Workload:
         return {"rel_fro_err_mean": float(np.mean(res["err"])), "rel_fro_err_std": float(np.std(res["err"])),
                 "rel_fro_err_max": float(np.max(res["err"])), "swaps_mean": float(np.mean(res["info"][:, 1])),
                 "statuses": sorted(set(int(x) for x in res["info"][:, 3])),
-                "flops_note": "entry cost = 2 x mean nonzeros per multiplier column (fma per term)"}
+                "flops_note": ("per launch of the dominant kernel: 2 x n^2 x mean nonzeros of a multiplier column"
+                               if self.mat else "entry cost = 2 x mean nonzeros per multiplier column")}
 
     def e2e_setup(self, h, d):
         import torch
         hp = dict(W=torch.from_numpy(h["p"].W).pin_memory())
-        hp["out"] = [{key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in o.items()
-                      if not key.startswith("_")} for o in d["outs"]]
+        if self.mat:
+            hp["out"] = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in d["bt"].out.items()}
+        else:
+            hp["out"] = {f"{r}_{key}": torch.empty(v.shape, dtype=v.dtype).pin_memory()
+                         for r, o in enumerate(d["outs"]) for key, v in o.items() if not key.startswith("_")}
         hp["stats"] = torch.empty(self.runs, 5, dtype=torch.float64).pin_memory()
         h2d = hp["W"].numel() * 8
-        d2h = sum(v.numel() * v.element_size() for o in hp["out"] for v in o.values()) + 40 * self.runs
+        d2h = sum(v.numel() * v.element_size() for v in hp["out"].values()) + 40 * self.runs
         return hp, h2d, d2h
 
     def e2e_step(self, hp, d):
         import torch
         d["W"].copy_(hp["W"], non_blocking=True)
         self.step(d)
+        for key, v in hp["out"].items():
+            if self.mat:
+                v.copy_(d["bt"].out[key], non_blocking=True)
+            else:
+                r, name = key.split("_", 1)
+                v.copy_(d["outs"][int(r)][name], non_blocking=True)
         for r in range(self.runs):
-            for key, v in hp["out"][r].items():
-                v.copy_(d["outs"][r][key], non_blocking=True)
             hp["stats"][r].copy_(d["stats"][r], non_blocking=True)
         torch.cuda.current_stream().synchronize()
 
@@ -879,6 +926,7 @@ WORKLOADS = {
     "fmm_oversample8_cycles4": lambda: FmmOversampleWorkload(8, pmax=4),
     "fmm_small": FmmSmallWorkload,
     "hmt11_n1024_k39_bidiag20": Hmt11Workload,
+    "hmt11_n1024_k39_bidiag20_onthefly": lambda: Hmt11Workload(materialize=False),
     "hmt11_n256_k31_bidiag20": lambda: Hmt11Workload(n=256, k=31),
     **{f"laplace65536_k{k}{sfx}": (lambda k=k, e=e: LaplaceSingleWorkload(k, e))
        for k in (16, 32, 64) for sfx, e in (("", "f64"), ("_f32", "f32"))},

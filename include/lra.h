@@ -119,6 +119,37 @@ lra_status lra_precondition(lra_multiplier* out, int32_t kind, int64_t n, int32_
 /* Free a multiplier handle (NULL is accepted). */
 lra_status lra_multiplier_destroy(lra_multiplier mult);
 
+/*
+ * lra_multiplier_apply -- the pre-processed input W' = W M written out as a
+ * dense FP64 matrix (paper: the bidiagonal pre-processing tests multiply each
+ * input by the factors before C-A; the CUR of W from generators of W' is
+ * C = W'[:, J], U = pinv(W'[I, J]), R = W[I, :], as for lra_ca_run with a
+ * multiplier).  Entry (i, j) is formed exactly as the C-A gathers form w'_ij
+ * (same terms, same order, same rounding), so a C-A run on the dense W' with no
+ * multiplier selects the same I and J and returns the same C and U as a run on
+ * (W, M); its R is W'[I, :], and lra_gather_rows gives R = W[I, :].
+ * prob: W (dense F64/F32, or kernel entries), m x n.  mult: a handle for n
+ * columns, or NULL (W' = W).  Wp: caller-owned device buffer, m x n row-major,
+ * leading dimension ldwp >= n.  Cost: m n times the nonzeros of a column of M
+ * fused multiply-adds (n for the 20-factor bidiagonal products).  Entries of W
+ * must be finite.  Asynchronous on the stream.
+ * Errors: LRA_ERR_INVALID_ARG (bad problem, sizes, n of the handle), LRA_ERR_CUDA.
+ */
+lra_status lra_multiplier_apply(const lra_problem* prob, lra_multiplier mult, double* Wp, int64_t ldwp,
+                                lra_stream_t stream);
+
+/*
+ * lra_gather_rows -- R = W[I, :] (k x n FP64, row-major, caller-owned device
+ * buffer) read from the original input (paper: the row factor of the CUR LRA,
+ * Section "CUR LRA"; for a pre-processed input it is taken from W, not W').
+ * I: k device int32 row indices.  A row index outside [0, m) fills its row of R
+ * with NaN and sets *status_dev (device int32, may be NULL; the caller zeroes it)
+ * to LRA_ERR_INVALID_ARG.  Asynchronous on the stream.
+ * Errors: LRA_ERR_INVALID_ARG (bad problem, k < 1, NULL buffers), LRA_ERR_CUDA.
+ */
+lra_status lra_gather_rows(const lra_problem* prob, const int32_t* I, int32_t k, double* R, int32_t* status_dev,
+                           lra_stream_t stream);
+
 /* ------------------------------------------------------------------------- */
 /* Cross-approximation                                                        */
 /* ------------------------------------------------------------------------- */

@@ -116,6 +116,8 @@ def _load():
                                            ct.POINTER(i32), ct.POINTER(i32), vp]
     L.lra_oversample_batched_workspace_size.argtypes = [P, PB, PP, i32, ct.POINTER(sz)]
     L.lra_oversample_batched.argtypes = [P, PB, PP, i32, PCB, PCB, vp, sz, vp]
+    L.lra_multiplier_apply.argtypes = [P, vp, vp, i64, vp]
+    L.lra_gather_rows.argtypes = [P, vp, i32, vp, vp, vp]
     L.lra_oversample_cycle_batched_workspace_size.argtypes = [P, PB, PP, i32, i32, ct.POINTER(sz)]
     L.lra_oversample_cycle_batched.argtypes = [P, PB, PP, i32, i32, PCB, PCB, vp, sz, vp]
     L.lra_residual_sample_batched_rect.argtypes = [P, PB, i32, i32, PCB, vp, i32, vp, i32, vp, vp]
@@ -135,7 +137,8 @@ def _load():
               "lra_ca_batched_workspace_size", "lra_ca_run_batched", "lra_residual_sample_batched",
               "lra_ca_batched_tune", "lra_cynical_batched_workspace_size", "lra_cynical_run_batched",
               "lra_cynical_batched_tune", "lra_oversample_batched_workspace_size", "lra_oversample_batched",
-              "lra_oversample_cycle_batched_workspace_size", "lra_oversample_cycle_batched",
+              "lra_oversample_cycle_batched_workspace_size", "lra_oversample_cycle_batched", "lra_multiplier_apply",
+              "lra_gather_rows",
               "lra_residual_sample_batched_rect",
               "lra_gauss_cur_forward", "lra_gauss_cur_backward"):
         getattr(L, f).restype = ct.c_int
@@ -254,6 +257,44 @@ def lra_multiplier_destroy(mult: Multiplier) -> None:
     if mult is not None and mult.handle:
         _check(_load().lra_multiplier_destroy(mult.handle), "lra_multiplier_destroy")
         mult.handle = None
+
+
+def lra_multiplier_apply(problem: Problem, multiplier: Optional[Multiplier], out: Optional[torch.Tensor] = None,
+                         stream=None) -> torch.Tensor:
+    """W' = W M written out as a dense m x n FP64 tensor; every entry is the value
+    the C-A gathers form on the fly, so a C-A run on Problem.dense(W') picks the
+    pivots of a run on (W, M).  ``out`` (m x n float64, unit column stride) is
+    written in place when given."""
+    dev = (problem.W if problem.W is not None else problem.X).device
+    if out is None:
+        out = torch.empty(problem.m, problem.n, dtype=torch.float64, device=dev)
+    if out.dim() != 2 or tuple(out.shape) != (problem.m, problem.n) or out.dtype != torch.float64 or \
+            out.stride(1) != 1:
+        raise ValueError("out must be an m x n float64 tensor with unit column stride")
+    _dev(out, torch.float64, "out")
+    pc = problem._c()
+    _check(_load().lra_multiplier_apply(ct.byref(pc), multiplier.handle if multiplier is not None else None,
+                                        out.data_ptr(), out.stride(0), _stream(stream)), "lra_multiplier_apply")
+    return out
+
+
+def lra_gather_rows(problem: Problem, I: torch.Tensor, out: Optional[torch.Tensor] = None,
+                    status: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """R = W[I, :] (k x n FP64) from the original input: the row factor of the
+    CUR of W when the generators came from a materialised W' = W M.  ``out``:
+    k x n float64 (contiguous) or None; ``status``: a device int32 scalar that a
+    row index outside [0, m) sets to LRA_ERR_INVALID_ARG."""
+    _dev(I, torch.int32, "I")
+    k = I.numel()
+    if out is None:
+        out = torch.empty(k, problem.n, dtype=torch.float64, device=I.device)
+    if out.numel() != k * problem.n or out.dtype != torch.float64 or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 tensor of k x n entries")
+    pc = problem._c()
+    _check(_load().lra_gather_rows(ct.byref(pc), I.data_ptr(), k, out.data_ptr(),
+                                   status.data_ptr() if status is not None else None, _stream(stream)),
+           "lra_gather_rows")
+    return out
 
 
 def _params(k, sweeps, h, rank_tol, max_swaps, mode, stages=None, rank_margin=0) -> _Params:

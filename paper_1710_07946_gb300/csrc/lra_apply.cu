@@ -124,11 +124,17 @@ __device__ double block_max(double v, double* red) {
   return r;
 }
 
-__global__ void __launch_bounds__(NT) resid_stats_kernel(const double* __restrict__ E, const double* __restrict__ W2,
-                                                         int64_t K, double* __restrict__ stats) {
+// Sample statistics over K = q s errors in three grid passes: per-CTA partial
+// sums (sum e, sum |e|, max |e|, sum e^2, sum w^2), then each CTA folds the
+// partial sums into the mean and adds its share of sum (e - mean)^2, then one
+// CTA folds the partials in CTA order into the five statistics.
+constexpr int RESID_MAX_PARTS = 1024;
+
+__global__ void __launch_bounds__(NT) resid_part_kernel(const double* __restrict__ E, const double* __restrict__ W2,
+                                                        int64_t K, double* __restrict__ part) {
   __shared__ double red[33];
   double s = 0.0, sa = 0.0, mx = 0.0, se2 = 0.0, sw2 = 0.0;
-  for (int64_t t = threadIdx.x; t < K; t += blockDim.x) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < K; t += (int64_t)gridDim.x * blockDim.x) {
     const double e = E[t];
     s += e;
     sa += fabs(e);
@@ -141,20 +147,45 @@ __global__ void __launch_bounds__(NT) resid_stats_kernel(const double* __restric
   mx = block_max(mx, red);
   se2 = block_sum(se2, red);
   sw2 = block_sum(sw2, red);
-  const double mean = s / (double)K;
+  if (threadIdx.x == 0) {
+    double* o = part + 6 * (size_t)blockIdx.x;
+    o[0] = s; o[1] = sa; o[2] = mx; o[3] = se2; o[4] = sw2;
+  }
+}
+
+__global__ void __launch_bounds__(NT) resid_var_kernel(const double* __restrict__ E, int64_t K,
+                                                       double* __restrict__ part) {
+  __shared__ double red[33];
+  __shared__ double s_mean;
+  const int nparts = gridDim.x;
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int b = 0; b < nparts; ++b) s += part[6 * (size_t)b];
+    s_mean = s / (double)K;
+  }
+  __syncthreads();
+  const double mean = s_mean;
   double v = 0.0;
-  for (int64_t t = threadIdx.x; t < K; t += blockDim.x) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < K; t += (int64_t)gridDim.x * blockDim.x) {
     const double d = E[t] - mean;
     v = fma(d, d, v);
   }
   v = block_sum(v, red);
-  if (threadIdx.x == 0) {
-    stats[0] = mean;
-    stats[1] = v / (double)K;
-    stats[2] = sa / (double)K;
-    stats[3] = mx;
-    stats[4] = sw2 > 0.0 ? sqrt(se2) / sqrt(sw2) : 0.0;
+  if (threadIdx.x == 0) part[6 * (size_t)blockIdx.x + 5] = v;
+}
+
+__global__ void resid_final_kernel(const double* __restrict__ part, int nparts, int64_t K, double* __restrict__ stats) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0, sa = 0.0, mx = 0.0, se2 = 0.0, sw2 = 0.0, v = 0.0;
+  for (int b = 0; b < nparts; ++b) {
+    const double* o = part + 6 * (size_t)b;
+    s += o[0]; sa += o[1]; mx = fmax(mx, o[2]); se2 += o[3]; sw2 += o[4]; v += o[5];
   }
+  stats[0] = s / (double)K;
+  stats[1] = v / (double)K;
+  stats[2] = sa / (double)K;
+  stats[3] = mx;
+  stats[4] = sw2 > 0.0 ? sqrt(se2) / sqrt(sw2) : 0.0;
 }
 
 }  // namespace lra
@@ -203,7 +234,8 @@ lra_status lra_cur_apply(const double* C, const double* U, const double* R, int6
 
 lra_status lra_residual_sample_workspace_size(int32_t k, int32_t q, int32_t s, size_t* bytes) {
   if (bytes == nullptr || k < 1 || k > KMAX || q < 1 || s < 1) return LRA_ERR_INVALID_ARG;
-  *bytes = align_up(sizeof(double) * (size_t)q * k, 256) + 2 * align_up(sizeof(double) * (size_t)q * s, 256);
+  *bytes = align_up(sizeof(double) * (size_t)q * k, 256) + 2 * align_up(sizeof(double) * (size_t)q * s, 256) +
+           align_up(sizeof(double) * 6 * RESID_MAX_PARTS, 256);
   return LRA_OK;
 }
 
@@ -224,6 +256,7 @@ lra_status lra_residual_sample(const lra_problem* prob, const double* C, const d
   double* CU = reinterpret_cast<double*>(ws);
   double* Ews = reinterpret_cast<double*>(ws + align_up(sizeof(double) * (size_t)q * k, 256));
   double* W2 = Ews + align_up(sizeof(double) * (size_t)q * s, 256) / sizeof(double);
+  double* part = W2 + align_up(sizeof(double) * (size_t)q * s, 256) / sizeof(double);
   double* Eout = E ? E : Ews;
   DeviceInfo dev;
   if ((st = current_device_info(&dev)) != LRA_OK) return st;
@@ -231,7 +264,12 @@ lra_status lra_residual_sample(const lra_problem* prob, const double* C, const d
   { LaunchScope ls(stream, "resid_cu_kernel"); resid_cu_kernel<<<g1, NT, 0, stream>>>(C, U, Q, q, k, CU); }
   const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)q * s + NT - 1) / NT, dev.sms * 8));
   { LaunchScope ls(stream, "resid_e_kernel"); resid_e_kernel<<<g2, NT, 0, stream>>>(P, CU, R, Q, S, q, s, k, Eout, W2); }
-  { LaunchScope ls(stream, "resid_stats_kernel"); resid_stats_kernel<<<1, NT, 0, stream>>>(Eout, W2, (int64_t)q * s, stats); }
+  const int64_t K = (int64_t)q * s;
+  const int g3 = (int)std::max<int64_t>(1, std::min<int64_t>((K + 4 * NT - 1) / (4 * NT),
+                                                             std::min<int64_t>(RESID_MAX_PARTS, dev.sms * 4)));
+  { LaunchScope ls(stream, "resid_part_kernel"); resid_part_kernel<<<g3, NT, 0, stream>>>(Eout, W2, K, part); }
+  { LaunchScope ls(stream, "resid_var_kernel"); resid_var_kernel<<<g3, NT, 0, stream>>>(Eout, K, part); }
+  { LaunchScope ls(stream, "resid_final_kernel"); resid_final_kernel<<<1, 32, 0, stream>>>(part, g3, K, stats); }
   return cuda_status(cudaGetLastError());
 }
 
