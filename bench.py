@@ -360,7 +360,7 @@ class Hmt11Workload:
     def __init__(self, n=1024, k=39, q=20, runs=10, sweeps=5, materialize=True):
         self.n, self.k, self.q, self.runs, self.sweeps, self.mat = n, k, q, runs, sweeps, materialize
         self.name = f"hmt11_laplacian{n}_bidiag{q}_k{k}_s{sweeps}_x{runs}" + ("" if materialize else "_onthefly")
-        self.kernel = "multiplier_apply_kernel" if materialize else "ca_kernel"
+        self.kernel = "apply_dense_kernel" if materialize else "ca_kernel"
 
     def host(self, rank):
         p = li.hmt11_laplacian(self.n)

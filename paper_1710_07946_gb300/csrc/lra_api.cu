@@ -145,12 +145,27 @@ static lra_status make_bidiag(lra_multiplier* out, int64_t n, int32_t q, const i
   m->d_idx = nullptr;
   m->d_sign = nullptr;
   m->d_val = nullptr;
-  if (cudaMalloc(&m->d_idx, rows.size() * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&m->d_val, vals.size() * sizeof(int32_t)) != cudaSuccess ||
-      cudaMemcpy(m->d_idx, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(m->d_val, vals.data(), vals.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+  m->d_dense = nullptr;
+  bool ok = cudaMalloc(&m->d_idx, rows.size() * sizeof(int32_t)) == cudaSuccess &&
+            cudaMalloc(&m->d_val, vals.size() * sizeof(int32_t)) == cudaSuccess &&
+            cudaMemcpy(m->d_idx, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(m->d_val, vals.data(), vals.size() * sizeof(int32_t), cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok && w == n && n <= 16384) {
+    // every column can be full: keep M's integers densely as well, for the
+    // register-tiled product of lra_multiplier_apply
+    std::vector<double> dense((size_t)n * (size_t)n, 0.0);
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t t = 0; t < w; ++t) {
+        const int32_t v = vals[(size_t)j * w + t];
+        if (v != 0) dense[(size_t)rows[(size_t)j * w + t] * n + j] = (double)v;
+      }
+    ok = cudaMalloc(&m->d_dense, dense.size() * sizeof(double)) == cudaSuccess &&
+         cudaMemcpy(m->d_dense, dense.data(), dense.size() * sizeof(double), cudaMemcpyHostToDevice) == cudaSuccess;
+  }
+  if (!ok) {
     cudaFree(m->d_idx);
     cudaFree(m->d_val);
+    cudaFree(m->d_dense);
     delete m;
     return LRA_ERR_CUDA;
   }
@@ -217,6 +232,7 @@ lra_status lra_precondition(lra_multiplier* out, int32_t kind, int64_t n, int32_
   m->d_idx = nullptr;
   m->d_sign = nullptr;
   m->d_val = nullptr;
+  m->d_dense = nullptr;
   if (cudaMalloc(&m->d_idx, cnt * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&m->d_sign, cnt * sizeof(int8_t)) != cudaSuccess ||
       cudaMemcpy(m->d_idx, idx, cnt * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -235,8 +251,9 @@ lra_status lra_multiplier_destroy(lra_multiplier m) {
   cudaError_t e1 = cudaFree(m->d_idx);
   cudaError_t e2 = cudaFree(m->d_sign);
   cudaError_t e3 = cudaFree(m->d_val);
+  cudaError_t e4 = cudaFree(m->d_dense);
   delete m;
-  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess) ? LRA_OK : LRA_ERR_CUDA;
+  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess) ? LRA_OK : LRA_ERR_CUDA;
 }
 
 const char* lra_version(void) { return "lra-gb300 0.1 (sm_103a)"; }

@@ -18,6 +18,7 @@ struct lra_multiplier_s {
   int32_t* d_idx;       // ARHT perm (n), sparse rows (n*nnz) or bidiagonal rows (n*width)
   int8_t* d_sign;       // ARHT diagonal (n) or sparse signs (n*nnz)
   int32_t* d_val;       // bidiagonal integer weights (n*width)
+  double* d_dense;      // bidiagonal with 2^q >= n: the integers of M as an n x n row-major matrix, else null
   double scale;         // 2^{-d/2}, 1/sqrt(nnz) or 2^{-q/2}
 };
 

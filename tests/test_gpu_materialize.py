@@ -41,6 +41,19 @@ def test_apply_is_bit_exact(kind):
     np.testing.assert_array_equal(Wp, ref)
 
 
+@pytest.mark.parametrize("m,n", [(300, 200), (33, 65), (1, 1000)])
+def test_dense_product_ragged_tiles(m, n):
+    """Products whose columns can all be full (2^q >= n) take the register-tiled
+    kernel: ragged row and column tiles, FP64 input."""
+    import paper_1710_07946_gb300 as lra
+    g = np.random.default_rng(m + n)
+    p = li.Problem(li.SRC_DENSE, m, n, W=g.standard_normal((m, n)))
+    li.with_bidiag(p, 20, 17)
+    prob, mult = to_device(p)
+    Wp = lra.lra_multiplier_apply(prob, mult).cpu().numpy()
+    np.testing.assert_array_equal(Wp, oracle.gather_rows(p, np.arange(m, dtype=np.int32)))
+
+
 def test_apply_on_laplace_entries_and_strided_output():
     import paper_1710_07946_gb300 as lra
     p = li.laplace_clusters(300, 256, seed=3)
