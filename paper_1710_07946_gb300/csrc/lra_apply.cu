@@ -158,10 +158,11 @@ __global__ void __launch_bounds__(NT) resid_var_kernel(const double* __restrict_
   __shared__ double red[33];
   __shared__ double s_mean;
   const int nparts = gridDim.x;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {          // every CTA folds the partial sums in the same order
     double s = 0.0;
-    for (int b = 0; b < nparts; ++b) s += part[6 * (size_t)b];
-    s_mean = s / (double)K;
+    for (int b = threadIdx.x; b < nparts; b += 32) s += part[6 * (size_t)b];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (threadIdx.x == 0) s_mean = s / (double)K;
   }
   __syncthreads();
   const double mean = s_mean;
@@ -175,17 +176,28 @@ __global__ void __launch_bounds__(NT) resid_var_kernel(const double* __restrict_
 }
 
 __global__ void resid_final_kernel(const double* __restrict__ part, int nparts, int64_t K, double* __restrict__ stats) {
-  if (threadIdx.x != 0) return;
+  // one warp: lane l folds the partials l, l + 32, ..., then a butterfly
+  const int lane = threadIdx.x;
   double s = 0.0, sa = 0.0, mx = 0.0, se2 = 0.0, sw2 = 0.0, v = 0.0;
-  for (int b = 0; b < nparts; ++b) {
+  for (int b = lane; b < nparts; b += 32) {
     const double* o = part + 6 * (size_t)b;
     s += o[0]; sa += o[1]; mx = fmax(mx, o[2]); se2 += o[3]; sw2 += o[4]; v += o[5];
   }
-  stats[0] = s / (double)K;
-  stats[1] = v / (double)K;
-  stats[2] = sa / (double)K;
-  stats[3] = mx;
-  stats[4] = sw2 > 0.0 ? sqrt(se2) / sqrt(sw2) : 0.0;
+  for (int off = 16; off > 0; off >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, off);
+    sa += __shfl_xor_sync(0xffffffffu, sa, off);
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    se2 += __shfl_xor_sync(0xffffffffu, se2, off);
+    sw2 += __shfl_xor_sync(0xffffffffu, sw2, off);
+    v += __shfl_xor_sync(0xffffffffu, v, off);
+  }
+  if (lane == 0) {
+    stats[0] = s / (double)K;
+    stats[1] = v / (double)K;
+    stats[2] = sa / (double)K;
+    stats[3] = mx;
+    stats[4] = sw2 > 0.0 ? sqrt(se2) / sqrt(sw2) : 0.0;
+  }
 }
 
 }  // namespace lra
