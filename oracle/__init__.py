@@ -57,6 +57,8 @@ def lib():
         L.orc_oversample.restype = ct.c_int
         L.orc_oversample_cycle.argtypes = [P, vp, vp, i32, i32, i32, i32, f64, f64, vp, vp, vp, vp, vp]
         L.orc_oversample_cycle.restype = ct.c_int
+        L.orc_rhtcur.argtypes = [P, vp, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
+        L.orc_rhtcur.restype = ct.c_int
         L.orc_cynical.argtypes = [P, i32, i32, i32, vp, vp, vp, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp]
         L.orc_cynical.restype = ct.c_int
         L.orc_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp]
@@ -217,6 +219,24 @@ def ca_run(p, k, sweeps, I0, h=1.01, max_swaps=1000, rank_tol=1e-13, J0=None):
                           _ptr(U), _ptr(R), _ptr(lv), _ptr(info))
     return dict(I=I, J=J, C=C, U=U, R=R, logvol=lv, rank=int(info[0]), swaps=int(info[1]),
                 loops=int(info[2]), status=int(info[3]))
+
+
+def rhtcur(p, Hbar, h=1.01, max_swaps=1000, rank_tol=1e-13):
+    """CUR LRA with Gaussian sampling (Algorithm algrhtcur, lbar = l = k):
+    rows I from the sketch S = W Hbar (Hbar n x k), then columns J from W[I, :]
+    (orc_rhtcur).  Returns ca_run's dict (logvol of the second run)."""
+    assert p.mkind == 0, "Algorithm algrhtcur samples W itself"
+    mp = _Marshalled(p)
+    Hbar = np.ascontiguousarray(Hbar, dtype=np.float64)
+    assert Hbar.ndim == 2 and Hbar.shape[0] == p.n
+    k = Hbar.shape[1]
+    I = np.empty(k, dtype=np.int32); J = np.empty(k, dtype=np.int32)
+    C = np.zeros((p.m, k)); U = np.zeros((k, k)); R = np.zeros((k, p.n))
+    lv = np.empty(2); info = np.zeros(4, dtype=np.int32)
+    lib().orc_rhtcur(mp.ref, _ptr(Hbar), k, h, max_swaps, rank_tol, _ptr(I), _ptr(J), _ptr(C), _ptr(U), _ptr(R),
+                     _ptr(lv), _ptr(info))
+    return dict(I=I, J=J, C=C, U=U, R=R, logvol=lv, rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]),
+                status=int(info[3]))
 
 
 def ca_run_adaptive(p, stages, margin, sweeps, I0, h=1.01, max_swaps=1000, rank_tol=1e-6):

@@ -656,6 +656,80 @@ int orc_ca_run_warm(const orc_problem* p, int32_t k, int32_t sweeps, const int32
 }
 
 /*
+ * orc_rhtcur: CUR LRA with Gaussian sampling (Algorithm algrhtcur), with
+ * lbar = l = k (a square k x k generator):
+ *  1. S = W Hbar (m x k) for the caller's n x k Gaussian Hbar (row-major),
+ *     S[i][a] = sum over j ascending of fma(Hbar[j][a], w_ij, .) (the plain
+ *     product; the input is W itself, no multiplier).
+ *  2. The algorithms of GE96 on S: the k rows I of a k x k submatrix with
+ *     locally maximal volume in S.  Taken as a one-loop C-A run on S^T
+ *     (k x m) from all its k rows, whose cold first column step (LU with
+ *     column pivoting, then dominance swaps while max |B^{-1} S^T| > h) picks
+ *     k columns of S^T, i.e. rows of S.
+ *  3. The same on W[I, :] (k x n): a one-loop C-A run from all k rows; its cold
+ *     column step picks J, its row step puts the rows in generator order, and
+ *     its nucleus is U = pinv of the rank-r QRP truncation of W[I, J].
+ *  4. C = W[:, J] (m x k) and R = W[I, :] (k x n) in that order.
+ * Outputs: I, J (k), C, U (k x k), R, logvol (2: the second run's), info:
+ * rank, swaps (both runs), loops (2), status (an error of either run, else the
+ * worse warning).
+ */
+int orc_rhtcur(const orc_problem* p, const double* Hbar, int32_t k, double h, int32_t max_swaps, double rank_tol,
+               int32_t* I, int32_t* J, double* C, double* U, double* R, double* logvol, int32_t* info) {
+  int64_t m = p->m, n = p->n;
+  double* ST = (double*)malloc(sizeof(double) * (size_t)k * (size_t)m);
+  for (int32_t a = 0; a < k; ++a)
+    for (int64_t i = 0; i < m; ++i) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < n; ++j) acc = fma(Hbar[j * k + a], entry_w(p, i, j), acc);
+      ST[(int64_t)a * m + i] = acc;
+    }
+  int32_t* I0 = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  for (int32_t a = 0; a < k; ++a) I0[a] = a;
+  orc_problem ps;
+  memset(&ps, 0, sizeof(ps));
+  ps.src = ORC_DENSE; ps.dtype = ORC_F64; ps.m = k; ps.n = m; ps.W = ST; ps.ldw = m; ps.mkind = ORC_MULT_NONE;
+  int32_t* I1 = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  int32_t* J1 = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  double* C1 = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+  double* U1 = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+  double* R1 = (double*)malloc(sizeof(double) * (size_t)k * (size_t)m);
+  double lv1[2];
+  int32_t inf1[4], inf2[4];
+  int st1 = orc_ca_run(&ps, k, 1, I0, h, max_swaps, rank_tol, I1, J1, C1, U1, R1, lv1, inf1);
+  int status;
+  if (st1 != ORC_OK && st1 < 16) {
+    info[0] = 0; info[1] = inf1[1]; info[2] = 1; info[3] = st1;
+    logvol[0] = logvol[1] = NAN;
+    status = st1;
+  } else {
+    /* the k x n row strip W[I, :] as a dense problem of its own */
+    double* R0 = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
+    orc_gather_rows_orig(p, J1, k, R0);
+    orc_problem pr;
+    memset(&pr, 0, sizeof(pr));
+    pr.src = ORC_DENSE; pr.dtype = ORC_F64; pr.m = k; pr.n = n; pr.W = R0; pr.ldw = n; pr.mkind = ORC_MULT_NONE;
+    int32_t* I2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+    double* C2 = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+    int st2 = orc_ca_run(&pr, k, 1, I0, h, max_swaps, rank_tol, I2, J, C2, U, R, logvol, inf2);
+    for (int32_t a = 0; a < k; ++a) I[a] = J1[I2[a]];
+    if (st2 != ORC_OK && st2 < 16) status = st2;
+    else status = st1 > st2 ? st1 : st2;
+    if (!(st2 != ORC_OK && st2 < 16)) {
+      double* Ct = (double*)malloc(sizeof(double) * (size_t)k * (size_t)m);
+      orc_gather_cols_t(p, J, k, Ct);
+      for (int64_t i = 0; i < m; ++i)
+        for (int32_t a = 0; a < k; ++a) C[i * k + a] = Ct[(int64_t)a * m + i];
+      free(Ct);
+    }
+    info[0] = inf2[0]; info[1] = inf1[1] + inf2[1]; info[2] = 2; info[3] = status;
+    free(R0); free(I2); free(C2);
+  }
+  free(ST); free(I0); free(I1); free(J1); free(C1); free(U1); free(R1);
+  return status;
+}
+
+/*
  * orc_ca_run_adaptive: C-A with the generator size fitted to the numerical
  * rank.  The paper's tests take r x r generators with r the numerical rank of
  * the input at 1e-6 (section "Numerical Experiments", Test Overview); here

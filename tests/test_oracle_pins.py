@@ -716,6 +716,57 @@ def test_oversampled_generators_reduce_the_error():
     assert means[0] > means[1] > means[2], means
 
 
+# ------------------------------------------------------------------ Gaussian-sampling CUR
+def test_rhtcur_recovers_exact_low_rank():
+    """Algorithm algrhtcur: on an exact rank-k input with a Gaussian Hbar (n x k)
+    the CUR reproduces W to rounding."""
+    for seed in range(3):
+        p = li.factor_gaussian(300, 10, 0.0, seed=seed)
+        H = np.random.default_rng(seed).standard_normal((300, 10))
+        o = oracle.rhtcur(p, H)
+        assert o["status"] == 0 and o["rank"] == 10 and o["loops"] == 2
+        assert np.linalg.norm(p.W - o["C"] @ o["U"] @ o["R"]) <= 1e-12 * np.linalg.norm(p.W)
+
+
+def test_rhtcur_selections_are_dominant():
+    """Step 2 picks rows I whose k x k submatrix of S = W Hbar is h-dominant in S
+    (|S S_I^{-1}| <= h), step 3 columns J with W[I, J] h-dominant in W[I, :];
+    C, R are the gathered W[:, J], W[I, :] and U the inverse of W[I, J]."""
+    h = 1.05
+    for seed in range(4):
+        p = li.dense_lowrank(200, 180, r=20, noise=1e-6, seed=seed)
+        H = np.random.default_rng(10 + seed).standard_normal((180, 8))
+        o = oracle.rhtcur(p, H, h=h)
+        S = p.W @ H
+        assert np.abs(S @ np.linalg.inv(S[o["I"], :])).max() <= h * (1 + 1e-9)
+        B = p.W[np.ix_(o["I"], o["J"])]
+        assert np.abs(np.linalg.solve(B, p.W[o["I"], :])).max() <= h * (1 + 1e-9)
+        np.testing.assert_array_equal(o["C"], p.W[:, o["J"]])
+        np.testing.assert_array_equal(o["R"], p.W[o["I"], :])
+        np.testing.assert_allclose(o["U"] @ B, np.eye(8), atol=1e-8)
+
+
+def test_rhtcur_with_a_selection_matrix_samples_columns():
+    """Hbar = the first k columns of the identity makes S = W[:, :k] exactly
+    (every fma adds an exact zero or the entry itself): the rows are those of a
+    dominant submatrix of W[:, :k]."""
+    p = li.dense_lowrank(120, 90, r=6, noise=1e-7, seed=5)
+    H = np.eye(90)[:, :6]
+    o = oracle.rhtcur(p, H, h=1.01)
+    S = p.W[:, :6]
+    assert np.abs(S @ np.linalg.inv(S[o["I"], :])).max() <= 1.01 * (1 + 1e-12)
+
+
+def test_rhtcur_error_near_optimal_on_decaying_spectra():
+    p = li.dense_lowrank(400, 350, r=20, noise=1e-9, seed=3)
+    sv = np.linalg.svd(p.W, compute_uv=False)
+    for k, seed in [(8, 0), (12, 1)]:
+        H = np.random.default_rng(seed).standard_normal((350, k))
+        o = oracle.rhtcur(p, H)
+        err = np.linalg.norm(p.W - o["C"] @ o["U"] @ o["R"], 2)
+        assert sv[k] <= err <= 20 * sv[k], (k, err / sv[k])
+
+
 # ------------------------------------------------------------------ expansion/contraction cycles
 def _leverages(Rs, J):
     """s_q = b_q^T (A A^T)^{-1} b_q for every column b_q of Rs, A = Rs[:, J] (Theorem th2)."""
