@@ -342,6 +342,85 @@ class DenseWorkload:
         return n, n, el, f"{n} complete LRAs of the same input (C-A + nucleus + residual sample)"
 
 
+class RhtcurWorkload:
+    """CUR LRA with Gaussian sampling (Algorithm algrhtcur, lbar = l = k) on the
+    dense benchmark input (8192^2 FP32, rank 32 + 1% spikes): one step = the
+    sketch S = W Hbar (Hbar 8192 x 48 Gaussian), the row and column selections,
+    the nucleus and the sampled residual."""
+    kernel = "sketch_kernel"
+    unit = "LRA/s"
+
+    def __init__(self, n=8192, k=48):
+        self.n, self.k, self.q, self.s = n, k, 256, 256
+        self.name = f"rhtcur_dense{n}_f32_rank32_spikes1pct_gaussian_k{k}"
+
+    def host(self, rank):
+        p = li.dense_spiky(self.n, r=32, seed=1000 * rank)
+        H = li.gaussian_sketch(self.n, self.k, 21 + rank)
+        Q, S = li.sample_positions(self.n, self.n, self.q, self.s, 13)
+        return dict(p=p, H=H, Q=Q, S=S)
+
+    def config(self, h):
+        return {"workload": self.name, "m": self.n, "n": self.n, "k": self.k, "input_dtype": "f32",
+                "sketch": f"Gaussian Hbar {self.n} x {self.k} (FP64)", "residual_sample": f"{self.q}x{self.s}"}
+
+    def device(self, h, dev):
+        import torch
+        import paper_1710_07946_gb300 as lra
+        W = torch.from_numpy(h["p"].W).to(dev)
+        prob = lra.Problem.dense(W)
+        H = torch.from_numpy(h["H"]).to(dev)
+        out = lra.lra_rhtcur_run(prob, H)
+        return dict(W=W, prob=prob, H=H, out=out, Q=torch.from_numpy(h["Q"]).to(dev),
+                    S=torch.from_numpy(h["S"]).to(dev), stats=None)
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        lra.lra_rhtcur_run(d["prob"], d["H"], out=d["out"], workspace=d["out"]["_workspace"])
+        d["stats"] = lra.lra_residual_sample(d["prob"], d["out"]["C"], d["out"]["U"], d["out"]["R"], d["Q"], d["S"])
+
+    def check(self, d):
+        info = d["out"]["info"].cpu().numpy()[None, :]
+        err = d["stats"].cpu().numpy()[4:5]
+        return dict(units=1, info=info, err=err)      # spikes: the error bound is not attainable here
+
+    def flops(self, h, res):
+        return 2.0 * self.n * self.n * self.k        # the sketch: one fma per (i, j, column of Hbar)
+
+    def extra(self, res):
+        inf = res["info"][0]
+        return {"rank": int(inf[0]), "swaps": int(inf[1]), "status": int(inf[3]),
+                "rel_fro_err_sampled": float(res["err"][0])}
+
+    def e2e_setup(self, h, d):
+        import torch
+        hp = dict(W=torch.from_numpy(h["p"].W).pin_memory(), H=torch.from_numpy(h["H"]).pin_memory())
+        hp["out"] = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in d["out"].items()
+                     if not key.startswith("_")}
+        hp["stats"] = torch.empty(5, dtype=torch.float64).pin_memory()
+        h2d = hp["W"].numel() * 4 + hp["H"].numel() * 8
+        d2h = sum(v.numel() * v.element_size() for v in hp["out"].values()) + 40
+        return hp, h2d, d2h
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["W"].copy_(hp["W"], non_blocking=True)
+        d["H"].copy_(hp["H"], non_blocking=True)
+        self.step(d)
+        for key, v in hp["out"].items():
+            v.copy_(d["out"][key], non_blocking=True)
+        hp["stats"].copy_(d["stats"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        t0 = time.perf_counter()
+        o = oracle.rhtcur(h["p"], h["H"])
+        oracle.residual_sample(h["p"], o["C"], o["U"], o["R"], h["Q"], h["S"])
+        el = time.perf_counter() - t0
+        return 1, 1, el, "1 complete LRA of the same input (sketch + selections + nucleus + residual sample)"
+
+
 class Hmt11Workload:
     """The single-layer Laplacian inputs of the bidiagonal pre-processing tests
     (inputs (i), [HMT11, Section 7.1]): n x n dense FP64, pre-processed by the
@@ -926,6 +1005,7 @@ WORKLOADS = {
     "fmm_oversample8_cycles4": lambda: FmmOversampleWorkload(8, pmax=4),
     "fmm_small": FmmSmallWorkload,
     "hmt11_n1024_k39_bidiag20": Hmt11Workload,
+    "rhtcur_dense8192_k48": RhtcurWorkload,
     "hmt11_n1024_k39_bidiag20_onthefly": lambda: Hmt11Workload(materialize=False),
     "hmt11_n256_k31_bidiag20": lambda: Hmt11Workload(n=256, k=31),
     **{f"laplace65536_k{k}{sfx}": (lambda k=k, e=e: LaplaceSingleWorkload(k, e))

@@ -259,6 +259,34 @@ lra_status lra_ca_run_warm(const lra_problem* prob, const lra_ca_params* par, lr
                            lra_stream_t stream);
 
 /*
+ * lra_rhtcur_run -- CUR LRA with Gaussian sampling (paper: Algorithm algrhtcur,
+ * "Computation of a CUR LRA with Gaussian sampling"), with lbar = l = k:
+ *   1. S = W Hbar (m x k): Hbar is the caller's n x k Gaussian matrix (device,
+ *      FP64, row-major; the random draws are inputs), each entry of S the fma
+ *      chain over the columns j of W in ascending order.  W is read as given
+ *      (no multiplier); m n k fused multiply-adds, the step the paper marks as
+ *      not superfast.
+ *   2. Rows I: the algorithms of GE96 on S, here the maxvol selection of a
+ *      k x k submatrix of locally maximal volume in S -- a one-loop C-A run on
+ *      S^T from all k rows, whose cold first column step (LU with column
+ *      pivoting, then swaps while max |B^{-1} S^T| > par->h) picks them.
+ *   3. Columns J: a one-loop C-A run on the row strip W[I, :] from all k rows:
+ *      its cold column step picks J, its row step orders I, its nucleus is U.
+ *   4. C = W[:, J] (m x k), R = W[I, :] (k x n).
+ * par: k (1..min(m, n, 64)), h, rank_tol, max_swaps as for lra_ca_run; sweeps
+ * and mode are ignored (one loop each, FP64); nstages must be 0.
+ * out: as lra_ca_run (logvol holds 2 doubles: the second run's).  info: rank,
+ * swaps of both runs, loops 2, status (an error of either run first, else the
+ * worse warning), 0, FP64 maxvol steps, k, k.
+ * The workspace (lra_rhtcur_workspace_size) holds S^T (k x m), the row strip
+ * (k x n) and the two runs' buffers.  Asynchronous on the stream.
+ * Errors: LRA_ERR_INVALID_ARG, LRA_ERR_WORKSPACE, LRA_ERR_CUDA.
+ */
+lra_status lra_rhtcur_workspace_size(const lra_problem* prob, const lra_ca_params* par, size_t* bytes);
+lra_status lra_rhtcur_run(const lra_problem* prob, const double* Hbar, const lra_ca_params* par, const lra_cur* out,
+                          void* workspace, size_t workspace_bytes, lra_stream_t stream);
+
+/*
  * lra_ca_run_noalloc -- lra_ca_run without a caller-supplied workspace, for
  * callers that cannot allocate device memory themselves: for instance a plug-in
  * running inside a host application whose own allocator owns the whole device

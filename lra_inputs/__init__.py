@@ -103,6 +103,12 @@ def sparse_pm1_descriptor(n: int, nnz: int, seed: int):
     return srow, ssign
 
 
+def gaussian_sketch(n: int, k: int, seed: int) -> np.ndarray:
+    """An n x k Gaussian matrix (FP64, standard normal): the Hbar of the
+    Gaussian-sampling CUR."""
+    return np.ascontiguousarray(rng(seed).standard_normal((n, k)))
+
+
 def bidiag_descriptor(n: int, q: int, seed: int):
     """q factors (I + D_i S) P_i: per factor a random permutation (column a of P_i
     is e_{perm[i, a]}) and Rademacher signs D_i (q x n each)."""

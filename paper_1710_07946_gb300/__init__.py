@@ -117,6 +117,8 @@ def _load():
     L.lra_oversample_batched_workspace_size.argtypes = [P, PB, PP, i32, ct.POINTER(sz)]
     L.lra_oversample_batched.argtypes = [P, PB, PP, i32, PCB, PCB, vp, sz, vp]
     L.lra_multiplier_apply.argtypes = [P, vp, vp, i64, vp]
+    L.lra_rhtcur_workspace_size.argtypes = [P, PP, ct.POINTER(sz)]
+    L.lra_rhtcur_run.argtypes = [P, vp, PP, ct.POINTER(_Cur), vp, sz, vp]
     L.lra_gather_rows.argtypes = [P, vp, i32, vp, vp, vp]
     L.lra_oversample_cycle_batched_workspace_size.argtypes = [P, PB, PP, i32, i32, ct.POINTER(sz)]
     L.lra_oversample_cycle_batched.argtypes = [P, PB, PP, i32, i32, PCB, PCB, vp, sz, vp]
@@ -138,7 +140,7 @@ def _load():
               "lra_ca_batched_tune", "lra_cynical_batched_workspace_size", "lra_cynical_run_batched",
               "lra_cynical_batched_tune", "lra_oversample_batched_workspace_size", "lra_oversample_batched",
               "lra_oversample_cycle_batched_workspace_size", "lra_oversample_cycle_batched", "lra_multiplier_apply",
-              "lra_gather_rows",
+              "lra_gather_rows", "lra_rhtcur_workspace_size", "lra_rhtcur_run",
               "lra_residual_sample_batched_rect",
               "lra_gauss_cur_forward", "lra_gauss_cur_backward"):
         getattr(L, f).restype = ct.c_int
@@ -357,6 +359,39 @@ def lra_ca_run(problem: Problem, I0: torch.Tensor, k: int, sweeps: int = 3, h: f
         setattr(cur, f, _dev(out[f], name=f).data_ptr())
     _check(L.lra_ca_run_warm(ct.byref(pc), ct.byref(pp), mh, I0.data_ptr(), None if J0 is None else J0.data_ptr(),
                              ct.byref(cur), workspace.data_ptr(), workspace.numel(), _stream(stream)), "lra_ca_run")
+    out["_workspace"] = workspace
+    return out
+
+
+def lra_rhtcur_run(problem: Problem, Hbar: torch.Tensor, h: float = 1.01, rank_tol: float = 1e-13,
+                   max_swaps: int = 1000, out: Optional[dict] = None, workspace: Optional[torch.Tensor] = None,
+                   stream=None) -> dict:
+    """CUR LRA with Gaussian sampling (Algorithm algrhtcur, lbar = l = k): rows
+    from the sketch S = W Hbar (Hbar: n x k float64 CUDA tensor of Gaussian
+    draws), columns from W[I, :].  Returns lra_ca_run's dict (logvol: 2 values)."""
+    L = _load()
+    dev = (problem.W if problem.W is not None else problem.X).device
+    _dev(Hbar, torch.float64, "Hbar")
+    if Hbar.dim() != 2 or Hbar.shape[0] != problem.n:
+        raise ValueError("Hbar must be n x k")
+    k = Hbar.shape[1]
+    pc, pp = problem._c(), _params(k, 1, h, rank_tol, max_swaps, LRA_MODE_FP64)
+    if out is None:
+        out = dict(I=torch.empty(k, dtype=torch.int32, device=dev), J=torch.empty(k, dtype=torch.int32, device=dev),
+                   C=torch.empty(problem.m, k, dtype=torch.float64, device=dev),
+                   U=torch.empty(k, k, dtype=torch.float64, device=dev),
+                   R=torch.empty(k, problem.n, dtype=torch.float64, device=dev),
+                   logvol=torch.empty(2, dtype=torch.float64, device=dev),
+                   info=torch.empty(LRA_INFO_LEN, dtype=torch.int32, device=dev))
+    if workspace is None:
+        nb = ct.c_size_t()
+        _check(L.lra_rhtcur_workspace_size(ct.byref(pc), ct.byref(pp), ct.byref(nb)), "lra_rhtcur_workspace_size")
+        workspace = _workspace(nb.value, dev)
+    cur = _Cur()
+    for f in ("I", "J", "C", "U", "R", "logvol", "info"):
+        setattr(cur, f, _dev(out[f], name=f).data_ptr())
+    _check(L.lra_rhtcur_run(ct.byref(pc), Hbar.data_ptr(), ct.byref(pp), ct.byref(cur), workspace.data_ptr(),
+                            workspace.numel(), _stream(stream)), "lra_rhtcur_run")
     out["_workspace"] = workspace
     return out
 
