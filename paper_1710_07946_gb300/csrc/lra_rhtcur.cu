@@ -20,51 +20,53 @@
 
 namespace lra {
 
-// S^T = (W Hbar)^T: CTA tile 32 rows of W x 64 sketch columns, 16-deep steps
-// over the columns j of W; thread (ty, tx) of 16 x 16 owns rows ty + 16a
-// (a < 2) and sketch columns tx + 16b (b < 4).  S[i][c] = sum over j ascending
-// of fma(Hbar[j][c], w_ij, .); the zero padding past n adds exact zeros.
+// S^T = (W Hbar)^T: CTA tile 32 rows of W x 16 KB sketch columns (KB =
+// ceil(k / 16)), 16-deep steps over the columns j of W; thread (ty, tx) of
+// 16 x 16 owns rows ty + 16a (a < 2) and sketch columns tx + 16b (b < KB).
+// S[i][c] = sum over j ascending of fma(Hbar[j][c], w_ij, .); the zero padding
+// past n adds exact zeros.
+template <int KB>
 __global__ void __launch_bounds__(256) sketch_kernel(DevProblem P, const double* __restrict__ Hbar, int k,
                                                      double* __restrict__ ST) {
   __shared__ double Ws[32][17];
-  __shared__ double Hs[16][64];
+  __shared__ double Hs[16][16 * KB];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
   const int64_t i0 = (int64_t)blockIdx.x * 32;
-  double acc[2][4];
+  double acc[2][KB];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    for (int b = 0; b < KB; ++b) acc[a][b] = 0.0;
   for (int64_t j0 = 0; j0 < P.n; j0 += 16) {
     for (int e = threadIdx.x; e < 512; e += 256) {
       const int ii = e >> 4, jj = e & 15;
       const int64_t i = i0 + ii, j = j0 + jj;
       Ws[ii][jj] = (i < P.m && j < P.n) ? w_entry(P, i, j) : 0.0;
     }
-    for (int e = threadIdx.x; e < 1024; e += 256) {
-      const int jj = e >> 6, c = e & 63;
+    for (int e = threadIdx.x; e < 256 * KB; e += 256) {
+      const int jj = e / (16 * KB), c = e - jj * (16 * KB);
       const int64_t j = j0 + jj;
       Hs[jj][c] = (j < P.n && c < k) ? Hbar[j * k + c] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int rr = 0; rr < 16; ++rr) {
-      double w[2], hv[4];
+      double w[2], hv[KB];
 #pragma unroll
       for (int a = 0; a < 2; ++a) w[a] = Ws[ty + 16 * a][rr];
 #pragma unroll
-      for (int b = 0; b < 4; ++b) hv[b] = Hs[rr][tx + 16 * b];
+      for (int b = 0; b < KB; ++b) hv[b] = Hs[rr][tx + 16 * b];
 #pragma unroll
       for (int a = 0; a < 2; ++a)
 #pragma unroll
-        for (int b = 0; b < 4; ++b) acc[a][b] = fma(hv[b], w[a], acc[a][b]);
+        for (int b = 0; b < KB; ++b) acc[a][b] = fma(hv[b], w[a], acc[a][b]);
     }
     __syncthreads();
   }
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) {
+    for (int b = 0; b < KB; ++b) {
       const int64_t i = i0 + ty + 16 * a;
       const int c = tx + 16 * b;
       if (i < P.m && c < k) ST[(int64_t)c * P.m + i] = acc[a][b];
@@ -239,7 +241,13 @@ lra_status lra_rhtcur_run(const lra_problem* prob, const double* Hbar, const lra
   LRA_CUDA_TRY(cudaMemsetAsync(gstatus, 0, sizeof(int32_t), stream));
   {
     LaunchScope ls(stream, "sketch_kernel");
-    sketch_kernel<<<(unsigned)((P.m + 31) / 32), 256, 0, stream>>>(P, Hbar, k, ST);
+    const unsigned grid = (unsigned)((P.m + 31) / 32);
+    switch ((k + 15) / 16) {
+      case 1: sketch_kernel<1><<<grid, 256, 0, stream>>>(P, Hbar, k, ST); break;
+      case 2: sketch_kernel<2><<<grid, 256, 0, stream>>>(P, Hbar, k, ST); break;
+      case 3: sketch_kernel<3><<<grid, 256, 0, stream>>>(P, Hbar, k, ST); break;
+      default: sketch_kernel<4><<<grid, 256, 0, stream>>>(P, Hbar, k, ST); break;
+    }
   }
   {
     LaunchScope ls(stream, "iota_kernel");
