@@ -37,7 +37,8 @@ def run_both(p, k, seed, h=1.01):
     return o, g
 
 
-@pytest.mark.parametrize("m,n,k", [(700, 500, 8), (513, 301, 16), (64, 2000, 12), (2001, 33, 20)])
+@pytest.mark.parametrize("m,n,k", [(700, 500, 8), (513, 301, 16), (64, 2000, 12), (2001, 33, 20), (300, 280, 64),
+                                   (90, 400, 33)])
 def test_dense_f64(m, n, k):
     p = li.dense_lowrank(m, n, r=min(m, n, 24), noise=1e-7, seed=m)
     run_both(p, k, m + n)
