@@ -59,6 +59,14 @@ def lib():
         L.orc_oversample_cycle.restype = ct.c_int
         L.orc_rhtcur.argtypes = [P, vp, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_rhtcur.restype = ct.c_int
+        L.orc_jacobi_eig.argtypes = [vp, vp, i32]
+        L.orc_jacobi_eig.restype = None
+        L.orc_lev_scores.argtypes = [vp, i32, i64, i32, vp]
+        L.orc_lev_scores.restype = i32
+        L.orc_lev_sample.argtypes = [vp, i64, i32, i32, vp, vp]
+        L.orc_lev_sample.restype = i32
+        L.orc_ca_lev.argtypes = [P, i32, i32, i32, i32, vp, vp, f64, vp, vp, vp, vp, vp, vp]
+        L.orc_ca_lev.restype = ct.c_int
         L.orc_cynical.argtypes = [P, i32, i32, i32, vp, vp, vp, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp]
         L.orc_cynical.restype = ct.c_int
         L.orc_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp]
@@ -237,6 +245,57 @@ def rhtcur(p, Hbar, h=1.01, max_swaps=1000, rank_tol=1e-13):
                      _ptr(lv), _ptr(info))
     return dict(I=I, J=J, C=C, U=U, R=R, logvol=lv, rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]),
                 status=int(info[3]))
+
+
+def jacobi_eig(G):
+    """Round-robin Jacobi eigen-decomposition (orc_jacobi_eig): returns the
+    rotated G (diagonal to rounding) and Q with G_in = Q G Q^T."""
+    G = np.array(G, dtype=np.float64, order="C", copy=True)
+    k = G.shape[0]
+    Q = np.empty((k, k))
+    lib().orc_jacobi_eig(_ptr(G), _ptr(Q), k)
+    return G, Q
+
+
+def lev_scores(A, r):
+    """SVD-based leverage scores v_j = ||row j of V^(r)||^2 of the columns of a
+    k x n sketch (orc_lev_scores); returns (v, eigenpairs used)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    k, n = A.shape
+    v = np.empty(n)
+    re = lib().orc_lev_scores(_ptr(A), k, n, int(r), _ptr(v))
+    return v, int(re)
+
+
+def lev_sample(v, l, kind, u):
+    """Exactly(l) (kind 0) / Expected(l) (kind 1) sampling by the scores v
+    (orc_lev_sample); u: the uniform draws.  Returns the picked indices."""
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    out = np.empty(max(int(l), 1), dtype=np.int32)
+    cnt = lib().orc_lev_sample(_ptr(v), len(v), int(l), int(kind), _ptr(u), _ptr(out))
+    return out[:cnt].copy()
+
+
+def ca_lev(p, k, r, iters, kind, draws, I0, rank_tol=1e-6):
+    """C-A iterations with DMM08 Algorithm 1 on the sketches (orc_ca_lev):
+    draws (2 iters x max(m, n) uniforms).  Returns I (kI), J (kJ), C (m x kJ),
+    U (kJ x kI), R (kI x n), rank, kI, kJ, status."""
+    mp = _Marshalled(p)
+    L = max(p.m, p.n)
+    draws = np.ascontiguousarray(draws, dtype=np.float64).reshape(-1)
+    assert draws.size >= 2 * iters * L
+    I0 = np.ascontiguousarray(I0, dtype=np.int32)
+    assert len(I0) == k
+    I = np.zeros(k, dtype=np.int32); J = np.zeros(k, dtype=np.int32)
+    C = np.zeros(p.m * k); U = np.zeros(k * k); R = np.zeros(k * p.n)
+    info = np.zeros(4, dtype=np.int32)
+    lib().orc_ca_lev(mp.ref, int(k), int(r), int(iters), int(kind), _ptr(draws), _ptr(I0), rank_tol, _ptr(I),
+                     _ptr(J), _ptr(C), _ptr(U), _ptr(R), _ptr(info))
+    kI, kJ = int(info[1]), int(info[2])
+    return dict(I=I[:kI].copy(), J=J[:kJ].copy(), C=C[:p.m * kJ].reshape(p.m, kJ).copy(),
+                U=U[:kJ * kI].reshape(kJ, kI).copy(), R=R[:kI * p.n].reshape(kI, p.n).copy(), rank=int(info[0]),
+                kI=kI, kJ=kJ, status=int(info[3]))
 
 
 def ca_run_adaptive(p, stages, margin, sweeps, I0, h=1.01, max_swaps=1000, rank_tol=1e-6):

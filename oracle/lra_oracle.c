@@ -1074,6 +1074,256 @@ int orc_oversample(const orc_problem* p, const int32_t* I, const int32_t* J, int
 }
 
 /* ------------------------------------------------------------------ */
+/* Leverage-score sampling inside C-A (DMM08 Algorithm 1 on sketches)   */
+/* ------------------------------------------------------------------ */
+#define ORC_JAC_SWEEPS 10
+#define ORC_LEV_EIG_TOL 1e-12
+
+/* Pair i of round t of the round-robin (circle) schedule over kp (even)
+ * indices: index 0 meets 1 + t, and 1 + ((t + i) mod (kp - 1)) meets
+ * 1 + ((t - i) mod (kp - 1)); every pair meets once in kp - 1 rounds. */
+static void jac_pair(int32_t kp, int32_t t, int32_t i, int32_t* p, int32_t* q) {
+  int32_t a = (i == 0) ? 0 : 1 + (t + i) % (kp - 1);
+  int32_t b = 1 + (t + kp - 1 - i) % (kp - 1);
+  *p = a < b ? a : b;
+  *q = a < b ? b : a;
+}
+
+/*
+ * orc_jacobi_eig: eigen-decomposition of a symmetric k x k G (row-major, in
+ * place) by ORC_JAC_SWEEPS sweeps of Jacobi rotations in the round-robin
+ * order (k rounded up to even kp; pairs with an index >= k are skipped).  In
+ * each round every rotation is computed from G as it stands at the round's
+ * start (the pairs are disjoint): for G[p][q] != 0, tau = (G[q][q] -
+ * G[p][p]) / (2 G[p][q]), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
+ * c = 1 / sqrt(1 + t^2), s = t c (the classical symmetric Schur rotation that
+ * zeroes G[p][q]); then all row pairs (row p <- c row_p - s row_q, row q <-
+ * s row_p + c row_q), then all column pairs the same way, then the columns of
+ * Q (Q starts as I).  On return G is diagonal to rounding and G_in = Q G Q^T.
+ */
+void orc_jacobi_eig(double* G, double* Q, int32_t k) {
+  int32_t kp = k + (k & 1);
+  int32_t half = kp / 2;
+  double* cs = (double*)malloc(sizeof(double) * 2 * (size_t)(half > 0 ? half : 1));
+  for (int32_t i = 0; i < k; ++i)
+    for (int32_t j = 0; j < k; ++j) Q[i * k + j] = (i == j) ? 1.0 : 0.0;
+  for (int32_t sw = 0; sw < ORC_JAC_SWEEPS; ++sw)
+    for (int32_t t = 0; t < kp - 1; ++t) {
+      for (int32_t i = 0; i < half; ++i) {
+        int32_t p, q;
+        jac_pair(kp, t, i, &p, &q);
+        double c = 1.0, sn = 0.0;
+        if (q < k && G[p * k + q] != 0.0) {
+          double tau = (G[q * k + q] - G[p * k + p]) / (2.0 * G[p * k + q]);
+          double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + tt * tt);
+          sn = tt * c;
+        }
+        cs[2 * i] = c; cs[2 * i + 1] = sn;
+      }
+      for (int32_t i = 0; i < half; ++i) {
+        int32_t p, q;
+        jac_pair(kp, t, i, &p, &q);
+        if (q >= k) continue;
+        double c = cs[2 * i], sn = cs[2 * i + 1];
+        for (int32_t j = 0; j < k; ++j) {
+          double x = G[p * k + j], y = G[q * k + j];
+          G[p * k + j] = c * x - sn * y;
+          G[q * k + j] = sn * x + c * y;
+        }
+      }
+      for (int32_t i = 0; i < half; ++i) {
+        int32_t p, q;
+        jac_pair(kp, t, i, &p, &q);
+        if (q >= k) continue;
+        double c = cs[2 * i], sn = cs[2 * i + 1];
+        for (int32_t j = 0; j < k; ++j) {
+          double x = G[j * k + p], y = G[j * k + q];
+          G[j * k + p] = c * x - sn * y;
+          G[j * k + q] = sn * x + c * y;
+        }
+        for (int32_t j = 0; j < k; ++j) {
+          double x = Q[j * k + p], y = Q[j * k + q];
+          Q[j * k + p] = c * x - sn * y;
+          Q[j * k + q] = sn * x + c * y;
+        }
+      }
+    }
+  free(cs);
+}
+
+/*
+ * orc_lev_scores: SVD-based leverage scores (eq. eqlevsc with beta = 1) of the
+ * columns of a k x n sketch A (row-major): v_j = ||row j of V^(r)||^2, with
+ * V^(r) the top-r right singular vectors of A, from the Gram matrix:
+ *  1. G = A A^T, G[a][b] = ascending fma chain over j, for a <= b, mirrored;
+ *  2. orc_jacobi_eig(G) -> eigenvalues d_a = G[a][a], eigenvectors Q[:, a];
+ *  3. the r largest eigenvalues (largest first, lowest index on ties) that are
+ *     >= ORC_LEV_EIG_TOL times the largest and positive (sigma >= 1e-6 sigma_max);
+ *  4. v_j = sum over them, in that order, of w / d_t with w = e^2, e the
+ *     ascending fma chain of Q[:, t] . A[:, j] (v_j = (a_j . u_t)^2 / sigma_t^2).
+ * The scores p_j = v_j / sum v are the sampling probabilities.  Returns the
+ * number of eigenpairs used (0 when A has no positive eigenvalue).
+ */
+int32_t orc_lev_scores(const double* A, int32_t k, int64_t n, int32_t r, double* v) {
+  double* G = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+  double* Q = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+  int32_t* sel = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  unsigned char* used = (unsigned char*)calloc((size_t)k, 1);
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t b = a; b < k; ++b) {
+      double acc = 0.0;
+      for (int64_t j = 0; j < n; ++j) acc = fma(A[(int64_t)a * n + j], A[(int64_t)b * n + j], acc);
+      G[a * k + b] = acc;
+      G[b * k + a] = acc;
+    }
+  orc_jacobi_eig(G, Q, k);
+  int32_t re = 0;
+  double dmax = 0.0;
+  for (int32_t t = 0; t < r && t < k; ++t) {
+    int32_t best = -1;
+    for (int32_t a = 0; a < k; ++a)
+      if (!used[a] && (best < 0 || G[a * k + a] > G[best * k + best])) best = a;
+    if (best < 0 || !(G[best * k + best] > 0.0)) break;
+    if (t == 0) dmax = G[best * k + best];
+    else if (G[best * k + best] < ORC_LEV_EIG_TOL * dmax) break;
+    used[best] = 1;
+    sel[re++] = best;
+  }
+  for (int64_t j = 0; j < n; ++j) {
+    double acc = 0.0;
+    for (int32_t t = 0; t < re; ++t) {
+      int32_t c = sel[t];
+      double e = 0.0;
+      for (int32_t a = 0; a < k; ++a) e = fma(Q[a * k + c], A[(int64_t)a * n + j], e);
+      double w = e * e;
+      acc = acc + w / G[c * k + c];
+    }
+    v[j] = acc;
+  }
+  free(G); free(Q); free(sel); free(used);
+  return re;
+}
+
+/*
+ * orc_lev_sample: DMM08's sampling of l indices out of n by the scores v
+ * (probabilities p_j = v_j / total, total = the ascending sum of v):
+ *  kind 0, Exactly(l) (Algorithm algsmplex): for t = 0..l-1 the smallest j with
+ *    cum_j > u_t * total (cum_j the ascending running sum of v; if none, the
+ *    last j with v_j > 0): l indices in draw order, repeats allowed;
+ *  kind 1, Expected(l) (Algorithm algsmplexp): j ascending is picked when u_j <
+ *    min(1, (l v_j) / total), at most l picks.
+ * u: l (kind 0) or n (kind 1) uniform draws in [0, 1).  With total <= 0 (no
+ * scores) the first min(l, n) indices are taken.  A kind-1 scan that picks
+ * nothing takes the index of the largest v_j (lowest on ties).  Returns the
+ * number of indices written to out.
+ */
+int32_t orc_lev_sample(const double* v, int64_t n, int32_t l, int32_t kind, const double* u, int32_t* out) {
+  double* cum = (double*)malloc(sizeof(double) * (size_t)n);
+  double c = 0.0;
+  int64_t last = -1;
+  for (int64_t j = 0; j < n; ++j) {
+    c = c + v[j];
+    cum[j] = c;
+    if (v[j] > 0.0) last = j;
+  }
+  double total = c;
+  int32_t cnt = 0;
+  if (!(total > 0.0) || last < 0) {
+    for (int64_t j = 0; j < n && cnt < l; ++j) out[cnt++] = (int32_t)j;
+  } else if (kind == 0) {
+    for (int32_t t = 0; t < l; ++t) {
+      double target = u[t] * total;
+      int64_t lo = 0, hi = n;                 /* smallest j with cum[j] > target */
+      while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (cum[mid] > target) hi = mid; else lo = mid + 1;
+      }
+      out[cnt++] = (int32_t)(lo < n ? lo : last);
+    }
+  } else {
+    for (int64_t j = 0; j < n && cnt < l; ++j) {
+      double pr = ((double)l * v[j]) / total;
+      if (pr > 1.0) pr = 1.0;
+      if (u[j] < pr) out[cnt++] = (int32_t)j;
+    }
+    if (cnt == 0) {
+      int64_t best = 0;
+      for (int64_t j = 1; j < n; ++j) if (v[j] > v[best]) best = j;
+      out[cnt++] = (int32_t)best;
+    }
+  }
+  free(cum);
+  return cnt;
+}
+
+/*
+ * orc_ca_lev: C-A iterations whose steps select by DMM08 Algorithm 1 on the
+ * sketches (the C-A lines of the tables "LRA errors of Cross-Approximation
+ * tests incorporating [DMM08, Algorithm 1]"): from the rows I0 (k of them),
+ * iters times
+ *   horizontal step: the scores of the columns of W'[I, :] (kI x n, rank r) ->
+ *     orc_lev_sample(l = k) with the draws u_{2s} -> J (kJ indices);
+ *   vertical step: the scores of the rows, i.e. of the columns of W'[:, J]^T
+ *     (kJ x m) -> orc_lev_sample with u_{2s+1} -> I (kI indices);
+ * then U = pinv of the rank-r QRP truncation of G = W'[I, J] (kI x kJ; the
+ * rectangular nucleus, of G^T when kI > kJ, transposed back), C = W'[:, J]
+ * (m x kJ), R = W[I, :] (kI x n).  Repeated indices (Exactly) stay in the sets.
+ * draws: 2 iters steps of max(m, n) uniforms each.  Outputs sized for k.
+ * info: rank, kI, kJ, status (ORC_WARN_RANK_DEFICIENT when a sketch had no
+ * positive eigenvalue or the nucleus rank is below min(kI, kJ)).
+ */
+int orc_ca_lev(const orc_problem* p, int32_t k, int32_t r, int32_t iters, int32_t kind, const double* draws,
+               const int32_t* I0, double rank_tol, int32_t* I, int32_t* J, double* C, double* U, double* R,
+               int32_t* info) {
+  int64_t m = p->m, n = p->n, L = m > n ? m : n;
+  double* S = (double*)malloc(sizeof(double) * (size_t)k * (size_t)L);
+  double* v = (double*)malloc(sizeof(double) * (size_t)L);
+  int32_t kI = k, kJ = 0;
+  int status = ORC_OK;
+  memcpy(I, I0, sizeof(int32_t) * (size_t)k);
+  for (int32_t it = 0; it < iters; ++it) {
+    orc_gather_rows(p, I, kI, S);
+    if (!all_finite(S, (int64_t)kI * n)) { status = ORC_ERR_NONFINITE; break; }
+    if (orc_lev_scores(S, kI, n, r < kI ? r : kI, v) == 0) status = ORC_WARN_RANK_DEFICIENT;
+    kJ = orc_lev_sample(v, n, k, kind, draws + (size_t)(2 * it) * L, J);
+    orc_gather_cols_t(p, J, kJ, S);
+    if (!all_finite(S, (int64_t)kJ * m)) { status = ORC_ERR_NONFINITE; break; }
+    if (orc_lev_scores(S, kJ, m, r < kJ ? r : kJ, v) == 0) status = ORC_WARN_RANK_DEFICIENT;
+    kI = orc_lev_sample(v, m, k, kind, draws + (size_t)(2 * it + 1) * L, I);
+  }
+  if (status == ORC_ERR_NONFINITE) {
+    info[0] = 0; info[1] = kI; info[2] = kJ; info[3] = status;
+    free(S); free(v);
+    return status;
+  }
+  double* Ct = (double*)malloc(sizeof(double) * (size_t)kJ * (size_t)m);
+  orc_gather_cols_t(p, J, kJ, Ct);
+  for (int64_t i = 0; i < m; ++i)
+    for (int32_t a = 0; a < kJ; ++a) C[i * kJ + a] = Ct[(int64_t)a * m + i];
+  orc_gather_rows_orig(p, I, kI, R);
+  double* G = (double*)malloc(sizeof(double) * (size_t)kI * (size_t)kJ);
+  int32_t rank;
+  if (kI <= kJ) {
+    for (int32_t a = 0; a < kI; ++a)
+      for (int32_t b = 0; b < kJ; ++b) G[(int64_t)a * kJ + b] = C[(int64_t)I[a] * kJ + b];
+    rank = orc_nucleus_rect(G, kI, kJ, rank_tol, U);               /* kJ x kI */
+  } else {
+    double* Ut = (double*)malloc(sizeof(double) * (size_t)kI * (size_t)kJ);
+    for (int32_t b = 0; b < kJ; ++b)
+      for (int32_t a = 0; a < kI; ++a) G[(int64_t)b * kI + a] = C[(int64_t)I[a] * kJ + b];
+    rank = orc_nucleus_rect(G, kJ, kI, rank_tol, Ut);              /* kI x kJ = pinv(G^T) */
+    for (int32_t b = 0; b < kJ; ++b)
+      for (int32_t a = 0; a < kI; ++a) U[(int64_t)b * kI + a] = Ut[(int64_t)a * kJ + b];
+    free(Ut);
+  }
+  if (rank < (kI < kJ ? kI : kJ) && status == ORC_OK) status = ORC_WARN_RANK_DEFICIENT;
+  info[0] = rank; info[1] = kI; info[2] = kJ; info[3] = status;
+  free(S); free(v); free(Ct); free(G);
+  return status;
+}
+
+/* ------------------------------------------------------------------ */
 /* CUR apply and sampled residual                                      */
 /* ------------------------------------------------------------------ */
 /* Y = C (U (R X)): C m x k, U k x k, R k x n, X n x nrhs, Y m x nrhs, all

@@ -767,6 +767,86 @@ def test_rhtcur_error_near_optimal_on_decaying_spectra():
         assert sv[k] <= err <= 20 * sv[k], (k, err / sv[k])
 
 
+# ------------------------------------------------------------------ leverage-score sampling inside C-A
+def test_jacobi_eigendecomposition():
+    """The round-robin Jacobi sweeps diagonalise a symmetric matrix: eigenvalues
+    equal LAPACK's, G = Q diag Q^T, Q orthogonal."""
+    g = np.random.default_rng(1)
+    for k in (1, 2, 7, 16, 33):
+        A = g.standard_normal((k, 3 * k + 5))
+        G0 = A @ A.T
+        D, Q = oracle.jacobi_eig(G0)
+        off = D - np.diag(np.diag(D))
+        assert np.abs(off).max() <= 1e-14 * np.abs(G0).max()
+        np.testing.assert_allclose(np.sort(np.diag(D)), np.linalg.eigvalsh(G0), rtol=1e-11, atol=1e-13)
+        assert np.abs(Q @ np.diag(np.diag(D)) @ Q.T - G0).max() <= 1e-13 * np.abs(G0).max()
+        assert np.abs(Q.T @ Q - np.eye(k)).max() <= 1e-13
+
+
+def test_leverage_scores_are_the_row_norms_of_the_top_singular_vectors():
+    """Eq. eqlevsc with beta = 1: v_j = ||V^(r)[j, :]||^2 for the top-r right
+    singular vectors (numpy's SVD), summing to r; eigenvalues below 1e-12 of the
+    largest (sigma below 1e-6 sigma_max) are left out."""
+    g = np.random.default_rng(2)
+    A = g.standard_normal((12, 5)) @ np.diag(2.0 ** -np.arange(5)) @ g.standard_normal((5, 200))
+    A += 1e-9 * g.standard_normal(A.shape)
+    _, sv, Vt = np.linalg.svd(A, full_matrices=False)
+    for r in (1, 3, 5):
+        v, used = oracle.lev_scores(A, r)
+        assert used == r
+        np.testing.assert_allclose(v, (Vt[:r] ** 2).sum(axis=0), atol=1e-11)
+        assert abs(v.sum() - r) <= 1e-10
+    v, used = oracle.lev_scores(A, 9)            # sigma_6.. ~ 1e-9 sigma_1: left out
+    assert used == 5
+
+
+def test_exactly_sampling_is_the_inverse_cdf():
+    """Algorithm algsmplex: draw t picks the smallest j with cum_j > u_t total;
+    zero-score indices are never picked; u near 1 falls back to the last
+    positive score."""
+    v = np.array([0.0, 1.0, 0.0, 2.0, 3.0, 0.0, 4.0, 0.0])
+    cum, tot = np.cumsum(v), v.sum()
+    u = np.array([0.0, 0.05, 0.1 - 1e-12, 0.1, 0.35, 0.6, 0.999999, 1.0 - 2.0 ** -53])
+    got = oracle.lev_sample(v, len(u), 0, u)
+    ref = [int(np.argmax(cum > x * tot)) if (cum > x * tot).any() else 6 for x in u]
+    np.testing.assert_array_equal(got, ref)
+    assert not set(got) & {0, 2, 5, 7}
+
+
+def test_exactly_sampling_frequencies_follow_the_scores():
+    g = np.random.default_rng(3)
+    v = g.random(20) ** 2
+    u = g.random(200000)
+    got = oracle.lev_sample(v, len(u), 0, u)
+    freq = np.bincount(got, minlength=20) / len(u)
+    p = v / v.sum()
+    assert np.abs(freq - p).max() <= 5 * np.sqrt(p.max() / len(u))
+
+
+def test_expected_sampling_keeps_each_index_with_its_probability():
+    """Algorithm algsmplexp: j (ascending) is kept when u_j < min(1, l p_j), at
+    most l of them; nothing kept -> the largest score."""
+    v = np.array([4.0, 1.0, 0.0, 3.0, 2.0])
+    l, tot = 2, v.sum()
+    u = np.array([0.79, 0.21, 0.0, 0.59, 0.3])
+    pr = np.minimum(1.0, l * v / tot)               # 0.8 0.2 0 0.6 0.4
+    ref = [j for j in range(5) if u[j] < pr[j]][:l]
+    np.testing.assert_array_equal(oracle.lev_sample(v, l, 1, u), ref)
+    np.testing.assert_array_equal(oracle.lev_sample(v, l, 1, np.full(5, 0.9999)), [0])
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_ca_with_leverage_sampling_recovers_low_rank(kind):
+    """C-A iterations with DMM08 Algorithm 1 on the sketches (k = 2r, 4r samples
+    per step) reproduce an exact rank-r input."""
+    g = np.random.default_rng(4)
+    for k, seed in [(16, 0), (32, 1)]:
+        p = li.factor_gaussian(300, 8, 0.0, seed=seed)
+        o = oracle.ca_lev(p, k, 8, 8, kind, g.random(2 * 8 * 300), li.initial_rows(300, k, seed))
+        assert o["rank"] == 8 and o["kI"] <= k and o["kJ"] <= k
+        assert np.linalg.norm(p.W - o["C"] @ o["U"] @ o["R"]) <= 1e-10 * np.linalg.norm(p.W)
+
+
 # ------------------------------------------------------------------ expansion/contraction cycles
 def _leverages(Rs, J):
     """s_q = b_q^T (A A^T)^{-1} b_q for every column b_q of Rs, A = Rs[:, J] (Theorem th2)."""
