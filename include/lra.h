@@ -483,6 +483,43 @@ lra_status lra_oversample_cycle_batched(const lra_problem* base, const lra_batch
                                         lra_stream_t stream);
 
 /*
+ * lra_ca_lev_batched -- C-A iterations whose steps select by DMM08 Algorithm 1
+ * on the sketches (paper: the tests of C-A incorporating [DMM08, Algorithm 1],
+ * with SVD-based leverage scores, eq. eqlevsc with beta = 1, and the sampling of
+ * Algorithms algsmplex / algsmplexp), one CTA per block of the batch.  Per
+ * block, from the rows I0 (k of them), iters times:
+ *   horizontal: the k_I x n sketch A = W[I, :]; G = A A^T (ascending fma
+ *   chains); 10 sweeps of round-robin Jacobi rotations (all angles of a round
+ *   from G at its start, then the row pairs, then the column pairs and Q); the
+ *   r' = min(r, k_I) largest eigenvalues (lowest index on ties) that are
+ *   positive and >= 1e-12 of the largest; scores v_j = sum_t (Q_t . a_j)^2 / d_t;
+ *   then l = k columns: kind 0 Exactly(l) -- draw t picks the smallest j with
+ *   cum_j > u_t * total (ascending running sums; none: the last j with v_j > 0),
+ *   repeats allowed; kind 1 Expected(l) -- j ascending is kept when u_j <
+ *   min(1, (l v_j) / total), at most l, none kept: the largest v_j.  No
+ *   positive score: the first l indices.
+ *   vertical: the same on W[:, J]^T (k_J x m) for the rows.
+ * Then U = pinv of the rank-r QRP truncation of W[I, J] (k_I x k_J; of its
+ * transpose when k_I > k_J, transposed back), C = W[:, J], R = W[I, :].
+ * k: 1..64, <= every block's rows and columns; r: 1..k; iters >= 1; I0: nb x k
+ * block-local rows; draws: nb x (2 iters) x batch->max_len uniforms in [0, 1)
+ * (step s of block b at (b * 2 iters + s) * max_len; Exactly reads k of them,
+ * Expected one per index).  Outputs (lra_cur_batch): I, J (nb x k: the first
+ * k_I, k_J used), C_b (nrows x k_J) and R_b (k_I x ncols) at batch->offsets
+ * (slots nrows x k and k x ncols), U (nb x k x k, the first k_J x k_I row-major),
+ * info: rank, 0, iters, status (LRA_WARN_RANK_DEFICIENT when a sketch had no
+ * positive eigenvalue or the rank is below min(k_I, k_J); LRA_ERR_NONFINITE;
+ * LRA_ERR_INVALID_ARG for a bad block), 0, 0, k_I, k_J.  logvol is not used.
+ * Errors: LRA_ERR_INVALID_ARG, LRA_ERR_WORKSPACE, LRA_ERR_CUDA.
+ */
+lra_status lra_ca_lev_batched_workspace_size(const lra_problem* base, const lra_batch* batch, int32_t k, int32_t r,
+                                             int32_t iters, int32_t kind, size_t* bytes);
+lra_status lra_ca_lev_batched(const lra_problem* base, const lra_batch* batch, int32_t k, int32_t r, int32_t iters,
+                              int32_t kind, double rank_tol, const int32_t* I0, const double* draws,
+                              const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
+                              lra_stream_t stream);
+
+/*
  * lra_ca_batched_shapes -- the CTA shapes the batched kernel is built for:
  * writes up to cap (threads per CTA, CTAs per SM) pairs and returns their
  * number.  Each shape holds 16 warps per SM (128 registers a thread); they

@@ -118,6 +118,8 @@ def _load():
     L.lra_oversample_batched.argtypes = [P, PB, PP, i32, PCB, PCB, vp, sz, vp]
     L.lra_multiplier_apply.argtypes = [P, vp, vp, i64, vp]
     L.lra_rhtcur_workspace_size.argtypes = [P, PP, ct.POINTER(sz)]
+    L.lra_ca_lev_batched_workspace_size.argtypes = [P, PB, i32, i32, i32, i32, ct.POINTER(sz)]
+    L.lra_ca_lev_batched.argtypes = [P, PB, i32, i32, i32, i32, f64, vp, vp, PCB, vp, sz, vp]
     L.lra_rhtcur_run.argtypes = [P, vp, PP, ct.POINTER(_Cur), vp, sz, vp]
     L.lra_gather_rows.argtypes = [P, vp, i32, vp, vp, vp]
     L.lra_oversample_cycle_batched_workspace_size.argtypes = [P, PB, PP, i32, i32, ct.POINTER(sz)]
@@ -140,7 +142,8 @@ def _load():
               "lra_ca_batched_tune", "lra_cynical_batched_workspace_size", "lra_cynical_run_batched",
               "lra_cynical_batched_tune", "lra_oversample_batched_workspace_size", "lra_oversample_batched",
               "lra_oversample_cycle_batched_workspace_size", "lra_oversample_cycle_batched", "lra_multiplier_apply",
-              "lra_gather_rows", "lra_rhtcur_workspace_size", "lra_rhtcur_run",
+              "lra_gather_rows", "lra_rhtcur_workspace_size", "lra_rhtcur_run", "lra_ca_lev_batched_workspace_size",
+              "lra_ca_lev_batched",
               "lra_residual_sample_batched_rect",
               "lra_gauss_cur_forward", "lra_gauss_cur_backward"):
         getattr(L, f).restype = ct.c_int
@@ -690,6 +693,76 @@ def lra_oversample_cycle_batched(batch: Batch, pextra: int, pmax: int, max_cycle
                                                 ov.workspace.data_ptr(), ov.workspace.numel(), _stream(stream)),
            "lra_oversample_cycle_batched")
     return ov
+
+
+class LevBatch:
+    """Device buffers of a batch of blocks for lra_ca_lev_batched: C-A
+    iterations with DMM08 Algorithm 1 on the sketches (kind 0 Exactly(k),
+    1 Expected(k)), rank r leverage scores, ``draws`` uniforms per step."""
+
+    def __init__(self, problem: Problem, blocks, k: int, r: int, iters: int, kind: int, I0, draws,
+                 rank_tol: float = 1e-6, order="lpt"):
+        import numpy as np
+        blocks = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64).reshape(-1, 4))
+        nb = len(blocks)
+        dev = (problem.W if problem.W is not None else problem.X).device
+        csz, rsz = blocks[:, 1] * k, k * blocks[:, 3]
+        offs = np.zeros((nb, 2), dtype=np.int64)
+        offs[1:, 0] = np.cumsum(csz)[:-1]
+        offs[1:, 1] = np.cumsum(rsz)[:-1]
+        if isinstance(order, str) and order == "lpt":
+            order = np.argsort(-(blocks[:, 1] * blocks[:, 3]), kind="stable").astype(np.int32)
+        self.problem, self.k, self.r, self.iters, self.kind, self.nb = problem, int(k), int(r), int(iters), \
+            int(kind), nb
+        self.rank_tol = float(rank_tol)
+        self.blocks_np, self.offs_np = blocks, offs
+        t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).to(dev)
+        self.blocks, self.offs = t(blocks, np.int64), t(offs, np.int64)
+        self.order = None if order is None else t(order, np.int32)
+        self.max_len = int(max(blocks[:, 1].max(), blocks[:, 3].max()))
+        self.I0 = t(np.asarray(I0).reshape(nb, k), np.int32)
+        draws = torch.as_tensor(draws, dtype=torch.float64).reshape(-1)
+        if draws.numel() != nb * 2 * self.iters * self.max_len:
+            raise ValueError("draws: nb x (2 iters) x max_len uniforms")
+        self.draws = draws.to(dev).contiguous()
+        self.out = dict(I=torch.zeros(nb, k, dtype=torch.int32, device=dev),
+                        J=torch.zeros(nb, k, dtype=torch.int32, device=dev),
+                        C=torch.zeros(max(int(csz.sum()), 1), dtype=torch.float64, device=dev),
+                        U=torch.zeros(nb, k, k, dtype=torch.float64, device=dev),
+                        R=torch.zeros(max(int(rsz.sum()), 1), dtype=torch.float64, device=dev),
+                        logvol=torch.zeros(1, dtype=torch.float64, device=dev),
+                        info=torch.zeros(nb, LRA_INFO_LEN, dtype=torch.int32, device=dev))
+        self.cb = _Batch()
+        self.cb.blocks, self.cb.offsets = self.blocks.data_ptr(), self.offs.data_ptr()
+        self.cb.order = self.order.data_ptr() if self.order is not None else None
+        self.cb.nb, self.cb.max_len = nb, self.max_len
+        self.cur = _CurBatch()
+        for f in ("I", "J", "C", "U", "R", "logvol", "info"):
+            setattr(self.cur, f, self.out[f].data_ptr())
+        self.pc = problem._c()
+        nbytes = ct.c_size_t()
+        _check(_load().lra_ca_lev_batched_workspace_size(ct.byref(self.pc), ct.byref(self.cb), self.k, self.r,
+                                                         self.iters, self.kind, ct.byref(nbytes)),
+               "lra_ca_lev_batched_workspace_size")
+        self.workspace = _workspace(nbytes.value, dev)
+
+    def block(self, b: int) -> dict:
+        (r0, nr, c0, nc) = self.blocks_np[b]
+        oc, orr = self.offs_np[b]
+        o = {key: v.cpu().numpy() for key, v in self.out.items()}
+        info = o["info"][b]
+        kI, kJ = int(info[6]), int(info[7])
+        return dict(I=o["I"][b, :kI], J=o["J"][b, :kJ], C=o["C"][oc:oc + nr * kJ].reshape(nr, kJ),
+                    U=o["U"][b].reshape(-1)[:kJ * kI].reshape(kJ, kI), R=o["R"][orr:orr + kI * nc].reshape(kI, nc),
+                    rank=int(info[0]), status=int(info[3]), kI=kI, kJ=kJ)
+
+
+def lra_ca_lev_batched(lb: LevBatch, stream=None) -> None:
+    """Run C-A with leverage-score sampling on every block of ``lb`` (asynchronous)."""
+    _check(_load().lra_ca_lev_batched(ct.byref(lb.pc), ct.byref(lb.cb), lb.k, lb.r, lb.iters, lb.kind, lb.rank_tol,
+                                      lb.I0.data_ptr(), lb.draws.data_ptr(), ct.byref(lb.cur),
+                                      lb.workspace.data_ptr(), lb.workspace.numel(), _stream(stream)),
+           "lra_ca_lev_batched")
 
 
 def lra_residual_sample_oversampled(ov: Oversampled, Q: torch.Tensor, S: torch.Tensor,
