@@ -421,6 +421,99 @@ class RhtcurWorkload:
         return 1, 1, el, "1 complete LRA of the same input (sketch + selections + nucleus + residual sample)"
 
 
+class LevCaWorkload:
+    """C-A with DMM08 Algorithm 1 on the sketches (the tests of C-A incorporating
+    [DMM08, Algorithm 1]): a 1000 x 1000 input of numerical rank r = 10 at 1e-6
+    (U diag(2^-1..2^-10) V^T + 1e-9 G), k = l = 4r samples per step by
+    Exactly(l), eight C-A iterations; one step = ``runs`` independent runs (own
+    initial rows and draws, one CTA each) + each run's sampled residual."""
+    kernel = "lev_batched_kernel"
+    unit = "LRA/s"
+
+    def __init__(self, n=1000, r=10, k=40, iters=8, runs=152, kind=0):
+        self.n, self.r, self.k, self.iters, self.runs, self.kind = n, r, k, iters, runs, kind
+        self.q = self.s = 256
+        tag = "exactly" if kind == 0 else "expected"
+        self.name = f"levca_n{n}_r{r}_k{k}_{tag}_it{iters}_x{runs}"
+
+    def host(self, rank):
+        p = li.dense_lowrank(self.n, self.n, r=self.r, noise=1e-9, seed=1000 * rank)
+        blocks = np.array([[0, self.n, 0, self.n]] * self.runs, dtype=np.int64)
+        draws = li.rng(77 + rank).random((self.runs, 2 * self.iters, self.n))
+        I0 = li.block_initial_rows(blocks, self.k, 5 + rank)
+        Q, S = li.block_sample_positions(blocks, self.q, self.s, 13)
+        return dict(p=p, blocks=blocks, draws=draws, I0=I0, Q=Q, S=S)
+
+    def config(self, h):
+        return {"workload": self.name, "m": self.n, "n": self.n, "nrank": self.r, "k_eq_l": self.k,
+                "ca_iterations": self.iters, "sampling": "Exactly(l)" if self.kind == 0 else "Expected(l)",
+                "runs_per_step": self.runs, "residual_sample": f"{self.q}x{self.s} per run"}
+
+    def device(self, h, dev):
+        import torch
+        import paper_1710_07946_gb300 as lra
+        W = torch.from_numpy(h["p"].W).to(dev)
+        prob = lra.Problem.dense(W)
+        lb = lra.LevBatch(prob, h["blocks"], self.k, self.r, self.iters, self.kind, h["I0"], h["draws"], order=None)
+        return dict(W=W, prob=prob, lb=lb, Q=torch.from_numpy(h["Q"]).to(dev), S=torch.from_numpy(h["S"]).to(dev),
+                    stats=torch.empty(self.runs, 5, dtype=torch.float64, device=dev))
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        lra.lra_ca_lev_batched(d["lb"])
+        lra.lra_residual_sample_lev(d["lb"], d["Q"], d["S"], d["stats"])
+
+    def check(self, d):
+        info = d["lb"].out["info"].cpu().numpy()
+        err = d["stats"].cpu().numpy()[:, 4]
+        return dict(units=self.runs, info=info, err=err)
+
+    def flops(self, h, res):
+        # per block: 2 iters sketches of k x n: Gram k^2 n, 10 Jacobi sweeps of (k-1) rounds x k/2 rotations x 12 k,
+        # scores r k n (fma = 2 flops)
+        k, n = self.k, self.n
+        per_step = k * k * n + 10 * (k - 1) * (k // 2) * 12 * k + 2 * self.r * k * n
+        return 2.0 * self.iters * per_step * self.runs      # one launch runs every block
+
+    def extra(self, res):
+        return {"rel_fro_err_mean": float(np.mean(res["err"])), "rel_fro_err_std": float(np.std(res["err"])),
+                "rel_fro_err_max": float(np.max(res["err"])), "ranks": sorted(set(int(x) for x in res["info"][:, 0])),
+                "statuses": sorted(set(int(x) for x in res["info"][:, 3])),
+                "flops_note": ("per launch (all runs): Gram k^2 n + Jacobi 10 (k-1) (k/2) 12 k + scores 2 r k n per "
+                               "sketch, 2 x iters sketches per run")}
+
+    def e2e_setup(self, h, d):
+        import torch
+        hp = dict(W=torch.from_numpy(h["p"].W).pin_memory())
+        hp["out"] = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in d["lb"].out.items()}
+        hp["stats"] = torch.empty(self.runs, 5, dtype=torch.float64).pin_memory()
+        h2d = hp["W"].numel() * 8
+        d2h = sum(v.numel() * v.element_size() for v in hp["out"].values()) + hp["stats"].numel() * 8
+        return hp, h2d, d2h
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["W"].copy_(hp["W"], non_blocking=True)
+        self.step(d)
+        for key, v in hp["out"].items():
+            v.copy_(d["lb"].out[key], non_blocking=True)
+        hp["stats"].copy_(d["stats"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        t0 = time.perf_counter()
+        n = 0
+        for b in range(self.runs):
+            o = oracle.ca_lev(h["p"], self.k, self.r, self.iters, self.kind, h["draws"][b], h["I0"][b])
+            oracle.residual_sample(h["p"], o["C"], o["U"], o["R"], h["Q"][b], h["S"][b])
+            n += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        el = time.perf_counter() - t0
+        return n, n, el, f"{n} complete runs (8 C-A iterations + nucleus + residual sample) of the step's {self.runs}"
+
+
 class Hmt11Workload:
     """The single-layer Laplacian inputs of the bidiagonal pre-processing tests
     (inputs (i), [HMT11, Section 7.1]): n x n dense FP64, pre-processed by the
@@ -1006,6 +1099,8 @@ WORKLOADS = {
     "fmm_small": FmmSmallWorkload,
     "hmt11_n1024_k39_bidiag20": Hmt11Workload,
     "rhtcur_dense8192_k48": RhtcurWorkload,
+    "levca_n1000_r10_k40": LevCaWorkload,
+    "levca_n1000_r10_k40_expected": lambda: LevCaWorkload(kind=1),
     "hmt11_n1024_k39_bidiag20_onthefly": lambda: Hmt11Workload(materialize=False),
     "hmt11_n256_k31_bidiag20": lambda: Hmt11Workload(n=256, k=31),
     **{f"laplace65536_k{k}{sfx}": (lambda k=k, e=e: LaplaceSingleWorkload(k, e))

@@ -781,6 +781,19 @@ def lra_residual_sample_oversampled(ov: Oversampled, Q: torch.Tensor, S: torch.T
     return stats
 
 
+def lra_residual_sample_lev(lb: "LevBatch", Q: torch.Tensor, S: torch.Tensor, stats: Optional[torch.Tensor] = None,
+                            stream=None) -> torch.Tensor:
+    """Per-block residual sample statistics (nb x 5) of a LevBatch's k_I x k_J generators."""
+    if stats is None:
+        stats = torch.empty(lb.nb, 5, dtype=torch.float64, device=lb.blocks.device)
+    _check(_load().lra_residual_sample_batched_rect(ct.byref(lb.pc), ct.byref(lb.cb), lb.k, lb.k, ct.byref(lb.cur),
+                                                    _dev(Q, torch.int32, "Q").data_ptr(), Q.shape[1],
+                                                    _dev(S, torch.int32, "S").data_ptr(), S.shape[1],
+                                                    stats.data_ptr(), _stream(stream)),
+           "lra_residual_sample_batched_rect")
+    return stats
+
+
 def lra_ca_run_batched(batch: Batch, stream=None) -> None:
     """C-A CUR of every block of `batch` in one persistent launch (results in batch.out)."""
     L = _load()
