@@ -432,7 +432,7 @@ class LevCaWorkload:
 
     def __init__(self, n=1000, r=10, k=40, iters=8, runs=152, kind=0):
         self.n, self.r, self.k, self.iters, self.runs, self.kind = n, r, k, iters, runs, kind
-        self.q = self.s = 256
+        self.q = self.s = 64       # the batched residual holds its q x s sample in shared memory
         tag = "exactly" if kind == 0 else "expected"
         self.name = f"levca_n{n}_r{r}_k{k}_{tag}_it{iters}_x{runs}"
 
