@@ -520,6 +520,51 @@ lra_status lra_ca_lev_batched(const lra_problem* base, const lra_batch* batch, i
                               lra_stream_t stream);
 
 /*
+ * lra_hmatvec -- y = M x for the kernel matrix M = K(P, P) (n x n, M_ii = 0)
+ * held as far blocks with C-A generators plus a dense near field (paper: the
+ * FMM's stage (iii), multiplying generators and diagonal blocks by subvectors;
+ * section "Application: HSS / FMM").  The far blocks are the interaction-list
+ * pairs of every octree level, their generators C_b U_b R_b the outputs of
+ * lra_ca_run_batched on them; the near blocks are the touching leaf pairs,
+ * whose entries are formed on the fly (the diagonal i = j skipped).
+ * Per far block t_b = U_b (R_b x[cols]) (kf_b values, ascending fma chains);
+ * per (level, target box) group, row i of the box gets y_lev[i] = sum over the
+ * group's blocks in order of sum_a C_b[i][a] t_b[a] (one fma chain); per near
+ * group (target leaf) y_near[i] = sum over its blocks in order, columns j
+ * ascending, of fma(w_ij, x_j, .); finally y = y_near + y_2 + ... + y_L in that
+ * order (rows in no group of a level add 0).
+ * prob: the kernel problem (X = Y, m = n).  H (device arrays, caller-owned):
+ * far (nfar x 4: row0, nrows, col0, ncols), far_offsets (nfar x 2: offsets of
+ * C_b and R_b in C and R), C, U (nfar x kmax x kmax, kf_b x kf_b used), R,
+ * info (nfar x LRA_INFO_LEN; kf_b = info[6]) -- the batch's outputs;
+ * far_groups (ngroups x 5: level (2..levels), row0, nrows, first block,
+ * block count; the blocks of a group contiguous); near (nnear x 4), near_groups
+ * (nnear_groups x 4: row0, nrows, first block, count).  x, y: n doubles
+ * (device).  The workspace holds t (nfar x kmax) and (levels - 1 + 1) partial
+ * vectors of n doubles.  Asynchronous on the stream.
+ * Errors: LRA_ERR_INVALID_ARG, LRA_ERR_WORKSPACE, LRA_ERR_CUDA.
+ */
+typedef struct {
+  int64_t n;
+  int32_t levels;
+  int32_t kmax;
+  int32_t nfar, nfar_groups, nnear, nnear_groups;
+  const int64_t* far;
+  const int64_t* far_offsets;
+  const double* C;
+  const double* U;
+  const double* R;
+  const int32_t* info;
+  const int64_t* far_groups;
+  const int64_t* near;
+  const int64_t* near_groups;
+} lra_hmatrix;
+
+lra_status lra_hmatvec_workspace_size(const lra_hmatrix* H, size_t* bytes);
+lra_status lra_hmatvec(const lra_problem* prob, const lra_hmatrix* H, const double* x, double* y, void* workspace,
+                       size_t workspace_bytes, lra_stream_t stream);
+
+/*
  * lra_ca_batched_shapes -- the CTA shapes the batched kernel is built for:
  * writes up to cap (threads per CTA, CTAs per SM) pairs and returns their
  * number.  Each shape holds 16 warps per SM (128 registers a thread); they

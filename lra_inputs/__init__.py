@@ -305,6 +305,95 @@ def fmm_blocks(npts: int = 1 << 20, leaf: int = 64, min_size: int = 64, max_size
     return prob, blocks, levels
 
 
+def fmm_partition(npts: int = 1 << 16, leaf: int = 128, seed: int = 0):
+    """The complete far/near partition of the Laplace matrix K(P, P) over npts
+    uniform points in [0,1]^3 (the octree and interaction lists of fmm_blocks,
+    every level, no sampling): the points sorted by the Morton code of their
+    finest box; far blocks (target box, source box) from the interaction lists
+    of every level 2..L (children of the parent's neighbours that do not touch
+    the box); near blocks (leaf, leaf) for touching leaves, the leaf itself
+    included.  Together the blocks cover every (i, j) exactly once (the diagonal
+    i = j lies in the near field).  Empty boxes are skipped.
+
+    Returns (Problem over the sorted points, far int64 (nf, 6) = (row0, nrows,
+    col0, ncols, level, target box), near int64 (nn, 5) = (row0, nrows, col0,
+    ncols, target leaf), levels L).  Far blocks are ordered by level, then
+    target box, then source box; near blocks by target leaf, then source leaf."""
+    g = rng(seed)
+    P = g.random((npts, 3))
+    L = 1
+    while npts / (8 ** L) > leaf:
+        L += 1
+    side = 1 << L
+    ijk = np.minimum((P * side).astype(np.int64), side - 1)
+    code = _morton3(ijk[:, 0], ijk[:, 1], ijk[:, 2], L)
+    order = np.argsort(code, kind="stable")
+    P = np.ascontiguousarray(P[order])
+    code = code[order]
+
+    def level_boxes(lev):
+        shift = 3 * (L - lev)
+        bcode = code >> shift
+        nbox = 8 ** lev
+        starts = np.searchsorted(bcode, np.arange(nbox), side="left")
+        counts = np.searchsorted(bcode, np.arange(nbox), side="right") - starts
+        codes = np.arange(nbox, dtype=np.int64)
+        bx = np.zeros_like(codes); by = np.zeros_like(codes); bz = np.zeros_like(codes)
+        for b in range(lev):
+            bx |= ((codes >> (3 * b + 2)) & 1) << b
+            by |= ((codes >> (3 * b + 1)) & 1) << b
+            bz |= ((codes >> (3 * b)) & 1) << b
+        n = 1 << lev
+        c2c = np.empty((n, n, n), dtype=np.int64)
+        c2c[bx, by, bz] = codes
+        return starts, counts, bx, by, bz, c2c
+
+    far = []
+    for lev in range(2, L + 1):
+        starts, counts, bx, by, bz, c2c = level_boxes(lev)
+        n = 1 << lev
+        for c in range(8 ** lev):
+            if counts[c] == 0:
+                continue
+            x, y, z = bx[c], by[c], bz[c]
+            srcs = []
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for dz in (-1, 0, 1):
+                        qx, qy, qz = (x >> 1) + dx, (y >> 1) + dy, (z >> 1) + dz
+                        if not (0 <= qx < n // 2 and 0 <= qy < n // 2 and 0 <= qz < n // 2):
+                            continue
+                        for cx in (0, 1):
+                            for cy in (0, 1):
+                                for cz in (0, 1):
+                                    sx, sy, sz = 2 * qx + cx, 2 * qy + cy, 2 * qz + cz
+                                    if max(abs(sx - x), abs(sy - y), abs(sz - z)) <= 1:
+                                        continue
+                                    sc = c2c[sx, sy, sz]
+                                    if counts[sc] > 0:
+                                        srcs.append(int(sc))
+            for sc in sorted(srcs):
+                far.append((starts[c], counts[c], starts[sc], counts[sc], lev, c))
+    starts, counts, bx, by, bz, c2c = level_boxes(L)
+    n = 1 << L
+    near = []
+    for c in range(8 ** L):
+        if counts[c] == 0:
+            continue
+        x, y, z = bx[c], by[c], bz[c]
+        srcs = []
+        for dx in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dz in (-1, 0, 1):
+                    sx, sy, sz = x + dx, y + dy, z + dz
+                    if 0 <= sx < n and 0 <= sy < n and 0 <= sz < n and counts[c2c[sx, sy, sz]] > 0:
+                        srcs.append(int(c2c[sx, sy, sz]))
+        for sc in sorted(srcs):
+            near.append((starts[c], counts[c], starts[sc], counts[sc], c))
+    prob = Problem(SRC_LAPLACE, npts, npts, X=P, Y=P, meta={"levels": L})
+    return prob, np.asarray(far, dtype=np.int64).reshape(-1, 6), np.asarray(near, dtype=np.int64).reshape(-1, 5), L
+
+
 def gaussian_blocks(nblk: int = 256, size: int = 1024, ell: float = 0.3, offset: float = 2.0, seed: int = 0):
     """nblk independent (targets, sources) pairs of point clouds in separated unit
     cubes; returns lists of (m,3) and (n,3) arrays."""

@@ -298,6 +298,24 @@ def ca_lev(p, k, r, iters, kind, draws, I0, rank_tol=1e-6):
                 kI=kI, kJ=kJ, status=int(info[3]))
 
 
+def hmatvec(p, far, near, gens, x):
+    """y = M x for M = K(P, P) (M_ii = 0) partitioned into far blocks with
+    generators gens[b] = (C, U, R) (far order) and near blocks taken densely
+    (the FMM's stage (iii)): plain numpy FP64 products, block by block."""
+    P = np.asarray(p.X, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    y = np.zeros(p.m)
+    for b, (r0, nr, c0, nc) in enumerate(np.asarray(far)[:, :4]):
+        C, U, R = gens[b]
+        y[r0:r0 + nr] += C @ (U @ (R @ x[c0:c0 + nc]))
+    for (r0, nr, c0, nc) in np.asarray(near)[:, :4]:
+        d = np.sqrt(((P[r0:r0 + nr, None, :] - P[None, c0:c0 + nc, :]) ** 2).sum(axis=2))
+        with np.errstate(divide="ignore"):
+            K = np.where(d > 0.0, 1.0 / d, 0.0)
+        y[r0:r0 + nr] += K @ x[c0:c0 + nc]
+    return y
+
+
 def ca_run_adaptive(p, stages, margin, sweeps, I0, h=1.01, max_swaps=1000, rank_tol=1e-6):
     """C-A with staged generator sizes (orc_ca_run_adaptive): a run at each size
     k_s of ``stages`` (clipped to min(m, n)) until the nucleus rank r_s < k_s -

@@ -68,6 +68,14 @@ class _CurBatch(ct.Structure):
                 ("R", ct.c_void_p), ("logvol", ct.c_void_p), ("info", ct.c_void_p)]
 
 
+class _HMatrix(ct.Structure):
+    _fields_ = [("n", ct.c_int64), ("levels", ct.c_int32), ("kmax", ct.c_int32), ("nfar", ct.c_int32),
+                ("nfar_groups", ct.c_int32), ("nnear", ct.c_int32), ("nnear_groups", ct.c_int32),
+                ("far", ct.c_void_p), ("far_offsets", ct.c_void_p), ("C", ct.c_void_p), ("U", ct.c_void_p),
+                ("R", ct.c_void_p), ("info", ct.c_void_p), ("far_groups", ct.c_void_p), ("near", ct.c_void_p),
+                ("near_groups", ct.c_void_p)]
+
+
 class _Gauss(ct.Structure):
     _fields_ = [("X", ct.c_void_p), ("Y", ct.c_void_p), ("I", ct.c_void_p), ("J", ct.c_void_p),
                 ("nb", ct.c_int32), ("m", ct.c_int32), ("n", ct.c_int32), ("k", ct.c_int32),
@@ -119,6 +127,9 @@ def _load():
     L.lra_multiplier_apply.argtypes = [P, vp, vp, i64, vp]
     L.lra_rhtcur_workspace_size.argtypes = [P, PP, ct.POINTER(sz)]
     L.lra_ca_lev_batched_workspace_size.argtypes = [P, PB, i32, i32, i32, i32, ct.POINTER(sz)]
+    PH = ct.POINTER(_HMatrix)
+    L.lra_hmatvec_workspace_size.argtypes = [PH, ct.POINTER(sz)]
+    L.lra_hmatvec.argtypes = [P, PH, vp, vp, vp, sz, vp]
     L.lra_ca_lev_batched.argtypes = [P, PB, i32, i32, i32, i32, f64, vp, vp, PCB, vp, sz, vp]
     L.lra_rhtcur_run.argtypes = [P, vp, PP, ct.POINTER(_Cur), vp, sz, vp]
     L.lra_gather_rows.argtypes = [P, vp, i32, vp, vp, vp]
@@ -143,7 +154,7 @@ def _load():
               "lra_cynical_batched_tune", "lra_oversample_batched_workspace_size", "lra_oversample_batched",
               "lra_oversample_cycle_batched_workspace_size", "lra_oversample_cycle_batched", "lra_multiplier_apply",
               "lra_gather_rows", "lra_rhtcur_workspace_size", "lra_rhtcur_run", "lra_ca_lev_batched_workspace_size",
-              "lra_ca_lev_batched",
+              "lra_ca_lev_batched", "lra_hmatvec_workspace_size", "lra_hmatvec",
               "lra_residual_sample_batched_rect",
               "lra_gauss_cur_forward", "lra_gauss_cur_backward"):
         getattr(L, f).restype = ct.c_int
@@ -779,6 +790,65 @@ def lra_residual_sample_oversampled(ov: Oversampled, Q: torch.Tensor, S: torch.T
                                                     stats.data_ptr(), _stream(stream)),
            "lra_residual_sample_batched_rect")
     return stats
+
+
+class HMatrix:
+    """A kernel matrix K(P, P) (M_ii = 0) partitioned FMM-style: far blocks (the
+    interaction-list pairs of every level, rows (nf, >= 6): row0, nrows, col0,
+    ncols, level, target box) whose generators a batched C-A run computes, and
+    near blocks (touching leaves, rows (nn, >= 5): row0, nrows, col0, ncols,
+    target leaf) formed on the fly; y = M x by lra_hmatvec.  ``I0`` holds the
+    C-A initial rows per far block (nf x k, block-local)."""
+
+    def __init__(self, problem: Problem, far, near, levels: int, I0, k: int = 64, sweeps: int = 3, h: float = 1.05,
+                 rank_tol: float = 1e-6, stages=(28, 40, 64), rank_margin: int = 2):
+        import numpy as np
+        far = np.asarray(far, dtype=np.int64)
+        near = np.asarray(near, dtype=np.int64)
+        dev = problem.X.device
+        self.problem, self.n, self.levels = problem, problem.m, int(levels)
+        self.batch = Batch(problem, far[:, :4], k, sweeps, I0, h=h, rank_tol=rank_tol, stages=stages,
+                           rank_margin=rank_margin)
+        # groups: runs of consecutive blocks with the same (level, target box) / target leaf
+        fg = []
+        for i in range(len(far)):
+            if i == 0 or far[i, 4] != far[i - 1, 4] or far[i, 5] != far[i - 1, 5]:
+                fg.append([far[i, 4], far[i, 0], far[i, 1], i, 0])
+            fg[-1][4] += 1
+        ng = []
+        for i in range(len(near)):
+            if i == 0 or near[i, 4] != near[i - 1, 4]:
+                ng.append([near[i, 0], near[i, 1], i, 0])
+            ng[-1][3] += 1
+        t = lambda a, w: torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.int64).reshape(-1, w))).to(dev)
+        self.far_groups, self.near = t(fg, 5), t(near[:, :4], 4)
+        self.near_groups = t(ng, 4)
+        H = _HMatrix()
+        H.n, H.levels, H.kmax = self.n, self.levels, int(k)
+        H.nfar, H.nfar_groups, H.nnear, H.nnear_groups = len(far), len(fg), len(near), len(ng)
+        b = self.batch
+        H.far, H.far_offsets = b.blocks.data_ptr(), b.offs.data_ptr()
+        H.C, H.U, H.R, H.info = (b.out[f].data_ptr() for f in ("C", "U", "R", "info"))
+        H.far_groups, H.near, H.near_groups = (self.far_groups.data_ptr(), self.near.data_ptr(),
+                                               self.near_groups.data_ptr())
+        self.H = H
+        nbytes = ct.c_size_t()
+        _check(_load().lra_hmatvec_workspace_size(ct.byref(H), ct.byref(nbytes)), "lra_hmatvec_workspace_size")
+        self.workspace = _workspace(nbytes.value, dev)
+
+    def build(self, stream=None) -> None:
+        """Compute every far block's generators (lra_ca_run_batched)."""
+        lra_ca_run_batched(self.batch, stream)
+
+    def matvec(self, x: torch.Tensor, y: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        _dev(x, torch.float64, "x")
+        if y is None:
+            y = torch.empty_like(x)
+        pc = self.problem._c()
+        _check(_load().lra_hmatvec(ct.byref(pc), ct.byref(self.H), x.data_ptr(), _dev(y, torch.float64, "y").data_ptr(),
+                                   self.workspace.data_ptr(), self.workspace.numel(), _stream(stream)),
+               "lra_hmatvec")
+        return y
 
 
 def lra_residual_sample_lev(lb: "LevBatch", Q: torch.Tensor, S: torch.Tensor, stats: Optional[torch.Tensor] = None,

@@ -1,0 +1,179 @@
+// lra_hmatvec.cu -- y = M x for a kernel matrix held as far blocks with C-A
+// generators plus a dense near field (the FMM's stage (iii): generators and
+// diagonal blocks times subvectors).  Three passes, each deterministic:
+//   1. per far block, t_b = U_b (R_b x[cols]);
+//   2. per (level, target box), each row's fma chain over the box's blocks in
+//      order, C_b[i][:] . t_b, into the level's partial vector; per target
+//      leaf, the near field's fma chain over the source leaves in order;
+//   3. y = y_near + y_2 + ... + y_L, in that order.
+// Rows outside every group of a level keep the 0 the partial vector starts with.
+// Blocks whose generator run ended in an error (info status 1..15) and block or
+// group entries outside the matrix contribute nothing.
+#include <algorithm>
+
+#include "lra_device.cuh"
+#include "lra_internal.h"
+#include "lra_profile.h"
+
+namespace lra {
+
+// Pass 1: one CTA per far block (grid-stride): t1 = R_b x[cols], a thread per
+// row of R_b (an ascending fma chain), then t = U_b t1 the same way.
+__device__ __forceinline__ int hm_kf(const lra_hmatrix& H, int64_t b) {
+  const int32_t* inf = H.info + LRA_INFO_LEN * (size_t)b;
+  if (inf[3] != LRA_OK && inf[3] < 16) return 0;
+  return max(0, min(inf[6], H.kmax));
+}
+
+__global__ void __launch_bounds__(256) hm_t_kernel(lra_hmatrix H, const double* __restrict__ x,
+                                                   double* __restrict__ t) {
+  __shared__ double t1[KMAX];
+  for (int b = blockIdx.x; b < H.nfar; b += gridDim.x) {
+    const int64_t nc = H.far[4 * (size_t)b + 3], c0 = H.far[4 * (size_t)b + 2];
+    const int kf = (c0 < 0 || nc < 0 || c0 + nc > H.n) ? 0 : hm_kf(H, b);
+    const double* R = H.R + H.far_offsets[2 * (size_t)b + 1];
+    const double* U = H.U + (size_t)b * H.kmax * H.kmax;
+    for (int a = threadIdx.x; a < kf; a += blockDim.x) {
+      double acc = 0.0;
+      for (int64_t c = 0; c < nc; ++c) acc = fma(R[(int64_t)a * nc + c], x[c0 + c], acc);
+      t1[a] = acc;
+    }
+    __syncthreads();
+    for (int a = threadIdx.x; a < kf; a += blockDim.x) {
+      double acc = 0.0;
+      for (int c = 0; c < kf; ++c) acc = fma(U[a * kf + c], t1[c], acc);
+      t[(size_t)b * H.kmax + a] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// Pass 2a: one CTA per (level, target box) group, a thread per row.
+__global__ void __launch_bounds__(256) hm_far_kernel(lra_hmatrix H, const double* __restrict__ t,
+                                                     double* __restrict__ ylev) {
+  for (int g = blockIdx.x; g < H.nfar_groups; g += gridDim.x) {
+    const int64_t* G = H.far_groups + 5 * (size_t)g;
+    const int lev = (int)G[0];
+    const int64_t r0 = G[1], nr = G[2], first = G[3], cnt = G[4];
+    if (lev < 2 || lev > H.levels || r0 < 0 || nr < 0 || r0 + nr > H.n || first < 0 || cnt < 0 ||
+        first + cnt > H.nfar)
+      continue;
+    double* yl = ylev + (size_t)(lev - 2) * H.n;
+    for (int64_t i = threadIdx.x; i < nr; i += blockDim.x) {
+      double acc = 0.0;
+      for (int64_t b = first; b < first + cnt; ++b) {
+        const int64_t br0 = H.far[4 * (size_t)b], bnr = H.far[4 * (size_t)b + 1];
+        if (br0 != r0 || bnr != nr) continue;             // a block of another box: not this group's
+        const int kf = hm_kf(H, b);
+        const double* C = H.C + H.far_offsets[2 * (size_t)b];
+        const double* tb = t + (size_t)b * H.kmax;
+        for (int a = 0; a < kf; ++a) acc = fma(C[i * kf + a], tb[a], acc);
+      }
+      yl[r0 + i] = acc;
+    }
+  }
+}
+
+// Pass 2b: one CTA per target leaf, a thread per row; entries on the fly.
+__global__ void __launch_bounds__(256) hm_near_kernel(DevProblem P, lra_hmatrix H, const double* __restrict__ x,
+                                                      double* __restrict__ ynear) {
+  for (int g = blockIdx.x; g < H.nnear_groups; g += gridDim.x) {
+    const int64_t* G = H.near_groups + 4 * (size_t)g;
+    const int64_t r0 = G[0], nr = G[1], first = G[2], cnt = G[3];
+    if (r0 < 0 || nr < 0 || r0 + nr > H.n || first < 0 || cnt < 0 || first + cnt > H.nnear) continue;
+    for (int64_t i = threadIdx.x; i < nr; i += blockDim.x) {
+      const int64_t gi = r0 + i;
+      double acc = 0.0;
+      for (int64_t b = first; b < first + cnt; ++b) {
+        const int64_t c0 = H.near[4 * (size_t)b + 2], nc = H.near[4 * (size_t)b + 3];
+        if (c0 < 0 || nc < 0 || c0 + nc > H.n) continue;
+        for (int64_t j = c0; j < c0 + nc; ++j)
+          if (j != gi) acc = fma(w_entry(P, gi, j), x[j], acc);
+      }
+      ynear[gi] = acc;
+    }
+  }
+}
+
+// Pass 3: y = y_near + y_2 + ... + y_L.
+__global__ void hm_sum_kernel(const double* __restrict__ parts, int nparts, int64_t n, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = parts[i];
+    for (int p = 1; p < nparts; ++p) acc = acc + parts[(size_t)p * n + i];
+    y[i] = acc;
+  }
+}
+
+static lra_status hm_check(const lra_hmatrix* H) {
+  if (H == nullptr || H->n < 1 || H->levels < 2 || H->kmax < 1 || H->kmax > KMAX || H->nfar < 0 ||
+      H->nfar_groups < 0 || H->nnear < 0 || H->nnear_groups < 0)
+    return LRA_ERR_INVALID_ARG;
+  if (H->nfar > 0 && (!H->far || !H->far_offsets || !H->C || !H->U || !H->R || !H->info || !H->far_groups))
+    return LRA_ERR_INVALID_ARG;
+  if (H->nnear > 0 && (!H->near || !H->near_groups)) return LRA_ERR_INVALID_ARG;
+  return LRA_OK;
+}
+
+static size_t hm_bytes(const lra_hmatrix* H) {
+  return align_up(sizeof(double) * (size_t)std::max(H->nfar, 1) * H->kmax, 256) +
+         align_up(sizeof(double) * (size_t)H->levels * H->n, 256);
+}
+
+}  // namespace lra
+
+using namespace lra;
+
+extern "C" {
+
+lra_status lra_hmatvec_workspace_size(const lra_hmatrix* H, size_t* bytes) {
+  if (bytes == nullptr) return LRA_ERR_INVALID_ARG;
+  lra_status st = hm_check(H);
+  if (st != LRA_OK) return st;
+  *bytes = hm_bytes(H);
+  return LRA_OK;
+}
+
+lra_status lra_hmatvec(const lra_problem* prob, const lra_hmatrix* H, const double* x, double* y, void* workspace,
+                       size_t workspace_bytes, lra_stream_t stream_) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  DevProblem P;
+  lra_status st = make_dev_problem(prob, nullptr, &P);
+  if (st != LRA_OK) return st;
+  if ((st = hm_check(H)) != LRA_OK) return st;
+  if (P.m != H->n || P.n != H->n || x == nullptr || y == nullptr) return LRA_ERR_INVALID_ARG;
+  const size_t need = hm_bytes(H);
+  if (workspace == nullptr || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+    return LRA_ERR_WORKSPACE;
+  DeviceInfo dev;
+  if ((st = current_device_info(&dev)) != LRA_OK) return st;
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  double* t = reinterpret_cast<double*>(ws);
+  double* parts = reinterpret_cast<double*>(ws + align_up(sizeof(double) * (size_t)std::max(H->nfar, 1) * H->kmax,
+                                                          256));
+  // parts[0] = y_near, parts[1 + lev - 2] = y_lev
+  LRA_CUDA_TRY(cudaMemsetAsync(parts, 0, sizeof(double) * (size_t)H->levels * H->n, stream));
+  const lra_hmatrix Hv = *H;
+  const int cap = dev.sms * 8;
+  if (H->nfar > 0) {
+    {
+      LaunchScope ls(stream, "hm_t_kernel");
+      hm_t_kernel<<<std::min(H->nfar, cap), 256, 0, stream>>>(Hv, x, t);
+    }
+    {
+      LaunchScope ls(stream, "hm_far_kernel");
+      hm_far_kernel<<<std::max(1, std::min(H->nfar_groups, cap)), 256, 0, stream>>>(Hv, t, parts + H->n);
+    }
+  }
+  if (H->nnear_groups > 0) {
+    LaunchScope ls(stream, "hm_near_kernel");
+    hm_near_kernel<<<std::min(H->nnear_groups, cap), 256, 0, stream>>>(P, Hv, x, parts);
+  }
+  {
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((H->n + 255) / 256, cap));
+    LaunchScope ls(stream, "hm_sum_kernel");
+    hm_sum_kernel<<<grid, 256, 0, stream>>>(parts, H->levels, H->n, y);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+}  // extern "C"

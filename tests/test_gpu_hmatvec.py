@@ -1,0 +1,67 @@
+"""y = M x for the Laplace matrix of uniform points held FMM-style (far blocks
+with batched C-A generators, dense near field) through the C ABI: against the
+oracle's matvec built from the oracle's own generators (pivots bit-exact, so
+within rounding), and against the direct product."""
+import numpy as np
+import pytest
+
+import lra_inputs as li
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+
+def build(npts, leaf, seed, k=64, stages=(28, 40, 64)):
+    import paper_1710_07946_gb300 as lra
+    p, far, near, L = li.fmm_partition(npts, leaf=leaf, seed=seed)
+    X = torch.from_numpy(p.X).cuda()
+    prob = lra.Problem.kernel("laplace", X, X)
+    I0 = li.block_initial_rows(far[:, :4], k, seed + 1)
+    hm = lra.HMatrix(prob, far, near, L, I0, k=k, stages=stages)
+    hm.build()
+    return p, far, near, L, I0, hm
+
+
+def direct_rows(P, x, rows):
+    d = np.sqrt(((P[rows, None, :] - P[None, :, :]) ** 2).sum(axis=2))
+    with np.errstate(divide="ignore"):
+        K = np.where(d > 0.0, 1.0 / d, 0.0)
+    return K @ x
+
+
+def test_matvec_matches_oracle_and_direct():
+    p, far, near, L, I0, hm = build(1 << 13, 128, 0)
+    x = li.rhs(p.m, 1, 7)[:, 0]
+    y = hm.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    info = hm.batch.out["info"].cpu().numpy()
+    assert np.all((info[:, 3] == 0) | (info[:, 3] >= 16))
+    gens = []
+    for b, (r0, nr, c0, nc, lev, tb) in enumerate(far):
+        sub = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.X[c0:c0 + nc])
+        o = oracle.ca_run_adaptive(sub, (28, 40, 64), 2, 3, I0[b], h=1.05, rank_tol=1e-6)
+        assert int(info[b, 6]) == o["k"], b
+        gens.append((o["C"], o["U"], o["R"]))
+    y_o = oracle.hmatvec(p, far, near, gens, x)
+    assert np.abs(y - y_o).max() <= 1e-10 * np.abs(y_o).max()
+    rows = np.arange(0, p.m, 7)
+    y_d = direct_rows(p.X, x, rows)
+    assert np.linalg.norm(y[rows] - y_d) <= 2e-6 * np.linalg.norm(y_d)
+
+
+def test_three_levels_against_direct_rows():
+    p, far, near, L, I0, hm = build(1 << 15, 64, 3)
+    assert L == 3
+    x = li.rhs(p.m, 1, 9)[:, 0]
+    y = hm.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    rows = np.random.default_rng(1).choice(p.m, 400, replace=False)
+    y_d = direct_rows(p.X, x, rows)
+    assert np.linalg.norm(y[rows] - y_d) <= 2e-6 * np.linalg.norm(y_d)
+    # linear in x
+    x2 = li.rhs(p.m, 1, 10)[:, 0]
+    y2 = hm.matvec(torch.from_numpy(x2).cuda()).cpu().numpy()
+    y3 = hm.matvec(torch.from_numpy(x + 2.0 * x2).cuda()).cpu().numpy()
+    assert np.abs(y3 - (y + 2.0 * y2)).max() <= 1e-12 * np.abs(y3).max()

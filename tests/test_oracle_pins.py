@@ -847,6 +847,56 @@ def test_ca_with_leverage_sampling_recovers_low_rank(kind):
         assert np.linalg.norm(p.W - o["C"] @ o["U"] @ o["R"]) <= 1e-10 * np.linalg.norm(p.W)
 
 
+# ------------------------------------------------------------------ FMM partition and matvec
+def test_fmm_partition_covers_every_entry_once_and_far_blocks_are_separated():
+    """Far blocks (interaction lists of every level) and near blocks (touching
+    leaves) cover each (i, j) exactly once; the boxes of a far block at level l
+    are at least one box side (2^-l) apart."""
+    p, far, near, L = li.fmm_partition(1 << 12, leaf=32, seed=1)
+    cov = np.zeros((p.m, p.m), dtype=np.int32)
+    for r0, nr, c0, nc, lev, tb in far:
+        cov[r0:r0 + nr, c0:c0 + nc] += 1
+        A, B = p.X[r0:r0 + nr], p.X[c0:c0 + nc]
+        gap = np.max(np.maximum(A.min(0) - B.max(0), B.min(0) - A.max(0)))
+        assert gap >= 2.0 ** -lev - 1e-12
+    for r0, nr, c0, nc, tb in near:
+        cov[r0:r0 + nr, c0:c0 + nc] += 1
+    assert cov.min() == 1 and cov.max() == 1
+    assert set(far[:, 4]) == set(range(2, L + 1))
+
+
+def _direct(P, x):
+    d = np.sqrt(((P[:, None, :] - P[None, :, :]) ** 2).sum(axis=2))
+    with np.errstate(divide="ignore"):
+        K = np.where(d > 0.0, 1.0 / d, 0.0)
+    return K @ x, K
+
+
+def test_hmatvec_with_exact_generators_is_the_dense_product():
+    p, far, near, L = li.fmm_partition(1 << 11, leaf=32, seed=2)
+    x = li.rhs(p.m, 1, 3)[:, 0]
+    y_ref, K = _direct(p.X, x)
+    gens = [(K[r0:r0 + nr, c0:c0 + nc], np.eye(nc), np.eye(nc)) for r0, nr, c0, nc, _, _ in far]
+    y = oracle.hmatvec(p, far, near, gens, x)
+    assert np.abs(y - y_ref).max() <= 1e-12 * np.abs(y_ref).max()
+
+
+def test_hmatvec_with_ca_generators_meets_the_tolerance():
+    """Generators from staged C-A runs at tol 1e-6 (the FMM recipe): the
+    matvec's relative error stays below 1e-5."""
+    p, far, near, L = li.fmm_partition(1 << 12, leaf=64, seed=3)
+    I0 = li.block_initial_rows(far[:, :4], 32, 4)
+    gens = []
+    for b, (r0, nr, c0, nc, lev, tb) in enumerate(far):
+        sub = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.X[c0:c0 + nc])
+        o = oracle.ca_run_adaptive(sub, (16, 24, 32), 2, 3, I0[b], h=1.05, rank_tol=1e-6)
+        gens.append((o["C"], o["U"], o["R"]))
+    x = li.rhs(p.m, 1, 5)[:, 0]
+    y_ref, _ = _direct(p.X, x)
+    y = oracle.hmatvec(p, far, near, gens, x)
+    assert np.linalg.norm(y - y_ref) <= 1e-5 * np.linalg.norm(y_ref)
+
+
 # ------------------------------------------------------------------ expansion/contraction cycles
 def _leverages(Rs, J):
     """s_q = b_q^T (A A^T)^{-1} b_q for every column b_q of Rs, A = Rs[:, J] (Theorem th2)."""
