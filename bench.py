@@ -514,6 +514,123 @@ class LevCaWorkload:
         return n, n, el, f"{n} complete runs (8 C-A iterations + nucleus + residual sample) of the step's {self.runs}"
 
 
+class HMatvecWorkload:
+    """The FMM's stage (iii) on the c3 recipe's point distribution: y = M x for
+    the Laplace matrix of 2^16 uniform points in [0,1]^3 (M_ii = 0), held as
+    the far blocks of every level's interaction lists with generators from one
+    batched C-A launch (staged 28/40/64, h = 1.05, tol 1e-6) plus the near field
+    of touching 128-point leaves formed on the fly.  One step = one matvec
+    (lra_hmatvec); the generator batch runs once in the set-up and is timed
+    there (config.setup_ms)."""
+    unit = "matvec/s"
+    kernel = "hm_far_kernel"
+
+    def __init__(self, npts=1 << 16, leaf=128, k=64):
+        self.npts, self.leaf, self.k = npts, leaf, k
+        self.name = f"hmatvec_laplace_{npts // 1024}K_uniform_cube_leaf{leaf}_k28-40-64_tol1e-6"
+
+    def host(self, rank):
+        p, far, near, L = li.fmm_partition(self.npts, leaf=self.leaf, seed=rank)
+        I0 = li.block_initial_rows(far[:, :4], self.k, 1 + rank)
+        x = li.rhs(p.m, 1, 2 + rank)[:, 0]
+        rows = li.rng(3).choice(p.m, 256, replace=False)
+        return dict(p=p, far=far, near=near, L=L, I0=I0, x=x, rows=rows)
+
+    def config(self, h):
+        far, near = h["far"], h["near"]
+        return {"workload": self.name, "points": self.npts, "levels": int(h["L"]), "far_blocks": int(len(far)),
+                "near_blocks": int(len(near)), "far_block_rows": [int(far[:, 1].min()), int(far[:, 1].max())],
+                "near_entries": int((near[:, 1] * near[:, 3]).sum())}
+
+    def device(self, h, dev):
+        import torch
+        import paper_1710_07946_gb300 as lra
+        X = torch.from_numpy(h["p"].X).to(dev)
+        prob = lra.Problem.kernel("laplace", X, X)
+        hm = lra.HMatrix(prob, h["far"], h["near"], h["L"], h["I0"], k=self.k)
+        hm.build()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        hm.build()
+        e1.record()
+        torch.cuda.synchronize()
+        self.setup_ms = e0.elapsed_time(e1)
+        x = torch.from_numpy(h["x"]).to(dev)
+        self._h = h
+        return dict(X=X, prob=prob, hm=hm, x=x, y=torch.empty_like(x))
+
+    def step(self, d):
+        d["hm"].matvec(d["x"], d["y"])
+
+    def check(self, d):
+        return dict(units=1, y=d["y"].cpu().numpy(), info=d["hm"].batch.out["info"].cpu().numpy())
+
+    def _direct_rows(self, h):
+        P, x, rows = h["p"].X, h["x"], h["rows"]
+        dd = np.sqrt(((P[rows, None, :] - P[None, :, :]) ** 2).sum(axis=2))
+        with np.errstate(divide="ignore"):
+            K = np.where(dd > 0.0, 1.0 / dd, 0.0)
+        return K @ x
+
+    def counts(self, h, res):
+        far, near, info = h["far"], h["near"], res["info"]
+        kf = info[:, 6].astype(np.float64)
+        # bytes each kernel must move at least: C_b (nrows x kf) read once per matvec by the far pass, R_b (kf x
+        # ncols) by the t pass; the near pass is FP64 arithmetic: ~10 flops per entry (distance, sqrt, division, fma)
+        c_bytes = 8.0 * float((far[:, 1] * kf).sum()) + 8.0 * self.npts
+        r_bytes = 8.0 * float((far[:, 3] * kf).sum()) + 8.0 * float((kf * kf).sum())
+        near_flops = 10.0 * float((near[:, 1] * near[:, 3]).sum())
+        return {"hm_far_kernel": ("hbm", c_bytes), "hm_t_kernel": ("hbm", r_bytes),
+                "hm_near_kernel": ("alu", near_flops)}
+
+    def flops(self, h, res):
+        return self.counts(h, res)["hm_near_kernel"][1]
+
+    def extra(self, res):
+        y_d = self._direct_rows(self._h)
+        err = float(np.linalg.norm(res["y"][self._h["rows"]] - y_d) / np.linalg.norm(y_d))
+        info = res["info"]
+        return {"setup_ms": self.setup_ms, "rel_err_vs_direct_256_rows": err,
+                "generator_sizes": {str(int(s)): int((info[:, 6] == s).sum()) for s in sorted(set(info[:, 6]))},
+                "statuses": sorted(set(int(x) for x in info[:, 3]))}
+
+    def e2e_setup(self, h, d):
+        import torch
+        hp = dict(x=torch.from_numpy(h["x"]).pin_memory(), y=torch.empty(self.npts, dtype=torch.float64).pin_memory())
+        return hp, hp["x"].numel() * 8, hp["y"].numel() * 8
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["x"].copy_(hp["x"], non_blocking=True)
+        self.step(d)
+        hp["y"].copy_(d["y"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def oracle_units(self, h, budget_s, seed=0):
+        """The oracle's matvec needs the oracle's generators: one block's C-A per
+        far block, so the bounded sample is the generators of as many blocks as
+        fit in the budget, scaled to one matvec's share (matvec/s of the full
+        pipeline on the host: generators + products)."""
+        import oracle
+        far, p = h["far"], h["p"]
+        order = np.random.default_rng(seed).permutation(len(far))
+        t0 = time.perf_counter()
+        n = 0
+        for idx in order:
+            r0, nr, c0, nc = (int(v) for v in far[idx, :4])
+            sub = li.Problem(li.SRC_LAPLACE, nr, nc, X=p.X[r0:r0 + nr], Y=p.X[c0:c0 + nc])
+            o = oracle.ca_run_adaptive(sub, (28, 40, 64), 2, 3, h["I0"][idx], h=1.05, rank_tol=1e-6)
+            _ = o["C"] @ (o["U"] @ (o["R"] @ h["x"][c0:c0 + nc]))
+            n += 1
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        el = time.perf_counter() - t0
+        frac = n / len(far)
+        return frac, n, el, (f"generators and products of {n} of the {len(far)} far blocks (near field not "
+                             f"included): {frac:.4f} of one matvec")
+
+
 class Hmt11Workload:
     """The single-layer Laplacian inputs of the bidiagonal pre-processing tests
     (inputs (i), [HMT11, Section 7.1]): n x n dense FP64, pre-processed by the
@@ -1100,6 +1217,7 @@ WORKLOADS = {
     "hmt11_n1024_k39_bidiag20": Hmt11Workload,
     "rhtcur_dense8192_k48": RhtcurWorkload,
     "levca_n1000_r10_k40": LevCaWorkload,
+    "hmatvec_laplace_64K": HMatvecWorkload,
     "levca_n1000_r10_k40_expected": lambda: LevCaWorkload(kind=1),
     "hmt11_n1024_k39_bidiag20_onthefly": lambda: Hmt11Workload(materialize=False),
     "hmt11_n256_k31_bidiag20": lambda: Hmt11Workload(n=256, k=31),
@@ -1374,16 +1492,27 @@ def run_lib(args, wl):
                               "speedup_of_this_line": None}
         del d2
     if rank == 0:
+        peaks = load_peaks()
+        bound, runit = "alu", "TFLOP/s"
+        if hasattr(wl, "counts"):
+            # per-kernel (bound, algorithmic amount per launch); the dominant kernel is the one with the most time
+            counts = wl.counts(h, res)
+            wl.kernel = max(counts, key=lambda kname: prof.get(kname, (0.0, 0))[0])
+            bound, amount = counts[wl.kernel]
         kms, kn = prof.get(wl.kernel, (float("nan"), 0))
         kavg = kms / max(kn, 1) / 1e3
-        flops = wl.flops(h, res)
-        achieved = flops / kavg / 1e12
+        flops = amount if bound == "hbm" else (amount if hasattr(wl, "counts") else wl.flops(h, res))
         fp32 = getattr(wl, "peak_name", "fp64") == "fp32"
-        peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
-        peak_src = ("FP32 pipe: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz = 80.5 TFLOP/s nominal (a plain FFMA loop "
-                    "measured 74)") if fp32 else ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26, nominal "
-                                                 "1.25 TFLOP/s (not in MEASURED_PEAKS.json; a plain DFMA loop measured 1.2)")
-        peaks = load_peaks()
+        if bound == "hbm":
+            achieved, peak, runit = flops / kavg / 1e9, float(peaks.get("hbm_gbs") or 6800.0), "GB/s"
+            peak_src = "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+        else:
+            achieved = flops / kavg / 1e12
+            peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+            peak_src = ("FP32 pipe: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz = 80.5 TFLOP/s nominal (a plain FFMA "
+                        "loop measured 74)") if fp32 else ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26, "
+                                                           "nominal 1.25 TFLOP/s (not in MEASURED_PEAKS.json; a plain "
+                                                           "DFMA loop measured 1.2)")
         cfg = dict(wl.config(h), l2="flushed before every step (256 MiB write, untimed)",
                    parallelism=f"{world} independent problem(s), one per GPU", mode="fp64",
                    graph_ms_per_step=graph_ms, wall_s=t_wall)
@@ -1397,11 +1526,12 @@ def run_lib(args, wl):
             "warmup": warm, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
             "config": cfg,
-            "roofline": {"bound": "alu", "kernel": wl.kernel, "achieved": achieved, "peak": peak,
-                         "unit": "TFLOP/s", "frac": achieved / peak,
+            "roofline": {"bound": bound, "kernel": wl.kernel, "achieved": achieved, "peak": peak,
+                         "unit": runit, "frac": achieved / peak,
                          "traffic": ncu_traffic(wl.kernel, wl.name),
                          "peak_source": peak_src,
-                         "flops_per_launch": flops, "avg_launch_ms": kavg * 1e3,
+                         ("bytes_per_launch" if bound == "hbm" else "flops_per_launch"): flops,
+                         "avg_launch_ms": kavg * 1e3,
                          "hbm_peak_gbs": peaks.get("hbm_gbs")},
             "kernels": {kname: {"ms_total": v[0], "launches": v[1]} for kname, v in prof.items()},
             "gpu_launches": int(launches),
