@@ -60,8 +60,11 @@ def test_three_levels_against_direct_rows():
     rows = np.random.default_rng(1).choice(p.m, 400, replace=False)
     y_d = direct_rows(p.X, x, rows)
     assert np.linalg.norm(y[rows] - y_d) <= 2e-6 * np.linalg.norm(y_d)
-    # linear in x
+    # linear in x up to rounding (sums of 1/r terms up to ~1e3 in the near field)
     x2 = li.rhs(p.m, 1, 10)[:, 0]
     y2 = hm.matvec(torch.from_numpy(x2).cuda()).cpu().numpy()
     y3 = hm.matvec(torch.from_numpy(x + 2.0 * x2).cuda()).cpu().numpy()
-    assert np.abs(y3 - (y + 2.0 * y2)).max() <= 1e-12 * np.abs(y3).max()
+    assert np.abs(y3 - (y + 2.0 * y2)).max() <= 1e-9 * np.abs(y3).max()
+    # the same x twice: bit-identical (fixed summation order)
+    y4 = hm.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    np.testing.assert_array_equal(y4, y)
