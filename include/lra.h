@@ -527,13 +527,17 @@ lra_status lra_ca_lev_batched(const lra_problem* base, const lra_batch* batch, i
  * pairs of every octree level, their generators C_b U_b R_b the outputs of
  * lra_ca_run_batched on them; the near blocks are the touching leaf pairs,
  * whose entries are formed on the fly (the diagonal i = j skipped).
- * Per far block t_b = U_b (R_b x[cols]) (kf_b values, ascending fma chains);
- * per (level, target box) group, row i of the box gets y_lev[i] = sum over the
+ * Per far block t_b = U_b (R_b x[cols]) (R_b x by a warp per row: lane-strided
+ * fma partial sums and a fixed butterfly; U_b t1 by ascending fma chains); per
+ * (level, target box) group, row i of the box gets y_lev[i] = sum over the
  * group's blocks in order of sum_a C_b[i][a] t_b[a] (one fma chain); per near
- * group (target leaf) y_near[i] = sum over its blocks in order, columns j
- * ascending, of fma(w_ij, x_j, .); finally y = y_near + y_2 + ... + y_L in that
- * order (rows in no group of a level add 0).
- * prob: the kernel problem (X = Y, m = n).  H (device arrays, caller-owned):
+ * group (target leaf) y_near[i] = the sum over its blocks in order, columns j
+ * ascending, of w_ij x_j with w_ij = rsqrt(|x_i - x_j|^2) (within an ulp of
+ * 1/|x_i - x_j|), in two interleaved accumulators added at the end; finally
+ * y = y_near + y_2 + ... + y_L in that order (rows in no group of a level add
+ * 0).  The order of every sum is fixed: repeated calls give identical bits.
+ * Blocks whose generator run ended in an error contribute nothing.
+ * prob: a Laplace kernel problem (X = Y, m = n).  H (device arrays, caller-owned):
  * far (nfar x 4: row0, nrows, col0, ncols), far_offsets (nfar x 2: offsets of
  * C_b and R_b in C and R), C, U (nfar x kmax x kmax, kf_b x kf_b used), R,
  * info (nfar x LRA_INFO_LEN; kf_b = info[6]) -- the batch's outputs;

@@ -4,7 +4,7 @@
 //   1. per far block, t_b = U_b (R_b x[cols]);
 //   2. per (level, target box), each row's fma chain over the box's blocks in
 //      order, C_b[i][:] . t_b, into the level's partial vector; per target
-//      leaf, the near field's fma chain over the source leaves in order;
+//      leaf, the near field's sums over the source leaves in order;
 //   3. y = y_near + y_2 + ... + y_L, in that order.
 // Rows outside every group of a level keep the 0 the partial vector starts with.
 // Blocks whose generator run ended in an error (info status 1..15) and block or
@@ -28,15 +28,18 @@ __device__ __forceinline__ int hm_kf(const lra_hmatrix& H, int64_t b) {
 __global__ void __launch_bounds__(256) hm_t_kernel(lra_hmatrix H, const double* __restrict__ x,
                                                    double* __restrict__ t) {
   __shared__ double t1[KMAX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int b = blockIdx.x; b < H.nfar; b += gridDim.x) {
     const int64_t nc = H.far[4 * (size_t)b + 3], c0 = H.far[4 * (size_t)b + 2];
     const int kf = (c0 < 0 || nc < 0 || c0 + nc > H.n) ? 0 : hm_kf(H, b);
     const double* R = H.R + H.far_offsets[2 * (size_t)b + 1];
     const double* U = H.U + (size_t)b * H.kmax * H.kmax;
-    for (int a = threadIdx.x; a < kf; a += blockDim.x) {
+    // a warp per row of R_b: lane-strided partial sums (coalesced), then a fixed butterfly
+    for (int a = warp; a < kf; a += nw) {
       double acc = 0.0;
-      for (int64_t c = 0; c < nc; ++c) acc = fma(R[(int64_t)a * nc + c], x[c0 + c], acc);
-      t1[a] = acc;
+      for (int64_t c = lane; c < nc; c += 32) acc = fma(R[(int64_t)a * nc + c], x[c0 + c], acc);
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+      if (lane == 0) t1[a] = acc;
     }
     __syncthreads();
     for (int a = threadIdx.x; a < kf; a += blockDim.x) {
@@ -74,8 +77,11 @@ __global__ void __launch_bounds__(256) hm_far_kernel(lra_hmatrix H, const double
   }
 }
 
-// Pass 2b: one CTA per target leaf, a thread per row; entries on the fly.
-__global__ void __launch_bounds__(256) hm_near_kernel(DevProblem P, lra_hmatrix H, const double* __restrict__ x,
+// Pass 2b: one CTA of 128 threads per target leaf, a thread per row; entries
+// on the fly as rsqrt(r2) (the FP64 reciprocal square root, within an ulp of
+// 1/sqrt(r2)), the source points taken in order with two interleaved
+// accumulators (even and odd positions of the leaf's source list) added at the end.
+__global__ void __launch_bounds__(128) hm_near_kernel(DevProblem P, lra_hmatrix H, const double* __restrict__ x,
                                                       double* __restrict__ ynear) {
   for (int g = blockIdx.x; g < H.nnear_groups; g += gridDim.x) {
     const int64_t* G = H.near_groups + 4 * (size_t)g;
@@ -83,14 +89,21 @@ __global__ void __launch_bounds__(256) hm_near_kernel(DevProblem P, lra_hmatrix 
     if (r0 < 0 || nr < 0 || r0 + nr > H.n || first < 0 || cnt < 0 || first + cnt > H.nnear) continue;
     for (int64_t i = threadIdx.x; i < nr; i += blockDim.x) {
       const int64_t gi = r0 + i;
-      double acc = 0.0;
+      const double xi = P.X[3 * gi], yi = P.X[3 * gi + 1], zi = P.X[3 * gi + 2];
+      double acc0 = 0.0, acc1 = 0.0;
+      int par = 0;
       for (int64_t b = first; b < first + cnt; ++b) {
         const int64_t c0 = H.near[4 * (size_t)b + 2], nc = H.near[4 * (size_t)b + 3];
         if (c0 < 0 || nc < 0 || c0 + nc > H.n) continue;
-        for (int64_t j = c0; j < c0 + nc; ++j)
-          if (j != gi) acc = fma(w_entry(P, gi, j), x[j], acc);
+        for (int64_t j = c0; j < c0 + nc; ++j, par ^= 1) {
+          const double dx = xi - P.Y[3 * j], dy = yi - P.Y[3 * j + 1], dz = zi - P.Y[3 * j + 2];
+          const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+          const double w = (j == gi) ? 0.0 : rsqrt(r2);
+          if (par) acc1 = fma(w, x[j], acc1);
+          else acc0 = fma(w, x[j], acc0);
+        }
       }
-      ynear[gi] = acc;
+      ynear[gi] = acc0 + acc1;
     }
   }
 }
@@ -140,7 +153,8 @@ lra_status lra_hmatvec(const lra_problem* prob, const lra_hmatrix* H, const doub
   lra_status st = make_dev_problem(prob, nullptr, &P);
   if (st != LRA_OK) return st;
   if ((st = hm_check(H)) != LRA_OK) return st;
-  if (P.m != H->n || P.n != H->n || x == nullptr || y == nullptr) return LRA_ERR_INVALID_ARG;
+  if (P.src != LRA_KERNEL_LAPLACE || P.m != H->n || P.n != H->n || x == nullptr || y == nullptr)
+    return LRA_ERR_INVALID_ARG;
   const size_t need = hm_bytes(H);
   if (workspace == nullptr || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u))
     return LRA_ERR_WORKSPACE;
@@ -166,7 +180,7 @@ lra_status lra_hmatvec(const lra_problem* prob, const lra_hmatrix* H, const doub
   }
   if (H->nnear_groups > 0) {
     LaunchScope ls(stream, "hm_near_kernel");
-    hm_near_kernel<<<std::min(H->nnear_groups, cap), 256, 0, stream>>>(P, Hv, x, parts);
+    hm_near_kernel<<<std::min(H->nnear_groups, dev.sms * 16), 128, 0, stream>>>(P, Hv, x, parts);
   }
   {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((H->n + 255) / 256, cap));
