@@ -108,18 +108,39 @@ __device__ void lev_jacobi(double* G, double* Q, double* cs, int k) {
 // Scores v_j of the n columns of the kS x n sketch S (global, row-major) for
 // rank r: Gram matrix, Jacobi, top eigenpairs, squared projections.  Returns
 // the number of eigenpairs used (in every thread).
-__device__ int lev_scores(const double* S, int kS, int64_t n, int r, double* G, double* Q, double* cs, int* sel,
-                          int* s_re, double* v) {
+__device__ int lev_scores(const double* S, int kS, int64_t n, int r, double* G, double* Q, double* tile, double* cs,
+                          int* sel, int* s_re, double* v) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int npair = kS * (kS + 1) / 2;
+  // Gram matrix over 32-column tiles of S staged in shared memory (tile: kS x
+  // 33 doubles): every entry is still one ascending chain over the columns
   for (int e = tid; e < npair; e += nt) {
     int a = 0, rem = e;
     while (rem >= kS - a) { rem -= kS - a; ++a; }
-    const int b = a + rem;
-    double acc = 0.0;
-    for (int64_t j = 0; j < n; ++j) acc = fma(S[(int64_t)a * n + j], S[(int64_t)b * n + j], acc);
-    G[a * kS + b] = acc;
-    G[b * kS + a] = acc;
+    G[a * kS + a + rem] = 0.0;
+  }
+  for (int64_t j0 = 0; j0 < n; j0 += 32) {
+    const int w = (int)min((int64_t)32, n - j0);
+    __syncthreads();
+    for (int e = tid; e < kS * 32; e += nt) {
+      const int a = e >> 5, jj = e & 31;
+      tile[a * 33 + jj] = jj < w ? S[(int64_t)a * n + j0 + jj] : 0.0;
+    }
+    __syncthreads();
+    for (int e = tid; e < npair; e += nt) {
+      int a = 0, rem = e;
+      while (rem >= kS - a) { rem -= kS - a; ++a; }
+      const int b = a + rem;
+      double acc = G[a * kS + b];
+      for (int jj = 0; jj < w; ++jj) acc = fma(tile[a * 33 + jj], tile[b * 33 + jj], acc);
+      G[a * kS + b] = acc;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < npair; e += nt) {
+    int a = 0, rem = e;
+    while (rem >= kS - a) { rem -= kS - a; ++a; }
+    G[(a + rem) * kS + a] = G[a * kS + a + rem];
   }
   __syncthreads();
   lev_jacobi(G, Q, cs, kS);
@@ -229,6 +250,7 @@ __global__ void __launch_bounds__(NT, 1) lev_batched_kernel(LevArgs B) {
   const int tid = threadIdx.x, nt = blockDim.x, k = B.k;
   double* Gs = reinterpret_cast<double*>(smem);               // k x k
   double* Qs = Gs + (size_t)k * k;                             // k x k
+  double* Ts = Qs + (size_t)k * k;                             // k x 33: Gram tiles
   double* S = B.scratch + (size_t)blockIdx.x * B.scratch_stride;
   double* v = S + (size_t)k * B.max_len;
   double* cum = v + B.max_len;
@@ -290,7 +312,7 @@ __global__ void __launch_bounds__(NT, 1) lev_batched_kernel(LevArgs B) {
         }
         __syncthreads();
         if (s_bad) { st = LRA_ERR_NONFINITE; break; }
-        const int re = lev_scores(S, kS, len, min(B.r, kS), Gs, Qs, s_cs, s_sel, &s_re, v);
+        const int re = lev_scores(S, kS, len, min(B.r, kS), Gs, Qs, Ts, s_cs, s_sel, &s_re, v);
         if (re == 0) st = max(st, (int)LRA_WARN_RANK_DEFICIENT);
         const double* u = ub + (size_t)(2 * it + dir) * B.max_len;
         const int cnt = lev_sample(v, len, k, B.kind, u, cum, flags, dir == 0 ? s_J : s_I, &s_cnt, &s_tot, &s_last);
@@ -362,7 +384,7 @@ static lra_status lev_plan(int k, int64_t max_len, LevPlan* pl) {
   DeviceInfo dev;
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
-  const size_t need = std::max(2 * sizeof(double) * (size_t)k * k, nucleus_rect_smem_bytes(k, k));
+  const size_t need = std::max(sizeof(double) * (2 * (size_t)k * k + 33 * (size_t)k), nucleus_rect_smem_bytes(k, k));
   if (need > dev.smem_optin - 8192) return LRA_ERR_INVALID_ARG;
   LRA_CUDA_TRY(cudaFuncSetAttribute(lev_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
   int occ = 0;
