@@ -1099,7 +1099,10 @@ static void jac_pair(int32_t kp, int32_t t, int32_t i, int32_t* p, int32_t* q) {
  * c = 1 / sqrt(1 + t^2), s = t c (the classical symmetric Schur rotation that
  * zeroes G[p][q]); then all row pairs (row p <- c row_p - s row_q, row q <-
  * s row_p + c row_q), then all column pairs the same way, then the columns of
- * Q (Q starts as I).  On return G is diagonal to rounding and G_in = Q G Q^T.
+ * Q (Q starts as I).  After each sweep the iteration stops when the largest
+ * |G[p][q]|, p < q, is at most 2^-60 times the largest |G[p][p]| (a maximum of
+ * absolute values, the same in any order of evaluation).  On return G is
+ * diagonal to rounding and G_in = Q G Q^T.
  */
 void orc_jacobi_eig(double* G, double* Q, int32_t k) {
   int32_t kp = k + (k & 1);
@@ -1107,7 +1110,7 @@ void orc_jacobi_eig(double* G, double* Q, int32_t k) {
   double* cs = (double*)malloc(sizeof(double) * 2 * (size_t)(half > 0 ? half : 1));
   for (int32_t i = 0; i < k; ++i)
     for (int32_t j = 0; j < k; ++j) Q[i * k + j] = (i == j) ? 1.0 : 0.0;
-  for (int32_t sw = 0; sw < ORC_JAC_SWEEPS; ++sw)
+  for (int32_t sw = 0; sw < ORC_JAC_SWEEPS; ++sw) {
     for (int32_t t = 0; t < kp - 1; ++t) {
       for (int32_t i = 0; i < half; ++i) {
         int32_t p, q;
@@ -1149,6 +1152,14 @@ void orc_jacobi_eig(double* G, double* Q, int32_t k) {
         }
       }
     }
+    double off = 0.0, dmax = 0.0;
+    for (int32_t p = 0; p < k; ++p) {
+      if (fabs(G[p * k + p]) > dmax) dmax = fabs(G[p * k + p]);
+      for (int32_t q = p + 1; q < k; ++q)
+        if (fabs(G[p * k + q]) > off) off = fabs(G[p * k + q]);
+    }
+    if (off <= ldexp(1.0, -60) * dmax) break;
+  }
   free(cs);
 }
 
