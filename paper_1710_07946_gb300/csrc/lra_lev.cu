@@ -55,13 +55,15 @@ __device__ __forceinline__ void lev_pair(int kp, int t, int i, int& p, int& q) {
 
 // Round-robin Jacobi on the symmetric k x k G (shared, row-major, ld k): every
 // rotation of a round from G at the round's start, then all row pairs, then all
-// column pairs and the columns of Q.
-__device__ void lev_jacobi(double* G, double* Q, double* cs, int k) {
+// column pairs and the columns of Q; after each sweep, stop when the largest
+// off-diagonal |G| is at most 2^-60 times the largest diagonal |G| (maxima of
+// absolute values: the same decision in any evaluation order).
+__device__ void lev_jacobi(double* G, double* Q, double* cs, double* red, int k) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int kp = k + (k & 1), half = kp / 2;
   for (int e = tid; e < k * k; e += nt) Q[e] = (e / k == e % k) ? 1.0 : 0.0;
   __syncthreads();
-  for (int sw = 0; sw < LEV_JAC_SWEEPS; ++sw)
+  for (int sw = 0; sw < LEV_JAC_SWEEPS; ++sw) {
     for (int t = 0; t < kp - 1; ++t) {
       for (int i = tid; i < half; i += nt) {
         int p, q;
@@ -103,6 +105,24 @@ __device__ void lev_jacobi(double* G, double* Q, double* cs, int k) {
       }
       __syncthreads();
     }
+    double off = 0.0, dmax = 0.0;
+    for (int e = tid; e < k * k; e += nt) {
+      const int p = e / k, q = e - p * k;
+      if (p == q) dmax = fmax(dmax, fabs(G[e]));
+      else if (p < q) off = fmax(off, fabs(G[e]));
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off = fmax(off, __shfl_xor_sync(0xffffffffu, off, o));
+      dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+    }
+    if ((tid & 31) == 0) { red[2 * (tid >> 5)] = off; red[2 * (tid >> 5) + 1] = dmax; }
+    __syncthreads();
+    off = 0.0;
+    dmax = 0.0;
+    for (int w = 0; w < (nt >> 5); ++w) { off = fmax(off, red[2 * w]); dmax = fmax(dmax, red[2 * w + 1]); }
+    __syncthreads();
+    if (off <= ldexp(1.0, -60) * dmax) break;
+  }
 }
 
 // Scores v_j of the n columns of the kS x n sketch S (global, row-major) for
@@ -143,7 +163,7 @@ __device__ int lev_scores(const double* S, int kS, int64_t n, int r, double* G, 
     G[(a + rem) * kS + a] = G[a * kS + a + rem];
   }
   __syncthreads();
-  lev_jacobi(G, Q, cs, kS);
+  lev_jacobi(G, Q, cs, tile, kS);
   if (tid == 0) {
     int re = 0;
     double dmax = 0.0;
