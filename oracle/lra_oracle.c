@@ -1100,7 +1100,7 @@ static void jac_pair(int32_t kp, int32_t t, int32_t i, int32_t* p, int32_t* q) {
  * zeroes G[p][q]); then all row pairs (row p <- c row_p - s row_q, row q <-
  * s row_p + c row_q), then all column pairs the same way, then the columns of
  * Q (Q starts as I).  After each sweep the iteration stops when the largest
- * |G[p][q]|, p < q, is at most 2^-60 times the largest |G[p][p]| (a maximum of
+ * |G[p][q]|, p < q, is at most 2^-48 times the largest |G[p][p]| (a maximum of
  * absolute values, the same in any order of evaluation).  On return G is
  * diagonal to rounding and G_in = Q G Q^T.
  */
@@ -1158,7 +1158,7 @@ void orc_jacobi_eig(double* G, double* Q, int32_t k) {
       for (int32_t q = p + 1; q < k; ++q)
         if (fabs(G[p * k + q]) > off) off = fabs(G[p * k + q]);
     }
-    if (off <= ldexp(1.0, -60) * dmax) break;
+    if (off <= ldexp(1.0, -48) * dmax) break;
   }
   free(cs);
 }
