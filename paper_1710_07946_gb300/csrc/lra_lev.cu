@@ -56,7 +56,7 @@ __device__ __forceinline__ void lev_pair(int kp, int t, int i, int& p, int& q) {
 // Round-robin Jacobi on the symmetric k x k G (shared, row-major, ld k): every
 // rotation of a round from G at the round's start, then all row pairs, then all
 // column pairs and the columns of Q; after each sweep, stop when the largest
-// off-diagonal |G| is at most 2^-60 times the largest diagonal |G| (maxima of
+// off-diagonal |G| is at most 2^-48 times the largest diagonal |G| (maxima of
 // absolute values: the same decision in any evaluation order).
 __device__ void lev_jacobi(double* G, double* Q, double* cs, double* red, int k) {
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -121,7 +121,7 @@ __device__ void lev_jacobi(double* G, double* Q, double* cs, double* red, int k)
     dmax = 0.0;
     for (int w = 0; w < (nt >> 5); ++w) { off = fmax(off, red[2 * w]); dmax = fmax(dmax, red[2 * w + 1]); }
     __syncthreads();
-    if (off <= ldexp(1.0, -60) * dmax) break;
+    if (off <= ldexp(1.0, -48) * dmax) break;
   }
 }
 
