@@ -68,3 +68,27 @@ def test_three_levels_against_direct_rows():
     # the same x twice: bit-identical (fixed summation order)
     y4 = hm.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
     np.testing.assert_array_equal(y4, y)
+
+
+def test_benchmark_size_sampled_blocks_and_rows():
+    """The benchmark's partition (2^16 points, 128-point leaves, 56,448 far
+    blocks): 60 randomly chosen far blocks' generators against the oracle (pivots,
+    sizes and gathered factors bit-exact), the matvec against direct rows."""
+    p, far, near, L, I0, hm = build(1 << 16, 128, 0)
+    b = hm.batch
+    rng = np.random.default_rng(5)
+    for idx in rng.choice(len(far), 60, replace=False):
+        r0, nr, c0, nc = (int(v) for v in far[idx, :4])
+        sub = li.Problem(li.SRC_LAPLACE, nr, nc, X=p.X[r0:r0 + nr], Y=p.X[c0:c0 + nc])
+        o = oracle.ca_run_adaptive(sub, (28, 40, 64), 2, 3, I0[idx], h=1.05, rank_tol=1e-6)
+        g = b.block(int(idx))
+        assert (g["k"], g["status"], g["rank"]) == (o["k"], o["status"], o["rank"]), idx
+        np.testing.assert_array_equal(g["I"], o["I"])
+        np.testing.assert_array_equal(g["J"], o["J"])
+        np.testing.assert_array_equal(g["C"], o["C"])
+        np.testing.assert_array_equal(g["R"], o["R"])
+    x = li.rhs(p.m, 1, 2)[:, 0]
+    y = hm.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    rows = rng.choice(p.m, 256, replace=False)
+    y_d = direct_rows(p.X, x, rows)
+    assert np.linalg.norm(y[rows] - y_d) <= 2e-6 * np.linalg.norm(y_d)

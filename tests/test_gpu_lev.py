@@ -75,3 +75,10 @@ def test_hmt11_laplacian_and_exact_low_rank():
 def test_laplace_kernel_blocks():
     p, blocks, lev = li.fmm_blocks(npts=1 << 14, leaf=64, min_size=64, max_size=2048, nblocks=24, seed=4)
     run(p, blocks, 16, 8, 4, 0, seed=11)
+
+
+def test_benchmark_configuration_sampled_runs():
+    """The benchmark's configuration (1000 x 1000 of numerical rank 10, k = 40,
+    r = 10, eight iterations, Exactly) on 8 runs, all compared."""
+    p = li.dense_lowrank(1000, 1000, r=10, noise=1e-9, seed=0)
+    run(p, [[0, 1000, 0, 1000]] * 8, 40, 10, 8, 0, seed=77)
