@@ -53,34 +53,12 @@ __device__ __forceinline__ void lev_pair(int kp, int t, int i, int& p, int& q) {
   q = a < b ? b : a;
 }
 
-// Jacobi rotation data of one round (shared): per pair i its indices, cosine,
-// sine and tangent; per index its pair.
-struct JacRound {
-  int* p;
-  int* q;
-  double* c;
-  double* s;
-  double* t;
-  int* pairof;
-};
-
-// Row a of J^T G at column y (the oracle's fma forms); a without a partner: G[a][y].
-__device__ __forceinline__ double jac_row(const double* G, int k, const JacRound& R, int i, int a, int y) {
-  const int p = R.p[i], q = R.q[i];
-  if (q >= k) return G[a * k + y];
-  const double gp = G[p * k + y], gq = G[q * k + y];
-  return (a == p) ? fma(R.c[i], gp, -(R.s[i] * gq)) : fma(R.s[i], gp, R.c[i] * gq);
-}
-
-// Round-robin Jacobi on the symmetric k x k G (shared, row-major, ld k), the
-// oracle's rounds: every rotation from G at the round's start, then the new G
-// = J^T G J written into the other buffer in one pass (entry (a, b), a < b, the
-// column rotation of b's pair applied to a's two row rotations, mirrored;
-// within a pair the Rutishauser form), and Q's column rotations; after each
-// sweep, stop when the largest off-diagonal |G| is at most 2^-48 times the
-// largest diagonal |G| (maxima of absolute values: the same decision in any
-// evaluation order).  Returns the buffer holding the final G.
-__device__ double* lev_jacobi(double* G, double* G2, double* Q, const JacRound& R, double* red, int k) {
+// Round-robin Jacobi on the symmetric k x k G (shared, row-major, ld k): every
+// rotation of a round from G at the round's start, then all row pairs, then all
+// column pairs and the columns of Q; after each sweep, stop when the largest
+// off-diagonal |G| is at most 2^-48 times the largest diagonal |G| (maxima of
+// absolute values: the same decision in any evaluation order).
+__device__ void lev_jacobi(double* G, double* Q, double* cs, double* red, int k) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int kp = k + (k & 1), half = kp / 2;
   for (int e = tid; e < k * k; e += nt) Q[e] = (e / k == e % k) ? 1.0 : 0.0;
@@ -88,58 +66,44 @@ __device__ double* lev_jacobi(double* G, double* G2, double* Q, const JacRound& 
   for (int sw = 0; sw < LEV_JAC_SWEEPS; ++sw) {
     for (int t = 0; t < kp - 1; ++t) {
       for (int i = tid; i < half; i += nt) {
-        const int a = (i == 0) ? 0 : 1 + (t + i) % (kp - 1);
-        const int b = 1 + (t + kp - 1 - i) % (kp - 1);
-        const int p = a < b ? a : b, q = a < b ? b : a;
-        double c = 1.0, sn = 0.0, tt = 0.0;
+        int p, q;
+        lev_pair(kp, t, i, p, q);
+        double c = 1.0, sn = 0.0;
         if (q < k && G[p * k + q] != 0.0) {
           const double tau = (G[q * k + q] - G[p * k + p]) / (2.0 * G[p * k + q]);
-          tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
           c = 1.0 / sqrt(1.0 + tt * tt);
           sn = tt * c;
         }
-        R.p[i] = p; R.q[i] = q; R.c[i] = c; R.s[i] = sn; R.t[i] = tt;
-        R.pairof[p] = i;
-        R.pairof[q] = i;
+        cs[2 * i] = c;
+        cs[2 * i + 1] = sn;
       }
       __syncthreads();
-      for (int e = tid; e < k * k; e += nt) {
-        const int a = e / k, b = e - a * k;
-        if (a > b) continue;
-        const int ia = R.pairof[a];
-        if (a == b) {
-          const int q = R.q[ia];
-          if (q < k) {
-            const double gpq = G[R.p[ia] * k + q];
-            G2[e] = (a == R.p[ia]) ? G[e] - R.t[ia] * gpq : G[e] + R.t[ia] * gpq;
-          } else {
-            G2[e] = G[e];
-          }
-          continue;
-        }
-        const int ib = R.pairof[b];
-        double v;
-        if (ia == ib) {
-          v = 0.0;
-        } else if (R.q[ib] >= k) {
-          v = jac_row(G, k, R, ia, a, b);
-        } else {
-          const double xp = jac_row(G, k, R, ia, a, R.p[ib]), xq = jac_row(G, k, R, ia, a, R.q[ib]);
-          v = (b == R.p[ib]) ? fma(R.c[ib], xp, -(R.s[ib] * xq)) : fma(R.s[ib], xp, R.c[ib] * xq);
-        }
-        G2[e] = v;
-        G2[b * k + a] = v;
-      }
       for (int e = tid; e < half * k; e += nt) {
         const int i = e / k, j = e - i * k;
-        const int p = R.p[i], q = R.q[i];
+        int p, q;
+        lev_pair(kp, t, i, p, q);
         if (q >= k) continue;
-        const double x = Q[j * k + p], y = Q[j * k + q];
-        Q[j * k + p] = fma(R.c[i], x, -(R.s[i] * y));
-        Q[j * k + q] = fma(R.s[i], x, R.c[i] * y);
+        const double c = cs[2 * i], sn = cs[2 * i + 1];
+        const double x = G[p * k + j], y = G[q * k + j];
+        G[p * k + j] = c * x - sn * y;
+        G[q * k + j] = sn * x + c * y;
       }
       __syncthreads();
-      double* tmp = G; G = G2; G2 = tmp;
+      for (int e = tid; e < half * k; e += nt) {
+        const int i = e / k, j = e - i * k;
+        int p, q;
+        lev_pair(kp, t, i, p, q);
+        if (q >= k) continue;
+        const double c = cs[2 * i], sn = cs[2 * i + 1];
+        const double x = G[j * k + p], y = G[j * k + q];
+        G[j * k + p] = c * x - sn * y;
+        G[j * k + q] = sn * x + c * y;
+        const double xq = Q[j * k + p], yq = Q[j * k + q];
+        Q[j * k + p] = c * xq - sn * yq;
+        Q[j * k + q] = sn * xq + c * yq;
+      }
+      __syncthreads();
     }
     double off = 0.0, dmax = 0.0;
     for (int e = tid; e < k * k; e += nt) {
@@ -159,14 +123,13 @@ __device__ double* lev_jacobi(double* G, double* G2, double* Q, const JacRound& 
     __syncthreads();
     if (off <= ldexp(1.0, -48) * dmax) break;
   }
-  return G;
 }
 
 // Scores v_j of the n columns of the kS x n sketch S (global, row-major) for
 // rank r: Gram matrix, Jacobi, top eigenpairs, squared projections.  Returns
 // the number of eigenpairs used (in every thread).
-__device__ int lev_scores(const double* S, int kS, int64_t n, int r, double* G, double* G2, double* Q, double* tile,
-                          const JacRound& R, int* sel, int* s_re, double* v) {
+__device__ int lev_scores(const double* S, int kS, int64_t n, int r, double* G, double* Q, double* tile, double* cs,
+                          int* sel, int* s_re, double* v) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int npair = kS * (kS + 1) / 2;
   // Gram matrix over 32-column tiles of S staged in shared memory (tile: kS x
@@ -200,7 +163,7 @@ __device__ int lev_scores(const double* S, int kS, int64_t n, int r, double* G, 
     G[(a + rem) * kS + a] = G[a * kS + a + rem];
   }
   __syncthreads();
-  G = lev_jacobi(G, G2, Q, R, tile, kS);
+  lev_jacobi(G, Q, cs, tile, kS);
   if (tid == 0) {
     int re = 0;
     double dmax = 0.0;
@@ -301,16 +264,13 @@ __global__ void __launch_bounds__(NT, 1) lev_batched_kernel(LevArgs B) {
   __shared__ int s_b, s_re, s_cnt, s_bad;
   __shared__ double s_tot;
   __shared__ long long s_last;
-  __shared__ int s_rp[KMAX / 2], s_rq[KMAX / 2], s_pairof[KMAX];
-  __shared__ double s_rc[KMAX / 2], s_rs[KMAX / 2], s_rt[KMAX / 2];
+  __shared__ double s_cs[KMAX + 2];
   __shared__ int s_sel[KMAX];
   __shared__ int32_t s_I[KMAX], s_J[KMAX];
   const int tid = threadIdx.x, nt = blockDim.x, k = B.k;
   double* Gs = reinterpret_cast<double*>(smem);               // k x k
-  double* G2s = Gs + (size_t)k * k;                            // k x k: the other Jacobi buffer
-  double* Qs = G2s + (size_t)k * k;                            // k x k
+  double* Qs = Gs + (size_t)k * k;                             // k x k
   double* Ts = Qs + (size_t)k * k;                             // k x 33: Gram tiles
-  const JacRound JR{s_rp, s_rq, s_rc, s_rs, s_rt, s_pairof};
   double* S = B.scratch + (size_t)blockIdx.x * B.scratch_stride;
   double* v = S + (size_t)k * B.max_len;
   double* cum = v + B.max_len;
@@ -372,7 +332,7 @@ __global__ void __launch_bounds__(NT, 1) lev_batched_kernel(LevArgs B) {
         }
         __syncthreads();
         if (s_bad) { st = LRA_ERR_NONFINITE; break; }
-        const int re = lev_scores(S, kS, len, min(B.r, kS), Gs, G2s, Qs, Ts, JR, s_sel, &s_re, v);
+        const int re = lev_scores(S, kS, len, min(B.r, kS), Gs, Qs, Ts, s_cs, s_sel, &s_re, v);
         if (re == 0) st = max(st, (int)LRA_WARN_RANK_DEFICIENT);
         const double* u = ub + (size_t)(2 * it + dir) * B.max_len;
         const int cnt = lev_sample(v, len, k, B.kind, u, cum, flags, dir == 0 ? s_J : s_I, &s_cnt, &s_tot, &s_last);
@@ -444,7 +404,7 @@ static lra_status lev_plan(int k, int64_t max_len, LevPlan* pl) {
   DeviceInfo dev;
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
-  const size_t need = std::max(sizeof(double) * (3 * (size_t)k * k + 33 * (size_t)k), nucleus_rect_smem_bytes(k, k));
+  const size_t need = std::max(sizeof(double) * (2 * (size_t)k * k + 33 * (size_t)k), nucleus_rect_smem_bytes(k, k));
   if (need > dev.smem_optin - 8192) return LRA_ERR_INVALID_ARG;
   LRA_CUDA_TRY(cudaFuncSetAttribute(lev_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
   int occ = 0;
