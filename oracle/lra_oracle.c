@@ -1089,43 +1089,25 @@ static void jac_pair(int32_t kp, int32_t t, int32_t i, int32_t* p, int32_t* q) {
   *q = a < b ? b : a;
 }
 
-/* The rotation of index a in round t: its pair (partner index, role) with
- * cosine c and sine s; an index without a partner (k odd) keeps c = 1, s = 0. */
-typedef struct { int32_t p, q; double c, s, t; } jac_rot;
-
-/* Row a of J^T G restricted to column y: c g_p - s g_q (a = p) or s g_p + c g_q
- * (a = q), as fma(c, g_p, -(s g_q)) and fma(s, g_p, c g_q); a without a
- * partner: g_a unchanged. */
-static double jac_row(const double* G, int32_t k, const jac_rot* r, int32_t a, int32_t y) {
-  if (r->q >= k) return G[a * k + y];
-  double gp = G[r->p * k + y], gq = G[r->q * k + y];
-  return (a == r->p) ? fma(r->c, gp, -(r->s * gq)) : fma(r->s, gp, r->c * gq);
-}
-
 /*
  * orc_jacobi_eig: eigen-decomposition of a symmetric k x k G (row-major, in
- * place) by at most ORC_JAC_SWEEPS sweeps of Jacobi rotations in the
- * round-robin order (k rounded up to even kp; an index paired with kp - 1 >= k
- * has no partner in that round).  In each round every rotation comes from G at
- * the round's start: for G[p][q] != 0, tau = (G[q][q] - G[p][p]) / (2 G[p][q]),
- * t = sign(tau) / (|tau| + sqrt(1 + tau^2)), c = 1 / sqrt(1 + t^2), s = t c
- * (the classical symmetric Schur rotation); otherwise c = 1, s = t = 0.  The
- * new G = J^T G J is then formed from the old one: for a < b in different
- * pairs, entry (a, b) is the column rotation of b's pair applied to the two row
- * rotations jac_row(a, p_b), jac_row(a, q_b) (the same fma forms), mirrored to
- * (b, a); within a pair G[p][q] = G[q][p] = 0, G[p][p] -= t G[p][q],
- * G[q][q] += t G[p][q] (Rutishauser's form of the same rotation).  Q (starting
- * at I) gets the column rotations in the fma forms.  After each sweep the
- * iteration stops when the largest |G[p][q]|, p < q, is at most 2^-48 times the
- * largest |G[p][p]| (a maximum of absolute values, the same in any order of
- * evaluation).  On return G is diagonal to rounding and G_in = Q G Q^T.
+ * place) by ORC_JAC_SWEEPS sweeps of Jacobi rotations in the round-robin
+ * order (k rounded up to even kp; pairs with an index >= k are skipped).  In
+ * each round every rotation is computed from G as it stands at the round's
+ * start (the pairs are disjoint): for G[p][q] != 0, tau = (G[q][q] -
+ * G[p][p]) / (2 G[p][q]), t = sign(tau) / (|tau| + sqrt(1 + tau^2)),
+ * c = 1 / sqrt(1 + t^2), s = t c (the classical symmetric Schur rotation that
+ * zeroes G[p][q]); then all row pairs (row p <- c row_p - s row_q, row q <-
+ * s row_p + c row_q), then all column pairs the same way, then the columns of
+ * Q (Q starts as I).  After each sweep the iteration stops when the largest
+ * |G[p][q]|, p < q, is at most 2^-48 times the largest |G[p][p]| (a maximum of
+ * absolute values, the same in any order of evaluation).  On return G is
+ * diagonal to rounding and G_in = Q G Q^T.
  */
 void orc_jacobi_eig(double* G, double* Q, int32_t k) {
   int32_t kp = k + (k & 1);
   int32_t half = kp / 2;
-  jac_rot* rot = (jac_rot*)malloc(sizeof(jac_rot) * (size_t)(half > 0 ? half : 1));
-  int32_t* pairof = (int32_t*)malloc(sizeof(int32_t) * (size_t)(kp > 0 ? kp : 1));
-  double* N = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
+  double* cs = (double*)malloc(sizeof(double) * 2 * (size_t)(half > 0 ? half : 1));
   for (int32_t i = 0; i < k; ++i)
     for (int32_t j = 0; j < k; ++j) Q[i * k + j] = (i == j) ? 1.0 : 0.0;
   for (int32_t sw = 0; sw < ORC_JAC_SWEEPS; ++sw) {
@@ -1133,49 +1115,40 @@ void orc_jacobi_eig(double* G, double* Q, int32_t k) {
       for (int32_t i = 0; i < half; ++i) {
         int32_t p, q;
         jac_pair(kp, t, i, &p, &q);
-        jac_rot r = {p, q, 1.0, 0.0, 0.0};
+        double c = 1.0, sn = 0.0;
         if (q < k && G[p * k + q] != 0.0) {
           double tau = (G[q * k + q] - G[p * k + p]) / (2.0 * G[p * k + q]);
           double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          r.c = 1.0 / sqrt(1.0 + tt * tt);
-          r.s = tt * r.c;
-          r.t = tt;
+          c = 1.0 / sqrt(1.0 + tt * tt);
+          sn = tt * c;
         }
-        rot[i] = r;
-        pairof[p] = i;
-        if (q < kp) pairof[q] = i;
+        cs[2 * i] = c; cs[2 * i + 1] = sn;
       }
-      for (int32_t a = 0; a < k; ++a) {
-        const jac_rot* ra = &rot[pairof[a]];
-        for (int32_t b = a + 1; b < k; ++b) {
-          const jac_rot* rb = &rot[pairof[b]];
-          double v;
-          if (ra == rb) {
-            v = 0.0;
-          } else if (rb->q >= k) {
-            v = jac_row(G, k, ra, a, b);
-          } else {
-            double xp = jac_row(G, k, ra, a, rb->p), xq = jac_row(G, k, ra, a, rb->q);
-            v = (b == rb->p) ? fma(rb->c, xp, -(rb->s * xq)) : fma(rb->s, xp, rb->c * xq);
-          }
-          N[a * k + b] = v;
-          N[b * k + a] = v;
-        }
-        if (ra->q < k) {
-          double gpq = G[ra->p * k + ra->q];
-          N[a * k + a] = (a == ra->p) ? G[a * k + a] - ra->t * gpq : G[a * k + a] + ra->t * gpq;
-        } else {
-          N[a * k + a] = G[a * k + a];
-        }
-      }
-      memcpy(G, N, sizeof(double) * (size_t)k * (size_t)k);
       for (int32_t i = 0; i < half; ++i) {
-        const jac_rot* r = &rot[i];
-        if (r->q >= k) continue;
+        int32_t p, q;
+        jac_pair(kp, t, i, &p, &q);
+        if (q >= k) continue;
+        double c = cs[2 * i], sn = cs[2 * i + 1];
         for (int32_t j = 0; j < k; ++j) {
-          double x = Q[j * k + r->p], y = Q[j * k + r->q];
-          Q[j * k + r->p] = fma(r->c, x, -(r->s * y));
-          Q[j * k + r->q] = fma(r->s, x, r->c * y);
+          double x = G[p * k + j], y = G[q * k + j];
+          G[p * k + j] = c * x - sn * y;
+          G[q * k + j] = sn * x + c * y;
+        }
+      }
+      for (int32_t i = 0; i < half; ++i) {
+        int32_t p, q;
+        jac_pair(kp, t, i, &p, &q);
+        if (q >= k) continue;
+        double c = cs[2 * i], sn = cs[2 * i + 1];
+        for (int32_t j = 0; j < k; ++j) {
+          double x = G[j * k + p], y = G[j * k + q];
+          G[j * k + p] = c * x - sn * y;
+          G[j * k + q] = sn * x + c * y;
+        }
+        for (int32_t j = 0; j < k; ++j) {
+          double x = Q[j * k + p], y = Q[j * k + q];
+          Q[j * k + p] = c * x - sn * y;
+          Q[j * k + q] = sn * x + c * y;
         }
       }
     }
@@ -1187,7 +1160,7 @@ void orc_jacobi_eig(double* G, double* Q, int32_t k) {
     }
     if (off <= ldexp(1.0, -48) * dmax) break;
   }
-  free(rot); free(pairof); free(N);
+  free(cs);
 }
 
 /*
