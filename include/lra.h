@@ -489,8 +489,10 @@ lra_status lra_oversample_cycle_batched(const lra_problem* base, const lra_batch
  * Algorithms algsmplex / algsmplexp), one CTA per block of the batch.  Per
  * block, from the rows I0 (k of them), iters times:
  *   horizontal: the k_I x n sketch A = W[I, :]; G = A A^T (ascending fma
- *   chains); 10 sweeps of round-robin Jacobi rotations (all angles of a round
- *   from G at its start, then the row pairs, then the column pairs and Q); the
+ *   chains); at most 10 sweeps of round-robin Jacobi rotations (all angles of a
+ *   round from G at its start, then the row pairs, then the column pairs and Q;
+ *   stop after a sweep that leaves every off-diagonal |G| at most 2^-48 times
+ *   the largest diagonal |G|); the
  *   r' = min(r, k_I) largest eigenvalues (lowest index on ties) that are
  *   positive and >= 1e-12 of the largest; scores v_j = sum_t (Q_t . a_j)^2 / d_t;
  *   then l = k columns: kind 0 Exactly(l) -- draw t picks the smallest j with

@@ -1091,7 +1091,7 @@ static void jac_pair(int32_t kp, int32_t t, int32_t i, int32_t* p, int32_t* q) {
 
 /*
  * orc_jacobi_eig: eigen-decomposition of a symmetric k x k G (row-major, in
- * place) by ORC_JAC_SWEEPS sweeps of Jacobi rotations in the round-robin
+ * place) by at most ORC_JAC_SWEEPS sweeps of Jacobi rotations in the round-robin
  * order (k rounded up to even kp; pairs with an index >= k are skipped).  In
  * each round every rotation is computed from G as it stands at the round's
  * start (the pairs are disjoint): for G[p][q] != 0, tau = (G[q][q] -
