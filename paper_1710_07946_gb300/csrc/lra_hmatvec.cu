@@ -1,7 +1,7 @@
 // lra_hmatvec.cu -- y = M x for a kernel matrix held as far blocks with C-A
 // generators plus a dense near field (the FMM's stage (iii): generators and
 // diagonal blocks times subvectors).  Three passes, each deterministic:
-//   1. per far block, t_b = U_b (R_b x[cols]);
+//   1. per far block, t_b = U_b (R_b x[cols]) (a warp per block);
 //   2. per (level, target box), each row's fma chain over the box's blocks in
 //      order, C_b[i][:] . t_b, into the level's partial vector; per target
 //      leaf, the near field's sums over the source leaves in order;
@@ -17,43 +17,53 @@
 
 namespace lra {
 
-// Pass 1: one CTA per far block (grid-stride): t1 = R_b x[cols], a thread per
-// row of R_b (an ascending fma chain), then t = U_b t1 the same way.
+// Generator size of far block b; 0 for a block whose run ended in an error.
 __device__ __forceinline__ int hm_kf(const lra_hmatrix& H, int64_t b) {
   const int32_t* inf = H.info + LRA_INFO_LEN * (size_t)b;
   if (inf[3] != LRA_OK && inf[3] < 16) return 0;
   return max(0, min(inf[6], H.kmax));
 }
 
+// Pass 1: a warp per far block (eight in flight per CTA, grid-stride over the
+// blocks): t1 = R_b x[cols] row by row (lane-strided fma partial sums over the
+// columns, then a fixed butterfly), then t = U_b t1 with each lane owning
+// entries lane, lane + 32 (an ascending fma chain over the row of U_b).
 __global__ void __launch_bounds__(256) hm_t_kernel(lra_hmatrix H, const double* __restrict__ x,
                                                    double* __restrict__ t) {
-  __shared__ double t1[KMAX];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int b = blockIdx.x; b < H.nfar; b += gridDim.x) {
+  __shared__ double t1s[8][KMAX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double* t1 = t1s[warp];
+  for (int64_t b = (int64_t)blockIdx.x * 8 + warp; b < H.nfar; b += (int64_t)gridDim.x * 8) {
     const int64_t nc = H.far[4 * (size_t)b + 3], c0 = H.far[4 * (size_t)b + 2];
     const int kf = (c0 < 0 || nc < 0 || c0 + nc > H.n) ? 0 : hm_kf(H, b);
     const double* R = H.R + H.far_offsets[2 * (size_t)b + 1];
     const double* U = H.U + (size_t)b * H.kmax * H.kmax;
-    // a warp per row of R_b: lane-strided partial sums (coalesced), then a fixed butterfly
-    for (int a = warp; a < kf; a += nw) {
+    for (int a = 0; a < kf; ++a) {
       double acc = 0.0;
       for (int64_t c = lane; c < nc; c += 32) acc = fma(R[(int64_t)a * nc + c], x[c0 + c], acc);
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
       if (lane == 0) t1[a] = acc;
     }
-    __syncthreads();
-    for (int a = threadIdx.x; a < kf; a += blockDim.x) {
+    __syncwarp();
+    for (int a = lane; a < kf; a += 32) {
       double acc = 0.0;
       for (int c = 0; c < kf; ++c) acc = fma(U[a * kf + c], t1[c], acc);
       t[(size_t)b * H.kmax + a] = acc;
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
-// Pass 2a: one CTA per (level, target box) group, a thread per row.
+// Pass 2a: one CTA per (level, target box) group, a thread per row; each
+// block's C_b (nrows x kf, one contiguous array) is staged through shared memory
+// in chunks of rows with coalesced loads, then every row's fma chain continues
+// over it: acc = sum over the group's blocks in order, then a ascending.
+constexpr int HM_FAR_STAGE = 4096;      // doubles of C staged at a time (32 KB)
+
 __global__ void __launch_bounds__(256) hm_far_kernel(lra_hmatrix H, const double* __restrict__ t,
                                                      double* __restrict__ ylev) {
+  __shared__ double cs[HM_FAR_STAGE];
+  __shared__ double ts[KMAX];
   for (int g = blockIdx.x; g < H.nfar_groups; g += gridDim.x) {
     const int64_t* G = H.far_groups + 5 * (size_t)g;
     const int lev = (int)G[0];
@@ -62,48 +72,73 @@ __global__ void __launch_bounds__(256) hm_far_kernel(lra_hmatrix H, const double
         first + cnt > H.nfar)
       continue;
     double* yl = ylev + (size_t)(lev - 2) * H.n;
-    for (int64_t i = threadIdx.x; i < nr; i += blockDim.x) {
+    // rows in passes of blockDim.x; within a pass, chunks of rows that fit the stage
+    for (int64_t i0 = 0; i0 < nr; i0 += blockDim.x) {
+      const int64_t i = i0 + threadIdx.x;
+      const int64_t rows = min((int64_t)blockDim.x, nr - i0);
       double acc = 0.0;
       for (int64_t b = first; b < first + cnt; ++b) {
         const int64_t br0 = H.far[4 * (size_t)b], bnr = H.far[4 * (size_t)b + 1];
-        if (br0 != r0 || bnr != nr) continue;             // a block of another box: not this group's
-        const int kf = hm_kf(H, b);
-        const double* C = H.C + H.far_offsets[2 * (size_t)b];
-        const double* tb = t + (size_t)b * H.kmax;
-        for (int a = 0; a < kf; ++a) acc = fma(C[i * kf + a], tb[a], acc);
+        const int kf = (br0 != r0 || bnr != nr) ? 0 : hm_kf(H, b);    // a block of another box: not this group's
+        if (kf == 0) continue;
+        const double* C = H.C + H.far_offsets[2 * (size_t)b] + i0 * kf;
+        const int64_t rchunk = max((int64_t)1, min(rows, (int64_t)(HM_FAR_STAGE / kf)));
+        __syncthreads();
+        for (int a = threadIdx.x; a < kf; a += blockDim.x) ts[a] = t[(size_t)b * H.kmax + a];
+        for (int64_t q0 = 0; q0 < rows; q0 += rchunk) {
+          const int64_t qn = min(rchunk, rows - q0);
+          __syncthreads();
+          for (int64_t e = threadIdx.x; e < qn * kf; e += blockDim.x) cs[e] = C[q0 * kf + e];
+          __syncthreads();
+          const int64_t li = (int64_t)threadIdx.x - q0;
+          if (li >= 0 && li < qn)
+            for (int a = 0; a < kf; ++a) acc = fma(cs[li * kf + a], ts[a], acc);
+        }
       }
-      yl[r0 + i] = acc;
+      if (i < nr) yl[r0 + i] = acc;
     }
   }
 }
 
-// Pass 2b: one CTA of 128 threads per target leaf, a thread per row; entries
-// on the fly as rsqrt(r2) (the FP64 reciprocal square root, within an ulp of
-// 1/sqrt(r2)), the source points taken in order with two interleaved
-// accumulators (even and odd positions of the leaf's source list) added at the end.
-__global__ void __launch_bounds__(128) hm_near_kernel(DevProblem P, lra_hmatrix H, const double* __restrict__ x,
+// Pass 2b: one CTA of 256 threads per target leaf: thread t takes row
+// t mod 128 (and every 128th after it) over the first (t < 128) or the second
+// half of the leaf's source blocks; entries on the fly as rsqrt(r2) (the FP64
+// reciprocal square root, within an ulp of 1/sqrt(r2)), the source points in
+// order with two interleaved accumulators; the row's value is (first half's
+// acc0 + acc1) + (second half's acc0 + acc1).
+__global__ void __launch_bounds__(256) hm_near_kernel(DevProblem P, lra_hmatrix H, const double* __restrict__ x,
                                                       double* __restrict__ ynear) {
+  __shared__ double part[128];
+  const int half = threadIdx.x >> 7, tr = threadIdx.x & 127;
   for (int g = blockIdx.x; g < H.nnear_groups; g += gridDim.x) {
     const int64_t* G = H.near_groups + 4 * (size_t)g;
     const int64_t r0 = G[0], nr = G[1], first = G[2], cnt = G[3];
     if (r0 < 0 || nr < 0 || r0 + nr > H.n || first < 0 || cnt < 0 || first + cnt > H.nnear) continue;
-    for (int64_t i = threadIdx.x; i < nr; i += blockDim.x) {
-      const int64_t gi = r0 + i;
-      const double xi = P.X[3 * gi], yi = P.X[3 * gi + 1], zi = P.X[3 * gi + 2];
+    const int64_t mid = first + (cnt + 1) / 2;
+    const int64_t bl = half == 0 ? first : mid, bh = half == 0 ? mid : first + cnt;
+    for (int64_t i0 = 0; i0 < nr; i0 += 128) {
+      const int64_t i = i0 + tr;
       double acc0 = 0.0, acc1 = 0.0;
-      int par = 0;
-      for (int64_t b = first; b < first + cnt; ++b) {
-        const int64_t c0 = H.near[4 * (size_t)b + 2], nc = H.near[4 * (size_t)b + 3];
-        if (c0 < 0 || nc < 0 || c0 + nc > H.n) continue;
-        for (int64_t j = c0; j < c0 + nc; ++j, par ^= 1) {
-          const double dx = xi - P.Y[3 * j], dy = yi - P.Y[3 * j + 1], dz = zi - P.Y[3 * j + 2];
-          const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-          const double w = (j == gi) ? 0.0 : rsqrt(r2);
-          if (par) acc1 = fma(w, x[j], acc1);
-          else acc0 = fma(w, x[j], acc0);
+      if (i < nr) {
+        const int64_t gi = r0 + i;
+        const double xi = P.X[3 * gi], yi = P.X[3 * gi + 1], zi = P.X[3 * gi + 2];
+        int par = 0;
+        for (int64_t b = bl; b < bh; ++b) {
+          const int64_t c0 = H.near[4 * (size_t)b + 2], nc = H.near[4 * (size_t)b + 3];
+          if (c0 < 0 || nc < 0 || c0 + nc > H.n) continue;
+          for (int64_t j = c0; j < c0 + nc; ++j, par ^= 1) {
+            const double dx = xi - P.Y[3 * j], dy = yi - P.Y[3 * j + 1], dz = zi - P.Y[3 * j + 2];
+            const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
+            const double w = (j == gi) ? 0.0 : rsqrt(r2);
+            if (par) acc1 = fma(w, x[j], acc1);
+            else acc0 = fma(w, x[j], acc0);
+          }
         }
       }
-      ynear[gi] = acc0 + acc1;
+      __syncthreads();
+      if (half == 1) part[tr] = acc0 + acc1;
+      __syncthreads();
+      if (half == 0 && i < nr) ynear[r0 + i] = (acc0 + acc1) + part[tr];
     }
   }
 }
@@ -171,7 +206,7 @@ lra_status lra_hmatvec(const lra_problem* prob, const lra_hmatrix* H, const doub
   if (H->nfar > 0) {
     {
       LaunchScope ls(stream, "hm_t_kernel");
-      hm_t_kernel<<<std::min(H->nfar, cap), 256, 0, stream>>>(Hv, x, t);
+      hm_t_kernel<<<std::max(1, std::min((H->nfar + 7) / 8, cap)), 256, 0, stream>>>(Hv, x, t);
     }
     {
       LaunchScope ls(stream, "hm_far_kernel");
@@ -180,7 +215,7 @@ lra_status lra_hmatvec(const lra_problem* prob, const lra_hmatrix* H, const doub
   }
   if (H->nnear_groups > 0) {
     LaunchScope ls(stream, "hm_near_kernel");
-    hm_near_kernel<<<std::min(H->nnear_groups, dev.sms * 16), 128, 0, stream>>>(P, Hv, x, parts);
+    hm_near_kernel<<<std::min(H->nnear_groups, dev.sms * 8), 256, 0, stream>>>(P, Hv, x, parts);
   }
   {
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((H->n + 255) / 256, cap));
