@@ -1,7 +1,7 @@
 // lra_hmatvec.cu -- y = M x for a kernel matrix held as far blocks with C-A
 // generators plus a dense near field (the FMM's stage (iii): generators and
 // diagonal blocks times subvectors).  Three passes, each deterministic:
-//   1. per far block, t_b = U_b (R_b x[cols]) (a warp per block);
+//   1. per far block, t_b = U_b (R_b x[cols]);
 //   2. per (level, target box), each row's fma chain over the box's blocks in
 //      order, C_b[i][:] . t_b, into the level's partial vector; per target
 //      leaf, the near field's sums over the source leaves in order;
@@ -24,46 +24,38 @@ __device__ __forceinline__ int hm_kf(const lra_hmatrix& H, int64_t b) {
   return max(0, min(inf[6], H.kmax));
 }
 
-// Pass 1: a warp per far block (eight in flight per CTA, grid-stride over the
-// blocks): t1 = R_b x[cols] row by row (lane-strided fma partial sums over the
-// columns, then a fixed butterfly), then t = U_b t1 with each lane owning
-// entries lane, lane + 32 (an ascending fma chain over the row of U_b).
+// Pass 1: one CTA per far block (grid-stride): t1 = R_b x[cols], a warp per row
+// of R_b (lane-strided fma partial sums, then a fixed butterfly), then t = U_b t1
+// with a thread per entry (an ascending fma chain).
 __global__ void __launch_bounds__(256) hm_t_kernel(lra_hmatrix H, const double* __restrict__ x,
                                                    double* __restrict__ t) {
-  __shared__ double t1s[8][KMAX];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double* t1 = t1s[warp];
-  for (int64_t b = (int64_t)blockIdx.x * 8 + warp; b < H.nfar; b += (int64_t)gridDim.x * 8) {
+  __shared__ double t1[KMAX];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int b = blockIdx.x; b < H.nfar; b += gridDim.x) {
     const int64_t nc = H.far[4 * (size_t)b + 3], c0 = H.far[4 * (size_t)b + 2];
     const int kf = (c0 < 0 || nc < 0 || c0 + nc > H.n) ? 0 : hm_kf(H, b);
     const double* R = H.R + H.far_offsets[2 * (size_t)b + 1];
     const double* U = H.U + (size_t)b * H.kmax * H.kmax;
-    for (int a = 0; a < kf; ++a) {
+    // a warp per row of R_b: lane-strided partial sums (coalesced), then a fixed butterfly
+    for (int a = warp; a < kf; a += nw) {
       double acc = 0.0;
       for (int64_t c = lane; c < nc; c += 32) acc = fma(R[(int64_t)a * nc + c], x[c0 + c], acc);
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
       if (lane == 0) t1[a] = acc;
     }
-    __syncwarp();
-    for (int a = lane; a < kf; a += 32) {
+    __syncthreads();
+    for (int a = threadIdx.x; a < kf; a += blockDim.x) {
       double acc = 0.0;
       for (int c = 0; c < kf; ++c) acc = fma(U[a * kf + c], t1[c], acc);
       t[(size_t)b * H.kmax + a] = acc;
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
-// Pass 2a: one CTA per (level, target box) group, a thread per row; each
-// block's C_b (nrows x kf, one contiguous array) is staged through shared memory
-// in chunks of rows with coalesced loads, then every row's fma chain continues
-// over it: acc = sum over the group's blocks in order, then a ascending.
-constexpr int HM_FAR_STAGE = 4096;      // doubles of C staged at a time (32 KB)
-
+// Pass 2a: one CTA per (level, target box) group, a thread per row.
 __global__ void __launch_bounds__(256) hm_far_kernel(lra_hmatrix H, const double* __restrict__ t,
                                                      double* __restrict__ ylev) {
-  __shared__ double cs[HM_FAR_STAGE];
-  __shared__ double ts[KMAX];
   for (int g = blockIdx.x; g < H.nfar_groups; g += gridDim.x) {
     const int64_t* G = H.far_groups + 5 * (size_t)g;
     const int lev = (int)G[0];
@@ -72,30 +64,17 @@ __global__ void __launch_bounds__(256) hm_far_kernel(lra_hmatrix H, const double
         first + cnt > H.nfar)
       continue;
     double* yl = ylev + (size_t)(lev - 2) * H.n;
-    // rows in passes of blockDim.x; within a pass, chunks of rows that fit the stage
-    for (int64_t i0 = 0; i0 < nr; i0 += blockDim.x) {
-      const int64_t i = i0 + threadIdx.x;
-      const int64_t rows = min((int64_t)blockDim.x, nr - i0);
+    for (int64_t i = threadIdx.x; i < nr; i += blockDim.x) {
       double acc = 0.0;
       for (int64_t b = first; b < first + cnt; ++b) {
         const int64_t br0 = H.far[4 * (size_t)b], bnr = H.far[4 * (size_t)b + 1];
-        const int kf = (br0 != r0 || bnr != nr) ? 0 : hm_kf(H, b);    // a block of another box: not this group's
-        if (kf == 0) continue;
-        const double* C = H.C + H.far_offsets[2 * (size_t)b] + i0 * kf;
-        const int64_t rchunk = max((int64_t)1, min(rows, (int64_t)(HM_FAR_STAGE / kf)));
-        __syncthreads();
-        for (int a = threadIdx.x; a < kf; a += blockDim.x) ts[a] = t[(size_t)b * H.kmax + a];
-        for (int64_t q0 = 0; q0 < rows; q0 += rchunk) {
-          const int64_t qn = min(rchunk, rows - q0);
-          __syncthreads();
-          for (int64_t e = threadIdx.x; e < qn * kf; e += blockDim.x) cs[e] = C[q0 * kf + e];
-          __syncthreads();
-          const int64_t li = (int64_t)threadIdx.x - q0;
-          if (li >= 0 && li < qn)
-            for (int a = 0; a < kf; ++a) acc = fma(cs[li * kf + a], ts[a], acc);
-        }
+        if (br0 != r0 || bnr != nr) continue;             // a block of another box: not this group's
+        const int kf = hm_kf(H, b);
+        const double* C = H.C + H.far_offsets[2 * (size_t)b];
+        const double* tb = t + (size_t)b * H.kmax;
+        for (int a = 0; a < kf; ++a) acc = fma(C[i * kf + a], tb[a], acc);
       }
-      if (i < nr) yl[r0 + i] = acc;
+      yl[r0 + i] = acc;
     }
   }
 }
@@ -206,7 +185,7 @@ lra_status lra_hmatvec(const lra_problem* prob, const lra_hmatrix* H, const doub
   if (H->nfar > 0) {
     {
       LaunchScope ls(stream, "hm_t_kernel");
-      hm_t_kernel<<<std::max(1, std::min((H->nfar + 7) / 8, cap)), 256, 0, stream>>>(Hv, x, t);
+      hm_t_kernel<<<std::min(H->nfar, cap), 256, 0, stream>>>(Hv, x, t);
     }
     {
       LaunchScope ls(stream, "hm_far_kernel");
