@@ -1254,6 +1254,7 @@ WORKLOADS = {
     "rhtcur_dense8192_k48": RhtcurWorkload,
     "levca_n1000_r10_k40": LevCaWorkload,
     "hmatvec_laplace_64K": HMatvecWorkload,
+    "hmatvec_laplace_8K": lambda: HMatvecWorkload(npts=1 << 13),
     "levca_n1000_r10_k40_expected": lambda: LevCaWorkload(kind=1),
     "hmt11_n1024_k39_bidiag20_onthefly": lambda: Hmt11Workload(materialize=False),
     "hmt11_n256_k31_bidiag20": lambda: Hmt11Workload(n=256, k=31),
