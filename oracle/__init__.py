@@ -57,6 +57,10 @@ def lib():
         L.orc_oversample.restype = ct.c_int
         L.orc_oversample_cycle.argtypes = [P, vp, vp, i32, i32, i32, i32, f64, f64, vp, vp, vp, vp, vp]
         L.orc_oversample_cycle.restype = ct.c_int
+        L.orc_alg1tor.argtypes = [vp, i32, i64, f64, vp]
+        L.orc_alg1tor.restype = i32
+        L.orc_prjvol.argtypes = [P, vp, vp, i32, i32, f64, i32, f64, vp, vp, vp, vp, vp]
+        L.orc_prjvol.restype = ct.c_int
         L.orc_rhtcur.argtypes = [P, vp, i32, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_rhtcur.restype = ct.c_int
         L.orc_jacobi_eig.argtypes = [vp, vp, i32]
@@ -399,6 +403,40 @@ def oversample(p, I, J, pextra, h=1.01, rank_tol=1e-13, pmax=0, max_cycles=0):
     return dict(J=Jo[:l].copy(), C=np.ascontiguousarray(C.reshape(-1)[:p.m * l].reshape(p.m, l)),
                 U=np.ascontiguousarray(U.reshape(-1)[:l * k].reshape(l, k)), R=R, rank=int(info[0]), l=l,
                 status=int(info[2]), cycles=int(info[3]), ptried=int(info[4]))
+
+
+def alg1tor(A, tol=1e-13):
+    """Algorithm alg1tor on the k x n matrix A (Householder QR with column
+    pivoting, stopped at the numerical rank r at tol; orc_alg1tor).  Returns
+    r, the pivots J0 (r), and the reduced matrix (k x n) whose first r rows are
+    R' of Algorithm algprjvlm's factorisation A = Q R P, columns in their
+    original order."""
+    A = np.array(A, dtype=np.float64, order="C", copy=True)
+    k, n = A.shape
+    J0 = np.zeros(max(min(k, n), 1), dtype=np.int32)
+    r = int(lib().orc_alg1tor(_ptr(A), k, n, float(tol), _ptr(J0)))
+    return r, J0[:r].copy(), A
+
+
+def prjvol(p, I, J, pextra, h=1.01, max_swaps=1000, rank_tol=1e-13):
+    """k x l generator (l = min(k + pextra, n)) of maximal r-projective volume in
+    the row strip W'[I, :] (Algorithm algprjvlm with Algorithm alg1tor for the
+    rank-revealing stage, Algorithm algdomin's swaps on R' and Algorithm algrup
+    up to l columns; orc_prjvol).  Returns J (l), C (m x l), U (l x k), R (k x n),
+    rank (nucleus), l, status, swaps, srank (the strip's numerical rank r)."""
+    mp = _Marshalled(p)
+    I = np.ascontiguousarray(I, dtype=np.int32)
+    J = np.ascontiguousarray(J, dtype=np.int32)
+    k, L = len(I), len(I) + int(pextra)
+    Jo = np.zeros(L, dtype=np.int32)
+    C = np.zeros((p.m, L)); U = np.zeros((L, k)); R = np.zeros((k, p.n))
+    info = np.zeros(5, dtype=np.int32)
+    lib().orc_prjvol(mp.ref, _ptr(I), _ptr(J), k, int(pextra), h, int(max_swaps), rank_tol, _ptr(Jo), _ptr(C),
+                     _ptr(U), _ptr(R), _ptr(info))
+    l = int(info[1])
+    return dict(J=Jo[:l].copy(), C=np.ascontiguousarray(C.reshape(-1)[:p.m * l].reshape(p.m, l)),
+                U=np.ascontiguousarray(U.reshape(-1)[:l * k].reshape(l, k)), R=R, rank=int(info[0]), l=l,
+                status=int(info[2]), swaps=int(info[3]), srank=int(info[4]))
 
 
 def cur_apply(C, U, R, X):

@@ -1074,6 +1074,145 @@ int orc_oversample(const orc_problem* p, const int32_t* I, const int32_t* J, int
 }
 
 /* ------------------------------------------------------------------ */
+/* r-projective volume: Algorithm alg1tor, then Algorithm algprjvlm     */
+/* ------------------------------------------------------------------ */
+
+/*
+ * orc_alg1tor: Algorithm alg1tor (greedy expansions from a vector up to a
+ * square matrix) on the k x n matrix A (row-major, overwritten), stopped at the
+ * numerical rank.  At step g = 0, 1, ...:
+ *   1. the pivot j_g is the column outside the chosen set whose subvector of
+ *      rows g..k-1 has the largest squared norm s_j (an ascending fma chain,
+ *      recomputed from the current A), lowest j on ties.  The loop stops before
+ *      step g when g = min(k, n), when that largest s_j is 0, or, for g > 0,
+ *      when sqrt(s_{j_g}) <= tol * sqrt(s_{j_0}); the numerical rank is r = g;
+ *   2. a Householder reflection on rows g..k-1 maps x = A[g.., j_g] to
+ *      alpha e_1 with alpha = -sqrt(s) for x_0 >= 0 and +sqrt(s) otherwise:
+ *      v = x - alpha e_1 and tau = 1 / (sqrt(s) (sqrt(s) + |x_0|)), which is
+ *      2 / v^T v.  Column j_g becomes (alpha, 0, ..., 0) exactly.  Every other
+ *      column c outside the chosen set gets t = v . A[g.., c] (ascending fma
+ *      chain) and A[g + i][c] <- fma(-(tau t), v_i, A[g + i][c]).  The chosen
+ *      columns are zero below their own row and stay unchanged.
+ * This is Householder QR with column pivoting (Businger-Golub).  The leading r
+ * rows of the result are R' of the rank-revealing factorisation A = Q R P in
+ * stage 1 of Algorithm algprjvlm, with the columns in their original order;
+ * R'[:, J0] is upper triangular in pivot order, J0 = (j_0, ..., j_{r-1}).
+ * Returns r.
+ */
+int32_t orc_alg1tor(double* A, int32_t k, int64_t n, double tol, int32_t* J0) {
+  unsigned char* chosen = (unsigned char*)calloc((size_t)n, 1);
+  double* v = (double*)malloc(sizeof(double) * (size_t)k);
+  int32_t g = 0;
+  double thr = 0.0;
+  int64_t gmax = (n < k) ? n : k;
+  for (; g < gmax; ++g) {
+    int64_t js = -1;
+    double sbest = 0.0;
+    for (int64_t c = 0; c < n; ++c) {
+      if (chosen[c]) continue;
+      double sc = 0.0;
+      for (int32_t i = g; i < k; ++i) sc = fma(A[(int64_t)i * n + c], A[(int64_t)i * n + c], sc);
+      if (js < 0 || sc > sbest) { js = c; sbest = sc; }
+    }
+    if (js < 0 || !(sbest > 0.0)) break;
+    double nrm = sqrt(sbest);
+    if (g == 0) thr = tol * nrm;
+    else if (!(nrm > thr)) break;
+    double x0 = A[(int64_t)g * n + js];
+    double alpha = (x0 >= 0.0) ? -nrm : nrm;
+    double tau = 1.0 / (nrm * (nrm + fabs(x0)));
+    v[0] = x0 - alpha;
+    for (int32_t i = 1; i < k - g; ++i) v[i] = A[(int64_t)(g + i) * n + js];
+    chosen[js] = 1;
+    J0[g] = (int32_t)js;
+    for (int64_t c = 0; c < n; ++c) {
+      if (chosen[c]) continue;
+      double t = 0.0;
+      for (int32_t i = 0; i < k - g; ++i) t = fma(v[i], A[(int64_t)(g + i) * n + c], t);
+      double cc = tau * t;
+      for (int32_t i = 0; i < k - g; ++i) A[(int64_t)(g + i) * n + c] = fma(-cc, v[i], A[(int64_t)(g + i) * n + c]);
+    }
+    A[(int64_t)g * n + js] = alpha;
+    for (int32_t i = g + 1; i < k; ++i) A[(int64_t)i * n + js] = 0.0;
+  }
+  free(chosen); free(v);
+  return g;
+}
+
+/*
+ * orc_prjvol: a k x l generator of maximal r-projective volume in the row
+ * strip A = W'[I, :] of a square generator's rows I (k = |I|),
+ * l = min(k + pextra, n) (Algorithm algprjvlm; Lemma leprwnmp maps the volumes
+ * of R' back to r-projective volumes in A):
+ *  1. stage 1: orc_alg1tor on A at rank_tol gives the numerical rank r, R'
+ *     (the first r rows, r x n) and J0;
+ *  2. stage 2's black box for a submatrix of maximal volume in the full-rank
+ *     R': the dominance swaps of Algorithm algdomin (orc_maxvol on R'
+ *     warm-started at J0, threshold h, at most max_swaps swaps; R'[:, J0] is
+ *     upper triangular, so the warm LU is R'[:, J0] itself), then Algorithm
+ *     algrup's greedy expansions (ov_expand on X = B^{-1} R') up to l columns;
+ *  3. outputs W'[:, J'] and the nucleus as orc_oversample_cycle's: C =
+ *     W'[:, J'] (m x l), U = orc_nucleus_rect(W'[I, J'], k, l, rank_tol),
+ *     R = W[I, :] (k x n).
+ * A zero strip (r = 0) keeps J' = J and l = k.  C (m x (k + pextra)) and U
+ * ((k + pextra) x k) are sized for l = k + pextra.  info: nucleus rank, l,
+ * status (worst of the swaps and the nucleus: ORC_WARN_NOT_CONVERGED when
+ * max_swaps stopped the swaps, ORC_WARN_RANK_DEFICIENT when the nucleus rank
+ * is below k or r = 0), swaps, r.
+ */
+int orc_prjvol(const orc_problem* p, const int32_t* I, const int32_t* J, int32_t k, int32_t pextra, double h,
+               int32_t max_swaps, double rank_tol, int32_t* Jo, double* C, double* U, double* R, int32_t* info) {
+  int64_t m = p->m, n = p->n;
+  int32_t lt = (k + pextra < n) ? k + pextra : (int32_t)n;
+  double* A = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
+  orc_gather_rows(p, I, k, A);
+  if (!all_finite(A, (int64_t)k * n)) {
+    info[0] = 0; info[1] = k; info[2] = ORC_ERR_NONFINITE; info[3] = 0; info[4] = 0;
+    free(A);
+    return ORC_ERR_NONFINITE;
+  }
+  int32_t* J0 = (int32_t*)malloc(sizeof(int32_t) * (size_t)k);
+  int32_t r = orc_alg1tor(A, k, n, rank_tol, J0);
+  int status = ORC_OK;
+  int32_t l = k, nsw = 0;
+  if (r == 0) {
+    memcpy(Jo, J, sizeof(int32_t) * (size_t)k);
+    status = ORC_WARN_RANK_DEFICIENT;
+  } else {
+    double* X = (double*)malloc(sizeof(double) * (size_t)r * (size_t)n);
+    double* s = (double*)malloc(sizeof(double) * (size_t)n);
+    double* x = (double*)malloc(sizeof(double) * (size_t)r);
+    unsigned char* in = (unsigned char*)calloc((size_t)n, 1);
+    double ld;
+    /* A's first r rows are R' (row-major, leading dimension n) */
+    status = orc_maxvol(A, r, n, J0, h, max_swaps, Jo, X, &ld, &nsw);
+    l = r;
+    for (int32_t a = 0; a < r; ++a) in[Jo[a]] = 1;
+    for (int64_t j = 0; j < n; ++j) {
+      double v = 0.0;
+      for (int32_t i = 0; i < r; ++i) v = fma(X[(int64_t)i * n + j], X[(int64_t)i * n + j], v);
+      s[j] = v;
+    }
+    double rho = 1.0;
+    ov_expand(X, s, x, in, Jo, &l, r, n, lt - r, &rho);
+    free(X); free(s); free(x); free(in);
+  }
+  double* Ct = (double*)malloc(sizeof(double) * (size_t)l * (size_t)m);
+  orc_gather_cols_t(p, Jo, l, Ct);
+  for (int64_t i = 0; i < m; ++i)
+    for (int32_t a = 0; a < l; ++a) C[i * l + a] = Ct[(int64_t)a * m + i];
+  orc_gather_rows_orig(p, I, k, R);
+  double* G = (double*)malloc(sizeof(double) * (size_t)k * (size_t)l);
+  for (int32_t a = 0; a < k; ++a)
+    for (int32_t b = 0; b < l; ++b) G[(int64_t)a * l + b] = C[(int64_t)I[a] * l + b];
+  int32_t rk = orc_nucleus_rect(G, k, l, rank_tol, U);
+  if (rk < k && status == ORC_OK) status = ORC_WARN_RANK_DEFICIENT;
+  info[0] = rk; info[1] = l; info[2] = status; info[3] = nsw; info[4] = r;
+  free(A); free(J0); free(Ct); free(G);
+  return status;
+}
+
+/* ------------------------------------------------------------------ */
 /* Leverage-score sampling inside C-A (DMM08 Algorithm 1 on sketches)   */
 /* ------------------------------------------------------------------ */
 #define ORC_JAC_SWEEPS 10

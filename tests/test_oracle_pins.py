@@ -1136,3 +1136,116 @@ def test_gauss_cur_backward_finite_differences(seed):
         args_p[key] = Mp; args_m[key] = Mm
         fdv = (f(**args_p) - f(**args_m)) / (2 * h)
         assert abs(fdv - b[name][idx]) <= 1e-6 * max(1.0, abs(fdv)), (name, fdv, b[name][idx])
+
+
+# ------------------------------------------------------------------ r-projective volume (Alg. alg1tor, algprjvlm)
+def _vol_r(M, r):
+    """r-projective volume v_{2,r}: the product of the r largest singular values."""
+    return float(np.prod(np.linalg.svd(M, compute_uv=False)[:r]))
+
+
+@pytest.mark.parametrize("seed", range(5))
+@pytest.mark.parametrize("k,n", [(6, 30), (12, 40), (8, 8), (10, 6)])
+def test_alg1tor_is_column_pivoted_qr(seed, k, n):
+    """Algorithm alg1tor's greedy expansions are Householder QR with column
+    pivoting: the same pivots as LAPACK's pivoted QR (scipy.linalg.qr), the same
+    |R|, the column Gram matrix kept (the reflections are orthogonal), and the
+    pivot columns exactly zero below their step."""
+    sl = pytest.importorskip("scipy.linalg")
+    A = np.random.default_rng(100 + seed).standard_normal((k, n))
+    r, J0, Ah = oracle.alg1tor(A, tol=1e-13)
+    q = min(k, n)
+    assert r == q
+    _, R, P = sl.qr(A, pivoting=True, mode="economic")
+    np.testing.assert_array_equal(J0, P[:q])
+    scale = np.linalg.norm(A)
+    np.testing.assert_allclose(np.abs(np.triu(Ah[:q][:, J0])), np.abs(R[:q, :q]), rtol=0, atol=1e-13 * scale)
+    np.testing.assert_allclose(Ah.T @ Ah, A.T @ A, rtol=0, atol=1e-13 * scale ** 2)
+    for g, j in enumerate(J0):
+        assert np.all(Ah[g + 1:, j] == 0.0)
+
+
+def test_alg1tor_numerical_rank():
+    """The greedy sequence stops at the numerical rank: exact rank-r products
+    give r (tol 1e-10), a generic matrix min(k, n), the zero matrix 0; the
+    stop is the first |R_gg| <= tol |R_00| of LAPACK's pivoted QR."""
+    sl = pytest.importorskip("scipy.linalg")
+    g = np.random.default_rng(7)
+    for (k, n, r) in [(10, 50, 4), (16, 30, 9), (8, 8, 1)]:
+        A = g.standard_normal((k, r)) @ g.standard_normal((r, n))
+        assert oracle.alg1tor(A, tol=1e-10)[0] == r
+        d = np.abs(np.diag(sl.qr(A, pivoting=True, mode="economic")[1]))
+        assert d[r - 1] > 1e-10 * d[0] >= d[r] if r < min(k, n) else True
+        assert oracle.alg1tor(A + 1e-3 * g.standard_normal((k, n)), tol=1e-10)[0] == min(k, n)
+    assert oracle.alg1tor(np.zeros((5, 9)))[0] == 0
+
+
+def _prj_case(seed, r=6, k=10, m=70, n=90):
+    p = li.dense_lowrank(m, n, r=r, noise=0.0, seed=seed)
+    o = oracle.ca_run(p, k, 3, li.initial_rows(m, k, seed))
+    return p, o
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_prjvol_swaps_then_expansions_maximise_r_projective_volume(seed):
+    """Algorithm algprjvlm on a rank-r strip W[I, :] with k > r rows: the r
+    columns after the swaps have locally h-maximal r-projective volume in the
+    strip (no single exchange raises v_{2,r} by more than h), and each column
+    Algorithm algrup appends maximises v_{2,r} of the grown set.  Every volume
+    here comes from numpy singular values of the original strip (Lemma
+    leprwnmp ties them to R')."""
+    h, r = 1.01, 6
+    p, o = _prj_case(seed, r=r)
+    pv = oracle.prjvol(p, o["I"], o["J"], 2, h=h, rank_tol=1e-10)
+    assert pv["srank"] == r and pv["l"] == 12
+    A = p.W[o["I"], :]
+    J = [int(j) for j in pv["J"]]
+    base = _vol_r(A[:, J[:r]], r)
+    for i in range(r):
+        for q in range(p.n):
+            if q in J[:r]:
+                continue
+            S = J[:r].copy()
+            S[i] = q
+            assert _vol_r(A[:, S], r) <= h * base * (1 + 1e-9), (i, q)
+    for g in range(r, len(J)):
+        vols = [(_vol_r(A[:, J[:g] + [q]], r) if q not in J[:g] else -1.0) for q in range(p.n)]
+        assert _vol_r(A[:, J[:g + 1]], r) >= max(vols) * (1 - 1e-9), g
+
+
+def test_prjvol_recovers_exact_low_rank_and_full_rank_strips_are_dominant():
+    """On an exact rank-r input the k x l generator (k > r) reproduces W to
+    rounding with the nucleus truncated at rank r; on a full-rank strip the
+    first k columns are a dominant k x k submatrix of the strip (Lemma
+    lelcliden: |B^{-1} A| <= h)."""
+    for seed in range(3):
+        p, o = _prj_case(seed, r=7)
+        pv = oracle.prjvol(p, o["I"], o["J"], 3, rank_tol=1e-10)
+        assert pv["srank"] == 7 and pv["rank"] == 7 and pv["status"] == 16
+        assert np.linalg.norm(p.W - pv["C"] @ pv["U"] @ pv["R"]) <= 1e-12 * np.linalg.norm(p.W)
+        np.testing.assert_array_equal(pv["C"], p.W[:, pv["J"]])
+        np.testing.assert_array_equal(pv["R"], p.W[o["I"], :])
+    h = 1.01
+    p = li.dense_lowrank(60, 80, r=12, noise=1e-3, seed=5)
+    o = oracle.ca_run(p, 8, 3, li.initial_rows(60, 8, 5))
+    pv = oracle.prjvol(p, o["I"], o["J"], 0, h=h, rank_tol=1e-10)
+    assert pv["srank"] == 8 and pv["l"] == 8 and pv["status"] == 0
+    A = p.W[o["I"], :]
+    assert np.abs(np.linalg.solve(A[:, pv["J"]], A)).max() <= h * (1 + 1e-12)
+
+
+def test_prjvol_degenerate_cases():
+    """A zero strip keeps the square generator (r = 0); with no swaps allowed
+    the first r columns are Algorithm alg1tor's pivots; l is clipped at n."""
+    p = li.Problem(li.SRC_DENSE, 20, 12, W=np.zeros((20, 12)))
+    I = np.arange(4, dtype=np.int32); J = np.array([3, 1, 7, 0], dtype=np.int32)
+    pv = oracle.prjvol(p, I, J, 3)
+    assert pv["srank"] == 0 and pv["l"] == 4 and pv["status"] == 16
+    np.testing.assert_array_equal(pv["J"], J)
+    p, o = _prj_case(2, r=5, k=8, m=40, n=11)
+    r, J0, _ = oracle.alg1tor(p.W[o["I"], :], tol=1e-10)
+    pv = oracle.prjvol(p, o["I"], o["J"], 0, h=1e300, max_swaps=0, rank_tol=1e-10)
+    assert pv["srank"] == r == 5 and pv["swaps"] == 0
+    np.testing.assert_array_equal(pv["J"][:r], J0)
+    pv = oracle.prjvol(p, o["I"], o["J"], 20, rank_tol=1e-10)
+    assert pv["l"] == 11 and sorted(pv["J"].tolist()) == list(range(11))
