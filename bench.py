@@ -1232,6 +1232,66 @@ class FmmOversampleWorkload(FmmWorkload):
         return good, n, el, f"{n} randomly chosen blocks of the same batch (C-A + expansion + residual sample each)"
 
 
+class FmmPrjvolWorkload(FmmOversampleWorkload):
+    """The FMM batch (mixed form) with every block's generator rebuilt as a
+    k x (k + p) one of maximal r-projective volume in the row strip W'[I, :]
+    (Algorithm algprjvlm: pivoted Householder QR to the numerical rank r,
+    Algorithm alg1tor; dominance swaps on R'; greedy expansion, Algorithm
+    algrup); one step = the batched C-A launch + the batched selection + the
+    rectangular residual sample against the FP64 entries."""
+
+    def __init__(self, pextra=8, **kw):
+        super().__init__(pextra, **kw)
+        self.name = self.name.replace(f"_oversample{pextra}", f"_prjvol{pextra}")
+
+    def config(self, h):
+        c = super().config(h)
+        c["generator"] = (f"k x (k + {self.pextra}) of maximal r-projective volume: pivoted QR of W'[I, :] to the "
+                          f"numerical rank r at rank_tol, dominance swaps on R' at h, greedy expansion")
+        return c
+
+    def device(self, h, dev):
+        import paper_1710_07946_gb300 as lra
+        d = FmmWorkload.device(self, h, dev)
+        d["ov"] = lra.Oversampled(d["bt"], self.pextra, prjvol=True)
+        return d
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        lra.lra_ca_run_batched(d["bt"])
+        lra.lra_prjvol_batched(d["bt"], self.pextra, d["ov"])
+        lra.lra_residual_sample_oversampled(d["ov"], d["Q"], d["S"], d["stats"], problem=d["prob64"])
+
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        b = h["blocks"]
+        order = np.random.default_rng(seed).permutation(len(b))
+        t0 = time.perf_counter()
+        n = good = 0
+        for idx in order:
+            r0, nr, c0, nc = b[idx]
+            sub = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=h["p"].X[r0:r0 + nr], Y=h["p"].Y[c0:c0 + nc])
+            sube = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=sub.X, Y=sub.Y, entries=self.entries)
+            o = oracle.ca_run_adaptive(sube, self.stages, self.margin, self.sweeps, h["I0"][idx], h=self.h,
+                                       rank_tol=self.tol)
+            pv = oracle.prjvol(sube, o["I"], o["J"], self.pextra, h=self.h, rank_tol=self.tol)
+            st = oracle.residual_sample(sub, pv["C"], pv["U"], pv["R"], h["Q"][idx], h["S"][idx])
+            n += 1
+            good += st[4] <= ERR_BOUND
+            if time.perf_counter() - t0 >= budget_s:
+                break
+        el = time.perf_counter() - t0
+        return good, n, el, f"{n} randomly chosen blocks of the same batch (C-A + selection + residual sample each)"
+
+
+class FmmSmallPrjvolWorkload(FmmPrjvolWorkload):
+    """fmm_prjvol8's recipe on 2^17 points and 512 block pairs (profiling size)."""
+    base = "fmm_laplace_128K_octree_512blocks"
+
+    def __init__(self):
+        super().__init__(8, npts=1 << 17, nblocks=512)
+
+
 class FmmSmallWorkload(FmmWorkload):
     """The headline recipe (mixed form) on 2^17 points and 512 block pairs (profiling size)."""
     base = "fmm_laplace_128K_octree_512blocks"
@@ -1249,6 +1309,8 @@ WORKLOADS = {
     "fmm_fixedk": lambda: FmmWorkload(stages=None),
     "fmm_oversample8": lambda: FmmOversampleWorkload(8),
     "fmm_oversample8_cycles4": lambda: FmmOversampleWorkload(8, pmax=4),
+    "fmm_prjvol8": lambda: FmmPrjvolWorkload(8),
+    "fmm_small_prjvol8": FmmSmallPrjvolWorkload,
     "fmm_small": FmmSmallWorkload,
     "hmt11_n1024_k39_bidiag20": Hmt11Workload,
     "rhtcur_dense8192_k48": RhtcurWorkload,

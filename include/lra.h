@@ -483,6 +483,46 @@ lra_status lra_oversample_cycle_batched(const lra_problem* base, const lra_batch
                                         lra_stream_t stream);
 
 /*
+ * lra_prjvol_batched -- k_b x l_b generators of maximal r-projective volume
+ * for every block of a batch that lra_ca_run_batched has processed (paper:
+ * Algorithm algprjvlm, maximisation of r-projective volume through the volume
+ * of a full-rank matrix; Algorithm alg1tor for its rank-revealing stage;
+ * Theorem coc-avlm for the C-A steps built on it), one CTA per block from a
+ * work queue.  For block b with rows I = in->I (k_b = in->info[6] of them) and
+ * l_b = min(k_b + pextra, ncols):
+ *   1. Algorithm alg1tor on the strip A = W'[I, :] (k_b x ncols): Householder
+ *      QR with column pivoting (pivot = the column outside the chosen set with
+ *      the largest squared norm of the remaining rows, an ascending fma chain,
+ *      lowest index on ties), stopped at the numerical rank r_b: the first step
+ *      whose pivot norm is <= par->rank_tol times the first pivot's, or
+ *      min(k_b, ncols).  Its first r_b rows are R' (r_b x ncols), the pivots J0;
+ *   2. Algorithm algdomin on R' warm-started at J0 (R'[:, J0] is upper
+ *      triangular): swaps while some |(R'[:, J])^{-1} R'| > par->h, at most
+ *      par->max_swaps of them, in lra_ca_run's maxvol arithmetic;
+ *   3. Algorithm algrup's greedy expansions from those r_b columns to l_b,
+ *      as in lra_oversample_batched.
+ *   A zero strip (r_b = 0) keeps J' = in->J (k_b columns).
+ * Outputs (out, layout of lra_oversample_batched): I, J' (l_b entries of an
+ * (par->k + pextra) slot), C_b = W'[:, J'], R_b = W[I, :], U_b = pinv of the
+ * rank-r QRP truncation of W'[I, J'] at par->rank_tol; info[0] = nucleus rank,
+ * info[1] = swaps made on R', info[2] = r_b, info[3] = status
+ * (LRA_WARN_NOT_CONVERGED when max_swaps stopped the swaps,
+ * LRA_WARN_RANK_DEFICIENT when the nucleus rank is below k_b or r_b = 0,
+ * LRA_ERR_NONFINITE for a strip holding NaN or Inf), info[6] = k_b,
+ * info[7] = l_b.  Blocks whose C-A run failed keep its status.
+ * With par->max_swaps = 0 and pextra = 0, J'[0..r_b) are Algorithm alg1tor's
+ * pivots (the status then says whether a swap was wanted).
+ * Errors: LRA_ERR_INVALID_ARG (also par->max_swaps < 0, and a rectangular
+ * nucleus of par->k x (par->k + pextra) that does not fit in shared memory),
+ * LRA_ERR_WORKSPACE, LRA_ERR_CUDA.
+ */
+lra_status lra_prjvol_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
+                                             const lra_ca_params* par, int32_t pextra, size_t* bytes);
+lra_status lra_prjvol_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                              int32_t pextra, const lra_cur_batch* in, const lra_cur_batch* out, void* workspace,
+                              size_t workspace_bytes, lra_stream_t stream);
+
+/*
  * lra_ca_lev_batched -- C-A iterations whose steps select by DMM08 Algorithm 1
  * on the sketches (paper: the tests of C-A incorporating [DMM08, Algorithm 1],
  * with SVD-based leverage scores, eq. eqlevsc with beta = 1, and the sampling of

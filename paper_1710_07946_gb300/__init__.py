@@ -135,6 +135,8 @@ def _load():
     L.lra_gather_rows.argtypes = [P, vp, i32, vp, vp, vp]
     L.lra_oversample_cycle_batched_workspace_size.argtypes = [P, PB, PP, i32, i32, ct.POINTER(sz)]
     L.lra_oversample_cycle_batched.argtypes = [P, PB, PP, i32, i32, PCB, PCB, vp, sz, vp]
+    L.lra_prjvol_batched_workspace_size.argtypes = [P, PB, PP, i32, ct.POINTER(sz)]
+    L.lra_prjvol_batched.argtypes = [P, PB, PP, i32, PCB, PCB, vp, sz, vp]
     L.lra_residual_sample_batched_rect.argtypes = [P, PB, i32, i32, PCB, vp, i32, vp, i32, vp, vp]
     L.lra_ca_batched_shapes.argtypes = [vp, vp, i32]
     L.lra_ca_batched_shapes.restype = i32
@@ -155,7 +157,7 @@ def _load():
               "lra_oversample_cycle_batched_workspace_size", "lra_oversample_cycle_batched", "lra_multiplier_apply",
               "lra_gather_rows", "lra_rhtcur_workspace_size", "lra_rhtcur_run", "lra_ca_lev_batched_workspace_size",
               "lra_ca_lev_batched", "lra_hmatvec_workspace_size", "lra_hmatvec",
-              "lra_residual_sample_batched_rect",
+              "lra_residual_sample_batched_rect", "lra_prjvol_batched_workspace_size", "lra_prjvol_batched",
               "lra_gauss_cur_forward", "lra_gauss_cur_backward"):
         getattr(L, f).restype = ct.c_int
     _lib = L
@@ -631,10 +633,11 @@ def lra_cynical_run_batched(batch: Batch, kind: int, q: int, K: torch.Tensor, L:
 
 class Oversampled:
     """Device outputs of lra_oversample_batched (or, with pmax > 0,
-    lra_oversample_cycle_batched) for a processed Batch: rectangular k_b x l_b
-    generators (l_b = min(k_b + pextra, ncols))."""
+    lra_oversample_cycle_batched; with prjvol, lra_prjvol_batched) for a
+    processed Batch: rectangular k_b x l_b generators (l_b = min(k_b + pextra,
+    ncols))."""
 
-    def __init__(self, batch: Batch, pextra: int, pmax: int = 0):
+    def __init__(self, batch: Batch, pextra: int, pmax: int = 0, prjvol: bool = False):
         import numpy as np
         b, k, p = batch, batch.k, int(pextra)
         self.pmax = int(pmax)
@@ -662,10 +665,15 @@ class Oversampled:
         for f in ("I", "J", "C", "U", "R", "logvol", "info"):
             setattr(self.cur, f, self.out[f].data_ptr())
         nbytes = ct.c_size_t()
-        _check(_load().lra_oversample_cycle_batched_workspace_size(ct.byref(b.pc), ct.byref(self.cb),
-                                                                   ct.byref(b.params), p, self.pmax,
-                                                                   ct.byref(nbytes)),
-               "lra_oversample_cycle_batched_workspace_size")
+        self.prjvol = bool(prjvol)
+        if self.prjvol:
+            _check(_load().lra_prjvol_batched_workspace_size(ct.byref(b.pc), ct.byref(self.cb), ct.byref(b.params), p,
+                                                             ct.byref(nbytes)), "lra_prjvol_batched_workspace_size")
+        else:
+            _check(_load().lra_oversample_cycle_batched_workspace_size(ct.byref(b.pc), ct.byref(self.cb),
+                                                                       ct.byref(b.params), p, self.pmax,
+                                                                       ct.byref(nbytes)),
+                   "lra_oversample_cycle_batched_workspace_size")
         self.workspace = _workspace(nbytes.value, dev)
 
     def block(self, i: int) -> dict:
@@ -676,7 +684,8 @@ class Oversampled:
         oc, orr = self.offs_np[i]
         return dict(I=o["I"][i, :k], J=o["J"][i, :l], C=o["C"][oc:oc + nr * l].reshape(nr, l),
                     U=o["U"][i].reshape(-1)[:l * k].reshape(l, k), R=o["R"][orr:orr + k * nc].reshape(k, nc),
-                    rank=int(info[0]), status=int(info[3]), k=k, l=l, cycles=int(info[1]), ptried=int(info[2]))
+                    rank=int(info[0]), status=int(info[3]), k=k, l=l, cycles=int(info[1]), ptried=int(info[2]),
+                    swaps=int(info[1]), srank=int(info[2]))
 
 
 def lra_oversample_batched(batch: Batch, pextra: int, ov: Optional[Oversampled] = None, stream=None) -> Oversampled:
@@ -706,10 +715,31 @@ def lra_oversample_cycle_batched(batch: Batch, pextra: int, pmax: int, max_cycle
     return ov
 
 
+def lra_prjvol_batched(batch: Batch, pextra: int, ov: Optional[Oversampled] = None, max_swaps: Optional[int] = None,
+                       stream=None) -> Oversampled:
+    """Generators of maximal r-projective volume in each block's row strip
+    W'[I, :] (Algorithm algprjvlm: Algorithm alg1tor's pivoted QR at the batch's
+    rank_tol, dominance swaps on R' at the batch's h, greedy expansion to
+    l_b = min(k_b + pextra, ncols)); run lra_ca_run_batched first.  max_swaps
+    defaults to the batch's.  block(i) gives srank (r_b) and swaps."""
+    ov = ov or Oversampled(batch, pextra, prjvol=True)
+    if not ov.prjvol:
+        raise ValueError("the Oversampled buffers were sized for lra_oversample_batched")
+    par = _Params()
+    ct.memmove(ct.byref(par), ct.byref(batch.params), ct.sizeof(_Params))
+    if max_swaps is not None:
+        par.max_swaps = int(max_swaps)
+    _check(_load().lra_prjvol_batched(ct.byref(batch.pc), ct.byref(ov.cb), ct.byref(par), ov.pextra,
+                                      ct.byref(batch.cur), ct.byref(ov.cur), ov.workspace.data_ptr(),
+                                      ov.workspace.numel(), _stream(stream)), "lra_prjvol_batched")
+    return ov
+
+
 class LevBatch:
     """Device buffers of a batch of blocks for lra_ca_lev_batched: C-A
     iterations with DMM08 Algorithm 1 on the sketches (kind 0 Exactly(k),
-    1 Expected(k)), rank r leverage scores, ``draws`` uniforms per step."""
+    1 Expected(k) with rank r SVD-based leverage scores; 2, 3 the same with
+    uniform scores, no SVD stage), ``draws`` uniforms per step."""
 
     def __init__(self, problem: Problem, blocks, k: int, r: int, iters: int, kind: int, I0, draws,
                  rank_tol: float = 1e-6, order="lpt"):

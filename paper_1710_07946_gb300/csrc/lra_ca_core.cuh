@@ -228,8 +228,10 @@ __device__ inline int gather_chunk(const DevProblem& P, int phase, const CaSmem&
 // a_p * (1/pivot), column-sweep back substitution with the reciprocals of the
 // U0 diagonal, swaps t_q = C[i*][q] * (1/c*), C[p][q] = fma(-x_p, t_q, C[p][q]).
 // The k x k LU is stored with the odd row stride ldl = k | 1 (no bank conflicts
-// when a warp walks down one of its columns).
-template <class Group>
+// when a warp walks down one of its columns).  kPre: the strip is already in
+// the chunk M (a single CTA holding all of it, rows 0..k-1); nothing is
+// gathered and the warm start reads B = M[:, Jsel].
+template <class Group, bool kPre = false>
 __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSmem& S, int phase, bool cold,
                                   int32_t* Jsel, unsigned long long& seq, bool lead) {
   const DevProblem& P = A.P;
@@ -249,7 +251,9 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
   if (tid == 0) S.ctl[0] = 0;
   for (int c = tid; c < qn; c += nt) S.pos[c] = 0;
   __syncthreads();
-  if (gather_chunk(P, phase, S, k, q0, qn, ldm, mp)) atomicOr(&S.ctl[0], 1);
+  if constexpr (!kPre) {
+    if (gather_chunk(P, phase, S, k, q0, qn, ldm, mp)) atomicOr(&S.ctl[0], 1);
+  }
   __syncthreads();
   const unsigned long long myflags = S.ctl[0] ? FLAG_NONFINITE : 0ull;
   bool deficient = false;
@@ -258,7 +262,8 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
     // ---- warm start: B = strip[:, Jsel]; the pivoted LU of B is replayed by every CTA
     for (int it = tid; it < k * k; it += nt) {
       const int a = it / k, t = it - a * k;
-      LU[a * ldl + t] = strip_entry(P, phase, S.Is, S.Js, a, Jsel[t]);
+      if constexpr (kPre) LU[a * ldl + t] = M[(int64_t)a * ldm + (Jsel[t] - q0)];
+      else LU[a * ldl + t] = strip_entry(P, phase, S.Is, S.Js, a, Jsel[t]);
     }
     __syncthreads();
     int fallback = 0;

@@ -19,6 +19,13 @@
 // the set and raised the volume is kept and p restarts at 1, otherwise X, s and
 // J' are restored from a per-CTA copy and p grows.  Outputs C = W'[:, J'], the
 // rectangular nucleus U of W'[I, J'] and R = W[I, :].
+//
+// prjvol_kernel picks the columns by r-projective volume instead (Algorithm
+// algprjvlm): Algorithm alg1tor (Householder QR with column pivoting, stopped
+// at the numerical rank r) reduces the strip W'[I, :] to R' (r x n) in place,
+// a warm maxvol step on R' from the QR's pivots makes the r x r submatrix
+// locally h-maximal (Algorithm algdomin), and Algorithm algrup's expansions
+// take it to l columns; the outputs are those of oversample_kernel.
 #include <algorithm>
 #include <cstring>
 
@@ -36,6 +43,7 @@ struct OvArgs {
   const int32_t* order;
   int32_t nb, kmax, pextra, lmax;
   int32_t pmax, max_cycles;   // expansion/contraction cycles (pmax = 0: none)
+  int32_t max_swaps;          // prjvol: dominance swaps on R'
   double h, rank_tol;
   const int32_t* Iin;         // nb x kmax
   const int32_t* Jin;         // nb x kmax
@@ -331,12 +339,211 @@ __global__ void __launch_bounds__(NT) oversample_kernel(OvArgs B) {
   }
 }
 
+// Algorithm alg1tor on the k x nc strip M (leading dimension ldm), stopped at
+// the numerical rank: Householder QR with column pivoting in the FP64
+// reference's arithmetic.  Step g: the pivot is the unchosen column with the
+// largest squared norm s_c of rows g.. (lowest c on ties); the loop stops when
+// that norm is 0, or (g > 0) when its square root is <= tol times the first
+// pivot's; alpha = -sqrt(s) for x_0 >= 0, else +sqrt(s); v = x - alpha e_1;
+// tau = 1 / (sqrt(s) (sqrt(s) + |x_0|)); every unchosen column c gets
+// t = v . M[g.., c] (ascending fma chain), M[g + i][c] = fma(-(tau t), v_i,
+// M[g + i][c]) and, in the same pass, its squared norm over rows g + 1.. for
+// the next search; the pivot column becomes (alpha, 0, ..., 0).  s: nc
+// doubles; pos: nc flags (1 + step for the pivots); J0: the pivots; v: KMAX
+// doubles.  Returns r.  Called by the whole CTA.
+__device__ int alg1tor_cta(double* M, int ldm, int k, int nc, double tol, double* s, int32_t* pos, int32_t* J0,
+                           double* v, CandRed* red) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int c = tid; c < nc; c += nt) {
+    double a = 0.0;
+    for (int i = 0; i < k; ++i) a = fma(M[(int64_t)i * ldm + c], M[(int64_t)i * ldm + c], a);
+    s[c] = a;
+    pos[c] = 0;
+  }
+  __syncthreads();
+  const int gmax = min(k, nc);
+  double thr = 0.0;
+  int g = 0;
+  for (; g < gmax; ++g) {
+    Cand mine = cand_none();
+    for (int c = tid; c < nc; c += nt)
+      if (!pos[c]) cand_consider(mine, mag_key(s[c]), 0, c);
+    unsigned long long fl = 0;
+    const Cand w = block_best(mine, fl, red);
+    if (w.key == 0ull || w.key == mag_key(0.0)) break;
+    const int js = w.j;
+    const double nrm = sqrt(s[js]);
+    if (g == 0) thr = tol * nrm;
+    else if (!(nrm > thr)) break;
+    const double x0 = M[(int64_t)g * ldm + js];
+    const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+    const double tau = 1.0 / (nrm * (nrm + fabs(x0)));
+    const int len = k - g;
+    for (int i = tid; i < len; i += nt) v[i] = (i == 0) ? x0 - alpha : M[(int64_t)(g + i) * ldm + js];
+    if (tid == 0) {
+      pos[js] = g + 1;
+      J0[g] = js;
+    }
+    __syncthreads();
+    for (int c = tid; c < nc; c += nt) {
+      if (pos[c]) continue;
+      double t = 0.0;
+      for (int i = 0; i < len; ++i) t = fma(v[i], M[(int64_t)(g + i) * ldm + c], t);
+      const double cc = tau * t;
+      double a = 0.0;
+      for (int i = 0; i < len; ++i) {
+        const double y = fma(-cc, v[i], M[(int64_t)(g + i) * ldm + c]);
+        M[(int64_t)(g + i) * ldm + c] = y;
+        if (i > 0) a = fma(y, y, a);
+      }
+      s[c] = a;
+    }
+    for (int i = tid; i < len; i += nt) M[(int64_t)(g + i) * ldm + js] = (i == 0) ? alpha : 0.0;
+    __syncthreads();
+  }
+  return g;
+}
+
+__global__ void __launch_bounds__(NT) prjvol_kernel(OvArgs B) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_b;
+  __shared__ double s_x[KMAX];
+  __shared__ double s_g[2];
+  __shared__ double s_rho[1];
+  __shared__ int32_t s_Jw[2 * KMAX];
+  double* G = B.scratch + (size_t)blockIdx.x * B.scratch_stride;
+  double* gstrip = G + (size_t)B.kmax * B.lmax;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (;;) {
+    if (tid == 0) {
+      const unsigned int qh = atomicAdd(B.counter, 1u);
+      s_b = (qh < (unsigned)B.nb) ? (B.order ? B.order[qh] : (int)qh) : -1;
+    }
+    __syncthreads();
+    const int b = s_b;
+    __syncthreads();
+    if (b < 0) break;
+    int32_t* info = B.info + LRA_INFO_LEN * (size_t)b;
+    const int32_t* inf0 = B.info_in + LRA_INFO_LEN * (size_t)b;
+    const int64_t r0 = B.blocks[4 * (size_t)b], nr = B.blocks[4 * (size_t)b + 1];
+    const int64_t c0 = B.blocks[4 * (size_t)b + 2], nc = B.blocks[4 * (size_t)b + 3];
+    const int st_in = inf0[3];
+    const int k = inf0[6];
+    if (r0 < 0 || c0 < 0 || nr < 1 || nc < 1 || r0 + nr > B.base.m || c0 + nc > B.base.n || nr > B.max_len ||
+        nc > B.max_len || (st_in != LRA_OK && st_in < 16) || k < 1 || k > B.kmax || k > min(nr, nc)) {
+      for (int e = tid; e < LRA_INFO_LEN; e += nt)
+        info[e] = (e == 3) ? ((st_in != LRA_OK && st_in < 16) ? st_in : LRA_ERR_INVALID_ARG) : 0;
+      continue;
+    }
+    const int lb = (int)min((int64_t)(k + B.pextra), nc);
+    CaArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.P = B.base;
+    A.P.m = nr;
+    A.P.n = nc;
+    if (A.P.src == LRA_DENSE) {
+      const size_t esz = (A.P.dtype == LRA_F32) ? 4 : 8;
+      A.P.W = static_cast<const unsigned char*>(B.base.W) + (size_t)(r0 * B.base.ldw + c0) * esz;
+    } else {
+      A.P.X = B.base.X + 3 * r0;
+      A.P.Y = B.base.Y + 3 * c0;
+    }
+    A.k = k;
+    A.max_swaps = B.max_swaps;
+    A.h = B.h;
+    A.chunk_n = (int)nc;
+    A.chunk_m = (int)nr;
+    A.ldm = (int)nc;
+    A.strip_in_smem = ca_smem_fixed(k, A.ldm) + sizeof(double) * (size_t)k * A.ldm <= B.smem_bytes;
+    A.gstrip = A.strip_in_smem ? nullptr : gstrip;
+    int32_t* Jb = B.J + (size_t)b * B.lmax;
+    int l = k, st = LRA_OK, nsw = 0, r = 0;
+    {
+      const CaSmem S = ca_smem_carve(smem, k, A.ldm, A.gstrip);
+      for (int a = tid; a < k; a += nt) S.Is[a] = B.Iin[(size_t)b * B.kmax + a];
+      if (tid == 0) S.ctl[0] = 0;
+      __syncthreads();
+      // the strip W'[I, :] (k x nc)
+      if (gather_chunk(A.P, 0, S, k, 0, (int)nc, A.ldm, Map2D((int)nc))) atomicOr(&S.ctl[0], 1);
+      __syncthreads();
+      if (S.ctl[0]) {
+        for (int e = tid; e < LRA_INFO_LEN; e += nt)
+          info[e] = (e == 3) ? LRA_ERR_NONFINITE : (e == 6 || e == 7) ? k : 0;
+        continue;
+      }
+      // stage 1: R' (rows 0..r-1 of M, in place) and the pivots J0 (into S.Js)
+      r = alg1tor_cta(S.M, A.ldm, k, (int)nc, B.rank_tol, S.tq, S.pos, S.Js, s_x, S.red);
+      if (r == 0) {
+        // a zero strip: the square generator as given
+        for (int a = tid; a < k; a += nt) Jb[a] = B.Jin[(size_t)b * B.kmax + a];
+        st = LRA_WARN_RANK_DEFICIENT;
+      } else {
+        // stage 2: dominance swaps on R' from J0, then greedy expansions to lb columns
+        CaArgs A2 = A;
+        A2.k = r;
+        unsigned long long seq = 0;
+        const StepResult sr = maxvol_step<SoloGroup, true>(SoloGroup{}, A2, S, 0, false, S.Js, seq, true);
+        __syncthreads();
+        st = sr.status;
+        nsw = sr.nswaps;
+        if (st != LRA_OK && st < 16) {
+          for (int e = tid; e < LRA_INFO_LEN; e += nt) info[e] = (e == 3) ? st : (e == 6 || e == 7) ? k : 0;
+          continue;
+        }
+        for (int a = tid; a < r; a += nt) s_Jw[a] = S.Js[a];
+        double* M = S.M;
+        double* s = S.tq;
+        for (int c = tid; c < nc; c += nt) {
+          double v = 0.0;
+          for (int i = 0; i < r; ++i) v = fma(M[(int64_t)i * A.ldm + c], M[(int64_t)i * A.ldm + c], v);
+          s[c] = v;
+        }
+        if (tid == 0) s_rho[0] = 1.0;
+        __syncthreads();
+        l = r;
+        ov_expand(M, A.ldm, s, S.pos, s_Jw, l, r, (int)nc, lb - r, s_rho, s_x, s_g, S.red);
+        for (int a = tid; a < l; a += nt) Jb[a] = s_Jw[a];
+      }
+    }
+    __syncthreads();
+    // outputs at l: C = W'[:, J'] (nr x l), R = W[I, :] (k x nc), G = W'[I, J'] -> U
+    const int32_t* Ib = B.Iin + (size_t)b * B.kmax;
+    double* Cb = B.C + B.offs[2 * (size_t)b];
+    double* Rb = B.R + B.offs[2 * (size_t)b + 1];
+    for (int64_t it = tid; it < nr * l; it += nt) {
+      const int64_t i = it / l;
+      const int a = (int)(it - i * l);
+      Cb[it] = wp_entry(A.P, i, Jb[a]);
+    }
+    for (int64_t it = tid; it < (int64_t)k * nc; it += nt) {
+      const int a = (int)(it / nc);
+      const int64_t c = it - (int64_t)a * nc;
+      Rb[it] = w_entry(A.P, Ib[a], c);
+    }
+    for (int it = tid; it < k * l; it += nt) {
+      const int a = it / l, c = it - a * l;
+      G[it] = wp_entry(A.P, Ib[a], Jb[c]);
+    }
+    for (int a = tid; a < k; a += nt) B.I[(size_t)b * B.kmax + a] = Ib[a];
+    __syncthreads();
+    const int rank = nucleus_rect_cta(G, k, l, B.rank_tol, B.U + (size_t)b * B.lmax * B.kmax, smem);
+    if (tid == 0) {
+      if (rank < k && st == LRA_OK) st = LRA_WARN_RANK_DEFICIENT;
+      info[0] = rank; info[1] = nsw; info[2] = r; info[3] = st; info[4] = 0; info[5] = 0; info[6] = k;
+      info[7] = l;
+    }
+    __syncthreads();
+  }
+}
+
 struct OvPlan {
   int grid;
   size_t smem, scratch_stride, backup_offset, bytes;
 };
 
-static lra_status ov_plan(int kmax, int lmax, int64_t max_len, int pmax, OvPlan* pl) {
+static lra_status ov_plan(bool prj, int kmax, int lmax, int64_t max_len, int pmax, OvPlan* pl) {
+  const void* kern =
+      prj ? reinterpret_cast<const void*>(prjvol_kernel) : reinterpret_cast<const void*>(oversample_kernel);
   DeviceInfo dev;
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
@@ -347,9 +554,9 @@ static lra_status ov_plan(int kmax, int lmax, int64_t max_len, int pmax, OvPlan*
   bool gstrip = true;
   if (std::max(fixed + strip, need) <= budget) { need = std::max(fixed + strip, need); gstrip = false; }
   if (need > budget) return LRA_ERR_INVALID_ARG;
-  LRA_CUDA_TRY(cudaFuncSetAttribute(oversample_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
+  LRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need));
   int occ = 0;
-  LRA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, oversample_kernel, NT, need));
+  LRA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, NT, need));
   if (occ < 1) return LRA_ERR_INVALID_ARG;
   pl->grid = occ * dev.sms;
   pl->smem = need;
@@ -359,8 +566,8 @@ static lra_status ov_plan(int kmax, int lmax, int64_t max_len, int pmax, OvPlan*
   return LRA_OK;
 }
 
-static lra_status ov_check(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par, int32_t pextra,
-                           int32_t pmax, DevProblem* P) {
+static lra_status ov_check(bool prj, const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                           int32_t pextra, int32_t pmax, DevProblem* P) {
   lra_status st = make_dev_problem(base, nullptr, P);
   if (st != LRA_OK) return st;
   if (batch == nullptr || par == nullptr || batch->blocks == nullptr || batch->offsets == nullptr || batch->nb < 1 ||
@@ -370,20 +577,21 @@ static lra_status ov_check(const lra_problem* base, const lra_batch* batch, cons
       !(par->rank_tol >= 0.0) || !(par->rank_tol < 1.0))
     return LRA_ERR_INVALID_ARG;
   if (pmax < 0 || pmax > PMAX || (pmax > 0 && par->max_swaps < 0)) return LRA_ERR_INVALID_ARG;
+  if (prj && (pmax != 0 || par->max_swaps < 0)) return LRA_ERR_INVALID_ARG;
   return LRA_OK;
 }
 
-static lra_status ov_run(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par, int32_t pextra,
-                         int32_t pmax, const lra_cur_batch* in, const lra_cur_batch* out, void* workspace,
-                         size_t workspace_bytes, cudaStream_t stream) {
+static lra_status ov_run(bool prj, const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                         int32_t pextra, int32_t pmax, const lra_cur_batch* in, const lra_cur_batch* out,
+                         void* workspace, size_t workspace_bytes, cudaStream_t stream) {
   DevProblem P;
-  lra_status st = ov_check(base, batch, par, pextra, pmax, &P);
+  lra_status st = ov_check(prj, base, batch, par, pextra, pmax, &P);
   if (st != LRA_OK) return st;
   if (in == nullptr || out == nullptr || !in->I || !in->J || !in->info || !out->I || !out->J || !out->C || !out->U ||
       !out->R || !out->info)
     return LRA_ERR_INVALID_ARG;
   OvPlan pl;
-  if ((st = ov_plan(par->k, par->k + pextra, batch->max_len, pmax, &pl)) != LRA_OK) return st;
+  if ((st = ov_plan(prj, par->k, par->k + pextra, batch->max_len, pmax, &pl)) != LRA_OK) return st;
   if (workspace == nullptr || workspace_bytes < pl.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255u))
     return LRA_ERR_WORKSPACE;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
@@ -399,6 +607,7 @@ static lra_status ov_run(const lra_problem* base, const lra_batch* batch, const 
   A.lmax = par->k + pextra;
   A.pmax = pmax;
   A.max_cycles = pmax > 0 ? par->max_swaps : 0;
+  A.max_swaps = prj ? par->max_swaps : 0;
   A.h = par->h;
   A.rank_tol = par->rank_tol;
   A.Iin = in->I;
@@ -417,21 +626,24 @@ static lra_status ov_run(const lra_problem* base, const lra_batch* batch, const 
   A.smem_bytes = pl.smem;
   A.max_len = batch->max_len;
   LRA_CUDA_TRY(cudaMemsetAsync(ws, 0, 256, stream));
-  {
+  if (prj) {
+    LaunchScope ls(stream, "prjvol_kernel");
+    prjvol_kernel<<<pl.grid, NT, pl.smem, stream>>>(A);
+  } else {
     LaunchScope ls(stream, "oversample_kernel");
     oversample_kernel<<<pl.grid, NT, pl.smem, stream>>>(A);
   }
   return cuda_status(cudaGetLastError());
 }
 
-static lra_status ov_workspace(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+static lra_status ov_workspace(bool prj, const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
                                int32_t pextra, int32_t pmax, size_t* bytes) {
   if (bytes == nullptr) return LRA_ERR_INVALID_ARG;
   DevProblem P;
-  lra_status st = ov_check(base, batch, par, pextra, pmax, &P);
+  lra_status st = ov_check(prj, base, batch, par, pextra, pmax, &P);
   if (st != LRA_OK) return st;
   OvPlan pl;
-  if ((st = ov_plan(par->k, par->k + pextra, batch->max_len, pmax, &pl)) != LRA_OK) return st;
+  if ((st = ov_plan(prj, par->k, par->k + pextra, batch->max_len, pmax, &pl)) != LRA_OK) return st;
   *bytes = pl.bytes;
   return LRA_OK;
 }
@@ -444,27 +656,39 @@ extern "C" {
 
 lra_status lra_oversample_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
                                                  const lra_ca_params* par, int32_t pextra, size_t* bytes) {
-  return ov_workspace(base, batch, par, pextra, 0, bytes);
+  return ov_workspace(false, base, batch, par, pextra, 0, bytes);
 }
 
 lra_status lra_oversample_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
                                   int32_t pextra, const lra_cur_batch* in, const lra_cur_batch* out, void* workspace,
                                   size_t workspace_bytes, lra_stream_t stream) {
-  return ov_run(base, batch, par, pextra, 0, in, out, workspace, workspace_bytes,
+  return ov_run(false, base, batch, par, pextra, 0, in, out, workspace, workspace_bytes,
                 reinterpret_cast<cudaStream_t>(stream));
 }
 
 lra_status lra_oversample_cycle_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
                                                        const lra_ca_params* par, int32_t pextra, int32_t pmax,
                                                        size_t* bytes) {
-  return ov_workspace(base, batch, par, pextra, pmax, bytes);
+  return ov_workspace(false, base, batch, par, pextra, pmax, bytes);
 }
 
 lra_status lra_oversample_cycle_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
                                         int32_t pextra, int32_t pmax, const lra_cur_batch* in,
                                         const lra_cur_batch* out, void* workspace, size_t workspace_bytes,
                                         lra_stream_t stream) {
-  return ov_run(base, batch, par, pextra, pmax, in, out, workspace, workspace_bytes,
+  return ov_run(false, base, batch, par, pextra, pmax, in, out, workspace, workspace_bytes,
+                reinterpret_cast<cudaStream_t>(stream));
+}
+
+lra_status lra_prjvol_batched_workspace_size(const lra_problem* base, const lra_batch* batch,
+                                             const lra_ca_params* par, int32_t pextra, size_t* bytes) {
+  return ov_workspace(true, base, batch, par, pextra, 0, bytes);
+}
+
+lra_status lra_prjvol_batched(const lra_problem* base, const lra_batch* batch, const lra_ca_params* par,
+                              int32_t pextra, const lra_cur_batch* in, const lra_cur_batch* out, void* workspace,
+                              size_t workspace_bytes, lra_stream_t stream) {
+  return ov_run(true, base, batch, par, pextra, 0, in, out, workspace, workspace_bytes,
                 reinterpret_cast<cudaStream_t>(stream));
 }
 
