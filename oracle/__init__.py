@@ -283,8 +283,9 @@ def lev_sample(v, l, kind, u):
 
 def ca_lev(p, k, r, iters, kind, draws, I0, rank_tol=1e-6):
     """C-A iterations with DMM08 Algorithm 1 on the sketches (orc_ca_lev):
-    draws (2 iters x max(m, n) uniforms).  Returns I (kI), J (kJ), C (m x kJ),
-    U (kJ x kI), R (kI x n), rank, kI, kJ, status."""
+    kind 0 Exactly(k), 1 Expected(k) with SVD-based scores; 2, 3 the same with
+    uniform scores; draws (2 iters x max(m, n) uniforms).  Returns I (kI),
+    J (kJ), C (m x kJ), U (kJ x kI), R (kI x n), rank, kI, kJ, status."""
     mp = _Marshalled(p)
     L = max(p.m, p.n)
     draws = np.ascontiguousarray(draws, dtype=np.float64).reshape(-1)

@@ -1419,10 +1419,21 @@ int32_t orc_lev_sample(const double* v, int64_t n, int32_t l, int32_t kind, cons
  * then U = pinv of the rank-r QRP truncation of G = W'[I, J] (kI x kJ; the
  * rectangular nucleus, of G^T when kI > kJ, transposed back), C = W'[:, J]
  * (m x kJ), R = W[I, :] (kI x n).  Repeated indices (Exactly) stay in the sets.
+ * kind: bit 0 selects the sampling (0 Exactly, 1 Expected); bit 1 replaces the
+ * SVD-based scores by uniform ones (lev_uniform), so kind 2 and 3 sample with
+ * probabilities 1/n.
  * draws: 2 iters steps of max(m, n) uniforms each.  Outputs sized for k.
  * info: rank, kI, kJ, status (ORC_WARN_RANK_DEFICIENT when a sketch had no
  * positive eigenvalue or the nucleus rank is below min(kI, kJ)).
  */
+/* Uniform scores v_j = 1 (probabilities 1/n): the leverage scores of a perturbed
+ * factor-Gaussian input with r << n are nearly equal (the chi-square argument of
+ * the section on superfast leverage scores, Lemma lmchitail and its corollary),
+ * so the SVD stage is skipped. */
+static void lev_uniform(double* v, int64_t n) {
+  for (int64_t j = 0; j < n; ++j) v[j] = 1.0;
+}
+
 int orc_ca_lev(const orc_problem* p, int32_t k, int32_t r, int32_t iters, int32_t kind, const double* draws,
                const int32_t* I0, double rank_tol, int32_t* I, int32_t* J, double* C, double* U, double* R,
                int32_t* info) {
@@ -1435,12 +1446,14 @@ int orc_ca_lev(const orc_problem* p, int32_t k, int32_t r, int32_t iters, int32_
   for (int32_t it = 0; it < iters; ++it) {
     orc_gather_rows(p, I, kI, S);
     if (!all_finite(S, (int64_t)kI * n)) { status = ORC_ERR_NONFINITE; break; }
-    if (orc_lev_scores(S, kI, n, r < kI ? r : kI, v) == 0) status = ORC_WARN_RANK_DEFICIENT;
-    kJ = orc_lev_sample(v, n, k, kind, draws + (size_t)(2 * it) * L, J);
+    if (kind & 2) lev_uniform(v, n);
+    else if (orc_lev_scores(S, kI, n, r < kI ? r : kI, v) == 0) status = ORC_WARN_RANK_DEFICIENT;
+    kJ = orc_lev_sample(v, n, k, kind & 1, draws + (size_t)(2 * it) * L, J);
     orc_gather_cols_t(p, J, kJ, S);
     if (!all_finite(S, (int64_t)kJ * m)) { status = ORC_ERR_NONFINITE; break; }
-    if (orc_lev_scores(S, kJ, m, r < kJ ? r : kJ, v) == 0) status = ORC_WARN_RANK_DEFICIENT;
-    kI = orc_lev_sample(v, m, k, kind, draws + (size_t)(2 * it + 1) * L, I);
+    if (kind & 2) lev_uniform(v, m);
+    else if (orc_lev_scores(S, kJ, m, r < kJ ? r : kJ, v) == 0) status = ORC_WARN_RANK_DEFICIENT;
+    kI = orc_lev_sample(v, m, k, kind & 1, draws + (size_t)(2 * it + 1) * L, I);
   }
   if (status == ORC_ERR_NONFINITE) {
     info[0] = 0; info[1] = kI; info[2] = kJ; info[3] = status;

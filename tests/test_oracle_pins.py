@@ -847,6 +847,42 @@ def test_ca_with_leverage_sampling_recovers_low_rank(kind):
         assert np.linalg.norm(p.W - o["C"] @ o["U"] @ o["R"]) <= 1e-10 * np.linalg.norm(p.W)
 
 
+def test_uniform_scores_sample_by_the_uniform_cdf():
+    """Uniform scores (kind 2, 3) make the sampling independent of the sketch:
+    Exactly(k) takes floor(u n) for each draw (the inverse CDF of 1/n), and
+    Expected(k) keeps j ascending with u_j < k / n, at most k of them; the final
+    sets come from the last iteration's draws."""
+    p = li.dense_lowrank(90, 70, r=6, noise=1e-9, seed=1)
+    it, k = 3, 10
+    d = np.random.default_rng(5).random((2 * it, 90))
+    I0 = li.initial_rows(90, k, 3)
+    o = oracle.ca_lev(p, k, 6, it, 2, d, I0)
+    np.testing.assert_array_equal(o["J"], np.floor(d[2 * it - 2][:k] * 70).astype(int))
+    np.testing.assert_array_equal(o["I"], np.floor(d[2 * it - 1][:k] * 90).astype(int))
+    o = oracle.ca_lev(p, k, 6, it, 3, d, I0)
+    np.testing.assert_array_equal(o["J"], np.flatnonzero(d[2 * it - 2][:70] < k / 70)[:k])
+    np.testing.assert_array_equal(o["I"], np.flatnonzero(d[2 * it - 1][:90] < k / 90)[:k])
+
+
+@pytest.mark.parametrize("kind", [2, 3])
+def test_uniform_scores_suffice_for_factor_gaussian_inputs(kind):
+    """The section on superfast leverage scores: for a perturbed factor-Gaussian
+    input with r << n the leverage scores are nearly uniform (chi-square
+    concentration, Lemma lmchitail), so sampling 4r rows and columns uniformly
+    gives a CUR within a small factor of the perturbation, as the SVD-based
+    scores do."""
+    g = np.random.default_rng(9)
+    for seed in range(4):
+        p = li.factor_gaussian(400, 8, 1e-10, seed=seed)
+        d = g.random(2 * 3 * 400)
+        I0 = li.initial_rows(400, 32, seed)
+        u = oracle.ca_lev(p, 32, 8, 3, kind, d, I0)
+        s = oracle.ca_lev(p, 32, 8, 3, kind - 2, d, I0)
+        eu = np.linalg.norm(p.W - u["C"] @ u["U"] @ u["R"]) / np.linalg.norm(p.W)
+        es = np.linalg.norm(p.W - s["C"] @ s["U"] @ s["R"]) / np.linalg.norm(p.W)
+        assert u["rank"] == 8 and eu <= 1e-8 and eu <= 10 * es, (seed, eu, es)
+
+
 # ------------------------------------------------------------------ FMM partition and matvec
 def test_fmm_partition_covers_every_entry_once_and_far_blocks_are_separated():
     """Far blocks (interaction lists of every level) and near blocks (touching
