@@ -456,11 +456,15 @@ class LevCaWorkload:
     def __init__(self, n=1000, r=10, k=40, iters=8, runs=152, kind=0):
         self.n, self.r, self.k, self.iters, self.runs, self.kind = n, r, k, iters, runs, kind
         self.q = self.s = 64       # the batched residual holds its q x s sample in shared memory
-        tag = "exactly" if kind == 0 else "expected"
+        tag = ("uniform_" if kind & 2 else "") + ("expected" if kind & 1 else "exactly")
         self.name = f"levca_n{n}_r{r}_k{k}_{tag}_it{iters}_x{runs}"
 
     def host(self, rank):
-        p = li.dense_lowrank(self.n, self.n, r=self.r, noise=1e-9, seed=1000 * rank)
+        if self.kind & 2:
+            # uniform scores are the paper's route for perturbed factor-Gaussian inputs
+            p = li.factor_gaussian(self.n, self.r, 1e-9, seed=1000 * rank)
+        else:
+            p = li.dense_lowrank(self.n, self.n, r=self.r, noise=1e-9, seed=1000 * rank)
         blocks = np.array([[0, self.n, 0, self.n]] * self.runs, dtype=np.int64)
         draws = li.rng(77 + rank).random((self.runs, 2 * self.iters, self.n))
         I0 = li.block_initial_rows(blocks, self.k, 5 + rank)
@@ -469,7 +473,10 @@ class LevCaWorkload:
 
     def config(self, h):
         return {"workload": self.name, "m": self.n, "n": self.n, "nrank": self.r, "k_eq_l": self.k,
-                "ca_iterations": self.iters, "sampling": "Exactly(l)" if self.kind == 0 else "Expected(l)",
+                "ca_iterations": self.iters, "sampling": "Expected(l)" if self.kind & 1 else "Exactly(l)",
+                "scores": "uniform (no SVD)" if self.kind & 2 else "SVD-based (Gram + round-robin Jacobi)",
+                "input": ("G1 G2 + 1e-9 G3 (Gaussian factors)" if self.kind & 2 else
+                          "U diag(2^-1..2^-r) V^T + 1e-9 G"),
                 "runs_per_step": self.runs, "residual_sample": f"{self.q}x{self.s} per run"}
 
     def device(self, h, dev):
@@ -495,6 +502,8 @@ class LevCaWorkload:
         # per block: 2 iters sketches of k x n: Gram k^2 n, 10 Jacobi sweeps of (k-1) rounds x k/2 rotations x 12 k,
         # scores r k n (fma = 2 flops)
         k, n = self.k, self.n
+        if self.kind & 2:
+            return 5.0 * k ** 3 * self.runs                  # uniform scores: only the nucleus computes
         per_step = k * k * n + 10 * (k - 1) * (k // 2) * 12 * k + 2 * self.r * k * n
         return 2.0 * self.iters * per_step * self.runs      # one launch runs every block
 
@@ -502,7 +511,9 @@ class LevCaWorkload:
         return {"rel_fro_err_mean": float(np.mean(res["err"])), "rel_fro_err_std": float(np.std(res["err"])),
                 "rel_fro_err_max": float(np.max(res["err"])), "ranks": sorted(set(int(x) for x in res["info"][:, 0])),
                 "statuses": sorted(set(int(x) for x in res["info"][:, 3])),
-                "flops_note": ("per launch (all runs): Gram k^2 n + Jacobi 10 (k-1) (k/2) 12 k + scores 2 r k n per "
+                "flops_note": ("per launch (all runs): the nucleus, 5 k^3 per run (uniform scores: no SVD stage)"
+                               if self.kind & 2 else
+                               "per launch (all runs): Gram k^2 n + Jacobi 10 (k-1) (k/2) 12 k + scores 2 r k n per "
                                "sketch, 2 x iters sketches per run")}
 
     def e2e_setup(self, h, d):
@@ -1318,6 +1329,7 @@ WORKLOADS = {
     "hmatvec_laplace_64K": HMatvecWorkload,
     "hmatvec_laplace_8K": lambda: HMatvecWorkload(npts=1 << 13),
     "levca_n1000_r10_k40_expected": lambda: LevCaWorkload(kind=1),
+    "levca_n1000_r10_k40_uniform": lambda: LevCaWorkload(kind=2),
     "hmt11_n1024_k39_bidiag20_onthefly": lambda: Hmt11Workload(materialize=False),
     "hmt11_n256_k31_bidiag20": lambda: Hmt11Workload(n=256, k=31),
     **{f"laplace65536_k{k}{sfx}": (lambda k=k, e=e: LaplaceSingleWorkload(k, e))

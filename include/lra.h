@@ -541,6 +541,11 @@ lra_status lra_prjvol_batched(const lra_problem* base, const lra_batch* batch, c
  *   min(1, (l v_j) / total), at most l, none kept: the largest v_j.  No
  *   positive score: the first l indices.
  *   vertical: the same on W[:, J]^T (k_J x m) for the rows.
+ *   kind 2 and 3: Exactly(l) and Expected(l) with uniform scores v_j = 1 in
+ *   place of the SVD-based ones (the paper's superfast route for perturbed
+ *   factor-Gaussian inputs with r << n, whose leverage scores are nearly equal
+ *   by the chi-square concentration of Lemma lmchitail): no Gram matrix and no
+ *   Jacobi sweeps; r is then unused (but must still be valid).
  * Then U = pinv of the rank-r QRP truncation of W[I, J] (k_I x k_J; of its
  * transpose when k_I > k_J, transposed back), C = W[:, J], R = W[I, :].
  * k: 1..64, <= every block's rows and columns; r: 1..k; iters >= 1; I0: nb x k

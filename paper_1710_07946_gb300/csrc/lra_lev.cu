@@ -11,7 +11,10 @@
 // W[:, J] for the rows.  Finally U = pinv of the rank-r QRP truncation of
 // W[I, J], C = W[:, J], R = W[I, :].  Every floating-point step is the oracle's
 // operation for operation (sequential sums where the oracle sums sequentially),
-// so the sampled indices match bit for bit.
+// so the sampled indices match bit for bit.  With uniform scores (kind 2, 3) the
+// SVD stage is skipped and every score is 1: for perturbed factor-Gaussian
+// inputs with r << n the leverage scores are nearly equal, which is how the
+// paper makes that stage superfast.
 #include <algorithm>
 #include <cstring>
 
@@ -332,10 +335,17 @@ __global__ void __launch_bounds__(NT, 1) lev_batched_kernel(LevArgs B) {
         }
         __syncthreads();
         if (s_bad) { st = LRA_ERR_NONFINITE; break; }
-        const int re = lev_scores(S, kS, len, min(B.r, kS), Gs, Qs, Ts, s_cs, s_sel, &s_re, v);
-        if (re == 0) st = max(st, (int)LRA_WARN_RANK_DEFICIENT);
+        if (B.kind & 2) {
+          // uniform scores (the SVD stage bypassed): v_j = 1
+          for (int64_t j = tid; j < len; j += nt) v[j] = 1.0;
+          __syncthreads();
+        } else {
+          const int re = lev_scores(S, kS, len, min(B.r, kS), Gs, Qs, Ts, s_cs, s_sel, &s_re, v);
+          if (re == 0) st = max(st, (int)LRA_WARN_RANK_DEFICIENT);
+        }
         const double* u = ub + (size_t)(2 * it + dir) * B.max_len;
-        const int cnt = lev_sample(v, len, k, B.kind, u, cum, flags, dir == 0 ? s_J : s_I, &s_cnt, &s_tot, &s_last);
+        const int cnt = lev_sample(v, len, k, B.kind & 1, u, cum, flags, dir == 0 ? s_J : s_I, &s_cnt, &s_tot,
+                                   &s_last);
         if (dir == 0) kJ = cnt;
         else kI = cnt;
       }
@@ -425,7 +435,7 @@ static lra_status lev_check(const lra_problem* base, const lra_batch* batch, int
   if (batch == nullptr || batch->blocks == nullptr || batch->offsets == nullptr || batch->nb < 1 ||
       batch->max_len < 1)
     return LRA_ERR_INVALID_ARG;
-  if (k < 1 || k > KMAX || r < 1 || r > k || iters < 1 || (kind != 0 && kind != 1)) return LRA_ERR_INVALID_ARG;
+  if (k < 1 || k > KMAX || r < 1 || r > k || iters < 1 || kind < 0 || kind > 3) return LRA_ERR_INVALID_ARG;
   return LRA_OK;
 }
 

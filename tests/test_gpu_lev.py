@@ -82,3 +82,17 @@ def test_benchmark_configuration_sampled_runs():
     r = 10, eight iterations, Exactly) on 8 runs, all compared."""
     p = li.dense_lowrank(1000, 1000, r=10, noise=1e-9, seed=0)
     run(p, [[0, 1000, 0, 1000]] * 8, 40, 10, 8, 0, seed=77)
+
+
+@pytest.mark.parametrize("kind", [2, 3])
+def test_uniform_scores(kind):
+    """Uniform scores (no SVD stage) on perturbed factor-Gaussian inputs and on
+    blocks of a graded low-rank one; the benchmark's uniform configuration."""
+    p = li.factor_gaussian(600, 10, 1e-9, seed=kind)
+    run(p, [[0, 600, 0, 600], [100, 300, 50, 500], [17, 64, 3, 65]], 40, 10, 4, kind, seed=kind)
+    q = li.dense_lowrank(700, 650, r=20, noise=1e-9, seed=3)
+    run(q, [[0, 700, 0, 650], [50, 300, 100, 500]], 24, 6, 3, kind, seed=5)
+    f = li.factor_gaussian(1000, 10, 1e-9, seed=0)
+    lb = run(f, [[0, 1000, 0, 1000]] * 4, 40, 10, 8, kind, seed=77)
+    g = lb.block(0)
+    assert np.linalg.norm(f.W - g["C"] @ g["U"] @ g["R"]) <= 1e-7 * np.linalg.norm(f.W)

@@ -43,7 +43,8 @@ def test_leverage_batch_rejects_bad_parameters():
     I0 = li.block_initial_rows(blocks, 8, 1)
     draws = np.zeros((1, 2, 100))
     assert "INVALID_ARG" in str(_err(lra.LevBatch, prob, blocks, 8, 9, 1, 0, I0, draws))          # r > k
-    assert "INVALID_ARG" in str(_err(lra.LevBatch, prob, blocks, 8, 4, 1, 2, I0, draws))          # kind 2
+    assert "INVALID_ARG" in str(_err(lra.LevBatch, prob, blocks, 8, 4, 1, 4, I0, draws))          # kind 4
+    assert "INVALID_ARG" in str(_err(lra.LevBatch, prob, blocks, 8, 4, 1, -1, I0, draws))         # kind -1
     with pytest.raises(ValueError):
         lra.LevBatch(prob, blocks, 8, 4, 2, 0, I0, draws)                                          # draws too short
 
