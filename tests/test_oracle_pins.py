@@ -883,6 +883,44 @@ def test_uniform_scores_suffice_for_factor_gaussian_inputs(kind):
         assert u["rank"] == 8 and eu <= 1e-8 and eu <= 10 * es, (seed, eu, es)
 
 
+def _bidiag_dense(n, q, seed):
+    """The oracle's product of q bidiagonal factors, as a dense integer matrix."""
+    perms, signs = li.bidiag_descriptor(n, q, seed)
+    rows, vals = oracle.bidiag_columns(n, q, perms, signs)
+    cols = np.broadcast_to(np.arange(n)[:, None], rows.shape)
+    m = vals != 0
+    M = np.zeros((n, n))
+    M[rows[m], cols[m]] = vals[m]
+    return M
+
+
+def test_bidiag_products_are_nearly_gaussian():
+    """Theorem thm1 and the experiment of Figure LowRkTest1 (n = 1024, 20 random
+    permuted cyclic bidiagonal factors).  Every factor doubles the expected
+    squared norm of a column and the rows are exchangeable, so each entry has
+    mean 0 and variance exactly 2^q / n.  After that scaling, one fixed entry
+    taken over independent products passes the Kolmogorov-Smirnov test for
+    N(0, 1), and two such entries are uncorrelated.  Over all 2^20 entries of
+    one product the first four moments are Gaussian's and the KS distance is
+    below 0.005."""
+    st = pytest.importorskip("scipy.stats")
+    n, q, reps = 1024, 20, 120
+    sd = np.sqrt(2.0 ** q / n)
+    a, b = [], []
+    for rep in range(reps):
+        M = _bidiag_dense(n, q, 3000 + rep)
+        a.append(M[17, 400] / sd)
+        b.append(M[900, 33] / sd)
+        if rep < 2:
+            x = M.ravel() / sd
+            assert abs(x.mean()) < 0.01 and abs(x.var() - 1.0) < 0.03 and abs(st.kurtosis(x)) < 0.1
+            jit = (M.ravel() + np.random.default_rng(rep).random(n * n) - 0.5) / sd   # continuous version
+            assert st.kstest(jit, "norm").statistic < 0.005
+    assert st.kstest(np.array(a), "norm").pvalue > 0.01
+    assert st.kstest(np.array(b), "norm").pvalue > 0.01
+    assert abs(np.corrcoef(a, b)[0, 1]) < 4.0 / np.sqrt(reps)
+
+
 # ------------------------------------------------------------------ FMM partition and matvec
 def test_fmm_partition_covers_every_entry_once_and_far_blocks_are_separated():
     """Far blocks (interaction lists of every level) and near blocks (touching
