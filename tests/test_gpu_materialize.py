@@ -156,3 +156,34 @@ def test_residual_statistics_over_a_million_entries():
     assert abs(st_g[0] - st_o[0]) <= 1e-9 * st_o[2]
     E = p.W - o["C"] @ o["U"] @ o["R"]
     assert abs(st_g[4] - np.linalg.norm(E) / np.linalg.norm(p.W)) <= 1e-9 * st_g[4]
+
+
+def test_bidiag20_products_written_out_are_nearly_gaussian():
+    """Figure LowRkTest1's experiment on the device path: W' = I M for products
+    M of 20 permuted cyclic bidiagonal factors (n = 1024), written out by
+    lra_multiplier_apply with M's scale 2^{-10}.  The first product equals the
+    oracle's integer product bit for bit.  One fixed entry over 60 independent
+    products, times 32 (1 / its standard deviation 2^{-10} sqrt(2^20 / 1024)),
+    passes the Kolmogorov-Smirnov test for N(0, 1), and two entries are
+    uncorrelated."""
+    import paper_1710_07946_gb300 as lra
+    st = pytest.importorskip("scipy.stats")
+    n, q, reps = 1024, 20, 60
+    prob = lra.Problem.dense(torch.eye(n, dtype=torch.float64, device="cuda"))
+    a, b = [], []
+    for rep in range(reps):
+        perms, signs = li.bidiag_descriptor(n, q, 7000 + rep)
+        mult = lra.lra_precondition("bidiag", n, q, perms, signs)
+        Mp = lra.lra_multiplier_apply(prob, mult)
+        if rep == 0:
+            rows, vals = oracle.bidiag_columns(n, q, perms, signs)
+            M = np.zeros((n, n))
+            cols = np.broadcast_to(np.arange(n)[:, None], rows.shape)
+            msk = vals != 0
+            M[rows[msk], cols[msk]] = vals[msk]
+            np.testing.assert_array_equal(Mp.cpu().numpy(), M * 2.0 ** -10)
+        a.append(Mp[17, 400].item() * 32.0)
+        b.append(Mp[900, 33].item() * 32.0)
+    assert st.kstest(np.array(a), "norm").pvalue > 0.01
+    assert st.kstest(np.array(b), "norm").pvalue > 0.01
+    assert abs(np.corrcoef(a, b)[0, 1]) < 4.0 / np.sqrt(reps)
