@@ -111,6 +111,47 @@ def staged_flops(stages, kb, m, n, nrun, loops, swaps, entry_flops):
     return f
 
 
+def fmm_oracle_blocks(c, idxs, budget_s):
+    """The FP64 oracle on the FMM blocks idxs (in order) until budget_s: the
+    staged (or fixed-size) C-A, the nucleus and the sampled residual against
+    FP64 entries.  Returns (blocks within the error bound, blocks, seconds)."""
+    import oracle
+    b = c["blocks"]
+    t0 = time.perf_counter()
+    n = good = 0
+    for idx in idxs:
+        r0, nr, c0, nc = b[idx]
+        kb = int(min(c["k"], nr, nc))
+        sub = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=c["X"][r0:r0 + nr], Y=c["Y"][c0:c0 + nc])
+        sube = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=sub.X, Y=sub.Y, entries=c["entries"])
+        if c["stages"]:
+            o = oracle.ca_run_adaptive(sube, c["stages"], c["margin"], c["sweeps"], c["I0"][idx], h=c["h"],
+                                       rank_tol=c["tol"])
+        else:
+            o = oracle.ca_run(sube, kb, c["sweeps"], c["I0"][idx, :kb], h=c["h"], rank_tol=c["tol"])
+        st = oracle.residual_sample(sub, o["C"], o["U"], o["R"], c["Q"][idx], c["S"][idx])
+        n += 1
+        good += st[4] <= ERR_BOUND
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return good, n, time.perf_counter() - t0
+
+
+_FMM_CTX = None
+
+
+def _fmm_oracle_init(ctx):
+    global _FMM_CTX
+    _FMM_CTX = ctx
+    import oracle
+    oracle.lib()
+
+
+def _fmm_oracle_chunk(args):
+    idxs, budget_s = args
+    return fmm_oracle_blocks(_FMM_CTX, idxs, budget_s)
+
+
 class FmmWorkload:
     base = "fmm_laplace_1M_octree_4096blocks"
     kernel = "ca_batched_kernel"
@@ -241,30 +282,31 @@ class FmmWorkload:
         hp["copy"].synchronize()
 
     # the FP64 oracle on one block
+    def oracle_ctx(self, h):
+        return dict(X=h["p"].X, Y=h["p"].Y, blocks=h["blocks"], I0=h["I0"], Q=h["Q"], S=h["S"], k=self.k,
+                    entries=self.entries, stages=self.stages, margin=self.margin, sweeps=self.sweeps, h=self.h,
+                    tol=self.tol)
+
     def oracle_units(self, h, budget_s, seed=0):
-        import oracle
-        b = h["blocks"]
-        order = np.random.default_rng(seed).permutation(len(b))
-        t0 = time.perf_counter()
-        n = 0
-        good = 0
-        for idx in order:
-            r0, nr, c0, nc = b[idx]
-            kb = int(min(self.k, nr, nc))
-            sub = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=h["p"].X[r0:r0 + nr], Y=h["p"].Y[c0:c0 + nc])
-            sube = li.Problem(li.SRC_LAPLACE, int(nr), int(nc), X=sub.X, Y=sub.Y, entries=self.entries)
-            if self.stages:
-                o = oracle.ca_run_adaptive(sube, self.stages, self.margin, self.sweeps, h["I0"][idx], h=self.h,
-                                           rank_tol=self.tol)
-            else:
-                o = oracle.ca_run(sube, kb, self.sweeps, h["I0"][idx, :kb], h=self.h, rank_tol=self.tol)
-            st = oracle.residual_sample(sub, o["C"], o["U"], o["R"], h["Q"][idx], h["S"][idx])
-            n += 1
-            good += st[4] <= ERR_BOUND
-            if time.perf_counter() - t0 >= budget_s:
-                break
-        el = time.perf_counter() - t0
+        order = np.random.default_rng(seed).permutation(len(h["blocks"]))
+        good, n, el = fmm_oracle_blocks(self.oracle_ctx(h), order, budget_s)
         return good, n, el, f"{n} randomly chosen blocks of the same batch (C-A + nucleus + residual sample each)"
+
+    def oracle_units_allcores(self, h, budget_s, seed=0):
+        """The same oracle over blocks on every host core: one spawned process per
+        core, each taking its share of a random block order until budget_s;
+        value = all processes' good blocks / the longest process time."""
+        import multiprocessing as mp
+        ncpu = os.cpu_count() or 1
+        order = np.random.default_rng(seed).permutation(len(h["blocks"]))
+        chunks = [(order[i::ncpu], budget_s) for i in range(ncpu)]
+        with mp.get_context("spawn").Pool(ncpu, initializer=_fmm_oracle_init, initargs=(self.oracle_ctx(h),)) as pool:
+            res = pool.map(_fmm_oracle_chunk, chunks)
+        good = sum(r[0] for r in res)
+        n = sum(r[1] for r in res)
+        el = max(r[2] for r in res)
+        return good, n, el, ncpu, (f"{n} randomly chosen blocks of the same batch (C-A + nucleus + residual sample "
+                                   f"each) in {ncpu} processes, one per host core, {el:.1f} s")
 
 
 class DenseWorkload:
@@ -1659,6 +1701,13 @@ def run_lib(args, wl):
             good, n, el, desc = wl.oracle_units(h, args.cpu_budget)
             line["cpu_baseline"] = {"value": good / el, "unit": wl.unit, "cores": cpu_cores_used(), "kind": "oracle",
                                     "sample": f"{desc}; {el:.1f} s on 1 host thread"}
+            if isinstance(wl, FmmWorkload) and type(wl).oracle_units is FmmWorkload.oracle_units:
+                try:
+                    good, n, el, ncpu, desc = wl.oracle_units_allcores(h, args.cpu_budget)
+                    line["cpu_baseline_allcores"] = {"value": good / el, "unit": wl.unit, "cores": ncpu,
+                                                     "kind": "oracle", "sample": desc}
+                except Exception as e:          # the single-thread figure above stands on its own
+                    line["cpu_baseline_allcores"] = {"error": f"{type(e).__name__}: {e}"}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
