@@ -159,6 +159,101 @@ __device__ bool ov_contract(double* M, int ldm, double* s, int32_t* pos, int32_t
   return true;
 }
 
+// The next block of the batch from the work queue, or -1 once it is empty (the
+// same value in every thread).  Called by the whole CTA.
+__device__ int ov_next_block(const OvArgs& B, int* s_b) {
+  if (threadIdx.x == 0) {
+    const unsigned int qh = atomicAdd(B.counter, 1u);
+    *s_b = (qh < (unsigned)B.nb) ? (B.order ? B.order[qh] : (int)qh) : -1;
+  }
+  __syncthreads();
+  const int b = *s_b;
+  __syncthreads();
+  return b;
+}
+
+// Block b's sub-problem: false, after writing the block's status, when its
+// descriptor or its C-A run is unusable (a failed run keeps its status).
+// Otherwise nr, nc, k (the run's generator size), lb = min(k + pextra, nc) and
+// the maxvol arguments A for the row strip W'[I, :] (no swaps; leading
+// dimension nc when cols_only, else max(nr, nc); the strip in shared memory
+// when it fits, else in gstrip).
+__device__ bool ov_block_begin(const OvArgs& B, int b, bool cols_only, double* gstrip, CaArgs& A, int64_t& nr,
+                               int64_t& nc, int& k, int& lb) {
+  int32_t* info = B.info + LRA_INFO_LEN * (size_t)b;
+  const int32_t* inf0 = B.info_in + LRA_INFO_LEN * (size_t)b;
+  const int64_t r0 = B.blocks[4 * (size_t)b], c0 = B.blocks[4 * (size_t)b + 2];
+  nr = B.blocks[4 * (size_t)b + 1];
+  nc = B.blocks[4 * (size_t)b + 3];
+  const int st_in = inf0[3];
+  k = inf0[6];
+  if (r0 < 0 || c0 < 0 || nr < 1 || nc < 1 || r0 + nr > B.base.m || c0 + nc > B.base.n || nr > B.max_len ||
+      nc > B.max_len || (st_in != LRA_OK && st_in < 16) || k < 1 || k > B.kmax || k > min(nr, nc)) {
+    for (int e = threadIdx.x; e < LRA_INFO_LEN; e += blockDim.x)
+      info[e] = (e == 3) ? ((st_in != LRA_OK && st_in < 16) ? st_in : LRA_ERR_INVALID_ARG) : 0;
+    return false;
+  }
+  lb = (int)min((int64_t)(k + B.pextra), nc);
+  std::memset(&A, 0, sizeof(A));
+  A.P = B.base;
+  A.P.m = nr;
+  A.P.n = nc;
+  if (A.P.src == LRA_DENSE) {
+    const size_t esz = (A.P.dtype == LRA_F32) ? 4 : 8;
+    A.P.W = static_cast<const unsigned char*>(B.base.W) + (size_t)(r0 * B.base.ldw + c0) * esz;
+  } else {
+    A.P.X = B.base.X + 3 * r0;
+    A.P.Y = B.base.Y + 3 * c0;
+  }
+  A.k = k;
+  A.max_swaps = 0;
+  A.h = B.h;
+  A.chunk_n = (int)nc;
+  A.chunk_m = (int)nr;
+  A.ldm = cols_only ? (int)nc : (int)max(nr, nc);
+  A.strip_in_smem = ca_smem_fixed(k, A.ldm) + sizeof(double) * (size_t)k * A.ldm <= B.smem_bytes;
+  A.gstrip = A.strip_in_smem ? nullptr : gstrip;
+  return true;
+}
+
+// Outputs of block b at l columns J' = Jb: C = W'[:, J'] (nr x l), R = W[I, :]
+// (k x nc), the rows I, U = the rectangular nucleus of G = W'[I, J'] (formed in
+// the CTA's scratch G), and info = (rank, i1, i2, status, 0, 0, k, l), the
+// status turned to LRA_WARN_RANK_DEFICIENT when it was LRA_OK and the rank is
+// below k.  Called by the whole CTA.
+__device__ void ov_block_finish(const OvArgs& B, int b, const CaArgs& A, int64_t nr, int64_t nc, int k, int l,
+                                const int32_t* Jb, int st, int i1, int i2, double* G, unsigned char* smem) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int32_t* info = B.info + LRA_INFO_LEN * (size_t)b;
+  __syncthreads();
+  const int32_t* Ib = B.Iin + (size_t)b * B.kmax;
+  double* Cb = B.C + B.offs[2 * (size_t)b];
+  double* Rb = B.R + B.offs[2 * (size_t)b + 1];
+  for (int64_t it = tid; it < nr * l; it += nt) {
+    const int64_t i = it / l;
+    const int a = (int)(it - i * l);
+    Cb[it] = wp_entry(A.P, i, Jb[a]);
+  }
+  for (int64_t it = tid; it < (int64_t)k * nc; it += nt) {
+    const int a = (int)(it / nc);
+    const int64_t c = it - (int64_t)a * nc;
+    Rb[it] = w_entry(A.P, Ib[a], c);
+  }
+  for (int it = tid; it < k * l; it += nt) {
+    const int a = it / l, c = it - a * l;
+    G[it] = wp_entry(A.P, Ib[a], Jb[c]);
+  }
+  for (int a = tid; a < k; a += nt) B.I[(size_t)b * B.kmax + a] = Ib[a];
+  __syncthreads();
+  const int rank = nucleus_rect_cta(G, k, l, B.rank_tol, B.U + (size_t)b * B.lmax * B.kmax, smem);
+  if (tid == 0) {
+    if (rank < k && st == LRA_OK) st = LRA_WARN_RANK_DEFICIENT;
+    info[0] = rank; info[1] = i1; info[2] = i2; info[3] = st; info[4] = 0; info[5] = 0; info[6] = k;
+    info[7] = l;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(NT) oversample_kernel(OvArgs B) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_b;
@@ -172,47 +267,13 @@ __global__ void __launch_bounds__(NT) oversample_kernel(OvArgs B) {
   double* gstrip = G + (size_t)B.kmax * B.lmax;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (;;) {
-    if (tid == 0) {
-      const unsigned int qh = atomicAdd(B.counter, 1u);
-      s_b = (qh < (unsigned)B.nb) ? (B.order ? B.order[qh] : (int)qh) : -1;
-    }
-    __syncthreads();
-    const int b = s_b;
-    __syncthreads();
+    const int b = ov_next_block(B, &s_b);
     if (b < 0) break;
     int32_t* info = B.info + LRA_INFO_LEN * (size_t)b;
-    const int32_t* inf0 = B.info_in + LRA_INFO_LEN * (size_t)b;
-    const int64_t r0 = B.blocks[4 * (size_t)b], nr = B.blocks[4 * (size_t)b + 1];
-    const int64_t c0 = B.blocks[4 * (size_t)b + 2], nc = B.blocks[4 * (size_t)b + 3];
-    const int st_in = inf0[3];
-    const int k = inf0[6];
-    if (r0 < 0 || c0 < 0 || nr < 1 || nc < 1 || r0 + nr > B.base.m || c0 + nc > B.base.n || nr > B.max_len ||
-        nc > B.max_len || (st_in != LRA_OK && st_in < 16) || k < 1 || k > B.kmax || k > min(nr, nc)) {
-      for (int e = tid; e < LRA_INFO_LEN; e += nt)
-        info[e] = (e == 3) ? ((st_in != LRA_OK && st_in < 16) ? st_in : LRA_ERR_INVALID_ARG) : 0;
-      continue;
-    }
-    const int lb = (int)min((int64_t)(k + B.pextra), nc);
     CaArgs A;
-    std::memset(&A, 0, sizeof(A));
-    A.P = B.base;
-    A.P.m = nr;
-    A.P.n = nc;
-    if (A.P.src == LRA_DENSE) {
-      const size_t esz = (A.P.dtype == LRA_F32) ? 4 : 8;
-      A.P.W = static_cast<const unsigned char*>(B.base.W) + (size_t)(r0 * B.base.ldw + c0) * esz;
-    } else {
-      A.P.X = B.base.X + 3 * r0;
-      A.P.Y = B.base.Y + 3 * c0;
-    }
-    A.k = k;
-    A.max_swaps = 0;
-    A.h = B.h;
-    A.chunk_n = (int)nc;
-    A.chunk_m = (int)nr;
-    A.ldm = (int)max(nr, nc);
-    A.strip_in_smem = ca_smem_fixed(k, A.ldm) + sizeof(double) * (size_t)k * A.ldm <= B.smem_bytes;
-    A.gstrip = A.strip_in_smem ? nullptr : gstrip;
+    int64_t nr, nc;
+    int k, lb;
+    if (!ov_block_begin(B, b, false, gstrip, A, nr, nc, k, lb)) continue;
     int32_t* Jb = B.J + (size_t)b * B.lmax;
     int l = k, st = LRA_OK, cycles = 0, ptried = 0;
     {
@@ -308,34 +369,7 @@ __global__ void __launch_bounds__(NT) oversample_kernel(OvArgs B) {
         for (int a = tid; a < l; a += nt) Jb[a] = s_Jw[a];
       }
     }
-    __syncthreads();
-    // outputs at l: C = W'[:, J'] (nr x l), R = W[I, :] (k x nc), G = W'[I, J'] -> U
-    const int32_t* Ib = B.Iin + (size_t)b * B.kmax;
-    double* Cb = B.C + B.offs[2 * (size_t)b];
-    double* Rb = B.R + B.offs[2 * (size_t)b + 1];
-    for (int64_t it = tid; it < nr * l; it += nt) {
-      const int64_t i = it / l;
-      const int a = (int)(it - i * l);
-      Cb[it] = wp_entry(A.P, i, Jb[a]);
-    }
-    for (int64_t it = tid; it < (int64_t)k * nc; it += nt) {
-      const int a = (int)(it / nc);
-      const int64_t c = it - (int64_t)a * nc;
-      Rb[it] = w_entry(A.P, Ib[a], c);
-    }
-    for (int it = tid; it < k * l; it += nt) {
-      const int a = it / l, c = it - a * l;
-      G[it] = wp_entry(A.P, Ib[a], Jb[c]);
-    }
-    for (int a = tid; a < k; a += nt) B.I[(size_t)b * B.kmax + a] = Ib[a];
-    __syncthreads();
-    const int rank = nucleus_rect_cta(G, k, l, B.rank_tol, B.U + (size_t)b * B.lmax * B.kmax, smem);
-    if (tid == 0) {
-      if (rank < k && st == LRA_OK) st = LRA_WARN_RANK_DEFICIENT;
-      info[0] = rank; info[1] = cycles; info[2] = ptried; info[3] = st; info[4] = 0; info[5] = 0; info[6] = k;
-      info[7] = l;
-    }
-    __syncthreads();
+    ov_block_finish(B, b, A, nr, nc, k, l, Jb, st, cycles, ptried, G, smem);
   }
 }
 
@@ -415,47 +449,14 @@ __global__ void __launch_bounds__(NT) prjvol_kernel(OvArgs B) {
   double* gstrip = G + (size_t)B.kmax * B.lmax;
   const int tid = threadIdx.x, nt = blockDim.x;
   for (;;) {
-    if (tid == 0) {
-      const unsigned int qh = atomicAdd(B.counter, 1u);
-      s_b = (qh < (unsigned)B.nb) ? (B.order ? B.order[qh] : (int)qh) : -1;
-    }
-    __syncthreads();
-    const int b = s_b;
-    __syncthreads();
+    const int b = ov_next_block(B, &s_b);
     if (b < 0) break;
     int32_t* info = B.info + LRA_INFO_LEN * (size_t)b;
-    const int32_t* inf0 = B.info_in + LRA_INFO_LEN * (size_t)b;
-    const int64_t r0 = B.blocks[4 * (size_t)b], nr = B.blocks[4 * (size_t)b + 1];
-    const int64_t c0 = B.blocks[4 * (size_t)b + 2], nc = B.blocks[4 * (size_t)b + 3];
-    const int st_in = inf0[3];
-    const int k = inf0[6];
-    if (r0 < 0 || c0 < 0 || nr < 1 || nc < 1 || r0 + nr > B.base.m || c0 + nc > B.base.n || nr > B.max_len ||
-        nc > B.max_len || (st_in != LRA_OK && st_in < 16) || k < 1 || k > B.kmax || k > min(nr, nc)) {
-      for (int e = tid; e < LRA_INFO_LEN; e += nt)
-        info[e] = (e == 3) ? ((st_in != LRA_OK && st_in < 16) ? st_in : LRA_ERR_INVALID_ARG) : 0;
-      continue;
-    }
-    const int lb = (int)min((int64_t)(k + B.pextra), nc);
     CaArgs A;
-    std::memset(&A, 0, sizeof(A));
-    A.P = B.base;
-    A.P.m = nr;
-    A.P.n = nc;
-    if (A.P.src == LRA_DENSE) {
-      const size_t esz = (A.P.dtype == LRA_F32) ? 4 : 8;
-      A.P.W = static_cast<const unsigned char*>(B.base.W) + (size_t)(r0 * B.base.ldw + c0) * esz;
-    } else {
-      A.P.X = B.base.X + 3 * r0;
-      A.P.Y = B.base.Y + 3 * c0;
-    }
-    A.k = k;
+    int64_t nr, nc;
+    int k, lb;
+    if (!ov_block_begin(B, b, true, gstrip, A, nr, nc, k, lb)) continue;
     A.max_swaps = B.max_swaps;
-    A.h = B.h;
-    A.chunk_n = (int)nc;
-    A.chunk_m = (int)nr;
-    A.ldm = (int)nc;
-    A.strip_in_smem = ca_smem_fixed(k, A.ldm) + sizeof(double) * (size_t)k * A.ldm <= B.smem_bytes;
-    A.gstrip = A.strip_in_smem ? nullptr : gstrip;
     int32_t* Jb = B.J + (size_t)b * B.lmax;
     int l = k, st = LRA_OK, nsw = 0, r = 0;
     {
@@ -505,34 +506,7 @@ __global__ void __launch_bounds__(NT) prjvol_kernel(OvArgs B) {
         for (int a = tid; a < l; a += nt) Jb[a] = s_Jw[a];
       }
     }
-    __syncthreads();
-    // outputs at l: C = W'[:, J'] (nr x l), R = W[I, :] (k x nc), G = W'[I, J'] -> U
-    const int32_t* Ib = B.Iin + (size_t)b * B.kmax;
-    double* Cb = B.C + B.offs[2 * (size_t)b];
-    double* Rb = B.R + B.offs[2 * (size_t)b + 1];
-    for (int64_t it = tid; it < nr * l; it += nt) {
-      const int64_t i = it / l;
-      const int a = (int)(it - i * l);
-      Cb[it] = wp_entry(A.P, i, Jb[a]);
-    }
-    for (int64_t it = tid; it < (int64_t)k * nc; it += nt) {
-      const int a = (int)(it / nc);
-      const int64_t c = it - (int64_t)a * nc;
-      Rb[it] = w_entry(A.P, Ib[a], c);
-    }
-    for (int it = tid; it < k * l; it += nt) {
-      const int a = it / l, c = it - a * l;
-      G[it] = wp_entry(A.P, Ib[a], Jb[c]);
-    }
-    for (int a = tid; a < k; a += nt) B.I[(size_t)b * B.kmax + a] = Ib[a];
-    __syncthreads();
-    const int rank = nucleus_rect_cta(G, k, l, B.rank_tol, B.U + (size_t)b * B.lmax * B.kmax, smem);
-    if (tid == 0) {
-      if (rank < k && st == LRA_OK) st = LRA_WARN_RANK_DEFICIENT;
-      info[0] = rank; info[1] = nsw; info[2] = r; info[3] = st; info[4] = 0; info[5] = 0; info[6] = k;
-      info[7] = l;
-    }
-    __syncthreads();
+    ov_block_finish(B, b, A, nr, nc, k, l, Jb, st, nsw, r, G, smem);
   }
 }
 

@@ -96,3 +96,16 @@ def test_fmm_benchmark_workload_sampled_blocks():
     sizes = blocks[:, 1] * blocks[:, 3]
     pick = list(np.argsort(sizes)[:3]) + list(np.argsort(sizes)[-3:])
     run(q, blocks, 64, 8, 1e-6, stages=(28, 40, 64), h=1.05, check=pick, margin=2)
+
+
+def test_dense_fp32_input_single_column_generators_and_no_extra_columns():
+    """A dense FP32 input (entries widened exactly) of rank 6 plus noise: k = 12
+    with no extra columns (l = k), and k = 1 grown by three columns."""
+    g = np.random.default_rng(4)
+    W = (g.standard_normal((500, 6)) @ g.standard_normal((6, 400)) + 1e-4 * g.standard_normal((500, 400)))
+    p = li.Problem(li.SRC_DENSE, 500, 400, W=np.ascontiguousarray(W.astype(np.float32)))
+    blocks = np.array([[0, 500, 0, 400], [10, 200, 30, 300], [100, 64, 100, 65], [7, 33, 5, 29]], dtype=np.int64)
+    _, _, out = run(p, blocks, 12, 0, 1e-3)
+    assert all(g_["l"] == g_["k"] for g_, _ in out)
+    assert any(g_["srank"] < g_["k"] for g_, _ in out)
+    run(p, blocks, 1, 3, 1e-13)
