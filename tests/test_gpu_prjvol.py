@@ -109,3 +109,20 @@ def test_dense_fp32_input_single_column_generators_and_no_extra_columns():
     assert all(g_["l"] == g_["k"] for g_, _ in out)
     assert any(g_["srank"] < g_["k"] for g_, _ in out)
     run(p, blocks, 1, 3, 1e-13)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_configurations(seed):
+    """Randomised sweep: input rank 2..24 with no, small or large noise; block
+    sizes from 1 to 300 in every pairing; k 1..32; 0..8 extra columns; h and
+    rank tolerances across their useful range."""
+    g = np.random.default_rng(500 + seed)
+    r = int(g.integers(2, 25))
+    noise = (0.0, 1e-9, 1e-4)[seed % 3]
+    p = li.factor_gaussian(700, r, noise, seed=seed)
+    blocks = li.dense_blocks(700, sizes=(1, 9, 33, 64, 300), seed=seed)
+    k = int(g.integers(1, 33))
+    pextra = int(g.integers(0, 9))
+    tol = (1e-13, 1e-8, 1e-4)[(seed // 3 + seed) % 3]
+    h = (1.01, 1.05, 1.2)[seed % 3]
+    run(p, blocks, k, pextra, tol, h=h, seed=seed)
