@@ -85,6 +85,41 @@ __device__ double block_sum_d(double v, double* red) {
   return r;
 }
 
+// Row stride (floats) of the right-hand-side tiles and of t2, s2: nrhs + 4 when
+// nrhs is a multiple of 4 (rows 16-byte aligned for float4 loads; the pad puts
+// consecutive rows 4 banks apart, so the 8 rows of one 128-bit load phase fall in
+// distinct banks), else nrhs | 1 (odd: consecutive rows in distinct banks).
+__host__ __device__ inline int gauss_ldr(int nrhs) { return (nrhs & 3) == 0 ? nrhs + 4 : (nrhs | 1); }
+
+// Four outputs at once (the register-tiled form of the scalar loops, same
+// arithmetic): s[q] = fmaf(P[r * pr], Q[r * ldq + q], s[q]) for r = 0..nr-1 in
+// ascending order, q < 4; Q 16-byte aligned with ldq a multiple of 4.  Each
+// s[q] is the one ascending fmaf chain the scalar loop forms for its output.
+__device__ __forceinline__ void chain4(const float* P, int pr, int nr, const float* Q, int ldq, float s[4]) {
+  for (int r = 0; r < nr; ++r) {
+    const float p = P[r * pr];
+    const float4 q = *reinterpret_cast<const float4*>(Q + (size_t)r * ldq);
+    s[0] = fmaf(p, q.x, s[0]);
+    s[1] = fmaf(p, q.y, s[1]);
+    s[2] = fmaf(p, q.z, s[2]);
+    s[3] = fmaf(p, q.w, s[3]);
+  }
+}
+
+// Two dot products over c < nrhs (a multiple of 4) sharing the row A:
+// s0 = sum A[c] B0[c], s1 = sum A[c] B1[c], each one ascending fmaf chain (the
+// scalar loop's order), the rows read as float4.
+__device__ __forceinline__ void dot2(const float* A, const float* B0, const float* B1, int nrhs, float& s0,
+                                     float& s1) {
+  for (int c = 0; c < nrhs; c += 4) {
+    const float4 a = *reinterpret_cast<const float4*>(A + c);
+    const float4 b0 = *reinterpret_cast<const float4*>(B0 + c);
+    const float4 b1 = *reinterpret_cast<const float4*>(B1 + c);
+    s0 = fmaf(a.x, b0.x, s0); s0 = fmaf(a.y, b0.y, s0); s0 = fmaf(a.z, b0.z, s0); s0 = fmaf(a.w, b0.w, s0);
+    s1 = fmaf(a.x, b1.x, s1); s1 = fmaf(a.y, b1.y, s1); s1 = fmaf(a.z, b1.z, s1); s1 = fmaf(a.w, b1.w, s1);
+  }
+}
+
 // U = G^{-1} (k x k, FP64) by Gauss-Jordan with partial pivoting on [G | I] in
 // shared memory A (k x 2k).  Returns 0 when a pivot is exactly zero.
 __device__ int gauss_jordan(double* A, int k, double* f, int* ctl) {
@@ -126,10 +161,12 @@ __device__ int gauss_jordan(double* A, int k, double* f, int* ctl) {
   return 1;
 }
 
-__global__ void __launch_bounds__(GT) gauss_fwd_kernel(GaussArgs g) {
+__global__ void __launch_bounds__(GT, 2) gauss_fwd_kernel(GaussArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = g.k, nrhs = g.nrhs, m = g.m, n = g.n, tid = threadIdx.x, nt = blockDim.x;
-  const int ldr = nrhs | 1;                                      // odd strides: no bank conflicts
+  const int ldr = gauss_ldr(nrhs);
+  const bool v4 = (nrhs & 3) == 0;                               // register-tiled loops
+  const int nq = nrhs >> 2;
   const float inv2l2 = (float)(1.0 / (2.0 * g.ell * g.ell));
   double* A = reinterpret_cast<double*>(smem);                  // k x 2k
   double* f = A + (size_t)k * 2 * k;                            // KMAX
@@ -181,11 +218,20 @@ __global__ void __launch_bounds__(GT) gauss_fwd_kernel(GaussArgs g) {
         tile[j * ldk + a] = gk32s(pk[a], pt[j], inv2l2, &d2);
       }
       __syncthreads();
-      for (int o = tid; o < k * nrhs; o += nt) {
-        const int a = o / nrhs, c = o - a * nrhs;
-        float s = 0.f;
-        for (int j = 0; j < tj; ++j) s = fmaf(tile[j * ldk + a], xt[j * ldr + c], s);
-        t1d[o] += (double)s;
+      if (v4) {
+        for (int o = tid; o < k * nq; o += nt) {
+          const int a = o / nq, c = (o - a * nq) << 2;
+          float s4[4] = {0.f, 0.f, 0.f, 0.f};
+          chain4(tile + a, ldk, tj, xt + c, ldr, s4);
+          for (int q = 0; q < 4; ++q) t1d[a * nrhs + c + q] += (double)s4[q];
+        }
+      } else {
+        for (int o = tid; o < k * nrhs; o += nt) {
+          const int a = o / nrhs, c = o - a * nrhs;
+          float s = 0.f;
+          for (int j = 0; j < tj; ++j) s = fmaf(tile[j * ldk + a], xt[j * ldr + c], s);
+          t1d[o] += (double)s;
+        }
       }
       __syncthreads();
     }
@@ -211,21 +257,33 @@ __global__ void __launch_bounds__(GT) gauss_fwd_kernel(GaussArgs g) {
         tile[i * ldk + a] = gk32s(pt[i], pk[a], inv2l2, &d2);
       }
       __syncthreads();
-      for (int o = tid; o < ti * nrhs; o += nt) {
-        const int i = o / nrhs, c = o - i * nrhs;
-        float s = 0.f;
-        for (int a = 0; a < k; ++a) s = fmaf(tile[i * ldk + a], t2f[a * ldr + c], s);
-        g.y[((size_t)b * m + i0) * nrhs + o] = s;
+      if (v4) {
+        for (int o = tid; o < ti * nq; o += nt) {
+          const int i = o / nq, c = (o - i * nq) << 2;
+          float s4[4] = {0.f, 0.f, 0.f, 0.f};
+          chain4(tile + i * ldk, 1, k, t2f + c, ldr, s4);
+          float* yo = g.y + ((size_t)b * m + i0 + i) * nrhs + c;
+          for (int q = 0; q < 4; ++q) yo[q] = s4[q];
+        }
+      } else {
+        for (int o = tid; o < ti * nrhs; o += nt) {
+          const int i = o / nrhs, c = o - i * nrhs;
+          float s = 0.f;
+          for (int a = 0; a < k; ++a) s = fmaf(tile[i * ldk + a], t2f[a * ldr + c], s);
+          g.y[((size_t)b * m + i0) * nrhs + o] = s;
+        }
       }
       __syncthreads();
     }
   }
 }
 
-__global__ void __launch_bounds__(GT) gauss_bwd_kernel(GaussArgs g) {
+__global__ void __launch_bounds__(GT, 2) gauss_bwd_kernel(GaussArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = g.k, nrhs = g.nrhs, m = g.m, n = g.n, tid = threadIdx.x, nt = blockDim.x;
-  const int ldr = nrhs | 1, ldk = k | 1;
+  const int ldr = gauss_ldr(nrhs), ldk = k | 1;
+  const bool v4 = (nrhs & 3) == 0;                               // register-tiled loops
+  const int nq = nrhs >> 2;
   const float inv2l2 = (float)(1.0 / (2.0 * g.ell * g.ell));
   const float il3 = (float)(1.0 / (g.ell * g.ell * g.ell));
   double* s1 = reinterpret_cast<double*>(smem);                 // k x nrhs
@@ -271,19 +329,42 @@ __global__ void __launch_bounds__(GT) gauss_bwd_kernel(GaussArgs g) {
         dtile[i * ldk + a] = kv * d2 * il3;
       }
       __syncthreads();
-      for (int o = tid; o < k * nrhs; o += nt) {
-        const int a = o / nrhs, c = o - a * nrhs;
-        float s = 0.f;
-        for (int i = 0; i < ti; ++i) s = fmaf(tile[i * ldk + a], vt[i * ldr + c], s);
-        s1[o] += (double)s;
-      }
       float dls = 0.f;
-      for (int it = tid; it < ti * k; it += nt) {
-        const int i = it / k, a = it - i * k;
-        float s = 0.f;
-        for (int c = 0; c < nrhs; ++c) s = fmaf(vt[i * ldr + c], t2f[a * ldr + c], s);
-        if (g.dC) g.dC[((size_t)b * m + i0 + i) * k + a] = s;
-        dls = fmaf(s, dtile[i * ldk + a], dls);
+      if (v4) {
+        for (int o = tid; o < k * nq; o += nt) {
+          const int a = o / nq, c = (o - a * nq) << 2;
+          float s4[4] = {0.f, 0.f, 0.f, 0.f};
+          chain4(tile + a, ldk, ti, vt + c, ldr, s4);
+          for (int q = 0; q < 4; ++q) s1[a * nrhs + c + q] += (double)s4[q];
+        }
+        // two rows i per thread, lanes over a (rows of t2f in distinct banks)
+        const int nip = (ti + 1) >> 1;
+        for (int it = tid; it < nip * k; it += nt) {
+          const int ip = it / k, a = it - ip * k, i = 2 * ip;
+          const int i1 = min(i + 1, ti - 1);
+          float s0 = 0.f, s1v = 0.f;
+          dot2(t2f + a * ldr, vt + i * ldr, vt + i1 * ldr, nrhs, s0, s1v);
+          if (g.dC) g.dC[((size_t)b * m + i0 + i) * k + a] = s0;
+          dls = fmaf(s0, dtile[i * ldk + a], dls);
+          if (i + 1 < ti) {
+            if (g.dC) g.dC[((size_t)b * m + i0 + i + 1) * k + a] = s1v;
+            dls = fmaf(s1v, dtile[(i + 1) * ldk + a], dls);
+          }
+        }
+      } else {
+        for (int o = tid; o < k * nrhs; o += nt) {
+          const int a = o / nrhs, c = o - a * nrhs;
+          float s = 0.f;
+          for (int i = 0; i < ti; ++i) s = fmaf(tile[i * ldk + a], vt[i * ldr + c], s);
+          s1[o] += (double)s;
+        }
+        for (int it = tid; it < ti * k; it += nt) {
+          const int i = it / k, a = it - i * k;
+          float s = 0.f;
+          for (int c = 0; c < nrhs; ++c) s = fmaf(vt[i * ldr + c], t2f[a * ldr + c], s);
+          if (g.dC) g.dC[((size_t)b * m + i0 + i) * k + a] = s;
+          dls = fmaf(s, dtile[i * ldk + a], dls);
+        }
       }
       dl += (double)dls;
       __syncthreads();
@@ -315,19 +396,43 @@ __global__ void __launch_bounds__(GT) gauss_bwd_kernel(GaussArgs g) {
         dtile[j * ldk + a] = kv * d2 * il3;
       }
       __syncthreads();
-      for (int o = tid; o < tj * nrhs; o += nt) {
-        const int j = o / nrhs, c = o - j * nrhs;
-        float s = 0.f;
-        for (int a = 0; a < k; ++a) s = fmaf(tile[j * ldk + a], s2f[a * ldr + c], s);
-        g.dx[((size_t)b * n + j0) * nrhs + o] = s;
-      }
       float dls = 0.f;
-      for (int it = tid; it < k * tj; it += nt) {
-        const int j = it / k, a = it - j * k;
-        float s = 0.f;
-        for (int c = 0; c < nrhs; ++c) s = fmaf(s2f[a * ldr + c], vt[j * ldr + c], s);
-        if (g.dR) g.dR[((size_t)b * k + a) * n + j0 + j] = s;
-        dls = fmaf(s, dtile[j * ldk + a], dls);
+      if (v4) {
+        for (int o = tid; o < tj * nq; o += nt) {
+          const int j = o / nq, c = (o - j * nq) << 2;
+          float s4[4] = {0.f, 0.f, 0.f, 0.f};
+          chain4(tile + j * ldk, 1, k, s2f + c, ldr, s4);
+          float* dxo = g.dx + ((size_t)b * n + j0 + j) * nrhs + c;
+          for (int q = 0; q < 4; ++q) dxo[q] = s4[q];
+        }
+        // two rows a per thread, lanes over j (rows of vt in distinct banks; dR stores coalesced)
+        const int nap = (k + 1) >> 1;
+        for (int it = tid; it < nap * tj; it += nt) {
+          const int ap = it / tj, j = it - ap * tj, a = 2 * ap;
+          const int a1 = min(a + 1, k - 1);
+          float s0 = 0.f, s1v = 0.f;
+          dot2(vt + j * ldr, s2f + a * ldr, s2f + a1 * ldr, nrhs, s0, s1v);
+          if (g.dR) g.dR[((size_t)b * k + a) * n + j0 + j] = s0;
+          dls = fmaf(s0, dtile[j * ldk + a], dls);
+          if (a + 1 < k) {
+            if (g.dR) g.dR[((size_t)b * k + a + 1) * n + j0 + j] = s1v;
+            dls = fmaf(s1v, dtile[j * ldk + a + 1], dls);
+          }
+        }
+      } else {
+        for (int o = tid; o < tj * nrhs; o += nt) {
+          const int j = o / nrhs, c = o - j * nrhs;
+          float s = 0.f;
+          for (int a = 0; a < k; ++a) s = fmaf(tile[j * ldk + a], s2f[a * ldr + c], s);
+          g.dx[((size_t)b * n + j0) * nrhs + o] = s;
+        }
+        for (int it = tid; it < k * tj; it += nt) {
+          const int j = it / k, a = it - j * k;
+          float s = 0.f;
+          for (int c = 0; c < nrhs; ++c) s = fmaf(s2f[a * ldr + c], vt[j * ldr + c], s);
+          if (g.dR) g.dR[((size_t)b * k + a) * n + j0 + j] = s;
+          dls = fmaf(s, dtile[j * ldk + a], dls);
+        }
       }
       dl += (double)dls;
       __syncthreads();
@@ -358,11 +463,11 @@ static lra_status gauss_check(const lra_gauss_blocks* gb, int32_t nrhs) {
 
 static size_t fwd_smem(int k, int nrhs) {
   return sizeof(double) * ((size_t)k * 2 * k + KMAX + (size_t)k * nrhs) + sizeof(P32) * (KMAX + TILE) +
-         sizeof(float) * ((size_t)TILE * (k | 1) + (size_t)TILE * (nrhs | 1) + (size_t)k * (nrhs | 1));
+         sizeof(float) * ((size_t)TILE * (k | 1) + (size_t)TILE * gauss_ldr(nrhs) + (size_t)k * gauss_ldr(nrhs));
 }
 static size_t bwd_smem(int k, int nrhs) {
   return sizeof(double) * 2 * (size_t)k * nrhs + sizeof(P32) * (KMAX + TILE) +
-         sizeof(float) * (2 * (size_t)k * (nrhs | 1) + 2 * (size_t)TILE * (k | 1) + (size_t)TILE * (nrhs | 1));
+         sizeof(float) * (2 * (size_t)k * gauss_ldr(nrhs) + 2 * (size_t)TILE * (k | 1) + (size_t)TILE * gauss_ldr(nrhs));
 }
 
 }  // namespace lra

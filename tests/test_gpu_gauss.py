@@ -80,3 +80,33 @@ def test_autograd_function_and_finite_differences():
         Lp = (lra.gauss_cur_apply(xd, ELL + h, Xd, Yd, Id, Jd).double() * dyd.double()).sum().item()
         Lm = (lra.gauss_cur_apply(xd, ELL - h, Xd, Yd, Id, Jd).double() * dyd.double()).sum().item()
     assert abs((Lp - Lm) / (2 * h) - ell.grad.item()) <= 2e-3 * abs(ell.grad.item())
+
+
+def test_register_tiled_loops_equal_the_scalar_ones_bit_for_bit():
+    """With nrhs a multiple of 4 the apply takes four right-hand sides per thread
+    (vector loads, the same per-output fmaf chains), so column c of y and of dx
+    equals, bit for bit, the nrhs = 1 run on column c alone.  Odd sizes: 999
+    points per block (a ragged last tile of 39) and rank 31; also against the
+    oracle."""
+    import paper_1710_07946_gb300 as lra
+    X, Y, I, J, x, dy = blocks(nb=2, size=999, k=31, nrhs=8, seed=5)
+    Xd, Yd, Id, Jd, xd, dyd = dev(X, Y, I, J, x, dy)
+    y8, ctx8 = lra.lra_gauss_cur_forward(Xd, Yd, Id, Jd, ELL, xd)
+    g8 = lra.lra_gauss_cur_backward(Xd, Yd, Id, Jd, ELL, xd, dyd, ctx8, entry_grads=True)
+    torch.cuda.synchronize()
+    for c in range(8):
+        xc, dyc = xd[:, :, c:c + 1].contiguous(), dyd[:, :, c:c + 1].contiguous()
+        y1, ctx1 = lra.lra_gauss_cur_forward(Xd, Yd, Id, Jd, ELL, xc)
+        g1 = lra.lra_gauss_cur_backward(Xd, Yd, Id, Jd, ELL, xc, dyc, ctx1)
+        torch.cuda.synchronize()
+        assert torch.equal(y8[:, :, c], y1[:, :, 0]), c
+        assert torch.equal(g8["dx"][:, :, c], g1["dx"][:, :, 0]), c
+    for b in range(2):
+        yo = oracle.gauss_cur_apply(X[b], Y[b], I[b], J[b], ELL, x[b].astype(np.float64))[0]
+        assert rel(y8[b].cpu().numpy(), yo) < 2e-5
+        bo = oracle.gauss_cur_backward(X[b], Y[b], I[b], J[b], ELL, x[b].astype(np.float64),
+                                       dy[b].astype(np.float64))
+        assert rel(g8["dx"][b].cpu().numpy(), bo["dx"]) < 2e-5
+        assert abs(g8["dell"][b].item() - bo["dell"]) <= 1e-4 * abs(bo["dell"])
+        for key in ("dC", "dR", "dG"):
+            assert rel(g8[key][b].cpu().numpy(), bo[key]) < 5e-4, key
