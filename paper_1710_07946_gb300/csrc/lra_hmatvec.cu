@@ -79,22 +79,12 @@ __global__ void __launch_bounds__(256) hm_far_kernel(lra_hmatrix H, const double
   }
 }
 
-// 1/sqrt(r2) for a positive FP64 r2 in FP32's normal range: the FP32 reciprocal
-// square root (relative error e within a few 2^-24) refined by one Newton step
-// in FP64, y1 = y0 (3/2 - r2 y0^2 / 2), whose relative error is about 1.5 e^2,
-// i.e. below 1e-13.  Four FP64 operations instead of a full FP64 rsqrt.
-__device__ __forceinline__ double rsqrt_refined(double r2) {
-  const double y0 = (double)rsqrtf((float)r2);
-  const double t = (r2 * y0) * y0;
-  return y0 * fma(-0.5, t, 1.5);
-}
-
 // Pass 2b: one CTA of 256 threads per target leaf: thread t takes row
 // t mod 128 (and every 128th after it) over the first (t < 128) or the second
-// half of the leaf's source blocks; entries on the fly as rsqrt_refined(r2)
-// (within about 1e-13 of 1/sqrt(r2)), the source points in order with two
-// interleaved accumulators; the row's value is (first half's acc0 + acc1) +
-// (second half's acc0 + acc1).
+// half of the leaf's source blocks; entries on the fly as rsqrt(r2) (the FP64
+// reciprocal square root, within an ulp of 1/sqrt(r2)), the source points in
+// order with two interleaved accumulators; the row's value is (first half's
+// acc0 + acc1) + (second half's acc0 + acc1).
 __global__ void __launch_bounds__(256) hm_near_kernel(DevProblem P, lra_hmatrix H, const double* __restrict__ x,
                                                       double* __restrict__ ynear) {
   __shared__ double part[128];
@@ -118,7 +108,7 @@ __global__ void __launch_bounds__(256) hm_near_kernel(DevProblem P, lra_hmatrix 
           for (int64_t j = c0; j < c0 + nc; ++j, par ^= 1) {
             const double dx = xi - P.Y[3 * j], dy = yi - P.Y[3 * j + 1], dz = zi - P.Y[3 * j + 2];
             const double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
-            const double w = (j == gi) ? 0.0 : rsqrt_refined(r2);
+            const double w = (j == gi) ? 0.0 : rsqrt(r2);
             if (par) acc1 = fma(w, x[j], acc1);
             else acc0 = fma(w, x[j], acc0);
           }
