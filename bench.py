@@ -309,6 +309,54 @@ class FmmWorkload:
                                    f"each) in {ncpu} processes, one per host core, {el:.1f} s")
 
 
+class TwoSlotPipe:
+    """Plumbing of a two-slot end-to-end pipeline.  Slot i's inputs are uploaded on
+    one copy stream once the compute that last read them is done; the compute
+    waits for them and for the read-back that last used slot i's outputs; the
+    read-back runs on a second copy stream.  Step s's copies thus overlap the
+    compute of steps s - 1 and s + 1, and every step still moves its own inputs
+    and results."""
+
+    def __init__(self, dev):
+        import torch
+        self.up, self.down = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        self.uploaded = [torch.cuda.Event(), torch.cuda.Event()]
+        self.done = [torch.cuda.Event(), torch.cuda.Event()]
+        self.copied = [torch.cuda.Event(), torch.cuda.Event()]
+        self.slot = 0
+
+    def next_slot(self):
+        i = self.slot
+        self.slot = 1 - i
+        return i
+
+    def upload(self, i, pairs):
+        import torch
+        with torch.cuda.stream(self.up):
+            self.up.wait_event(self.done[i])
+            for dst, src in pairs:
+                dst.copy_(src, non_blocking=True)
+            self.uploaded[i].record(self.up)
+        cur = torch.cuda.current_stream()
+        cur.wait_event(self.uploaded[i])
+        cur.wait_event(self.copied[i])
+
+    def download(self, i, pairs, keep=()):
+        import torch
+        self.done[i].record(torch.cuda.current_stream())
+        with torch.cuda.stream(self.down):
+            self.down.wait_event(self.done[i])
+            for dst, src in pairs:
+                dst.copy_(src, non_blocking=True)
+            self.copied[i].record(self.down)
+        for t in keep:
+            t.record_stream(self.down)       # not reused before the read-back has run
+
+    def finish(self):
+        self.up.synchronize()
+        self.down.synchronize()
+
+
 class DenseWorkload:
     kernel = "ca_kernel"
     unit = "LRA/s"
@@ -373,25 +421,38 @@ class DenseWorkload:
         return {"rank": int(inf[0]), "swaps": int(inf[1]), "loops": int(inf[2]), "status": int(inf[3]),
                 "rel_fro_err_sampled": float(res["err"][0])}
 
+    # end to end: W and I0 uploaded, C, U, R, the indices and the statistics read back, every step, through a
+    # two-slot pipeline (TwoSlotPipe)
     def e2e_setup(self, h, d):
         import torch
-        hp = dict(W=torch.from_numpy(h["p"].W).pin_memory(), I0=torch.from_numpy(h["I0"]).pin_memory())
-        hp["out"] = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in d["out"].items()
-                     if not key.startswith("_")}
-        hp["stats"] = torch.empty(5, dtype=torch.float64).pin_memory()
+        import paper_1710_07946_gb300 as lra
+        W1, I01 = d["W"].clone(), d["I0"].clone()
+        prob1 = lra.Problem.dense(W1)
+        out1 = lra.lra_ca_run(prob1, I01, self.k, self.sweeps, multiplier=d["mult"])
+        torch.cuda.synchronize()
+        hp = dict(pipe=TwoSlotPipe(d["W"].device), W=torch.from_numpy(h["p"].W).pin_memory(),
+                  I0=torch.from_numpy(h["I0"]).pin_memory(),
+                  slots=[(d["W"], d["I0"], d["prob"], d["out"]), (W1, I01, prob1, out1)])
+        hp["out"] = [{key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in d["out"].items()
+                      if not key.startswith("_")} for _ in range(2)]
+        hp["stats"] = [torch.empty(5, dtype=torch.float64).pin_memory() for _ in range(2)]
         h2d = hp["W"].numel() * 4 + hp["I0"].numel() * 4
-        d2h = sum(v.numel() * v.element_size() for v in hp["out"].values()) + 40
+        d2h = sum(v.numel() * v.element_size() for v in hp["out"][0].values()) + 40
         return hp, h2d, d2h
 
     def e2e_step(self, hp, d):
-        import torch
-        d["W"].copy_(hp["W"], non_blocking=True)
-        d["I0"].copy_(hp["I0"], non_blocking=True)
-        self.step(d)
-        for key, v in hp["out"].items():
-            v.copy_(d["out"][key], non_blocking=True)
-        hp["stats"].copy_(d["stats"], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        import paper_1710_07946_gb300 as lra
+        pipe = hp["pipe"]
+        i = pipe.next_slot()
+        W, I0, prob, out = hp["slots"][i]
+        pipe.upload(i, [(W, hp["W"]), (I0, hp["I0"])])
+        lra.lra_ca_run(prob, I0, self.k, self.sweeps, multiplier=d["mult"], out=out, workspace=out["_workspace"])
+        stats = lra.lra_residual_sample(prob, out["C"], out["U"], out["R"], d["Q"], d["S"])
+        pipe.download(i, [(v, out[key]) for key, v in hp["out"][i].items()] + [(hp["stats"][i], stats)],
+                      keep=(stats,))
+
+    def e2e_finish(self, hp, d):
+        hp["pipe"].finish()
 
     def oracle_units(self, h, budget_s, seed=0):
         import oracle
@@ -457,25 +518,38 @@ class RhtcurWorkload:
         return {"rank": int(inf[0]), "swaps": int(inf[1]), "status": int(inf[3]),
                 "rel_fro_err_sampled": float(res["err"][0])}
 
+    # end to end: W and Hbar uploaded, the CUR and the statistics read back, every step, through a two-slot
+    # pipeline (TwoSlotPipe)
     def e2e_setup(self, h, d):
         import torch
-        hp = dict(W=torch.from_numpy(h["p"].W).pin_memory(), H=torch.from_numpy(h["H"]).pin_memory())
-        hp["out"] = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in d["out"].items()
-                     if not key.startswith("_")}
-        hp["stats"] = torch.empty(5, dtype=torch.float64).pin_memory()
+        import paper_1710_07946_gb300 as lra
+        W1, H1 = d["W"].clone(), d["H"].clone()
+        prob1 = lra.Problem.dense(W1)
+        out1 = lra.lra_rhtcur_run(prob1, H1)
+        torch.cuda.synchronize()
+        hp = dict(pipe=TwoSlotPipe(d["W"].device), W=torch.from_numpy(h["p"].W).pin_memory(),
+                  H=torch.from_numpy(h["H"]).pin_memory(),
+                  slots=[(d["W"], d["H"], d["prob"], d["out"]), (W1, H1, prob1, out1)])
+        hp["out"] = [{key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in d["out"].items()
+                      if not key.startswith("_")} for _ in range(2)]
+        hp["stats"] = [torch.empty(5, dtype=torch.float64).pin_memory() for _ in range(2)]
         h2d = hp["W"].numel() * 4 + hp["H"].numel() * 8
-        d2h = sum(v.numel() * v.element_size() for v in hp["out"].values()) + 40
+        d2h = sum(v.numel() * v.element_size() for v in hp["out"][0].values()) + 40
         return hp, h2d, d2h
 
     def e2e_step(self, hp, d):
-        import torch
-        d["W"].copy_(hp["W"], non_blocking=True)
-        d["H"].copy_(hp["H"], non_blocking=True)
-        self.step(d)
-        for key, v in hp["out"].items():
-            v.copy_(d["out"][key], non_blocking=True)
-        hp["stats"].copy_(d["stats"], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        import paper_1710_07946_gb300 as lra
+        pipe = hp["pipe"]
+        i = pipe.next_slot()
+        W, H, prob, out = hp["slots"][i]
+        pipe.upload(i, [(W, hp["W"]), (H, hp["H"])])
+        lra.lra_rhtcur_run(prob, H, out=out, workspace=out["_workspace"])
+        stats = lra.lra_residual_sample(prob, out["C"], out["U"], out["R"], d["Q"], d["S"])
+        pipe.download(i, [(v, out[key]) for key, v in hp["out"][i].items()] + [(hp["stats"][i], stats)],
+                      keep=(stats,))
+
+    def e2e_finish(self, hp, d):
+        hp["pipe"].finish()
 
     def oracle_units(self, h, budget_s, seed=0):
         import oracle
@@ -1060,24 +1134,38 @@ class RandomTestsWorkload:
                 "rel_fro_err_sampled_median": float(np.median(err)), "rel_fro_err_sampled_max": float(err.max()),
                 "frac_blocks_err_le_1e-6": float((err <= ERR_BOUND).mean())}
 
+    # end to end: the stacked inputs uploaded, every block's factors and statistics read back, every step,
+    # through a two-slot pipeline (TwoSlotPipe); slot 1 has its own input copy, batch and statistics
     def e2e_setup(self, h, d):
         import torch
-        out = d["bt"].out
-        hp = dict(W=torch.from_numpy(h["W"]).pin_memory())
-        hp["out"] = {key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in out.items()}
-        hp["stats"] = torch.empty(d["stats"].shape, dtype=torch.float64).pin_memory()
+        import paper_1710_07946_gb300 as lra
+        W1 = d["W"].clone()
+        prob1 = lra.Problem.dense(W1)
+        bt1 = lra.Batch(prob1, h["blocks"], self.r, self.sweeps, h["I0"] if self.test == 2 else h["I0s"],
+                        rank_tol=1e-13)
+        bt1.cb.cta_threads, bt1.cb.ctas_per_sm = d["bt"].cb.cta_threads, d["bt"].cb.ctas_per_sm
+        d1 = dict(d, W=W1, prob=prob1, bt=bt1, stats=torch.empty_like(d["stats"]))
+        self.step(d1)                         # sizes slot 1's workspaces (untimed)
+        torch.cuda.synchronize()
+        hp = dict(pipe=TwoSlotPipe(d["W"].device), W=torch.from_numpy(h["W"]).pin_memory(), slots=[d, d1])
+        hp["out"] = [{key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in d["bt"].out.items()}
+                     for _ in range(2)]
+        hp["stats"] = [torch.empty(d["stats"].shape, dtype=torch.float64).pin_memory() for _ in range(2)]
         h2d = hp["W"].numel() * 8
-        d2h = sum(v.numel() * v.element_size() for v in hp["out"].values()) + hp["stats"].numel() * 8
+        d2h = sum(v.numel() * v.element_size() for v in hp["out"][0].values()) + hp["stats"][0].numel() * 8
         return hp, h2d, d2h
 
     def e2e_step(self, hp, d):
-        import torch
-        d["W"].copy_(hp["W"], non_blocking=True)
-        self.step(d)
-        for key, v in hp["out"].items():
-            v.copy_(d["bt"].out[key], non_blocking=True)
-        hp["stats"].copy_(d["stats"], non_blocking=True)
-        torch.cuda.current_stream().synchronize()
+        pipe = hp["pipe"]
+        i = pipe.next_slot()
+        ds = hp["slots"][i]
+        pipe.upload(i, [(ds["W"], hp["W"])])
+        self.step(ds)
+        pipe.download(i, [(v, ds["bt"].out[key]) for key, v in hp["out"][i].items()] +
+                      [(hp["stats"][i], ds["stats"])])
+
+    def e2e_finish(self, hp, d):
+        hp["pipe"].finish()
 
     def oracle_units(self, h, budget_s, seed=0):
         import oracle
