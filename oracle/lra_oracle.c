@@ -1078,9 +1078,9 @@ int orc_oversample(const orc_problem* p, const int32_t* I, const int32_t* J, int
 /* ------------------------------------------------------------------ */
 
 /*
- * orc_alg1tor: Algorithm alg1tor (greedy expansions from a vector up to a
- * square matrix) on the k x n matrix A (row-major, overwritten), stopped at the
- * numerical rank.  At step g = 0, 1, ...:
+ * orc_alg1tor: Algorithm alg1tor (a column set grown one greedy column at a
+ * time, starting from the column of largest norm) on the k x n matrix A
+ * (row-major, overwritten), stopped at the numerical rank.  At step g = 0, 1, ...:
  *   1. the pivot j_g is the column outside the chosen set whose subvector of
  *      rows g..k-1 has the largest squared norm s_j (an ascending fma chain,
  *      recomputed from the current A), lowest j on ties.  The loop stops before
