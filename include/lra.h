@@ -485,8 +485,8 @@ lra_status lra_oversample_cycle_batched(const lra_problem* base, const lra_batch
 /*
  * lra_prjvol_batched -- k_b x l_b generators of maximal r-projective volume
  * for every block of a batch that lra_ca_run_batched has processed (paper:
- * Algorithm algprjvlm, maximisation of r-projective volume through the volume
- * of a full-rank matrix; Algorithm alg1tor for its rank-revealing stage;
+ * Algorithm algprjvlm, which turns the search into a volume maximisation in the
+ * r x n factor R' of a rank-revealing QR; Algorithm alg1tor for that QR;
  * Theorem coc-avlm for the C-A steps built on it), one CTA per block from a
  * work queue.  For block b with rows I = in->I (k_b = in->info[6] of them) and
  * l_b = min(k_b + pextra, ncols):
