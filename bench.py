@@ -205,6 +205,13 @@ class FmmWorkload:
         lra.lra_ca_run_batched(d["bt"])
         lra.lra_residual_sample_batched(d["bt"], d["Q"], d["S"], d["stats"], problem=d["prob64"])
 
+    def precision(self):
+        """What ran in which arithmetic: the mode label and the per-stage precisions."""
+        if self.entries == "f32":
+            return "mixed: FP32 Laplace entries, FP64 pivots/LU/swaps/nucleus", {
+                "kernel_entries": "f32", "pivots_lu_swaps": "f64", "nucleus": "f64", "residual": "f64"}
+        return "plain fp64", {"kernel_entries": "f64", "pivots_lu_swaps": "f64", "nucleus": "f64", "residual": "f64"}
+
     def comparisons(self):
         """The plain FP64 GPU forms of the same batch, measured in the same run."""
         if self.entries != "f32":
@@ -248,14 +255,19 @@ class FmmWorkload:
         bt1 = lra.Batch(d["prob"], h["blocks"], self.k, self.sweeps, h["I0"], h=self.h, rank_tol=self.tol,
                         stages=self.stages, rank_margin=self.margin)
         bt1.cb.cta_threads, bt1.cb.ctas_per_sm = bt0.cb.cta_threads, bt0.cb.ctas_per_sm
+        pin = lambda t: t.cpu().pin_memory()
+        # every per-problem input is uploaded each step: the points, the block descriptors (rows, columns,
+        # output offsets, processing order), the initial rows I0 and the residual sample positions Q, S
         hp = dict(X=torch.from_numpy(h["p"].X).pin_memory(), bts=[bt0, bt1],
+                  inputs=dict(blocks=pin(bt0.blocks), offs=pin(bt0.offs), order=pin(bt0.order), I0=pin(bt0.I0),
+                              Q=pin(d["Q"]), S=pin(d["S"])),
                   stats_dev=[d["stats"], torch.empty_like(d["stats"])],
                   copy=torch.cuda.Stream(d["X"].device), slot=0,
                   done=[torch.cuda.Event(), torch.cuda.Event()], copied=[torch.cuda.Event(), torch.cuda.Event()])
         hp["out"] = [{key: torch.empty(v.shape, dtype=v.dtype).pin_memory() for key, v in bt0.out.items()}
                      for _ in range(2)]
         hp["stats"] = [torch.empty(d["stats"].shape, dtype=torch.float64).pin_memory() for _ in range(2)]
-        h2d = hp["X"].numel() * 8
+        h2d = hp["X"].numel() * 8 + sum(v.numel() * v.element_size() for v in hp["inputs"].values())
         d2h = sum(v.numel() * v.element_size() for v in hp["out"][0].values()) + hp["stats"][0].numel() * 8
         return hp, h2d, d2h
 
@@ -268,6 +280,11 @@ class FmmWorkload:
         cur.wait_event(hp["copied"][i])                  # the read-back that last used output set i is done
         d["X"].copy_(hp["X"], non_blocking=True)
         bt, st = hp["bts"][i], hp["stats_dev"][i]
+        hin = hp["inputs"]
+        for key in ("blocks", "offs", "order", "I0"):
+            getattr(bt, key).copy_(hin[key], non_blocking=True)
+        d["Q"].copy_(hin["Q"], non_blocking=True)
+        d["S"].copy_(hin["S"], non_blocking=True)
         lra.lra_ca_run_batched(bt)
         lra.lra_residual_sample_batched(bt, d["Q"], d["S"], st, problem=d["prob64"])
         hp["done"][i].record(cur)
@@ -1743,10 +1760,10 @@ def run_lib(args, wl):
     comparisons = {}
     for label, other in (wl.comparisons() if hasattr(wl, "comparisons") else []):
         d2 = other.device(h, dev)
-        for _ in range(2):
+        for _ in range(warm):
             other.step(d2)
         torch.cuda.synchronize()
-        nst = max(1, min(args.steps, 3))
+        nst = args.steps                 # the same number of timed steps as this line
         ms2 = 0.0
         for i in range(nst):
             flush.fill_(float(i))
@@ -1785,9 +1802,12 @@ def run_lib(args, wl):
                         "loop measured 74)") if fp32 else ("FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz = 1.26, "
                                                            "nominal 1.25 TFLOP/s (not in MEASURED_PEAKS.json; a plain "
                                                            "DFMA loop measured 1.2)")
+        mode, precision = wl.precision() if hasattr(wl, "precision") else ("fp64", None)
         cfg = dict(wl.config(h), l2="flushed before every step (256 MiB write, untimed)",
-                   parallelism=f"{world} independent problem(s), one per GPU", mode="fp64",
+                   parallelism=f"{world} independent problem(s), one per GPU", mode=mode,
                    graph_ms_per_step=graph_ms, wall_s=t_wall)
+        if precision:
+            cfg["precision"] = precision
         cfg.update(wl.extra(res))
         for c in comparisons.values():
             c["speedup_of_this_line"] = value / c["value"] if c["value"] > 0 else None

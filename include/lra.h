@@ -306,7 +306,10 @@ lra_status lra_rhtcur_run(const lra_problem* prob, const double* Hbar, const lra
  * device share the one array: calls whose executions overlap on the GPU (other
  * streams, other host threads) race and must be serialised by the caller.
  * The array keeps the last call's contents; every call clears the parts that
- * must start at zero.
+ * must start at zero.  The looked-up address belongs to the device's current
+ * context: after a cudaDeviceReset the array may move, so do not call this
+ * entry point again in that process until a call has returned LRA_ERR_CUDA
+ * (which drops the cached address, so the next call looks it up afresh).
  */
 #define LRA_NOALLOC_SCRATCH_BYTES (256u * 1024u)
 lra_status lra_ca_run_noalloc(const lra_problem* prob, const lra_ca_params* par, lra_multiplier mult,
@@ -644,7 +647,9 @@ lra_status lra_ca_batched_tune(const lra_problem* base, const lra_batch* batch, 
  * lra_residual_sample_batched -- the a-posteriori sample of lra_residual_sample
  * for every block of a batch, in one launch: for block b, rows Q[b*q .. b*q+q)
  * and columns S[b*s .. b*s+s) (block-local, device int32) of W_b - C_b U_b R_b;
- * stats (device, nb x 5) as in lra_residual_sample (NaN for failed blocks).
+ * stats (device, nb x 5) as in lra_residual_sample (NaN for failed blocks, and
+ * for blocks with a sample position outside 0 <= Q < nrows, 0 <= S < ncols,
+ * which is caught before any entry is read).
  * kmax: the par->k of the batched run.  8 (q k + 2 q s) bytes must fit in
  * shared memory.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
  */
@@ -686,8 +691,10 @@ typedef struct {
  * and never stored; R x is accumulated in FP32, U (R x) in FP64, C (U R x) in
  * FP32.  x: nb x n x nrhs FP32, y: nb x m x nrhs FP32 (1 <= nrhs <= 256).
  * ctx: nb x (k*k + 2*k*nrhs) FP64 written for the backward (U, R x, U R x).
- * A singular core gives NaN outputs for its block.  Errors: LRA_ERR_INVALID_ARG,
- * LRA_ERR_CUDA.
+ * A singular core gives NaN outputs for its block.  A pivot outside
+ * 0 <= I[b][a] < m or 0 <= J[b][a] < n is caught on the device before any point
+ * is read through it: the block's y and ctx are then NaN.  Errors:
+ * LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
  */
 lra_status lra_gauss_cur_forward(const lra_gauss_blocks* g, const float* x, int32_t nrhs, float* y, double* ctx,
                                  lra_stream_t stream);
@@ -701,7 +708,8 @@ lra_status lra_gauss_cur_forward(const lra_gauss_blocks* g, const float* x, int3
  *   optional (may be NULL): dC = dy (U R x)^T (nb x m x k), dR = U^T C^T dy x^T
  *   (nb x k x n), dG = -U^T C^T dy (U R x)^T (nb x k x k), the gradients with
  *   respect to the sampled kernel entries (FP32).
- * Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
+ * A block whose pivots are out of range (as in the forward) gets NaN gradients
+ * and reads no point through them.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
  */
 lra_status lra_gauss_cur_backward(const lra_gauss_blocks* g, const float* x, const float* dy, int32_t nrhs,
                                   const double* ctx, float* dx, double* dell, float* dC, float* dR, float* dG,
@@ -728,7 +736,10 @@ lra_status lra_cur_apply_workspace_size(int64_t n, int32_t k, int32_t nrhs, size
  * q*s >= 1.  stats (device, 5 doubles): mean of e, variance (1/K) sum (e-mean)^2,
  * mean |e|, max |e|, ||E[Q,S]||_F / ||W[Q,S]||_F with K = q s.  E (device q x s,
  * optional, may be NULL) receives the sampled errors.  W is read through prob
- * (original matrix, no multiplier).  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
+ * (original matrix, no multiplier).  Every Q[a] must lie in 0 <= Q[a] < m and
+ * every S[c] in 0 <= S[c] < n: the device checks each index before it reads
+ * through it, and a bad one makes all five statistics NaN (the entry is not
+ * read).  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
  */
 lra_status lra_residual_sample(const lra_problem* prob, const double* C, const double* U, const double* R,
                                int32_t k, const int32_t* Q, int32_t q, const int32_t* S, int32_t s, double* stats,

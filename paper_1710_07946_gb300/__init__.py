@@ -329,6 +329,21 @@ def _params(k, sweeps, h, rank_tol, max_swaps, mode, stages=None, rank_margin=0)
     return p
 
 
+def _check_cur_out(out: dict, m: int, n: int, k: int, sweeps: int) -> None:
+    """Raise unless every output tensor of a C-A run is a contiguous device
+    tensor of the dtype and size the library writes (I, J: k int32; C: m k,
+    U: k k, R: k n, logvol: 2 sweeps float64; info: LRA_INFO_LEN int32)."""
+    want = dict(I=(torch.int32, k), J=(torch.int32, k), C=(torch.float64, m * k), U=(torch.float64, k * k),
+                R=(torch.float64, k * n), logvol=(torch.float64, 2 * sweeps), info=(torch.int32, LRA_INFO_LEN))
+    for f, (dt, numel) in want.items():
+        if f not in out:
+            raise ValueError(f"out is missing {f}")
+        t = out[f]
+        _dev(t, dt, f)
+        if t.numel() < numel or not t.is_contiguous():
+            raise ValueError(f"out[{f!r}] must be a contiguous {dt} tensor of at least {numel} elements")
+
+
 def lra_ca_workspace_size(problem: Problem, k: int, sweeps: int = 3, h: float = 1.01, rank_tol: float = 1e-13,
                           max_swaps: int = 1000, mode: int = LRA_MODE_FP64,
                           multiplier: Optional[Multiplier] = None) -> int:
@@ -366,6 +381,7 @@ def lra_ca_run(problem: Problem, I0: torch.Tensor, k: int, sweeps: int = 3, h: f
                    R=torch.empty(k, problem.n, dtype=torch.float64, device=dev),
                    logvol=torch.empty(2 * sweeps, dtype=torch.float64, device=dev),
                    info=torch.empty(LRA_INFO_LEN, dtype=torch.int32, device=dev))
+    _check_cur_out(out, problem.m, problem.n, k, sweeps)
     if workspace is None:
         nb = ct.c_size_t()
         _check(L.lra_ca_workspace_size(ct.byref(pc), ct.byref(pp), mh, ct.byref(nb)), "lra_ca_workspace_size")
@@ -420,6 +436,7 @@ def lra_ca_run_noalloc(problem: Problem, I0: torch.Tensor, out: dict, k: int, sw
     (I, J, C, U, R, logvol, info as returned by lra_ca_run)."""
     L = _load()
     _dev(I0, torch.int32, "I0")
+    _check_cur_out(out, problem.m, problem.n, k, sweeps)
     pc, pp = problem._c(), _params(k, sweeps, h, rank_tol, max_swaps, mode)
     cur = _Cur()
     for f in ("I", "J", "C", "U", "R", "logvol", "info"):

@@ -64,13 +64,20 @@ __global__ void __launch_bounds__(NT) apply_c_kernel(const double* __restrict__ 
 }
 
 // Residual: rows of C U at the sampled rows, then E and its statistics.
+// A sample index outside 0 <= Q[a] < m, 0 <= S[c] < n is never dereferenced:
+// the kernels set *bad instead, and the statistics come out NaN.
 __global__ void __launch_bounds__(NT) resid_cu_kernel(const double* __restrict__ C, const double* __restrict__ U,
-                                                      const int32_t* __restrict__ Q, int q, int k,
-                                                      double* __restrict__ CU) {
+                                                      const int32_t* __restrict__ Q, int q, int k, int64_t m,
+                                                      double* __restrict__ CU, int* bad) {
   for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < (int64_t)q * k;
        it += (int64_t)gridDim.x * blockDim.x) {
     const int a = (int)(it / k), b = (int)(it - (int64_t)a * k);
     const int64_t row = Q[a];
+    if (row < 0 || row >= m) {
+      atomicOr(bad, 1);
+      CU[it] = __longlong_as_double(0x7ff8000000000000ll);
+      continue;
+    }
     double t = 0.0;
     for (int d = 0; d < k; ++d) t = fma(C[row * k + d], U[d * k + b], t);
     CU[it] = t;
@@ -80,14 +87,20 @@ __global__ void __launch_bounds__(NT) resid_cu_kernel(const double* __restrict__
 __global__ void __launch_bounds__(NT) resid_e_kernel(DevProblem P, const double* __restrict__ CU,
                                                      const double* __restrict__ R, const int32_t* __restrict__ Q,
                                                      const int32_t* __restrict__ S, int q, int s, int k,
-                                                     double* __restrict__ E, double* __restrict__ W2) {
+                                                     double* __restrict__ E, double* __restrict__ W2, int* bad) {
   for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < (int64_t)q * s;
        it += (int64_t)gridDim.x * blockDim.x) {
     const int a = (int)(it / s), c = (int)(it - (int64_t)a * s);
-    const int64_t col = S[c];
+    const int64_t col = S[c], row = Q[a];
+    if (row < 0 || row >= P.m || col < 0 || col >= P.n) {
+      atomicOr(bad, 1);
+      E[it] = __longlong_as_double(0x7ff8000000000000ll);
+      W2[it] = 0.0;
+      continue;
+    }
     double t = 0.0;
     for (int b = 0; b < k; ++b) t = fma(CU[(int64_t)a * k + b], R[(int64_t)b * P.n + col], t);
-    const double w = w_entry(P, Q[a], col);
+    const double w = w_entry(P, row, col);
     E[it] = w - t;
     W2[it] = w * w;
   }
@@ -175,7 +188,8 @@ __global__ void __launch_bounds__(NT) resid_var_kernel(const double* __restrict_
   if (threadIdx.x == 0) part[6 * (size_t)blockIdx.x + 5] = v;
 }
 
-__global__ void resid_final_kernel(const double* __restrict__ part, int nparts, int64_t K, double* __restrict__ stats) {
+__global__ void resid_final_kernel(const double* __restrict__ part, int nparts, int64_t K, const int* bad,
+                                   double* __restrict__ stats) {
   // one warp: lane l folds the partials l, l + 32, ..., then a butterfly
   const int lane = threadIdx.x;
   double s = 0.0, sa = 0.0, mx = 0.0, se2 = 0.0, sw2 = 0.0, v = 0.0;
@@ -197,6 +211,8 @@ __global__ void resid_final_kernel(const double* __restrict__ part, int nparts, 
     stats[2] = sa / (double)K;
     stats[3] = mx;
     stats[4] = sw2 > 0.0 ? sqrt(se2) / sqrt(sw2) : 0.0;
+    if (*bad)
+      for (int e = 0; e < 5; ++e) stats[e] = __longlong_as_double(0x7ff8000000000000ll);
   }
 }
 
@@ -247,7 +263,7 @@ lra_status lra_cur_apply(const double* C, const double* U, const double* R, int6
 lra_status lra_residual_sample_workspace_size(int32_t k, int32_t q, int32_t s, size_t* bytes) {
   if (bytes == nullptr || k < 1 || k > KMAX || q < 1 || s < 1) return LRA_ERR_INVALID_ARG;
   *bytes = align_up(sizeof(double) * (size_t)q * k, 256) + 2 * align_up(sizeof(double) * (size_t)q * s, 256) +
-           align_up(sizeof(double) * 6 * RESID_MAX_PARTS, 256);
+           align_up(sizeof(double) * 6 * RESID_MAX_PARTS, 256) + 256;
   return LRA_OK;
 }
 
@@ -269,19 +285,21 @@ lra_status lra_residual_sample(const lra_problem* prob, const double* C, const d
   double* Ews = reinterpret_cast<double*>(ws + align_up(sizeof(double) * (size_t)q * k, 256));
   double* W2 = Ews + align_up(sizeof(double) * (size_t)q * s, 256) / sizeof(double);
   double* part = W2 + align_up(sizeof(double) * (size_t)q * s, 256) / sizeof(double);
+  int* bad = reinterpret_cast<int*>(part + align_up(sizeof(double) * 6 * RESID_MAX_PARTS, 256) / sizeof(double));
   double* Eout = E ? E : Ews;
   DeviceInfo dev;
   if ((st = current_device_info(&dev)) != LRA_OK) return st;
+  LRA_CUDA_TRY(cudaMemsetAsync(bad, 0, sizeof(int), stream));
   const int g1 = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)q * k + NT - 1) / NT, dev.sms * 4));
-  { LaunchScope ls(stream, "resid_cu_kernel"); resid_cu_kernel<<<g1, NT, 0, stream>>>(C, U, Q, q, k, CU); }
+  { LaunchScope ls(stream, "resid_cu_kernel"); resid_cu_kernel<<<g1, NT, 0, stream>>>(C, U, Q, q, k, P.m, CU, bad); }
   const int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)q * s + NT - 1) / NT, dev.sms * 8));
-  { LaunchScope ls(stream, "resid_e_kernel"); resid_e_kernel<<<g2, NT, 0, stream>>>(P, CU, R, Q, S, q, s, k, Eout, W2); }
+  { LaunchScope ls(stream, "resid_e_kernel"); resid_e_kernel<<<g2, NT, 0, stream>>>(P, CU, R, Q, S, q, s, k, Eout, W2, bad); }
   const int64_t K = (int64_t)q * s;
   const int g3 = (int)std::max<int64_t>(1, std::min<int64_t>((K + 4 * NT - 1) / (4 * NT),
                                                              std::min<int64_t>(RESID_MAX_PARTS, dev.sms * 4)));
   { LaunchScope ls(stream, "resid_part_kernel"); resid_part_kernel<<<g3, NT, 0, stream>>>(Eout, W2, K, part); }
   { LaunchScope ls(stream, "resid_var_kernel"); resid_var_kernel<<<g3, NT, 0, stream>>>(Eout, K, part); }
-  { LaunchScope ls(stream, "resid_final_kernel"); resid_final_kernel<<<1, 32, 0, stream>>>(part, g3, K, stats); }
+  { LaunchScope ls(stream, "resid_final_kernel"); resid_final_kernel<<<1, 32, 0, stream>>>(part, g3, K, bad, stats); }
   return cuda_status(cudaGetLastError());
 }
 

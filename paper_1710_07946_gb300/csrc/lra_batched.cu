@@ -42,6 +42,16 @@ __global__ void __launch_bounds__(256) resid_batched_kernel(DevProblem base, con
     const double* Ub = U + (size_t)b * lmax * kmax;
     const int32_t* Q = Qs + (size_t)b * q;
     const int32_t* S = Ss + (size_t)b * s;
+    {
+      // sample positions outside the block are not read: the block's stats are NaN
+      int bad = 0;
+      for (int a = threadIdx.x; a < q; a += blockDim.x) bad |= (Q[a] < 0) | ((int64_t)Q[a] >= nr);
+      for (int c = threadIdx.x; c < s; c += blockDim.x) bad |= (S[c] < 0) | ((int64_t)S[c] >= nc);
+      if (__syncthreads_or(bad)) {
+        if (threadIdx.x < 5) st[threadIdx.x] = __longlong_as_double(0x7ff8000000000000ll);
+        continue;
+      }
+    }
     DevProblem P = base;
     P.m = nr;
     P.n = nc;
@@ -54,7 +64,7 @@ __global__ void __launch_bounds__(256) resid_batched_kernel(DevProblem base, con
     }
     for (int it = threadIdx.x; it < q * k; it += blockDim.x) {
       const int a = it / k, bb = it - a * k;
-      const int64_t row = min((int64_t)Q[a], nr - 1);
+      const int64_t row = Q[a];
       double t = 0.0;
       for (int d = 0; d < l; ++d) t = fma(Cb[row * l + d], Ub[d * k + bb], t);
       CU[it] = t;
@@ -62,10 +72,10 @@ __global__ void __launch_bounds__(256) resid_batched_kernel(DevProblem base, con
     __syncthreads();
     for (int it = threadIdx.x; it < q * s; it += blockDim.x) {
       const int a = it / s, c = it - a * s;
-      const int64_t col = min((int64_t)S[c], nc - 1);
+      const int64_t col = S[c];
       double t = 0.0;
       for (int bb = 0; bb < k; ++bb) t = fma(CU[a * k + bb], Rb[(int64_t)bb * nc + col], t);
-      const double w = w_entry(P, min((int64_t)Q[a], nr - 1), col);
+      const double w = w_entry(P, Q[a], col);
       E[it] = w - t;
       W2[it] = w * w;
     }

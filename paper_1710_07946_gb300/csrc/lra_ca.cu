@@ -268,5 +268,15 @@ extern "C" lra_status lra_ca_run_noalloc(const lra_problem* prob, const lra_ca_p
   if (need > NOALLOC_SCRATCH_BYTES) return LRA_ERR_WORKSPACE;
   void* scratch = nullptr;
   if ((st = noalloc_scratch(&scratch)) != LRA_OK) return st;
-  return lra_ca_run(prob, par, mult, I0, out, scratch, NOALLOC_SCRATCH_BYTES, stream);
+  st = lra_ca_run(prob, par, mult, I0, out, scratch, NOALLOC_SCRATCH_BYTES, stream);
+  if (st == LRA_ERR_CUDA) {
+    // a failed CUDA call may mean the context was torn down: look the array up
+    // again on the next call instead of trusting the cached address
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < NOALLOC_MAX_DEVICES) {
+      std::lock_guard<std::mutex> lk(g_noalloc_mu);
+      g_noalloc_addr[dev] = nullptr;
+    }
+  }
+  return st;
 }

@@ -161,6 +161,14 @@ __device__ int gauss_jordan(double* A, int k, double* f, int* ctl) {
   return 1;
 }
 
+// Every CTA thread checks its share of the block's pivots: true when all
+// 0 <= I[a] < m and 0 <= J[a] < n (a block with a bad pivot reads no point).
+__device__ __forceinline__ bool pivots_in_range(const int32_t* I, const int32_t* J, int k, int m, int n) {
+  int bad = 0;
+  for (int a = threadIdx.x; a < k; a += blockDim.x) bad |= (I[a] < 0) | (I[a] >= m) | (J[a] < 0) | (J[a] >= n);
+  return !__syncthreads_or(bad);
+}
+
 __global__ void __launch_bounds__(GT, 2) gauss_fwd_kernel(GaussArgs g) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int k = g.k, nrhs = g.nrhs, m = g.m, n = g.n, tid = threadIdx.x, nt = blockDim.x;
@@ -187,6 +195,13 @@ __global__ void __launch_bounds__(GT, 2) gauss_fwd_kernel(GaussArgs g) {
     double* U = ctx;
     double* t1 = U + (size_t)k * k;
     double* t2 = t1 + (size_t)k * nrhs;
+    if (!pivots_in_range(I, J, k, m, n)) {      // failed block: NaN context and outputs
+      const double qn = __longlong_as_double(0x7ff8000000000000ll);
+      for (size_t it = tid; it < (size_t)k * k + 2 * (size_t)k * nrhs; it += nt) ctx[it] = qn;
+      for (size_t it = tid; it < (size_t)m * nrhs; it += nt) g.y[(size_t)b * m * nrhs + it] = __int_as_float(0x7fc00000);
+      __syncthreads();
+      continue;
+    }
     // G and U = G^{-1}
     for (int it = tid; it < k * k; it += nt) {
       const int a = it / k, c = it - a * k;
@@ -304,6 +319,16 @@ __global__ void __launch_bounds__(GT, 2) gauss_bwd_kernel(GaussArgs g) {
     const double* ctx = g.ctx + (size_t)b * ((size_t)k * k + 2 * (size_t)k * nrhs);
     const double* U = ctx;
     const double* t2 = ctx + (size_t)k * k + (size_t)k * nrhs;
+    if (!pivots_in_range(I, J, k, m, n)) {      // failed block: NaN gradients
+      const float qf = __int_as_float(0x7fc00000);
+      for (size_t it = tid; it < (size_t)n * nrhs; it += nt) g.dx[(size_t)b * n * nrhs + it] = qf;
+      if (g.dC) for (size_t it = tid; it < (size_t)m * k; it += nt) g.dC[(size_t)b * m * k + it] = qf;
+      if (g.dR) for (size_t it = tid; it < (size_t)k * n; it += nt) g.dR[(size_t)b * k * n + it] = qf;
+      if (g.dG) for (size_t it = tid; it < (size_t)k * k; it += nt) g.dG[(size_t)b * k * k + it] = qf;
+      if (tid == 0) g.dell[b] = __longlong_as_double(0x7ff8000000000000ll);
+      __syncthreads();
+      continue;
+    }
     double dl = 0.0;
     for (int it = tid; it < k * nrhs; it += nt) {
       const int a = it / nrhs, c = it - a * nrhs;

@@ -98,3 +98,67 @@ def test_multiplier_apply_and_gather_reject_bad_arguments():
     assert "INVALID_ARG" in str(_err(lra.lra_gather_rows, prob, torch.zeros(0, dtype=torch.int32, device="cuda")))
     with pytest.raises(ValueError):
         lra.lra_multiplier_apply(prob, None, out=torch.zeros(30, 19, dtype=torch.float64, device="cuda"))
+
+
+def test_residual_sample_catches_out_of_range_indices():
+    """A sample index outside [0, m) or [0, n) is caught on the device before it
+    is read through: every statistic is NaN, and the next valid call is fine."""
+    import paper_1710_07946_gb300 as lra
+    p = li.dense_lowrank(64, 48, r=4, seed=5)
+    prob, _ = to_device(p)
+    I0 = torch.arange(4, dtype=torch.int32, device="cuda")
+    out = lra.lra_ca_run(prob, I0, 4, 2)
+    good_q = torch.arange(0, 64, 3, dtype=torch.int32, device="cuda")
+    good_s = torch.arange(0, 48, 5, dtype=torch.int32, device="cuda")
+    for q, s in ((torch.tensor([0, -1, 5], dtype=torch.int32, device="cuda"), good_s),
+                 (torch.tensor([0, 64], dtype=torch.int32, device="cuda"), good_s),
+                 (good_q, torch.tensor([48, 1], dtype=torch.int32, device="cuda")),
+                 (good_q, torch.tensor([2, -7], dtype=torch.int32, device="cuda"))):
+        st = lra.lra_residual_sample(prob, out["C"], out["U"], out["R"], q, s).cpu().numpy()
+        assert np.isnan(st).all(), st
+    st = lra.lra_residual_sample(prob, out["C"], out["U"], out["R"], good_q, good_s).cpu().numpy()
+    assert np.isfinite(st).all() and st[4] < 1e-10
+
+
+def test_batched_residual_flags_only_the_block_with_a_bad_index():
+    import paper_1710_07946_gb300 as lra
+    p, blocks, lev = li.fmm_blocks(npts=1 << 13, leaf=64, min_size=64, max_size=2048, nblocks=4, seed=9)
+    prob, _ = to_device(p)
+    bt = lra.Batch(prob, blocks, 8, 2, li.block_initial_rows(blocks, 8, 1))
+    lra.lra_ca_run_batched(bt)
+    nb = len(blocks)
+    Q = np.zeros((nb, 6), dtype=np.int32)
+    S = np.zeros((nb, 5), dtype=np.int32)
+    for b in range(nb):
+        Q[b] = np.arange(6) % blocks[b, 1]
+        S[b] = np.arange(5) % blocks[b, 3]
+    Q[1, 2] = -3                       # negative row in block 1
+    S[2, 4] = blocks[2, 3]             # one past the last column in block 2
+    st = lra.lra_residual_sample_batched(bt, torch.from_numpy(Q).cuda(), torch.from_numpy(S).cuda()).cpu().numpy()
+    assert np.isnan(st[1]).all() and np.isnan(st[2]).all()
+    assert np.isfinite(st[0]).all() and np.isfinite(st[3]).all()
+
+
+def test_gauss_apply_flags_out_of_range_pivots():
+    import paper_1710_07946_gb300 as lra
+    rng = np.random.default_rng(11)
+    nb, m, n, k, nrhs = 3, 96, 80, 8, 4
+    X = torch.from_numpy(rng.random((nb, m, 3))).cuda()
+    Y = torch.from_numpy(rng.random((nb, n, 3)) + np.array([2.0, 0, 0])).cuda()
+    I = np.stack([rng.choice(m, k, replace=False) for _ in range(nb)]).astype(np.int32)
+    J = np.stack([rng.choice(n, k, replace=False) for _ in range(nb)]).astype(np.int32)
+    I[1, 3] = m                        # block 1: row pivot out of range
+    J[2, 0] = -1                       # block 2: column pivot out of range
+    x = torch.from_numpy(rng.standard_normal((nb, n, nrhs)).astype(np.float32)).cuda()
+    y, ctx = lra.lra_gauss_cur_forward(X, Y, torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda(), 0.3, x)
+    y = y.cpu().numpy()
+    assert np.isnan(y[1]).all() and np.isnan(y[2]).all() and np.isfinite(y[0]).all()
+    assert np.isnan(ctx[1].cpu().numpy()).all()
+    dy = torch.ones(nb, m, nrhs, dtype=torch.float32, device="cuda")
+    g = lra.lra_gauss_cur_backward(X, Y, torch.from_numpy(I).cuda(), torch.from_numpy(J).cuda(), 0.3, x, dy, ctx,
+                                   entry_grads=True)
+    for key in ("dx", "dC", "dR", "dG"):
+        v = g[key].cpu().numpy()
+        assert np.isnan(v[1]).all() and np.isnan(v[2]).all() and np.isfinite(v[0]).all(), key
+    dl = g["dell"].cpu().numpy()
+    assert np.isnan(dl[1]) and np.isnan(dl[2]) and np.isfinite(dl[0])
