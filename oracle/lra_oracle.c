@@ -364,28 +364,11 @@ static double house(double* x, int len, int str) {
   return tau;
 }
 
-/* Sum of x[i] y[i] over i = 0..len-1 as four interleaved ascending fma chains
- * (i mod 4 = 0, 1, 2, 3), combined as (s0 + s1) + (s2 + s3).  The QR with
- * column pivoting of the nuclei takes its inner products in this order (the
- * paper fixes none); four chains a quarter as long as one. */
-static double dot4(const double* x, int sx, const double* y, int sy, int len) {
-  double s[4] = {0.0, 0.0, 0.0, 0.0};
-  for (int i = 0; i < len; ++i) s[i & 3] = fma(x[i * sx], y[i * sy], s[i & 3]);
-  return (s[0] + s[1]) + (s[2] + s[3]);
-}
-
-/* house with ||x[1..len-1]||^2 taken by dot4. */
-static double house4(double* x, int len, int str) {
-  double alpha = x[0];
-  double xn2 = dot4(x + str, str, x + str, str, len - 1);
-  if (xn2 == 0.0) return 0.0;
-  double nrm = sqrt(fma(alpha, alpha, xn2));
-  double beta = (alpha >= 0.0) ? -nrm : nrm;
-  double tau = (beta - alpha) / beta;
-  double scal = 1.0 / (alpha - beta);
-  for (int i = 1; i < len; ++i) x[i * str] = x[i * str] * scal;
-  x[0] = beta;
-  return tau;
+/* Squared norm of column segment x[0..len-1] (unit stride): one ascending fma chain. */
+static double sqnorm(const double* x, int len) {
+  double s = 0.0;
+  for (int i = 0; i < len; ++i) s = fma(x[i], x[i], s);
+  return s;
 }
 
 /* Apply H = I - tau v v^T (v[0] = 1 implicit, v[1..] at vv[1..], stride vs)
@@ -399,15 +382,6 @@ static void apply_house(const double* vv, int vs, double tau, double* y, int len
   for (int i = 1; i < len; ++i) y[i * ys] = fma(-c, vv[i * vs], y[i * ys]);
 }
 
-/* apply_house with v^T y = y[0] + dot4(v[1..], y[1..]). */
-static void apply_house4(const double* vv, int vs, double tau, double* y, int len, int ys) {
-  if (tau == 0.0) return;
-  double w = y[0] + dot4(vv + vs, vs, y + ys, ys, len - 1);
-  double c = tau * w;
-  y[0] = y[0] - c;
-  for (int i = 1; i < len; ++i) y[i * ys] = fma(-c, vv[i * vs], y[i * ys]);
-}
-
 /*
  * orc_nucleus: Algorithm algcnnncl with a rank-revealing factorisation in place
  * of the SVD (Remark reubsc).
@@ -415,7 +389,7 @@ static void apply_house4(const double* vv, int vs, double tau, double* y, int le
  *      the column with the largest remaining squared norm (rows t.., recomputed)
  *      is moved to position t, lowest index on ties.  Every inner product of
  *      this QR (the column norms, ||x||^2 of each reflector, v^T y of each
- *      application) is dot4's four interleaved chains.
+ *      application) is one ascending fma chain.
  *   2. Numerical rank r = number of leading |R_tt| > tol |R_00|.
  *   3. U = pinv(G_r) for the truncation G_r = Q_r [R11 R12] P^T: with
  *      T = [R11 R12] (r x k) and the QR factorisation T^T = Z S,
@@ -435,15 +409,15 @@ int32_t orc_nucleus(const double* G, int32_t k, double tol, double* U) {
   for (int32_t t = 0; t < k; ++t) {
     int32_t pj = t; double bn = -1.0;
     for (int32_t j = t; j < k; ++j) {
-      double s = dot4(&A[j * k + t], 1, &A[j * k + t], 1, k - t);
+      double s = sqnorm(&A[j * k + t], k - t);
       if (s > bn) { bn = s; pj = j; }
     }
     if (pj != t) {
       for (int32_t i = 0; i < k; ++i) { double tmp = A[t * k + i]; A[t * k + i] = A[pj * k + i]; A[pj * k + i] = tmp; }
       int32_t tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp;
     }
-    taus[t] = house4(&A[t * k + t], k - t, 1);
-    for (int32_t j = t + 1; j < k; ++j) apply_house4(&A[t * k + t], 1, taus[t], &A[j * k + t], k - t, 1);
+    taus[t] = house(&A[t * k + t], k - t, 1);
+    for (int32_t j = t + 1; j < k; ++j) apply_house(&A[t * k + t], 1, taus[t], &A[j * k + t], k - t, 1);
   }
   int32_t r = 0;
   double r00 = fabs(A[0]);
@@ -512,7 +486,7 @@ int32_t orc_nucleus(const double* G, int32_t k, double tol, double* U) {
  * (Algorithm algcnnncl with Remark reubsc's rank-revealing factorisation),
  * l x k row-major.  As orc_nucleus: Householder QR with column pivoting over
  * the l columns (k steps, column norms over rows t.. recomputed each step,
- * lowest index on ties; the QR's inner products by dot4), r = #{|R_tt| >
+ * lowest index on ties; every inner product one ascending fma chain), r = #{|R_tt| >
  * tol |R_00|}, then the complete
  * orthogonal decomposition: T^T = (rows 0..r-1 of R)^T (l x r) = Z S, and
  * U = P Z S^{-T} Q_r^T.  Returns r.
@@ -527,7 +501,7 @@ int32_t orc_nucleus_rect(const double* G, int32_t k, int32_t l, double tol, doub
   for (int32_t t = 0; t < k; ++t) {
     int32_t pj = t; double bn = -1.0;
     for (int32_t j = t; j < l; ++j) {
-      double s = dot4(&A[(int64_t)j * k + t], 1, &A[(int64_t)j * k + t], 1, k - t);
+      double s = sqnorm(&A[(int64_t)j * k + t], k - t);
       if (s > bn) { bn = s; pj = j; }
     }
     if (pj != t) {
@@ -536,8 +510,8 @@ int32_t orc_nucleus_rect(const double* G, int32_t k, int32_t l, double tol, doub
       }
       int32_t tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp;
     }
-    taus[t] = house4(&A[(int64_t)t * k + t], k - t, 1);
-    for (int32_t j = t + 1; j < l; ++j) apply_house4(&A[(int64_t)t * k + t], 1, taus[t], &A[(int64_t)j * k + t], k - t, 1);
+    taus[t] = house(&A[(int64_t)t * k + t], k - t, 1);
+    for (int32_t j = t + 1; j < l; ++j) apply_house(&A[(int64_t)t * k + t], 1, taus[t], &A[(int64_t)j * k + t], k - t, 1);
   }
   int32_t r = 0;
   double r00 = fabs(A[0]);

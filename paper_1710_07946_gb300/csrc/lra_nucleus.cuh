@@ -4,9 +4,9 @@
 //
 //   1. Householder QR with column pivoting, G P = Q R: at step t the column with
 //      the largest squared norm over rows t.. (recomputed each step) moves to
-//      position t, the lowest index winning ties.  The QR's inner products (the
-//      norms, each reflector's ||x||^2 and v^T y) are four interleaved fma
-//      chains combined (s0 + s1) + (s2 + s3), four lanes per column.
+//      position t, the lowest index winning ties.  Every inner product of the
+//      QR (the norms, each reflector's ||x||^2 and v^T y) is one ascending fma
+//      chain owned by one thread.
 //   2. r = number of leading |R_tt| > tol |R_00|.
 //   3. U = P Z S^{-T} Q_r^T, where T = [R11 R12] (r x k) and T^T = Z S is its QR
 //      (a complete orthogonal decomposition); for r = k this is P R^{-1} Q^T.
@@ -52,86 +52,6 @@ __device__ inline double house_cta(double* x, int len, double* bcast) {
   return tau;
 }
 
-// Four lanes (lane & 3 = w) of an aligned group take sum_i x[i] y[i] over
-// i = 0..len-1: lane w the ascending fma chain of i = w, w+4, ..., combined as
-// (s0 + s1) + (s2 + s3), the total in every lane of the group.  Called by all
-// lanes of the warp (len 0 for groups without work).
-__device__ __forceinline__ double dot4_group(const double* x, const double* y, int len, int w) {
-  double s = 0.0;
-  for (int i = w; i < len; i += 4) s = fma(x[i], y[i], s);
-  s = s + __shfl_xor_sync(0xffffffffu, s, 1);     // s0 + s1 (commutative, so both lanes agree)
-  s = s + __shfl_xor_sync(0xffffffffu, s, 2);     // (s0 + s1) + (s2 + s3)
-  return s;
-}
-
-// Trips of a loop over n items handled by groups of four lanes (nt / 4 groups),
-// equal for all lanes of a warp so that every lane reaches the shuffles.
-__device__ __forceinline__ int group_trips(int n) {
-  const int ngrp = blockDim.x >> 2, g0 = (threadIdx.x & ~31) >> 2;
-  return g0 < n ? (n - g0 + ngrp - 1) / ngrp : 0;
-}
-
-// house_cta with ||x[1..len-1]||^2 taken by lanes 0..3 of warp 0 (dot4_group).
-__device__ inline double house4_cta(double* x, int len, double* bcast) {
-  if (threadIdx.x < 32) {
-    const int lane = threadIdx.x;
-    const double xn2 = dot4_group(x + 1, x + 1, lane < 4 ? len - 1 : 0, lane & 3);
-    if (lane == 0) {
-      double alpha = x[0], tau = 0.0, scal = 0.0, beta = alpha;
-      if (xn2 != 0.0) {
-        double nrm = sqrt(fma(alpha, alpha, xn2));
-        beta = (alpha >= 0.0) ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-        scal = 1.0 / (alpha - beta);
-      }
-      bcast[0] = tau; bcast[1] = scal; bcast[2] = beta;
-    }
-  }
-  __syncthreads();
-  const double tau = bcast[0], scal = bcast[1];
-  if (tau != 0.0) {
-    for (int i = 1 + threadIdx.x; i < len; i += blockDim.x) x[i] = x[i] * scal;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0 && tau != 0.0) x[0] = bcast[2];
-  __syncthreads();
-  return tau;
-}
-
-// Columns j = j0 .. j0 + ncol - 1 (stride ld) <- (I - tau v v^T) applied to
-// rows 0..len-1, four lanes per column: v^T y = y[0] + dot4_group(v[1..],
-// y[1..]), then each lane updates its own rows.
-__device__ inline void apply_house4_cols(const double* v, double tau, double* A, int ld, int j0, int ncol, int len) {
-  const int w = threadIdx.x & 3, grp = threadIdx.x >> 2, ngrp = blockDim.x >> 2;
-  const int trips = group_trips(ncol);
-  for (int u = 0; u < trips; ++u) {
-    const int g = grp + u * ngrp;
-    const bool act = g < ncol && tau != 0.0;
-    double* y = A + (size_t)(j0 + (g < ncol ? g : 0)) * ld;
-    const double y0 = act ? y[0] : 0.0;
-    const double d = dot4_group(v + 1, y + 1, act ? len - 1 : 0, w);
-    if (act) {
-      const double c = tau * (y0 + d);
-      if (w == 0) y[0] = y0 - c;
-      for (int i = 1 + w; i < len; i += 4) y[i] = fma(-c, v[i], y[i]);
-    }
-  }
-}
-
-// Squared norms over rows t..k-1 of columns j0 .. j0 + ncol - 1 into nrm[j],
-// four lanes per column (dot4_group).
-__device__ inline void col_norms4(const double* A, int ld, int t, int k, int j0, int ncol, double* nrm) {
-  const int w = threadIdx.x & 3, grp = threadIdx.x >> 2, ngrp = blockDim.x >> 2;
-  const int trips = group_trips(ncol);
-  for (int u = 0; u < trips; ++u) {
-    const int g = grp + u * ngrp;
-    const bool act = g < ncol;
-    const double* col = A + (size_t)(j0 + (act ? g : 0)) * ld + t;
-    const double s = dot4_group(col, col, act ? k - t : 0, w);
-    if (act && w == 0) nrm[j0 + g] = s;
-  }
-}
-
 // y <- (I - tau v v^T) y for one column, by the calling thread alone.
 __device__ __forceinline__ void apply_house_seq(const double* v, double tau, double* y, int len) {
   if (tau == 0.0) return;
@@ -140,6 +60,24 @@ __device__ __forceinline__ void apply_house_seq(const double* v, double tau, dou
   const double c = tau * w;
   y[0] = y[0] - c;
   for (int i = 1; i < len; ++i) y[i] = fma(-c, v[i], y[i]);
+}
+
+// Columns j = j0 .. j0 + ncol - 1 (stride ld) <- (I - tau v v^T) applied to
+// rows 0..len-1: one thread per column, v^T y = y[0] + v[1] y[1] + ... as one
+// ascending fma chain (apply_house_seq).
+__device__ inline void apply_house_cols(const double* v, double tau, double* A, int ld, int j0, int ncol, int len) {
+  for (int g = threadIdx.x; g < ncol; g += blockDim.x) apply_house_seq(v, tau, A + (size_t)(j0 + g) * ld, len);
+}
+
+// Squared norms over rows t..k-1 of columns j0 .. j0 + ncol - 1 into nrm[j]:
+// one thread per column, one ascending fma chain.
+__device__ inline void col_norms(const double* A, int ld, int t, int k, int j0, int ncol, double* nrm) {
+  for (int g = threadIdx.x; g < ncol; g += blockDim.x) {
+    const double* col = A + (size_t)(j0 + g) * ld;
+    double s = 0.0;
+    for (int i = t; i < k; ++i) s = fma(col[i], col[i], s);
+    nrm[j0 + g] = s;
+  }
 }
 
 // U (k x k, row-major, global or shared) <- pinv of the rank-r QRP truncation of
@@ -164,7 +102,7 @@ __device__ inline int nucleus_cta(const double* G, int k, double tol, double* U,
   for (int j = tid; j < k; j += nt) perm[j] = j;
   __syncthreads();
   for (int t = 0; t < k; ++t) {
-    col_norms4(A, ld, t, k, t, k - t, nrm);
+    col_norms(A, ld, t, k, t, k - t, nrm);
     __syncthreads();
     if (tid < 32) {
       // largest squared norm, lowest column on ties (integer keys, one warp)
@@ -190,9 +128,9 @@ __device__ inline int nucleus_cta(const double* G, int k, double tol, double* U,
         double tmp = A[t * ld + i]; A[t * ld + i] = A[pj * ld + i]; A[pj * ld + i] = tmp;
       }
     __syncthreads();
-    const double tau = house4_cta(&A[t * ld + t], k - t, bc);
+    const double tau = house_cta(&A[t * ld + t], k - t, bc);
     if (tid == 0) taus[t] = tau;
-    apply_house4_cols(&A[t * ld + t], tau, &A[t], ld, t + 1, k - t - 1, k - t);
+    apply_house_cols(&A[t * ld + t], tau, &A[t], ld, t + 1, k - t - 1, k - t);
     __syncthreads();
   }
   if (tid == 0) {
@@ -289,7 +227,7 @@ __device__ inline int nucleus_rect_cta(const double* G, int k, int l, double tol
     // largest squared column norm over rows t.., lowest column on ties (one thread
     // per column accumulates, one warp compares integer keys)
     double* nrm = X;                                    // l scratch doubles (X is unused yet)
-    col_norms4(A, ldk, t, k, t, l - t, nrm);
+    col_norms(A, ldk, t, k, t, l - t, nrm);
     __syncthreads();
     if (tid < 32) {
       Cand c = cand_none();
@@ -314,9 +252,9 @@ __device__ inline int nucleus_rect_cta(const double* G, int k, int l, double tol
         double tmp = A[t * ldk + i]; A[t * ldk + i] = A[pj * ldk + i]; A[pj * ldk + i] = tmp;
       }
     __syncthreads();
-    const double tau = house4_cta(&A[t * ldk + t], k - t, bc);
+    const double tau = house_cta(&A[t * ldk + t], k - t, bc);
     if (tid == 0) taus[t] = tau;
-    apply_house4_cols(&A[t * ldk + t], tau, &A[t], ldk, t + 1, l - t - 1, k - t);
+    apply_house_cols(&A[t * ldk + t], tau, &A[t], ldk, t + 1, l - t - 1, k - t);
     __syncthreads();
   }
   if (tid == 0) {
