@@ -80,13 +80,29 @@ typedef enum {
 
 typedef struct lra_multiplier_s* lra_multiplier;   /* opaque, library-owned */
 
+/* Which side the multiplier is applied on (paper: Remark re2orddmn -- for
+ * m > n pre-multiply instead of post-multiplying). */
+typedef enum {
+  LRA_SIDE_RIGHT = 0,       /* W' = W M, M n x n: C = W'[:, J], R = W[I, :]          */
+  LRA_SIDE_LEFT = 1         /* W' = M^T W, M m x m: C = W[:, J], R = W'[I, :]        */
+} lra_mult_side;
+
 /*
- * lra_precondition -- describe the right multiplier M of the pre-processed
- * matrix W' = W M, which C-A then approximates (paper: Section "Pre-processing
- * with matrices of abridged Hadamard and Fourier transforms"; Appendix
- * "Abridged Hadamard and Fourier Multipliers", eqs. eqrfd / eqbschf; Section
- * "Pre-processing with quasi Gaussian matrices", case (i)).  M is never formed:
- * the strip gathers evaluate the needed columns of W M on the fly.
+ * lra_precondition -- describe the multiplier M of the pre-processed matrix
+ * W' = W M (side LRA_SIDE_RIGHT, M n x n) or W' = M^T W (side LRA_SIDE_LEFT,
+ * M m x m, for m > n), which C-A then approximates (paper: Section
+ * "Pre-processing with matrices of abridged Hadamard and Fourier transforms";
+ * Appendix "Abridged Hadamard and Fourier Multipliers", eqs. eqrfd / eqbschf;
+ * Section "Pre-processing with quasi Gaussian matrices", case (i); Remark
+ * re2orddmn for the left side).  M is never formed: the strip gathers evaluate
+ * the needed entries of W' on the fly.  Below, n is the order of M (the
+ * problem's n for the right side, its m for the left side).  With a left
+ * multiplier, w'_ij combines entries of column j of W with the weights of
+ * column i of M, in the order stated for the right side, and the CUR of W from
+ * the generator (I, J) of W' is C = W[:, J], U = pinv(W'[I, J]), R = W'[I, :]
+ * (the right-side back-transform applied to W^T).  Left multipliers serve
+ * lra_ca_run, lra_ca_run_warm, lra_ca_run_noalloc and lra_multiplier_apply;
+ * certified-FP32 mode runs them in FP64.
  *
  *   kind = LRA_MULT_ARHT: M = 2^{-d/2} D H_{n,d} P, depth_or_nnz = d (1..10),
  *     n = 2^d s.  H_{n,d} = H_{2^d} (x) I_s is the d-step abridged Hadamard
@@ -110,17 +126,20 @@ typedef struct lra_multiplier_s* lra_multiplier;   /* opaque, library-owned */
  * The random draws (signs, permutation, positions) are inputs, so that runs are
  * reproducible.  The descriptor is copied to device memory owned by the handle;
  * the host arrays may be freed on return.  The copy is synchronous.
- * Errors: LRA_ERR_INVALID_ARG (bad kind, sizes, out-of-range or unsorted
- * indices, signs not +-1), LRA_ERR_CUDA.
+ * Errors: LRA_ERR_INVALID_ARG (bad kind or side, sizes, out-of-range or
+ * unsorted indices, signs not +-1), LRA_ERR_CUDA.  A call that uses the handle
+ * with a problem whose m (left) or n (right) differs from the handle's n
+ * returns LRA_ERR_INVALID_ARG.
  */
-lra_status lra_precondition(lra_multiplier* out, int32_t kind, int64_t n, int32_t depth_or_nnz,
+lra_status lra_precondition(lra_multiplier* out, int32_t kind, int32_t side, int64_t n, int32_t depth_or_nnz,
                             const int32_t* perm_or_rows, const int8_t* signs);
 
 /* Free a multiplier handle (NULL is accepted). */
 lra_status lra_multiplier_destroy(lra_multiplier mult);
 
 /*
- * lra_multiplier_apply -- the pre-processed input W' = W M written out as a
+ * lra_multiplier_apply -- the pre-processed input W' = W M (or M^T W for a
+ * left multiplier) written out as a
  * dense FP64 matrix (paper: the bidiagonal pre-processing tests multiply each
  * input by the factors before C-A; the CUR of W from generators of W' is
  * C = W'[:, J], U = pinv(W'[I, J]), R = W[I, :], as for lra_ca_run with a

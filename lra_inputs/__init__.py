@@ -55,6 +55,7 @@ class Problem:
     srow: Optional[np.ndarray] = None       # (n, nnz) int32 ascending per column
     ssign: Optional[np.ndarray] = None      # (n, nnz) int8, +-1
     entries: str = "f64"                    # kernel: entries evaluated in "f64" or "f32"
+    mside: int = 0                          # multiplier side: 0 right (W M, M n x n), 1 left (M^T W, M m x m)
     meta: dict = field(default_factory=dict)
 
     @property
@@ -120,20 +121,30 @@ def bidiag_descriptor(n: int, q: int, seed: int):
     return perms, signs
 
 
-def with_bidiag(p: Problem, q: int, seed: int) -> Problem:
-    perms, signs = bidiag_descriptor(p.n, q, seed)
+def _side(p: Problem, side: str):
+    """(order of M, mside) for a multiplier on the given side of p."""
+    if side not in ("right", "left"):
+        raise ValueError("side is 'right' or 'left'")
+    return (p.n, 0) if side == "right" else (p.m, 1)
+
+
+def with_bidiag(p: Problem, q: int, seed: int, side: str = "right") -> Problem:
+    order, p.mside = _side(p, side)
+    perms, signs = bidiag_descriptor(order, q, seed)
     p.mkind, p.depth, p.perm, p.dsign = MULT_BIDIAG, q, perms, signs
     return p
 
 
-def with_arht(p: Problem, depth: int, seed: int) -> Problem:
-    perm, dsign = arht_descriptor(p.n, depth, seed)
+def with_arht(p: Problem, depth: int, seed: int, side: str = "right") -> Problem:
+    order, p.mside = _side(p, side)
+    perm, dsign = arht_descriptor(order, depth, seed)
     p.mkind, p.depth, p.perm, p.dsign = MULT_ARHT, depth, perm, dsign
     return p
 
 
-def with_sparse(p: Problem, nnz: int, seed: int) -> Problem:
-    srow, ssign = sparse_pm1_descriptor(p.n, nnz, seed)
+def with_sparse(p: Problem, nnz: int, seed: int, side: str = "right") -> Problem:
+    order, p.mside = _side(p, side)
+    srow, ssign = sparse_pm1_descriptor(order, nnz, seed)
     p.mkind, p.nnz, p.srow, p.ssign = MULT_SPARSE, nnz, srow, ssign
     return p
 

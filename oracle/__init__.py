@@ -26,6 +26,7 @@ class _Problem(ct.Structure):
         ("ell", ct.c_double), ("mkind", ct.c_int32), ("depth", ct.c_int32),
         ("perm", ct.c_void_p), ("dsign", ct.c_void_p), ("nnz", ct.c_int32),
         ("srow", ct.c_void_p), ("ssign", ct.c_void_p), ("brow", ct.c_void_p), ("bval", ct.c_void_p),
+        ("mside", ct.c_int32),
     ]
 
 
@@ -115,6 +116,8 @@ class _Marshalled:
                 setattr(s, name, a.ctypes.data)
         s.ell = float(p.ell)
         s.mkind = int(p.mkind)
+        s.mside = int(getattr(p, "mside", 0))
+        order = int(p.m) if s.mside else int(p.n)          # M is order x order
         if p.mkind == 1:
             perm = np.ascontiguousarray(p.perm, dtype=np.int32)
             ds = np.ascontiguousarray(p.dsign, dtype=np.int8)
@@ -128,7 +131,7 @@ class _Marshalled:
         elif p.mkind == 3:
             perms = np.ascontiguousarray(p.perm, dtype=np.int32)
             sg = np.ascontiguousarray(p.dsign, dtype=np.int8)
-            brow, bval = bidiag_columns(p.n, p.depth, perms, sg)
+            brow, bval = bidiag_columns(order, p.depth, perms, sg)
             self.keep += [perms, sg, brow, bval]
             s.depth, s.perm, s.dsign = int(p.depth), perms.ctypes.data, sg.ctypes.data
             s.brow, s.bval = brow.ctypes.data, bval.ctypes.data
@@ -479,9 +482,11 @@ def hadamard_abridged(n, d):
 
 
 def multiplier_dense(p):
-    """Dense n x n multiplier M of the problem (ARHT or sparse +-1)."""
+    """Dense multiplier M of the problem (n x n for a right multiplier, m x m for
+    a left one), assembled from its definition."""
     mp = _Marshalled(p)
-    M = np.empty((p.n, p.n))
+    N = p.m if getattr(p, "mside", 0) else p.n
+    M = np.empty((N, N))
     lib().orc_multiplier_dense(mp.ref, _ptr(M))
     return M
 

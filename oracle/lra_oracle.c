@@ -69,6 +69,9 @@ typedef struct {
    * marking an unused slot */
   const int32_t* brow;
   const int32_t* bval;
+  /* side of the multiplier (Remark re2orddmn): 0 = right, W' = W M with M
+   * n x n; 1 = left, W' = M^T W with M m x m (for m > n) */
+  int32_t mside;
 } orc_problem;
 
 /* Entry w_ij of the input W (no multiplier).  Kernel entries follow the
@@ -137,45 +140,58 @@ static double arht_scale(int d) { return 1.0 / sqrt((double)(1LL << d)); }
 
 static int popcount32(uint32_t v) { int c = 0; while (v) { c += (int)(v & 1u); v >>= 1; } return c; }
 
-/* Entry w'_ij of the pre-processed matrix W' = W M.
- * ARHT: M = 2^(-d/2) D H_{n,d} P with H_{n,d} = H_{2^d} (x) I_s, n = 2^d s
- *   (recursion eqrfd cut at depth d with H_s = I_s).  With perm[j] = b s + t,
- *   column j of M holds 2^d nonzeros, at rows a s + t, a = 0..2^d-1, equal to
+/* One term of a pre-processed entry: the input entry that row r of the
+ * combining column of M multiplies.  Right multiplier, W' = W M: w'_ij = sum_r
+ * w_ir M_rj, so column j of M combines entries of row i.  Left multiplier,
+ * W' = M^T W: w'_ij = sum_r M_ri w_rj, so column i of M combines entries of
+ * column j. */
+static double entry_term(const orc_problem* p, int64_t i, int64_t j, int64_t r) {
+  return p->mside ? entry_w(p, r, j) : entry_w(p, i, r);
+}
+
+/* Entry w'_ij of the pre-processed matrix W' = W M (or M^T W).  Below, c is
+ * the column of M that combines the terms (j for the right side, i for the
+ * left) and N the order of M.
+ * ARHT: M = 2^(-d/2) D H_{N,d} P with H_{N,d} = H_{2^d} (x) I_s, N = 2^d s
+ *   (recursion eqrfd cut at depth d with H_s = I_s).  With perm[c] = b s + t,
+ *   column c of M holds 2^d nonzeros, at rows a s + t, a = 0..2^d-1, equal to
  *   2^(-d/2) D_{a s + t} (-1)^{popcount(a & b)}.  The 2^d terms are summed in
  *   ascending a, then scaled once.
- * Sparse +-1: column j of M holds nnz entries +-1/2 (for nnz = 4; in general
- *   +-1/sqrt(nnz)) at rows srow[j*nnz + t]; summed in ascending t, scaled once. */
+ * Sparse +-1: column c of M holds nnz entries +-1/2 (for nnz = 4; in general
+ *   +-1/sqrt(nnz)) at rows srow[c*nnz + t]; summed in ascending t, scaled once. */
 static double entry_wp(const orc_problem* p, int64_t i, int64_t j) {
   if (p->mkind == ORC_MULT_NONE) return entry_w(p, i, j);
+  int64_t c = p->mside ? i : j;
+  int64_t N = p->mside ? p->m : p->n;
   if (p->mkind == ORC_MULT_ARHT) {
-    int64_t s = p->n >> p->depth;
-    int64_t pj = p->perm[j];
-    int64_t b = pj / s, t = pj % s;
+    int64_t s = N >> p->depth;
+    int64_t pc = p->perm[c];
+    int64_t b = pc / s, t = pc % s;
     double acc = 0.0;
     for (int64_t a = 0; a < (1LL << p->depth); ++a) {
       int64_t r = a * s + t;
-      double v = entry_w(p, i, r) * (double)p->dsign[r];
+      double v = entry_term(p, i, j, r) * (double)p->dsign[r];
       if (popcount32((uint32_t)(a & b)) & 1) acc = acc - v; else acc = acc + v;
     }
     return acc * arht_scale(p->depth);
   }
   if (p->mkind == ORC_MULT_BIDIAG) {
     /* nonzero slots in ascending row order, each an fma with its integer weight */
-    int64_t w = (1LL << p->depth) < p->n ? (1LL << p->depth) : p->n;
+    int64_t w = (1LL << p->depth) < N ? (1LL << p->depth) : N;
     double acc = 0.0;
     for (int64_t t = 0; t < w; ++t) {
-      int32_t v = p->bval[j * w + t];
+      int32_t v = p->bval[c * w + t];
       if (v == 0) continue;
-      acc = fma((double)v, entry_w(p, i, p->brow[j * w + t]), acc);
+      acc = fma((double)v, entry_term(p, i, j, p->brow[c * w + t]), acc);
     }
     return acc * arht_scale(p->depth);
   }
   /* sparse */
   double acc = 0.0;
   for (int t = 0; t < p->nnz; ++t) {
-    int64_t r = p->srow[j * p->nnz + t];
-    double v = entry_w(p, i, r);
-    if (p->ssign[j * p->nnz + t] < 0) acc = acc - v; else acc = acc + v;
+    int64_t r = p->srow[c * p->nnz + t];
+    double v = entry_term(p, i, j, r);
+    if (p->ssign[c * p->nnz + t] < 0) acc = acc - v; else acc = acc + v;
   }
   return acc * (1.0 / sqrt((double)p->nnz));
 }
@@ -196,6 +212,19 @@ void orc_gather_cols_t(const orc_problem* p, const int32_t* J, int32_t k, double
 void orc_gather_rows_orig(const orc_problem* p, const int32_t* I, int32_t k, double* out) {
   for (int32_t a = 0; a < k; ++a)
     for (int64_t j = 0; j < p->n; ++j) out[(int64_t)a * p->n + j] = entry_w(p, I[a], j);
+}
+
+/* The factors of the CUR of W from a generator (I, J) of W' = M^T W (a left
+ * multiplier): W ~ W[:, J] pinv(W'[I, J]) W'[I, :], which is reading 1's
+ * back-transform (C from W', R from W) applied to W^T = W^T M.  So C holds the
+ * original columns (m x kJ) and R the pre-processed rows (kI x n).  Called after
+ * the core W'[I, J] has been taken; a no-op for a right multiplier. */
+static void left_outputs(const orc_problem* p, const int32_t* I, int32_t kI, const int32_t* J, int32_t kJ,
+                         double* C, double* R) {
+  if (!p->mside || p->mkind == ORC_MULT_NONE) return;
+  for (int64_t i = 0; i < p->m; ++i)
+    for (int32_t a = 0; a < kJ; ++a) C[i * kJ + a] = entry_w(p, i, J[a]);
+  orc_gather_rows(p, I, kI, R);
 }
 
 /* ------------------------------------------------------------------ */
@@ -623,6 +652,7 @@ int orc_ca_run_warm(const orc_problem* p, int32_t k, int32_t sweeps, const int32
   for (int32_t a = 0; a < k; ++a)
     for (int32_t b = 0; b < k; ++b) G[a * k + b] = C[(int64_t)I[a] * k + b];
   int32_t r = orc_nucleus(G, k, rank_tol, U);
+  left_outputs(p, I, k, J, k, C, R);
   if (r < k && status == ORC_OK) status = ORC_WARN_RANK_DEFICIENT;
   info[0] = r; info[1] = total; info[2] = loops; info[3] = status;
   free(Rs); free(Cs); free(G); free(Jn); free(In);
@@ -837,6 +867,7 @@ int orc_cynical(const orc_problem* p, int32_t kind, int32_t r, int32_t q, int32_
       for (int32_t a = 0; a < r; ++a) C[i * r + a] = Ct[(int64_t)a * m + i];
     free(Ct);
     orc_gather_rows_orig(p, I, r, R);
+    left_outputs(p, I, r, J, r, C, R);
     info[0] = inf[0]; info[1] = swaps; info[2] = inf[2]; info[3] = status;
   }
   free(S); free(Ii); free(Jj); free(Cq); free(Rq); free(lv);
@@ -1031,6 +1062,7 @@ int orc_oversample_cycle(const orc_problem* p, const int32_t* I, const int32_t* 
   for (int32_t a = 0; a < k; ++a)
     for (int32_t b = 0; b < l; ++b) G[(int64_t)a * l + b] = C[(int64_t)I[a] * l + b];
   int32_t r = orc_nucleus_rect(G, k, l, rank_tol, U);
+  left_outputs(p, I, k, Jo, l, C, R);
   if (r < k && status == ORC_OK) status = ORC_WARN_RANK_DEFICIENT;
   info[0] = r; info[1] = l; info[2] = status; info[3] = cycles; info[4] = ptried;
   free(X); free(Rs); free(in); free(s); free(x); free(Ct); free(G);
@@ -1180,6 +1212,7 @@ int orc_prjvol(const orc_problem* p, const int32_t* I, const int32_t* J, int32_t
   for (int32_t a = 0; a < k; ++a)
     for (int32_t b = 0; b < l; ++b) G[(int64_t)a * l + b] = C[(int64_t)I[a] * l + b];
   int32_t rk = orc_nucleus_rect(G, k, l, rank_tol, U);
+  left_outputs(p, I, k, Jo, l, C, R);
   if (rk < k && status == ORC_OK) status = ORC_WARN_RANK_DEFICIENT;
   info[0] = rk; info[1] = l; info[2] = status; info[3] = nsw; info[4] = r;
   free(A); free(J0); free(Ct); free(G);
@@ -1454,6 +1487,7 @@ int orc_ca_lev(const orc_problem* p, int32_t k, int32_t r, int32_t iters, int32_
       for (int32_t a = 0; a < kI; ++a) U[(int64_t)b * kI + a] = Ut[(int64_t)a * kJ + b];
     free(Ut);
   }
+  left_outputs(p, I, kI, J, kJ, C, R);
   if (rank < (kI < kJ ? kI : kJ) && status == ORC_OK) status = ORC_WARN_RANK_DEFICIENT;
   info[0] = rank; info[1] = kI; info[2] = kJ; info[3] = status;
   free(S); free(v); free(Ct); free(G);
@@ -1606,11 +1640,12 @@ void orc_hadamard_abridged(int64_t n, int32_t d, double* H) {
   }
 }
 
-/* Dense multiplier M (n x n) of the problem, assembled from its definition:
- * ARHT M = 2^(-d/2) D H_{n,d} P (H from the recursion above, P moving column
- * perm[j] of D H to position j); sparse: M[srow][j] = ssign / sqrt(nnz). */
+/* Dense multiplier M (N x N, N = n for a right multiplier, m for a left one)
+ * of the problem, assembled from its definition: ARHT M = 2^(-d/2) D H_{N,d} P
+ * (H from the recursion above, P moving column perm[j] of D H to position j);
+ * sparse: M[srow][j] = ssign / sqrt(nnz). */
 void orc_multiplier_dense(const orc_problem* p, double* M) {
-  int64_t n = p->n;
+  int64_t n = p->mside ? p->m : p->n;
   memset(M, 0, sizeof(double) * (size_t)n * (size_t)n);
   if (p->mkind == ORC_MULT_NONE) { for (int64_t i = 0; i < n; ++i) M[i * n + i] = 1.0; return; }
   if (p->mkind == ORC_MULT_SPARSE) {

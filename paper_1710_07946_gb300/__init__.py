@@ -32,6 +32,7 @@ LRA_WARN_RANK_DEFICIENT, LRA_WARN_NOT_CONVERGED = 16, 17
 LRA_F64, LRA_F32 = 0, 1
 LRA_DENSE, LRA_KERNEL_LAPLACE, LRA_KERNEL_GAUSSIAN = 0, 1, 2
 LRA_MULT_NONE, LRA_MULT_ARHT, LRA_MULT_SPARSE_PM1, LRA_MULT_BIDIAG = 0, 1, 2, 3
+LRA_SIDE_RIGHT, LRA_SIDE_LEFT = 0, 1
 LRA_MODE_FP64, LRA_MODE_MIXED = 0, 1
 LRA_INFO_LEN = 8
 LRA_MAX_STAGES = 8
@@ -103,7 +104,7 @@ def _load():
     L = ct.CDLL(_build.LIB)
     vp, i32, i64, f64, sz = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_double, ct.c_size_t
     P, PP, PC = ct.POINTER(_Problem), ct.POINTER(_Params), ct.POINTER(_Cur)
-    L.lra_precondition.argtypes = [ct.POINTER(vp), i32, i64, i32, vp, vp]
+    L.lra_precondition.argtypes = [ct.POINTER(vp), i32, i32, i64, i32, vp, vp]
     L.lra_multiplier_destroy.argtypes = [vp]
     L.lra_ca_workspace_size.argtypes = [P, PP, vp, ct.POINTER(sz)]
     L.lra_ca_run.argtypes = [P, PP, vp, vp, PC, vp, sz, vp]
@@ -255,18 +256,20 @@ def lra_version() -> str:
     return _load().lra_version().decode()
 
 
-def lra_precondition(kind: str, n: int, depth_or_nnz: int, perm_or_rows, signs) -> Multiplier:
-    """Right multiplier M of W' = W M: ``kind`` 'arht' (2^{-d/2} D H_{n,d} P),
-    'sparse' (+-1/sqrt(nnz) entries) or 'bidiag' (2^{-q/2} prod (I + D_i S) P_i,
-    q = depth_or_nnz factors; perm_or_rows, signs q x n).  perm_or_rows / signs:
-    host int32 / int8 arrays (numpy or CPU tensors) holding the random draws."""
+def lra_precondition(kind: str, n: int, depth_or_nnz: int, perm_or_rows, signs, side: str = "right") -> Multiplier:
+    """Multiplier M (n x n) of W' = W M (``side`` 'right') or W' = M^T W ('left',
+    n = the problem's m): ``kind`` 'arht' (2^{-d/2} D H_{n,d} P), 'sparse'
+    (+-1/sqrt(nnz) entries) or 'bidiag' (2^{-q/2} prod (I + D_i S) P_i, q =
+    depth_or_nnz factors; perm_or_rows, signs q x n).  perm_or_rows / signs: host
+    int32 / int8 arrays (numpy or CPU tensors) holding the random draws."""
     import numpy as np
     L = _load()
     k = {"arht": LRA_MULT_ARHT, "sparse": LRA_MULT_SPARSE_PM1, "bidiag": LRA_MULT_BIDIAG}[kind]
+    sd = {"right": LRA_SIDE_RIGHT, "left": LRA_SIDE_LEFT}[side]
     idx = np.ascontiguousarray(np.asarray(perm_or_rows), dtype=np.int32).reshape(-1)
     sg = np.ascontiguousarray(np.asarray(signs), dtype=np.int8).reshape(-1)
     h = ct.c_void_p()
-    _check(L.lra_precondition(ct.byref(h), k, int(n), int(depth_or_nnz), idx.ctypes.data, sg.ctypes.data),
+    _check(L.lra_precondition(ct.byref(h), k, sd, int(n), int(depth_or_nnz), idx.ctypes.data, sg.ctypes.data),
            "lra_precondition")
     return Multiplier(h.value, k, n)
 

@@ -36,14 +36,16 @@ lra_status make_dev_problem(const lra_problem* p, lra_multiplier mult, DevProble
   }
   d.mkind = LRA_MULT_NONE;
   if (mult != nullptr && mult->kind != LRA_MULT_NONE) {
-    if (mult->n != p->n) return LRA_ERR_INVALID_ARG;
+    const int64_t dim = (mult->side == LRA_SIDE_LEFT) ? p->m : p->n;   // M is dim x dim
+    if (mult->n != dim) return LRA_ERR_INVALID_ARG;
     d.mkind = mult->kind;
+    d.mside = (mult->side == LRA_SIDE_LEFT) ? 1 : 0;
     d.perm = mult->d_idx;
     d.sign = mult->d_sign;
     d.mscale = mult->scale;
     if (mult->kind == LRA_MULT_ARHT) {
       d.depth = mult->param;
-      d.s = p->n >> mult->param;
+      d.s = dim >> mult->param;
     } else if (mult->kind == LRA_MULT_BIDIAG) {
       d.depth = mult->param;
       d.nnz = mult->width;
@@ -93,7 +95,7 @@ lra_status current_device_info(DeviceInfo* info) {
 // that many slots per column in ascending rows, value 0 in the unused slots.
 // |values| <= 2^q (int32 for q <= 30); the scale 2^{-q/2} is applied by the
 // gathers.
-static lra_status make_bidiag(lra_multiplier* out, int64_t n, int32_t q, const int32_t* perms,
+static lra_status make_bidiag(lra_multiplier* out, int32_t side, int64_t n, int32_t q, const int32_t* perms,
                               const int8_t* signs) {
   const int64_t w = std::min<int64_t>(int64_t(1) << q, n);
   std::vector<int32_t> rows((size_t)n * (size_t)w, 0);
@@ -138,6 +140,7 @@ static lra_status make_bidiag(lra_multiplier* out, int64_t n, int32_t q, const i
   }
   lra_multiplier m = new lra_multiplier_s;
   m->kind = LRA_MULT_BIDIAG;
+  m->side = side;
   m->n = n;
   m->param = q;
   m->width = (int32_t)w;
@@ -177,10 +180,11 @@ static lra_status make_bidiag(lra_multiplier* out, int64_t n, int32_t q, const i
 
 extern "C" {
 
-lra_status lra_precondition(lra_multiplier* out, int32_t kind, int64_t n, int32_t param, const int32_t* idx,
-                            const int8_t* signs) {
+lra_status lra_precondition(lra_multiplier* out, int32_t kind, int32_t side, int64_t n, int32_t param,
+                            const int32_t* idx, const int8_t* signs) {
   if (out == nullptr) return LRA_ERR_INVALID_ARG;
   *out = nullptr;
+  if (side != LRA_SIDE_RIGHT && side != LRA_SIDE_LEFT) return LRA_ERR_INVALID_ARG;
   if (n < 1 || n >= (int64_t(1) << 31) || idx == nullptr || signs == nullptr) return LRA_ERR_INVALID_ARG;
   size_t cnt = 0;
   double scale = 1.0;
@@ -219,12 +223,13 @@ lra_status lra_precondition(lra_multiplier* out, int32_t kind, int64_t n, int32_
         if (sg != 1 && sg != -1) return LRA_ERR_INVALID_ARG;
       }
     }
-    return lra::make_bidiag(out, n, param, idx, signs);
+    return lra::make_bidiag(out, side, n, param, idx, signs);
   } else {
     return LRA_ERR_INVALID_ARG;
   }
   lra_multiplier m = new lra_multiplier_s;
   m->kind = kind;
+  m->side = side;
   m->n = n;
   m->param = param;
   m->scale = scale;

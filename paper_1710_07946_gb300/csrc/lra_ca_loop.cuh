@@ -90,13 +90,13 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
     const int rn = (int)max((int64_t)0, min((int64_t)A.chunk_m, P.m - r0));
     for (int it = tid; it < rn * k; it += nt) {
       int c = it / k, a = it - c * k;
-      A.C[(r0 + c) * k + a] = wp_entry(P, r0 + c, S.Js[a]);
+      A.C[(r0 + c) * k + a] = c_entry(P, r0 + c, S.Js[a]);
     }
     const int64_t c0 = (int64_t)grp.rank() * A.chunk_n;
     const int cn = (int)max((int64_t)0, min((int64_t)A.chunk_n, P.n - c0));
     for (int it = tid; it < k * cn; it += nt) {
       int a = it / cn, c = it - a * cn;
-      A.R[(int64_t)a * P.n + c0 + c] = w_entry(P, S.Is[a], c0 + c);
+      A.R[(int64_t)a * P.n + c0 + c] = r_entry(P, S.Is[a], c0 + c);
     }
   }
   if (lead) {

@@ -212,12 +212,12 @@ __global__ void __launch_bounds__(NTB, MINB) cynical_batched_kernel(CynArgs B) {
     for (int64_t it = tid; it < nr * r; it += nt) {
       const int64_t i = it / r;
       const int a = (int)(it - i * r);
-      Cb[it] = wp_entry(A.P, i, Jb[a]);
+      Cb[it] = c_entry(A.P, i, Jb[a]);
     }
     for (int64_t it = tid; it < (int64_t)r * nc; it += nt) {
       const int a = (int)(it / nc);
       const int64_t c = it - (int64_t)a * nc;
-      Rb[it] = w_entry(A.P, Ib[a], c);
+      Rb[it] = r_entry(A.P, Ib[a], c);
     }
     if (tid == 0) {
       int s = max(st, st2);

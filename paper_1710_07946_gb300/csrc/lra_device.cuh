@@ -38,7 +38,8 @@ struct DevProblem {
   double ell;
   // multiplier
   int32_t mkind, depth, nnz;
-  int64_t s;                 // ARHT block size n / 2^d
+  int32_t mside;             // 0: W' = W M (right, M n x n); 1: W' = M^T W (left, M m x m)
+  int64_t s;                 // ARHT block size (n or m) / 2^d
   const int32_t* perm;       // ARHT permutation, or sparse rows (n*nnz)
   const int8_t* sign;        // ARHT diagonal, or sparse signs (n*nnz)
   const int32_t* bval;       // bidiagonal products: integer weights (n*nnz, nnz = min(2^q, n) slots)
@@ -71,19 +72,27 @@ __device__ __forceinline__ double w_entry(const DevProblem& P, int64_t i, int64_
   return exp(-(r2 / (2.0 * P.ell * P.ell)));
 }
 
-// w'_ij = (W M)_ij.  ARHT: column j of M has 2^d entries, at rows a*s + t for
-// perm[j] = b*s + t, of sign D_{a s + t} (-1)^{popcount(a & b)}; the terms are
-// added in ascending a and the sum is scaled once.  Sparse: nnz signed terms in
-// ascending stored order, scaled once.  The terms are fetched TERMS at a time
-// before they are added (same order of additions), so their loads overlap.
+// w'_ij of the pre-processed input.  Right multiplier: W' = W M, w'_ij =
+// sum over the nonzeros M_rj of M_rj w_ir (column j of M combines entries of
+// row i).  Left multiplier: W' = M^T W, w'_ij = sum over the nonzeros M_ri of
+// M_ri w_rj (column i of M combines entries of column j).  In both cases the
+// terms of one column mc of M are taken in the same order.  ARHT: column mc of
+// M has 2^d entries, at rows a*s + t for perm[mc] = b*s + t, of sign
+// D_{a s + t} (-1)^{popcount(a & b)}; the terms are added in ascending a and
+// the sum is scaled once.  Sparse: nnz signed terms in ascending stored order,
+// scaled once.  The terms are fetched TERMS at a time before they are added
+// (same order of additions), so their loads overlap.
 __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64_t j) {
   if (P.mkind == LRA_MULT_NONE) return w_entry(P, i, j);
+  const bool left = P.mside != 0;
+  const int64_t mc = left ? i : j;                  // the column of M that combines the terms
+  auto term = [&](int64_t r) -> double { return left ? w_entry(P, r, j) : w_entry(P, i, r); };
   double acc = 0.0;
   if (P.mkind == LRA_MULT_BIDIAG) {
     // product of bidiagonal factors: up to min(2^q, n) integer-weighted terms
     // in ascending rows (value 0 = unused slot), each fma(value, w, sum)
-    const int32_t* rows = P.perm + j * P.nnz;
-    const int32_t* vs = P.bval + j * P.nnz;
+    const int32_t* rows = P.perm + mc * P.nnz;
+    const int32_t* vs = P.bval + mc * P.nnz;
     for (int t0 = 0; t0 < P.nnz; t0 += TERMS) {
       double v[TERMS];
       int c[TERMS];
@@ -92,7 +101,7 @@ __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64
         c[e] = 0;
         if (t0 + e < P.nnz) {
           c[e] = __ldg(vs + t0 + e);
-          if (c[e] != 0) v[e] = w_entry(P, i, __ldg(rows + t0 + e));
+          if (c[e] != 0) v[e] = term(__ldg(rows + t0 + e));
         }
       }
 #pragma unroll
@@ -102,7 +111,7 @@ __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64
     return acc * P.mscale;
   }
   if (P.mkind == LRA_MULT_ARHT) {
-    const int64_t pj = __ldg(P.perm + j);
+    const int64_t pj = __ldg(P.perm + mc);
     const int64_t b = pj / P.s, t = pj - b * P.s;
     const int nt = 1 << P.depth;
     for (int a0 = 0; a0 < nt; a0 += TERMS) {
@@ -112,7 +121,7 @@ __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64
         const int a = a0 + e;
         if (a < nt) {
           const int64_t r = (int64_t)a * P.s + t;
-          const double w = w_entry(P, i, r);
+          const double w = term(r);
           v[e] = (__ldg(P.sign + r) < 0) ? -w : w;       // == w * (double)sign, exactly
         }
       }
@@ -125,15 +134,15 @@ __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64
       }
     }
   } else {
-    const int32_t* rows = P.perm + j * P.nnz;
-    const int8_t* sg = P.sign + j * P.nnz;
+    const int32_t* rows = P.perm + mc * P.nnz;
+    const int8_t* sg = P.sign + mc * P.nnz;
     for (int t0 = 0; t0 < P.nnz; t0 += TERMS) {
       double v[TERMS];
       bool neg[TERMS];
 #pragma unroll
       for (int e = 0; e < TERMS; ++e) {
         if (t0 + e < P.nnz) {
-          v[e] = w_entry(P, i, __ldg(rows + t0 + e));
+          v[e] = term(__ldg(rows + t0 + e));
           neg[e] = __ldg(sg + t0 + e) < 0;
         }
       }
@@ -144,6 +153,17 @@ __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64
     }
   }
   return acc * P.mscale;
+}
+
+// Entries of the CUR factors of W from a generator (I, J) of the pre-processed
+// W' (the back-transform of a pre-processed CUR): with a right multiplier
+// C = W'[:, J] and R = W[I, :]; with a left one the roles swap, C = W[:, J] and
+// R = W'[I, :].  The nucleus is pinv(W'[I, J]) in both cases.
+__device__ __forceinline__ double c_entry(const DevProblem& P, int64_t i, int64_t j) {
+  return P.mside ? w_entry(P, i, j) : wp_entry(P, i, j);
+}
+__device__ __forceinline__ double r_entry(const DevProblem& P, int64_t i, int64_t j) {
+  return P.mside ? wp_entry(P, i, j) : w_entry(P, i, j);
 }
 
 // ---------------------------------------------------------------------------

@@ -12,6 +12,7 @@
 
 struct lra_multiplier_s {
   int32_t kind;
+  int32_t side;         // LRA_SIDE_RIGHT (W' = W M) or LRA_SIDE_LEFT (W' = M^T W)
   int64_t n;
   int32_t param;        // depth d (ARHT), nnz (sparse) or the number of factors q (bidiagonal)
   int32_t width;        // bidiagonal: slots per column, min(2^q, n)
@@ -98,6 +99,7 @@ inline bool stages_valid(const lra_ca_params* par) {
 // without the bidiagonal-product multiplier.
 inline bool mixed_supported(const DevProblem& P) {
   if (P.mkind == LRA_MULT_BIDIAG) return false;       // no FP32 bounds for integer-weighted sums
+  if (P.mside != 0) return false;                     // FP32 gathers are written for right multipliers
   return P.src == LRA_DENSE || (P.src == LRA_KERNEL_LAPLACE && P.dtype == LRA_F64);
 }
 

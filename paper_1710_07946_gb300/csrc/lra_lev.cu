@@ -363,12 +363,12 @@ __global__ void __launch_bounds__(NT, 1) lev_batched_kernel(LevArgs B) {
     for (int64_t e = tid; e < nr * kJ; e += nt) {
       const int64_t i = e / kJ;
       const int a = (int)(e - i * kJ);
-      Cb[e] = wp_entry(P, i, s_J[a]);
+      Cb[e] = c_entry(P, i, s_J[a]);
     }
     for (int64_t e = tid; e < (int64_t)kI * nc; e += nt) {
       const int a = (int)(e / nc);
       const int64_t c = e - (int64_t)a * nc;
-      Rb[e] = w_entry(P, s_I[a], c);
+      Rb[e] = r_entry(P, s_I[a], c);
     }
     const bool tr = kI > kJ;
     for (int e = tid; e < kI * kJ; e += nt) {

@@ -116,6 +116,7 @@ lra_status lra_multiplier_apply(const lra_problem* prob, lra_multiplier mult, do
   if (st != LRA_OK) return st;
   if (Wp == nullptr || ldwp < P.n || P.m < 1 || P.n < 1) return LRA_ERR_INVALID_ARG;
   if (mult != nullptr && mult->kind == LRA_MULT_BIDIAG && mult->d_dense != nullptr && P.src == LRA_DENSE &&
+      P.mside == 0 &&
       (P.m + 31) / 32 <= 65535 && (P.n + 63) / 64 <= INT32_MAX) {
     // every column of M can be full: the register-tiled product
     const dim3 grid((unsigned)((P.n + 63) / 64), (unsigned)((P.m + 31) / 32));

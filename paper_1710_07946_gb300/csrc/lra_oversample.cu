@@ -232,12 +232,12 @@ __device__ void ov_block_finish(const OvArgs& B, int b, const CaArgs& A, int64_t
   for (int64_t it = tid; it < nr * l; it += nt) {
     const int64_t i = it / l;
     const int a = (int)(it - i * l);
-    Cb[it] = wp_entry(A.P, i, Jb[a]);
+    Cb[it] = c_entry(A.P, i, Jb[a]);
   }
   for (int64_t it = tid; it < (int64_t)k * nc; it += nt) {
     const int a = (int)(it / nc);
     const int64_t c = it - (int64_t)a * nc;
-    Rb[it] = w_entry(A.P, Ib[a], c);
+    Rb[it] = r_entry(A.P, Ib[a], c);
   }
   for (int it = tid; it < k * l; it += nt) {
     const int a = it / l, c = it - a * l;

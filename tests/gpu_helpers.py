@@ -16,12 +16,14 @@ def to_device(p: li.Problem):
         prob = lra.Problem.kernel(kind, torch.from_numpy(p.X).to(dev), torch.from_numpy(p.Y).to(dev), p.ell,
                                   entries=p.entries)
     mult = None
+    side = "left" if p.mside else "right"
+    order = p.m if p.mside else p.n
     if p.mkind == li.MULT_ARHT:
-        mult = lra.lra_precondition("arht", p.n, p.depth, p.perm, p.dsign)
+        mult = lra.lra_precondition("arht", order, p.depth, p.perm, p.dsign, side=side)
     elif p.mkind == li.MULT_SPARSE:
-        mult = lra.lra_precondition("sparse", p.n, p.nnz, p.srow, p.ssign)
+        mult = lra.lra_precondition("sparse", order, p.nnz, p.srow, p.ssign, side=side)
     elif p.mkind == li.MULT_BIDIAG:
-        mult = lra.lra_precondition("bidiag", p.n, p.depth, p.perm, p.dsign)
+        mult = lra.lra_precondition("bidiag", order, p.depth, p.perm, p.dsign, side=side)
     return prob, mult
 
 

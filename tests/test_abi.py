@@ -41,14 +41,19 @@ def test_host_validation_without_gpu():
     """Argument checks run on the host before any CUDA call."""
     from paper_1710_07946_gb300 import build
     L = ctypes.CDLL(build.build())
+    L.lra_precondition.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                   ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
+    L.lra_precondition.restype = ctypes.c_int
     h = ctypes.c_void_p()
     # bad kind, bad depth, n not a multiple of 2^d
-    assert L.lra_precondition(ctypes.byref(h), 7, 8, 1, None, None) == 1
+    assert L.lra_precondition(ctypes.byref(h), 7, 0, 8, 1, None, None) == 1
     import numpy as np
     perm = np.arange(6, dtype=np.int32); sg = np.ones(6, dtype=np.int8)
-    assert L.lra_precondition(ctypes.byref(h), 1, 6, 2, perm.ctypes.data, sg.ctypes.data) == 1
+    assert L.lra_precondition(ctypes.byref(h), 1, 0, 6, 2, perm.ctypes.data, sg.ctypes.data) == 1
+    # bad side
+    assert L.lra_precondition(ctypes.byref(h), 1, 2, 6, 1, perm.ctypes.data, sg.ctypes.data) == 1
     bad = perm.copy(); bad[0] = 1
-    assert L.lra_precondition(ctypes.byref(h), 1, 6, 1, bad.ctypes.data, sg.ctypes.data) == 1
+    assert L.lra_precondition(ctypes.byref(h), 1, 0, 6, 1, bad.ctypes.data, sg.ctypes.data) == 1
     # unsorted sparse rows
     rows = np.array([[1, 0]], dtype=np.int32).repeat(3, 0); s2 = np.ones((3, 2), np.int8)
-    assert L.lra_precondition(ctypes.byref(h), 2, 3, 2, rows.ctypes.data, s2.ctypes.data) == 1
+    assert L.lra_precondition(ctypes.byref(h), 2, 0, 3, 2, rows.ctypes.data, s2.ctypes.data) == 1

@@ -49,6 +49,41 @@ def test_dense_multi_cta_ragged(m, n, k):
     assert_parity(o, g)
 
 
+@pytest.mark.parametrize("mult,arg", [("arht", 2), ("arht", 3), ("sparse", 4), ("bidiag", 3)])
+@pytest.mark.parametrize("m,n", [(3000, 700), (1024, 96)])
+def test_left_multipliers_tall_inputs(mult, arg, m, n):
+    """m > n: the multiplier pre-multiplies (Remark re2orddmn), W' = M^T W with M
+    m x m; C = W[:, J], R = W'[I, :].  Multi-CTA grid (3000 x 700) and one CTA
+    (1024 x 96), FP32 spiky and FP64 factor-Gaussian inputs."""
+    if m == 3000:
+        p = li.factor_gaussian(m, 20, 1e-4, seed=m + arg)
+        p.W = np.ascontiguousarray(p.W[:, :n])
+        p.n = n
+    else:
+        p = li.dense_spiky(m, r=12, seed=8)
+        p.W = np.ascontiguousarray(p.W[:, :n])
+        p.n = n
+    if mult == "arht":
+        li.with_arht(p, arg, 31, side="left")
+    elif mult == "bidiag":
+        li.with_bidiag(p, arg, 31, side="left")
+    else:
+        li.with_sparse(p, arg, 31, side="left")
+    I0 = li.initial_rows(m, 16, 5)
+    o, g = run_both(p, 16, 4, I0)
+    assert_parity(o, g)
+
+
+def test_left_multiplier_laplace_entries():
+    """A tall Laplace block (targets 4000, sources 600) with a left ARHT: the
+    pre-processed rows combine kernel entries evaluated on the fly."""
+    p = li.laplace_clusters(4000, 600, seed=3)
+    li.with_arht(p, 3, 12, side="left")
+    I0 = li.initial_rows(4000, 24, 2)
+    o, g = run_both(p, 24, 3, I0)
+    assert_parity(o, g)
+
+
 @pytest.mark.parametrize("mult,arg", [("arht", 1), ("arht", 2), ("arht", 3), ("sparse", 4), ("bidiag", 1), ("bidiag", 3), ("bidiag", 5)])
 def test_float32_with_multipliers(mult, arg):
     p = li.dense_spiky(1024, r=16, seed=3)

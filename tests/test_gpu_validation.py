@@ -162,3 +162,21 @@ def test_gauss_apply_flags_out_of_range_pivots():
         assert np.isnan(v[1]).all() and np.isnan(v[2]).all() and np.isfinite(v[0]).all(), key
     dl = g["dell"].cpu().numpy()
     assert np.isnan(dl[1]) and np.isnan(dl[2]) and np.isfinite(dl[0])
+
+
+def test_left_multiplier_order_must_match_rows():
+    """A left multiplier is m x m: a handle of order n (or a right one of order m)
+    is refused before anything is launched."""
+    import paper_1710_07946_gb300 as lra
+    p = li.dense_lowrank(64, 32, r=3, seed=6)
+    prob, _ = to_device(p)
+    q = li.Problem(li.SRC_DENSE, 64, 32, W=np.zeros((64, 32)))
+    li.with_arht(q, 2, 1, side="right")                       # order 32
+    wrong = lra.lra_precondition("arht", 32, 2, q.perm, q.dsign, side="left")
+    I0 = torch.arange(3, dtype=torch.int32, device="cuda")
+    assert "INVALID_ARG" in str(_err(lra.lra_ca_run, prob, I0, 3, 2, multiplier=wrong))
+    li.with_arht(q, 2, 1, side="left")                        # order 64
+    right64 = lra.lra_precondition("arht", 64, 2, q.perm, q.dsign, side="right")
+    assert "INVALID_ARG" in str(_err(lra.lra_ca_run, prob, I0, 3, 2, multiplier=right64))
+    with pytest.raises(KeyError):
+        lra.lra_precondition("arht", 64, 2, q.perm, q.dsign, side="up")

@@ -181,6 +181,55 @@ def test_exact_recovery_rank_r(seed, mult):
     np.testing.assert_array_equal(o["R"], W[o["I"], :])
 
 
+@pytest.mark.parametrize("seed", range(3))
+@pytest.mark.parametrize("mult", ["arht", "sparse", "bidiag"])
+def test_exact_recovery_rank_r_left_multiplier(seed, mult):
+    """Remark re2orddmn (m > n: pre-multiply): with W' = M^T W the CUR of W from
+    the generator (I, J) of W' is W[:, J] pinv(W'[I, J]) W'[I, :] (the
+    right-multiplier back-transform applied to W^T), exact for rank-r W with a
+    nonsingular core; C and R are the submatrices they claim to be, with M built
+    densely from its definition."""
+    p = li.dense_lowrank(160, 96, r=5, noise=0.0, seed=seed)
+    if mult == "arht":
+        li.with_arht(p, 3, seed + 60, side="left")
+    elif mult == "sparse":
+        li.with_sparse(p, 4, seed + 60, side="left")
+    else:
+        li.with_bidiag(p, 3, seed + 60, side="left")
+    o = oracle.ca_run(p, 5, 3, li.initial_rows(160, 5, seed + 7))
+    W = p.W
+    err = np.linalg.norm(W - o["C"] @ o["U"] @ o["R"]) / np.linalg.norm(W)
+    assert err < 1e-11, err
+    assert o["rank"] == 5
+    M = oracle.multiplier_dense(p)
+    assert M.shape == (160, 160)
+    MtW = M.T @ W
+    np.testing.assert_array_equal(o["C"], W[:, o["J"]])
+    np.testing.assert_allclose(o["R"], MtW[o["I"], :], atol=1e-14)
+    # the nucleus is the (pseudo-)inverse of the pre-processed core
+    np.testing.assert_allclose(o["U"] @ MtW[np.ix_(o["I"], o["J"])], np.eye(5), atol=1e-9)
+
+
+@pytest.mark.parametrize("mult", ["arht2", "sparse", "bidiag3"])
+def test_left_multiplier_gathers_equal_dense_product(mult):
+    """With a left multiplier the gathers are rows / columns of M^T W, M m x m
+    assembled from its definition (the transpose of the right-side case)."""
+    g = np.random.default_rng(14)
+    W = g.standard_normal((48, 20))
+    p = li.Problem(li.SRC_DENSE, 48, 20, W=W)
+    if mult.startswith("arht"):
+        li.with_arht(p, int(mult[-1]), 9, side="left")
+    elif mult.startswith("bidiag"):
+        li.with_bidiag(p, int(mult[-1]), 9, side="left")
+    else:
+        li.with_sparse(p, 4, 9, side="left")
+    MtW = oracle.multiplier_dense(p).T @ W
+    I = np.array([3, 0, 47, 17], dtype=np.int32)
+    J = np.array([19, 5, 6, 0], dtype=np.int32)
+    np.testing.assert_allclose(oracle.gather_rows(p, I), MtW[I], atol=1e-14)
+    np.testing.assert_allclose(oracle.gather_cols(p, J), MtW[:, J], atol=1e-14)
+
+
 @pytest.mark.parametrize("seed", range(5))
 def test_volume_non_decreasing_across_steps(seed):
     """C-A steps warm-started from the current sets never decrease the volume
