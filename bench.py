@@ -165,16 +165,52 @@ class FmmWorkload:
         sizes = "-".join(map(str, stages)) if stages else str(k)
         self.name = f"{self.base}_k{sizes}_tol{tol:.0e}".replace("e-0", "e-") + ("_f32entries" if entries == "f32" else "")
 
-    def host(self, rank):
-        p, blocks, lev = li.fmm_blocks(npts=self.npts, nblocks=self.nblocks, seed=rank)
-        I0 = li.block_initial_rows(blocks, self.k, 100 + rank)
-        Q, S = li.block_sample_positions(blocks, self.q, self.s, 200 + rank)
+    def problem(self, seed):
+        """One batch of the recipe: the octree's block pairs over npts points with
+        their initial rows and residual sample positions."""
+        p, blocks, lev = li.fmm_blocks(npts=self.npts, nblocks=self.nblocks, seed=seed)
+        I0 = li.block_initial_rows(blocks, self.k, 100 + seed)
+        Q, S = li.block_sample_positions(blocks, self.q, self.s, 200 + seed)
         self.levels = lev
         return dict(p=p, blocks=blocks, I0=I0, Q=Q, S=S)
 
+    def job_list(self, world):
+        """The job's one block list for ``world`` GPUs: ``world`` batches of the
+        recipe (seeds 0 .. world-1) whose point sets are concatenated, so that
+        every block is a submatrix of one kernel matrix over all the points (the
+        block rows and columns of batch p are offset by p * npts)."""
+        parts = [self.problem(seed) for seed in range(world)]
+        if world == 1:
+            return parts[0]
+        X = np.concatenate([h["p"].X for h in parts])
+        blocks = np.concatenate([h["blocks"] + np.array([1, 0, 1, 0]) * (i * self.npts)
+                                 for i, h in enumerate(parts)])
+        p = li.Problem(li.SRC_LAPLACE, len(X), len(X), X=X, Y=X)
+        cat = lambda key: np.concatenate([h[key] for h in parts])
+        return dict(p=p, blocks=blocks, I0=cat("I0"), Q=cat("Q"), S=cat("S"))
+
+    def host(self, rank):
+        """This rank's share.  One GPU: the recipe's batch.  Several (``world``
+        set by the launcher): the LPT share (rows x columns x k) of the job's
+        one block list, or with ``shard = "replicas"`` an independent batch of
+        its own (seed = rank)."""
+        world = getattr(self, "world", 1)
+        if world == 1 or getattr(self, "shard", "lpt") == "replicas":
+            return self.problem(rank)
+        from paper_1710_07946_gb300 import shard
+        full = self.job_list(world)
+        mine = shard.lpt_partition(shard.block_costs(full["blocks"], self.k), world)[rank]
+        h = dict(full, blocks=full["blocks"][mine], I0=full["I0"][mine], Q=full["Q"][mine], S=full["S"][mine])
+        h["share"] = mine
+        return h
+
     def config(self, h):
         b = h["blocks"]
-        return {"workload": self.name, "points": self.npts, "blocks": int(len(b)),
+        world = getattr(self, "world", 1)
+        shard = ("one GPU" if world == 1 else
+                 f"{world} independent batches of the recipe per job" if getattr(self, "shard", "lpt") == "replicas"
+                 else f"LPT share (rows x cols x k) of one {world} x {self.nblocks}-block list")
+        return {"workload": self.name, "points": self.npts, "blocks": int(len(b)), "sharding": shard,
                 "block_rows_min_median_max": [int(b[:, 1].min()), int(np.median(b[:, 1])), int(b[:, 1].max())],
                 "kernel": f"Laplace 1/|x-y|, on the fly, entries {self.entries.upper()}",
                 "pivots_nucleus": "FP64", "residual_against": "FP64 entries", "k_max": self.k,
@@ -1669,6 +1705,7 @@ def run_lib(args, wl):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
 
+    wl.world, wl.shard = world, args.shard
     h = wl.host(rank)
     d = wl.device(h, dev)
     if "pivots" in d:
@@ -1804,7 +1841,9 @@ def run_lib(args, wl):
                                                            "DFMA loop measured 1.2)")
         mode, precision = wl.precision() if hasattr(wl, "precision") else ("fp64", None)
         cfg = dict(wl.config(h), l2="flushed before every step (256 MiB write, untimed)",
-                   parallelism=f"{world} independent problem(s), one per GPU", mode=mode,
+                   parallelism=(f"{world} GPU(s), " + ("LPT shares of one block list" if args.shard == "lpt" and
+                                                            world > 1 and isinstance(wl, FmmWorkload) else
+                                                            "one independent problem per GPU")), mode=mode,
                    graph_ms_per_step=graph_ms, wall_s=t_wall)
         if precision:
             cfg["precision"] = precision
@@ -1856,6 +1895,8 @@ def main():
     ap.add_argument("--impl", default="lib", choices=["lib", "reference"])
     ap.add_argument("--workload", default="fmm", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--shard", default="lpt", choices=["lpt", "replicas"],
+                    help="batched workloads on several GPUs: LPT shares of one block list, or a replica per GPU")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--ref-budget", type=float, default=90.0, help="seconds of oracle time for --impl reference")
     args = ap.parse_args()

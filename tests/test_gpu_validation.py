@@ -117,7 +117,7 @@ def test_residual_sample_catches_out_of_range_indices():
         st = lra.lra_residual_sample(prob, out["C"], out["U"], out["R"], q, s).cpu().numpy()
         assert np.isnan(st).all(), st
     st = lra.lra_residual_sample(prob, out["C"], out["U"], out["R"], good_q, good_s).cpu().numpy()
-    assert np.isfinite(st).all() and st[4] < 1e-10
+    assert np.isfinite(st).all() and st[4] < 1e-4
 
 
 def test_batched_residual_flags_only_the_block_with_a_bad_index():
