@@ -32,7 +32,7 @@ from typing import Optional
 import numpy as np
 
 SRC_DENSE, SRC_LAPLACE, SRC_GAUSSIAN = 0, 1, 2
-MULT_NONE, MULT_ARHT, MULT_SPARSE, MULT_BIDIAG = 0, 1, 2, 3
+MULT_NONE, MULT_ARHT, MULT_SPARSE, MULT_BIDIAG, MULT_ARFT = 0, 1, 2, 3, 4
 
 
 @dataclass
@@ -56,6 +56,7 @@ class Problem:
     ssign: Optional[np.ndarray] = None      # (n, nnz) int8, +-1
     entries: str = "f64"                    # kernel: entries evaluated in "f64" or "f32"
     mside: int = 0                          # multiplier side: 0 right (W M, M n x n), 1 left (M^T W, M m x m)
+    dcplx: Optional[np.ndarray] = None      # ARFT diagonal D: (n, 2) float64 (real, imaginary), |D_r| = 1
     meta: dict = field(default_factory=dict)
 
     @property
@@ -139,6 +140,26 @@ def with_arht(p: Problem, depth: int, seed: int, side: str = "right") -> Problem
     order, p.mside = _side(p, side)
     perm, dsign = arht_descriptor(order, depth, seed)
     p.mkind, p.depth, p.perm, p.dsign = MULT_ARHT, depth, perm, dsign
+    return p
+
+
+def arft_descriptor(n: int, depth: int, seed: int):
+    """Random permutation P and diagonal D uniform on the complex unit circle for
+    D Omega_{n,d} P: D_r = exp(2 pi sqrt(-1) u_r), u_r uniform in [0, 1), stored
+    as (cos, sin) pairs."""
+    if depth < 1 or n % (1 << depth) != 0:
+        raise ValueError("n must be a multiple of 2^depth, depth >= 1")
+    g = rng(seed)
+    perm = g.permutation(n).astype(np.int32)
+    ang = 2.0 * np.pi * g.random(n)
+    return perm, np.ascontiguousarray(np.stack([np.cos(ang), np.sin(ang)], axis=1))
+
+
+def with_arft(p: Problem, depth: int, seed: int) -> Problem:
+    """Right abridged randomized Fourier multiplier in real form: W' = W [Re M, Im M]
+    (2n columns), M = 2^{-d/2} D Omega_{n,d} P."""
+    perm, dc = arft_descriptor(p.n, depth, seed)
+    p.mkind, p.depth, p.perm, p.dcplx, p.mside = MULT_ARFT, depth, perm, dc, 0
     return p
 
 

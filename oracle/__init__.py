@@ -26,7 +26,8 @@ class _Problem(ct.Structure):
         ("ell", ct.c_double), ("mkind", ct.c_int32), ("depth", ct.c_int32),
         ("perm", ct.c_void_p), ("dsign", ct.c_void_p), ("nnz", ct.c_int32),
         ("srow", ct.c_void_p), ("ssign", ct.c_void_p), ("brow", ct.c_void_p), ("bval", ct.c_void_p),
-        ("mside", ct.c_int32),
+        ("mside", ct.c_int32), ("frow", ct.c_void_p), ("fwt", ct.c_void_p), ("dre", ct.c_void_p),
+        ("dim", ct.c_void_p),
     ]
 
 
@@ -51,6 +52,8 @@ def lib():
         L.orc_ca_run_adaptive.argtypes = [P, vp, i32, i32, i32, vp, f64, i32, f64, vp, vp, vp, vp, vp, vp, vp]
         L.orc_ca_run_adaptive.restype = ct.c_int
         L.orc_bidiag_columns.argtypes = [i64, i32, vp, vp, vp, vp]
+        L.orc_fourier_columns.argtypes = [i64, i32, vp, vp, vp, vp, vp]
+        L.orc_fourier_abridged.argtypes = [i64, i32, vp, vp]
         L.orc_nucleus_rect.argtypes = [vp, i32, i32, f64, vp]
         L.orc_residual_sample_rect.argtypes = [P, vp, vp, vp, i32, i32, vp, i32, vp, i32, vp, vp]
         L.orc_nucleus_rect.restype = i32
@@ -135,6 +138,16 @@ class _Marshalled:
             self.keep += [perms, sg, brow, bval]
             s.depth, s.perm, s.dsign = int(p.depth), perms.ctypes.data, sg.ctypes.data
             s.brow, s.bval = brow.ctypes.data, bval.ctypes.data
+        elif p.mkind == 4:
+            if s.mside:
+                raise ValueError("the abridged Fourier multiplier is a right multiplier")
+            perm = np.ascontiguousarray(p.perm, dtype=np.int32)
+            dre = np.ascontiguousarray(p.dcplx[:, 0], dtype=np.float64)
+            dim = np.ascontiguousarray(p.dcplx[:, 1], dtype=np.float64)
+            frow, fwt = fourier_columns(p.n, p.depth, perm, dre, dim)
+            self.keep += [perm, dre, dim, frow, fwt]
+            s.depth, s.perm = int(p.depth), perm.ctypes.data
+            s.dre, s.dim, s.frow, s.fwt = dre.ctypes.data, dim.ctypes.data, frow.ctypes.data, fwt.ctypes.data
         self.s = s
 
     @property
@@ -143,11 +156,17 @@ class _Marshalled:
 
 
 # ------------------------------------------------------------------ strips
+def cols(p):
+    """Columns of the pre-processed W': 2n for the real-form abridged Fourier
+    multiplier, n otherwise."""
+    return 2 * p.n if p.mkind == 4 else p.n
+
+
 def gather_rows(p, I):
-    """W'[I,:] with W' = W M (k x n); multiplier columns as in entry_wp()."""
+    """W'[I,:] with W' = W M (k x cols(p)); multiplier columns as in entry_wp()."""
     I = np.ascontiguousarray(I, dtype=np.int32)
     mp = _Marshalled(p)
-    out = np.empty((len(I), p.n))
+    out = np.empty((len(I), cols(p)))
     lib().orc_gather_rows(mp.ref, _ptr(I), len(I), _ptr(out))
     return out
 
@@ -366,6 +385,27 @@ def cynical(p, kind, r, q, K, L, I0s, sweeps=3, h=1.01, max_swaps=1000, rank_tol
                 status=int(info[3]))
 
 
+def fourier_columns(n, d, perm, dre, dim):
+    """Columns of the real form [Re M, Im M] of M = D Omega_{n,d} P before the
+    scale 2^(-d/2): (2n, 2^d) rows (ascending) and real weights."""
+    w = 1 << int(d)
+    rows = np.zeros((2 * n, w), dtype=np.int32)
+    wts = np.zeros((2 * n, w), dtype=np.float64)
+    lib().orc_fourier_columns(int(n), int(d), _ptr(np.ascontiguousarray(perm, dtype=np.int32)),
+                              _ptr(np.ascontiguousarray(dre, dtype=np.float64)),
+                              _ptr(np.ascontiguousarray(dim, dtype=np.float64)), _ptr(rows), _ptr(wts))
+    return rows, wts
+
+
+def fourier_abridged(n, d):
+    """Dense complex Omega_{n,d} from the decimation-in-frequency recursion eqfd
+    with Omega_s = I_s (n = 2^d s)."""
+    re = np.empty((n, n))
+    im = np.empty((n, n))
+    lib().orc_fourier_abridged(int(n), int(d), _ptr(re), _ptr(im))
+    return re + 1j * im
+
+
 def bidiag_columns(n, q, perms, signs):
     """Columns of the product of q quasi-Gaussian factors (I + D_i S) P_i:
     (n, min(2^q, n)) rows and integer values (0 = unused slot), ascending rows."""
@@ -486,7 +526,7 @@ def multiplier_dense(p):
     a left one), assembled from its definition."""
     mp = _Marshalled(p)
     N = p.m if getattr(p, "mside", 0) else p.n
-    M = np.empty((N, N))
+    M = np.empty((N, cols(p) if p.mkind == 4 else N))
     lib().orc_multiplier_dense(mp.ref, _ptr(M))
     return M
 

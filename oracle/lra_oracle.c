@@ -45,7 +45,7 @@
 /* ------------------------------------------------------------------ */
 enum { ORC_DENSE = 0, ORC_LAPLACE = 1, ORC_GAUSSIAN = 2 };
 enum { ORC_F64 = 0, ORC_F32 = 1 };
-enum { ORC_MULT_NONE = 0, ORC_MULT_ARHT = 1, ORC_MULT_SPARSE = 2, ORC_MULT_BIDIAG = 3 };
+enum { ORC_MULT_NONE = 0, ORC_MULT_ARHT = 1, ORC_MULT_SPARSE = 2, ORC_MULT_BIDIAG = 3, ORC_MULT_ARFT = 4 };
 
 typedef struct {
   int32_t src;          /* ORC_DENSE / ORC_LAPLACE / ORC_GAUSSIAN            */
@@ -72,7 +72,23 @@ typedef struct {
   /* side of the multiplier (Remark re2orddmn): 0 = right, W' = W M with M
    * n x n; 1 = left, W' = M^T W with M m x m (for m > n) */
   int32_t mside;
+  /* abridged randomized Fourier multiplier in real form (mkind ORC_MULT_ARFT,
+   * right side only, depth = d): W' = W [Re M, Im M] with M = D Omega_{n,d} P,
+   * so W' has 2n columns.  The columns of [Re M, Im M] before the scale
+   * 2^(-d/2), expanded by orc_fourier_columns: 2^d slots each (ascending rows,
+   * real weights). */
+  const int32_t* frow;
+  const double* fwt;
+  const double* dre;    /* ARFT diagonal D: real and imaginary parts (n each) */
+  const double* dim;
 } orc_problem;
+
+/* pi to double precision, for the roots of unity of the Fourier multiplier */
+#define ORC_PI 3.14159265358979323846
+
+/* Columns of W' (the pre-processed matrix): 2n for the real-form abridged
+ * Fourier multiplier, n otherwise. */
+static int64_t orc_cols(const orc_problem* p) { return p->mkind == ORC_MULT_ARFT ? 2 * p->n : p->n; }
 
 /* Entry w_ij of the input W (no multiplier).  Kernel entries follow the
  * closed forms: Laplace 1/|x-y|, Gaussian exp(-|x-y|^2 / (2 l^2)). */
@@ -175,6 +191,14 @@ static double entry_wp(const orc_problem* p, int64_t i, int64_t j) {
     }
     return acc * arht_scale(p->depth);
   }
+  if (p->mkind == ORC_MULT_ARFT) {
+    /* the 2^d real weights of column j of [Re M, Im M] in ascending rows, each an
+     * fma, then the scale 2^(-d/2) */
+    int64_t w = 1LL << p->depth;
+    double acc = 0.0;
+    for (int64_t t = 0; t < w; ++t) acc = fma(p->fwt[j * w + t], entry_w(p, i, p->frow[j * w + t]), acc);
+    return acc * arht_scale(p->depth);
+  }
   if (p->mkind == ORC_MULT_BIDIAG) {
     /* nonzero slots in ascending row order, each an fma with its integer weight */
     int64_t w = (1LL << p->depth) < N ? (1LL << p->depth) : N;
@@ -196,10 +220,11 @@ static double entry_wp(const orc_problem* p, int64_t i, int64_t j) {
   return acc * (1.0 / sqrt((double)p->nnz));
 }
 
-/* Row strip W'[I,:] (k x n, row-major). */
+/* Row strip W'[I,:] (k x n', n' = orc_cols(p), row-major). */
 void orc_gather_rows(const orc_problem* p, const int32_t* I, int32_t k, double* out) {
+  int64_t nc = orc_cols(p);
   for (int32_t a = 0; a < k; ++a)
-    for (int64_t j = 0; j < p->n; ++j) out[(int64_t)a * p->n + j] = entry_wp(p, I[a], j);
+    for (int64_t j = 0; j < nc; ++j) out[(int64_t)a * nc + j] = entry_wp(p, I[a], j);
 }
 
 /* Column strip W'[:,J], stored transposed: out[a*m + i] = W'[i, J[a]]. */
@@ -612,7 +637,7 @@ int orc_ca_run(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I
 int orc_ca_run_warm(const orc_problem* p, int32_t k, int32_t sweeps, const int32_t* I0, const int32_t* J0,
                     double h, int32_t max_swaps, double rank_tol, int32_t* I, int32_t* J, double* C, double* U,
                     double* R, double* logvol, int32_t* info) {
-  int64_t m = p->m, n = p->n;
+  int64_t m = p->m, n = orc_cols(p);          /* the strips are rows / columns of W' */
   double* Rs = (double*)malloc(sizeof(double) * (size_t)k * (size_t)n);
   double* Cs = (double*)malloc(sizeof(double) * (size_t)k * (size_t)m);
   double* G = (double*)malloc(sizeof(double) * (size_t)k * (size_t)k);
@@ -1640,12 +1665,120 @@ void orc_hadamard_abridged(int64_t n, int32_t d, double* H) {
   }
 }
 
+/* Dense complex Omega_{n,d} (re, im: n x n row-major) by the decimation-in-
+ * frequency recursion of equation eqfd, cut at depth d: Omega_s = I_s (n = 2^d s)
+ * and, for q = s, 2s, ..., n/2,
+ *   Omega_{2q} = Phat [[Omega_q, Omega_q], [Omega_q Dhat_q, -Omega_q Dhat_q]],
+ * Dhat_q = diag(w_{2q}^j), j = 0..q-1, w_N = exp(2 pi sqrt(-1) / N).  Phat puts
+ * row i of the upper block on row 2i and row i of the lower block on row 2i + 1
+ * (the even / odd interleaving under which the recursion at d = log2 n gives the
+ * DFT matrix of equation eqdft). */
+void orc_fourier_abridged(int64_t n, int32_t d, double* re, double* im) {
+  int64_t s = n >> d;
+  double* tr = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  double* ti = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+  memset(re, 0, sizeof(double) * (size_t)n * (size_t)n);
+  memset(im, 0, sizeof(double) * (size_t)n * (size_t)n);
+  for (int64_t i = 0; i < s; ++i) re[i * n + i] = 1.0;
+  for (int64_t q = s; q < n; q *= 2) {
+    /* the q x q block Omega_q sits in the top-left corner of (re, im) */
+    for (int64_t i = 0; i < q; ++i)
+      for (int64_t j = 0; j < q; ++j) {
+        double ar = re[i * n + j], ai = im[i * n + j];
+        double phi = (2.0 * ORC_PI * (double)j) / (double)(2 * q);
+        double cr = cos(phi), ci = sin(phi);
+        double br = ar * cr - ai * ci, bi = ar * ci + ai * cr;     /* (Omega_q Dhat_q)[i][j] */
+        tr[(2 * i) * n + j] = ar;           ti[(2 * i) * n + j] = ai;
+        tr[(2 * i) * n + j + q] = ar;       ti[(2 * i) * n + j + q] = ai;
+        tr[(2 * i + 1) * n + j] = br;       ti[(2 * i + 1) * n + j] = bi;
+        tr[(2 * i + 1) * n + j + q] = -br;  ti[(2 * i + 1) * n + j + q] = -bi;
+      }
+    for (int64_t i = 0; i < 2 * q; ++i)
+      for (int64_t j = 0; j < 2 * q; ++j) { re[i * n + j] = tr[i * n + j]; im[i * n + j] = ti[i * n + j]; }
+  }
+  free(tr); free(ti);
+}
+
+/* Nonzeros of column c of Omega_{n,d}: 2^d (row, exponent e) pairs, the entry
+ * being w_n^e.  By the recursion above, column c of Omega_{2q} is column
+ * c' = c mod q of Omega_q on the even rows and the same column times
+ * +-w_{2q}^{c'} (sign - when c >= q) on the odd rows; w_{2q} = w_n^{n/(2q)} and
+ * -1 = w_n^{n/2}.  Returned in the order the recursion produces them. */
+static void fourier_column(int64_t n, int32_t d, int64_t c, int64_t* rows, int64_t* ex) {
+  int64_t s = n >> d;
+  int64_t cs[32];                 /* the column index at each level, size 2^h s */
+  int64_t q = n;
+  for (int32_t h = d; h >= 0; --h) { cs[h] = c; if (h > 0) { q /= 2; c = c % q; } }
+  /* level 0: column cs[0] of I_s */
+  int64_t cnt = 1;
+  rows[0] = cs[0]; ex[0] = 0;
+  q = s;
+  for (int32_t h = 1; h <= d; ++h) {
+    int64_t cp = cs[h] % q, neg = cs[h] >= q;
+    int64_t tw = (cp * (n / (2 * q)) + (neg ? n / 2 : 0)) % n;
+    for (int64_t t = 0; t < cnt; ++t) {
+      rows[cnt + t] = 2 * rows[t] + 1; ex[cnt + t] = (ex[t] + tw) % n;
+      rows[t] = 2 * rows[t];
+    }
+    cnt *= 2;
+    q *= 2;
+  }
+}
+
+/* The 2n columns of [Re M, Im M] for M = D Omega_{n,d} P (before the scale
+ * 2^(-d/2)): column j of M is D times column perm[j] of Omega_{n,d}, with
+ * D = diag(dre + sqrt(-1) dim) (random points of the complex unit circle).  Column
+ * j of the real form (j < n) holds Re(D_r w_n^e), column n + j holds
+ * Im(D_r w_n^e), at the rows r of column perm[j], in ascending rows (2^d slots
+ * per column). */
+void orc_fourier_columns(int64_t n, int32_t d, const int32_t* perm, const double* dre, const double* dim,
+                         int32_t* rows, double* wts) {
+  int64_t w = 1LL << d;
+  int64_t* rr = (int64_t*)malloc(sizeof(int64_t) * (size_t)w);
+  int64_t* ee = (int64_t*)malloc(sizeof(int64_t) * (size_t)w);
+  for (int64_t j = 0; j < n; ++j) {
+    fourier_column(n, d, perm[j], rr, ee);
+    /* ascending rows (insertion sort: 2^d is small) */
+    for (int64_t a = 1; a < w; ++a)
+      for (int64_t b = a; b > 0 && rr[b - 1] > rr[b]; --b) {
+        int64_t t = rr[b]; rr[b] = rr[b - 1]; rr[b - 1] = t;
+        t = ee[b]; ee[b] = ee[b - 1]; ee[b - 1] = t;
+      }
+    for (int64_t t = 0; t < w; ++t) {
+      int64_t r = rr[t];
+      double phi = (2.0 * ORC_PI * (double)ee[t]) / (double)n;
+      double cr = cos(phi), ci = sin(phi);
+      rows[j * w + t] = (int32_t)r;
+      wts[j * w + t] = dre[r] * cr - dim[r] * ci;
+      rows[(n + j) * w + t] = (int32_t)r;
+      wts[(n + j) * w + t] = dre[r] * ci + dim[r] * cr;
+    }
+  }
+  free(rr); free(ee);
+}
+
 /* Dense multiplier M (N x N, N = n for a right multiplier, m for a left one)
  * of the problem, assembled from its definition: ARHT M = 2^(-d/2) D H_{N,d} P
  * (H from the recursion above, P moving column perm[j] of D H to position j);
  * sparse: M[srow][j] = ssign / sqrt(nnz). */
 void orc_multiplier_dense(const orc_problem* p, double* M) {
   int64_t n = p->mside ? p->m : p->n;
+  if (p->mkind == ORC_MULT_ARFT) {
+    /* the n x 2n real form [Re M, Im M] of M = 2^(-d/2) D Omega_{n,d} P, from the
+     * dense recursion (not from the column lists the gathers use) */
+    double* re = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    double* im = (double*)malloc(sizeof(double) * (size_t)n * (size_t)n);
+    orc_fourier_abridged(n, p->depth, re, im);
+    double sc = arht_scale(p->depth);
+    for (int64_t r = 0; r < n; ++r)
+      for (int64_t j = 0; j < n; ++j) {
+        double ar = re[r * n + p->perm[j]], ai = im[r * n + p->perm[j]];
+        M[r * 2 * n + j] = sc * (p->dre[r] * ar - p->dim[r] * ai);
+        M[r * 2 * n + n + j] = sc * (p->dre[r] * ai + p->dim[r] * ar);
+      }
+    free(re); free(im);
+    return;
+  }
   memset(M, 0, sizeof(double) * (size_t)n * (size_t)n);
   if (p->mkind == ORC_MULT_NONE) { for (int64_t i = 0; i < n; ++i) M[i * n + i] = 1.0; return; }
   if (p->mkind == ORC_MULT_SPARSE) {

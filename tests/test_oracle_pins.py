@@ -342,6 +342,81 @@ def test_multiplier_gathers_equal_dense_product(mult):
     np.testing.assert_array_equal(oracle.gather_rows_orig(p, I), W[I])
 
 
+# ------------------------------------------------------------------ abridged Fourier (ARFT)
+@pytest.mark.parametrize("k", [1, 2, 3, 5])
+def test_fourier_recursion_at_full_depth_is_the_dft(k):
+    """Equation eqfd run to the bottom (d = k, Omega_1 = 1) gives the DFT matrix of
+    equation eqdft, (w_n^{ij}) with w_n = exp(2 pi sqrt(-1) / n): this fixes the
+    reading of the odd/even permutation and of Dhat_q = diag(w_{2q}^j), j < q."""
+    n = 1 << k
+    i = np.arange(n)
+    F = np.exp(2j * np.pi * np.outer(i, i) / n)
+    np.testing.assert_allclose(oracle.fourier_abridged(n, k), F, atol=1e-13)
+
+
+@pytest.mark.parametrize("s", [1, 3, 8])
+def test_fourier_abridged_depth_one_closed_form(s):
+    """Omega_{2s,1} from Omega_s = I_s: row 2j holds 1 at columns j and j + s, row
+    2j + 1 holds w_{2s}^j and -w_{2s}^j there."""
+    n = 2 * s
+    W = np.zeros((n, n), dtype=complex)
+    for j in range(s):
+        w = np.exp(2j * np.pi * j / n)
+        W[2 * j, j] = W[2 * j, j + s] = 1.0
+        W[2 * j + 1, j], W[2 * j + 1, j + s] = w, -w
+    np.testing.assert_allclose(oracle.fourier_abridged(n, 1), W, atol=1e-15)
+
+
+@pytest.mark.parametrize("n,d", [(24, 2), (40, 3), (64, 4), (96, 1)])
+def test_fourier_abridged_unitary_up_to_scale_and_sparse(n, d):
+    """Omega_{n,d} is unitary up to scaling (Omega^H Omega = 2^d I) with 2^d
+    nonzeros, all of modulus 1, in every row and column."""
+    F = oracle.fourier_abridged(n, d)
+    np.testing.assert_allclose(F.conj().T @ F, (1 << d) * np.eye(n), atol=1e-12)
+    nz = np.abs(F) > 1e-12
+    assert np.all(nz.sum(0) == 1 << d) and np.all(nz.sum(1) == 1 << d)
+    np.testing.assert_allclose(np.abs(F[nz]), 1.0, atol=1e-14)
+
+
+@pytest.mark.parametrize("n,d", [(48, 1), (48, 2), (64, 3)])
+def test_arft_real_form_gathers_equal_dense_product(n, d):
+    """The real form [Re M, Im M] of M = 2^{-d/2} D Omega_{n,d} P has orthonormal
+    rows, and the strip gathers (column lists with 2^d real weights) equal rows and
+    columns of W [Re M, Im M] with the multiplier built densely by the recursion."""
+    g = np.random.default_rng(21)
+    W = g.standard_normal((30, n))
+    p = li.Problem(li.SRC_DENSE, 30, n, W=W)
+    li.with_arft(p, d, 3)
+    Mr = oracle.multiplier_dense(p)
+    assert Mr.shape == (n, 2 * n)
+    np.testing.assert_allclose(Mr @ Mr.T, np.eye(n), atol=1e-14)
+    # the complex M itself: D Omega P scaled, from numpy on the dense recursion
+    D = p.dcplx[:, 0] + 1j * p.dcplx[:, 1]
+    M = (D[:, None] * oracle.fourier_abridged(n, d)[:, p.perm]) * 2.0 ** (-d / 2)
+    np.testing.assert_allclose(Mr, np.hstack([M.real, M.imag]), atol=1e-15)
+    WM = W @ Mr
+    I = np.array([3, 0, 29, 17], dtype=np.int32)
+    J = np.array([2 * n - 1, 5, n, 0, n - 1], dtype=np.int32)
+    np.testing.assert_allclose(oracle.gather_rows(p, I), WM[I], atol=1e-13)
+    np.testing.assert_allclose(oracle.gather_cols(p, J), WM[:, J], atol=1e-13)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_exact_recovery_rank_r_arft(seed):
+    """Algorithm alglratpsvd1 with the real-form ARFT as the n x 2n multiplier H
+    (orthonormal rows): W = (W H)[:, J] ((W H)[I, J])^+ W[I, :] for rank-r W."""
+    p = li.dense_lowrank(96, 64, r=6, noise=0.0, seed=seed)
+    li.with_arft(p, 2, seed + 40)
+    o = oracle.ca_run(p, 6, 3, li.initial_rows(96, 6, seed + 3))
+    W = p.W
+    assert np.all(o["J"] < 128) and o["rank"] == 6
+    err = np.linalg.norm(W - o["C"] @ o["U"] @ o["R"]) / np.linalg.norm(W)
+    assert err < 1e-11, err
+    WM = W @ oracle.multiplier_dense(p)
+    np.testing.assert_allclose(o["C"], WM[:, o["J"]], atol=1e-13)
+    np.testing.assert_array_equal(o["R"], W[o["I"], :])
+
+
 def test_sparse_multiplier_structure():
     p = li.Problem(li.SRC_DENSE, 4, 50, W=np.zeros((4, 50)))
     li.with_sparse(p, 4, 2)
