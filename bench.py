@@ -416,13 +416,15 @@ class DenseWorkload:
 
     def __init__(self, mult, n=8192, k=48, sweeps=4):
         self.mult, self.n, self.k, self.sweeps, self.q, self.s = mult, n, k, sweeps, 256, 256
-        tag = {"arht": "arht2", "sparse": "sparse4", "bidiag": "bidiag3"}[mult]
+        tag = {"arht": "arht2", "sparse": "sparse4", "bidiag": "bidiag3", "arft": "arft2"}[mult]
         self.name = f"dense{n}_f32_rank32_spikes1pct_{tag}_k{k}_s{sweeps}"
 
     def host(self, rank):
         p = li.dense_spiky(self.n, r=32, seed=1000 * rank)
         if self.mult == "arht":
             li.with_arht(p, 2, 7)
+        elif self.mult == "arft":
+            li.with_arft(p, 2, 7)
         elif self.mult == "bidiag":
             li.with_bidiag(p, 3, 7)
         else:
@@ -434,7 +436,8 @@ class DenseWorkload:
     def config(self, h):
         return {"workload": self.name, "m": self.n, "n": self.n, "k": self.k, "sweeps": self.sweeps,
                 "multiplier": {"arht": "ARHT d=2", "sparse": "sparse +-1, 4 nnz/col",
-                               "bidiag": "product of 3 cyclic bidiagonal +-1 factors"}[self.mult],
+                               "bidiag": "product of 3 cyclic bidiagonal +-1 factors",
+                               "arft": "ARFT d=2 in real form (W' = W [Re M, Im M], 2n columns)"}[self.mult],
                 "input_dtype": "f32", "residual_sample": f"{self.q}x{self.s}"}
 
     def device(self, h, dev):
@@ -445,6 +448,8 @@ class DenseWorkload:
         prob = lra.Problem.dense(W)
         if p.mkind == li.MULT_ARHT:
             mult = lra.lra_precondition("arht", p.n, p.depth, p.perm, p.dsign)
+        elif p.mkind == li.MULT_ARFT:
+            mult = lra.lra_precondition_fourier(p.n, p.depth, p.perm, p.dcplx)
         elif p.mkind == li.MULT_BIDIAG:
             mult = lra.lra_precondition("bidiag", p.n, p.depth, p.perm, p.dsign)
         else:
@@ -467,7 +472,8 @@ class DenseWorkload:
 
     def flops(self, h, res):
         inf = res["info"][0]
-        return ca_flops(self.k, self.n, self.n, self.sweeps, int(inf[1]), 0.0, nucleus=False)
+        ncols = 2 * self.n if self.mult == "arft" else self.n          # columns of W'
+        return ca_flops(self.k, self.n, ncols, self.sweeps, int(inf[1]), 0.0, nucleus=False)
 
     def extra(self, res):
         inf = res["info"][0]
@@ -1554,6 +1560,7 @@ WORKLOADS = {
     "dense8192_arht": lambda: DenseWorkload("arht"),
     "dense8192_sparse": lambda: DenseWorkload("sparse"),
     "dense8192_bidiag": lambda: DenseWorkload("bidiag"),
+    "dense8192_arft": lambda: DenseWorkload("arft"),
 }
 
 

@@ -75,7 +75,8 @@ typedef enum {
   LRA_MULT_NONE = 0,
   LRA_MULT_ARHT = 1,        /* abridged randomized Hadamard 2^{-d/2} D H_{n,d} P     */
   LRA_MULT_SPARSE_PM1 = 2,  /* sparse +-1/sqrt(nnz) multiplier, nnz entries / column */
-  LRA_MULT_BIDIAG = 3       /* 2^{-q/2} prod_{i=1..q} (I + D_i S) P_i, quasi-Gaussian */
+  LRA_MULT_BIDIAG = 3,      /* 2^{-q/2} prod_{i=1..q} (I + D_i S) P_i, quasi-Gaussian */
+  LRA_MULT_ARFT = 4         /* real form [Re M, Im M], M = 2^{-d/2} D Omega_{n,d} P     */
 } lra_mult_kind;
 
 typedef struct lra_multiplier_s* lra_multiplier;   /* opaque, library-owned */
@@ -134,6 +135,36 @@ typedef enum {
 lra_status lra_precondition(lra_multiplier* out, int32_t kind, int32_t side, int64_t n, int32_t depth_or_nnz,
                             const int32_t* perm_or_rows, const int8_t* signs);
 
+/*
+ * lra_precondition_fourier -- the abridged randomized Fourier multiplier
+ * (paper: Appendix "Abridged Hadamard and Fourier Multipliers", eq. eqfd; the
+ * ARFT of the pre-processing tests) in real form, for real inputs: a right
+ * multiplier M' = [Re M, Im M] (n x 2n) with M = 2^{-d/2} D Omega_{n,d} P, so
+ * the pre-processed W' = W M' has 2n columns and C-A selects J among them.
+ *   Omega_{n,d}: the DIF recursion Omega_{2q} = Phat [[Omega_q, Omega_q],
+ *     [Omega_q Dhat_q, -Omega_q Dhat_q]] from Omega_s = I_s (n = 2^d s), with
+ *     Dhat_q = diag(w_{2q}^j), j < q, w_N = exp(2 pi sqrt(-1) / N), and Phat
+ *     placing row i of the upper block on row 2i, of the lower on row 2i + 1
+ *     (at d = log2 n this is the DFT matrix).  Every column has 2^d nonzeros.
+ *   D = diag(diag[2r] + sqrt(-1) diag[2r+1]): n host (cos, sin) pairs of
+ *     random points on the complex unit circle (|D_r| = 1 within 1e-12);
+ *   P: column j of M is D times column perm[j] of Omega_{n,d} (perm: n host
+ *     int32, a permutation of 0..n-1).
+ * Column j < n of M' holds Re(D_r w_n^e) and column n + j holds Im(D_r w_n^e)
+ * at the rows r of column perm[j] of Omega_{n,d} (entries w_n^e); the weights
+ * are formed on the host (cos and sin of 2 pi e / n, then the complex product)
+ * and w'_ij adds its 2^d terms in ascending rows, each as fma(weight, w, sum),
+ * then scales by 2^{-d/2}.  M' has orthonormal rows, so the CUR of W from the
+ * generator (I, J) of W' is C = W'[:, J], U = pinv(W'[I, J]), R = W[I, :]
+ * (Algorithm alglratpsvd1 with H = M').  depth 1..10, n a multiple of 2^d,
+ * 2 <= n < 2^30.  Serves lra_ca_run, lra_ca_run_warm, lra_ca_run_noalloc and
+ * lra_multiplier_apply (W' m x 2n); certified-FP32 mode runs it in FP64.
+ * Errors: LRA_ERR_INVALID_ARG (sizes, perm not a permutation, |D_r| != 1),
+ * LRA_ERR_CUDA.
+ */
+lra_status lra_precondition_fourier(lra_multiplier* out, int64_t n, int32_t depth, const int32_t* perm,
+                                    const double* diag);
+
 /* Free a multiplier handle (NULL is accepted). */
 lra_status lra_multiplier_destroy(lra_multiplier mult);
 
@@ -148,8 +179,8 @@ lra_status lra_multiplier_destroy(lra_multiplier mult);
  * multiplier selects the same I and J and returns the same C and U as a run on
  * (W, M); its R is W'[I, :], and lra_gather_rows gives R = W[I, :].
  * prob: W (dense F64/F32, or kernel entries), m x n.  mult: a handle for n
- * columns, or NULL (W' = W).  Wp: caller-owned device buffer, m x n row-major,
- * leading dimension ldwp >= n.  Cost: m n times the nonzeros of a column of M
+ * columns, or NULL (W' = W).  Wp: caller-owned device buffer, m x n' row-major,
+ * leading dimension ldwp >= n' (n' = 2n for LRA_MULT_ARFT, n otherwise).  Cost: m n times the nonzeros of a column of M
  * fused multiply-adds (n for the 20-factor bidiagonal products).  Entries of W
  * must be finite.  Asynchronous on the stream.
  * Errors: LRA_ERR_INVALID_ARG (bad problem, sizes, n of the handle), LRA_ERR_CUDA.
@@ -216,11 +247,13 @@ typedef struct {
 /* Outputs of one C-A CUR approximation W ~ C U R (all device, caller-owned). */
 typedef struct {
   int32_t* I;            /* k row indices, in generator order                        */
-  int32_t* J;            /* k column indices (of W' = W M), in generator order       */
-  double* C;             /* m x k: W'[:, J]                                          */
+  int32_t* J;            /* k column indices of W' (in [0, n'), n' = 2n for
+                            LRA_MULT_ARFT, n otherwise), in generator order        */
+  double* C;             /* m x k: W'[:, J] (right multiplier), W[:, J] (left)        */
   double* U;             /* k x k: nucleus, pinv of the rank-r truncation of W'[I,J] */
   double* R;             /* k x n: W[I, :] (original rows: for an orthogonal M this is
-                            the back-transform R_H M^T of Algorithm alglratpsvd1)     */
+                            the back-transform R_H M^T of Algorithm alglratpsvd1);
+                            W'[I, :] with a left multiplier                          */
   double* logvol;        /* 2*sweeps: log|det W'[I,J]| after each step (NaN if unrun) */
   int32_t* info;         /* LRA_INFO_LEN ints: numerical rank r, total swaps, loops run,
                             status, maxvol steps decided in FP32 (mixed mode), maxvol
@@ -266,7 +299,7 @@ lra_status lra_ca_run(const lra_problem* prob, const lra_ca_params* par, lra_mul
 
 /*
  * lra_ca_run_warm -- lra_ca_run with the first column step warm-started at the
- * columns J0 (device, k distinct indices in [0, n), or NULL for the cold
+ * columns J0 (device, k distinct indices in [0, n'), or NULL for the cold
  * start): resuming a run from its output (I, J) as (I0, J0) continues the
  * volume-increasing swaps, so the core's volume never decreases across the
  * restart (checkpoint / resume; the paper's C-A loops are defined by their

@@ -21,7 +21,7 @@ from . import build as _build
 __all__ = [
     "LRA_OK", "LRA_ERR_INVALID_ARG", "LRA_ERR_CUDA", "LRA_ERR_NONFINITE", "LRA_ERR_TIMEOUT", "LRA_ERR_WORKSPACE",
     "LRA_WARN_RANK_DEFICIENT", "LRA_WARN_NOT_CONVERGED", "LraError", "Problem", "Multiplier",
-    "lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run", "lra_cur_apply",
+    "lra_precondition", "lra_precondition_fourier", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run", "lra_cur_apply",
     "lra_residual_sample", "lra_version", "library_path", "lra_launch_count", "lra_profile_enable",
     "lra_profile_collect", "lra_ca_run_noalloc", "Batch", "lra_ca_run_batched", "lra_residual_sample_batched",
     "lra_gauss_cur_forward", "lra_gauss_cur_backward", "GaussCurApply", "gauss_cur_apply",
@@ -31,7 +31,7 @@ LRA_OK, LRA_ERR_INVALID_ARG, LRA_ERR_CUDA, LRA_ERR_NONFINITE, LRA_ERR_TIMEOUT, L
 LRA_WARN_RANK_DEFICIENT, LRA_WARN_NOT_CONVERGED = 16, 17
 LRA_F64, LRA_F32 = 0, 1
 LRA_DENSE, LRA_KERNEL_LAPLACE, LRA_KERNEL_GAUSSIAN = 0, 1, 2
-LRA_MULT_NONE, LRA_MULT_ARHT, LRA_MULT_SPARSE_PM1, LRA_MULT_BIDIAG = 0, 1, 2, 3
+LRA_MULT_NONE, LRA_MULT_ARHT, LRA_MULT_SPARSE_PM1, LRA_MULT_BIDIAG, LRA_MULT_ARFT = 0, 1, 2, 3, 4
 LRA_SIDE_RIGHT, LRA_SIDE_LEFT = 0, 1
 LRA_MODE_FP64, LRA_MODE_MIXED = 0, 1
 LRA_INFO_LEN = 8
@@ -105,6 +105,7 @@ def _load():
     vp, i32, i64, f64, sz = ct.c_void_p, ct.c_int32, ct.c_int64, ct.c_double, ct.c_size_t
     P, PP, PC = ct.POINTER(_Problem), ct.POINTER(_Params), ct.POINTER(_Cur)
     L.lra_precondition.argtypes = [ct.POINTER(vp), i32, i32, i64, i32, vp, vp]
+    L.lra_precondition_fourier.argtypes = [ct.POINTER(vp), i64, i32, vp, vp]
     L.lra_multiplier_destroy.argtypes = [vp]
     L.lra_ca_workspace_size.argtypes = [P, PP, vp, ct.POINTER(sz)]
     L.lra_ca_run.argtypes = [P, PP, vp, vp, PC, vp, sz, vp]
@@ -148,7 +149,7 @@ def _load():
     L.lra_launch_count.restype = ct.c_int64
     L.lra_profile_enable.argtypes = [i32]
     L.lra_profile_collect.argtypes = [i32, vp, vp, vp, ct.POINTER(i32)]
-    for f in ("lra_precondition", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run", "lra_ca_run_warm",
+    for f in ("lra_precondition", "lra_precondition_fourier", "lra_multiplier_destroy", "lra_ca_workspace_size", "lra_ca_run", "lra_ca_run_warm",
               "lra_ca_run_noalloc",
               "lra_cur_apply", "lra_cur_apply_workspace_size", "lra_residual_sample",
               "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect",
@@ -274,6 +275,23 @@ def lra_precondition(kind: str, n: int, depth_or_nnz: int, perm_or_rows, signs, 
     return Multiplier(h.value, k, n)
 
 
+def lra_precondition_fourier(n: int, depth: int, perm, diag) -> Multiplier:
+    """Abridged randomized Fourier multiplier in real form, [Re M, Im M] (n x 2n)
+    with M = 2^{-d/2} D Omega_{n,d} P: perm (n int32) and diag (n x 2 float64,
+    the real and imaginary parts of D on the complex unit circle) are host
+    arrays of the random draws.  The pre-processed W' has 2n columns."""
+    import numpy as np
+    L = _load()
+    idx = np.ascontiguousarray(np.asarray(perm), dtype=np.int32).reshape(-1)
+    dg = np.ascontiguousarray(np.asarray(diag), dtype=np.float64).reshape(-1)
+    if dg.size != 2 * idx.size:
+        raise ValueError("diag must hold n (real, imaginary) pairs")
+    h = ct.c_void_p()
+    _check(L.lra_precondition_fourier(ct.byref(h), int(n), int(depth), idx.ctypes.data, dg.ctypes.data),
+           "lra_precondition_fourier")
+    return Multiplier(h.value, LRA_MULT_ARFT, n)
+
+
 def lra_multiplier_destroy(mult: Multiplier) -> None:
     if mult is not None and mult.handle:
         _check(_load().lra_multiplier_destroy(mult.handle), "lra_multiplier_destroy")
@@ -287,11 +305,12 @@ def lra_multiplier_apply(problem: Problem, multiplier: Optional[Multiplier], out
     pivots of a run on (W, M).  ``out`` (m x n float64, unit column stride) is
     written in place when given."""
     dev = (problem.W if problem.W is not None else problem.X).device
+    ncols = 2 * problem.n if (multiplier is not None and multiplier.kind == LRA_MULT_ARFT) else problem.n
     if out is None:
-        out = torch.empty(problem.m, problem.n, dtype=torch.float64, device=dev)
-    if out.dim() != 2 or tuple(out.shape) != (problem.m, problem.n) or out.dtype != torch.float64 or \
+        out = torch.empty(problem.m, ncols, dtype=torch.float64, device=dev)
+    if out.dim() != 2 or tuple(out.shape) != (problem.m, ncols) or out.dtype != torch.float64 or \
             out.stride(1) != 1:
-        raise ValueError("out must be an m x n float64 tensor with unit column stride")
+        raise ValueError("out must be an m x n' float64 tensor with unit column stride (n' = columns of W')")
     _dev(out, torch.float64, "out")
     pc = problem._c()
     _check(_load().lra_multiplier_apply(ct.byref(pc), multiplier.handle if multiplier is not None else None,

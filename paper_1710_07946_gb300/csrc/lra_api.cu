@@ -50,6 +50,11 @@ lra_status make_dev_problem(const lra_problem* p, lra_multiplier mult, DevProble
       d.depth = mult->param;
       d.nnz = mult->width;
       d.bval = mult->d_val;
+    } else if (mult->kind == LRA_MULT_ARFT) {
+      if (mult->side != LRA_SIDE_RIGHT) return LRA_ERR_INVALID_ARG;
+      d.depth = mult->param;
+      d.nnz = mult->width;
+      d.fwt = mult->d_wt;
     } else {
       d.nnz = mult->param;
     }
@@ -149,6 +154,7 @@ static lra_status make_bidiag(lra_multiplier* out, int32_t side, int64_t n, int3
   m->d_sign = nullptr;
   m->d_val = nullptr;
   m->d_dense = nullptr;
+  m->d_wt = nullptr;
   bool ok = cudaMalloc(&m->d_idx, rows.size() * sizeof(int32_t)) == cudaSuccess &&
             cudaMalloc(&m->d_val, vals.size() * sizeof(int32_t)) == cudaSuccess &&
             cudaMemcpy(m->d_idx, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -174,6 +180,55 @@ static lra_status make_bidiag(lra_multiplier* out, int32_t side, int64_t n, int3
   }
   *out = m;
   return LRA_OK;
+}
+
+// Columns of the real form [Re M, Im M] of M = D Omega_{n,d} P (before the scale
+// 2^{-d/2}).  A column of Omega_{n,d} is built bottom-up from the recursion
+// Omega_{2q} = Phat [[Omega_q, Omega_q], [Omega_q Dhat_q, -Omega_q Dhat_q]],
+// Omega_s = I_s: column c of Omega_{2q} carries column c mod q of Omega_q to the
+// even rows 2r and, times +-w_{2q}^{c mod q} (minus for c >= q), to the odd rows
+// 2r + 1.  Entries are kept as exponents of w_n (w_{2q} = w_n^{n / 2q}, -1 =
+// w_n^{n/2}).  Column j of M is D times column perm[j]; the real form stores, in
+// ascending rows, Re(D_r w_n^e) for column j and Im(D_r w_n^e) for column n + j.
+void fourier_real_columns(int64_t n, int32_t d, const int32_t* perm, const double* diag,
+                          std::vector<int32_t>& rows, std::vector<double>& wts) {
+  const int64_t w = int64_t(1) << d, s = n >> d;
+  const double kPi = 3.14159265358979323846;
+  rows.assign((size_t)(2 * n * w), 0);
+  wts.assign((size_t)(2 * n * w), 0.0);
+  std::vector<std::pair<int64_t, int64_t>> ent((size_t)w), nxt((size_t)w);   // (row, exponent)
+  std::vector<int64_t> colat((size_t)d + 1);
+  for (int64_t j = 0; j < n; ++j) {
+    // the column index at every level, top (size n) down to the base (size s)
+    int64_t c = perm[j], size = n;
+    for (int32_t lev = d; lev >= 0; --lev) {
+      colat[(size_t)lev] = c;
+      if (lev > 0) { size /= 2; c %= size; }
+    }
+    int64_t cnt = 1, q = s;
+    ent[0] = {colat[0], 0};
+    for (int32_t lev = 1; lev <= d; ++lev, q *= 2) {
+      const int64_t cl = colat[(size_t)lev], cp = cl % q;
+      const int64_t tw = (cp * (n / (2 * q)) + (cl >= q ? n / 2 : 0)) % n;
+      for (int64_t t = 0; t < cnt; ++t) {
+        nxt[(size_t)t] = {2 * ent[(size_t)t].first, ent[(size_t)t].second};
+        nxt[(size_t)(cnt + t)] = {2 * ent[(size_t)t].first + 1, (ent[(size_t)t].second + tw) % n};
+      }
+      cnt *= 2;
+      std::swap(ent, nxt);
+    }
+    std::sort(ent.begin(), ent.begin() + w);
+    for (int64_t t = 0; t < w; ++t) {
+      const int64_t r = ent[(size_t)t].first;
+      const double phi = (2.0 * kPi * (double)ent[(size_t)t].second) / (double)n;
+      const double cr = std::cos(phi), ci = std::sin(phi);
+      const double dr = diag[2 * r], di = diag[2 * r + 1];
+      rows[(size_t)(j * w + t)] = (int32_t)r;
+      wts[(size_t)(j * w + t)] = dr * cr - di * ci;
+      rows[(size_t)((n + j) * w + t)] = (int32_t)r;
+      wts[(size_t)((n + j) * w + t)] = dr * ci + di * cr;
+    }
+  }
 }
 
 }  // namespace lra
@@ -238,6 +293,7 @@ lra_status lra_precondition(lra_multiplier* out, int32_t kind, int32_t side, int
   m->d_sign = nullptr;
   m->d_val = nullptr;
   m->d_dense = nullptr;
+  m->d_wt = nullptr;
   if (cudaMalloc(&m->d_idx, cnt * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&m->d_sign, cnt * sizeof(int8_t)) != cudaSuccess ||
       cudaMemcpy(m->d_idx, idx, cnt * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -257,8 +313,53 @@ lra_status lra_multiplier_destroy(lra_multiplier m) {
   cudaError_t e2 = cudaFree(m->d_sign);
   cudaError_t e3 = cudaFree(m->d_val);
   cudaError_t e4 = cudaFree(m->d_dense);
+  cudaError_t e5 = cudaFree(m->d_wt);
   delete m;
-  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess) ? LRA_OK : LRA_ERR_CUDA;
+  return (e1 == cudaSuccess && e2 == cudaSuccess && e3 == cudaSuccess && e4 == cudaSuccess && e5 == cudaSuccess)
+             ? LRA_OK
+             : LRA_ERR_CUDA;
+}
+
+lra_status lra_precondition_fourier(lra_multiplier* out, int64_t n, int32_t depth, const int32_t* perm,
+                                    const double* diag) {
+  if (out == nullptr) return LRA_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (perm == nullptr || diag == nullptr || depth < 1 || depth > 10 || n < 2 || n >= (int64_t(1) << 30) ||
+      (n % (int64_t(1) << depth)) != 0)
+    return LRA_ERR_INVALID_ARG;
+  std::vector<unsigned char> seen((size_t)n, 0);
+  for (int64_t j = 0; j < n; ++j) {
+    if (perm[j] < 0 || perm[j] >= n || seen[(size_t)perm[j]]) return LRA_ERR_INVALID_ARG;
+    seen[(size_t)perm[j]] = 1;
+    const double a = diag[2 * j], b = diag[2 * j + 1];
+    if (!(std::fabs(a * a + b * b - 1.0) <= 1e-12)) return LRA_ERR_INVALID_ARG;
+  }
+  std::vector<int32_t> rows;
+  std::vector<double> wts;
+  lra::fourier_real_columns(n, depth, perm, diag, rows, wts);
+  lra_multiplier m = new lra_multiplier_s;
+  m->kind = LRA_MULT_ARFT;
+  m->side = LRA_SIDE_RIGHT;
+  m->n = n;
+  m->param = depth;
+  m->width = 1 << depth;
+  m->scale = 1.0 / std::sqrt((double)(int64_t(1) << depth));
+  m->d_idx = nullptr;
+  m->d_sign = nullptr;
+  m->d_val = nullptr;
+  m->d_dense = nullptr;
+  m->d_wt = nullptr;
+  if (cudaMalloc(&m->d_idx, rows.size() * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&m->d_wt, wts.size() * sizeof(double)) != cudaSuccess ||
+      cudaMemcpy(m->d_idx, rows.data(), rows.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m->d_wt, wts.data(), wts.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(m->d_idx);
+    cudaFree(m->d_wt);
+    delete m;
+    return LRA_ERR_CUDA;
+  }
+  *out = m;
+  return LRA_OK;
 }
 
 const char* lra_version(void) { return "lra-gb300 0.1 (sm_103a)"; }

@@ -66,7 +66,7 @@ static lra_status make_plan(const DevProblem& P, const lra_ca_params* par, CaPla
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
   const int k = par->k;
-  const int64_t maxlen = std::max(P.m, P.n);
+  const int64_t maxlen = std::max(P.m, pcols(P));
   int nblk = (int)std::min<int64_t>((maxlen + MIN_COLS_PER_CTA - 1) / MIN_COLS_PER_CTA, dev.sms);
   nblk = std::max(nblk, 1);
   // mixed mode runs its certified FP32 steps on one CTA: take the single-CTA plan
@@ -74,7 +74,7 @@ static lra_status make_plan(const DevProblem& P, const lra_ca_params* par, CaPla
   if (par->mode == LRA_MODE_MIXED && mixed_supported(P) && maxlen <= MIXED_SOLO_MAX) nblk = 1;
   const size_t budget = dev.smem_optin - STATIC_SMEM_RESERVE;
   for (;;) {
-    const int cn = (int)((P.n + nblk - 1) / nblk);
+    const int cn = (int)((pcols(P) + nblk - 1) / nblk);      // columns of W' (R has P.n <= pcols)
     const int cm = (int)((P.m + nblk - 1) / nblk);
     const int ldm = std::max(cn, cm);
     const size_t fixed = ca_smem_fixed(k, ldm);

@@ -238,7 +238,7 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
   const int k = A.k, ldm = A.ldm, tid = threadIdx.x, nt = blockDim.x;
   const int ldl = k | 1;
   const int lane = tid & 31, warp = tid >> 5;
-  const int64_t len = phase == 0 ? P.n : P.m;
+  const int64_t len = phase == 0 ? pcols(P) : P.m;
   const int chunk = phase == 0 ? A.chunk_n : A.chunk_m;
   const int64_t q0 = (int64_t)grp.rank() * chunk;
   const int qn = (int)max((int64_t)0, min((int64_t)chunk, len - q0));

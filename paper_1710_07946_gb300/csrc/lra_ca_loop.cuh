@@ -50,7 +50,7 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
       for (int a = 0; a < k; ++a) {
         int32_t v = A.J0[a];
         S.Js[a] = v;
-        if (v < 0 || v >= P.n) bad = 1;
+        if (v < 0 || v >= pcols(P)) bad = 1;
         for (int b = 0; b < a; ++b) if (S.Js[b] == v) bad = 1;
       }
     S.ctl[4] = bad;

@@ -43,6 +43,7 @@ struct DevProblem {
   const int32_t* perm;       // ARHT permutation, or sparse rows (n*nnz)
   const int8_t* sign;        // ARHT diagonal, or sparse signs (n*nnz)
   const int32_t* bval;       // bidiagonal products: integer weights (n*nnz, nnz = min(2^q, n) slots)
+  const double* fwt;         // ARFT real form: weights of the 2n columns (2n*nnz, nnz = 2^d slots)
   double mscale;             // 2^{-d/2} or 1/sqrt(nnz), computed on the host
   // FP32 copies for the mixed-precision steps
   const float* X32;          // kernel points rounded to FP32 (m x 3), or null
@@ -50,6 +51,12 @@ struct DevProblem {
   float mscale32;            // mscale rounded to FP32
   float mscale_err;          // bound on |mscale32 - exact scale|
 };
+
+// Columns of the pre-processed W': 2n for the real-form Fourier multiplier
+// (W' = W [Re M, Im M]), n otherwise.
+__host__ __device__ __forceinline__ int64_t pcols(const DevProblem& P) {
+  return P.mkind == LRA_MULT_ARFT ? 2 * P.n : P.n;
+}
 
 // w_ij of the original input (no multiplier).
 __device__ __forceinline__ double w_entry(const DevProblem& P, int64_t i, int64_t j) {
@@ -88,6 +95,21 @@ __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64
   const int64_t mc = left ? i : j;                  // the column of M that combines the terms
   auto term = [&](int64_t r) -> double { return left ? w_entry(P, r, j) : w_entry(P, i, r); };
   double acc = 0.0;
+  if (P.mkind == LRA_MULT_ARFT) {
+    // real-form Fourier column: 2^d real weights in ascending rows, each fma(weight, w, sum)
+    const int32_t* rows = P.perm + mc * P.nnz;
+    const double* ws = P.fwt + mc * P.nnz;
+    for (int t0 = 0; t0 < P.nnz; t0 += TERMS) {
+      double v[TERMS], c[TERMS];
+#pragma unroll
+      for (int e = 0; e < TERMS; ++e)
+        if (t0 + e < P.nnz) { c[e] = __ldg(ws + t0 + e); v[e] = term(__ldg(rows + t0 + e)); }
+#pragma unroll
+      for (int e = 0; e < TERMS; ++e)
+        if (t0 + e < P.nnz) acc = fma(c[e], v[e], acc);
+    }
+    return acc * P.mscale;
+  }
   if (P.mkind == LRA_MULT_BIDIAG) {
     // product of bidiagonal factors: up to min(2^q, n) integer-weighted terms
     // in ascending rows (value 0 = unused slot), each fma(value, w, sum)

@@ -20,6 +20,7 @@ struct lra_multiplier_s {
   int8_t* d_sign;       // ARHT diagonal (n) or sparse signs (n*nnz)
   int32_t* d_val;       // bidiagonal integer weights (n*width)
   double* d_dense;      // bidiagonal with 2^q >= n: the integers of M as an n x n row-major matrix, else null
+  double* d_wt;         // ARFT real form: 2n x 2^d real weights (rows in d_idx), else null
   double scale;         // 2^{-d/2}, 1/sqrt(nnz) or 2^{-q/2}
 };
 
@@ -100,6 +101,7 @@ inline bool stages_valid(const lra_ca_params* par) {
 inline bool mixed_supported(const DevProblem& P) {
   if (P.mkind == LRA_MULT_BIDIAG) return false;       // no FP32 bounds for integer-weighted sums
   if (P.mside != 0) return false;                     // FP32 gathers are written for right multipliers
+  if (P.mkind == LRA_MULT_ARFT) return false;         // nor for the real-weighted Fourier columns
   return P.src == LRA_DENSE || (P.src == LRA_KERNEL_LAPLACE && P.dtype == LRA_F64);
 }
 

@@ -23,7 +23,7 @@ namespace lra {
 // are shared across the warp when the columns of M overlap), y over rows.
 __global__ void __launch_bounds__(256) multiplier_apply_kernel(DevProblem P, double* __restrict__ Wp, int64_t ldwp) {
   const int64_t j = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  if (j >= P.n) return;
+  if (j >= pcols(P)) return;
   for (int64_t i = (int64_t)blockIdx.y * 8 + threadIdx.y; i < P.m; i += (int64_t)gridDim.y * 8)
     Wp[i * ldwp + j] = wp_entry(P, i, j);
 }
@@ -114,7 +114,7 @@ lra_status lra_multiplier_apply(const lra_problem* prob, lra_multiplier mult, do
   DevProblem P;
   lra_status st = make_dev_problem(prob, mult, &P);
   if (st != LRA_OK) return st;
-  if (Wp == nullptr || ldwp < P.n || P.m < 1 || P.n < 1) return LRA_ERR_INVALID_ARG;
+  if (Wp == nullptr || ldwp < pcols(P) || P.m < 1 || P.n < 1) return LRA_ERR_INVALID_ARG;
   if (mult != nullptr && mult->kind == LRA_MULT_BIDIAG && mult->d_dense != nullptr && P.src == LRA_DENSE &&
       P.mside == 0 &&
       (P.m + 31) / 32 <= 65535 && (P.n + 63) / 64 <= INT32_MAX) {
@@ -129,7 +129,7 @@ lra_status lra_multiplier_apply(const lra_problem* prob, lra_multiplier mult, do
                                                            P.m, P.n, P.mscale, Wp, ldwp);
     return cuda_status(cudaGetLastError());
   }
-  const int64_t gx = (P.n + 31) / 32;
+  const int64_t gx = (pcols(P) + 31) / 32;
   if (gx > INT32_MAX) return LRA_ERR_INVALID_ARG;
   const int64_t gy = std::min<int64_t>((P.m + 7) / 8, 65535);
   {

@@ -24,6 +24,8 @@ def to_device(p: li.Problem):
         mult = lra.lra_precondition("sparse", order, p.nnz, p.srow, p.ssign, side=side)
     elif p.mkind == li.MULT_BIDIAG:
         mult = lra.lra_precondition("bidiag", order, p.depth, p.perm, p.dsign, side=side)
+    elif p.mkind == li.MULT_ARFT:
+        mult = lra.lra_precondition_fourier(p.n, p.depth, p.perm, p.dcplx)
     return prob, mult
 
 

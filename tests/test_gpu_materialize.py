@@ -28,10 +28,14 @@ def _with(p, kind):
         li.with_arht(p, 2, 7)
     elif kind == "sparse":
         li.with_sparse(p, 4, 8)
+    elif kind == "arft":
+        li.with_arft(p, 3, 9)
+    elif kind == "arht_left":
+        li.with_arht(p, 2, 10, side="left")
     return p
 
 
-@pytest.mark.parametrize("kind", ["none", "bidiag20", "bidiag3", "arht", "sparse"])
+@pytest.mark.parametrize("kind", ["none", "bidiag20", "bidiag3", "arht", "sparse", "arft", "arht_left"])
 def test_apply_is_bit_exact(kind):
     import paper_1710_07946_gb300 as lra
     p = _with(li.dense_spiky(512, r=12, seed=2), kind)

@@ -74,6 +74,36 @@ def test_left_multipliers_tall_inputs(mult, arg, m, n):
     assert_parity(o, g)
 
 
+@pytest.mark.parametrize("d", [1, 2, 3])
+def test_fourier_multiplier_real_form(d):
+    """The real-form ARFT (W' = W [Re M, Im M], 2n columns, real weights of
+    cos / sin of the roots of unity times D): J indexes the 2n columns; FP32
+    spiky input on one CTA."""
+    p = li.dense_spiky(1024, r=16, seed=13)
+    li.with_arft(p, d, 23)
+    I0 = li.initial_rows(1024, 24, 6)
+    o, g = run_both(p, 24, 4, I0)
+    assert_parity(o, g)
+    assert g["J"].max() < 2048
+
+
+def test_fourier_multiplier_multi_cta_and_laplace():
+    """ARFT on the cooperative grid (3000 x 2600 FP64 factor-Gaussian, depth 3)
+    and on Laplace entries evaluated on the fly (depth 2)."""
+    p = li.factor_gaussian(3000, 20, 1e-4, seed=77)
+    p.W = np.ascontiguousarray(p.W[:, :2600])
+    p.n = 2600
+    li.with_arft(p, 3, 5)
+    I0 = li.initial_rows(3000, 20, 8)
+    o, g = run_both(p, 20, 3, I0)
+    assert_parity(o, g)
+    q = li.laplace_clusters(2000, 1200, seed=5)
+    li.with_arft(q, 2, 6)
+    I0 = li.initial_rows(2000, 16, 4)
+    o, g = run_both(q, 16, 3, I0)
+    assert_parity(o, g)
+
+
 def test_left_multiplier_laplace_entries():
     """A tall Laplace block (targets 4000, sources 600) with a left ARHT: the
     pre-processed rows combine kernel entries evaluated on the fly."""
