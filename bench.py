@@ -723,6 +723,94 @@ class LevCaWorkload:
         return n, n, el, f"{n} complete runs (8 C-A iterations + nucleus + residual sample) of the step's {self.runs}"
 
 
+class CurApplyWorkload:
+    """Stored-factor CUR apply Y = C (U (R X)) (FMM stage (iii) with stored
+    generators): one rank-32 triple of a 2^20 x 2^20 matrix, C and R stored in
+    FP64, FP32 or BF16 (lra_cur_apply's dtype), one right-hand side.  The
+    factors are random (the product's cost does not depend on their values);
+    one step = one lra_cur_apply.  HBM-bound: R and C are streamed once."""
+    unit = "apply/s"
+    kernel = "apply_rx_lp_kernel"
+
+    def __init__(self, dtype="f32", m=1 << 20, n=1 << 20, k=32, nrhs=1):
+        self.dtype, self.m, self.n, self.k, self.nrhs = dtype, m, n, k, nrhs
+        self.name = f"cur_apply_{m >> 20}Mx{n >> 20}M_k{k}_nrhs{nrhs}_{dtype}"
+        if dtype == "f64":
+            self.kernel = "apply_rx_kernel"
+
+    def host(self, rank):
+        g = np.random.default_rng(50 + rank)
+        return dict(C=g.standard_normal((self.m, self.k)), R=g.standard_normal((self.k, self.n)),
+                    U=g.standard_normal((self.k, self.k)) / np.sqrt(self.k), X=g.standard_normal((self.n, self.nrhs)))
+
+    def config(self, h):
+        return {"workload": self.name, "m": self.m, "n": self.n, "k": self.k, "nrhs": self.nrhs,
+                "factor_storage": self.dtype, "accumulation": "fp64" if self.dtype == "f64" else
+                "fp32 runs, fp64 across runs, one refinement step on the vector operand"}
+
+    def device(self, h, dev):
+        import torch
+        tdt = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}[self.dtype]
+        t = lambda a, dt=torch.float64: torch.from_numpy(a).to(dev).to(dt)
+        import paper_1710_07946_gb300 as lra
+        d = dict(C=t(h["C"], tdt), R=t(h["R"], tdt), U=t(h["U"]), X=t(h["X"]))
+        d["Y"] = torch.empty(self.m, self.nrhs, dtype=torch.float64, device=dev)
+        d["ws"] = torch.empty(lra.lra_cur_apply_workspace_size(self.n, self.k, self.nrhs), dtype=torch.uint8,
+                              device=dev)
+        self._h = h
+        return d
+
+    def step(self, d):
+        import paper_1710_07946_gb300 as lra
+        lra.lra_cur_apply(d["C"], d["U"], d["R"], d["X"], Y=d["Y"], workspace=d["ws"])
+
+    def check(self, d):
+        return dict(units=1, Y=d["Y"][:4096].cpu().numpy())
+
+    def counts(self, h, res):
+        b = {"f64": 8, "f32": 4, "bf16": 2}[self.dtype]
+        rx = float(b * self.k * self.n + 8 * self.n * self.nrhs)
+        cy = float(b * self.m * self.k + 8 * self.m * self.nrhs)
+        if self.dtype == "f64":
+            return {"apply_rx_kernel": ("hbm", rx), "apply_c_kernel": ("hbm", cy)}
+        return {"apply_rx_lp_kernel": ("hbm", rx), "apply_c_lp_kernel": ("hbm", cy)}
+
+    def flops(self, h, res):
+        return 0.0
+
+    def extra(self, res):
+        # error of the first 4096 rows against the FP64 product of the unrounded factors
+        h = self._h
+        ref = h["C"][:4096] @ (h["U"] @ (h["R"] @ h["X"]))
+        return {"rel_err_vs_fp64_factors_4096_rows": float(np.linalg.norm(res["Y"] - ref) / np.linalg.norm(ref)),
+                "bytes_per_step": sum(v[1] for v in self.counts(None, None).values())}
+
+    def e2e_setup(self, h, d):
+        import torch
+        hp = dict(X=torch.from_numpy(h["X"]).pin_memory(), Y=torch.empty(self.m, self.nrhs,
+                                                                          dtype=torch.float64).pin_memory())
+        return hp, hp["X"].numel() * 8, hp["Y"].numel() * 8
+
+    def e2e_step(self, hp, d):
+        import torch
+        d["X"].copy_(hp["X"], non_blocking=True)
+        self.step(d)
+        hp["Y"].copy_(d["Y"], non_blocking=True)
+        torch.cuda.current_stream().synchronize()
+
+    def oracle_units(self, h, budget_s, seed=0):
+        import oracle
+        t0 = time.perf_counter()
+        n = 0
+        while True:
+            oracle.cur_apply(h["C"], h["U"], h["R"], h["X"])
+            n += 1
+            if time.perf_counter() - t0 >= budget_s or n >= 20:
+                break
+        el = time.perf_counter() - t0
+        return n, n, el, f"{n} FP64 applies of the same triple"
+
+
 class HMatvecWorkload:
     """The FMM's stage (iii) on the c3 recipe's point distribution: y = M x for
     the Laplace matrix of 2^16 uniform points in [0,1]^3 (M_ii = 0), held as
@@ -1561,6 +1649,7 @@ WORKLOADS = {
     "dense8192_sparse": lambda: DenseWorkload("sparse"),
     "dense8192_bidiag": lambda: DenseWorkload("bidiag"),
     "dense8192_arft": lambda: DenseWorkload("arft"),
+    **{f"cur_apply_{dt}": (lambda dt=dt: CurApplyWorkload(dt)) for dt in ("f64", "f32", "bf16")},
 }
 
 

@@ -770,14 +770,24 @@ lra_status lra_gauss_cur_backward(const lra_gauss_blocks* g, const float* x, con
 /*
  * lra_cur_apply -- Y = C (U (R X)) for one CUR triple (paper: FMM / HSS stage
  * (iii), multiplication with the generators of the neutered block columns).
- * C m x k, U k x k, R k x n (as written by lra_ca_run), X n x nrhs, Y m x nrhs,
- * all device FP64 row-major; 1 <= nrhs <= 1024.  Each product is accumulated in
- * FP64.  Errors: LRA_ERR_INVALID_ARG, LRA_ERR_CUDA.
+ * C m x k and R k x n (as written by lra_ca_run, or rounded copies of them),
+ * U k x k FP64, X n x nrhs and Y m x nrhs FP64, all device row-major.  dtype is
+ * the storage type of C and R:
+ *   LRA_F64: every product accumulated in FP64 (1 <= nrhs <= 1024);
+ *   LRA_F32 / LRA_BF16 (1 <= nrhs <= 64): C and R streamed at 4 / 2 bytes an
+ *     entry (half / a quarter of the FP64 HBM bytes; rows of R 16-byte aligned
+ *     take vector loads).  Products in FP32, accumulated in FP32 over runs of at
+ *     most 256 terms of R X and k terms of C T2, the runs in FP64; U T1 in FP64.
+ *     One refinement step: the FP64 vector operand (X, then T2 = U T1) is split
+ *     into an FP32 head and an FP32 tail, and both are multiplied by the same
+ *     stored entries, so the result carries only the storage rounding of C and
+ *     R (2^-24 or 2^-9 relative per entry) and the FP32 accumulation.
+ * Errors: LRA_ERR_INVALID_ARG (sizes, dtype), LRA_ERR_WORKSPACE, LRA_ERR_CUDA.
  */
-lra_status lra_cur_apply(const double* C, const double* U, const double* R, int64_t m, int64_t n, int32_t k,
-                         const double* X, int32_t nrhs, double* Y, void* workspace, size_t workspace_bytes,
-                         lra_stream_t stream);
-/* Workspace bytes of lra_cur_apply for an n-column R, rank k and nrhs right-hand sides. */
+lra_status lra_cur_apply(const void* C, const double* U, const void* R, int64_t m, int64_t n, int32_t k,
+                         const double* X, int32_t nrhs, double* Y, int32_t dtype, void* workspace,
+                         size_t workspace_bytes, lra_stream_t stream);
+/* Workspace bytes of lra_cur_apply for an n-column R, rank k and nrhs right-hand sides (any dtype). */
 lra_status lra_cur_apply_workspace_size(int64_t n, int32_t k, int32_t nrhs, size_t* bytes);
 
 /*

@@ -29,7 +29,7 @@ __all__ = [
 
 LRA_OK, LRA_ERR_INVALID_ARG, LRA_ERR_CUDA, LRA_ERR_NONFINITE, LRA_ERR_TIMEOUT, LRA_ERR_WORKSPACE = 0, 1, 2, 3, 4, 5
 LRA_WARN_RANK_DEFICIENT, LRA_WARN_NOT_CONVERGED = 16, 17
-LRA_F64, LRA_F32 = 0, 1
+LRA_F64, LRA_F32, LRA_BF16 = 0, 1, 2
 LRA_DENSE, LRA_KERNEL_LAPLACE, LRA_KERNEL_GAUSSIAN = 0, 1, 2
 LRA_MULT_NONE, LRA_MULT_ARHT, LRA_MULT_SPARSE_PM1, LRA_MULT_BIDIAG, LRA_MULT_ARFT = 0, 1, 2, 3, 4
 LRA_SIDE_RIGHT, LRA_SIDE_LEFT = 0, 1
@@ -111,7 +111,7 @@ def _load():
     L.lra_ca_run.argtypes = [P, PP, vp, vp, PC, vp, sz, vp]
     L.lra_ca_run_noalloc.argtypes = [P, PP, vp, vp, PC, vp]
     L.lra_ca_run_warm.argtypes = [P, PP, vp, vp, vp, PC, vp, sz, vp]
-    L.lra_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp, vp, sz, vp]
+    L.lra_cur_apply.argtypes = [vp, vp, vp, i64, i64, i32, vp, i32, vp, i32, vp, sz, vp]
     L.lra_cur_apply_workspace_size.argtypes = [i64, i32, i32, ct.POINTER(sz)]
     L.lra_residual_sample.argtypes = [P, vp, vp, vp, i32, vp, i32, vp, i32, vp, vp, vp, sz, vp]
     L.lra_residual_sample_workspace_size.argtypes = [i32, i32, i32, ct.POINTER(sz)]
@@ -471,9 +471,15 @@ def lra_ca_run_noalloc(problem: Problem, I0: torch.Tensor, out: dict, k: int, sw
 def lra_cur_apply(C: torch.Tensor, U: torch.Tensor, R: torch.Tensor, X: torch.Tensor,
                   Y: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None,
                   stream=None) -> torch.Tensor:
-    """Y = C (U (R X)) in FP64 on the device."""
+    """Y = C (U (R X)) on the device.  C and R are float64 (FP64 products) or
+    both float32 / bfloat16 (stored factors, FP32 products with one refinement
+    step, see lra_cur_apply in lra.h); U, X and Y are float64."""
     L = _load()
-    for t, nm in ((C, "C"), (U, "U"), (R, "R"), (X, "X")):
+    dt = {torch.float64: LRA_F64, torch.float32: LRA_F32, torch.bfloat16: LRA_BF16}.get(C.dtype)
+    if dt is None or R.dtype != C.dtype:
+        raise TypeError("C and R must both be float64, float32 or bfloat16")
+    _dev(C, C.dtype, "C"); _dev(R, C.dtype, "R")
+    for t, nm in ((U, "U"), (X, "X")):
         _dev(t, torch.float64, nm)
     m, k = C.shape
     n = R.shape[1]
@@ -486,8 +492,16 @@ def lra_cur_apply(C: torch.Tensor, U: torch.Tensor, R: torch.Tensor, X: torch.Te
         _check(L.lra_cur_apply_workspace_size(n, k, nrhs, ct.byref(nb)), "lra_cur_apply_workspace_size")
         workspace = _workspace(nb.value, C.device)
     _check(L.lra_cur_apply(C.data_ptr(), U.data_ptr(), R.data_ptr(), m, n, k, X2.data_ptr(), nrhs, Y.data_ptr(),
-                           workspace.data_ptr(), workspace.numel(), _stream(stream)), "lra_cur_apply")
+                           dt, workspace.data_ptr(), workspace.numel(), _stream(stream)), "lra_cur_apply")
     return Y
+
+
+def lra_cur_apply_workspace_size(n: int, k: int, nrhs: int) -> int:
+    """Bytes of device workspace lra_cur_apply needs (any storage dtype)."""
+    nb = ct.c_size_t()
+    _check(_load().lra_cur_apply_workspace_size(int(n), int(k), int(nrhs), ct.byref(nb)),
+           "lra_cur_apply_workspace_size")
+    return max(int(nb.value), 256)
 
 
 def lra_residual_sample(problem: Problem, C: torch.Tensor, U: torch.Tensor, R: torch.Tensor, Q: torch.Tensor,

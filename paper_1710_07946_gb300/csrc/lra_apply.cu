@@ -12,12 +12,144 @@
 //   filled with i.i.d. values of a single variable").
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "lra_internal.h"
 #include "lra_profile.h"
 
 namespace lra {
 
 constexpr int APPLY_ROWS_PER_CTA = 512;
+
+// ---------------------------------------------------------------------------
+// Stored factors in FP32 or BF16 (lra_cur_apply with dtype LRA_F32 / LRA_BF16).
+// The factors are streamed from HBM once at 4 or 2 bytes an entry; every
+// product is taken in FP32 and accumulated in FP32 over short runs (a tile of
+// LP_TJ columns of R, one row of C), the runs in FP64.  The FP64 vector operand
+// (X, then T2 = U T1) is split into an FP32 head and an FP32 tail and both go
+// through the same stored entries: one refinement step, after which the error
+// is the factors' storage rounding plus the FP32 accumulation.
+// ---------------------------------------------------------------------------
+constexpr int LP_TJ = 256;                 // columns of R per tile (8 per lane)
+constexpr int LP_MAX_NRHS = 64;
+constexpr int LP_THREADS = 256;
+
+__device__ __forceinline__ float lp_load(const float* p) { return __ldg(p); }
+__device__ __forceinline__ float lp_load(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+
+// Four consecutive entries (16-byte aligned for FP32, 8-byte for BF16) as floats.
+__device__ __forceinline__ void lp_load4(const float* p, float v[4]) {
+  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void lp_load4(const __nv_bfloat16* p, float v[4]) {
+  const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+  const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&q.x);
+  const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&q.y);
+  const float2 fa = __bfloat1622float2(a), fb = __bfloat1622float2(b);
+  v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
+}
+
+// Stage 1: partial[cta][a][c] = sum over this CTA's tiles of R[a][j] X[j][c]
+// (persistent CTAs over the tiles of LP_TJ columns).  Per tile and group of 16
+// right-hand sides: X's entries as FP32 head / tail in shared memory (column c
+// of the group contiguous in j), warp w takes rows a = w, w + 8, ..., lane l the
+// entries j0 + 4 l .. 4 l + 3 and j0 + 128 + 4 l .. (vector loads, coalesced), a
+// lane's eight products and the warp's butterfly in FP32, added to the row's
+// FP64 sum.  vec: R's rows allow the vector loads.  Dynamic shared memory:
+// lp_rx_smem(k, nrhs) bytes.
+__host__ __device__ inline size_t lp_rx_smem(int k, int nrhs) {
+  return sizeof(float) * 2 * (size_t)LP_TJ * 16 + sizeof(double) * (size_t)k * nrhs;
+}
+
+template <class T>
+__global__ void __launch_bounds__(LP_THREADS) apply_rx_lp_kernel(const T* __restrict__ R, const double* __restrict__ X,
+                                                                  int64_t n, int k, int nrhs, int vec,
+                                                                  double* __restrict__ partial) {
+  extern __shared__ __align__(16) unsigned char lp_smem[];
+  float* xh = reinterpret_cast<float*>(lp_smem);            // [16][LP_TJ]
+  float* xl = xh + 16 * LP_TJ;                              // [16][LP_TJ]
+  double* acc = reinterpret_cast<double*>(xl + 16 * LP_TJ); // [k][nrhs]
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) acc[it] = 0.0;
+  const int64_t ntiles = (n + LP_TJ - 1) / LP_TJ;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t j0 = tile * LP_TJ;
+    const int tj = (int)min((int64_t)LP_TJ, n - j0);
+    for (int c0 = 0; c0 < nrhs; c0 += 16) {
+      const int cn = min(16, nrhs - c0);
+      __syncthreads();
+      for (int it = threadIdx.x; it < LP_TJ * cn; it += blockDim.x) {
+        const int j = it / cn, c = it - j * cn;
+        const double v = (j < tj) ? X[(j0 + j) * nrhs + c0 + c] : 0.0;
+        const float h = __double2float_rn(v);
+        xh[c * LP_TJ + j] = h;
+        xl[c * LP_TJ + j] = __double2float_rn(v - (double)h);
+      }
+      __syncthreads();
+      for (int a = warp; a < k; a += nw) {
+        const T* row = R + (int64_t)a * n + j0;
+        float r[8];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int jj = 128 * h + 4 * lane;
+          if (vec && jj + 3 < tj) lp_load4(row + jj, r + 4 * h);
+          else
+#pragma unroll
+            for (int e = 0; e < 4; ++e) r[4 * h + e] = (jj + e < tj) ? lp_load(row + jj + e) : 0.f;
+        }
+        for (int c = 0; c < cn; ++c) {
+          float sh = 0.f, sl = 0.f;
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float4 vh = *reinterpret_cast<const float4*>(xh + c * LP_TJ + 128 * h + 4 * lane);
+            const float4 vl = *reinterpret_cast<const float4*>(xl + c * LP_TJ + 128 * h + 4 * lane);
+            sh = fmaf(r[4 * h], vh.x, sh); sh = fmaf(r[4 * h + 1], vh.y, sh);
+            sh = fmaf(r[4 * h + 2], vh.z, sh); sh = fmaf(r[4 * h + 3], vh.w, sh);
+            sl = fmaf(r[4 * h], vl.x, sl); sl = fmaf(r[4 * h + 1], vl.y, sl);
+            sl = fmaf(r[4 * h + 2], vl.z, sl); sl = fmaf(r[4 * h + 3], vl.w, sl);
+          }
+          for (int off = 16; off > 0; off >>= 1) {
+            sh += __shfl_xor_sync(0xffffffffu, sh, off);
+            sl += __shfl_xor_sync(0xffffffffu, sl, off);
+          }
+          if (lane == 0) acc[a * nrhs + c0 + c] += (double)sh + (double)sl;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) partial[(size_t)blockIdx.x * k * nrhs + it] = acc[it];
+}
+
+// Stage 3: Y[i][c] = sum_a C[i][a] T2[a][c], a thread per row: the row's k
+// stored entries in registers, T2 as FP32 head / tail in shared memory, each
+// output an FP32 sum over k products of the head plus one of the tail.
+template <class T, int KC>
+__global__ void __launch_bounds__(LP_THREADS) apply_c_lp_kernel(const T* __restrict__ C, const double* __restrict__ T2,
+                                                                 int64_t m, int k, int nrhs, double* __restrict__ Y) {
+  __shared__ float th[KMAX * LP_MAX_NRHS], tl[KMAX * LP_MAX_NRHS];
+  for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) {
+    const double v = T2[it];
+    const float h = __double2float_rn(v);
+    th[it] = h;
+    tl[it] = __double2float_rn(v - (double)h);
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    float cv[KC];
+    const T* row = C + i * k;
+#pragma unroll
+    for (int a = 0; a < KC; ++a) cv[a] = (a < k) ? lp_load(row + a) : 0.f;
+    for (int c = 0; c < nrhs; ++c) {
+      float sh = 0.f, sl = 0.f;
+#pragma unroll
+      for (int a = 0; a < KC; ++a)
+        if (a < k) { sh = fmaf(cv[a], th[a * nrhs + c], sh); sl = fmaf(cv[a], tl[a * nrhs + c], sl); }
+      Y[i * nrhs + c] = (double)sh + (double)sl;
+    }
+  }
+}
 
 // Stage 1: partial[b][a][c] = sum over this CTA's rows j of R[a][j] X[j][c].
 __global__ void __launch_bounds__(NT) apply_rx_kernel(const double* __restrict__ R, const double* __restrict__ X,
@@ -225,22 +357,75 @@ static size_t apply_ws_bytes(int64_t n, int32_t k, int32_t nrhs) {
   const int64_t nb = (n + APPLY_ROWS_PER_CTA - 1) / APPLY_ROWS_PER_CTA;
   return align_up(sizeof(double) * (size_t)nb * k * nrhs, 256) + 2 * align_up(sizeof(double) * (size_t)k * nrhs, 256);
 }
+
+// The low-precision path's persistent grid of stage 1 has a fixed number of
+// CTAs (LP_PARTS, at most), whose FP64 partial sums the FP64 stage 2 folds.
+constexpr int LP_PARTS = 608;
+static size_t apply_lp_ws_bytes(int32_t k, int32_t nrhs) {
+  return align_up(sizeof(double) * (size_t)LP_PARTS * k * nrhs, 256) + 2 * align_up(sizeof(double) * (size_t)k * nrhs, 256);
+}
+
+template <class T>
+static void launch_lp(const T* C, const double* U, const T* R, int64_t m, int64_t n, int k, const double* X, int nrhs,
+                      double* Y, int parts, int grid3, double* partial, double* T1, double* T2, cudaStream_t stream) {
+  const size_t esz = sizeof(T);
+  const int vec = ((n * esz) % 16 == 0 && (reinterpret_cast<uintptr_t>(R) & 15u) == 0) ? 1 : 0;
+  {
+    const size_t smem = lp_rx_smem(k, nrhs);
+    cudaFuncSetAttribute(apply_rx_lp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    LaunchScope ls(stream, "apply_rx_lp_kernel");
+    apply_rx_lp_kernel<T><<<parts, LP_THREADS, smem, stream>>>(R, X, n, k, nrhs, vec, partial);
+  }
+  { LaunchScope ls(stream, "apply_u_kernel"); apply_u_kernel<<<1, NT, 0, stream>>>(partial, parts, U, k, nrhs, T1, T2); }
+  LaunchScope ls(stream, "apply_c_lp_kernel");
+  if (k <= 16) apply_c_lp_kernel<T, 16><<<grid3, LP_THREADS, 0, stream>>>(C, T2, m, k, nrhs, Y);
+  else if (k <= 32) apply_c_lp_kernel<T, 32><<<grid3, LP_THREADS, 0, stream>>>(C, T2, m, k, nrhs, Y);
+  else apply_c_lp_kernel<T, 64><<<grid3, LP_THREADS, 0, stream>>>(C, T2, m, k, nrhs, Y);
+}
+
+static lra_status apply_lp(const void* C, const double* U, const void* R, int64_t m, int64_t n, int32_t k,
+                           const double* X, int32_t nrhs, double* Y, int32_t dtype, void* workspace,
+                           size_t workspace_bytes, cudaStream_t stream) {
+  if (nrhs > LP_MAX_NRHS) return LRA_ERR_INVALID_ARG;
+  const size_t need = apply_lp_ws_bytes(k, nrhs);
+  if (workspace == nullptr || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+    return LRA_ERR_WORKSPACE;
+  DeviceInfo dev;
+  lra_status st = current_device_info(&dev);
+  if (st != LRA_OK) return st;
+  const int64_t ntiles = (n + LP_TJ - 1) / LP_TJ;
+  const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::min(LP_PARTS, dev.sms * 4)));
+  const int grid3 = (int)std::max<int64_t>(1, std::min<int64_t>((m + LP_THREADS - 1) / LP_THREADS, (int64_t)dev.sms * 8));
+  unsigned char* ws = static_cast<unsigned char*>(workspace);
+  double* partial = reinterpret_cast<double*>(ws);
+  double* T1 = reinterpret_cast<double*>(ws + align_up(sizeof(double) * (size_t)LP_PARTS * k * nrhs, 256));
+  double* T2 = T1 + align_up(sizeof(double) * (size_t)k * nrhs, 256) / sizeof(double);
+  if (dtype == LRA_F32)
+    launch_lp(static_cast<const float*>(C), U, static_cast<const float*>(R), m, n, k, X, nrhs, Y, parts, grid3,
+              partial, T1, T2, stream);
+  else
+    launch_lp(static_cast<const __nv_bfloat16*>(C), U, static_cast<const __nv_bfloat16*>(R), m, n, k, X, nrhs, Y,
+              parts, grid3, partial, T1, T2, stream);
+  return cuda_status(cudaGetLastError());
+}
 }  // namespace lra
 
 extern "C" {
 
 lra_status lra_cur_apply_workspace_size(int64_t n, int32_t k, int32_t nrhs, size_t* bytes) {
   if (bytes == nullptr || n < 1 || k < 1 || k > KMAX || nrhs < 1 || nrhs > 1024) return LRA_ERR_INVALID_ARG;
-  *bytes = apply_ws_bytes(n, k, nrhs);
+  *bytes = std::max(apply_ws_bytes(n, k, nrhs), apply_lp_ws_bytes(k, nrhs));
   return LRA_OK;
 }
 
-lra_status lra_cur_apply(const double* C, const double* U, const double* R, int64_t m, int64_t n, int32_t k,
-                         const double* X, int32_t nrhs, double* Y, void* workspace, size_t workspace_bytes,
-                         lra_stream_t stream_) {
+lra_status lra_cur_apply(const void* C, const double* U, const void* R, int64_t m, int64_t n, int32_t k,
+                         const double* X, int32_t nrhs, double* Y, int32_t dtype, void* workspace,
+                         size_t workspace_bytes, lra_stream_t stream_) {
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   if (!C || !U || !R || !X || !Y || m < 1 || n < 1 || k < 1 || k > KMAX || nrhs < 1 || nrhs > 1024)
     return LRA_ERR_INVALID_ARG;
+  if (dtype != LRA_F64 && dtype != LRA_F32 && dtype != LRA_BF16) return LRA_ERR_INVALID_ARG;
+  if (dtype != LRA_F64) return apply_lp(C, U, R, m, n, k, X, nrhs, Y, dtype, workspace, workspace_bytes, stream);
   const size_t need = apply_ws_bytes(n, k, nrhs);
   if (workspace == nullptr || workspace_bytes < need || (reinterpret_cast<uintptr_t>(workspace) & 255u))
     return LRA_ERR_WORKSPACE;
@@ -249,14 +434,16 @@ lra_status lra_cur_apply(const double* C, const double* U, const double* R, int6
   double* partial = reinterpret_cast<double*>(ws);
   double* T1 = reinterpret_cast<double*>(ws + align_up(sizeof(double) * (size_t)nb * k * nrhs, 256));
   double* T2 = T1 + align_up(sizeof(double) * (size_t)k * nrhs, 256) / sizeof(double);
-  { LaunchScope ls(stream, "apply_rx_kernel"); apply_rx_kernel<<<nb, NT, 0, stream>>>(R, X, n, k, nrhs, partial); }
+  const double* R64 = static_cast<const double*>(R);
+  const double* C64 = static_cast<const double*>(C);
+  { LaunchScope ls(stream, "apply_rx_kernel"); apply_rx_kernel<<<nb, NT, 0, stream>>>(R64, X, n, k, nrhs, partial); }
   { LaunchScope ls(stream, "apply_u_kernel"); apply_u_kernel<<<1, NT, 0, stream>>>(partial, nb, U, k, nrhs, T1, T2); }
   DeviceInfo dev;
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
   const int64_t tot = m * nrhs;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tot + NT - 1) / NT, (int64_t)dev.sms * 8));
-  { LaunchScope ls(stream, "apply_c_kernel"); apply_c_kernel<<<grid, NT, 0, stream>>>(C, T2, m, k, nrhs, Y); }
+  { LaunchScope ls(stream, "apply_c_kernel"); apply_c_kernel<<<grid, NT, 0, stream>>>(C64, T2, m, k, nrhs, Y); }
   return cuda_status(cudaGetLastError());
 }
 

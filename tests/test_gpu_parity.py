@@ -270,6 +270,55 @@ def test_cur_apply_matches_oracle():
     assert np.abs(Yg - Yo).max() <= 1e-12 * np.abs(Yo).max()
 
 
+U32 = 2.0 ** -24
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("m,n,k,nrhs", [(700, 900, 6, 5), (3001, 2049, 40, 1), (1024, 4100, 64, 64),
+                                        (257, 255, 17, 16), (64, 1, 1, 3)])
+def test_cur_apply_stored_low_precision(dtype, m, n, k, nrhs):
+    """Stored factors in FP32 / BF16 with FP32 products and one refinement step
+    (the FP64 vector split into FP32 head and tail), element by element against
+    the oracle's FP64 product of the same rounded factors.  Bound: R X sums runs
+    of at most 256 terms as 8 products per lane and a 5-level butterfly (at most
+    14 roundings on any term's path), C T2 sums k terms: |dY| <= |C| |U| (14 u
+    |R| |X|) + (k + 1) u |C| |T2|, u = 2^-24 (the split leaves O(u^2)); asserted
+    with a factor 2 of slack.  Shapes: ragged tiles, rows of R not 16-byte
+    aligned (n = 255, 2049), k = 1 and 64, 1 to 64 right-hand sides."""
+    import paper_1710_07946_gb300 as lra
+    g = np.random.default_rng(m + n + k + nrhs)
+    C = g.standard_normal((m, k))
+    R = g.standard_normal((k, n))
+    U = g.standard_normal((k, k)) / np.sqrt(k)
+    X = g.standard_normal((n, nrhs))
+    tdt = torch.float32 if dtype == "f32" else torch.bfloat16
+    Cl = torch.from_numpy(C).to(tdt).cuda()
+    Rl = torch.from_numpy(R).to(tdt).cuda()
+    Ct, Rt = Cl.double().cpu().numpy(), Rl.double().cpu().numpy()      # the stored values, exactly
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    Yg = lra.lra_cur_apply(Cl, t(U), Rl, t(X)).cpu().numpy()
+    Yo = oracle.cur_apply(Ct, U, Rt, X)
+    T2 = U @ (Rt @ X)
+    bound = np.abs(Ct) @ (np.abs(U) @ (14 * U32 * (np.abs(Rt) @ np.abs(X)))) + (k + 1) * U32 * (np.abs(Ct) @ np.abs(T2))
+    err = np.abs(Yg - Yo)
+    assert np.all(err <= 2 * bound + 1e-300), (err / np.maximum(bound, 1e-300)).max()
+    # against the FP64 factors the storage rounding dominates (u or 2^-9 per entry)
+    rel = np.linalg.norm(Yg - oracle.cur_apply(C, U, R, X)) / np.linalg.norm(Yo)
+    assert rel < (1e-5 if dtype == "f32" else 3e-2), rel
+
+
+def test_cur_apply_rejects_mixed_or_unsupported_dtypes():
+    import paper_1710_07946_gb300 as lra
+    C = torch.zeros(8, 4, dtype=torch.float32, device="cuda")
+    R = torch.zeros(4, 8, dtype=torch.float64, device="cuda")
+    U = torch.zeros(4, 4, dtype=torch.float64, device="cuda")
+    X = torch.zeros(8, 1, dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        lra.lra_cur_apply(C, U, R, X)
+    with pytest.raises(lra.LraError):
+        lra.lra_cur_apply(C, U, R.float(), torch.zeros(8, 65, dtype=torch.float64, device="cuda"))   # nrhs > 64
+
+
 def test_residual_sample_matches_oracle():
     import paper_1710_07946_gb300 as lra
     from gpu_helpers import to_device
