@@ -163,7 +163,8 @@ class FmmWorkload:
         self.entries, self.stages, self.margin = entries, stages, margin
         self.h = h                        # dominance threshold, between the paper's "h = 1.1 or h = 1.01"
         sizes = "-".join(map(str, stages)) if stages else str(k)
-        self.name = f"{self.base}_k{sizes}_tol{tol:.0e}".replace("e-0", "e-") + ("_f32entries" if entries == "f32" else "")
+        self.name = f"{self.base}_k{sizes}_tol{tol:.0e}".replace("e-0", "e-") + (f"_{entries}entries" if entries != "f64"
+                                                                                 else "")
 
     def problem(self, seed):
         """One batch of the recipe: the octree's block pairs over npts points with
@@ -243,9 +244,9 @@ class FmmWorkload:
 
     def precision(self):
         """What ran in which arithmetic: the mode label and the per-stage precisions."""
-        if self.entries == "f32":
-            return "mixed: FP32 Laplace entries, FP64 pivots/LU/swaps/nucleus", {
-                "kernel_entries": "f32", "pivots_lu_swaps": "f64", "nucleus": "f64", "residual": "f64"}
+        if self.entries in ("f32", "bf16"):
+            return f"mixed: {self.entries.upper()} Laplace entries, FP64 pivots/LU/swaps/nucleus", {
+                "kernel_entries": self.entries, "pivots_lu_swaps": "f64", "nucleus": "f64", "residual": "f64"}
         return "plain fp64", {"kernel_entries": "f64", "pivots_lu_swaps": "f64", "nucleus": "f64", "residual": "f64"}
 
     def comparisons(self):
@@ -1622,6 +1623,7 @@ WORKLOADS = {
     "fmm": lambda: FmmWorkload(entries="f32"),
     "fmm_f64": FmmWorkload,
     "fmm_fixedk": lambda: FmmWorkload(stages=None),
+    "fmm_bf16entries": lambda: FmmWorkload(entries="bf16"),
     "fmm_oversample8": lambda: FmmOversampleWorkload(8),
     "fmm_oversample8_cycles4": lambda: FmmOversampleWorkload(8, pmax=4),
     "fmm_prjvol8": lambda: FmmPrjvolWorkload(8),

@@ -58,7 +58,10 @@ typedef struct {
                             LRA_F64 (w = 1/sqrt(r2), FP64) or LRA_F32 (w = fl32(1 /
                             sqrt(fl32(r2))), each FP32 operation correctly rounded,
                             r2 the FP64 squared distance; relative distance to the
-                            FP64 entry <= 1.5 * 2^-23).  Gaussian kernel: LRA_F64.
+                            FP64 entry <= 1.5 * 2^-23) or LRA_BF16 (that FP32
+                            entry rounded to bfloat16, to nearest even: relative
+                            distance <= 2^-8 + 1.5 * 2^-23).  Gaussian kernel:
+                            LRA_F64.
                             Any other value is LRA_ERR_INVALID_ARG.                  */
   int64_t m, n;          /* rows, columns; 1 <= m, n < 2^31                          */
   const void* W;         /* dense: device, m x n row-major, leading dimension ldw    */

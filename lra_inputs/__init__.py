@@ -54,7 +54,7 @@ class Problem:
     nnz: int = 0                            # sparse multiplier nonzeros per column
     srow: Optional[np.ndarray] = None       # (n, nnz) int32 ascending per column
     ssign: Optional[np.ndarray] = None      # (n, nnz) int8, +-1
-    entries: str = "f64"                    # kernel: entries evaluated in "f64" or "f32"
+    entries: str = "f64"                    # kernel: entries evaluated in "f64", "f32" or "bf16" (Laplace)
     mside: int = 0                          # multiplier side: 0 right (W M, M n x n), 1 left (M^T W, M m x m)
     dcplx: Optional[np.ndarray] = None      # ARFT diagonal D: (n, 2) float64 (real, imaginary), |D_r| = 1
     meta: dict = field(default_factory=dict)

@@ -110,7 +110,7 @@ class _Marshalled:
             s.W, s.ldw = W.ctypes.data, W.shape[1]
             s.dtype = 1 if W.dtype == np.float32 else 0
         if p.W is None:
-            s.dtype = 1 if getattr(p, "entries", "f64") == "f32" else 0
+            s.dtype = {"f64": 0, "f32": 1, "bf16": 2}[getattr(p, "entries", "f64")]
         for name in ("X", "Y"):
             a = getattr(p, name)
             if a is not None:

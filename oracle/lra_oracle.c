@@ -44,7 +44,7 @@
 /* Problem description (the oracle's own; not shared with the library) */
 /* ------------------------------------------------------------------ */
 enum { ORC_DENSE = 0, ORC_LAPLACE = 1, ORC_GAUSSIAN = 2 };
-enum { ORC_F64 = 0, ORC_F32 = 1 };
+enum { ORC_F64 = 0, ORC_F32 = 1, ORC_BF16 = 2 };
 enum { ORC_MULT_NONE = 0, ORC_MULT_ARHT = 1, ORC_MULT_SPARSE = 2, ORC_MULT_BIDIAG = 3, ORC_MULT_ARFT = 4 };
 
 typedef struct {
@@ -90,6 +90,20 @@ typedef struct {
  * Fourier multiplier, n otherwise. */
 static int64_t orc_cols(const orc_problem* p) { return p->mkind == ORC_MULT_ARFT ? 2 * p->n : p->n; }
 
+/* x rounded to bfloat16 (8 significant bits: the upper half of the IEEE single
+ * pattern), to nearest with ties to even, returned as a float.  For finite x. */
+static float round_bf16(float x) {
+  uint32_t u;
+  memcpy(&u, &x, sizeof u);
+  uint32_t keep = u >> 16;
+  uint32_t rest = u & 0xFFFFu;
+  if (rest > 0x8000u || (rest == 0x8000u && (keep & 1u))) keep += 1u;
+  uint32_t r = keep << 16;
+  float y;
+  memcpy(&y, &r, sizeof y);
+  return y;
+}
+
 /* Entry w_ij of the input W (no multiplier).  Kernel entries follow the
  * closed forms: Laplace 1/|x-y|, Gaussian exp(-|x-y|^2 / (2 l^2)). */
 static double entry_w(const orc_problem* p, int64_t i, int64_t j) {
@@ -102,12 +116,13 @@ static double entry_w(const orc_problem* p, int64_t i, int64_t j) {
   double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
   double r2 = fma(dz, dz, fma(dy, dy, dx * dx));
   if (p->src == ORC_LAPLACE) {
-    if (p->dtype == ORC_F32) {
+    if (p->dtype == ORC_F32 || p->dtype == ORC_BF16) {
       /* FP32 entries: r2 rounded to single precision, then the IEEE single
        * square root and quotient, each correctly rounded. */
       float r2f = (float)r2;
       float sf = sqrtf(r2f);
       float ef = 1.0f / sf;
+      if (p->dtype == ORC_BF16) return (double)round_bf16(ef);
       return (double)ef;
     }
     return 1.0 / sqrt(r2);

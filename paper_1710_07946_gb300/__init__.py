@@ -220,8 +220,8 @@ class Problem:
         """Kernel entries w_ij = K(x_i, y_j) evaluated on demand; ``entries``
         'f32' evaluates the Laplace kernel in FP32 (correctly rounded ops)."""
         src = {"laplace": LRA_KERNEL_LAPLACE, "gaussian": LRA_KERNEL_GAUSSIAN}[kind]
-        if entries not in ("f64", "f32"):
-            raise ValueError("entries must be 'f64' or 'f32'")
+        if entries not in ("f64", "f32", "bf16"):
+            raise ValueError("entries must be 'f64', 'f32' or 'bf16'")
         _dev(X, torch.float64, "X"); _dev(Y, torch.float64, "Y")
         return Problem(src, X.shape[0], Y.shape[0], X=X, Y=Y, length_scale=length_scale, entries=entries)
 
@@ -233,7 +233,7 @@ class Problem:
             p.W, p.ldw = self.W.data_ptr(), self.W.stride(0)
         if self.X is not None:
             p.X, p.Y = self.X.data_ptr(), self.Y.data_ptr()
-            p.dtype = LRA_F32 if self.entries == "f32" else LRA_F64
+            p.dtype = {"f64": LRA_F64, "f32": LRA_F32, "bf16": LRA_BF16}[self.entries]
         p.length_scale = float(self.length_scale)
         return p
 

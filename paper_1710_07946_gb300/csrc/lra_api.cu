@@ -29,8 +29,9 @@ lra_status make_dev_problem(const lra_problem* p, lra_multiplier mult, DevProble
   } else if (p->src == LRA_KERNEL_LAPLACE || p->src == LRA_KERNEL_GAUSSIAN) {
     if (p->X == nullptr || p->Y == nullptr) return LRA_ERR_INVALID_ARG;
     if (p->src == LRA_KERNEL_GAUSSIAN && !(p->length_scale > 0.0)) return LRA_ERR_INVALID_ARG;
-    // FP32 entries are defined for the Laplace kernel only
-    if (p->dtype != LRA_F64 && !(p->dtype == LRA_F32 && p->src == LRA_KERNEL_LAPLACE)) return LRA_ERR_INVALID_ARG;
+    // FP32 and BF16 entries are defined for the Laplace kernel only
+    if (p->dtype != LRA_F64 && !((p->dtype == LRA_F32 || p->dtype == LRA_BF16) && p->src == LRA_KERNEL_LAPLACE))
+      return LRA_ERR_INVALID_ARG;
   } else {
     return LRA_ERR_INVALID_ARG;
   }

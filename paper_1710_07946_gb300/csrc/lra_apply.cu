@@ -11,6 +11,7 @@
 //   (paper: Section "Superfast a posteriori error estimation for LRA of a matrix
 //   filled with i.i.d. values of a single variable").
 #include <algorithm>
+#include <type_traits>
 
 #include <cuda_bf16.h>
 
@@ -58,18 +59,28 @@ __device__ __forceinline__ void lp_load4(const __nv_bfloat16* p, float v[4]) {
 // lane's eight products and the warp's butterfly in FP32, added to the row's
 // FP64 sum.  vec: R's rows allow the vector loads.  Dynamic shared memory:
 // lp_rx_smem(k, nrhs) bytes.
-__host__ __device__ inline size_t lp_rx_smem(int k, int nrhs) {
-  return sizeof(float) * 2 * (size_t)LP_TJ * 16 + sizeof(double) * (size_t)k * nrhs;
+__host__ __device__ inline size_t lp_rx_smem(int k, int nrhs, size_t esz) {
+  return esz * 2 * (size_t)LP_TJ * 16 + sizeof(double) * (size_t)k * nrhs;
 }
 
+__device__ __forceinline__ void lp_load4(const double* p, double v[4]) {
+  const double2 q0 = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 q1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+}
+__device__ __forceinline__ double lp_load(const double* p) { return __ldg(p); }
+
+// FP64 storage runs the same tiles with FP64 products and sums (no split).
 template <class T>
 __global__ void __launch_bounds__(LP_THREADS) apply_rx_lp_kernel(const T* __restrict__ R, const double* __restrict__ X,
                                                                   int64_t n, int k, int nrhs, int vec,
                                                                   double* __restrict__ partial) {
+  constexpr bool kF64 = std::is_same<T, double>::value;
+  using A = typename std::conditional<kF64, double, float>::type;
   extern __shared__ __align__(16) unsigned char lp_smem[];
-  float* xh = reinterpret_cast<float*>(lp_smem);            // [16][LP_TJ]
-  float* xl = xh + 16 * LP_TJ;                              // [16][LP_TJ]
-  double* acc = reinterpret_cast<double*>(xl + 16 * LP_TJ); // [k][nrhs]
+  A* xh = reinterpret_cast<A*>(lp_smem);                     // [16][LP_TJ]
+  A* xl = xh + 16 * LP_TJ;                                   // [16][LP_TJ] (tail; unused for FP64)
+  double* acc = reinterpret_cast<double*>(xl + 16 * LP_TJ);  // [k][nrhs]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) acc[it] = 0.0;
   const int64_t ntiles = (n + LP_TJ - 1) / LP_TJ;
@@ -82,38 +93,51 @@ __global__ void __launch_bounds__(LP_THREADS) apply_rx_lp_kernel(const T* __rest
       for (int it = threadIdx.x; it < LP_TJ * cn; it += blockDim.x) {
         const int j = it / cn, c = it - j * cn;
         const double v = (j < tj) ? X[(j0 + j) * nrhs + c0 + c] : 0.0;
-        const float h = __double2float_rn(v);
-        xh[c * LP_TJ + j] = h;
-        xl[c * LP_TJ + j] = __double2float_rn(v - (double)h);
+        if (kF64) {
+          xh[c * LP_TJ + j] = (A)v;
+        } else {
+          const float h = __double2float_rn(v);
+          xh[c * LP_TJ + j] = h;
+          xl[c * LP_TJ + j] = __double2float_rn(v - (double)h);
+        }
       }
       __syncthreads();
-      for (int a = warp; a < k; a += nw) {
-        const T* row = R + (int64_t)a * n + j0;
-        float r[8];
+      // two rows per warp at a time: four vector loads of a lane in flight together
+      for (int ap = warp; 2 * ap < k; ap += nw) {
+        A r[2][8];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int jj = 128 * h + 4 * lane;
-          if (vec && jj + 3 < tj) lp_load4(row + jj, r + 4 * h);
-          else
-#pragma unroll
-            for (int e = 0; e < 4; ++e) r[4 * h + e] = (jj + e < tj) ? lp_load(row + jj + e) : 0.f;
-        }
-        for (int c = 0; c < cn; ++c) {
-          float sh = 0.f, sl = 0.f;
+        for (int q = 0; q < 2; ++q) {
+          const int a = 2 * ap + q;
+          const T* row = R + (int64_t)min(a, k - 1) * n + j0;
 #pragma unroll
           for (int h = 0; h < 2; ++h) {
-            const float4 vh = *reinterpret_cast<const float4*>(xh + c * LP_TJ + 128 * h + 4 * lane);
-            const float4 vl = *reinterpret_cast<const float4*>(xl + c * LP_TJ + 128 * h + 4 * lane);
-            sh = fmaf(r[4 * h], vh.x, sh); sh = fmaf(r[4 * h + 1], vh.y, sh);
-            sh = fmaf(r[4 * h + 2], vh.z, sh); sh = fmaf(r[4 * h + 3], vh.w, sh);
-            sl = fmaf(r[4 * h], vl.x, sl); sl = fmaf(r[4 * h + 1], vl.y, sl);
-            sl = fmaf(r[4 * h + 2], vl.z, sl); sl = fmaf(r[4 * h + 3], vl.w, sl);
+            const int jj = 128 * h + 4 * lane;
+            if (a < k && vec && jj + 3 < tj) lp_load4(row + jj, &r[q][4 * h]);
+            else
+#pragma unroll
+              for (int e = 0; e < 4; ++e) r[q][4 * h + e] = (a < k && jj + e < tj) ? (A)lp_load(row + jj + e) : (A)0;
           }
-          for (int off = 16; off > 0; off >>= 1) {
-            sh += __shfl_xor_sync(0xffffffffu, sh, off);
-            sl += __shfl_xor_sync(0xffffffffu, sl, off);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int a = 2 * ap + q;
+          if (a >= k) break;
+          for (int c = 0; c < cn; ++c) {
+            A sh = 0, sl = 0;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const int j = c * LP_TJ + 128 * h + 4 * lane + e;
+                sh = fma(r[q][4 * h + e], xh[j], sh);
+                if (!kF64) sl = fma(r[q][4 * h + e], xl[j], sl);
+              }
+            for (int off = 16; off > 0; off >>= 1) {
+              sh += __shfl_xor_sync(0xffffffffu, sh, off);
+              if (!kF64) sl += __shfl_xor_sync(0xffffffffu, sl, off);
+            }
+            if (lane == 0) acc[a * nrhs + c0 + c] += (double)sh + (double)sl;
           }
-          if (lane == 0) acc[a * nrhs + c0 + c] += (double)sh + (double)sl;
         }
       }
     }
@@ -164,14 +188,19 @@ __global__ void __launch_bounds__(NT) apply_rx_kernel(const double* __restrict__
   }
 }
 
-// Stage 2: T2 = U (sum_b partial[b]).
+// Stage 2: T2 = U (sum_b partial[b]).  A warp per entry of T1: lane l adds the
+// partials b = l, l + 32, ... in order, then a fixed butterfly (the same order
+// for a given number of partials).
 __global__ void __launch_bounds__(NT) apply_u_kernel(const double* __restrict__ partial, int nb, const double* U,
                                                      int k, int nrhs, double* __restrict__ T1,
                                                      double* __restrict__ T2) {
-  for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int it = warp; it < k * nrhs; it += nw) {
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s = s + partial[(size_t)b * k * nrhs + it];
-    T1[it] = s;
+#pragma unroll 8
+    for (int b = lane; b < nb; b += 32) s = s + partial[(size_t)b * k * nrhs + it];
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) T1[it] = s;
   }
   __syncthreads();
   for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) {
@@ -193,6 +222,116 @@ __global__ void __launch_bounds__(NT) apply_c_kernel(const double* __restrict__ 
     for (int a = 0; a < k; ++a) s = fma(__ldg(C + i * k + a), __ldg(T2 + a * nrhs + c), s);
     Y[it] = s;
   }
+}
+
+// Stage 3, vector form (k a multiple of the entries in 16 bytes, 16-byte
+// aligned rows, nrhs <= LP_MAX_NRHS): a row of C is read by L lanes, one
+// 16-byte vector each (a warp reads 32 / L consecutive rows, contiguous in
+// memory); each lane multiplies its VEC entries by T2, the L lanes' partial sums
+// meet in a fixed butterfly.  FP64 storage: FP64 products and sums.  FP32 /
+// BF16 storage: FP32 products and sums of T2's FP32 head and tail (the
+// refinement step), added in FP64.
+template <class T> struct Vec16;
+template <> struct Vec16<double> {
+  static constexpr int N = 2;
+  __device__ static void load(const double* p, double v[2]) {
+    const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = q.x; v[1] = q.y;
+  }
+};
+template <> struct Vec16<float> {
+  static constexpr int N = 4;
+  __device__ static void load(const float* p, float v[4]) { lp_load4(p, v); }
+};
+template <> struct Vec16<__nv_bfloat16> {
+  static constexpr int N = 8;
+  __device__ static void load(const __nv_bfloat16* p, float v[8]) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+    const unsigned w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w[e]));
+      v[2 * e] = f.x; v[2 * e + 1] = f.y;
+    }
+  }
+};
+
+template <class T>
+__global__ void __launch_bounds__(LP_THREADS) apply_c_vec_kernel(const T* __restrict__ C, const double* __restrict__ T2,
+                                                                  int64_t m, int k, int nrhs, int L,
+                                                                  double* __restrict__ Y) {
+  constexpr int VEC = Vec16<T>::N;
+  constexpr bool kF64 = std::is_same<T, double>::value;
+  __shared__ __align__(16) unsigned char tbuf[sizeof(double) * KMAX * LP_MAX_NRHS];
+  double* t64 = reinterpret_cast<double*>(tbuf);             // FP64 storage: T2
+  float* th = reinterpret_cast<float*>(tbuf);                // otherwise: T2's head
+  float* tl = th + (size_t)k * nrhs;                         //            and tail
+  for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) {
+    const double v = T2[it];
+    if (kF64) t64[it] = v;
+    else {
+      const float h = __double2float_rn(v);
+      th[it] = h;
+      tl[it] = __double2float_rn(v - (double)h);
+    }
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, sub = lane % L, rpw = 32 / L;
+  const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int a0 = sub * VEC;
+  constexpr int UNR = 4;                   // row groups whose loads are in flight together
+  for (int64_t g0 = gw * UNR; g0 * rpw < m; g0 += warps * UNR) {
+    typename std::conditional<kF64, double, float>::type vv[UNR][VEC];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const int64_t i = (g0 + u) * rpw + lane / L;
+      if (i < m && a0 < k) Vec16<T>::load(C + i * k + a0, vv[u]);
+      else
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) vv[u][e] = 0;
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+    const int64_t i = (g0 + u) * rpw + lane / L;
+    const bool act = i < m && a0 < k;
+    const auto* v = vv[u];
+    for (int c = 0; c < nrhs; ++c) {
+      if (kF64) {
+        double sacc = 0.0;
+        if (act)
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) sacc = fma((double)v[e], t64[(a0 + e) * nrhs + c], sacc);
+        for (int off = L >> 1; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+        if (sub == 0 && i < m) Y[i * nrhs + c] = sacc;
+      } else {
+        float sh = 0.f, sl = 0.f;
+        if (act)
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) {
+            sh = fmaf((float)v[e], th[(a0 + e) * nrhs + c], sh);
+            sl = fmaf((float)v[e], tl[(a0 + e) * nrhs + c], sl);
+          }
+        for (int off = L >> 1; off > 0; off >>= 1) {
+          sh += __shfl_xor_sync(0xffffffffu, sh, off);
+          sl += __shfl_xor_sync(0xffffffffu, sl, off);
+        }
+        if (sub == 0 && i < m) Y[i * nrhs + c] = (double)sh + (double)sl;
+      }
+    }
+    }
+  }
+}
+
+// Lanes per row of the vector form of stage 3 (a power of two >= k / VEC), or
+// 0 when the rows do not allow it.
+template <class T>
+static int vec_lanes(const T* C, int k, int nrhs) {
+  constexpr int VEC = Vec16<T>::N;
+  if (nrhs > LP_MAX_NRHS || k % VEC != 0 || (reinterpret_cast<uintptr_t>(C) & 15u) != 0) return 0;
+  int L = 1;
+  while (L * VEC < k) L *= 2;
+  return L <= 32 ? L : 0;
 }
 
 // Residual: rows of C U at the sampled rows, then E and its statistics.
@@ -371,12 +510,21 @@ static void launch_lp(const T* C, const double* U, const T* R, int64_t m, int64_
   const size_t esz = sizeof(T);
   const int vec = ((n * esz) % 16 == 0 && (reinterpret_cast<uintptr_t>(R) & 15u) == 0) ? 1 : 0;
   {
-    const size_t smem = lp_rx_smem(k, nrhs);
+    const size_t smem = lp_rx_smem(k, nrhs, std::is_same<T, double>::value ? 8 : 4);
     cudaFuncSetAttribute(apply_rx_lp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     LaunchScope ls(stream, "apply_rx_lp_kernel");
     apply_rx_lp_kernel<T><<<parts, LP_THREADS, smem, stream>>>(R, X, n, k, nrhs, vec, partial);
   }
   { LaunchScope ls(stream, "apply_u_kernel"); apply_u_kernel<<<1, NT, 0, stream>>>(partial, parts, U, k, nrhs, T1, T2); }
+  const int L = vec_lanes(C, k, nrhs);
+  if (L > 0) {
+    const int64_t rows_per_cta = (int64_t)(LP_THREADS / 32) * (32 / L) * 4;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((m + rows_per_cta - 1) / rows_per_cta,
+                                                                 (int64_t)grid3 * 8));
+    LaunchScope ls(stream, "apply_c_lp_kernel");
+    apply_c_vec_kernel<T><<<grid, LP_THREADS, 0, stream>>>(C, T2, m, k, nrhs, L, Y);
+    return;
+  }
   LaunchScope ls(stream, "apply_c_lp_kernel");
   if (k <= 16) apply_c_lp_kernel<T, 16><<<grid3, LP_THREADS, 0, stream>>>(C, T2, m, k, nrhs, Y);
   else if (k <= 32) apply_c_lp_kernel<T, 32><<<grid3, LP_THREADS, 0, stream>>>(C, T2, m, k, nrhs, Y);
@@ -436,11 +584,35 @@ lra_status lra_cur_apply(const void* C, const double* U, const void* R, int64_t 
   double* T2 = T1 + align_up(sizeof(double) * (size_t)k * nrhs, 256) / sizeof(double);
   const double* R64 = static_cast<const double*>(R);
   const double* C64 = static_cast<const double*>(C);
-  { LaunchScope ls(stream, "apply_rx_kernel"); apply_rx_kernel<<<nb, NT, 0, stream>>>(R64, X, n, k, nrhs, partial); }
-  { LaunchScope ls(stream, "apply_u_kernel"); apply_u_kernel<<<1, NT, 0, stream>>>(partial, nb, U, k, nrhs, T1, T2); }
   DeviceInfo dev;
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
+  if (nrhs <= LP_MAX_NRHS) {
+    // the tiled stage 1 (coalesced rows of R, persistent CTAs), FP64 products
+    const int64_t ntiles = (n + LP_TJ - 1) / LP_TJ;
+    const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::min<int64_t>(nb, dev.sms * 4)));
+    const int vec = ((n * 8) % 16 == 0 && (reinterpret_cast<uintptr_t>(R64) & 15u) == 0) ? 1 : 0;
+    const size_t smem = lp_rx_smem(k, nrhs, 8);
+    LRA_CUDA_TRY(cudaFuncSetAttribute(apply_rx_lp_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    {
+      LaunchScope ls(stream, "apply_rx_kernel");
+      apply_rx_lp_kernel<double><<<parts, LP_THREADS, smem, stream>>>(R64, X, n, k, nrhs, vec, partial);
+    }
+    { LaunchScope ls(stream, "apply_u_kernel"); apply_u_kernel<<<1, NT, 0, stream>>>(partial, parts, U, k, nrhs, T1, T2); }
+  } else {
+    { LaunchScope ls(stream, "apply_rx_kernel"); apply_rx_kernel<<<nb, NT, 0, stream>>>(R64, X, n, k, nrhs, partial); }
+    { LaunchScope ls(stream, "apply_u_kernel"); apply_u_kernel<<<1, NT, 0, stream>>>(partial, nb, U, k, nrhs, T1, T2); }
+  }
+  const int L = vec_lanes(C64, k, nrhs);
+  if (L > 0) {
+    const int64_t rows_per_cta = (int64_t)(LP_THREADS / 32) * (32 / L) * 4;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((m + rows_per_cta - 1) / rows_per_cta,
+                                                                 (int64_t)dev.sms * 64));
+    LaunchScope ls(stream, "apply_c_kernel");
+    apply_c_vec_kernel<double><<<grid, LP_THREADS, 0, stream>>>(C64, T2, m, k, nrhs, L, Y);
+    return cuda_status(cudaGetLastError());
+  }
   const int64_t tot = m * nrhs;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((tot + NT - 1) / NT, (int64_t)dev.sms * 8));
   { LaunchScope ls(stream, "apply_c_kernel"); apply_c_kernel<<<grid, NT, 0, stream>>>(C64, T2, m, k, nrhs, Y); }

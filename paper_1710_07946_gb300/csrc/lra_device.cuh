@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "lra.h"
@@ -74,6 +75,9 @@ __device__ __forceinline__ double w_entry(const DevProblem& P, int64_t i, int64_
     // FP32 entries: the FP64 squared distance rounded to FP32, then a correctly
     // rounded FP32 square root and reciprocal (the FP32 pipe instead of FP64)
     if (P.dtype == LRA_F32) return (double)__fdiv_rn(1.0f, __fsqrt_rn(__double2float_rn(r2)));
+    // BF16 entries: the FP32 entry rounded to bfloat16, to nearest even
+    if (P.dtype == LRA_BF16)
+      return (double)__bfloat162float(__float2bfloat16_rn(__fdiv_rn(1.0f, __fsqrt_rn(__double2float_rn(r2)))));
     return 1.0 / sqrt(r2);
   }
   return exp(-(r2 / (2.0 * P.ell * P.ell)));

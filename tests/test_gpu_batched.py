@@ -234,3 +234,12 @@ def test_headline_fmm_configuration_every_block():
         o_err[b] = oracle.residual_sample(sub, o["C"], o["U"], o["R"], h["Q"][b], h["S"][b])[4]
     np.testing.assert_allclose(gstats[:, 4], o_err, rtol=1e-6, atol=0)
     np.testing.assert_array_equal(gstats[:, 4] <= bench.ERR_BOUND, o_err <= bench.ERR_BOUND)
+
+
+def test_bf16_laplace_entries_fmm_blocks():
+    """BF16 Laplace entries (the FP32 entry rounded to bfloat16) with FP64 pivots,
+    LU, swaps and nucleus: every block of a staged batch equals the oracle's run
+    on the same BF16 entries, bit for bit in the pivots."""
+    p, blocks, lev = li.fmm_blocks(npts=1 << 15, leaf=64, min_size=64, max_size=2048, nblocks=48, seed=6)
+    p.entries = "bf16"
+    run_batch_staged(p, blocks, (28, 40, 64), 2, 3, 1e-6, h=1.05)

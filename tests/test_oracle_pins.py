@@ -342,6 +342,22 @@ def test_multiplier_gathers_equal_dense_product(mult):
     np.testing.assert_array_equal(oracle.gather_rows_orig(p, I), W[I])
 
 
+def test_bf16_laplace_entries_are_the_rounded_fp32_entries():
+    """BF16 entries: the FP32 entry rounded to bfloat16 to nearest, ties to even,
+    equal to PyTorch's float32 -> bfloat16 conversion on a million entries (with
+    ties among them), within 2^-8 of the FP32 entry."""
+    torch = pytest.importorskip("torch")
+    p = li.laplace_clusters(1000, 1000, seed=8)
+    I = np.arange(1000, dtype=np.int32)
+    f32 = oracle.gather_rows(li.Problem(li.SRC_LAPLACE, 1000, 1000, X=p.X, Y=p.Y, entries="f32"), I)
+    b16 = oracle.gather_rows(li.Problem(li.SRC_LAPLACE, 1000, 1000, X=p.X, Y=p.Y, entries="bf16"), I)
+    ref = torch.from_numpy(f32.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(b16, ref)
+    bits = f32.astype(np.float32).view(np.uint32)
+    assert ((bits & 0xFFFF) == 0x8000).sum() > 0           # ties were exercised
+    assert np.all(np.abs(b16 / f32 - 1) <= 2.0 ** -8)
+
+
 # ------------------------------------------------------------------ abridged Fourier (ARFT)
 @pytest.mark.parametrize("k", [1, 2, 3, 5])
 def test_fourier_recursion_at_full_depth_is_the_dft(k):
