@@ -780,7 +780,7 @@ lra_status lra_gauss_cur_backward(const lra_gauss_blocks* g, const float* x, con
  *   LRA_F32 / LRA_BF16 (1 <= nrhs <= 64): C and R streamed at 4 / 2 bytes an
  *     entry (half / a quarter of the FP64 HBM bytes; rows of R 16-byte aligned
  *     take vector loads).  Products in FP32, accumulated in FP32 over runs of at
- *     most 256 terms of R X and k terms of C T2, the runs in FP64; U T1 in FP64.
+ *     most 512 terms of R X and k terms of C T2, the runs in FP64; U T1 in FP64.
  *     One refinement step: the FP64 vector operand (X, then T2 = U T1) is split
  *     into an FP32 head and an FP32 tail, and both are multiplied by the same
  *     stored entries, so the result carries only the storage rounding of C and

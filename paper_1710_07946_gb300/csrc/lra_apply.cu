@@ -31,7 +31,7 @@ constexpr int APPLY_ROWS_PER_CTA = 512;
 // through the same stored entries: one refinement step, after which the error
 // is the factors' storage rounding plus the FP32 accumulation.
 // ---------------------------------------------------------------------------
-constexpr int LP_TJ = 256;                 // columns of R per tile (8 per lane)
+constexpr int LP_TJ = 512;                 // columns of R per tile (16 per lane)
 constexpr int LP_MAX_NRHS = 64;
 constexpr int LP_THREADS = 256;
 
@@ -51,36 +51,65 @@ __device__ __forceinline__ void lp_load4(const __nv_bfloat16* p, float v[4]) {
   v[0] = fa.x; v[1] = fa.y; v[2] = fb.x; v[3] = fb.y;
 }
 
-// Stage 1: partial[cta][a][c] = sum over this CTA's tiles of R[a][j] X[j][c]
-// (persistent CTAs over the tiles of LP_TJ columns).  Per tile and group of 16
-// right-hand sides: X's entries as FP32 head / tail in shared memory (column c
-// of the group contiguous in j), warp w takes rows a = w, w + 8, ..., lane l the
-// entries j0 + 4 l .. 4 l + 3 and j0 + 128 + 4 l .. (vector loads, coalesced), a
-// lane's eight products and the warp's butterfly in FP32, added to the row's
-// FP64 sum.  vec: R's rows allow the vector loads.  Dynamic shared memory:
-// lp_rx_smem(k, nrhs) bytes.
-__host__ __device__ inline size_t lp_rx_smem(int k, int nrhs, size_t esz) {
-  return esz * 2 * (size_t)LP_TJ * 16 + sizeof(double) * (size_t)k * nrhs;
+// Stage 2 on one CTA: T1 = sum_b partial[b] (a warp per entry of T1: lane l
+// adds the partials b = l, l + 32, ... in order, then a fixed butterfly -- the
+// same order for a given number of partials), then T2 = U T1 (a thread per entry,
+// an ascending fma chain).  Called by every thread of the CTA.
+__device__ inline void fold_and_apply_u(const double* __restrict__ partial, int nb, const double* __restrict__ U,
+                                        int k, int nrhs, double* __restrict__ T1, double* __restrict__ T2) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int it = warp; it < k * nrhs; it += nw) {
+    double s = 0.0;
+#pragma unroll 8
+    for (int b = lane; b < nb; b += 32) s = s + __ldcg(partial + (size_t)b * k * nrhs + it);
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) T1[it] = s;
+  }
+  __syncthreads();
+  for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) {
+    const int a = it / nrhs, c = it - a * nrhs;
+    double s = 0.0;
+#pragma unroll 8
+    for (int b = 0; b < k; ++b) s = fma(__ldg(U + a * k + b), __ldcg(T1 + b * nrhs + c), s);
+    T2[it] = s;
+  }
 }
 
+// Stage 1: partial[cta][a][c] = sum over this CTA's tiles of R[a][j] X[j][c]
+// (persistent CTAs over the tiles of LP_TJ columns).  Per tile and group of up
+// to 16 right-hand sides: X's entries in shared memory (FP32 head and tail for
+// FP32 / BF16 storage, column c of the group contiguous in j); warp w takes rows
+// a = w, w + 8, ..., four (FP64: two) at a time, lane l the 16 entries j0 + 128 g + 4 l + e
+// (g, e < 4) of each (vector loads, each covering 128 consecutive entries of
+// the row across the warp); a lane's 16 products and the warp's butterfly in
+// the product precision, added to the row's FP64 sum.  vec: R's rows allow the vector loads.
+// Dynamic shared memory: lp_rx_smem(k, nrhs, element size of the tile).
+__host__ __device__ inline size_t lp_rx_smem(int k, int nrhs, size_t esz) {
+  const int cg = nrhs < 16 ? nrhs : 16;
+  return esz * (esz == 8 ? 1 : 2) * (size_t)LP_TJ * cg + sizeof(double) * (size_t)k * nrhs;
+}
+
+__device__ __forceinline__ double lp_load(const double* p) { return __ldg(p); }
 __device__ __forceinline__ void lp_load4(const double* p, double v[4]) {
   const double2 q0 = __ldg(reinterpret_cast<const double2*>(p));
   const double2 q1 = __ldg(reinterpret_cast<const double2*>(p) + 1);
   v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
 }
-__device__ __forceinline__ double lp_load(const double* p) { return __ldg(p); }
 
-// FP64 storage runs the same tiles with FP64 products and sums (no split).
 template <class T>
 __global__ void __launch_bounds__(LP_THREADS) apply_rx_lp_kernel(const T* __restrict__ R, const double* __restrict__ X,
                                                                   int64_t n, int k, int nrhs, int vec,
-                                                                  double* __restrict__ partial) {
+                                                                  double* __restrict__ partial, const double* U,
+                                                                  double* __restrict__ T1, double* __restrict__ T2,
+                                                                  unsigned int* done) {
   constexpr bool kF64 = std::is_same<T, double>::value;
+  constexpr int RQ = kF64 ? 2 : 4;         // rows of a warp whose loads are in flight together
   using A = typename std::conditional<kF64, double, float>::type;
   extern __shared__ __align__(16) unsigned char lp_smem[];
-  A* xh = reinterpret_cast<A*>(lp_smem);                     // [16][LP_TJ]
-  A* xl = xh + 16 * LP_TJ;                                   // [16][LP_TJ] (tail; unused for FP64)
-  double* acc = reinterpret_cast<double*>(xl + 16 * LP_TJ);  // [k][nrhs]
+  const int cg = nrhs < 16 ? nrhs : 16;
+  A* xh = reinterpret_cast<A*>(lp_smem);                                  // [cg][LP_TJ]
+  A* xl = kF64 ? xh : xh + (size_t)cg * LP_TJ;                            // [cg][LP_TJ] (FP32 tail)
+  double* acc = reinterpret_cast<double*>(xl + (kF64 ? (size_t)cg * LP_TJ : (size_t)cg * LP_TJ));   // [k][nrhs]
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) acc[it] = 0.0;
   const int64_t ntiles = (n + LP_TJ - 1) / LP_TJ;
@@ -102,41 +131,45 @@ __global__ void __launch_bounds__(LP_THREADS) apply_rx_lp_kernel(const T* __rest
         }
       }
       __syncthreads();
-      // two rows per warp at a time: four vector loads of a lane in flight together
-      for (int ap = warp; 2 * ap < k; ap += nw) {
-        A r[2][8];
+      for (int ap = warp; RQ * ap < k; ap += nw) {
+        // lane l: entries 4 l + 128 g + e (g < 4, e < 4): each group's loads cover
+        // 128 consecutive entries of the row, and the float4 reads of X's tile are
+        // conflict-free
+        A r[RQ][16];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int a = 2 * ap + q;
+        for (int q = 0; q < RQ; ++q) {
+          const int a = RQ * ap + q;
           const T* row = R + (int64_t)min(a, k - 1) * n + j0;
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int jj = 128 * h + 4 * lane;
-            if (a < k && vec && jj + 3 < tj) lp_load4(row + jj, &r[q][4 * h]);
+          for (int g = 0; g < 4; ++g) {
+            const int jj = 128 * g + 4 * lane;
+            if (a < k && vec && jj + 3 < tj) lp_load4(row + jj, &r[q][4 * g]);
             else
 #pragma unroll
-              for (int e = 0; e < 4; ++e) r[q][4 * h + e] = (a < k && jj + e < tj) ? (A)lp_load(row + jj + e) : (A)0;
+              for (int e = 0; e < 4; ++e) r[q][4 * g + e] = (a < k && jj + e < tj) ? (A)lp_load(row + jj + e) : (A)0;
           }
         }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int a = 2 * ap + q;
+        for (int q = 0; q < RQ; ++q) {
+          const int a = RQ * ap + q;
           if (a >= k) break;
           for (int c = 0; c < cn; ++c) {
             A sh = 0, sl = 0;
 #pragma unroll
-            for (int h = 0; h < 2; ++h)
+            for (int g = 0; g < 4; ++g) {
+              const A* xr = xh + c * LP_TJ + 128 * g + 4 * lane;
+              const A* xt = xl + c * LP_TJ + 128 * g + 4 * lane;
 #pragma unroll
               for (int e = 0; e < 4; ++e) {
-                const int j = c * LP_TJ + 128 * h + 4 * lane + e;
-                sh = fma(r[q][4 * h + e], xh[j], sh);
-                if (!kF64) sl = fma(r[q][4 * h + e], xl[j], sl);
+                sh = fma(r[q][4 * g + e], xr[e], sh);
+                if (!kF64) sl = fma(r[q][4 * g + e], xt[e], sl);
               }
+            }
             for (int off = 16; off > 0; off >>= 1) {
               sh += __shfl_xor_sync(0xffffffffu, sh, off);
               if (!kF64) sl += __shfl_xor_sync(0xffffffffu, sl, off);
             }
-            if (lane == 0) acc[a * nrhs + c0 + c] += (double)sh + (double)sl;
+            if (lane == 0) acc[a * nrhs + c0 + c] += kF64 ? (double)sh : (double)sh + (double)sl;
           }
         }
       }
@@ -144,6 +177,18 @@ __global__ void __launch_bounds__(LP_THREADS) apply_rx_lp_kernel(const T* __rest
   }
   __syncthreads();
   for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) partial[(size_t)blockIdx.x * k * nrhs + it] = acc[it];
+  // stage 2 in the last CTA to finish (its partials and everyone's are visible
+  // after the fences); *done must be 0 at launch and is left at 0
+  __threadfence();
+  __shared__ unsigned int s_last;
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(done, 1u) == gridDim.x - 1) ? 1u : 0u;
+  __syncthreads();
+  if (s_last) {
+    __threadfence();
+    fold_and_apply_u(partial, gridDim.x, U, k, nrhs, T1, T2);
+    if (threadIdx.x == 0) *done = 0u;
+  }
 }
 
 // Stage 3: Y[i][c] = sum_a C[i][a] T2[a][c], a thread per row: the row's k
@@ -188,27 +233,11 @@ __global__ void __launch_bounds__(NT) apply_rx_kernel(const double* __restrict__
   }
 }
 
-// Stage 2: T2 = U (sum_b partial[b]).  A warp per entry of T1: lane l adds the
-// partials b = l, l + 32, ... in order, then a fixed butterfly (the same order
-// for a given number of partials).
+// Stage 2 as a kernel of its own (the untiled FP64 path).
 __global__ void __launch_bounds__(NT) apply_u_kernel(const double* __restrict__ partial, int nb, const double* U,
                                                      int k, int nrhs, double* __restrict__ T1,
                                                      double* __restrict__ T2) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int it = warp; it < k * nrhs; it += nw) {
-    double s = 0.0;
-#pragma unroll 8
-    for (int b = lane; b < nb; b += 32) s = s + partial[(size_t)b * k * nrhs + it];
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) T1[it] = s;
-  }
-  __syncthreads();
-  for (int it = threadIdx.x; it < k * nrhs; it += blockDim.x) {
-    const int a = it / nrhs, c = it - a * nrhs;
-    double s = 0.0;
-    for (int b = 0; b < k; ++b) s = fma(U[a * k + b], T1[b * nrhs + c], s);
-    T2[it] = s;
-  }
+  fold_and_apply_u(partial, nb, U, k, nrhs, T1, T2);
 }
 
 // Stage 3: Y[i][c] = sum_a C[i][a] T2[a][c].
@@ -280,7 +309,12 @@ __global__ void __launch_bounds__(LP_THREADS) apply_c_vec_kernel(const T* __rest
   const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
   const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int a0 = sub * VEC;
-  constexpr int UNR = 4;                   // row groups whose loads are in flight together
+  // UNR row groups of rpw rows each: their loads are in flight together, and
+  // their UNR * rpw results are gathered into lanes 0 .. UNR * rpw - 1 (row
+  // u * rpw + r from lane r * L of group u), so that the FP64 combination of
+  // head and tail and the store of Y take one warp instruction for all of them
+  constexpr int UNR = 4;
+  const int gu = lane / rpw, gr = lane % rpw;            // the gathered row of this lane
   for (int64_t g0 = gw * UNR; g0 * rpw < m; g0 += warps * UNR) {
     typename std::conditional<kF64, double, float>::type vv[UNR][VEC];
 #pragma unroll
@@ -291,34 +325,40 @@ __global__ void __launch_bounds__(LP_THREADS) apply_c_vec_kernel(const T* __rest
 #pragma unroll
         for (int e = 0; e < VEC; ++e) vv[u][e] = 0;
     }
-#pragma unroll
-    for (int u = 0; u < UNR; ++u) {
-    const int64_t i = (g0 + u) * rpw + lane / L;
-    const bool act = i < m && a0 < k;
-    const auto* v = vv[u];
+    const int64_t iout = g0 * rpw + lane;                // rows g0*rpw .. +UNR*rpw-1, one per gathering lane
     for (int c = 0; c < nrhs; ++c) {
       if (kF64) {
-        double sacc = 0.0;
-        if (act)
+        double got = 0.0;
 #pragma unroll
-          for (int e = 0; e < VEC; ++e) sacc = fma((double)v[e], t64[(a0 + e) * nrhs + c], sacc);
-        for (int off = L >> 1; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
-        if (sub == 0 && i < m) Y[i * nrhs + c] = sacc;
+        for (int u = 0; u < UNR; ++u) {
+          double sacc = 0.0;
+#pragma unroll
+          for (int e = 0; e < VEC; ++e) sacc = fma((double)vv[u][e], t64[min(a0 + e, k - 1) * nrhs + c], sacc);
+          for (int off = L >> 1; off > 0; off >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, off);
+          const double v = __shfl_sync(0xffffffffu, sacc, gr * L);
+          if (gu == u) got = v;
+        }
+        if (lane < UNR * rpw && iout < m) Y[iout * nrhs + c] = got;
       } else {
-        float sh = 0.f, sl = 0.f;
-        if (act)
+        float gh = 0.f, gl = 0.f;
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          float sh = 0.f, sl = 0.f;
 #pragma unroll
           for (int e = 0; e < VEC; ++e) {
-            sh = fmaf((float)v[e], th[(a0 + e) * nrhs + c], sh);
-            sl = fmaf((float)v[e], tl[(a0 + e) * nrhs + c], sl);
+            const int ae = min(a0 + e, k - 1);                 // lanes past the row's end hold zeros
+            sh = fmaf((float)vv[u][e], th[ae * nrhs + c], sh);
+            sl = fmaf((float)vv[u][e], tl[ae * nrhs + c], sl);
           }
-        for (int off = L >> 1; off > 0; off >>= 1) {
-          sh += __shfl_xor_sync(0xffffffffu, sh, off);
-          sl += __shfl_xor_sync(0xffffffffu, sl, off);
+          for (int off = L >> 1; off > 0; off >>= 1) {
+            sh += __shfl_xor_sync(0xffffffffu, sh, off);
+            sl += __shfl_xor_sync(0xffffffffu, sl, off);
+          }
+          const float vh = __shfl_sync(0xffffffffu, sh, gr * L), vl = __shfl_sync(0xffffffffu, sl, gr * L);
+          if (gu == u) { gh = vh; gl = vl; }
         }
-        if (sub == 0 && i < m) Y[i * nrhs + c] = (double)sh + (double)sl;
+        if (lane < UNR * rpw && iout < m) Y[iout * nrhs + c] = (double)gh + (double)gl;
       }
-    }
     }
   }
 }
@@ -329,7 +369,7 @@ template <class T>
 static int vec_lanes(const T* C, int k, int nrhs) {
   constexpr int VEC = Vec16<T>::N;
   if (nrhs > LP_MAX_NRHS || k % VEC != 0 || (reinterpret_cast<uintptr_t>(C) & 15u) != 0) return 0;
-  int L = 1;
+  int L = 4;                               // at least 4 lanes a row: a warp's 4 groups gather into <= 32 lanes
   while (L * VEC < k) L *= 2;
   return L <= 32 ? L : 0;
 }
@@ -494,33 +534,35 @@ using namespace lra;
 namespace lra {
 static size_t apply_ws_bytes(int64_t n, int32_t k, int32_t nrhs) {
   const int64_t nb = (n + APPLY_ROWS_PER_CTA - 1) / APPLY_ROWS_PER_CTA;
-  return align_up(sizeof(double) * (size_t)nb * k * nrhs, 256) + 2 * align_up(sizeof(double) * (size_t)k * nrhs, 256);
+  return align_up(sizeof(double) * (size_t)nb * k * nrhs, 256) + 2 * align_up(sizeof(double) * (size_t)k * nrhs, 256) +
+         256;   // the tiled stage 1's completion counter
 }
 
 // The low-precision path's persistent grid of stage 1 has a fixed number of
 // CTAs (LP_PARTS, at most), whose FP64 partial sums the FP64 stage 2 folds.
-constexpr int LP_PARTS = 608;
+constexpr int LP_PARTS = 2048;
 static size_t apply_lp_ws_bytes(int32_t k, int32_t nrhs) {
-  return align_up(sizeof(double) * (size_t)LP_PARTS * k * nrhs, 256) + 2 * align_up(sizeof(double) * (size_t)k * nrhs, 256);
+  return align_up(sizeof(double) * (size_t)LP_PARTS * k * nrhs, 256) + 2 * align_up(sizeof(double) * (size_t)k * nrhs, 256) +
+         256;   // the tiled stage 1's completion counter
 }
 
 template <class T>
 static void launch_lp(const T* C, const double* U, const T* R, int64_t m, int64_t n, int k, const double* X, int nrhs,
-                      double* Y, int parts, int grid3, double* partial, double* T1, double* T2, cudaStream_t stream) {
+                      double* Y, int parts, int grid3, double* partial, double* T1, double* T2, unsigned int* done,
+                      cudaStream_t stream) {
   const size_t esz = sizeof(T);
   const int vec = ((n * esz) % 16 == 0 && (reinterpret_cast<uintptr_t>(R) & 15u) == 0) ? 1 : 0;
   {
     const size_t smem = lp_rx_smem(k, nrhs, std::is_same<T, double>::value ? 8 : 4);
     cudaFuncSetAttribute(apply_rx_lp_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     LaunchScope ls(stream, "apply_rx_lp_kernel");
-    apply_rx_lp_kernel<T><<<parts, LP_THREADS, smem, stream>>>(R, X, n, k, nrhs, vec, partial);
+    apply_rx_lp_kernel<T><<<parts, LP_THREADS, smem, stream>>>(R, X, n, k, nrhs, vec, partial, U, T1, T2, done);
   }
-  { LaunchScope ls(stream, "apply_u_kernel"); apply_u_kernel<<<1, NT, 0, stream>>>(partial, parts, U, k, nrhs, T1, T2); }
   const int L = vec_lanes(C, k, nrhs);
   if (L > 0) {
     const int64_t rows_per_cta = (int64_t)(LP_THREADS / 32) * (32 / L) * 4;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((m + rows_per_cta - 1) / rows_per_cta,
-                                                                 (int64_t)grid3 * 8));
+                                                                 (int64_t)grid3));
     LaunchScope ls(stream, "apply_c_lp_kernel");
     apply_c_vec_kernel<T><<<grid, LP_THREADS, 0, stream>>>(C, T2, m, k, nrhs, L, Y);
     return;
@@ -542,18 +584,26 @@ static lra_status apply_lp(const void* C, const double* U, const void* R, int64_
   lra_status st = current_device_info(&dev);
   if (st != LRA_OK) return st;
   const int64_t ntiles = (n + LP_TJ - 1) / LP_TJ;
-  const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::min(LP_PARTS, dev.sms * 4)));
-  const int grid3 = (int)std::max<int64_t>(1, std::min<int64_t>((m + LP_THREADS - 1) / LP_THREADS, (int64_t)dev.sms * 8));
+  int occ = 1;
+  if (dtype == LRA_F32)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, apply_rx_lp_kernel<float>, LP_THREADS, lp_rx_smem(k, nrhs, 4));
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, apply_rx_lp_kernel<__nv_bfloat16>, LP_THREADS,
+                                                  lp_rx_smem(k, nrhs, 4));
+  const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::min(LP_PARTS, dev.sms * std::max(occ, 1))));
+  const int grid3 = (int)std::max<int64_t>(1, std::min<int64_t>((m + LP_THREADS - 1) / LP_THREADS, (int64_t)dev.sms * 7));
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   double* partial = reinterpret_cast<double*>(ws);
   double* T1 = reinterpret_cast<double*>(ws + align_up(sizeof(double) * (size_t)LP_PARTS * k * nrhs, 256));
   double* T2 = T1 + align_up(sizeof(double) * (size_t)k * nrhs, 256) / sizeof(double);
+  unsigned int* done = reinterpret_cast<unsigned int*>(T2 + align_up(sizeof(double) * (size_t)k * nrhs, 256) / 8);
+  LRA_CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(unsigned int), stream));
   if (dtype == LRA_F32)
     launch_lp(static_cast<const float*>(C), U, static_cast<const float*>(R), m, n, k, X, nrhs, Y, parts, grid3,
-              partial, T1, T2, stream);
+              partial, T1, T2, done, stream);
   else
     launch_lp(static_cast<const __nv_bfloat16*>(C), U, static_cast<const __nv_bfloat16*>(R), m, n, k, X, nrhs, Y,
-              parts, grid3, partial, T1, T2, stream);
+              parts, grid3, partial, T1, T2, done, stream);
   return cuda_status(cudaGetLastError());
 }
 }  // namespace lra
@@ -590,16 +640,20 @@ lra_status lra_cur_apply(const void* C, const double* U, const void* R, int64_t 
   if (nrhs <= LP_MAX_NRHS) {
     // the tiled stage 1 (coalesced rows of R, persistent CTAs), FP64 products
     const int64_t ntiles = (n + LP_TJ - 1) / LP_TJ;
-    const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::min<int64_t>(nb, dev.sms * 4)));
     const int vec = ((n * 8) % 16 == 0 && (reinterpret_cast<uintptr_t>(R64) & 15u) == 0) ? 1 : 0;
     const size_t smem = lp_rx_smem(k, nrhs, 8);
     LRA_CUDA_TRY(cudaFuncSetAttribute(apply_rx_lp_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
+    int occ = 1;
+    LRA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, apply_rx_lp_kernel<double>, LP_THREADS, smem));
+    const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::min<int64_t>(nb, dev.sms * std::max(occ, 1))));
+    unsigned int* done = reinterpret_cast<unsigned int*>(T2 + align_up(sizeof(double) * (size_t)k * nrhs, 256) / 8);
+    LRA_CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(unsigned int), stream));
     {
       LaunchScope ls(stream, "apply_rx_kernel");
-      apply_rx_lp_kernel<double><<<parts, LP_THREADS, smem, stream>>>(R64, X, n, k, nrhs, vec, partial);
+      apply_rx_lp_kernel<double><<<parts, LP_THREADS, smem, stream>>>(R64, X, n, k, nrhs, vec, partial, U, T1, T2,
+                                                                       done);
     }
-    { LaunchScope ls(stream, "apply_u_kernel"); apply_u_kernel<<<1, NT, 0, stream>>>(partial, parts, U, k, nrhs, T1, T2); }
   } else {
     { LaunchScope ls(stream, "apply_rx_kernel"); apply_rx_kernel<<<nb, NT, 0, stream>>>(R64, X, n, k, nrhs, partial); }
     { LaunchScope ls(stream, "apply_u_kernel"); apply_u_kernel<<<1, NT, 0, stream>>>(partial, nb, U, k, nrhs, T1, T2); }
@@ -608,7 +662,7 @@ lra_status lra_cur_apply(const void* C, const double* U, const void* R, int64_t 
   if (L > 0) {
     const int64_t rows_per_cta = (int64_t)(LP_THREADS / 32) * (32 / L) * 4;
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((m + rows_per_cta - 1) / rows_per_cta,
-                                                                 (int64_t)dev.sms * 64));
+                                                                 (int64_t)dev.sms * 7));
     LaunchScope ls(stream, "apply_c_kernel");
     apply_c_vec_kernel<double><<<grid, LP_THREADS, 0, stream>>>(C64, T2, m, k, nrhs, L, Y);
     return cuda_status(cudaGetLastError());
