@@ -79,7 +79,7 @@ __device__ inline void fold_and_apply_u(const double* __restrict__ partial, int 
 // (persistent CTAs over the tiles of LP_TJ columns).  Per tile and group of up
 // to 16 right-hand sides: X's entries in shared memory (FP32 head and tail for
 // FP32 / BF16 storage, column c of the group contiguous in j); warp w takes rows
-// a = w, w + 8, ..., four (FP64: two) at a time, lane l the 16 entries j0 + 128 g + 4 l + e
+// a = w, w + 8, ..., two at a time, lane l the 16 entries j0 + 128 g + 4 l + e
 // (g, e < 4) of each (vector loads, each covering 128 consecutive entries of
 // the row across the warp); a lane's 16 products and the warp's butterfly in
 // the product precision, added to the row's FP64 sum.  vec: R's rows allow the vector loads.
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(LP_THREADS) apply_rx_lp_kernel(const T* __rest
                                                                   double* __restrict__ T1, double* __restrict__ T2,
                                                                   unsigned int* done) {
   constexpr bool kF64 = std::is_same<T, double>::value;
-  constexpr int RQ = kF64 ? 2 : 4;         // rows of a warp whose loads are in flight together
+  constexpr int RQ = 2;                    // rows of a warp whose loads are in flight together
   using A = typename std::conditional<kF64, double, float>::type;
   extern __shared__ __align__(16) unsigned char lp_smem[];
   const int cg = nrhs < 16 ? nrhs : 16;
@@ -590,7 +590,8 @@ static lra_status apply_lp(const void* C, const double* U, const void* R, int64_
   else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, apply_rx_lp_kernel<__nv_bfloat16>, LP_THREADS,
                                                   lp_rx_smem(k, nrhs, 4));
-  const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::min(LP_PARTS, dev.sms * std::max(occ, 1))));
+  // at most two CTAs an SM: fewer partials for the last CTA to fold
+  const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::min(LP_PARTS, dev.sms * std::min(std::max(occ, 1), 2))));
   const int grid3 = (int)std::max<int64_t>(1, std::min<int64_t>((m + LP_THREADS - 1) / LP_THREADS, (int64_t)dev.sms * 7));
   unsigned char* ws = static_cast<unsigned char*>(workspace);
   double* partial = reinterpret_cast<double*>(ws);
@@ -646,7 +647,7 @@ lra_status lra_cur_apply(const void* C, const double* U, const void* R, int64_t 
                                       (int)smem));
     int occ = 1;
     LRA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, apply_rx_lp_kernel<double>, LP_THREADS, smem));
-    const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::min<int64_t>(nb, dev.sms * std::max(occ, 1))));
+    const int parts = (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, std::min<int64_t>(nb, dev.sms * std::min(std::max(occ, 1), 2))));
     unsigned int* done = reinterpret_cast<unsigned int*>(T2 + align_up(sizeof(double) * (size_t)k * nrhs, 256) / 8);
     LRA_CUDA_TRY(cudaMemsetAsync(done, 0, sizeof(unsigned int), stream));
     {
