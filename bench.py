@@ -823,9 +823,11 @@ class HMatvecWorkload:
     unit = "matvec/s"
     kernel = "hm_far_kernel"
 
-    def __init__(self, npts=1 << 16, leaf=128, k=64):
-        self.npts, self.leaf, self.k = npts, leaf, k
-        self.name = f"hmatvec_laplace_{npts // 1024}K_uniform_cube_leaf{leaf}_k28-40-64_tol1e-6"
+    def __init__(self, npts=1 << 16, leaf=128, k=64, matrix_free=False, entries="f64"):
+        self.npts, self.leaf, self.k, self.matrix_free, self.entries = npts, leaf, k, matrix_free, entries
+        size = f"{npts >> 20}M" if npts >= 1 << 20 else f"{npts // 1024}K"
+        self.name = (f"hmatvec_laplace_{size}_uniform_cube_leaf{leaf}_k28-40-64_tol1e-6" +
+                     ("_matrixfree" if matrix_free else "") + (f"_{entries}entries" if entries != "f64" else ""))
 
     def host(self, rank):
         p, far, near, L = li.fmm_partition(self.npts, leaf=self.leaf, seed=rank)
@@ -844,8 +846,8 @@ class HMatvecWorkload:
         import torch
         import paper_1710_07946_gb300 as lra
         X = torch.from_numpy(h["p"].X).to(dev)
-        prob = lra.Problem.kernel("laplace", X, X)
-        hm = lra.HMatrix(prob, h["far"], h["near"], h["L"], h["I0"], k=self.k)
+        prob = lra.Problem.kernel("laplace", X, X, entries=self.entries)
+        hm = lra.HMatrix(prob, h["far"], h["near"], h["L"], h["I0"], k=self.k, matrix_free=self.matrix_free)
         hm.build()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -866,10 +868,13 @@ class HMatvecWorkload:
 
     def _direct_rows(self, h):
         P, x, rows = h["p"].X, h["x"], h["rows"]
-        dd = np.sqrt(((P[rows, None, :] - P[None, :, :]) ** 2).sum(axis=2))
-        with np.errstate(divide="ignore"):
-            K = np.where(dd > 0.0, 1.0 / dd, 0.0)
-        return K @ x
+        out = []
+        for i in range(0, len(rows), 8):              # 8 rows at a time: bounded host memory at 2^20 points
+            dd = np.sqrt(((P[rows[i:i + 8], None, :] - P[None, :, :]) ** 2).sum(axis=2))
+            with np.errstate(divide="ignore"):
+                K = np.where(dd > 0.0, 1.0 / dd, 0.0)
+            out.append(K @ x)
+        return np.concatenate(out)
 
     def counts(self, h, res):
         far, near, info = h["far"], h["near"], res["info"]
@@ -879,6 +884,13 @@ class HMatvecWorkload:
         c_bytes = 8.0 * float((far[:, 1] * kf).sum()) + 8.0 * self.npts
         r_bytes = 8.0 * float((far[:, 3] * kf).sum()) + 8.0 * float((kf * kf).sum())
         near_flops = 10.0 * float((near[:, 1] * near[:, 3]).sum())
+        if self.matrix_free:
+            # entries re-evaluated on every call: FP64 work per entry (the squared distance, and for FP64
+            # entries the square root and division) plus the fma
+            per = (6.0 + 2.0) if self.entries == "f32" else LAPLACE_FLOPS + 2.0
+            return {"hm_far_kernel": ("alu", per * float((far[:, 1] * kf).sum())),
+                    "hm_t_kernel": ("alu", per * float((far[:, 3] * kf).sum())),
+                    "hm_near_kernel": ("alu", near_flops)}
         return {"hm_far_kernel": ("hbm", c_bytes), "hm_t_kernel": ("hbm", r_bytes),
                 "hm_near_kernel": ("alu", near_flops)}
 
@@ -1634,6 +1646,8 @@ WORKLOADS = {
     "levca_n1000_r10_k40": LevCaWorkload,
     "hmatvec_laplace_64K": HMatvecWorkload,
     "hmatvec_laplace_8K": lambda: HMatvecWorkload(npts=1 << 13),
+    "hmatvec_laplace_1M_matrixfree": lambda: HMatvecWorkload(npts=1 << 20, leaf=1024, matrix_free=True,
+                                                             entries="f32"),
     "levca_n1000_r10_k40_expected": lambda: LevCaWorkload(kind=1),
     "levca_n1000_r10_k40_uniform": lambda: LevCaWorkload(kind=2),
     "hmt11_n1024_k39_bidiag20_onthefly": lambda: Hmt11Workload(materialize=False),

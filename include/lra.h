@@ -398,9 +398,12 @@ typedef struct {
 typedef struct {
   int32_t* I;              /* nb x k: rows (block-local), first kf_b used                 */
   int32_t* J;              /* nb x k: columns (block-local)                               */
-  double* C;               /* packed C_b                                                  */
+  double* C;               /* packed C_b, or NULL together with R: lra_ca_run_batched then
+                              keeps only I, J, U, logvol and info (the factors' entries
+                              are recomputed where they are used, e.g. by a
+                              matrix-free lra_hmatvec); other batched calls need C, R  */
   double* U;               /* nb x k x k: U_b (kf_b x kf_b, row-major) at the slot start   */
-  double* R;               /* packed R_b                                                  */
+  double* R;               /* packed R_b (NULL with C)                                    */
   double* logvol;          /* nb x 2*sweeps                                               */
   int32_t* info;           /* nb x LRA_INFO_LEN (as lra_cur.info)                          */
 } lra_cur_batch;
@@ -651,6 +654,13 @@ lra_status lra_ca_lev_batched(const lra_problem* base, const lra_batch* batch, i
  * (nnear_groups x 4: row0, nrows, first block, count).  x, y: n doubles
  * (device).  The workspace holds t (nfar x kmax) and (levels - 1 + 1) partial
  * vectors of n doubles.  Asynchronous on the stream.
+ * Matrix-free form (C = R = NULL, I and J the batch's generator rows and
+ * columns, a batch run without stored factors): every entry of C_b and R_b is
+ * evaluated from prob's points exactly as the batch's gathers evaluated it
+ * (FP32 or FP64 entries, as prob's dtype), so y equals the stored form's bit for
+ * bit while the device holds only I, J and U (the stored C and R of 2^20
+ * uniform points would take about 250 GB).  Cost: the entries are recomputed
+ * on every call.
  * Errors: LRA_ERR_INVALID_ARG, LRA_ERR_WORKSPACE, LRA_ERR_CUDA.
  */
 typedef struct {
@@ -667,6 +677,8 @@ typedef struct {
   const int64_t* far_groups;
   const int64_t* near;
   const int64_t* near_groups;
+  const int32_t* I;        /* nfar x kmax generator rows (block-local): with C = R = NULL */
+  const int32_t* J;        /* nfar x kmax generator columns (block-local)                */
 } lra_hmatrix;
 
 lra_status lra_hmatvec_workspace_size(const lra_hmatrix* H, size_t* bytes);

@@ -74,7 +74,7 @@ class _HMatrix(ct.Structure):
                 ("nfar_groups", ct.c_int32), ("nnear", ct.c_int32), ("nnear_groups", ct.c_int32),
                 ("far", ct.c_void_p), ("far_offsets", ct.c_void_p), ("C", ct.c_void_p), ("U", ct.c_void_p),
                 ("R", ct.c_void_p), ("info", ct.c_void_p), ("far_groups", ct.c_void_p), ("near", ct.c_void_p),
-                ("near_groups", ct.c_void_p)]
+                ("near_groups", ct.c_void_p), ("I", ct.c_void_p), ("J", ct.c_void_p)]
 
 
 class _Gauss(ct.Structure):
@@ -557,10 +557,12 @@ class Batch:
 
     def __init__(self, problem: Problem, blocks, k: int, sweeps: int, I0, h: float = 1.01, rank_tol: float = 1e-6,
                  max_swaps: int = 1000, order="lpt", device=None, mode: int = LRA_MODE_FP64, stages=None,
-                 rank_margin: int = 2):
+                 rank_margin: int = 2, store_factors: bool = True):
         """``stages``: ascending generator sizes ending at k (the size of each block is
         fitted to its nucleus rank: a larger stage runs while rank >= size - rank_margin);
-        None runs every block at min(k, rows, cols)."""
+        None runs every block at min(k, rows, cols).  ``store_factors`` False keeps
+        only I, J, U (no C, R buffers: a matrix-free lra_hmatvec recomputes their
+        entries)."""
         import numpy as np
         blocks = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64).reshape(-1, 4))
         nb = len(blocks)
@@ -579,20 +581,22 @@ class Batch:
         self.blocks, self.offs = t(blocks, np.int64), t(offs, np.int64)
         self.order = None if order is None else t(order, np.int32)
         self.I0 = t(np.asarray(I0).reshape(nb, k), np.int32)
+        self.store_factors = bool(store_factors)
         self.out = dict(I=torch.zeros(nb, k, dtype=torch.int32, device=dev),
                         J=torch.zeros(nb, k, dtype=torch.int32, device=dev),
-                        C=torch.zeros(max(int(csz.sum()), 1), dtype=torch.float64, device=dev),
                         U=torch.zeros(nb, k, k, dtype=torch.float64, device=dev),
-                        R=torch.zeros(max(int(rsz.sum()), 1), dtype=torch.float64, device=dev),
                         logvol=torch.zeros(nb, 2 * sweeps, dtype=torch.float64, device=dev),
                         info=torch.zeros(nb, LRA_INFO_LEN, dtype=torch.int32, device=dev))
+        if self.store_factors:
+            self.out["C"] = torch.zeros(max(int(csz.sum()), 1), dtype=torch.float64, device=dev)
+            self.out["R"] = torch.zeros(max(int(rsz.sum()), 1), dtype=torch.float64, device=dev)
         self.cb = _Batch()
         self.cb.blocks, self.cb.offsets = self.blocks.data_ptr(), self.offs.data_ptr()
         self.cb.order = self.order.data_ptr() if self.order is not None else None
         self.cb.nb, self.cb.max_len = nb, int(max(blocks[:, 1].max(), blocks[:, 3].max()))
         self.cur = _CurBatch()
         for f in ("I", "J", "C", "U", "R", "logvol", "info"):
-            setattr(self.cur, f, self.out[f].data_ptr())
+            setattr(self.cur, f, self.out[f].data_ptr() if f in self.out else None)
         self.pc = problem._c()
         L = _load()
         nbytes = ct.c_size_t()
@@ -607,9 +611,10 @@ class Batch:
         o = {key: v.cpu().numpy() for key, v in self.out.items()}
         info = o["info"][b]
         kb = int(info[6]) if info[6] > 0 else int(self.kb[b])
-        return dict(I=o["I"][b, :kb], J=o["J"][b, :kb], C=o["C"][oc:oc + nr * kb].reshape(nr, kb),
+        return dict(I=o["I"][b, :kb], J=o["J"][b, :kb],
+                    C=o["C"][oc:oc + nr * kb].reshape(nr, kb) if "C" in o else None,
                     U=o["U"][b].reshape(-1)[:kb * kb].reshape(kb, kb),
-                    R=o["R"][orr:orr + kb * nc].reshape(kb, nc), logvol=o["logvol"][b],
+                    R=o["R"][orr:orr + kb * nc].reshape(kb, nc) if "R" in o else None, logvol=o["logvol"][b],
                     rank=int(info[0]), swaps=int(info[1]), loops=int(info[2]), status=int(info[3]),
                     fp32_steps=int(info[4]), fp64_steps=int(info[5]), k=kb)
 
@@ -884,14 +889,16 @@ class HMatrix:
     C-A initial rows per far block (nf x k, block-local)."""
 
     def __init__(self, problem: Problem, far, near, levels: int, I0, k: int = 64, sweeps: int = 3, h: float = 1.05,
-                 rank_tol: float = 1e-6, stages=(28, 40, 64), rank_margin: int = 2):
+                 rank_tol: float = 1e-6, stages=(28, 40, 64), rank_margin: int = 2, matrix_free: bool = False):
+        """``matrix_free``: keep only the generators' I, J and U (no C, R): each
+        matvec re-evaluates their entries from the points, bit for bit as stored."""
         import numpy as np
         far = np.asarray(far, dtype=np.int64)
         near = np.asarray(near, dtype=np.int64)
         dev = problem.X.device
-        self.problem, self.n, self.levels = problem, problem.m, int(levels)
+        self.problem, self.n, self.levels, self.matrix_free = problem, problem.m, int(levels), bool(matrix_free)
         self.batch = Batch(problem, far[:, :4], k, sweeps, I0, h=h, rank_tol=rank_tol, stages=stages,
-                           rank_margin=rank_margin)
+                           rank_margin=rank_margin, store_factors=not matrix_free)
         # groups: runs of consecutive blocks with the same (level, target box) / target leaf
         fg = []
         for i in range(len(far)):
@@ -911,7 +918,12 @@ class HMatrix:
         H.nfar, H.nfar_groups, H.nnear, H.nnear_groups = len(far), len(fg), len(near), len(ng)
         b = self.batch
         H.far, H.far_offsets = b.blocks.data_ptr(), b.offs.data_ptr()
-        H.C, H.U, H.R, H.info = (b.out[f].data_ptr() for f in ("C", "U", "R", "info"))
+        H.U, H.info = b.out["U"].data_ptr(), b.out["info"].data_ptr()
+        if self.matrix_free:
+            H.C = H.R = None
+            H.I, H.J = b.out["I"].data_ptr(), b.out["J"].data_ptr()
+        else:
+            H.C, H.R = b.out["C"].data_ptr(), b.out["R"].data_ptr()
         H.far_groups, H.near, H.near_groups = (self.far_groups.data_ptr(), self.near.data_ptr(),
                                                self.near_groups.data_ptr())
         self.H = H

@@ -252,7 +252,8 @@ lra_status batched_check(const lra_problem* base, const lra_batch* batch, const 
       !(par->h < 1e300) || !(par->rank_tol >= 0.0) || !(par->rank_tol < 1.0) ||
       (par->mode != LRA_MODE_FP64 && par->mode != LRA_MODE_MIXED) || !stages_valid(par))
     return LRA_ERR_INVALID_ARG;
-  if (!out->I || !out->J || !out->C || !out->U || !out->R || !out->logvol || !out->info) return LRA_ERR_INVALID_ARG;
+  if (!out->I || !out->J || !out->U || !out->logvol || !out->info) return LRA_ERR_INVALID_ARG;
+  if ((out->C == nullptr) != (out->R == nullptr)) return LRA_ERR_INVALID_ARG;   // both factors, or neither
   return LRA_OK;
 }
 

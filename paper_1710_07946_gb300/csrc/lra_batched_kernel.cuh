@@ -84,8 +84,8 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
     A.I0 = B.I0 + (size_t)b * B.kmax;
     A.I = B.I + (size_t)b * B.kmax;
     A.J = B.J + (size_t)b * B.kmax;
-    A.C = B.C + B.offs[2 * (size_t)b];
-    A.R = B.R + B.offs[2 * (size_t)b + 1];
+    A.C = B.C ? B.C + B.offs[2 * (size_t)b] : nullptr;        // null: the factors are not stored
+    A.R = B.R ? B.R + B.offs[2 * (size_t)b + 1] : nullptr;
     A.logvol = B.logvol + (size_t)b * 2 * B.sweeps;
     A.info = info;
     A.G = G;

@@ -85,7 +85,8 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
     return;
   }
   // outputs: C = W'[:, J] over this CTA's rows, R = W[I, :] over its columns
-  {
+  // (a batch may keep only I, J and U: null C and R are not written)
+  if (A.C != nullptr && A.R != nullptr) {
     const int64_t r0 = (int64_t)grp.rank() * A.chunk_m;
     const int rn = (int)max((int64_t)0, min((int64_t)A.chunk_m, P.m - r0));
     for (int it = tid; it < rn * k; it += nt) {

@@ -26,20 +26,31 @@ __device__ __forceinline__ int hm_kf(const lra_hmatrix& H, int64_t b) {
 
 // Pass 1: one CTA per far block (grid-stride): t1 = R_b x[cols], a warp per row
 // of R_b (lane-strided fma partial sums, then a fixed butterfly), then t = U_b t1
-// with a thread per entry (an ascending fma chain).
-__global__ void __launch_bounds__(256) hm_t_kernel(lra_hmatrix H, const double* __restrict__ x,
+// with a thread per entry (an ascending fma chain).  MF (matrix-free: the
+// batch kept only I, J, U): R_b[a][c] = w(r0 + I_b[a], c0 + c) is evaluated from
+// the points as the batch's gathers evaluated it, so the sums are those of the
+// stored form, bit for bit.
+template <bool MF>
+__global__ void __launch_bounds__(256) hm_t_kernel(DevProblem P, lra_hmatrix H, const double* __restrict__ x,
                                                    double* __restrict__ t) {
   __shared__ double t1[KMAX];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int b = blockIdx.x; b < H.nfar; b += gridDim.x) {
+    const int64_t r0 = H.far[4 * (size_t)b], nr = H.far[4 * (size_t)b + 1];
     const int64_t nc = H.far[4 * (size_t)b + 3], c0 = H.far[4 * (size_t)b + 2];
-    const int kf = (c0 < 0 || nc < 0 || c0 + nc > H.n) ? 0 : hm_kf(H, b);
-    const double* R = H.R + H.far_offsets[2 * (size_t)b + 1];
+    const int kf = (c0 < 0 || nc < 0 || c0 + nc > H.n || (MF && (r0 < 0 || nr < 1 || r0 + nr > H.n))) ? 0
+                                                                                                       : hm_kf(H, b);
+    const double* R = MF ? nullptr : H.R + H.far_offsets[2 * (size_t)b + 1];
+    const int32_t* Ib = MF ? H.I + (size_t)b * H.kmax : nullptr;
     const double* U = H.U + (size_t)b * H.kmax * H.kmax;
     // a warp per row of R_b: lane-strided partial sums (coalesced), then a fixed butterfly
     for (int a = warp; a < kf; a += nw) {
       double acc = 0.0;
-      for (int64_t c = lane; c < nc; c += 32) acc = fma(R[(int64_t)a * nc + c], x[c0 + c], acc);
+      const int64_t ia = MF ? r0 + min((int64_t)max(Ib[a], 0), nr - 1) : 0;
+      for (int64_t c = lane; c < nc; c += 32) {
+        const double r = MF ? w_entry(P, ia, c0 + c) : R[(int64_t)a * nc + c];
+        acc = fma(r, x[c0 + c], acc);
+      }
       for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
       if (lane == 0) t1[a] = acc;
     }
@@ -53,8 +64,10 @@ __global__ void __launch_bounds__(256) hm_t_kernel(lra_hmatrix H, const double* 
   }
 }
 
-// Pass 2a: one CTA per (level, target box) group, a thread per row.
-__global__ void __launch_bounds__(256) hm_far_kernel(lra_hmatrix H, const double* __restrict__ t,
+// Pass 2a: one CTA per (level, target box) group, a thread per row.  MF: C_b[i][a]
+// = w(r0 + i, c0 + J_b[a]) from the points (the batch's gathered value).
+template <bool MF>
+__global__ void __launch_bounds__(256) hm_far_kernel(DevProblem P, lra_hmatrix H, const double* __restrict__ t,
                                                      double* __restrict__ ylev) {
   for (int g = blockIdx.x; g < H.nfar_groups; g += gridDim.x) {
     const int64_t* G = H.far_groups + 5 * (size_t)g;
@@ -70,9 +83,17 @@ __global__ void __launch_bounds__(256) hm_far_kernel(lra_hmatrix H, const double
         const int64_t br0 = H.far[4 * (size_t)b], bnr = H.far[4 * (size_t)b + 1];
         if (br0 != r0 || bnr != nr) continue;             // a block of another box: not this group's
         const int kf = hm_kf(H, b);
-        const double* C = H.C + H.far_offsets[2 * (size_t)b];
         const double* tb = t + (size_t)b * H.kmax;
-        for (int a = 0; a < kf; ++a) acc = fma(C[i * kf + a], tb[a], acc);
+        if (MF) {
+          const int64_t bc0 = H.far[4 * (size_t)b + 2], bnc = H.far[4 * (size_t)b + 3];
+          if (bc0 < 0 || bnc < 1 || bc0 + bnc > H.n) continue;
+          const int32_t* Jb = H.J + (size_t)b * H.kmax;
+          for (int a = 0; a < kf; ++a)
+            acc = fma(w_entry(P, r0 + i, bc0 + min((int64_t)max(Jb[a], 0), bnc - 1)), tb[a], acc);
+        } else {
+          const double* C = H.C + H.far_offsets[2 * (size_t)b];
+          for (int a = 0; a < kf; ++a) acc = fma(C[i * kf + a], tb[a], acc);
+        }
       }
       yl[r0 + i] = acc;
     }
@@ -135,8 +156,9 @@ static lra_status hm_check(const lra_hmatrix* H) {
   if (H == nullptr || H->n < 1 || H->levels < 2 || H->kmax < 1 || H->kmax > KMAX || H->nfar < 0 ||
       H->nfar_groups < 0 || H->nnear < 0 || H->nnear_groups < 0)
     return LRA_ERR_INVALID_ARG;
-  if (H->nfar > 0 && (!H->far || !H->far_offsets || !H->C || !H->U || !H->R || !H->info || !H->far_groups))
-    return LRA_ERR_INVALID_ARG;
+  if (H->nfar > 0 && (!H->far || !H->far_offsets || !H->U || !H->info || !H->far_groups)) return LRA_ERR_INVALID_ARG;
+  // stored factors, or matrix-free from the generators' rows and columns
+  if (H->nfar > 0 && !((H->C && H->R) || (!H->C && !H->R && H->I && H->J))) return LRA_ERR_INVALID_ARG;
   if (H->nnear > 0 && (!H->near || !H->near_groups)) return LRA_ERR_INVALID_ARG;
   return LRA_OK;
 }
@@ -183,13 +205,17 @@ lra_status lra_hmatvec(const lra_problem* prob, const lra_hmatrix* H, const doub
   const lra_hmatrix Hv = *H;
   const int cap = dev.sms * 8;
   if (H->nfar > 0) {
+    const bool mf = H->C == nullptr;
     {
       LaunchScope ls(stream, "hm_t_kernel");
-      hm_t_kernel<<<std::min(H->nfar, cap), 256, 0, stream>>>(Hv, x, t);
+      if (mf) hm_t_kernel<true><<<std::min(H->nfar, cap), 256, 0, stream>>>(P, Hv, x, t);
+      else hm_t_kernel<false><<<std::min(H->nfar, cap), 256, 0, stream>>>(P, Hv, x, t);
     }
     {
       LaunchScope ls(stream, "hm_far_kernel");
-      hm_far_kernel<<<std::max(1, std::min(H->nfar_groups, cap)), 256, 0, stream>>>(Hv, t, parts + H->n);
+      const int grid = std::max(1, std::min(H->nfar_groups, cap));
+      if (mf) hm_far_kernel<true><<<grid, 256, 0, stream>>>(P, Hv, t, parts + H->n);
+      else hm_far_kernel<false><<<grid, 256, 0, stream>>>(P, Hv, t, parts + H->n);
     }
   }
   if (H->nnear_groups > 0) {

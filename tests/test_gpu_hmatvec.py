@@ -92,3 +92,50 @@ def test_benchmark_size_sampled_blocks_and_rows():
     rows = rng.choice(p.m, 256, replace=False)
     y_d = direct_rows(p.X, x, rows)
     assert np.linalg.norm(y[rows] - y_d) <= 2e-6 * np.linalg.norm(y_d)
+
+
+@pytest.mark.parametrize("entries", ["f64", "f32"])
+def test_matrix_free_matvec_equals_stored_factors(entries):
+    """The matrix-free form (the batch keeps only I, J and U; C_b and R_b are
+    re-evaluated from the points on every call) gives the stored form's y bit
+    for bit, on FP64 and FP32 kernel entries (2^16 points, 128-point leaves)."""
+    import paper_1710_07946_gb300 as lra
+    p, far, near, L = li.fmm_partition(1 << 16, leaf=128, seed=4)
+    X = torch.from_numpy(p.X).cuda()
+    prob = lra.Problem.kernel("laplace", X, X, entries=entries)
+    I0 = li.block_initial_rows(far[:, :4], 64, 5)
+    stored = lra.HMatrix(prob, far, near, L, I0, k=64)
+    free = lra.HMatrix(prob, far, near, L, I0, k=64, matrix_free=True)
+    assert "C" not in free.batch.out and "R" not in free.batch.out
+    stored.build()
+    free.build()
+    x = torch.from_numpy(li.rhs(p.m, 1, 11)[:, 0]).cuda()
+    y1 = stored.matvec(x)
+    y2 = free.matvec(x)
+    torch.cuda.synchronize()
+    for key in ("I", "J", "U", "info"):
+        assert torch.equal(stored.batch.out[key], free.batch.out[key]), key
+    assert torch.equal(y1, y2)
+
+
+def test_matrix_free_matvec_at_two_to_the_twenty_points():
+    """FMM stage (iii) on 2^20 uniform points (1024-point leaves: far blocks of
+    levels 2..4 with 16k-, 2k- and 256-point boxes, 640k generator runs in one
+    batched launch, FP32 kernel entries): the matrix-free matvec against the
+    direct product on 256 sampled rows.  The generators hold every block to
+    1e-6 (tolerance and staged sizes of the FMM batch), so the matvec's
+    relative error is of that order; 2e-6 is asserted."""
+    import paper_1710_07946_gb300 as lra
+    p, far, near, L = li.fmm_partition(1 << 20, leaf=1024, seed=1)
+    assert L == 4 and len(far) > 600000
+    X = torch.from_numpy(p.X).cuda()
+    prob = lra.Problem.kernel("laplace", X, X, entries="f32")
+    hm = lra.HMatrix(prob, far, near, L, li.block_initial_rows(far[:, :4], 64, 2), k=64, matrix_free=True)
+    hm.build()
+    x = li.rhs(p.m, 1, 3)[:, 0]
+    y = hm.matvec(torch.from_numpy(x).cuda()).cpu().numpy()
+    info = hm.batch.out["info"].cpu().numpy()
+    assert np.all((info[:, 3] == 0) | (info[:, 3] >= 16))
+    rows = np.random.default_rng(4).choice(p.m, 256, replace=False)
+    y_d = np.concatenate([direct_rows(p.X, x, rows[i:i + 4]) for i in range(0, 256, 4)])
+    assert np.linalg.norm(y[rows] - y_d) <= 2e-6 * np.linalg.norm(y_d)
