@@ -823,14 +823,15 @@ class HMatvecWorkload:
     unit = "matvec/s"
     kernel = "hm_far_kernel"
 
-    def __init__(self, npts=1 << 16, leaf=128, k=64, matrix_free=False, entries="f64"):
+    def __init__(self, npts=1 << 16, leaf=128, k=64, matrix_free=False, entries="f64", max_block=None):
         self.npts, self.leaf, self.k, self.matrix_free, self.entries = npts, leaf, k, matrix_free, entries
+        self.max_block = max_block
         size = f"{npts >> 20}M" if npts >= 1 << 20 else f"{npts // 1024}K"
         self.name = (f"hmatvec_laplace_{size}_uniform_cube_leaf{leaf}_k28-40-64_tol1e-6" +
                      ("_matrixfree" if matrix_free else "") + (f"_{entries}entries" if entries != "f64" else ""))
 
     def host(self, rank):
-        p, far, near, L = li.fmm_partition(self.npts, leaf=self.leaf, seed=rank)
+        p, far, near, L = li.fmm_partition(self.npts, leaf=self.leaf, seed=rank, max_block=self.max_block)
         I0 = li.block_initial_rows(far[:, :4], self.k, 1 + rank)
         x = li.rhs(p.m, 1, 2 + rank)[:, 0]
         rows = li.rng(3).choice(p.m, 256, replace=False)
@@ -1647,7 +1648,7 @@ WORKLOADS = {
     "hmatvec_laplace_64K": HMatvecWorkload,
     "hmatvec_laplace_8K": lambda: HMatvecWorkload(npts=1 << 13),
     "hmatvec_laplace_1M_matrixfree": lambda: HMatvecWorkload(npts=1 << 20, leaf=1024, matrix_free=True,
-                                                             entries="f32"),
+                                                             entries="f32", max_block=8192),
     "levca_n1000_r10_k40_expected": lambda: LevCaWorkload(kind=1),
     "levca_n1000_r10_k40_uniform": lambda: LevCaWorkload(kind=2),
     "hmt11_n1024_k39_bidiag20_onthefly": lambda: Hmt11Workload(materialize=False),

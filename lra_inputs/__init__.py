@@ -337,7 +337,21 @@ def fmm_blocks(npts: int = 1 << 20, leaf: int = 64, min_size: int = 64, max_size
     return prob, blocks, levels
 
 
-def fmm_partition(npts: int = 1 << 16, leaf: int = 128, seed: int = 0):
+def _pieces(start: int, count: int, max_len):
+    """[start, start + count) as consecutive pieces of at most max_len (nearly equal)."""
+    if max_len is None or count <= max_len:
+        return [(start, count)]
+    npc = -(-count // max_len)
+    base, extra = divmod(count, npc)
+    out, o = [], start
+    for i in range(npc):
+        sz = base + (1 if i < extra else 0)
+        out.append((o, sz))
+        o += sz
+    return out
+
+
+def fmm_partition(npts: int = 1 << 16, leaf: int = 128, seed: int = 0, max_block=None):
     """The complete far/near partition of the Laplace matrix K(P, P) over npts
     uniform points in [0,1]^3 (the octree and interaction lists of fmm_blocks,
     every level, no sampling): the points sorted by the Morton code of their
@@ -350,7 +364,12 @@ def fmm_partition(npts: int = 1 << 16, leaf: int = 128, seed: int = 0):
     Returns (Problem over the sorted points, far int64 (nf, 6) = (row0, nrows,
     col0, ncols, level, target box), near int64 (nn, 5) = (row0, nrows, col0,
     ncols, target leaf), levels L).  Far blocks are ordered by level, then
-    target box, then source box; near blocks by target leaf, then source leaf."""
+    target box, then source box; near blocks by target leaf, then source leaf.
+
+    max_block (optional): far blocks with more rows or columns than this are cut
+    into nearly equal row and column pieces (a sub-block of a well-separated
+    pair is still well separated, and the pieces cover the block once); a row
+    piece becomes a target of its own, with the id 64 box + piece."""
     g = rng(seed)
     P = g.random((npts, 3))
     L = 1
@@ -404,8 +423,14 @@ def fmm_partition(npts: int = 1 << 16, leaf: int = 128, seed: int = 0):
                                     sc = c2c[sx, sy, sz]
                                     if counts[sc] > 0:
                                         srcs.append(int(sc))
-            for sc in sorted(srcs):
-                far.append((starts[c], counts[c], starts[sc], counts[sc], lev, c))
+            if max_block is None:
+                for sc in sorted(srcs):
+                    far.append((starts[c], counts[c], starts[sc], counts[sc], lev, c))
+            else:
+                for pi, (r0, nr) in enumerate(_pieces(int(starts[c]), int(counts[c]), max_block)):
+                    for sc in sorted(srcs):
+                        for c0, nc in _pieces(int(starts[sc]), int(counts[sc]), max_block):
+                            far.append((r0, nr, c0, nc, lev, 64 * c + pi))
     starts, counts, bx, by, bz, c2c = level_boxes(L)
     n = 1 << L
     near = []

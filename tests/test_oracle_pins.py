@@ -1079,6 +1079,27 @@ def test_fmm_partition_covers_every_entry_once_and_far_blocks_are_separated():
     assert set(far[:, 4]) == set(range(2, L + 1))
 
 
+def test_fmm_partition_with_cut_far_blocks_still_covers_once():
+    """Far blocks cut into row and column pieces of at most max_block keep the
+    exact cover, each piece stays well separated, and a row piece is a target
+    group of its own (consecutive blocks, one row range per (level, target))."""
+    p, far, near, L = li.fmm_partition(1 << 12, leaf=32, seed=1, max_block=40)
+    assert far[:, 1].max() <= 40 and far[:, 3].max() <= 40
+    cov = np.zeros((p.m, p.m), dtype=np.int32)
+    for r0, nr, c0, nc, lev, tb in far:
+        cov[r0:r0 + nr, c0:c0 + nc] += 1
+        A, B = p.X[r0:r0 + nr], p.X[c0:c0 + nc]
+        assert np.max(np.maximum(A.min(0) - B.max(0), B.min(0) - A.max(0))) >= 2.0 ** -lev - 1e-12
+    for r0, nr, c0, nc, tb in near:
+        cov[r0:r0 + nr, c0:c0 + nc] += 1
+    assert cov.min() == 1 and cov.max() == 1
+    keys = [(int(a), int(b)) for a, b in far[:, 4:6]]
+    starts = [i for i in range(len(keys)) if i == 0 or keys[i] != keys[i - 1]]
+    assert len(starts) == len(set(keys))                     # every group contiguous
+    for i0, i1 in zip(starts, starts[1:] + [len(far)]):
+        assert len({(int(r0), int(nr)) for r0, nr in far[i0:i1, :2]}) == 1
+
+
 def _direct(P, x):
     d = np.sqrt(((P[:, None, :] - P[None, :, :]) ** 2).sum(axis=2))
     with np.errstate(divide="ignore"):
