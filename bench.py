@@ -1944,7 +1944,8 @@ def run_lib(args, wl):
         fp32 = getattr(wl, "peak_name", "fp64") == "fp32"
         if bound == "hbm":
             achieved, peak, runit = flops / kavg / 1e9, float(peaks.get("hbm_gbs") or 6800.0), "GB/s"
-            peak_src = "measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"
+            peak_src = ("measured HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)" if peaks.get("hbm_gbs") else
+                        "fallback 6.8 TB/s (MEASURED_PEAKS.json absent on this machine)")
         else:
             achieved = flops / kavg / 1e12
             peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
