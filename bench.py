@@ -263,9 +263,11 @@ class FmmWorkload:
         st = d["stats"].cpu().numpy()
         ok = (info[:, 3] == 0) | (info[:, 3] >= 16)
         good = ok & (st[:, 4] <= ERR_BOUND)
-        return dict(units=int(good.sum()), info=info, err=st[:, 4])
+        return dict(units=int(good.sum()), info=info, err=st[:, 4], work=float(d["bt"].work.sum().item()))
 
-    def flops(self, h, res):
+    def flops_lower_bound(self, h, res):
+        """The host-side model from the info counters alone (stages' loops and swaps not known
+        separately: the extra loops and all swaps charged to the smallest stage)."""
         b, info = h["blocks"], res["info"]
         f = 0.0
         for (r0, nr, c0, nc), inf in zip(b, info):
@@ -274,9 +276,15 @@ class FmmWorkload:
                               max(int(inf[2]), 1), int(inf[1]), LAPLACE_FLOPS)
         return f
 
+    def flops(self, h, res):
+        # every stage's maxvol steps and nuclei as counted by the kernel itself (lra_cur_batch.work)
+        return res["work"] if res.get("work") else self.flops_lower_bound(h, res)
+
     def extra(self, res):
         info, err = res["info"], res["err"]
-        return {"cta_shape_tuner": getattr(self, "tuned", None),"rank_min_median_max": [int(info[:, 0].min()), int(np.median(info[:, 0])), int(info[:, 0].max())],
+        return {"cta_shape_tuner": getattr(self, "tuned", None),
+                "flops_per_step_counted_by_kernel": res.get("work"),
+                "rank_min_median_max": [int(info[:, 0].min()), int(np.median(info[:, 0])), int(info[:, 0].max())],
                 "generator_size_hist": {int(k): int(c) for k, c in zip(*np.unique(info[:, 6], return_counts=True))},
                 "swaps_mean": float(info[:, 1].mean()), "loops_hist": np.bincount(info[:, 2]).tolist(),
                 "rel_fro_err_sampled_median": float(np.median(err)), "rel_fro_err_sampled_max": float(err.max()),

@@ -406,6 +406,10 @@ typedef struct {
   double* R;               /* packed R_b (NULL with C)                                    */
   double* logvol;          /* nb x 2*sweeps                                               */
   int32_t* info;           /* nb x LRA_INFO_LEN (as lra_cur.info)                          */
+  double* work;            /* nb, or NULL: lra_ca_run_batched writes the algorithmic flops
+                              of each block's run (every stage's maxvol steps -- LU,
+                              back substitution, swaps, entries, fma = 2 -- and 5 k^3
+                              per nucleus), for roofline accounting                    */
 } lra_cur_batch;
 
 /* Workspace bytes of lra_ca_run_batched (params: par->k is the largest rank),

@@ -66,7 +66,7 @@ class _Batch(ct.Structure):
 
 class _CurBatch(ct.Structure):
     _fields_ = [("I", ct.c_void_p), ("J", ct.c_void_p), ("C", ct.c_void_p), ("U", ct.c_void_p),
-                ("R", ct.c_void_p), ("logvol", ct.c_void_p), ("info", ct.c_void_p)]
+                ("R", ct.c_void_p), ("logvol", ct.c_void_p), ("info", ct.c_void_p), ("work", ct.c_void_p)]
 
 
 class _HMatrix(ct.Structure):
@@ -594,9 +594,11 @@ class Batch:
         self.cb.blocks, self.cb.offsets = self.blocks.data_ptr(), self.offs.data_ptr()
         self.cb.order = self.order.data_ptr() if self.order is not None else None
         self.cb.nb, self.cb.max_len = nb, int(max(blocks[:, 1].max(), blocks[:, 3].max()))
+        self.work = torch.zeros(nb, dtype=torch.float64, device=dev)   # per-block algorithmic flops
         self.cur = _CurBatch()
         for f in ("I", "J", "C", "U", "R", "logvol", "info"):
             setattr(self.cur, f, self.out[f].data_ptr() if f in self.out else None)
+        self.cur.work = self.work.data_ptr()
         self.pc = problem._c()
         L = _load()
         nbytes = ct.c_size_t()

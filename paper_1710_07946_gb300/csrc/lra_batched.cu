@@ -284,6 +284,7 @@ lra_status batched_launch(const DevProblem& P, const lra_batch* batch, const lra
   A.J = out->J;
   A.C = out->C;
   A.R = out->R;
+  A.work = out->work;
   A.U = out->U;
   A.logvol = out->logvol;
   A.info = out->info;

@@ -29,6 +29,7 @@ struct BatchArgs {
   double* U;                // nb x kmax x kmax (k_b x k_b at the start of each slot)
   double* logvol;           // nb x 2 sweeps
   int32_t* info;            // nb x LRA_INFO_LEN
+  double* work;             // nb: algorithmic flops of each block's run, or null
   unsigned int* counter;    // work queue head
   double* scratch;          // per CTA: G (kmax^2) then, if needed, a strip (kmax x max_len)
   size_t scratch_stride;    // doubles per CTA
@@ -46,6 +47,7 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_b;
   __shared__ int32_t s_I0[KMAX];
+  __shared__ double s_work;
   double* G = B.scratch + (size_t)blockIdx.x * B.scratch_stride;
   double* gstrip = G + (size_t)B.kmax * B.kmax;
   for (;;) {
@@ -93,6 +95,8 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
     A.chunk_m = (int)nr;
     A.ldm = (int)max(nr, nc);
     A.mixed = B.mixed;
+    if (threadIdx.x == 0) s_work = 0.0;
+    A.work = B.work ? &s_work : nullptr;
     if (B.mixed && A.P.src == LRA_KERNEL_LAPLACE) {
       A.P.X32 = B.base.X32 + 3 * r0;
       A.P.Y32 = B.base.Y32 + 3 * c0;
@@ -116,6 +120,7 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
       swaps += info[1]; loops += info[2]; n32 += info[4]; n64 += info[5];
       if (st != LRA_OK && st < 16) break;
       r = nucleus_cta(G, k, B.rank_tol, B.U + (size_t)b * B.kmax * B.kmax, smem);
+      if (threadIdx.x == 0) s_work += 5.0 * k * k * k;          // the nucleus, nominal
       if (r < k && st == LRA_OK) st = LRA_WARN_RANK_DEFICIENT;
       if (k >= kb || r < k - B.margin) break;
       int kn = k;
@@ -139,6 +144,7 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
       info[0] = (st != LRA_OK && st < 16) ? 0 : r;
       info[1] = swaps; info[2] = loops; info[3] = st;
       info[4] = n32; info[5] = n64; info[6] = k; info[7] = k;
+      if (B.work) B.work[b] = s_work;
     }
     __syncthreads();
   }

@@ -43,7 +43,27 @@ struct CaArgs {
   int32_t chunk_n, chunk_m, ldm;
   int32_t strip_in_smem;
   int32_t mixed;       // try the FP32 certified step first (single-CTA groups)
+  double* work = nullptr;   // if set (lead CTA, thread 0): += the algorithmic flops of each maxvol step
 };
+
+// Nominal FP64 flops of one kernel entry of the problem (dense: none).
+__host__ __device__ inline double entry_flops(const DevProblem& P) {
+  return P.src == LRA_DENSE ? 0.0 : (P.src == LRA_KERNEL_LAPLACE ? 8.0 : 10.0);
+}
+
+// Algorithmic flops of one maxvol step on a k x len strip (fma = 2, reciprocal
+// or division = 1) with nsw swaps: the LU (cold: with column pivoting over the
+// strip; warm: of B, then replayed on the other columns -- the same count
+// (len - k) k (k - 1) / 2 + (k - 1) k (2k - 1) / 6 fmas), the back substitution
+// (len - k) k (k - 1) / 2 fmas and (len - k) k + 2k reciprocals and products,
+// each swap 2 (k - 1) len + len, and the strip's entries (plus B's when warm).
+__host__ __device__ inline double maxvol_step_flops(int k, int64_t len, bool cold, int nsw, double ent) {
+  const double K = k, L = (double)len;
+  const double lu = (L - K) * K * (K - 1) / 2 + (K - 1) * K * (2 * K - 1) / 6;
+  const double bs = (L - K) * K * (K - 1) / 2;
+  const double div = (L - K) * K + 2 * K;
+  return 2 * (lu + bs) + div + nsw * (2 * (K - 1) * L + L) + ent * (K * L + (cold ? 0.0 : K * K));
+}
 
 struct Cert;           // lra_mixed.cuh
 

@@ -64,11 +64,15 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
   unsigned long long seq = 0;
   int status = LRA_OK, err = LRA_OK, total = 0, loops = 0, n32 = 0, n64 = 0;
   for (int s = 0; s < A.sweeps; ++s) {
-    StepResult r0 = run_step<Group, MIXED>(grp, A, S, 0, s == 0 && A.J0 == nullptr, S.Js, seq, lead, n32, n64);
+    const bool cold0 = s == 0 && A.J0 == nullptr;
+    StepResult r0 = run_step<Group, MIXED>(grp, A, S, 0, cold0, S.Js, seq, lead, n32, n64);
+    if (A.work != nullptr && lead && tid == 0)
+      *A.work += maxvol_step_flops(k, pcols(P), cold0, r0.nswaps, entry_flops(P));
     if (r0.status != LRA_OK && r0.status < 16) { err = r0.status; break; }
     if (r0.status > status) status = r0.status;
     __syncthreads();
     StepResult r1 = run_step<Group, MIXED>(grp, A, S, 1, false, S.Is, seq, lead, n32, n64);
+    if (A.work != nullptr && lead && tid == 0) *A.work += maxvol_step_flops(k, P.m, false, r1.nswaps, entry_flops(P));
     if (r1.status != LRA_OK && r1.status < 16) { err = r1.status; break; }
     if (r1.status > status) status = r1.status;
     if (lead && tid == 0) { A.logvol[2 * s] = r0.logdet; A.logvol[2 * s + 1] = r1.logdet; }

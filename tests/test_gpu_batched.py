@@ -243,3 +243,32 @@ def test_bf16_laplace_entries_fmm_blocks():
     p, blocks, lev = li.fmm_blocks(npts=1 << 15, leaf=64, min_size=64, max_size=2048, nblocks=48, seed=6)
     p.entries = "bf16"
     run_batch_staged(p, blocks, (28, 40, 64), 2, 3, 1e-6, h=1.05)
+
+
+def test_kernel_counts_the_algorithmic_flops_of_each_block():
+    """lra_cur_batch.work: per block, every maxvol step's LU, back substitution,
+    reciprocals, swaps and entries plus 5 k^3 per nucleus.  On square blocks
+    without stages both phases of a loop see the same strip length, so the total
+    follows from the loop and swap counts alone: the first (cold) step, then warm
+    steps, each swap 2 (k - 1) n + n."""
+    import paper_1710_07946_gb300 as lra
+    p = li.factor_gaussian(1200, 12, 1e-3, seed=9)
+    blocks = np.array([[0, 300, 300, 300], [300, 500, 700, 500], [100, 64, 900, 64]], dtype=np.int64)
+    prob, _ = to_device(p)
+    k = 16
+    I0 = li.block_initial_rows(blocks, k, 3)
+    bt = lra.Batch(prob, blocks, k, 3, I0, rank_tol=1e-9)
+    lra.lra_ca_run_batched(bt)
+    work = bt.work.cpu().numpy()
+    info = bt.out["info"].cpu().numpy()
+
+    def step(k, n):
+        lu = (n - k) * k * (k - 1) / 2 + (k - 1) * k * (2 * k - 1) / 6
+        bs = (n - k) * k * (k - 1) / 2
+        return 2 * (lu + bs) + (n - k) * k + 2 * k
+
+    for b, (r0, nr, c0, nc) in enumerate(blocks):
+        loops, swaps = int(info[b, 2]), int(info[b, 1])
+        kb = min(k, nr)
+        expect = 2 * loops * step(kb, nr) + swaps * (2 * (kb - 1) * nr + nr) + 5.0 * kb ** 3
+        np.testing.assert_allclose(work[b], expect, rtol=1e-12)
