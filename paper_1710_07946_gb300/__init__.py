@@ -606,11 +606,13 @@ class Batch:
                                                ct.byref(nbytes)), "lra_ca_batched_workspace_size")
         self.workspace = _workspace(nbytes.value, dev)
 
-    def block(self, b: int) -> dict:
-        """Host copies of block b's results (for checks)."""
+    def block(self, b: int, host: Optional[dict] = None) -> dict:
+        """Host copies of block b's results (for checks).  ``host``: the batch's
+        outputs already copied to the host ({name: numpy array}), to avoid one
+        device read-back per block."""
         (r0, nr, c0, nc) = self.blocks_np[b]
         oc, orr = self.offs_np[b]
-        o = {key: v.cpu().numpy() for key, v in self.out.items()}
+        o = host if host is not None else {key: v.cpu().numpy() for key, v in self.out.items()}
         info = o["info"][b]
         kb = int(info[6]) if info[6] > 0 else int(self.kb[b])
         return dict(I=o["I"][b, :kb], J=o["J"][b, :kb],

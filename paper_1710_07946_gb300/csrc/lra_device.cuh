@@ -93,8 +93,18 @@ __device__ __forceinline__ double w_entry(const DevProblem& P, int64_t i, int64_
 // the sum is scaled once.  Sparse: nnz signed terms in ascending stored order,
 // scaled once.  The terms are fetched TERMS at a time before they are added
 // (same order of additions), so their loads overlap.
+// The multiplier's column combination, out of line: the C-A kernels inline
+// wp_entry at every gather site, and only the no-multiplier case is hot there
+// (the batched kernels never have one); keeping the combinations in one called
+// function keeps them from crowding the registers of those sites.
+static __device__ __noinline__ double wp_entry_mult(const DevProblem& P, int64_t i, int64_t j);
+
 __device__ __forceinline__ double wp_entry(const DevProblem& P, int64_t i, int64_t j) {
   if (P.mkind == LRA_MULT_NONE) return w_entry(P, i, j);
+  return wp_entry_mult(P, i, j);
+}
+
+static __device__ __noinline__ double wp_entry_mult(const DevProblem& P, int64_t i, int64_t j) {
   const bool left = P.mside != 0;
   const int64_t mc = left ? i : j;                  // the column of M that combines the terms
   auto term = [&](int64_t r) -> double { return left ? w_entry(P, r, j) : w_entry(P, i, r); };

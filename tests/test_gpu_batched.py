@@ -222,13 +222,14 @@ def test_headline_fmm_configuration_every_block():
     gstats = d["stats"].cpu().numpy()
     p, blocks = h["p"], h["blocks"]
     assert len(blocks) == 4096
+    out = {key: v.cpu().numpy() for key, v in bt.out.items()}          # one read-back of the whole batch
     o_err = np.empty(len(blocks))
     for b in range(len(blocks)):
         r0, nr, c0, nc = (int(v) for v in blocks[b])
         sub = li.Problem(li.SRC_LAPLACE, nr, nc, X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc])
         sube = li.Problem(li.SRC_LAPLACE, nr, nc, X=sub.X, Y=sub.Y, entries="f32")
         o = oracle.ca_run_adaptive(sube, wl.stages, wl.margin, wl.sweeps, h["I0"][b], h=wl.h, rank_tol=wl.tol)
-        g = bt.block(b)
+        g = bt.block(b, out)
         assert g["k"] == o["k"], (b, g["k"], o["k"])
         check_block(o, g)
         o_err[b] = oracle.residual_sample(sub, o["C"], o["U"], o["R"], h["Q"][b], h["S"][b])[4]
