@@ -90,6 +90,7 @@ static lra_status make_plan(const DevProblem& P, const lra_ca_params* par, CaPla
     if (nblk >= dev.sms) return LRA_ERR_INVALID_ARG;
     nblk = std::min(dev.sms, nblk * 2);
   }
+  if (pl->nblk > 256) return LRA_ERR_INVALID_ARG;      // the grid exchange polls at most 8 slots a lane
   if (pl->nblk > 1) {
     int occ = 0;
     LRA_CUDA_TRY(cudaFuncSetAttribute(ca_kernel<GridGroup>, cudaFuncAttributeMaxDynamicSharedMemorySize,

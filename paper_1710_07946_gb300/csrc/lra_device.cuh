@@ -377,38 +377,64 @@ struct GridGroup {
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 32) {
       double* buf = slots + (size_t)(seq & 1ull) * nblk * SLOT;
-      if (lane == 0) {
+      {
+        // post: the warp writes the column (a lane per entry), then lane 0 the
+        // candidate and, after a fence and the warp barrier, the tag (release)
         double* me = buf + (size_t)blockIdx.x * SLOT;
         unsigned long long* mu = reinterpret_cast<unsigned long long*>(me);
         if (d.key != 0ull)
-          for (int a = 0; a < k; ++a) me[4 + a] = M[(int64_t)a * ldm + (d.j - q0)];
-        mu[0] = d.key;
-        reinterpret_cast<int2*>(me + 1)[0] = make_int2(d.i, d.j);
-        mu[2] = myflags;
-        st_release_u64(mu + 3, seq + 1ull);       // orders the slot before the tag
+          for (int a = lane; a < k; a += 32) me[4 + a] = M[(int64_t)a * ldm + (d.j - q0)];
+        if (lane == 0) {
+          mu[0] = d.key;
+          reinterpret_cast<int2*>(me + 1)[0] = make_int2(d.i, d.j);
+          mu[2] = myflags;
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) st_release_u64(mu + 3, seq + 1ull);       // orders the slot before the tag
       }
       Cand best = cand_none();
       unsigned long long f = 0;
       int fail = 0;
-      for (int r = lane; r < nblk && !fail; r += 32) {
-        const unsigned long long* sl = reinterpret_cast<const unsigned long long*>(buf + (size_t)r * SLOT);
+      // wait for all of this lane's slots (r = lane, lane + 32, ...) at once: their
+      // tags are polled together, so one round trip serves them all
+      constexpr int PER_LANE = 8;                   // slots per lane: nblk <= 256
+      unsigned ready = 0u, need = 0u;
+      for (int q = 0; q < PER_LANE; ++q)
+        if (lane + 32 * q < nblk) need |= 1u << q;
+      {
         unsigned long long t0 = 0;
         unsigned spins = 0;
-        while (ld_acquire_u64(sl + 3) != seq + 1ull) {
-          if ((++spins & 255u) == 0u) {
+        while (ready != need) {
+#pragma unroll
+          for (int q = 0; q < PER_LANE; ++q) {
+            const int r = lane + 32 * q;
+            if (((need & ~ready) >> q) & 1u) {
+              const unsigned long long* sl = reinterpret_cast<const unsigned long long*>(buf + (size_t)r * SLOT);
+              if (ld_acquire_u64(sl + 3) == seq + 1ull) ready |= 1u << q;
+            }
+          }
+          if (ready != need && (++spins & 63u) == 0u) {
             if (ld_relaxed_u32(abort) != 0u) { fail = 1; break; }
             const unsigned long long now = globaltimer_ns();
             if (t0 == 0) t0 = now;
             else if ((double)(now - t0) > WAIT_NS) { fail = 2; break; }
           }
         }
-        if (fail) break;
-        Cand c;
-        c.key = __ldcg(sl);
-        const int2 ij = __ldcg(reinterpret_cast<const int2*>(sl + 1));
-        c.i = ij.x; c.j = ij.y;
-        f |= __ldcg(sl + 2);
-        if (cand_better(c, best)) best = c;
+      }
+      if (!fail) {
+#pragma unroll
+        for (int q = 0; q < PER_LANE; ++q) {
+          const int r = lane + 32 * q;
+          if (r >= nblk) continue;
+          const unsigned long long* sl = reinterpret_cast<const unsigned long long*>(buf + (size_t)r * SLOT);
+          Cand c;
+          c.key = __ldcg(sl);
+          const int2 ij = __ldcg(reinterpret_cast<const int2*>(sl + 1));
+          c.i = ij.x; c.j = ij.y;
+          f |= __ldcg(sl + 2);
+          if (cand_better(c, best)) best = c;
+        }
       }
       if (fail == 2) atomicCAS(abort, 0u, (unsigned)LRA_ERR_TIMEOUT);
       fail = __any_sync(0xffffffffu, fail != 0);

@@ -82,7 +82,7 @@ __device__ inline void col_norms(const double* A, int ld, int t, int k, int j0, 
 
 // U (k x k, row-major, global or shared) <- pinv of the rank-r QRP truncation of
 // G (k x k row-major, global).  smem: nucleus_smem_bytes(k).  Returns r.
-__device__ inline int nucleus_cta(const double* G, int k, double tol, double* U, unsigned char* smem) {
+static __device__ __noinline__ int nucleus_cta(const double* G, int k, double tol, double* U, unsigned char* smem) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ld = nucleus_ld(k);
   double* A = reinterpret_cast<double*>(smem);          // column-major k x k, stride ld
