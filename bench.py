@@ -6,13 +6,13 @@ Default workload (``fmm``): the generators of an FMM / HSS matrix -- C-A CUR
 approximations of the 4096 well-separated block pairs of an octree over 2^20
 uniform points in [0,1]^3 (boxes of 64..2048 points, Laplace kernel evaluated
 on the fly, rank <= 64 adapted at tolerance 1e-6 with generator sizes staged
-28/40/64, 3 C-A loops), in the mixed form: kernel entries in FP32, pivots, LU,
+28/40/64, 2 C-A loops), in the mixed form: kernel entries in FP32, pivots, LU,
 swaps and nucleus in FP64.  One step = the batched C-A launch (all blocks,
 nuclei included) + the batched a-posteriori residual sample (16 x 16 entries
 per block, against the FP64 entries); the metric counts the blocks whose
 sampled relative Frobenius error is <= 1e-6.  The plain FP64 forms of the same
-batch (same sizes, and fixed k = 64) are measured in the same run and reported
-under config.comparisons.  Other workloads: ``fmm_f64``, ``fmm_fixedk``,
+batch (same sizes, and fixed k = 64) and the same form with 3 C-A loops are
+measured in the same run and reported under config.comparisons.  Other workloads: ``fmm_f64``, ``fmm_fixedk``,
 ``laplace65536_k*`` (one LRA of the 65536^2 Laplace kernel), ``dense8192_*``
 (one LRA of an 8192^2 FP32 input with a multiplier), ``tests{2,3,4}_*`` (the
 paper's random-input tests), ``gauss_apply`` (differentiable CUR apply).
@@ -157,7 +157,7 @@ class FmmWorkload:
     kernel = "ca_batched_kernel"
     unit = "LRA/s"
 
-    def __init__(self, npts=1 << 20, nblocks=4096, k=64, sweeps=3, tol=1e-6, q=16, s=16, entries="f64",
+    def __init__(self, npts=1 << 20, nblocks=4096, k=64, sweeps=2, tol=1e-6, q=16, s=16, entries="f64",
                  stages=(28, 40, 64), margin=2, h=1.05):
         self.npts, self.nblocks, self.k, self.sweeps, self.tol, self.q, self.s = npts, nblocks, k, sweeps, tol, q, s
         self.entries, self.stages, self.margin = entries, stages, margin
@@ -255,8 +255,10 @@ class FmmWorkload:
             return []
         kw = dict(npts=self.npts, nblocks=self.nblocks, k=self.k, sweeps=self.sweeps, tol=self.tol, q=self.q,
                   s=self.s, h=self.h)
+        kw3 = dict(kw, sweeps=3)
         return [("plain_fp64_same_sizes", type(self)(entries="f64", stages=self.stages, margin=self.margin, **kw)),
-                ("plain_fp64_fixed_k64", type(self)(entries="f64", stages=None, **kw))]
+                ("plain_fp64_fixed_k64", type(self)(entries="f64", stages=None, **kw)),
+                ("same_form_3_loops", type(self)(entries=self.entries, stages=self.stages, margin=self.margin, **kw3))]
 
     def check(self, d):
         info = d["bt"].out["info"].cpu().numpy()
