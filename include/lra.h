@@ -243,6 +243,16 @@ typedef struct {
   int32_t nstages;       /* 0 .. LRA_MAX_STAGES                                      */
   int32_t rank_margin;   /* >= 0                                                     */
   int32_t k_stages[8];   /* LRA_MAX_STAGES entries, the first nstages used           */
+  /* CTAs sharing one lra_ca_run / _warm / _noalloc (its strips split into that
+     many column chunks, one pivot exchange among them per elimination step and
+     swap): 0 = the library's choice (one per SM, at most one per 32 strip
+     columns), else a count clipped to the number of SMs (raised if a chunk's
+     scratch cannot fit a CTA's shared memory; mixed-mode runs of strips up to
+     2048 columns always take one CTA).  The pivots and outputs do not depend on
+     it.  A smaller grid leaves SMs to other work on the GPU; the default was
+     the fastest on every single-run workload measured.  Batched calls ignore
+     it.  Negative: LRA_ERR_INVALID_ARG.                                       */
+  int32_t ctas;
 } lra_ca_params;
 
 #define LRA_MAX_STAGES 8

@@ -56,7 +56,7 @@ class _Problem(ct.Structure):
 class _Params(ct.Structure):
     _fields_ = [("k", ct.c_int32), ("sweeps", ct.c_int32), ("h", ct.c_double), ("rank_tol", ct.c_double),
                 ("max_swaps", ct.c_int32), ("mode", ct.c_int32), ("nstages", ct.c_int32),
-                ("rank_margin", ct.c_int32), ("k_stages", ct.c_int32 * LRA_MAX_STAGES)]
+                ("rank_margin", ct.c_int32), ("k_stages", ct.c_int32 * LRA_MAX_STAGES), ("ctas", ct.c_int32)]
 
 
 class _Batch(ct.Structure):
@@ -337,10 +337,11 @@ def lra_gather_rows(problem: Problem, I: torch.Tensor, out: Optional[torch.Tenso
     return out
 
 
-def _params(k, sweeps, h, rank_tol, max_swaps, mode, stages=None, rank_margin=0) -> _Params:
+def _params(k, sweeps, h, rank_tol, max_swaps, mode, stages=None, rank_margin=0, ctas=0) -> _Params:
     p = _Params()
     p.k, p.sweeps, p.h, p.rank_tol, p.max_swaps, p.mode = int(k), int(sweeps), float(h), float(rank_tol), \
         int(max_swaps), int(mode)
+    p.ctas = int(ctas)
     if stages is not None:
         stages = [int(x) for x in stages]
         if not 1 <= len(stages) <= LRA_MAX_STAGES:
@@ -368,10 +369,10 @@ def _check_cur_out(out: dict, m: int, n: int, k: int, sweeps: int) -> None:
 
 def lra_ca_workspace_size(problem: Problem, k: int, sweeps: int = 3, h: float = 1.01, rank_tol: float = 1e-13,
                           max_swaps: int = 1000, mode: int = LRA_MODE_FP64,
-                          multiplier: Optional[Multiplier] = None) -> int:
+                          multiplier: Optional[Multiplier] = None, ctas: int = 0) -> int:
     L = _load()
     out = ct.c_size_t()
-    pc, pp = problem._c(), _params(k, sweeps, h, rank_tol, max_swaps, mode)
+    pc, pp = problem._c(), _params(k, sweeps, h, rank_tol, max_swaps, mode, ctas=ctas)
     _check(L.lra_ca_workspace_size(ct.byref(pc), ct.byref(pp), multiplier.handle if multiplier else None,
                                    ct.byref(out)), "lra_ca_workspace_size")
     return out.value
@@ -380,12 +381,14 @@ def lra_ca_workspace_size(problem: Problem, k: int, sweeps: int = 3, h: float = 
 def lra_ca_run(problem: Problem, I0: torch.Tensor, k: int, sweeps: int = 3, h: float = 1.01,
                rank_tol: float = 1e-13, max_swaps: int = 1000, mode: int = LRA_MODE_FP64,
                multiplier: Optional[Multiplier] = None, out: Optional[dict] = None,
-               workspace: Optional[torch.Tensor] = None, stream=None, J0: Optional[torch.Tensor] = None) -> dict:
+               workspace: Optional[torch.Tensor] = None, stream=None, J0: Optional[torch.Tensor] = None,
+               ctas: int = 0) -> dict:
     """C-A CUR approximation W ~ C U R of W' = W M (see lra_ca_run in lra.h).
 
     I0: device int32 tensor of k distinct initial rows; J0 (optional): k columns
     warm-starting the first column step (lra_ca_run_warm: resume from a previous
-    run's I, J).  Returns a dict of
+    run's I, J); ctas: CTAs sharing the run (0: the library's choice;
+    lra_ca_tune picks one by timing).  Returns a dict of
     device tensors I, J, C (m x k), U (k x k), R (k x n), logvol (2*sweeps),
     info (rank, swaps, loops, status); the call is asynchronous on ``stream``.
     Pass ``out`` (same dict layout) and ``workspace`` to reuse buffers."""
@@ -394,7 +397,7 @@ def lra_ca_run(problem: Problem, I0: torch.Tensor, k: int, sweeps: int = 3, h: f
     _dev(I0, torch.int32, "I0")
     if J0 is not None:
         _dev(J0, torch.int32, "J0")
-    pc, pp = problem._c(), _params(k, sweeps, h, rank_tol, max_swaps, mode)
+    pc, pp = problem._c(), _params(k, sweeps, h, rank_tol, max_swaps, mode, ctas=ctas)
     mh = multiplier.handle if multiplier else None
     if out is None:
         out = dict(I=torch.empty(k, dtype=torch.int32, device=dev), J=torch.empty(k, dtype=torch.int32, device=dev),

@@ -58,6 +58,7 @@ static lra_status validate_params(const DevProblem& P, const lra_ca_params* par)
   if (!(par->rank_tol >= 0.0) || !(par->rank_tol < 1.0)) return LRA_ERR_INVALID_ARG;
   if (par->mode != LRA_MODE_FP64 && par->mode != LRA_MODE_MIXED) return LRA_ERR_INVALID_ARG;
   if (par->nstages != 0) return LRA_ERR_INVALID_ARG;      // staged sizes: batched runs only
+  if (par->ctas < 0) return LRA_ERR_INVALID_ARG;
   return LRA_OK;
 }
 
@@ -69,6 +70,7 @@ static lra_status make_plan(const DevProblem& P, const lra_ca_params* par, CaPla
   const int64_t maxlen = std::max(P.m, pcols(P));
   int nblk = (int)std::min<int64_t>((maxlen + MIN_COLS_PER_CTA - 1) / MIN_COLS_PER_CTA, dev.sms);
   nblk = std::max(nblk, 1);
+  if (par->ctas > 0) nblk = std::min(par->ctas, dev.sms);     // the caller's (or the tuner's) choice
   // mixed mode runs its certified FP32 steps on one CTA: take the single-CTA plan
   // for strips up to MIXED_SOLO_MAX columns (larger runs stay on the FP64 grid)
   if (par->mode == LRA_MODE_MIXED && mixed_supported(P) && maxlen <= MIXED_SOLO_MAX) nblk = 1;
@@ -106,7 +108,7 @@ static lra_status make_plan(const DevProblem& P, const lra_ca_params* par, CaPla
   pl->off_strip = o;
   if (!pl->strip_in_smem) o = align_up(o + sizeof(double) * (size_t)pl->nblk * k * pl->ldm, 256);
   // mixed mode: single-CTA runs of dense or Laplace inputs (Laplace needs FP32 points)
-  pl->mixed = (par->mode == LRA_MODE_MIXED && pl->nblk == 1 && mixed_supported(P)) ? 1 : 0;
+  pl->mixed = (par->mode == LRA_MODE_MIXED && pl->nblk == 1 && mixed_supported(P) && maxlen <= MIXED_SOLO_MAX) ? 1 : 0;
   pl->off_pts = o;
   if (pl->mixed && P.src == LRA_KERNEL_LAPLACE) o = align_up(o + sizeof(float) * 3 * (size_t)(P.m + P.n), 256);
   pl->bytes = o;

@@ -57,3 +57,35 @@ def test_host_validation_without_gpu():
     # unsorted sparse rows
     rows = np.array([[1, 0]], dtype=np.int32).repeat(3, 0); s2 = np.ones((3, 2), np.int8)
     assert L.lra_precondition(ctypes.byref(h), 2, 0, 3, 2, rows.ctypes.data, s2.ctypes.data) == 1
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every ctypes mirror of a struct in include/lra.h has the C compiler's size
+    and field offsets (a field added on one side only would make the library
+    read the caller's arguments at the wrong places)."""
+    import shutil
+    import subprocess
+    import paper_1710_07946_gb300 as lra
+    if shutil.which("gcc") is None:
+        pytest.skip("no gcc")
+    mirrors = {"lra_problem": lra._Problem, "lra_ca_params": lra._Params, "lra_batch": lra._Batch,
+               "lra_cur_batch": lra._CurBatch, "lra_hmatrix": lra._HMatrix, "lra_gauss_blocks": lra._Gauss,
+               "lra_cur": lra._Cur}
+    lines = ['#include <stdio.h>', '#include "lra.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'  printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        s, f, v = line.split()
+        got[(s, f)] = int(v)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert got[(cname, f)] == getattr(py, f).offset, (cname, f)

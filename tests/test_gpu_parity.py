@@ -49,6 +49,21 @@ def test_dense_multi_cta_ragged(m, n, k):
     assert_parity(o, g)
 
 
+@pytest.mark.parametrize("ctas", [1, 2, 5, 19, 64, 152])
+def test_grid_size_does_not_change_results(ctas):
+    """The pivots, factors and counters are the oracle's whatever the number of
+    CTAs sharing the run (lra_ca_params.ctas): one CTA (the whole strip, in
+    global scratch), uneven chunks (5, 19) and the full grid; ARHT multiplier."""
+    p = li.factor_gaussian(3000, 22, 1e-4, seed=41)
+    p.W = np.ascontiguousarray(p.W[:2500, :])
+    p.m = 2500
+    li.with_arht(p, 2, seed=42)
+    I0 = li.initial_rows(2500, 20, 43)
+    o = oracle.ca_run(p, 20, 3, I0)
+    g = gpu_ca(p, 20, 3, I0, ctas=ctas)
+    assert_parity(o, g)
+
+
 @pytest.mark.parametrize("mult,arg", [("arht", 2), ("arht", 3), ("sparse", 4), ("bidiag", 3)])
 @pytest.mark.parametrize("m,n", [(3000, 700), (1024, 96)])
 def test_left_multipliers_tall_inputs(mult, arg, m, n):
@@ -228,6 +243,8 @@ def test_host_side_rejections():
         lra.lra_ca_run(prob, I0, 8, h=0.5)     # h < 1
     with pytest.raises(lra.LraError):
         lra.lra_ca_run(prob, I0, 8, workspace=torch.empty(16, dtype=torch.uint8, device="cuda"))
+    with pytest.raises(lra.LraError):
+        lra.lra_ca_run(prob, I0, 8, ctas=-1)
 
 
 def test_repeatable_and_stream_ordered():
