@@ -287,9 +287,6 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
     }
     __syncthreads();
     int fallback = 0;
-    // thread layout for the k x k elimination: column j = tid % 64, row group
-    // tid / 64 (shifts only; k <= 64)
-    const int jj = tid & (KMAX - 1), rg = tid >> 6, NRG = nt >> 6;
     for (int t = 0; t < k; ++t) {
       if (warp == 0) {
         // pivot row: largest |B(t)[p][t]| over p >= t, lowest p on ties; every
@@ -324,9 +321,16 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
       // multipliers l_p = B[p][t] * (1/pivot), kept in Lm for the replay below
       for (int p = t + 1 + tid; p < k; p += nt) S.Lm[p * ldl + t] = LU[p * ldl + t] * rp;
       __syncthreads();
-      if (jj > t && jj < k)
-        for (int p = t + 1 + rg; p < k; p += NRG)
-          LU[p * ldl + jj] = fma(-S.Lm[p * ldl + t], LU[t * ldl + jj], LU[p * ldl + jj]);
+      // trailing (k-t-1)^2 update, one entry per thread, consecutive threads
+      // along a row: every warp of the CTA takes a share, so all four SM
+      // sub-partitions' FP64 units work on it
+      {
+        const int w = k - t - 1;
+        for (int e = tid; e < w * w; e += nt) {
+          const int p = t + 1 + e / w, j = t + 1 + e % w;
+          LU[p * ldl + j] = fma(-S.Lm[p * ldl + t], LU[t * ldl + j], LU[p * ldl + j]);
+        }
+      }
       __syncthreads();
     }
     if (fallback) {
@@ -431,11 +435,12 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
         if (cm.G > 1) __syncwarp();
         if (act) {
           const double xi = M[(int64_t)i * ldm + c];
-          for (int p = cm.g; p < i; p += cm.G) {
-            double v = fma(-LU[p * ldl + i], xi, M[(int64_t)p * ldm + c]);
-            if (p == i - 1) v = v * S.rdiag[i - 1];
-            M[(int64_t)p * ldm + c] = v;
-          }
+          for (int p = cm.g; p < i; p += cm.G)
+            M[(int64_t)p * ldm + c] = fma(-LU[p * ldl + i], xi, M[(int64_t)p * ldm + c]);
+          // row i - 1 is complete: its owner scales it (one FP64 multiply per
+          // row, outside the loop, where a select would cost one per entry)
+          if (((i - 1) & (cm.G - 1)) == cm.g)
+            M[(int64_t)(i - 1) * ldm + c] = M[(int64_t)(i - 1) * ldm + c] * S.rdiag[i - 1];
         }
       }
       if (cm.G > 1) __syncwarp();
