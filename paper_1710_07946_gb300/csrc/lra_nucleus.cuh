@@ -24,7 +24,7 @@ namespace lra {
 // different columns hit different shared-memory banks.
 __host__ __device__ inline int nucleus_ld(int k) { return k | 1; }
 __host__ __device__ inline size_t nucleus_smem_bytes(int k) {
-  return sizeof(double) * (3 * (size_t)k * nucleus_ld(k) + 4 * (size_t)KMAX) + sizeof(int32_t) * 2 * KMAX + 64;
+  return sizeof(double) * (3 * (size_t)k * nucleus_ld(k) + 7 * (size_t)KMAX) + sizeof(int32_t) * 2 * KMAX + 64;
 }
 
 // Householder reflector of the column x[0..len) (unit stride, shared memory),
@@ -80,32 +80,87 @@ __device__ inline void col_norms(const double* A, int ld, int t, int k, int j0, 
   }
 }
 
+// Reflector scalars from alpha = x[0] and xn2 = x[1]^2 + ... (one ascending
+// fma chain, computed by the caller): beta = -sign(alpha) sqrt(alpha^2 + xn2),
+// tau = (beta - alpha) / beta, scal = 1 / (alpha - beta); tau = scal = 0 and
+// beta = alpha when xn2 = 0.  Called by a whole warp (the same operands in every
+// lane): lanes 0 and 1 take the two divisions in one instruction stream, so the
+// step costs one division's latency.  Lane 0 stores tau, scal, beta in bc.
+__device__ __forceinline__ void house_scalars_warp(double alpha, double xn2, double* bc) {
+  const int lane = threadIdx.x & 31;
+  double tau = 0.0, scal = 0.0, beta = alpha;
+  if (xn2 != 0.0) {
+    const double nrm = sqrt(fma(alpha, alpha, xn2));
+    beta = (alpha >= 0.0) ? -nrm : nrm;
+    const double num = (lane == 0) ? beta - alpha : 1.0;
+    const double den = (lane == 0) ? beta : alpha - beta;
+    const double q = num / den;
+    tau = __shfl_sync(0xffffffffu, q, 0);
+    scal = __shfl_sync(0xffffffffu, q, 1);
+  }
+  if (lane == 0) { bc[0] = tau; bc[1] = scal; bc[2] = beta; }
+}
+
 // U (k x k, row-major, global or shared) <- pinv of the rank-r QRP truncation of
 // G (k x k row-major, global).  smem: nucleus_smem_bytes(k).  Returns r.
+//
+// Every arithmetic operation, and the order of every inner product, is the one
+// the header comment states; what is parallel is only which thread runs which
+// chain when.  A warp's FP64 instruction costs its SM sub-partition the same
+// time whatever the number of active lanes, and one chain step costs that time,
+// so the work is laid out by sub-partition: the pivot-search norms run on warps
+// 0-1 while warps 2-3 run the norms the reflector needs (rows t+1..), the
+// reflector products with the columns of Q^T run on warps 2-3 while warps 0-1
+// run those with A's columns (Q^T is built during the QR, reflector by
+// reflector, in the same order as after it), and the rank-1 updates y -= c v
+// are spread over every thread.  CTAs of 64 threads run the second group's
+// chains after the first's.
 static __device__ __noinline__ int nucleus_cta(const double* G, int k, double tol, double* U, unsigned char* smem) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ld = nucleus_ld(k);
+  const int bbase = nt >= 128 ? 64 : 0;                // first thread of the second group
   double* A = reinterpret_cast<double*>(smem);          // column-major k x k, stride ld
   double* Q = A + (size_t)k * ld;                       // Q^T, column-major
   double* T = Q + (size_t)k * ld;                       // T^T (k x r), column-major
   double* taus = T + (size_t)k * ld;
   double* tz = taus + KMAX;
   double* nrm = tz + KMAX;
-  double* bc = nrm + KMAX;
+  double* nrm1 = nrm + KMAX;
+  double* cw = nrm1 + KMAX;                             // 2 KMAX: tau (v^T y) per column of A, then of Q^T
+  double* bc = cw + 2 * KMAX;
   int32_t* perm = reinterpret_cast<int32_t*>(bc + KMAX);
   int32_t* ctl = perm + KMAX;
 
   for (int it = tid; it < k * k; it += nt) {
-    int i = it / k, j = it - i * k;
+    const int i = it / k, j = it - i * k;
     A[j * ld + i] = G[it];
+    Q[j * ld + i] = (i == j) ? 1.0 : 0.0;
   }
   for (int j = tid; j < k; j += nt) perm[j] = j;
   __syncthreads();
   for (int t = 0; t < k; ++t) {
-    col_norms(A, ld, t, k, t, k - t, nrm);
+    const int nc = k - t;
+    // squared norms of columns t.. over rows t.. (pivot search) and over rows
+    // t+1.. (the reflector's ||x||^2 once the column is the pivot)
+    if (tid < nc) {
+      const double* col = A + (size_t)(t + tid) * ld;
+      double s = 0.0;
+      for (int i = t; i < k; ++i) s = fma(col[i], col[i], s);
+      nrm[t + tid] = s;
+    }
+    {
+      const int g = tid - bbase;
+      if (g >= 0 && g < nc) {
+        const double* col = A + (size_t)(t + g) * ld;
+        double s = 0.0;
+        for (int i = t + 1; i < k; ++i) s = fma(col[i], col[i], s);
+        nrm1[t + g] = s;
+      }
+    }
     __syncthreads();
     if (tid < 32) {
-      // largest squared norm, lowest column on ties (integer keys, one warp)
+      // largest squared norm, lowest column on ties (integer keys, one warp),
+      // then the reflector of the pivot column from its precomputed chain
       Cand c = cand_none();
       for (int j = t + tid; j < k; j += 32) cand_consider(c, mag_key(nrm[j]), 0, j);
       for (int off = 16; off > 0; off >>= 1) {
@@ -115,22 +170,61 @@ static __device__ __noinline__ int nucleus_cta(const double* G, int k, double to
         o.j = __shfl_down_sync(0xffffffffu, c.j, off);
         if (cand_better(o, c)) c = o;
       }
+      const int pj = __shfl_sync(0xffffffffu, (c.key == 0ull) ? t : c.j, 0);
+      house_scalars_warp(A[pj * ld + t], nrm1[pj], bc);
       if (tid == 0) {
-        const int pj = (c.key == 0ull) ? t : c.j;
         ctl[0] = pj;
-        if (pj != t) { int tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp; }
+        taus[t] = bc[0];
+        if (pj != t) { const int tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp; }
       }
     }
     __syncthreads();
     const int pj = ctl[0];
-    if (pj != t)
-      for (int i = tid; i < k; i += nt) {
-        double tmp = A[t * ld + i]; A[t * ld + i] = A[pj * ld + i]; A[pj * ld + i] = tmp;
+    const double tau = bc[0], scal = bc[1], beta = bc[2];
+    // interchange columns t and pj; column t becomes beta e_t + v (v scaled)
+    for (int i = tid; i < k; i += nt) {
+      const double at = A[t * ld + i], ap = A[pj * ld + i];
+      double nv = ap;
+      if (tau != 0.0) {
+        if (i > t) nv = ap * scal;
+        else if (i == t) nv = beta;
       }
+      A[t * ld + i] = nv;
+      if (pj != t) A[pj * ld + i] = at;
+    }
     __syncthreads();
-    const double tau = house_cta(&A[t * ld + t], k - t, bc);
-    if (tid == 0) taus[t] = tau;
-    apply_house_cols(&A[t * ld + t], tau, &A[t], ld, t + 1, k - t - 1, k - t);
+    if (tau == 0.0) continue;                           // H_t = I: nothing to apply (uniform)
+    const double* v = A + (size_t)t * ld;               // v[t] = 1 implicit, v[t+1..]
+    // w = y[t] + v[t+1] y[t+1] + ... (ascending chain), c = tau w: columns t+1..
+    // of A on the first group, the columns of Q^T on the second
+    if (t + 1 + tid < k) {
+      const double* y = A + (size_t)(t + 1 + tid) * ld;
+      double w = y[t];
+      for (int i = t + 1; i < k; ++i) w = fma(v[i], y[i], w);
+      cw[t + 1 + tid] = tau * w;
+    }
+    {
+      const int g = tid - bbase;
+      if (g >= 0 && g < k) {
+        const double* y = Q + (size_t)g * ld;
+        double w = y[t];
+        for (int i = t + 1; i < k; ++i) w = fma(v[i], y[i], w);
+        cw[KMAX + g] = tau * w;
+      }
+    }
+    __syncthreads();
+    // y[t] -= c, y[i] = fma(-c, v[i], y[i]): every thread, one entry at a time
+    {
+      const int na = k - t - 1, ncol = na + k;
+      for (int e = tid; e < ncol * nc; e += nt) {
+        const int cix = e / nc, i = t + (e - cix * nc);
+        double* y;
+        double c;
+        if (cix < na) { y = A + (size_t)(t + 1 + cix) * ld; c = cw[t + 1 + cix]; }
+        else { y = Q + (size_t)(cix - na) * ld; c = cw[KMAX + cix - na]; }
+        y[i] = fma(-c, (i == t) ? 1.0 : v[i], y[i]);     // i = t: y[t] - c, rounded once
+      }
+    }
     __syncthreads();
   }
   if (tid == 0) {
@@ -144,25 +238,47 @@ static __device__ __noinline__ int nucleus_cta(const double* G, int k, double to
   for (int it = tid; it < k * k; it += nt) U[it] = 0.0;
   if (r == 0) { __syncthreads(); return 0; }
 
-  // Q^T = H_{k-1} ... H_0 I, one column per thread
-  for (int j = tid; j < k; j += nt) {
-    for (int i = 0; i < k; ++i) Q[j * ld + i] = (i == j) ? 1.0 : 0.0;
-    for (int t = 0; t < k; ++t) apply_house_seq(&A[t * ld + t], taus[t], &Q[j * ld + t], k - t);
-  }
   if (r < k) {
     for (int it = tid; it < k * r; it += nt) {
-      int c = it / k, i = it - c * k;
+      const int c = it / k, i = it - c * k;
       T[c * ld + i] = (i >= c) ? A[i * ld + c] : 0.0;
     }
     __syncthreads();
+    // QR of T^T: reflector c from column c, applied to columns c+1..r-1
     for (int c = 0; c < r; ++c) {
-      const double tau = house_cta(&T[c * ld + c], k - c, bc);
-      if (tid == 0) tz[c] = tau;
-      for (int j = c + 1 + tid; j < r; j += nt) apply_house_seq(&T[c * ld + c], tau, &T[j * ld + c], k - c);
+      const int len = k - c;
+      double* x = T + (size_t)c * ld;
+      if (tid < 32) {
+        double xn2 = 0.0;
+        if (tid == 0)
+          for (int i = c + 1; i < k; ++i) xn2 = fma(x[i], x[i], xn2);
+        xn2 = __shfl_sync(0xffffffffu, xn2, 0);
+        house_scalars_warp(x[c], xn2, bc);
+        if (tid == 0) tz[c] = bc[0];
+      }
+      __syncthreads();
+      const double tau = bc[0], scal = bc[1], beta = bc[2];
+      if (tau == 0.0) { __syncthreads(); continue; }    // uniform; bc is rewritten next step
+      for (int i = c + 1 + tid; i < k; i += nt) x[i] = x[i] * scal;
+      if (tid == 0) x[c] = beta;
+      __syncthreads();
+      if (c + 1 + tid < r) {
+        const double* y = T + (size_t)(c + 1 + tid) * ld;
+        double w = y[c];
+        for (int i = c + 1; i < k; ++i) w = fma(x[i], y[i], w);
+        cw[c + 1 + tid] = tau * w;
+      }
+      __syncthreads();
+      const int na = r - c - 1;
+      for (int e = tid; e < na * len; e += nt) {
+        const int cix = e / len, i = c + (e - cix * len);
+        double* y = T + (size_t)(c + 1 + cix) * ld;
+        const double cc = cw[c + 1 + cix];
+        y[i] = fma(-cc, (i == c) ? 1.0 : x[i], y[i]);
+      }
       __syncthreads();
     }
   }
-  __syncthreads();
   // X = Z S^{-T} Q_r^T (or R^{-1} Q^T), one column per thread, in place in Q
   for (int col = tid; col < k; col += nt) {
     double* v = &Q[col * ld];
@@ -179,12 +295,34 @@ static __device__ __noinline__ int nucleus_cta(const double* G, int k, double to
         v[i] = s / T[i * ld + i];
       }
       for (int i = r; i < k; ++i) v[i] = 0.0;
-      for (int c = r - 1; c >= 0; --c) apply_house_seq(&T[c * ld + c], tz[c], &v[c], k - c);
     }
   }
   __syncthreads();
+  if (r < k) {
+    // v <- H'_0 ... H'_{r-1} v on every column: chains per column, updates by all threads
+    for (int c = r - 1; c >= 0; --c) {
+      const double tau = tz[c];
+      if (tau == 0.0) continue;                         // uniform
+      const double* x = T + (size_t)c * ld;
+      const int len = k - c;
+      if (tid < k) {
+        const double* y = Q + (size_t)tid * ld;
+        double w = y[c];
+        for (int i = c + 1; i < k; ++i) w = fma(x[i], y[i], w);
+        cw[tid] = tau * w;
+      }
+      __syncthreads();
+      for (int e = tid; e < k * len; e += nt) {
+        const int col = e / len, i = c + (e - col * len);
+        double* y = Q + (size_t)col * ld;
+        const double cc = cw[col];
+        y[i] = fma(-cc, (i == c) ? 1.0 : x[i], y[i]);
+      }
+      __syncthreads();
+    }
+  }
   for (int it = tid; it < k * k; it += nt) {
-    int i = it / k, col = it - i * k;
+    const int i = it / k, col = it - i * k;
     U[(size_t)perm[i] * k + col] = Q[col * ld + i];
   }
   __syncthreads();
