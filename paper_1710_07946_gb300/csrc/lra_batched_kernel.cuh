@@ -86,8 +86,11 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
     A.I0 = B.I0 + (size_t)b * B.kmax;
     A.I = B.I + (size_t)b * B.kmax;
     A.J = B.J + (size_t)b * B.kmax;
-    A.C = B.C ? B.C + B.offs[2 * (size_t)b] : nullptr;        // null: the factors are not stored
-    A.R = B.R ? B.R + B.offs[2 * (size_t)b + 1] : nullptr;
+    // the factors are written once, after the last stage (null: not stored)
+    double* const Cb = B.C ? B.C + B.offs[2 * (size_t)b] : nullptr;
+    double* const Rb = B.R ? B.R + B.offs[2 * (size_t)b + 1] : nullptr;
+    A.C = nullptr;
+    A.R = nullptr;
     A.logvol = B.logvol + (size_t)b * 2 * B.sweeps;
     A.info = info;
     A.G = G;
@@ -140,6 +143,18 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
       k = kn;
     }
     __syncthreads();
+    if (Cb != nullptr && Rb != nullptr && !(st != LRA_OK && st < 16)) {
+      // C_b = W'[:, J] (nr x k) and R_b = W[I, :] (k x nc) at the final size, from
+      // the final I, J that the last C-A run stored
+      for (int it = threadIdx.x; it < (int)nr * k; it += blockDim.x) {
+        const int c = it / k, a = it - c * k;
+        Cb[(int64_t)c * k + a] = c_entry(A.P, c, A.J[a]);
+      }
+      for (int it = threadIdx.x; it < k * (int)nc; it += blockDim.x) {
+        const int a = it / (int)nc, c = it - a * (int)nc;
+        Rb[(int64_t)a * nc + c] = r_entry(A.P, A.I[a], c);
+      }
+    }
     if (threadIdx.x == 0) {
       info[0] = (st != LRA_OK && st < 16) ? 0 : r;
       info[1] = swaps; info[2] = loops; info[3] = st;

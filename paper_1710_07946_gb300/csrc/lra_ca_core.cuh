@@ -304,9 +304,14 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
         const double rp = __shfl_sync(0xffffffffu, rsel, rl);
         if (lane == 0) {
           S.piv[t] = r;
-          S.bc[0] = (pv == 0.0) ? 0.0 : rp;
           S.ctl[1] = (pv == 0.0);
         }
+        // multipliers l_p = B[p][t] * (1/pivot) of the rows below t after the
+        // interchange (row r then holds row t's entry), kept in Lm for the replay
+        if (pv != 0.0)
+          for (int p = t + 1 + lane; p < k; p += 32)
+            S.Lm[p * ldl + t] = ((p == r) ? LU[t * ldl + t] : LU[p * ldl + t]) * rp;
+        __syncwarp();
         // interchange rows t and r in columns t.. only: column t' < t keeps the
         // multipliers of step t' in the row positions of that step, the order in
         // which they are replayed on the CTA's own columns below
@@ -317,10 +322,6 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
       }
       __syncthreads();
       if (S.ctl[1]) { fallback = 1; break; }          // same decision in every CTA
-      const double rp = S.bc[0];
-      // multipliers l_p = B[p][t] * (1/pivot), kept in Lm for the replay below
-      for (int p = t + 1 + tid; p < k; p += nt) S.Lm[p * ldl + t] = LU[p * ldl + t] * rp;
-      __syncthreads();
       // trailing (k-t-1)^2 update, one entry per thread, consecutive threads
       // along a row: every warp of the CTA takes a share, so all four SM
       // sub-partitions' FP64 units work on it
@@ -452,15 +453,18 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
       for (int a = mp.g; a < k; a += mp.G) M[(int64_t)a * ldm + c] = (S.pos[c] - 1 == a) ? 1.0 : 0.0;
   __syncthreads();
 
-  // ---- dominance swaps (Algorithm algdomin)
+  // ---- dominance swaps (Algorithm algdomin).  Each thread visits its entries
+  // column by column, rows ascending, so cand_take keeps the lowest (j, i) of
+  // equal keys; after the first scan, the search for the next swap runs inside
+  // the rank-1 update, on the values as they are written.
   const unsigned long long hkey = mag_key(A.h);
   int nsw = 0;
+  Cand mine = cand_none();
+  for (int c = mp.c0; c < qn; c += mp.cstep) {
+    if (S.pos[c]) continue;
+    for (int a = mp.g; a < k; a += mp.G) cand_take(mine, mag_key(M[(int64_t)a * ldm + c]), a, (int32_t)(q0 + c));
+  }
   for (;;) {
-    Cand mine = cand_none();
-    for (int c = mp.c0; c < qn; c += mp.cstep) {
-      if (S.pos[c]) continue;
-      for (int a = mp.g; a < k; a += mp.G) cand_consider(mine, mag_key(M[(int64_t)a * ldm + c]), a, (int32_t)(q0 + c));
-    }
     if (!grp.exchange(seq, mine, myflags, M, ldm, q0, k, chunk, S.xo)) {
       res.status = LRA_ERR_TIMEOUT;
       return res;
@@ -475,10 +479,18 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
     const double rcs = S.bc[0];
     for (int c = tid; c < qn; c += nt) S.tq[c] = M[(int64_t)w.i * ldm + c] * rcs;
     __syncthreads();
+    // the columns outside the selected set after this swap: the unselected ones
+    // but w.j, and the column leaving position w.i
+    const int64_t wjl = w.j - q0, oldl = (int64_t)Jsel[w.i] - q0;
+    mine = cand_none();
     for (int c = mp.c0; c < qn; c += mp.cstep) {
       const double tq = S.tq[c];
-      for (int p = mp.g; p < k; p += mp.G)
-        M[(int64_t)p * ldm + c] = (p == w.i) ? tq : fma(-S.x[p], tq, M[(int64_t)p * ldm + c]);
+      const bool cand = (c == oldl) || (S.pos[c] == 0 && c != wjl);
+      for (int p = mp.g; p < k; p += mp.G) {
+        const double v = (p == w.i) ? tq : fma(-S.x[p], tq, M[(int64_t)p * ldm + c]);
+        M[(int64_t)p * ldm + c] = v;
+        if (cand) cand_take(mine, mag_key(v), p, (int32_t)(q0 + c));
+      }
     }
     __syncthreads();
     if (w.j >= q0 && w.j < q0 + qn)

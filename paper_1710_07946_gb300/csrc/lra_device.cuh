@@ -238,6 +238,13 @@ __device__ __forceinline__ void cand_consider(Cand& best, unsigned long long key
   if (key != 0ull && cand_better(c, best)) best = c;
 }
 
+// cand_consider for a thread that visits its entries in ascending (j, i) order:
+// an equal key never replaces the earlier entry, which is the lower (j, i), so a
+// single 64-bit compare gives cand_consider's result.
+__device__ __forceinline__ void cand_take(Cand& best, unsigned long long key, int32_t i, int32_t j) {
+  if (key > best.key) best = Cand{key, i, j};
+}
+
 // Best candidate of the CTA (and the OR of the flags), returned to every thread.
 struct CandRed {
   Cand c[33];
