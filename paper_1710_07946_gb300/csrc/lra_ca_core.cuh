@@ -380,8 +380,9 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
     // ---- cold start: LU with column pivoting over the whole strip
     for (int t = 0; t < k; ++t) {
       Cand mine = cand_none();
+      unsigned bhi = 0;
       for (int c = tid; c < qn; c += nt)
-        if (S.pos[c] == 0) cand_consider(mine, mag_key(M[(int64_t)t * ldm + c]), 0, (int32_t)(q0 + c));
+        if (S.pos[c] == 0) cand_take_val(mine, bhi, M[(int64_t)t * ldm + c], 0, (int32_t)(q0 + c));
       if (!grp.exchange(seq, mine, myflags, M, ldm, q0, k, chunk, S.xo)) {
         res.status = LRA_ERR_TIMEOUT;
         return res;
@@ -460,9 +461,10 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
   const unsigned long long hkey = mag_key(A.h);
   int nsw = 0;
   Cand mine = cand_none();
+  unsigned bhi = 0;
   for (int c = mp.c0; c < qn; c += mp.cstep) {
     if (S.pos[c]) continue;
-    for (int a = mp.g; a < k; a += mp.G) cand_take(mine, mag_key(M[(int64_t)a * ldm + c]), a, (int32_t)(q0 + c));
+    for (int a = mp.g; a < k; a += mp.G) cand_take_val(mine, bhi, M[(int64_t)a * ldm + c], a, (int32_t)(q0 + c));
   }
   for (;;) {
     if (!grp.exchange(seq, mine, myflags, M, ldm, q0, k, chunk, S.xo)) {
@@ -483,13 +485,14 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
     // but w.j, and the column leaving position w.i
     const int64_t wjl = w.j - q0, oldl = (int64_t)Jsel[w.i] - q0;
     mine = cand_none();
+    bhi = 0;
     for (int c = mp.c0; c < qn; c += mp.cstep) {
       const double tq = S.tq[c];
       const bool cand = (c == oldl) || (S.pos[c] == 0 && c != wjl);
       for (int p = mp.g; p < k; p += mp.G) {
         const double v = (p == w.i) ? tq : fma(-S.x[p], tq, M[(int64_t)p * ldm + c]);
         M[(int64_t)p * ldm + c] = v;
-        if (cand) cand_take(mine, mag_key(v), p, (int32_t)(q0 + c));
+        if (cand) cand_take_val(mine, bhi, v, p, (int32_t)(q0 + c));
       }
     }
     __syncthreads();

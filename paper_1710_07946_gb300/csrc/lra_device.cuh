@@ -245,6 +245,18 @@ __device__ __forceinline__ void cand_take(Cand& best, unsigned long long key, in
   if (key > best.key) best = Cand{key, i, j};
 }
 
+// cand_take with a 32-bit pre-test: an entry whose |v| has a smaller high word
+// than the best's |v| cannot beat it, and most entries are rejected there.  bhi:
+// the high word of the best's |v| bits (0 while there is none).  NaN passes the
+// pre-test and is then refused (key 0), as by cand_take.
+__device__ __forceinline__ void cand_take_val(Cand& best, unsigned& bhi, double v, int32_t i, int32_t j) {
+  const unsigned h = (unsigned)__double2hiint(v) & 0x7fffffffu;
+  if (h >= bhi) {
+    const unsigned long long key = mag_key(v);
+    if (key > best.key) { best = Cand{key, i, j}; bhi = h; }
+  }
+}
+
 // Best candidate of the CTA (and the OR of the flags), returned to every thread.
 struct CandRed {
   Cand c[33];
@@ -334,16 +346,30 @@ struct ExchangeOut {
   CandRed* red;
 };
 
-// First half, common to all groups: the CTA's best candidate, in warp 0.
-__device__ __forceinline__ Cand cta_best_in_warp0(Cand mine, CandRed* red) {
+// warp_best for candidates of one CTA's columns (q0 <= j < q0 + 2^26, 0 <= i <
+// 64): the key's high word, then its low word, then the position (j - q0) * 64
+// + i -- the order of cand_better -- each reduced by one warp instruction.
+__device__ __forceinline__ Cand warp_best_local(Cand c, int64_t q0) {
+  const unsigned hi = (unsigned)(c.key >> 32), lo = (unsigned)c.key;
+  const unsigned mhi = __reduce_max_sync(0xffffffffu, hi);
+  const unsigned mlo = __reduce_max_sync(0xffffffffu, hi == mhi ? lo : 0u);
+  const unsigned pos = (c.key != 0ull && hi == mhi && lo == mlo) ? (unsigned)((c.j - q0) * 64 + c.i) : 0xffffffffu;
+  const unsigned mpos = __reduce_min_sync(0xffffffffu, pos);
+  if (mpos == 0xffffffffu) return cand_none();
+  return Cand{((unsigned long long)mhi << 32) | mlo, (int32_t)(mpos & 63u), (int32_t)(q0 + (mpos >> 6))};
+}
+
+// First half, common to all groups: the CTA's best candidate (its columns start
+// at q0), in warp 0.
+__device__ __forceinline__ Cand cta_best_in_warp0(Cand mine, CandRed* red, int64_t q0) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  mine = warp_best(mine);
+  mine = warp_best_local(mine, q0);
   if (lane == 0) red->c[warp] = mine;
   __syncthreads();
   Cand d = cand_none();
   if (warp == 0) {
     if (lane < (int)(blockDim.x >> 5)) d = red->c[lane];
-    d = warp_best(d);
+    d = warp_best_local(d, q0);
   }
   return d;       // meaningful in warp 0 only
 }
@@ -354,7 +380,7 @@ struct SoloGroup {
   __device__ __forceinline__ bool exchange(unsigned long long /*seq*/, Cand mine, unsigned long long myflags,
                                            const double* M, int ldm, int64_t q0, int k, int /*owner_chunk*/,
                                            const ExchangeOut& o) const {
-    const Cand d = cta_best_in_warp0(mine, o.red);
+    const Cand d = cta_best_in_warp0(mine, o.red, q0);
     if (threadIdx.x < 32) {
       if (threadIdx.x == 0) { *o.win = d; *o.flags = myflags; }
       if (d.key != 0ull)
@@ -380,7 +406,7 @@ struct GridGroup {
 
   __device__ bool exchange(unsigned long long seq, Cand mine, unsigned long long myflags, const double* M, int ldm,
                            int64_t q0, int k, int owner_chunk, const ExchangeOut& o) const {
-    const Cand d = cta_best_in_warp0(mine, o.red);
+    const Cand d = cta_best_in_warp0(mine, o.red, q0);
     const int lane = threadIdx.x & 31;
     if (threadIdx.x < 32) {
       double* buf = slots + (size_t)(seq & 1ull) * nblk * SLOT;
