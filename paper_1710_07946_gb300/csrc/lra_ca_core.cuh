@@ -296,7 +296,7 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
         const int p0 = t + lane, p1 = t + lane + 32;
         if (p0 < k) { const double v = LU[p0 * ldl + t]; cand_consider(c, mag_key(v), 0, p0); rc0 = 1.0 / v; }
         if (p1 < k) { const double v = LU[p1 * ldl + t]; cand_consider(c, mag_key(v), 0, p1); rc1 = 1.0 / v; }
-        c = warp_best(c);
+        c = warp_best_local(c, 0);                   // rows < 64 as positions: the order of cand_better
         const int r = (c.key == 0ull) ? t : c.j;
         const double pv = LU[r * ldl + t];
         const int rl = (r - t) & 31;
@@ -383,26 +383,28 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
       unsigned bhi = 0;
       for (int c = tid; c < qn; c += nt)
         if (S.pos[c] == 0) cand_take_val(mine, bhi, M[(int64_t)t * ldm + c], 0, (int32_t)(q0 + c));
-      if (!grp.exchange(seq, mine, myflags, M, ldm, q0, k, chunk, S.xo)) {
-        res.status = LRA_ERR_TIMEOUT;
-        return res;
-      }
+      grp.template exchange<false>(seq, mine, myflags, M, ldm, q0, k, chunk, S.xo);
       ++seq;
-      if (*S.flags & FLAG_NONFINITE) { res.status = LRA_ERR_NONFINITE; return res; }
-      const Cand w = *S.win;
-      if (tid == 0) {
-        Jsel[t] = w.j;
-        if (w.j >= q0 && w.j < q0 + qn) S.pos[w.j - q0] = t + 1;
+      if (warp == 0) {
+        // warp 0 holds the winner: the pivot's reciprocal, U0's column t and the
+        // multipliers of this elimination step
+        const Cand w = *S.win;
         const double pv = S.x[t];
-        S.bc[0] = (pv == 0.0) ? 0.0 : 1.0 / pv;
+        if (lane == 0) {
+          Jsel[t] = w.j;
+          if (w.j >= q0 && w.j < q0 + qn) S.pos[w.j - q0] = t + 1;
+        }
+        if (pv != 0.0) {
+          const double rp = 1.0 / pv;
+          for (int p = lane; p <= t; p += 32) LU[p * ldl + t] = S.x[p];
+          for (int p = t + 1 + lane; p < k; p += 32) S.lmul[p] = S.x[p] * rp;
+        }
       }
+      __syncthreads();
+      if (grp.failed(S.xo)) { res.status = LRA_ERR_TIMEOUT; return res; }
+      if (*S.flags & FLAG_NONFINITE) { res.status = LRA_ERR_NONFINITE; return res; }
       const double pv = S.x[t];
-      if (pv == 0.0) { deficient = true; __syncthreads(); continue; }
-      __syncthreads();
-      const double rp = S.bc[0];
-      for (int p = tid; p <= t; p += nt) LU[p * ldl + t] = S.x[p];
-      for (int p = t + 1 + tid; p < k; p += nt) S.lmul[p] = S.x[p] * rp;
-      __syncthreads();
+      if (pv == 0.0) { deficient = true; continue; }
       for (int c = mp.c0; c < qn; c += mp.cstep) {
         if (S.pos[c]) continue;
         const double mt = M[(int64_t)t * ldm + c];
@@ -467,17 +469,18 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
     for (int a = mp.g; a < k; a += mp.G) cand_take_val(mine, bhi, M[(int64_t)a * ldm + c], a, (int32_t)(q0 + c));
   }
   for (;;) {
-    if (!grp.exchange(seq, mine, myflags, M, ldm, q0, k, chunk, S.xo)) {
-      res.status = LRA_ERR_TIMEOUT;
-      return res;
-    }
+    grp.template exchange<false>(seq, mine, myflags, M, ldm, q0, k, chunk, S.xo);
     ++seq;
+    if (warp == 0) {                              // the reciprocal of the winner, before the barrier
+      const Cand w = *S.win;
+      if (w.key > hkey && lane == 0) S.bc[0] = 1.0 / S.x[w.i];
+    }
+    __syncthreads();
+    if (grp.failed(S.xo)) { res.status = LRA_ERR_TIMEOUT; return res; }
     if (*S.flags & FLAG_NONFINITE) { res.status = LRA_ERR_NONFINITE; return res; }
     const Cand w = *S.win;
     if (w.key <= hkey) break;                     // no |c| > h left (or no candidate)
     if (nsw >= A.max_swaps) { res.status = LRA_WARN_NOT_CONVERGED; break; }
-    if (tid == 0) S.bc[0] = 1.0 / S.x[w.i];
-    __syncthreads();
     const double rcs = S.bc[0];
     for (int c = tid; c < qn; c += nt) S.tq[c] = M[(int64_t)w.i * ldm + c] * rcs;
     __syncthreads();

@@ -375,8 +375,14 @@ __device__ __forceinline__ Cand cta_best_in_warp0(Cand mine, CandRed* red, int64
 }
 
 // A single CTA: nothing to exchange.
+//
+// exchange<false> skips the closing CTA barrier: the results are then visible to
+// warp 0 only (after a warp barrier), which can finish the step's serial work on
+// them before the caller's own CTA barrier; after that barrier failed() tells
+// every thread whether the exchange gave up.
 struct SoloGroup {
   __device__ __forceinline__ int rank() const { return 0; }
+  template <bool kBar = true>
   __device__ __forceinline__ bool exchange(unsigned long long /*seq*/, Cand mine, unsigned long long myflags,
                                            const double* M, int ldm, int64_t q0, int k, int /*owner_chunk*/,
                                            const ExchangeOut& o) const {
@@ -386,9 +392,11 @@ struct SoloGroup {
       if (d.key != 0ull)
         for (int a = threadIdx.x; a < k; a += 32) o.x[a] = M[(int64_t)a * ldm + (d.j - q0)];
     }
-    __syncthreads();
+    if (kBar) __syncthreads();
+    else __syncwarp();
     return true;
   }
+  __device__ __forceinline__ bool failed(const ExchangeOut&) const { return false; }
 };
 
 // All CTAs of a cooperative grid, through double-buffered slots in global memory.
@@ -404,6 +412,9 @@ struct GridGroup {
 
   __device__ __forceinline__ int rank() const { return blockIdx.x; }
 
+  __device__ __forceinline__ bool failed(const ExchangeOut& o) const { return *o.fail != 0; }
+
+  template <bool kBar = true>
   __device__ bool exchange(unsigned long long seq, Cand mine, unsigned long long myflags, const double* M, int ldm,
                            int64_t q0, int k, int owner_chunk, const ExchangeOut& o) const {
     const Cand d = cta_best_in_warp0(mine, o.red, q0);
@@ -478,6 +489,10 @@ struct GridGroup {
         for (int a = lane; a < k; a += 32) o.x[a] = __ldcg(ws + 4 + a);
       }
       if (lane == 0) { *o.win = best; *o.flags = f; *o.fail = fail; }
+    }
+    if (!kBar) {
+      __syncwarp();
+      return true;
     }
     __syncthreads();
     return *o.fail == 0;

@@ -163,14 +163,8 @@ static __device__ __noinline__ int nucleus_cta(const double* G, int k, double to
       // then the reflector of the pivot column from its precomputed chain
       Cand c = cand_none();
       for (int j = t + tid; j < k; j += 32) cand_consider(c, mag_key(nrm[j]), 0, j);
-      for (int off = 16; off > 0; off >>= 1) {
-        Cand o;
-        o.key = __shfl_down_sync(0xffffffffu, c.key, off);
-        o.i = __shfl_down_sync(0xffffffffu, c.i, off);
-        o.j = __shfl_down_sync(0xffffffffu, c.j, off);
-        if (cand_better(o, c)) c = o;
-      }
-      const int pj = __shfl_sync(0xffffffffu, (c.key == 0ull) ? t : c.j, 0);
+      c = warp_best_local(c, 0);                     // every lane holds the winner
+      const int pj = (c.key == 0ull) ? t : c.j;
       house_scalars_warp(A[pj * ld + t], nrm1[pj], bc);
       if (tid == 0) {
         ctl[0] = pj;
