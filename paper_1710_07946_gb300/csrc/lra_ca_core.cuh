@@ -456,17 +456,22 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
       for (int a = mp.g; a < k; a += mp.G) M[(int64_t)a * ldm + c] = (S.pos[c] - 1 == a) ? 1.0 : 0.0;
   __syncthreads();
 
-  // ---- dominance swaps (Algorithm algdomin).  Each thread visits its entries
-  // column by column, rows ascending, so cand_take keeps the lowest (j, i) of
-  // equal keys; after the first scan, the search for the next swap runs inside
-  // the rank-1 update, on the values as they are written.
+  // ---- dominance swaps (Algorithm algdomin).  Only entries with |c| > h can
+  // cause a swap, and the search's winner is used only when it is one of them:
+  // each thread keeps its best entry above h (none if there is none), which
+  // gives the same decision and the same winner as the best of all entries.
+  // Each thread visits its entries column by column, rows ascending, so an
+  // equal key never replaces the lower (j, i); after the first scan, the search
+  // for the next swap runs inside the rank-1 update, on the values as written.
   const unsigned long long hkey = mag_key(A.h);
+  const unsigned hhi = (unsigned)__double2hiint(A.h) & 0x7fffffffu;
   int nsw = 0;
   Cand mine = cand_none();
-  unsigned bhi = 0;
+  unsigned bhi = hhi;
   for (int c = mp.c0; c < qn; c += mp.cstep) {
     if (S.pos[c]) continue;
-    for (int a = mp.g; a < k; a += mp.G) cand_take_val(mine, bhi, M[(int64_t)a * ldm + c], a, (int32_t)(q0 + c));
+    for (int a = mp.g; a < k; a += mp.G)
+      cand_take_above(mine, bhi, M[(int64_t)a * ldm + c], a, (int32_t)(q0 + c), hkey);
   }
   for (;;) {
     grp.template exchange<false>(seq, mine, myflags, M, ldm, q0, k, chunk, S.xo);
@@ -488,14 +493,14 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
     // but w.j, and the column leaving position w.i
     const int64_t wjl = w.j - q0, oldl = (int64_t)Jsel[w.i] - q0;
     mine = cand_none();
-    bhi = 0;
+    bhi = hhi;
     for (int c = mp.c0; c < qn; c += mp.cstep) {
       const double tq = S.tq[c];
       const bool cand = (c == oldl) || (S.pos[c] == 0 && c != wjl);
       for (int p = mp.g; p < k; p += mp.G) {
         const double v = (p == w.i) ? tq : fma(-S.x[p], tq, M[(int64_t)p * ldm + c]);
         M[(int64_t)p * ldm + c] = v;
-        if (cand) cand_take_val(mine, bhi, v, p, (int32_t)(q0 + c));
+        if (cand) cand_take_above(mine, bhi, v, p, (int32_t)(q0 + c), hkey);
       }
     }
     __syncthreads();

@@ -257,6 +257,17 @@ __device__ __forceinline__ void cand_take_val(Cand& best, unsigned& bhi, double 
   }
 }
 
+// cand_take_val restricted to keys above `floor`: start with bhi = the high word
+// of the floor's |v| bits, and entries at or below the floor are never taken.
+__device__ __forceinline__ void cand_take_above(Cand& best, unsigned& bhi, double v, int32_t i, int32_t j,
+                                                unsigned long long floor) {
+  const unsigned h = (unsigned)__double2hiint(v) & 0x7fffffffu;
+  if (h >= bhi) {
+    const unsigned long long key = mag_key(v);
+    if (key > floor && key > best.key) { best = Cand{key, i, j}; bhi = h; }
+  }
+}
+
 // Best candidate of the CTA (and the OR of the flags), returned to every thread.
 struct CandRed {
   Cand c[33];
