@@ -6,7 +6,9 @@ Default workload (``fmm``): the generators of an FMM / HSS matrix -- C-A CUR
 approximations of the 4096 well-separated block pairs of an octree over 2^20
 uniform points in [0,1]^3 (boxes of 64..2048 points, Laplace kernel evaluated
 on the fly, rank <= 64 adapted at tolerance 1e-6 with generator sizes staged
-28/40/64, 2 C-A loops), in the mixed form: kernel entries in FP32, pivots, LU,
+28/40/50/64 -- the schedule lra_ca_batched_tune_stages picks among the
+candidates of STAGE_CANDIDATES (--tune-stages runs it again) -- 2 C-A loops),
+in the mixed form: kernel entries in FP32, pivots, LU,
 swaps and nucleus in FP64.  One step = the batched C-A launch (all blocks,
 nuclei included) + the batched a-posteriori residual sample (16 x 16 entries
 per block, against the FP64 entries); the metric counts the blocks whose
@@ -152,19 +154,27 @@ def _fmm_oracle_chunk(args):
     return fmm_oracle_blocks(_FMM_CTX, idxs, budget_s)
 
 
+# schedules of generator sizes the stage tuner (--tune-stages) tries besides the workload's own
+STAGE_CANDIDATES = [(28, 40, 64), (28, 40, 50, 64), (28, 40, 52, 64), (28, 40, 56, 64), (28, 44, 64),
+                    (28, 36, 44, 52, 64), (24, 32, 40, 52, 64), (28, 40, 48, 64), (32, 48, 64)]
+
+
 class FmmWorkload:
     base = "fmm_laplace_1M_octree_4096blocks"
     kernel = "ca_batched_kernel"
     unit = "LRA/s"
 
     def __init__(self, npts=1 << 20, nblocks=4096, k=64, sweeps=2, tol=1e-6, q=16, s=16, entries="f64",
-                 stages=(28, 40, 64), margin=2, h=1.05):
+                 stages=(28, 40, 50, 64), margin=2, h=1.05):
         self.npts, self.nblocks, self.k, self.sweeps, self.tol, self.q, self.s = npts, nblocks, k, sweeps, tol, q, s
         self.entries, self.stages, self.margin = entries, stages, margin
         self.h = h                        # dominance threshold, between the paper's "h = 1.1 or h = 1.01"
-        sizes = "-".join(map(str, stages)) if stages else str(k)
-        self.name = f"{self.base}_k{sizes}_tol{tol:.0e}".replace("e-0", "e-") + (f"_{entries}entries" if entries != "f64"
-                                                                                 else "")
+        self.name = self._name()
+
+    def _name(self):
+        sizes = "-".join(map(str, self.stages)) if self.stages else str(self.k)
+        return f"{self.base}_k{sizes}_tol{self.tol:.0e}".replace("e-0", "e-") + (
+            f"_{self.entries}entries" if self.entries != "f64" else "")
 
     def problem(self, seed):
         """One batch of the recipe: the octree's block pairs over npts points with
@@ -234,6 +244,17 @@ class FmmWorkload:
                       "ms": {f"{t}x{c}": round(v, 3) for (t, c), v in tuned.items()}}
         d = dict(X=X, prob=prob, prob64=prob64, bt=bt, Q=torch.from_numpy(h["Q"]).to(dev),
                  S=torch.from_numpy(h["S"]).to(dev))
+        if getattr(self, "tune_stages", False) and self.stages:
+            # untimed set-up: the schedule of generator sizes, fastest of those that keep every block's
+            # sampled error within the bound
+            cands = [self.stages] + [c for c in STAGE_CANDIDATES if c != tuple(self.stages) and c[-1] == self.k]
+            table = lra.lra_ca_batched_tune_stages(bt, [(c, self.margin) for c in cands], d["Q"], d["S"],
+                                                   exact=prob64, tol=self.tol, reps=2)
+            self.stages, self.margin = tuple(bt.stages), bt.rank_margin
+            self.name = self._name()
+            self.stage_tuner = {"chosen": "/".join(map(str, self.stages)),
+                                "ms": {"/".join(map(str, c)): round(v[0], 3) for (c, m), v in table.items()},
+                                "max_err": {"/".join(map(str, c)): v[1] for (c, m), v in table.items()}}
         d["stats"] = torch.empty(len(h["blocks"]), 5, dtype=torch.float64, device=dev)
         return d
 
@@ -285,6 +306,7 @@ class FmmWorkload:
     def extra(self, res):
         info, err = res["info"], res["err"]
         return {"cta_shape_tuner": getattr(self, "tuned", None),
+                "stage_tuner": getattr(self, "stage_tuner", None),
                 "flops_per_step_counted_by_kernel": res.get("work"),
                 "rank_min_median_max": [int(info[:, 0].min()), int(np.median(info[:, 0])), int(info[:, 0].max())],
                 "generator_size_hist": {int(k): int(c) for k, c in zip(*np.unique(info[:, 6], return_counts=True))},
@@ -1829,6 +1851,7 @@ def run_lib(args, wl):
     stream = torch.cuda.current_stream(dev)
 
     wl.world, wl.shard = world, args.shard
+    wl.tune_stages = args.tune_stages
     h = wl.host(rank)
     d = wl.device(h, dev)
     if "pivots" in d:
@@ -2019,6 +2042,8 @@ def main():
     ap.add_argument("--impl", default="lib", choices=["lib", "reference"])
     ap.add_argument("--workload", default="fmm", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tune-stages", action="store_true",
+                    help="FMM batches: pick the schedule of generator sizes by lra_ca_batched_tune_stages (untimed)")
     ap.add_argument("--shard", default="lpt", choices=["lpt", "replicas"],
                     help="batched workloads on several GPUs: LPT shares of one block list, or a replica per GPU")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time for cpu_baseline")

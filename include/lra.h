@@ -725,6 +725,32 @@ lra_status lra_ca_batched_tune(const lra_problem* base, const lra_batch* batch, 
                                float* ms);
 
 /*
+ * lra_ca_batched_tune_stages -- autotuner of the staged generator sizes, i.e. of
+ * the strip widths the C-A runs of a batch go through (no counterpart in the
+ * paper, which fixes no sizes): for each candidate schedule it runs the whole
+ * batch reps times, timing each launch with CUDA events on the stream, then
+ * samples every block's error with lra_residual_sample_batched on `exact` (the
+ * same input with FP64 entries; NULL: base itself) at rows Q and columns S as
+ * that call takes them.  A schedule qualifies when every block's status is
+ * LRA_OK or a warning and every sampled relative Frobenius error (stats column
+ * 4) is <= tol.  *best receives the index of the fastest qualifying schedule,
+ * whose results are left in out; ms[i] (optional) the fastest time of schedule
+ * i and err[i] (optional) its largest sampled error (NaN if a block failed).
+ * schedules: host, nsched rows of 2 + LRA_MAX_STAGES int32 -- nstages,
+ * rank_margin, then the ascending sizes, the last equal to par->k; par's own
+ * stage fields are ignored.  out must hold C and R; stats: device scratch of
+ * nb x 5 doubles.  Blocks the calling thread; not capturable.  Errors: as
+ * lra_ca_run_batched and lra_residual_sample_batched; LRA_ERR_INVALID_ARG also
+ * when a schedule is malformed or none qualifies.
+ */
+lra_status lra_ca_batched_tune_stages(const lra_problem* base, const lra_problem* exact, const lra_batch* batch,
+                                      const lra_ca_params* par, const int32_t* I0, const lra_cur_batch* out,
+                                      void* workspace, size_t workspace_bytes, const int32_t* Q, int32_t q,
+                                      const int32_t* S, int32_t s, double* stats, double tol,
+                                      const int32_t* schedules, int32_t nsched, int32_t reps, lra_stream_t stream,
+                                      int32_t* best, float* ms, double* err);
+
+/*
  * lra_residual_sample_batched -- the a-posteriori sample of lra_residual_sample
  * for every block of a batch, in one launch: for block b, rows Q[b*q .. b*q+q)
  * and columns S[b*s .. b*s+s) (block-local, device int32) of W_b - C_b U_b R_b;

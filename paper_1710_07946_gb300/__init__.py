@@ -120,6 +120,8 @@ def _load():
     L.lra_ca_run_batched.argtypes = [P, PB, PP, vp, PCB, vp, sz, vp]
     L.lra_residual_sample_batched.argtypes = [P, PB, i32, PCB, vp, i32, vp, i32, vp, vp]
     L.lra_ca_batched_tune.argtypes = [P, PB, PP, vp, PCB, vp, sz, vp, i32, ct.POINTER(i32), ct.POINTER(i32), vp]
+    L.lra_ca_batched_tune_stages.argtypes = [P, P, PB, PP, vp, PCB, vp, sz, vp, i32, vp, i32, vp, f64, vp, i32, i32,
+                                             vp, ct.POINTER(i32), vp, vp]
     L.lra_cynical_batched_workspace_size.argtypes = [P, PB, PP, i32, i32, ct.POINTER(sz)]
     L.lra_cynical_run_batched.argtypes = [P, PB, PP, i32, i32, vp, vp, vp, PCB, vp, sz, vp]
     L.lra_cynical_batched_tune.argtypes = [P, PB, PP, i32, i32, vp, vp, vp, PCB, vp, sz, vp, i32,
@@ -154,7 +156,7 @@ def _load():
               "lra_cur_apply", "lra_cur_apply_workspace_size", "lra_residual_sample",
               "lra_residual_sample_workspace_size", "lra_profile_enable", "lra_profile_collect",
               "lra_ca_batched_workspace_size", "lra_ca_run_batched", "lra_residual_sample_batched",
-              "lra_ca_batched_tune", "lra_cynical_batched_workspace_size", "lra_cynical_run_batched",
+              "lra_ca_batched_tune", "lra_ca_batched_tune_stages", "lra_cynical_batched_workspace_size", "lra_cynical_run_batched",
               "lra_cynical_batched_tune", "lra_oversample_batched_workspace_size", "lra_oversample_batched",
               "lra_oversample_cycle_batched_workspace_size", "lra_oversample_cycle_batched", "lra_multiplier_apply",
               "lra_gather_rows", "lra_rhtcur_workspace_size", "lra_rhtcur_run", "lra_ca_lev_batched_workspace_size",
@@ -648,6 +650,53 @@ def lra_ca_batched_tune(batch: Batch, reps: int = 2, stream=None) -> dict:
            "lra_ca_batched_tune")
     batch.cb.cta_threads, batch.cb.ctas_per_sm = th.value, cs.value
     return {shp: ms[i] for i, shp in enumerate(shapes) if ms[i] >= 0}
+
+
+def lra_ca_batched_tune_stages(batch: Batch, schedules, Q: torch.Tensor, S: torch.Tensor,
+                               exact: Optional[Problem] = None, tol: float = 1e-6, reps: int = 2,
+                               stats: Optional[torch.Tensor] = None, stream=None) -> dict:
+    """Autotuner of the staged generator sizes (see lra_ca_batched_tune_stages in
+    lra.h): times the batch under every schedule, keeps the schedules under which
+    every block's sampled error (rows Q, columns S: nb x q, nb x s device int32,
+    against ``exact``'s entries) is <= tol, stores the fastest in ``batch`` (later
+    lra_ca_run_batched calls use it; its results are left in batch.out) and
+    returns {(sizes, margin): (ms, max error)}.  ``schedules``: ascending size
+    tuples ending at batch.k, or (sizes, margin) pairs (default margin: the
+    batch's).  Synchronises the stream."""
+    import numpy as np
+    rows = []
+    for sc in schedules:
+        if len(sc) == 2 and isinstance(sc[0], (tuple, list)):
+            sizes, margin = tuple(int(x) for x in sc[0]), int(sc[1])
+        else:
+            sizes, margin = tuple(int(x) for x in sc), int(batch.params.rank_margin)
+        if not 1 <= len(sizes) <= LRA_MAX_STAGES:
+            raise ValueError(f"1..{LRA_MAX_STAGES} sizes per schedule")
+        rows.append((sizes, margin))
+    tab = np.zeros((len(rows), 2 + LRA_MAX_STAGES), dtype=np.int32)
+    for i, (sizes, margin) in enumerate(rows):
+        tab[i, 0], tab[i, 1] = len(sizes), margin
+        tab[i, 2:2 + len(sizes)] = sizes
+    if stats is None:
+        stats = torch.empty(batch.nb, 5, dtype=torch.float64, device=batch.blocks.device)
+    if exact is not None and (exact.m, exact.n) != (batch.problem.m, batch.problem.n):
+        raise ValueError("exact must have the batch problem's shape")
+    ms = (ct.c_float * len(rows))()
+    err = (ct.c_double * len(rows))()
+    best = ct.c_int32()
+    pe = exact._c() if exact is not None else None
+    _check(_load().lra_ca_batched_tune_stages(
+        ct.byref(batch.pc), ct.byref(pe) if pe is not None else None, ct.byref(batch.cb), ct.byref(batch.params),
+        batch.I0.data_ptr(), ct.byref(batch.cur), batch.workspace.data_ptr(), batch.workspace.numel(),
+        _dev(Q, torch.int32, "Q").data_ptr(), Q.shape[1], _dev(S, torch.int32, "S").data_ptr(), S.shape[1],
+        _dev(stats, torch.float64, "stats").data_ptr(), float(tol), tab.ctypes.data_as(ct.c_void_p), len(rows),
+        int(reps), _stream(stream), ct.byref(best), ms, err), "lra_ca_batched_tune_stages")
+    sizes, margin = rows[best.value]
+    batch.params.nstages, batch.params.rank_margin = len(sizes), margin
+    for i in range(LRA_MAX_STAGES):
+        batch.params.k_stages[i] = sizes[i] if i < len(sizes) else 0
+    batch.stages, batch.rank_margin = sizes, margin
+    return {rows[i]: (ms[i], err[i]) for i in range(len(rows))}
 
 
 def _cyn_workspace(batch: Batch, kind: int, q: int):

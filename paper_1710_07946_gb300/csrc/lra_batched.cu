@@ -4,6 +4,7 @@
 // batched residual sample.  The kernel itself is in lra_batched_kernel.cuh.
 #include <algorithm>
 #include <cstring>
+#include <vector>
 
 #include "lra_batched_kernel.cuh"
 #include "lra_internal.h"
@@ -348,6 +349,86 @@ lra_status lra_ca_batched_tune(const lra_problem* base, const lra_batch* batch, 
   if (st != LRA_OK) return st;
   *cta_threads = kShapes[bi].threads;
   *ctas_per_sm = kShapes[bi].ctas;
+  return LRA_OK;
+}
+
+lra_status lra_ca_batched_tune_stages(const lra_problem* base, const lra_problem* exact, const lra_batch* batch,
+                                      const lra_ca_params* par, const int32_t* I0, const lra_cur_batch* out,
+                                      void* workspace, size_t workspace_bytes, const int32_t* Q, int32_t q,
+                                      const int32_t* S, int32_t s, double* stats, double tol,
+                                      const int32_t* schedules, int32_t nsched, int32_t reps, lra_stream_t stream_,
+                                      int32_t* best, float* ms, double* err) {
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (par == nullptr || batch == nullptr || schedules == nullptr || best == nullptr || stats == nullptr ||
+      nsched < 1 || reps < 1 || !(tol >= 0.0) || out == nullptr || out->C == nullptr || out->R == nullptr)
+    return LRA_ERR_INVALID_ARG;
+  const lra_problem* ex = exact ? exact : base;
+  const int nb = batch->nb;
+  int threads, ctas;
+  batch_shape(batch, &threads, &ctas);
+  std::vector<double> hst((size_t)nb * 5);
+  std::vector<int32_t> hinfo((size_t)nb * LRA_INFO_LEN);
+  cudaEvent_t e0, e1;
+  LRA_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return LRA_ERR_CUDA; }
+  lra_status st = LRA_OK;
+  int bi = -1, last = -1;
+  float bt = 0.f;
+  for (int i = 0; i < nsched && st == LRA_OK; ++i) {
+    const int32_t* sc = schedules + (size_t)i * (2 + LRA_MAX_STAGES);
+    lra_ca_params pi = *par;
+    pi.nstages = sc[0];
+    pi.rank_margin = sc[1];
+    if (pi.nstages < 1 || pi.nstages > LRA_MAX_STAGES) { st = LRA_ERR_INVALID_ARG; break; }
+    for (int t = 0; t < LRA_MAX_STAGES; ++t) pi.k_stages[t] = t < pi.nstages ? sc[2 + t] : 0;
+    DevProblem P;
+    if ((st = batched_check(base, batch, &pi, I0, out, &P)) != LRA_OK) break;
+    float fastest = -1.f;
+    for (int r = 0; r < reps && st == LRA_OK; ++r) {
+      float t = 0.f;
+      if (cudaEventRecord(e0, stream) != cudaSuccess) { st = LRA_ERR_CUDA; break; }
+      if ((st = batched_launch(P, batch, &pi, I0, out, workspace, workspace_bytes, stream, threads, ctas)) != LRA_OK)
+        break;
+      if (cudaEventRecord(e1, stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) { st = LRA_ERR_CUDA; break; }
+      if (fastest < 0.f || t < fastest) fastest = t;
+    }
+    if (st != LRA_OK) break;
+    last = i;
+    // every block: a usable status and a sampled error within tol
+    if ((st = lra_residual_sample_batched(ex, batch, par->k, out, Q, q, S, s, stats, stream_)) != LRA_OK) break;
+    if (cudaMemcpyAsync(hst.data(), stats, sizeof(double) * hst.size(), cudaMemcpyDeviceToHost, stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(hinfo.data(), out->info, sizeof(int32_t) * hinfo.size(), cudaMemcpyDeviceToHost, stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess) { st = LRA_ERR_CUDA; break; }
+    double emax = 0.0;
+    bool ok = true;
+    for (int b = 0; b < nb; ++b) {
+      const double e = hst[(size_t)b * 5 + 4];
+      const int32_t bs = hinfo[(size_t)b * LRA_INFO_LEN + 3];
+      if (!(e <= tol) || (bs != LRA_OK && bs < 16)) ok = false;
+      if (!(e <= emax)) emax = e;           // NaN propagates
+    }
+    if (ms != nullptr) ms[i] = fastest;
+    if (err != nullptr) err[i] = emax;
+    if (ok && (bi < 0 || fastest < bt)) { bt = fastest; bi = i; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != LRA_OK) return st;
+  if (bi < 0) return LRA_ERR_INVALID_ARG;
+  *best = bi;
+  if (last != bi) {                          // leave the chosen schedule's results in out
+    const int32_t* sc = schedules + (size_t)bi * (2 + LRA_MAX_STAGES);
+    lra_ca_params pb = *par;
+    pb.nstages = sc[0];
+    pb.rank_margin = sc[1];
+    for (int t = 0; t < LRA_MAX_STAGES; ++t) pb.k_stages[t] = t < pb.nstages ? sc[2 + t] : 0;
+    DevProblem P;
+    if ((st = batched_check(base, batch, &pb, I0, out, &P)) != LRA_OK) return st;
+    return batched_launch(P, batch, &pb, I0, out, workspace, workspace_bytes, stream, threads, ctas);
+  }
   return LRA_OK;
 }
 

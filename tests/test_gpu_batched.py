@@ -133,6 +133,50 @@ def test_cta_shapes_give_identical_results_and_tuner_picks_one():
         lra.lra_ca_run_batched(bt)
 
 
+def test_stage_schedule_tuner_keeps_the_error_bound():
+    """lra_ca_batched_tune_stages times every candidate schedule of generator sizes,
+    keeps those under which every block's sampled error against the FP64 entries is
+    <= tol, and leaves the fastest one's results in the batch: they equal a direct
+    run of that schedule bit for bit, and every block equals the oracle run under it
+    on the same FP32 entries.  No qualifying schedule and a malformed one are errors."""
+    import paper_1710_07946_gb300 as lra
+    p, blocks, lev = li.fmm_blocks(npts=1 << 15, leaf=64, min_size=64, max_size=2048, nblocks=96, seed=9)
+    prob64, _ = to_device(p)
+    prob = lra.Problem.kernel("laplace", prob64.X, prob64.Y, entries="f32")
+    I0 = li.block_initial_rows(blocks, 64, 3)
+    Q, S = li.block_sample_positions(blocks, 16, 16, 4)
+    Qd, Sd = torch.from_numpy(Q).cuda(), torch.from_numpy(S).cuda()
+    cands = [(28, 40, 64), ((28, 40, 52, 64), 2), (24, 64), ((32, 48, 64), 1)]
+    bt = lra.Batch(prob, blocks, 64, 2, I0, h=1.05, rank_tol=1e-6, stages=(28, 40, 64))
+    table = lra.lra_ca_batched_tune_stages(bt, cands, Qd, Sd, exact=prob64, tol=1e-6, reps=1)
+    assert len(table) == len(cands)
+    chosen = (tuple(bt.stages), bt.rank_margin)
+    ok = {key: v for key, v in table.items() if v[1] <= 1e-6}
+    assert chosen in ok and table[chosen][0] == min(v[0] for v in ok.values())
+    tuned = {key: v.cpu().numpy() for key, v in bt.out.items()}
+    direct = lra.Batch(prob, blocks, 64, 2, I0, h=1.05, rank_tol=1e-6, stages=chosen[0], rank_margin=chosen[1])
+    lra.lra_ca_run_batched(direct)
+    torch.cuda.synchronize()
+    dout = {key: v.cpu().numpy() for key, v in direct.out.items()}
+    np.testing.assert_array_equal(dout["info"], tuned["info"])
+    np.testing.assert_array_equal(dout["logvol"], tuned["logvol"])
+    for b in range(len(blocks)):        # the slots a block uses (earlier candidates may have left the rest)
+        gd, gt = direct.block(b, dout), bt.block(b, tuned)
+        for key in ("I", "J", "C", "U", "R"):
+            np.testing.assert_array_equal(gd[key], gt[key], err_msg=f"{key} of block {b}")
+    for b in range(0, len(blocks), 7):
+        r0, nr, c0, nc = (int(x) for x in blocks[b])
+        pb = li.Problem(li.SRC_LAPLACE, nr, nc, X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], entries="f32")
+        o = oracle.ca_run_adaptive(pb, chosen[0], chosen[1], 2, I0[b], h=1.05, rank_tol=1e-6)
+        g = direct.block(b, dout)
+        assert g["k"] == o["k"], (b, g["k"], o["k"])
+        check_block(o, g)
+    with pytest.raises(lra.LraError):
+        lra.lra_ca_batched_tune_stages(bt, [(28, 40, 64)], Qd, Sd, exact=prob64, tol=1e-30, reps=1)
+    with pytest.raises(lra.LraError):
+        lra.lra_ca_batched_tune_stages(bt, [(28, 40, 60)], Qd, Sd, exact=prob64, tol=1e-6, reps=1)
+
+
 def test_dense_blocks_of_mixed_sizes():
     p = li.factor_gaussian(1500, 12, 1e-4, seed=3)
     blocks = li.dense_blocks(1500, sizes=(1, 7, 40, 64, 65, 300, 900), seed=1)
@@ -204,7 +248,7 @@ def test_fmm_benchmark_workload_sampled_blocks():
 
 def test_headline_fmm_configuration_every_block():
     """The benchmark's default step exactly as bench.py builds it (2^20 points,
-    4096 block pairs, FP32 Laplace entries, staged sizes 28/40/64 with margin 2,
+    4096 block pairs, FP32 Laplace entries, staged sizes 28/40/50/64 with margin 2,
     h = 1.05, tol 1e-6, the autotuned CTA shape, then the residual sample against
     the FP64 entries): every block equals the oracle's staged run on the same
     FP32 entries -- final size, counters, status, pivots, C and R bit for bit, U
