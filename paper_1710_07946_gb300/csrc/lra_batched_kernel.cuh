@@ -122,7 +122,11 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
       st = info[3];
       swaps += info[1]; loops += info[2]; n32 += info[4]; n64 += info[5];
       if (st != LRA_OK && st < 16) break;
-      r = nucleus_cta(G, k, B.rank_tol, B.U + (size_t)b * B.kmax * B.kmax, smem);
+      // a stage whose rank sends the block on to a larger size needs only the rank
+      int knext = k;
+      for (int sx = stage; sx + 1 < B.nstages && knext <= k;) knext = min(B.stages[++sx], kb);
+      const int rank_only = (k < kb && knext > k) ? k - B.margin : KMAX + 1;
+      r = nucleus_cta(G, k, B.rank_tol, B.U + (size_t)b * B.kmax * B.kmax, smem, max(rank_only, 0));
       if (threadIdx.x == 0) s_work += 5.0 * k * k * k;          // the nucleus, nominal
       if (r < k && st == LRA_OK) st = LRA_WARN_RANK_DEFICIENT;
       if (k >= kb || r < k - B.margin) break;

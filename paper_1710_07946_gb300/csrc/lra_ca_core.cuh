@@ -208,6 +208,7 @@ struct Map2D {
 // one warp share a column when there are fewer columns than threads (G a power
 // of two), lane g taking rows p with p % G == g and meeting its column's other
 // lanes at __syncwarp; every lane of a warp runs the same loop trip counts.
+// (One thread per column with half the threads idle was measured slower.)
 struct ColMap {
   int c0, cstep, g, G;
   __device__ __forceinline__ explicit ColMap(int qn) {

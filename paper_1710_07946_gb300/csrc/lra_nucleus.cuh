@@ -102,7 +102,9 @@ __device__ __forceinline__ void house_scalars_warp(double alpha, double xn2, dou
 }
 
 // U (k x k, row-major, global or shared) <- pinv of the rank-r QRP truncation of
-// G (k x k row-major, global).  smem: nucleus_smem_bytes(k).  Returns r.
+// G (k x k row-major, global).  smem: nucleus_smem_bytes(k).  Returns r.  When
+// r >= rank_only_from only r is computed and U is left as it is (a staged run
+// that will go on to a larger size needs the rank alone).
 //
 // Every arithmetic operation, and the order of every inner product, is the one
 // the header comment states; what is parallel is only which thread runs which
@@ -115,7 +117,8 @@ __device__ __forceinline__ void house_scalars_warp(double alpha, double xn2, dou
 // reflector, in the same order as after it), and the rank-1 updates y -= c v
 // are spread over every thread.  CTAs of 64 threads run the second group's
 // chains after the first's.
-static __device__ __noinline__ int nucleus_cta(const double* G, int k, double tol, double* U, unsigned char* smem) {
+static __device__ __noinline__ int nucleus_cta(const double* G, int k, double tol, double* U, unsigned char* smem,
+                                               int rank_only_from = KMAX + 1) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int ld = nucleus_ld(k);
   const int bbase = nt >= 128 ? 64 : 0;                // first thread of the second group
@@ -229,6 +232,7 @@ static __device__ __noinline__ int nucleus_cta(const double* G, int k, double to
   }
   __syncthreads();
   const int r = ctl[1];
+  if (r >= rank_only_from) return r;                    // uniform; nothing below is needed
   for (int it = tid; it < k * k; it += nt) U[it] = 0.0;
   if (r == 0) { __syncthreads(); return 0; }
 
