@@ -24,7 +24,7 @@ namespace lra {
 // different columns hit different shared-memory banks.
 __host__ __device__ inline int nucleus_ld(int k) { return k | 1; }
 __host__ __device__ inline size_t nucleus_smem_bytes(int k) {
-  return sizeof(double) * (3 * (size_t)k * nucleus_ld(k) + 7 * (size_t)KMAX) + sizeof(int32_t) * 2 * KMAX + 64;
+  return sizeof(double) * (3 * (size_t)k * nucleus_ld(k) + 9 * (size_t)KMAX) + sizeof(int32_t) * 2 * KMAX + 64;
 }
 
 // Householder reflector of the column x[0..len) (unit stride, shared memory),
@@ -101,6 +101,19 @@ __device__ __forceinline__ void house_scalars_warp(double alpha, double xn2, dou
   if (lane == 0) { bc[0] = tau; bc[1] = scal; bc[2] = beta; }
 }
 
+// The same scalars from one thread: tau, scal, beta into out[0..2] (the two
+// divisions are independent, so their latencies overlap).
+__device__ __forceinline__ void house_scalars(double alpha, double xn2, double* out) {
+  double tau = 0.0, scal = 0.0, beta = alpha;
+  if (xn2 != 0.0) {
+    const double nrm = sqrt(fma(alpha, alpha, xn2));
+    beta = (alpha >= 0.0) ? -nrm : nrm;
+    tau = (beta - alpha) / beta;
+    scal = 1.0 / (alpha - beta);
+  }
+  out[0] = tau; out[1] = scal; out[2] = beta;
+}
+
 // U (k x k, row-major, global or shared) <- pinv of the rank-r QRP truncation of
 // G (k x k row-major, global).  smem: nucleus_smem_bytes(k).  Returns r.  When
 // r >= rank_only_from only r is computed and U is left as it is (a staged run
@@ -111,7 +124,9 @@ __device__ __forceinline__ void house_scalars_warp(double alpha, double xn2, dou
 // chain when.  A warp's FP64 instruction costs its SM sub-partition the same
 // time whatever the number of active lanes, and one chain step costs that time,
 // so the work is laid out by sub-partition: the pivot-search norms run on warps
-// 0-1 while warps 2-3 run the norms the reflector needs (rows t+1..), the
+// 0-1 while warps 2-3 run the norms the reflector needs (rows t+1..) and the
+// reflector scalars each candidate would get (a square root and two divisions,
+// about 1800 cycles of latency, that no longer follow the pivot search), the
 // reflector products with the columns of Q^T run on warps 2-3 while warps 0-1
 // run those with A's columns (Q^T is built during the QR, reflector by
 // reflector, in the same order as after it), and the rank-1 updates y -= c v
@@ -128,10 +143,10 @@ static __device__ __noinline__ int nucleus_cta(const double* G, int k, double to
   double* taus = T + (size_t)k * ld;
   double* tz = taus + KMAX;
   double* nrm = tz + KMAX;
-  double* nrm1 = nrm + KMAX;
-  double* cw = nrm1 + KMAX;                             // 2 KMAX: tau (v^T y) per column of A, then of Q^T
+  double* cw = nrm + KMAX;                              // 2 KMAX: tau (v^T y) per column of A, then of Q^T
   double* bc = cw + 2 * KMAX;
-  int32_t* perm = reinterpret_cast<int32_t*>(bc + KMAX);
+  double* hs = bc + KMAX;                               // 3 KMAX: tau, scal, beta per column
+  int32_t* perm = reinterpret_cast<int32_t*>(hs + 3 * KMAX);
   int32_t* ctl = perm + KMAX;
 
   for (int it = tid; it < k * k; it += nt) {
@@ -152,32 +167,32 @@ static __device__ __noinline__ int nucleus_cta(const double* G, int k, double to
       nrm[t + tid] = s;
     }
     {
+      // and, from it, the reflector scalars every column would get as the
+      // pivot (its sqrt and two divisions then stay off the pivot's path)
       const int g = tid - bbase;
       if (g >= 0 && g < nc) {
         const double* col = A + (size_t)(t + g) * ld;
         double s = 0.0;
         for (int i = t + 1; i < k; ++i) s = fma(col[i], col[i], s);
-        nrm1[t + g] = s;
+        house_scalars(col[t], s, hs + 3 * (t + g));
       }
     }
     __syncthreads();
     if (tid < 32) {
-      // largest squared norm, lowest column on ties (integer keys, one warp),
-      // then the reflector of the pivot column from its precomputed chain
+      // largest squared norm, lowest column on ties (integer keys, one warp)
       Cand c = cand_none();
       for (int j = t + tid; j < k; j += 32) cand_consider(c, mag_key(nrm[j]), 0, j);
       c = warp_best_local(c, 0);                     // every lane holds the winner
       const int pj = (c.key == 0ull) ? t : c.j;
-      house_scalars_warp(A[pj * ld + t], nrm1[pj], bc);
       if (tid == 0) {
         ctl[0] = pj;
-        taus[t] = bc[0];
+        taus[t] = hs[3 * pj];
         if (pj != t) { const int tp = perm[t]; perm[t] = perm[pj]; perm[pj] = tp; }
       }
     }
     __syncthreads();
     const int pj = ctl[0];
-    const double tau = bc[0], scal = bc[1], beta = bc[2];
+    const double tau = hs[3 * pj], scal = hs[3 * pj + 1], beta = hs[3 * pj + 2];
     // interchange columns t and pj; column t becomes beta e_t + v (v scaled)
     for (int i = tid; i < k; i += nt) {
       const double at = A[t * ld + i], ap = A[pj * ld + i];
