@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
     A.mixed = B.mixed;
     if (threadIdx.x == 0) s_work = 0.0;
     A.work = B.work ? &s_work : nullptr;
+    // without a multiplier the row steps' strips are C itself: the last one stays as the output
+    A.Cstrip = (Cb != nullptr && A.P.mkind == LRA_MULT_NONE) ? Cb : nullptr;
     if (B.mixed && A.P.src == LRA_KERNEL_LAPLACE) {
       A.P.X32 = B.base.X32 + 3 * r0;
       A.P.Y32 = B.base.Y32 + 3 * c0;
@@ -150,10 +152,11 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
     if (Cb != nullptr && Rb != nullptr && !(st != LRA_OK && st < 16)) {
       // C_b = W'[:, J] (nr x k) and R_b = W[I, :] (k x nc) at the final size, from
       // the final I, J that the last C-A run stored
-      for (int it = threadIdx.x; it < (int)nr * k; it += blockDim.x) {
-        const int c = it / k, a = it - c * k;
-        Cb[(int64_t)c * k + a] = c_entry(A.P, c, A.J[a]);
-      }
+      if (A.Cstrip == nullptr)
+        for (int it = threadIdx.x; it < (int)nr * k; it += blockDim.x) {
+          const int c = it / k, a = it - c * k;
+          Cb[(int64_t)c * k + a] = c_entry(A.P, c, A.J[a]);
+        }
       for (int it = threadIdx.x; it < k * (int)nc; it += blockDim.x) {
         const int a = it / (int)nc, c = it - a * (int)nc;
         Rb[(int64_t)a * nc + c] = r_entry(A.P, A.I[a], c);

@@ -44,6 +44,8 @@ struct CaArgs {
   int32_t strip_in_smem;
   int32_t mixed;       // try the FP32 certified step first (single-CTA groups)
   double* work = nullptr;   // if set (lead CTA, thread 0): += the algorithmic flops of each maxvol step
+  double* Cstrip = nullptr; // if set (no multiplier): every row step stores the strip it gathers, W'[:, J] = C
+                            // (m x k row-major), so the last one leaves the run's C there
 };
 
 // Nominal FP64 flops of one kernel entry of the problem (dense: none).
@@ -274,6 +276,13 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
   __syncthreads();
   if constexpr (!kPre) {
     if (gather_chunk(P, phase, S, k, q0, qn, ldm, mp)) atomicOr(&S.ctl[0], 1);
+    if (phase == 1 && A.Cstrip != nullptr) {
+      __syncthreads();
+      for (int it = tid; it < qn * k; it += nt) {
+        const int c = it / k, a = it - c * k;
+        A.Cstrip[(q0 + c) * k + a] = M[(int64_t)a * ldm + c];
+      }
+    }
   }
   __syncthreads();
   const unsigned long long myflags = S.ctl[0] ? FLAG_NONFINITE : 0ull;
