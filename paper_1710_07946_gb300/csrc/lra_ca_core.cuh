@@ -82,6 +82,7 @@ struct CaSmem {
   int32_t* Js;       // KMAX : current columns J
   int32_t* piv;      // KMAX : row interchanges of the warm LU
   int32_t* pos;      // ldm  : 0 = unchosen, else 1 + position in the selected set
+  int32_t* ulist;    // ldm  : the unchosen columns of the chunk, ascending (warm replay, back substitution)
   Cand* win;         // the winner of the last exchange
   unsigned long long* flags;
   double* bc;        // 4 doubles of broadcast scratch
@@ -104,6 +105,7 @@ __host__ __device__ inline size_t ca_smem_fixed(int k, int ldm) {
   b += align16(sizeof(double) * LOGBUF);
   b += align16(sizeof(double) * (size_t)ldm);
   b += align16(sizeof(int32_t) * KMAX) * 3;
+  b += align16(sizeof(int32_t) * (size_t)ldm);
   b += align16(sizeof(int32_t) * (size_t)ldm);
   b += align16(sizeof(Cand));
   b += align16(sizeof(unsigned long long));
@@ -129,6 +131,7 @@ __device__ inline CaSmem ca_smem_carve(unsigned char* base, int k, int ldm, doub
   S.Js = reinterpret_cast<int32_t*>(base + o); o += align16(sizeof(int32_t) * KMAX);
   S.piv = reinterpret_cast<int32_t*>(base + o); o += align16(sizeof(int32_t) * KMAX);
   S.pos = reinterpret_cast<int32_t*>(base + o); o += align16(sizeof(int32_t) * (size_t)ldm);
+  S.ulist = reinterpret_cast<int32_t*>(base + o); o += align16(sizeof(int32_t) * (size_t)ldm);
   S.win = reinterpret_cast<Cand*>(base + o); o += align16(sizeof(Cand));
   S.flags = reinterpret_cast<unsigned long long*>(base + o); o += align16(sizeof(unsigned long long));
   S.bc = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * 4);
@@ -228,6 +231,21 @@ struct ColMap {
     return wc0 < qn ? (qn - wc0 + cstep - 1) / cstep : 0;
   }
 };
+
+// The chunk's unchosen columns (pos == 0), ascending, into S.ulist by warp 0
+// (a ballot per 32 columns); returns their number to warp 0's lanes.
+__device__ inline int list_unchosen_warp(const CaSmem& S, int qn) {
+  const int lane = threadIdx.x & 31;
+  int n = 0;
+  for (int c0 = 0; c0 < qn; c0 += 32) {
+    const int c = c0 + lane;
+    const bool f = c < qn && S.pos[c] == 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, f);
+    if (f) S.ulist[n + __popc(bal & ((1u << lane) - 1u))] = c;
+    n += __popc(bal);
+  }
+  return n;
+}
 
 // Gather the k x qn chunk of the strip; returns nonzero if any entry is not finite.
 __device__ inline int gather_chunk(const DevProblem& P, int phase, const CaSmem& S, int k, int64_t q0, int qn,
@@ -348,20 +366,27 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
       cold = true;
       __syncthreads();
     } else {
-      if (tid == 0)
-        for (int t = 0; t < k; ++t) {
+      if (warp == 0) {
+        for (int t = lane; t < k; t += 32) {
           const int64_t jt = Jsel[t];
           if (jt >= q0 && jt < q0 + qn) S.pos[jt - q0] = t + 1;
         }
+        __syncwarp();
+        const int nu = list_unchosen_warp(S, qn);
+        if (lane == 0) S.ctl[5] = nu;
+      }
       __syncthreads();
-      // replay the row interchanges and eliminations on every column, one column
+      // replay the row interchanges and eliminations on the unchosen columns (the
+      // chosen ones become unit columns after the back substitution), one column
       // (or one group of lanes) at a time: the columns are independent
       {
-        const ColMap cm(qn);
-        const int trips = cm.trips(qn);
+        const int nu = S.ctl[5];
+        const ColMap cm(nu);
+        const int trips = cm.trips(nu);
         for (int u = 0; u < trips; ++u) {
-          const int c = cm.c0 + u * cm.cstep;
-          const bool act = c < qn;
+          const int ix = cm.c0 + u * cm.cstep;
+          const bool act = ix < nu;
+          const int c = act ? S.ulist[ix] : 0;
           for (int t = 0; t < k; ++t) {
             const int r = S.piv[t];
             if (act && r != t && cm.g == 0) {
@@ -370,7 +395,7 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
               M[(int64_t)r * ldm + c] = tmp;
             }
             if (cm.G > 1) __syncwarp();
-            if (act && !S.pos[c]) {
+            if (act) {
               const double mt = M[(int64_t)t * ldm + c];
               int p = t + 1;
               p += (cm.g - p % cm.G + cm.G) % cm.G;
@@ -435,14 +460,21 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
   // The owner of row i scales it (x_i = b_i * (1/U0_ii)) right after its last
   // update, so one barrier per row suffices.
   for (int i = tid; i < k; i += nt) S.rdiag[i] = 1.0 / LU[i * ldl + i];
+  if (cold && warp == 0) {              // the unchosen columns after the cold LU (warm steps listed them above)
+    const int nu = list_unchosen_warp(S, qn);
+    if (lane == 0) S.ctl[5] = nu;
+  }
   __syncthreads();
   {
-    // column by column (lanes of one column meet at __syncwarp): no CTA barrier
-    const ColMap cm(qn);
-    const int trips = cm.trips(qn);
+    // column by column over the unchosen columns (lanes of one column meet at
+    // __syncwarp): no CTA barrier
+    const int nu = S.ctl[5];
+    const ColMap cm(nu);
+    const int trips = cm.trips(nu);
     for (int u = 0; u < trips; ++u) {
-      const int c = cm.c0 + u * cm.cstep;
-      const bool act = c < qn && S.pos[c] == 0;
+      const int ix = cm.c0 + u * cm.cstep;
+      const bool act = ix < nu;
+      const int c = act ? S.ulist[ix] : 0;
       if (act && (k - 1) % cm.G == cm.g)
         M[(int64_t)(k - 1) * ldm + c] = M[(int64_t)(k - 1) * ldm + c] * S.rdiag[k - 1];
       for (int i = k - 1; i >= 1; --i) {
