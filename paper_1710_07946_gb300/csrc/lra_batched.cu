@@ -149,8 +149,8 @@ struct BatchShape { int threads, ctas; };
 constexpr BatchShape kShapes[] = {{512, 1}, {256, 2}, {128, 4}, {64, 8}};
 constexpr int kNumShapes = 4;
 
-static size_t ca_need(int k, int ldm, bool strip) {
-  return ca_smem_fixed(k, ldm) + (strip ? sizeof(double) * (size_t)k * ldm : 0);
+static size_t ca_need(int k, int ldm, bool strip, bool mixed) {
+  return ca_smem_fixed(k, ldm, mixed) + (strip ? sizeof(double) * (size_t)k * ldm : 0);
 }
 
 static void* batched_kernel_ptr(bool mixed, int threads) {
@@ -178,10 +178,10 @@ static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int6
   // reserves per CTA and the kernel's static arrays
   const size_t budget = std::min(dev.smem_optin, (size_t)per_sm / ctas - 1024) - 512;
   const int ldm = (int)std::min<int64_t>(max_len, 1 << 30);
-  size_t smem = std::max(ca_need(kmax, ldm, true), nucleus_smem_bytes(kmax));
-  if (smem > budget) smem = budget;
-  if (ca_need(kmax, ldm, false) > smem || nucleus_smem_bytes(kmax) > smem) return LRA_ERR_INVALID_ARG;
   const bool mixed = par->mode == LRA_MODE_MIXED && mixed_supported(P);
+  size_t smem = std::max(ca_need(kmax, ldm, true, mixed), nucleus_smem_bytes(kmax));
+  if (smem > budget) smem = budget;
+  if (ca_need(kmax, ldm, false, mixed) > smem || nucleus_smem_bytes(kmax) > smem) return LRA_ERR_INVALID_ARG;
   const void* kern = batched_kernel_ptr(mixed, threads);
   LRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
@@ -192,7 +192,7 @@ static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int6
   pl->grid = std::min(occ, ctas) * dev.sms;         // resident CTAs of the persistent launch
   pl->smem = smem;
   // global strip scratch when the largest strip does not fit beside the fixed part
-  pl->scratch_stride = (size_t)kmax * kmax + (ca_need(kmax, ldm, true) > smem ? (size_t)kmax * max_len : 0);
+  pl->scratch_stride = (size_t)kmax * kmax + (ca_need(kmax, ldm, true, mixed) > smem ? (size_t)kmax * max_len : 0);
   pl->scratch_stride = align_up(pl->scratch_stride, 32);
   pl->off_pts = align_up(256 + sizeof(double) * pl->scratch_stride * pl->grid, 256);
   pl->bytes = pl->off_pts;

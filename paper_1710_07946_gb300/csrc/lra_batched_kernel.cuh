@@ -115,9 +115,9 @@ __global__ void __launch_bounds__(NTB, MINB) ca_batched_kernel(BatchArgs B) {
     for (;;) {
       A.k = k;
       A.I0 = (nrun == 0) ? I0b : s_I0;
-      A.strip_in_smem = ca_smem_fixed(k, A.ldm) + sizeof(double) * (size_t)k * A.ldm <= B.smem_bytes;
+      A.strip_in_smem = ca_smem_fixed(k, A.ldm, MIXED) + sizeof(double) * (size_t)k * A.ldm <= B.smem_bytes;
       A.gstrip = A.strip_in_smem ? nullptr : gstrip;
-      const CaSmem S = ca_smem_carve(smem, k, A.ldm, A.gstrip);
+      const CaSmem S = ca_smem_carve(smem, k, A.ldm, A.gstrip, MIXED);
       ca_loop<SoloGroup, MIXED>(SoloGroup{}, A, S);
       __syncthreads();
       ++nrun;

@@ -71,8 +71,8 @@ struct Cert;           // lra_mixed.cuh
 
 // Shared-memory layout of the C-A kernels (all offsets in bytes, 16-aligned).
 struct CaSmem {
-  double* LU;        // k*ldl : U0 (cold) or the pivoted LU of B (warm)
-  double* Lm;        // k*ldl : multipliers of the warm LU
+  double* LU;        // k*ldl : U0 (cold) or the pivoted LU of B (warm), its multipliers below the diagonal
+  double* Lm;        // k*ldl : the FP32 certified steps' multipliers and bounds (null when not carved)
   double* x;         // KMAX : the exchanged column
   double* lmul;      // KMAX : multipliers of the current elimination step
   double* rdiag;     // KMAX : reciprocals of the U0 diagonal
@@ -98,9 +98,11 @@ constexpr int LOGBUF = 64;
 
 __host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~size_t(15); }
 
-__host__ __device__ inline size_t ca_smem_fixed(int k, int ldm) {
+// lm: with the Lm region (the FP32 certified steps' multipliers and bounds);
+// the FP64 steps keep their multipliers in the LU's strictly lower triangle.
+__host__ __device__ inline size_t ca_smem_fixed(int k, int ldm, bool lm = true) {
   size_t b = 0;
-  b += align16(sizeof(double) * (size_t)k * (k | 1)) * 2;
+  b += align16(sizeof(double) * (size_t)k * (k | 1)) * (lm ? 2 : 1);
   b += align16(sizeof(double) * KMAX) * 3;
   b += align16(sizeof(double) * LOGBUF);
   b += align16(sizeof(double) * (size_t)ldm);
@@ -117,11 +119,12 @@ __host__ __device__ inline size_t ca_smem_fixed(int k, int ldm) {
   return b;
 }
 
-__device__ inline CaSmem ca_smem_carve(unsigned char* base, int k, int ldm, double* gchunk) {
+__device__ inline CaSmem ca_smem_carve(unsigned char* base, int k, int ldm, double* gchunk, bool lm = true) {
   CaSmem S;
   size_t o = 0;
   S.LU = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * (size_t)k * (k | 1));
-  S.Lm = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * (size_t)k * (k | 1));
+  S.Lm = nullptr;
+  if (lm) { S.Lm = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * (size_t)k * (k | 1)); }
   S.x = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * KMAX);
   S.lmul = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * KMAX);
   S.rdiag = reinterpret_cast<double*>(base + o); o += align16(sizeof(double) * KMAX);
@@ -335,10 +338,12 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
           S.ctl[1] = (pv == 0.0);
         }
         // multipliers l_p = B[p][t] * (1/pivot) of the rows below t after the
-        // interchange (row r then holds row t's entry), kept in Lm for the replay
-        if (pv != 0.0)
-          for (int p = t + 1 + lane; p < k; p += 32)
-            S.Lm[p * ldl + t] = ((p == r) ? LU[t * ldl + t] : LU[p * ldl + t]) * rp;
+        // interchange (row r then holds row t's entry)
+        double l0 = 0.0, l1 = 0.0;
+        if (pv != 0.0) {
+          if (t + 1 + lane < k) { const int p = t + 1 + lane; l0 = ((p == r) ? LU[t * ldl + t] : LU[p * ldl + t]) * rp; }
+          if (t + 33 + lane < k) { const int p = t + 33 + lane; l1 = ((p == r) ? LU[t * ldl + t] : LU[p * ldl + t]) * rp; }
+        }
         __syncwarp();
         // interchange rows t and r in columns t.. only: column t' < t keeps the
         // multipliers of step t' in the row positions of that step, the order in
@@ -347,6 +352,12 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
           for (int j = t + lane; j < k; j += 32) {
             const double tmp = LU[t * ldl + j]; LU[t * ldl + j] = LU[r * ldl + j]; LU[r * ldl + j] = tmp;
           }
+        __syncwarp();
+        // the multipliers go below the diagonal of column t, where the LU keeps them
+        if (pv != 0.0) {
+          if (t + 1 + lane < k) LU[(t + 1 + lane) * ldl + t] = l0;
+          if (t + 33 + lane < k) LU[(t + 33 + lane) * ldl + t] = l1;
+        }
       }
       __syncthreads();
       if (S.ctl[1]) { fallback = 1; break; }          // same decision in every CTA
@@ -357,7 +368,7 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
         const int w = k - t - 1;
         for (int e = tid; e < w * w; e += nt) {
           const int p = t + 1 + e / w, j = t + 1 + e % w;
-          LU[p * ldl + j] = fma(-S.Lm[p * ldl + t], LU[t * ldl + j], LU[p * ldl + j]);
+          LU[p * ldl + j] = fma(-LU[p * ldl + t], LU[t * ldl + j], LU[p * ldl + j]);
         }
       }
       __syncthreads();
@@ -400,7 +411,7 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
               int p = t + 1;
               p += (cm.g - p % cm.G + cm.G) % cm.G;
               for (; p < k; p += cm.G)
-                M[(int64_t)p * ldm + c] = fma(-S.Lm[p * ldl + t], mt, M[(int64_t)p * ldm + c]);
+                M[(int64_t)p * ldm + c] = fma(-LU[p * ldl + t], mt, M[(int64_t)p * ldm + c]);
             }
             if (cm.G > 1) __syncwarp();
           }
