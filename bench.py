@@ -169,6 +169,7 @@ class FmmWorkload:
         self.npts, self.nblocks, self.k, self.sweeps, self.tol, self.q, self.s = npts, nblocks, k, sweeps, tol, q, s
         self.entries, self.stages, self.margin = entries, stages, margin
         self.h = h                        # dominance threshold, between the paper's "h = 1.1 or h = 1.01"
+        self.pair_min_len = 512           # larger blocks run on CTA pairs
         self.name = self._name()
 
     def _name(self):
@@ -228,6 +229,7 @@ class FmmWorkload:
                 "generator_sizes": (f"staged {'/'.join(map(str, self.stages))}, grow while nucleus rank >= "
                                     f"size - {self.margin}" if self.stages else "fixed min(k_max, rows, cols)"),
                 "rank_tol": self.tol, "h": self.h,
+                "cta_pairs": f"blocks with more than {self.pair_min_len} rows or columns, each on 2 CTAs",
                 "sweeps": self.sweeps, "residual_sample": f"{self.q}x{self.s} per block"}
 
     def device(self, h, dev):
@@ -237,8 +239,9 @@ class FmmWorkload:
         X = torch.from_numpy(p.X).to(dev)
         prob = lra.Problem.kernel("laplace", X, X, entries=self.entries)
         prob64 = lra.Problem.kernel("laplace", X, X)
+        # blocks with more than 512 rows or columns run first, each on a pair of CTAs (lra_batch.pair_blocks)
         bt = lra.Batch(prob, h["blocks"], self.k, self.sweeps, h["I0"], h=self.h, rank_tol=self.tol,
-                       stages=self.stages, rank_margin=self.margin)
+                       stages=self.stages, rank_margin=self.margin, pair_min_len=self.pair_min_len)
         tuned = lra.lra_ca_batched_tune(bt, reps=2)          # untimed set-up: CTA shape autotuner
         self.tuned = {"chosen": f"{bt.cb.cta_threads}x{bt.cb.ctas_per_sm}",
                       "ms": {f"{t}x{c}": round(v, 3) for (t, c), v in tuned.items()}}
@@ -322,8 +325,9 @@ class FmmWorkload:
         import paper_1710_07946_gb300 as lra
         bt0 = d["bt"]
         bt1 = lra.Batch(d["prob"], h["blocks"], self.k, self.sweeps, h["I0"], h=self.h, rank_tol=self.tol,
-                        stages=self.stages, rank_margin=self.margin)
+                        stages=self.stages, rank_margin=self.margin, pair_min_len=self.pair_min_len)
         bt1.cb.cta_threads, bt1.cb.ctas_per_sm = bt0.cb.cta_threads, bt0.cb.ctas_per_sm
+        assert bt1.cb.pair_blocks == bt0.cb.pair_blocks
         pin = lambda t: t.cpu().pin_memory()
         # every per-problem input is uploaded each step: the points, the block descriptors (rows, columns,
         # output offsets, processing order), the initial rows I0 and the residual sample positions Q, S

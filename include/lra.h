@@ -398,6 +398,12 @@ typedef struct {
   int32_t cta_threads;     /* CTA shape of the batched kernel: threads per CTA and CTAs  */
   int32_t ctas_per_sm;     /* per SM, one of lra_ca_batched_shapes (0, 0: the library's
                               default 512 x 1; lra_ca_batched_tune picks the fastest)    */
+  int32_t pair_blocks;     /* 0 .. nb: lra_ca_run_batched runs the first pair_blocks
+                              entries of the order each on a pair of CTAs that split its
+                              strips (the shapes with 512 or 256 threads; FP64 mode), the
+                              rest on one CTA each: large blocks then keep a short
+                              critical path while small ones fill the SMs.  The results
+                              do not depend on it.  Other batched calls ignore it.       */
 } lra_batch;
 
 /* Outputs of a batch (device, caller-owned).  Block b has slots for k_b =

@@ -61,7 +61,8 @@ class _Params(ct.Structure):
 
 class _Batch(ct.Structure):
     _fields_ = [("blocks", ct.c_void_p), ("offsets", ct.c_void_p), ("order", ct.c_void_p), ("nb", ct.c_int32),
-                ("max_len", ct.c_int64), ("cta_threads", ct.c_int32), ("ctas_per_sm", ct.c_int32)]
+                ("max_len", ct.c_int64), ("cta_threads", ct.c_int32), ("ctas_per_sm", ct.c_int32),
+                ("pair_blocks", ct.c_int32)]
 
 
 class _CurBatch(ct.Structure):
@@ -562,12 +563,13 @@ class Batch:
 
     def __init__(self, problem: Problem, blocks, k: int, sweeps: int, I0, h: float = 1.01, rank_tol: float = 1e-6,
                  max_swaps: int = 1000, order="lpt", device=None, mode: int = LRA_MODE_FP64, stages=None,
-                 rank_margin: int = 2, store_factors: bool = True):
+                 rank_margin: int = 2, store_factors: bool = True, pair_min_len: Optional[int] = None):
         """``stages``: ascending generator sizes ending at k (the size of each block is
         fitted to its nucleus rank: a larger stage runs while rank >= size - rank_margin);
         None runs every block at min(k, rows, cols).  ``store_factors`` False keeps
         only I, J, U (no C, R buffers: a matrix-free lra_hmatvec recomputes their
-        entries)."""
+        entries).  ``pair_min_len``: blocks with more rows or columns than this run
+        first, each on a pair of CTAs (lra_batch.pair_blocks; None: none do)."""
         import numpy as np
         blocks = np.ascontiguousarray(np.asarray(blocks, dtype=np.int64).reshape(-1, 4))
         nb = len(blocks)
@@ -579,6 +581,14 @@ class Batch:
         offs[1:, 1] = np.cumsum(rsz)[:-1]
         if isinstance(order, str) and order == "lpt":
             order = np.argsort(-(blocks[:, 1] * blocks[:, 3]), kind="stable").astype(np.int32)
+        npairs = 0
+        if pair_min_len is not None:
+            if order is None:
+                order = np.arange(nb, dtype=np.int32)
+            order = np.asarray(order, dtype=np.int32)
+            big = np.maximum(blocks[order, 1], blocks[order, 3]) > int(pair_min_len)
+            order = np.concatenate([order[big], order[~big]]).astype(np.int32)
+            npairs = int(big.sum())
         self.problem, self.k, self.sweeps, self.nb = problem, int(k), int(sweeps), nb
         self.blocks_np, self.offs_np, self.kb = blocks, offs, kb
         self.params = _params(k, sweeps, h, rank_tol, max_swaps, mode, stages, rank_margin)
@@ -599,6 +609,7 @@ class Batch:
         self.cb.blocks, self.cb.offsets = self.blocks.data_ptr(), self.offs.data_ptr()
         self.cb.order = self.order.data_ptr() if self.order is not None else None
         self.cb.nb, self.cb.max_len = nb, int(max(blocks[:, 1].max(), blocks[:, 3].max()))
+        self.cb.pair_blocks = npairs
         self.work = torch.zeros(nb, dtype=torch.float64, device=dev)   # per-block algorithmic flops
         self.cur = _CurBatch()
         for f in ("I", "J", "C", "U", "R", "logvol", "info"):

@@ -136,6 +136,8 @@ struct BatchPlan {
   int grid;
   size_t smem;
   size_t scratch_stride;
+  size_t off_pairs;         // CTA pairs' exchange slots and abort words (pairs only)
+  size_t pairs_bytes;
   size_t off_pts;
   size_t bytes;
 };
@@ -153,9 +155,10 @@ static size_t ca_need(int k, int ldm, bool strip, bool mixed) {
   return ca_smem_fixed(k, ldm, mixed) + (strip ? sizeof(double) * (size_t)k * ldm : 0);
 }
 
-static void* batched_kernel_ptr(bool mixed, int threads) {
-  if (threads == 512) return batched_kernel_512(mixed);
-  if (threads == 256) return batched_kernel_256(mixed);
+static void* batched_kernel_ptr(bool mixed, int threads, bool pairs = false) {
+  if (threads == 512) return batched_kernel_512(mixed, pairs);
+  if (threads == 256) return batched_kernel_256(mixed, pairs);
+  if (pairs) return nullptr;
   if (threads == 128) return batched_kernel_128(mixed);
   return batched_kernel_64(mixed);
 }
@@ -166,8 +169,15 @@ static bool shape_known(int threads, int ctas) {
   return false;
 }
 
+// Whether a launch of this shape runs the batch's first pair_blocks blocks on CTA
+// pairs: the 512- and 256-thread shapes in FP64 mode.
+static bool use_pairs(const DevProblem& P, const lra_batch* batch, const lra_ca_params* par, int threads) {
+  const bool mixed = par->mode == LRA_MODE_MIXED && mixed_supported(P);
+  return batch->pair_blocks > 0 && !mixed && (threads == 512 || threads == 256);
+}
+
 static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int64_t max_len, int threads, int ctas,
-                             BatchPlan* pl) {
+                             BatchPlan* pl, bool pairs = false) {
   const int32_t kmax = par->k;
   DeviceInfo dev;
   lra_status st = current_device_info(&dev);
@@ -182,7 +192,8 @@ static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int6
   size_t smem = std::max(ca_need(kmax, ldm, true, mixed), nucleus_smem_bytes(kmax));
   if (smem > budget) smem = budget;
   if (ca_need(kmax, ldm, false, mixed) > smem || nucleus_smem_bytes(kmax) > smem) return LRA_ERR_INVALID_ARG;
-  const void* kern = batched_kernel_ptr(mixed, threads);
+  const void* kern = batched_kernel_ptr(mixed, threads, pairs);
+  if (kern == nullptr) return LRA_ERR_INVALID_ARG;       // no pair variant of this shape or mode
   LRA_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int occ = 0;
   LRA_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem));
@@ -194,7 +205,11 @@ static lra_status batch_plan(const DevProblem& P, const lra_ca_params* par, int6
   // global strip scratch when the largest strip does not fit beside the fixed part
   pl->scratch_stride = (size_t)kmax * kmax + (ca_need(kmax, ldm, true, mixed) > smem ? (size_t)kmax * max_len : 0);
   pl->scratch_stride = align_up(pl->scratch_stride, 32);
-  pl->off_pts = align_up(256 + sizeof(double) * pl->scratch_stride * pl->grid, 256);
+  pl->off_pairs = align_up(256 + sizeof(double) * pl->scratch_stride * pl->grid, 256);
+  pl->pairs_bytes = pairs ? align_up(sizeof(double) * 4 * SLOT * (size_t)(pl->grid / 2) +
+                                     sizeof(unsigned int) * (size_t)(pl->grid / 2), 256) : 0;
+  if (pairs && (pl->grid & 1)) return LRA_ERR_INVALID_ARG;
+  pl->off_pts = pl->off_pairs + pl->pairs_bytes;
   pl->bytes = pl->off_pts;
   if (mixed && P.src == LRA_KERNEL_LAPLACE)
     pl->bytes = align_up(pl->off_pts + sizeof(float) * 3 * (size_t)(P.m + P.n), 256);
@@ -229,7 +244,8 @@ lra_status lra_ca_batched_workspace_size(const lra_problem* base, const lra_batc
   lra_status first = LRA_ERR_INVALID_ARG;
   for (int i = 0; i < kNumShapes; ++i) {
     BatchPlan pl;
-    st = batch_plan(P, par, batch->max_len, kShapes[i].threads, kShapes[i].ctas, &pl);
+    st = batch_plan(P, par, batch->max_len, kShapes[i].threads, kShapes[i].ctas, &pl,
+                    use_pairs(P, batch, par, kShapes[i].threads));
     if (st == LRA_ERR_INVALID_ARG) continue;
     if (st != LRA_OK) return st;
     first = LRA_OK;
@@ -247,7 +263,8 @@ lra_status batched_check(const lra_problem* base, const lra_batch* batch, const 
   lra_status st = make_dev_problem(base, nullptr, P);
   if (st != LRA_OK) return st;
   if (batch == nullptr || par == nullptr || out == nullptr || I0 == nullptr) return LRA_ERR_INVALID_ARG;
-  if (batch->blocks == nullptr || batch->offsets == nullptr || batch->nb < 1 || batch->max_len < 1)
+  if (batch->blocks == nullptr || batch->offsets == nullptr || batch->nb < 1 || batch->max_len < 1 ||
+      batch->pair_blocks < 0 || batch->pair_blocks > batch->nb)
     return LRA_ERR_INVALID_ARG;
   if (par->k < 1 || par->k > KMAX || par->sweeps < 1 || par->max_swaps < 0 || !(par->h >= 1.0) ||
       !(par->h < 1e300) || !(par->rank_tol >= 0.0) || !(par->rank_tol < 1.0) ||
@@ -264,7 +281,8 @@ lra_status batched_launch(const DevProblem& P, const lra_batch* batch, const lra
   if (!shape_known(threads, ctas)) return LRA_ERR_INVALID_ARG;
   BatchPlan pl;
   lra_status st;
-  if ((st = batch_plan(P, par, batch->max_len, threads, ctas, &pl)) != LRA_OK) return st;
+  const bool pairs = use_pairs(P, batch, par, threads);
+  if ((st = batch_plan(P, par, batch->max_len, threads, ctas, &pl, pairs)) != LRA_OK) return st;
   if (workspace == nullptr || workspace_bytes < pl.bytes || (reinterpret_cast<uintptr_t>(workspace) & 255u))
     return LRA_ERR_WORKSPACE;
   unsigned char* ws = static_cast<unsigned char*>(workspace);
@@ -306,11 +324,35 @@ lra_status batched_launch(const DevProblem& P, const lra_batch* batch, const lra
     if ((st = points_to_f32(P.Y, P.n, X32 + 3 * P.m, stream)) != LRA_OK) return st;
   }
   LRA_CUDA_TRY(cudaMemsetAsync(ws, 0, 256, stream));
+  if (pairs) {
+    // the pairs' exchange slots and abort words start at zero in every launch
+    A.nteam = batch->pair_blocks;
+    A.tslots = reinterpret_cast<double*>(ws + pl.off_pairs);
+    A.tabort = reinterpret_cast<unsigned int*>(ws + pl.off_pairs + sizeof(double) * 4 * SLOT * (size_t)(pl.grid / 2));
+    LRA_CUDA_TRY(cudaMemsetAsync(ws + pl.off_pairs, 0, pl.pairs_bytes, stream));
+  }
   {
     LaunchScope ls(stream, "ca_batched_kernel");
-    const void* kern = batched_kernel_ptr(A.mixed != 0, pl.threads);
+    const void* kern = batched_kernel_ptr(A.mixed != 0, pl.threads, pairs);
     void* args[] = {&A};
-    LRA_CUDA_TRY(cudaLaunchKernel(kern, dim3(pl.grid), dim3(pl.threads), args, pl.smem, stream));
+    if (pairs) {
+      // the two CTAs of a pair wait for each other: a cooperative launch makes the
+      // whole grid resident at once
+      cudaLaunchConfig_t cfg;
+      std::memset(&cfg, 0, sizeof(cfg));
+      cfg.gridDim = dim3(pl.grid);
+      cfg.blockDim = dim3(pl.threads);
+      cfg.dynamicSmemBytes = pl.smem;
+      cfg.stream = stream;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      LRA_CUDA_TRY(cudaLaunchKernelExC(&cfg, kern, args));
+    } else {
+      LRA_CUDA_TRY(cudaLaunchKernel(kern, dim3(pl.grid), dim3(pl.threads), args, pl.smem, stream));
+    }
   }
   return cuda_status(cudaGetLastError());
 }
@@ -341,7 +383,8 @@ lra_status lra_ca_batched_tune(const lra_problem* base, const lra_batch* batch, 
   int bi = -1;
   st = time_shapes(kNumShapes, reps, stream, [&](int i) {
     BatchPlan pl;
-    const lra_status fit = batch_plan(P, par, batch->max_len, kShapes[i].threads, kShapes[i].ctas, &pl);
+    const lra_status fit = batch_plan(P, par, batch->max_len, kShapes[i].threads, kShapes[i].ctas, &pl,
+                                      use_pairs(P, batch, par, kShapes[i].threads));
     if (fit != LRA_OK) return fit;
     return batched_launch(P, batch, par, I0, out, workspace, workspace_bytes, stream, kShapes[i].threads,
                           kShapes[i].ctas);

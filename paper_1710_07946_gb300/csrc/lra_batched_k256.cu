@@ -4,7 +4,8 @@
 
 namespace lra {
 
-void* batched_kernel_256(bool mixed) {
+void* batched_kernel_256(bool mixed, bool pairs) {
+  if (pairs) return mixed ? nullptr : reinterpret_cast<void*>(ca_batched_kernel<false, 256, 2, true>);
   return mixed ? reinterpret_cast<void*>(ca_batched_kernel<true, 256, 2>)
                : reinterpret_cast<void*>(ca_batched_kernel<false, 256, 2>);
 }

@@ -4,7 +4,8 @@
 
 namespace lra {
 
-void* batched_kernel_512(bool mixed) {
+void* batched_kernel_512(bool mixed, bool pairs) {
+  if (pairs) return mixed ? nullptr : reinterpret_cast<void*>(ca_batched_kernel<false, 512, 1, true>);
   return mixed ? reinterpret_cast<void*>(ca_batched_kernel<true, 512, 1>)
                : reinterpret_cast<void*>(ca_batched_kernel<false, 512, 1>);
 }

@@ -46,6 +46,8 @@ struct CaArgs {
   double* work = nullptr;   // if set (lead CTA, thread 0): += the algorithmic flops of each maxvol step
   double* Cstrip = nullptr; // if set (no multiplier): every row step stores the strip it gathers, W'[:, J] = C
                             // (m x k row-major), so the last one leaves the run's C there
+  unsigned long long* seq = nullptr;   // the group's exchange round counter when it outlives one run (a CTA
+                                       // pair that runs several problems); null: the run counts from 0
 };
 
 // Nominal FP64 flops of one kernel entry of the problem (dense: none).

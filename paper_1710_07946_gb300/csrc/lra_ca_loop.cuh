@@ -61,7 +61,7 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
     if (lead) for (int e = tid; e < LRA_INFO_LEN; e += nt) A.info[e] = (e == 3) ? LRA_ERR_INVALID_ARG : 0;
     return;
   }
-  unsigned long long seq = 0;
+  unsigned long long seq = A.seq ? *A.seq : 0ull;
   int status = LRA_OK, err = LRA_OK, total = 0, loops = 0, n32 = 0, n64 = 0;
   for (int s = 0; s < A.sweeps; ++s) {
     const bool cold0 = s == 0 && A.J0 == nullptr;
@@ -81,6 +81,7 @@ __device__ void ca_loop(const Group& grp, const CaArgs& A, const CaSmem& S) {
     __syncthreads();
     if (s > 0 && r0.nswaps == 0 && r1.nswaps == 0) break;
   }
+  if (A.seq) *A.seq = seq;                         // every thread keeps its own copy of the counter
   if (err != LRA_OK) {
     if (lead && tid == 0) {
       A.info[0] = 0; A.info[1] = total; A.info[2] = loops; A.info[3] = err;

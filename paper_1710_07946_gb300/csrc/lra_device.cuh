@@ -420,8 +420,9 @@ struct GridGroup {
   double* slots;             // [2][nblk][SLOT]
   unsigned int* abort;       // 0, or the status of the CTA that gave up
   int nblk;
+  int first = 0;             // the group is CTAs first .. first + nblk - 1 of the grid
 
-  __device__ __forceinline__ int rank() const { return blockIdx.x; }
+  __device__ __forceinline__ int rank() const { return (int)blockIdx.x - first; }
 
   __device__ __forceinline__ bool failed(const ExchangeOut& o) const { return *o.fail != 0; }
 
@@ -435,7 +436,7 @@ struct GridGroup {
       {
         // post: the warp writes the column (a lane per entry), then lane 0 the
         // candidate and, after a fence and the warp barrier, the tag (release)
-        double* me = buf + (size_t)blockIdx.x * SLOT;
+        double* me = buf + (size_t)rank() * SLOT;
         unsigned long long* mu = reinterpret_cast<unsigned long long*>(me);
         if (d.key != 0ull)
           for (int a = lane; a < k; a += 32) me[4 + a] = M[(int64_t)a * ldm + (d.j - q0)];

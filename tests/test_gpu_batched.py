@@ -133,6 +133,42 @@ def test_cta_shapes_give_identical_results_and_tuner_picks_one():
         lra.lra_ca_run_batched(bt)
 
 
+@pytest.mark.parametrize("shape", [(512, 1), (256, 2)])
+def test_cta_pairs_for_large_blocks(shape):
+    """Blocks larger than pair_min_len run on pairs of CTAs that split their strips
+    (lra_batch.pair_blocks): every block equals the oracle's staged run on the same
+    FP32 entries, bit for bit in the pivots, and the outputs equal a run without
+    pairs."""
+    import paper_1710_07946_gb300 as lra
+    p, blocks, lev = li.fmm_blocks(npts=1 << 15, leaf=64, min_size=64, max_size=2048, nblocks=96, seed=8)
+    prob64, _ = to_device(p)
+    prob = lra.Problem.kernel("laplace", prob64.X, prob64.Y, entries="f32")
+    stages = (28, 40, 50, 64)
+    I0 = li.block_initial_rows(blocks, 64, 5)
+    mx = np.maximum(blocks[:, 1], blocks[:, 3])
+    lim = int(np.sort(mx)[len(mx) * 2 // 3])          # the largest third run on pairs
+    bp = lra.Batch(prob, blocks, 64, 2, I0, h=1.05, rank_tol=1e-6, stages=stages, rank_margin=2, pair_min_len=lim)
+    assert 0 < bp.cb.pair_blocks < len(blocks)
+    bp.cb.cta_threads, bp.cb.ctas_per_sm = shape
+    lra.lra_ca_run_batched(bp)
+    bs = lra.Batch(prob, blocks, 64, 2, I0, h=1.05, rank_tol=1e-6, stages=stages, rank_margin=2)
+    lra.lra_ca_run_batched(bs)
+    torch.cuda.synchronize()
+    op = {key: v.cpu().numpy() for key, v in bp.out.items()}
+    os_ = {key: v.cpu().numpy() for key, v in bs.out.items()}
+    np.testing.assert_array_equal(op["info"], os_["info"])
+    for b in range(len(blocks)):
+        gp, gs = bp.block(b, op), bs.block(b, os_)
+        for key in ("I", "J", "C", "U", "R"):
+            np.testing.assert_array_equal(gp[key], gs[key], err_msg=f"{key} of block {b}")
+        r0, nr, c0, nc = (int(x) for x in blocks[b])
+        if mx[b] > lim or b % 5 == 0:
+            pb = li.Problem(li.SRC_LAPLACE, nr, nc, X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], entries="f32")
+            o = oracle.ca_run_adaptive(pb, stages, 2, 2, I0[b], h=1.05, rank_tol=1e-6)
+            assert gp["k"] == o["k"], (b, gp["k"], o["k"])
+            check_block(o, gp)
+
+
 def test_stage_schedule_tuner_keeps_the_error_bound():
     """lra_ca_batched_tune_stages times every candidate schedule of generator sizes,
     keeps those under which every block's sampled error against the FP64 entries is
