@@ -1,7 +1,9 @@
 // lra_batched.cu -- many independent C-A CUR approximations (the generators of
 // the neutered block columns of an HSS / FMM matrix) in one persistent launch:
-// the launch plan per CTA shape, the autotuner over the shapes, and the
-// batched residual sample.  The kernel itself is in lra_batched_kernel.cuh.
+// the launch plan per CTA shape (with or without CTA pairs for the largest
+// blocks), the autotuners over the shapes and over the staged generator sizes,
+// and the batched residual sample.  The kernel itself is in
+// lra_batched_kernel.cuh.
 #include <algorithm>
 #include <cstring>
 #include <vector>

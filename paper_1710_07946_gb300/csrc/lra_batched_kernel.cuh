@@ -5,8 +5,11 @@
 // runs the whole C-A loop of a block, then its nucleus, on its own: the block's
 // strips sit in the CTA's shared memory when they fit, otherwise in the CTA's
 // slice of a global scratch area.  The per-block arithmetic is the single-CTA
-// path of lra_ca_run, operation for operation.  The kernel is built in one
-// translation unit per CTA shape (lra_batched_k*.cu).
+// path of lra_ca_run, operation for operation.  Optionally the first blocks
+// of the order run first, each on a pair of CTAs that split its strips and
+// meet through the grid exchange of lra_ca_run (a separate instantiation,
+// launched cooperatively).  The kernel is built in one translation unit per
+// CTA shape (lra_batched_k*.cu).
 #pragma once
 
 #include "lra_ca_loop.cuh"

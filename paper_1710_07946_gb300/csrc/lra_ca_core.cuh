@@ -1,6 +1,6 @@
 // lra_ca_core.cuh -- one maxvol step of cross-approximation and the whole C-A
 // loop, written once over a "group" of CTAs that share the search (a single CTA,
-// or every CTA of a cooperative grid).
+// every CTA of a cooperative grid, or a pair of CTAs of a batched launch).
 //
 // Paper: Algorithm algdomin (dominant submatrix by swaps), Algorithm alggos (its
 // LUP initialisation), the C-A loop of Section "CUR LRA; primitive, cynical, and
@@ -274,7 +274,9 @@ __device__ inline int gather_chunk(const DevProblem& P, int phase, const CaSmem&
 // a_p * (1/pivot), column-sweep back substitution with the reciprocals of the
 // U0 diagonal, swaps t_q = C[i*][q] * (1/c*), C[p][q] = fma(-x_p, t_q, C[p][q]).
 // The k x k LU is stored with the odd row stride ldl = k | 1 (no bank conflicts
-// when a warp walks down one of its columns).  kPre: the strip is already in
+// when a warp walks down one of its columns); a warm LU keeps its multipliers
+// below the diagonal.  The column-local phases (replay, back substitution) run
+// over the list of the unchosen columns.  kPre: the strip is already in
 // the chunk M (a single CTA holding all of it, rows 0..k-1); nothing is
 // gathered and the warm start reads B = M[:, Jsel].
 template <class Group, bool kPre = false>

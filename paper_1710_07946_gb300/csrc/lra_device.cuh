@@ -335,7 +335,8 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 // candidate's column, reads all posts and keeps the best one (the order above is
 // total, so all CTAs agree) with its column.  Results land in shared memory:
 //   win  -- the winning candidate,  x[0..k) -- its column,  flags -- OR of flags.
-// Two CTA barriers per exchange: warp results -> warp 0 does the rest.
+// Two CTA barriers per exchange: warp results -> warp 0 does the rest (one when
+// the caller lets warp 0 finish its step first: exchange<false>).
 // Returns false (in every thread) if a wait expired or another CTA aborted.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ Cand warp_best(Cand c) {
