@@ -544,15 +544,21 @@ __device__ StepResult maxvol_step(const Group& grp, const CaArgs& A, const CaSme
     if (w.key <= hkey) break;                     // no |c| > h left (or no candidate)
     if (nsw >= A.max_swaps) { res.status = LRA_WARN_NOT_CONVERGED; break; }
     const double rcs = S.bc[0];
-    for (int c = tid; c < qn; c += nt) S.tq[c] = M[(int64_t)w.i * ldm + c] * rcs;
-    __syncthreads();
+    // t_q = C[i*][q] * (1/c*): with one thread to a column (mp.G == 1, uniform)
+    // that thread reads row i* itself before it updates the column; otherwise
+    // all t_q first, then the update
+    const bool own_tq = mp.G == 1;
+    if (!own_tq) {
+      for (int c = tid; c < qn; c += nt) S.tq[c] = M[(int64_t)w.i * ldm + c] * rcs;
+      __syncthreads();
+    }
     // the columns outside the selected set after this swap: the unselected ones
     // but w.j, and the column leaving position w.i
     const int64_t wjl = w.j - q0, oldl = (int64_t)Jsel[w.i] - q0;
     mine = cand_none();
     bhi = hhi;
     for (int c = mp.c0; c < qn; c += mp.cstep) {
-      const double tq = S.tq[c];
+      const double tq = own_tq ? M[(int64_t)w.i * ldm + c] * rcs : S.tq[c];
       const bool cand = (c == oldl) || (S.pos[c] == 0 && c != wjl);
       for (int p = mp.g; p < k; p += mp.G) {
         const double v = (p == w.i) ? tq : fma(-S.x[p], tq, M[(int64_t)p * ldm + c]);
