@@ -409,6 +409,16 @@ lra_status lra_ca_batched_tune_stages(const lra_problem* base, const lra_problem
     return LRA_ERR_INVALID_ARG;
   const lra_problem* ex = exact ? exact : base;
   const int nb = batch->nb;
+  // every schedule well formed (host checks, before any CUDA call)
+  for (int i = 0; i < nsched; ++i) {
+    const int32_t* sc = schedules + (size_t)i * (2 + LRA_MAX_STAGES);
+    lra_ca_params pi = *par;
+    pi.nstages = sc[0];
+    pi.rank_margin = sc[1];
+    if (pi.nstages < 1 || pi.nstages > LRA_MAX_STAGES) return LRA_ERR_INVALID_ARG;
+    for (int t = 0; t < LRA_MAX_STAGES; ++t) pi.k_stages[t] = t < pi.nstages ? sc[2 + t] : 0;
+    if (!stages_valid(&pi)) return LRA_ERR_INVALID_ARG;
+  }
   int threads, ctas;
   batch_shape(batch, &threads, &ctas);
   std::vector<double> hst((size_t)nb * 5);

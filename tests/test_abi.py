@@ -89,3 +89,49 @@ def test_binding_structs_match_the_header(tmp_path):
         assert got[(cname, "size")] == ctypes.sizeof(py), cname
         for f, _ in py._fields_:
             assert got[(cname, f)] == getattr(py, f).offset, (cname, f)
+
+
+def test_new_arguments_rejected_without_gpu():
+    """The CTA-pair count, the stage tuner's schedules and the single-LRA grid size
+    are checked on the host, before any CUDA call."""
+    import numpy as np
+    import paper_1710_07946_gb300 as lra
+    L = lra._load()
+    nb, k = 4, 8
+    X = np.zeros((64, 3))                           # never read: the calls stop at the host checks
+    pc = lra._Problem()
+    pc.src, pc.dtype, pc.m, pc.n = 1, 0, 64, 64     # Laplace kernel, FP64 entries
+    pc.X = pc.Y = X.ctypes.data
+    blocks = np.array([[0, 16, 16, 16]] * nb, dtype=np.int64)
+    offs = np.zeros((nb, 2), dtype=np.int64)
+    cb = lra._Batch()
+    cb.blocks, cb.offsets, cb.nb, cb.max_len = blocks.ctypes.data, offs.ctypes.data, nb, 16
+    par = lra._params(k, 2, 1.05, 1e-6, 100, lra.LRA_MODE_FP64)
+    dummy = np.zeros(4096, dtype=np.float64)
+    cur = lra._CurBatch()
+    for f in ("I", "J", "C", "U", "R", "logvol", "info"):
+        setattr(cur, f, dummy.ctypes.data)
+    I0 = np.zeros((nb, k), dtype=np.int32)
+    cb.pair_blocks = nb + 1                          # more pair blocks than blocks
+    assert L.lra_ca_run_batched(ctypes.byref(pc), ctypes.byref(cb), ctypes.byref(par), I0.ctypes.data,
+                                ctypes.byref(cur), dummy.ctypes.data, dummy.nbytes, None) == lra.LRA_ERR_INVALID_ARG
+    cb.pair_blocks = -1
+    assert L.lra_ca_run_batched(ctypes.byref(pc), ctypes.byref(cb), ctypes.byref(par), I0.ctypes.data,
+                                ctypes.byref(cur), dummy.ctypes.data, dummy.nbytes, None) == lra.LRA_ERR_INVALID_ARG
+    cb.pair_blocks = 0
+    Q = np.zeros((nb, 2), dtype=np.int32)
+    best = ctypes.c_int32()
+    for sched in ([[2, 2, 4, 6] + [0] * 6], [[0, 2] + [0] * 8], [[2, -1, 4, 8] + [0] * 6]):
+        tab = np.array(sched, dtype=np.int32)     # sizes not ending at k; no sizes; negative margin
+        st = L.lra_ca_batched_tune_stages(ctypes.byref(pc), None, ctypes.byref(cb), ctypes.byref(par),
+                                          I0.ctypes.data, ctypes.byref(cur), dummy.ctypes.data, dummy.nbytes,
+                                          Q.ctypes.data, 2, Q.ctypes.data, 2, dummy.ctypes.data, 1e-6,
+                                          tab.ctypes.data, len(tab), 1, None, ctypes.byref(best), None, None)
+        assert st == lra.LRA_ERR_INVALID_ARG, sched
+    p1 = lra._params(k, 2, 1.05, 1e-6, 100, lra.LRA_MODE_FP64, ctas=-1)
+    pc1 = lra._Problem()
+    pc1.src, pc1.dtype, pc1.m, pc1.n = 1, 0, 64, 64
+    pc1.X = pc1.Y = X.ctypes.data
+    size = ctypes.c_size_t()
+    assert L.lra_ca_workspace_size(ctypes.byref(pc1), ctypes.byref(p1), None, ctypes.byref(size)) == \
+        lra.LRA_ERR_INVALID_ARG
