@@ -531,19 +531,6 @@ def multiplier_dense(p):
     return M
 
 
-def ca_run_blocks(p, blocks, k_max, sweeps, I0s, h=1.01, max_swaps=1000, rank_tol=1e-6):
-    """Independent C-A runs over the submatrices W[r0:r0+nr, c0:c0+nc] of a
-    kernel problem (the generators of the neutered block columns of an
-    HSS / FMM matrix).  Returns a list of ca_run results."""
-    from lra_inputs import Problem
-    out = []
-    for b, (r0, nr, c0, nc) in enumerate(np.asarray(blocks)):
-        sub = Problem(p.src, int(nr), int(nc), X=p.X[r0:r0 + nr], Y=p.Y[c0:c0 + nc], ell=p.ell)
-        k = min(k_max, int(nr), int(nc))
-        out.append(ca_run(sub, k, sweeps, I0s[b][:k], h, max_swaps, rank_tol))
-    return out
-
-
 def gauss_cur_apply(X, Y, I, J, ell, x):
     """y = C U R x with C = K(X, Y_J), R = K(X_I, Y), U = K(X_I, Y_J)^{-1},
     K(x, y) = exp(-|x - y|^2 / (2 ell^2)) (FMM stage (iii) product on a
