@@ -747,7 +747,8 @@ lra_status lra_ca_batched_tune(const lra_problem* base, const lra_batch* batch, 
  * stage fields are ignored.  out must hold C and R; stats: device scratch of
  * nb x 5 doubles.  Blocks the calling thread; not capturable.  Errors: as
  * lra_ca_run_batched and lra_residual_sample_batched; LRA_ERR_INVALID_ARG also
- * when a schedule is malformed or none qualifies.
+ * when a schedule is malformed (every schedule is checked on the host before
+ * the first launch) or none qualifies.
  */
 lra_status lra_ca_batched_tune_stages(const lra_problem* base, const lra_problem* exact, const lra_batch* batch,
                                       const lra_ca_params* par, const int32_t* I0, const lra_cur_batch* out,
