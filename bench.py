@@ -4,12 +4,13 @@
 
 Default workload (``fmm``): the generators of an FMM / HSS matrix -- C-A CUR
 approximations of the 4096 well-separated block pairs of an octree over 2^20
-uniform points in [0,1]^3 (boxes of 64..2048 points, Laplace kernel evaluated
+uniform points in [0,1]^3 (boxes of ~200..2048 points, Laplace kernel evaluated
 on the fly, rank <= 64 adapted at tolerance 1e-6 with generator sizes staged
 28/40/50/64 -- the schedule lra_ca_batched_tune_stages picks among the
 candidates of STAGE_CANDIDATES (--tune-stages runs it again) -- 2 C-A loops),
 in the mixed form: kernel entries in FP32, pivots, LU,
-swaps and nucleus in FP64.  One step = the batched C-A launch (all blocks,
+swaps and nucleus in FP64.  The blocks above 512 points run first, each on a
+pair of CTAs; the CTA shape is picked by lra_ca_batched_tune (untimed set-up).  One step = the batched C-A launch (all blocks,
 nuclei included) + the batched a-posteriori residual sample (16 x 16 entries
 per block, against the FP64 entries); the metric counts the blocks whose
 sampled relative Frobenius error is <= 1e-6.  The plain FP64 forms of the same
@@ -23,10 +24,14 @@ Inputs are seeded, synthetic and resident in HBM before the timed region; L2 is
 flushed (a 256 MiB write, untimed) before every timed step; each step is timed
 with CUDA events on the launching stream, and the library's own per-launch
 events give the dominant kernel's duration.  ``e2e`` repeats the steps through
-the same public API from pinned host buffers, copies included.  Under torchrun
-each rank runs an independent problem of the same size (weak scaling, no
-collective on the data path); rank 0 prints one JSON line with the whole-job
-throughput over the slowest rank.  ``--impl reference`` times the FP64 CPU
+the same public API from pinned host buffers, copies included (a two-slot
+pipeline: a step's read-back overlaps the next step's compute; both slots are
+used in the untimed warm-up).  Under torchrun the FMM batches are one block
+list of N recipe batches, split across the ranks by LPT on rows x cols x k
+(``--shard replicas``: an independent batch per rank); every other workload
+runs an independent replica per rank.  No collective on the data path (weak
+scaling); rank 0 prints one JSON line with the whole-job throughput over the
+slowest rank.  ``--impl reference`` times the FP64 CPU
 oracle on a bounded sample of the same workload (rank 0 only).
 """
 from __future__ import annotations
